@@ -1,0 +1,311 @@
+"""FP64 CPU oracle of the non-smooth Newton time stepper (ctypes binding).
+
+TEST INFRASTRUCTURE ONLY.  The oracle is the plain, slow, double-precision C
+implementation in ``oracle.c`` of Macklin et al. 2019 (Algorithm 1, Sec. 6-9,
+App. A-B).  Only the test suite, ``__graft_entry__.smoke()`` and the CPU
+baseline leg of ``bench.py`` may import this package.  It shares no code with
+the CUDA library in ``paper_1907_04587_gb300``; both consume the same scene
+dictionaries produced by ``paper_1907_04587_gb300.scenes``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+NCP_FB, NCP_MIN = 0, 1
+R_NONE, R_H2, R_EFFMASS = 0, 1, 2
+GS_OFF, GS_PARTICLES = 0, 1
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so with gcc (plain C99, -O2, no fast-math)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(
+            os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "oracle.h"))):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+_dp = C.POINTER(C.c_double)
+_ip = C.POINTER(C.c_int32)
+
+
+class _Scene(C.Structure):
+    _fields_ = [
+        ("n_bodies", C.c_int32), ("kind", _ip), ("pos", _dp), ("quat", _dp), ("vel", _dp),
+        ("omega", _dp), ("mass", _dp), ("inertia", _dp),
+        ("n_contacts", C.c_int32), ("c_body", _ip), ("c_pa", _dp), ("c_pb", _dp), ("c_n", _dp),
+        ("c_d", _dp), ("c_mu", _dp),
+        ("n_joints", C.c_int32), ("j_body", _ip), ("j_pa", _dp), ("j_pb", _dp), ("j_axa", _dp),
+        ("j_axb", _dp), ("j_compliance", _dp),
+        ("n_tets", C.c_int32), ("t_v", _ip), ("t_rest", _dp), ("t_E", _dp), ("t_nu", _dp),
+    ]
+
+
+class _Params(C.Structure):
+    _fields_ = [
+        ("h", C.c_double), ("gravity", C.c_double * 3), ("newton_iters", C.c_int32),
+        ("cr_iters", C.c_int32), ("damping", C.c_double), ("eps", C.c_double),
+        ("tol_rel", C.c_double), ("cr_tol_mode", C.c_int32), ("ncp", C.c_int32),
+        ("rscale", C.c_int32), ("geom_stiffness", C.c_int32),
+    ]
+
+
+class _Stats(C.Structure):
+    _fields_ = [("newton_done", C.c_int32), ("cr_total", C.c_int32), ("merit0", C.c_double),
+                ("merit_first", C.c_double), ("merit_final", C.c_double)]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(build())
+        L = _lib
+        L.orc_create.restype = C.c_void_p
+        L.orc_create.argtypes = [C.POINTER(_Scene), C.POINTER(_Params)]
+        L.orc_destroy.argtypes = [C.c_void_p]
+        L.orc_num_rows.argtypes = [C.c_void_p]
+        L.orc_num_dofs.argtypes = [C.c_void_p]
+        L.orc_step.argtypes = [C.c_void_p, _dp, C.POINTER(_Stats)]
+        L.orc_get_state.argtypes = [C.c_void_p, _dp, _dp, _dp, _dp]
+        L.orc_set_state.argtypes = [C.c_void_p, _dp, _dp, _dp, _dp]
+        L.orc_get_lambda.argtypes = [C.c_void_p, _dp]
+        L.orc_get_merit_history.argtypes = [C.c_void_p, _dp, C.c_int32]
+        L.orc_get_merit_history.restype = C.c_int32
+        L.orc_linearize.argtypes = [C.c_void_p, C.c_int32, _dp] + [_dp] * 8
+        L.orc_apply_A.argtypes = [C.c_void_p, _dp, _dp]
+        L.orc_pcr.argtypes = [C.c_void_p, C.c_int32, _dp, _dp]
+        L.orc_pcr.restype = C.c_int32
+        L.orc_eval_constraints.argtypes = [C.c_void_p, _dp, _dp]
+        L.orc_fb.restype = C.c_double
+        L.orc_fb.argtypes = [C.c_double, C.c_double]
+        for f in ("orc_fb_contact", "orc_min_contact"):
+            getattr(L, f).argtypes = [C.c_double, C.c_double, C.c_double, _dp, _dp, _dp]
+        for f in ("orc_w_fb", "orc_w_min"):
+            getattr(L, f).restype = C.c_double
+            getattr(L, f).argtypes = [C.c_double] * 4
+        L.orc_nh_params.argtypes = [C.c_double, C.c_double, _dp, _dp, _dp]
+        L.orc_nh_energy.restype = C.c_double
+        L.orc_nh_energy.argtypes = [_dp, C.c_double, C.c_double, C.c_double]
+        L.orc_nh_grad_hess.argtypes = [_dp, C.c_double, C.c_double, C.c_double, _dp, _dp]
+        L.orc_svd3.argtypes = [_dp, _dp, _dp, _dp]
+        L.orc_basis.argtypes = [_dp, _dp, _dp]
+    return _lib
+
+
+def _d(a, shape=None):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    if shape is not None:
+        a = a.reshape(shape)
+    return a
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if a.dtype == np.float64:
+        return a.ctypes.data_as(_dp)
+    return a.ctypes.data_as(_ip)
+
+
+DEFAULT_PARAMS = dict(h=1.0 / 60.0, gravity=(0.0, 0.0, -9.81), newton_iters=4, cr_iters=20,
+                      damping=0.75, eps=1e-6, tol_rel=0.0, cr_tol_mode=0, ncp=NCP_FB,
+                      rscale=R_EFFMASS, geom_stiffness=GS_PARTICLES)
+
+
+class Oracle:
+    """One oracle context over a scene dictionary (see ``scenes.py``)."""
+
+    def __init__(self, scene: dict, **params):
+        L = lib()
+        p = dict(DEFAULT_PARAMS)
+        p.update(params)
+        self.params = p
+        nb = len(scene["mass"])
+        self._keep = {}
+
+        def arr(name, dtype, shape):
+            if name in scene and scene[name] is not None and np.size(scene[name]):
+                a = np.ascontiguousarray(np.asarray(scene[name], dtype=dtype).reshape(shape))
+            else:
+                a = np.zeros(shape, dtype=dtype)
+            self._keep[name] = a
+            return a
+
+        nc = int(np.shape(scene.get("c_body", np.zeros((0, 2))))[0])
+        nj = int(np.shape(scene.get("j_body", np.zeros((0, 2))))[0])
+        nt = int(np.shape(scene.get("t_v", np.zeros((0, 4))))[0])
+        s = _Scene()
+        s.n_bodies = nb
+        s.kind = _ptr(arr("kind", np.int32, (nb,)))
+        s.pos = _ptr(arr("pos", np.float64, (nb, 3)))
+        s.quat = _ptr(arr("quat", np.float64, (nb, 4)))
+        s.vel = _ptr(arr("vel", np.float64, (nb, 3)))
+        s.omega = _ptr(arr("omega", np.float64, (nb, 3)))
+        s.mass = _ptr(arr("mass", np.float64, (nb,)))
+        s.inertia = _ptr(arr("inertia", np.float64, (nb, 3)))
+        s.n_contacts = nc
+        s.c_body = _ptr(arr("c_body", np.int32, (nc, 2)))
+        s.c_pa = _ptr(arr("c_pa", np.float64, (nc, 3)))
+        s.c_pb = _ptr(arr("c_pb", np.float64, (nc, 3)))
+        s.c_n = _ptr(arr("c_n", np.float64, (nc, 3)))
+        s.c_d = _ptr(arr("c_d", np.float64, (nc,)))
+        s.c_mu = _ptr(arr("c_mu", np.float64, (nc,)))
+        s.n_joints = nj
+        s.j_body = _ptr(arr("j_body", np.int32, (nj, 2)))
+        s.j_pa = _ptr(arr("j_pa", np.float64, (nj, 3)))
+        s.j_pb = _ptr(arr("j_pb", np.float64, (nj, 3)))
+        s.j_axa = _ptr(arr("j_axa", np.float64, (nj, 3)))
+        s.j_axb = _ptr(arr("j_axb", np.float64, (nj, 3)))
+        s.j_compliance = _ptr(arr("j_compliance", np.float64, (nj,)))
+        s.n_tets = nt
+        s.t_v = _ptr(arr("t_v", np.int32, (nt, 4)))
+        s.t_rest = _ptr(arr("t_rest", np.float64, (nt, 4, 3)))
+        s.t_E = _ptr(arr("t_E", np.float64, (nt,)))
+        s.t_nu = _ptr(arr("t_nu", np.float64, (nt,)))
+        pr = _Params()
+        pr.h = p["h"]
+        pr.gravity = (C.c_double * 3)(*p["gravity"])
+        pr.newton_iters = p["newton_iters"]
+        pr.cr_iters = p["cr_iters"]
+        pr.damping = p["damping"]
+        pr.eps = p["eps"]
+        pr.tol_rel = p["tol_rel"]
+        pr.cr_tol_mode = p["cr_tol_mode"]
+        pr.ncp = p["ncp"]
+        pr.rscale = p["rscale"]
+        pr.geom_stiffness = p["geom_stiffness"]
+        self._s, self._p = s, pr
+        self.ctx = L.orc_create(C.byref(s), C.byref(pr))
+        if not self.ctx:
+            raise ValueError("oracle rejected the scene")
+        self.nb, self.nc, self.nj, self.nt = nb, nc, nj, nt
+        self.R = L.orc_num_rows(self.ctx)
+        self.D = L.orc_num_dofs(self.ctx)
+        self.last_stats = None
+
+    def __del__(self):
+        if getattr(self, "ctx", None):
+            lib().orc_destroy(self.ctx)
+            self.ctx = None
+
+    def step(self, lambda0=None):
+        st = _Stats()
+        l0 = None if lambda0 is None else _d(lambda0, (self.R,))
+        lib().orc_step(self.ctx, _ptr(l0), C.byref(st))
+        self.last_stats = dict(newton_done=st.newton_done, cr_total=st.cr_total, merit0=st.merit0,
+                               merit_first=st.merit_first, merit_final=st.merit_final)
+        return self.last_stats
+
+    def get_state(self):
+        pos = np.zeros((self.nb, 3)); quat = np.zeros((self.nb, 4))
+        vel = np.zeros((self.nb, 3)); omega = np.zeros((self.nb, 3))
+        lib().orc_get_state(self.ctx, _ptr(pos), _ptr(quat), _ptr(vel), _ptr(omega))
+        return dict(pos=pos, quat=quat, vel=vel, omega=omega)
+
+    def set_state(self, pos=None, quat=None, vel=None, omega=None):
+        a = [None if x is None else _d(x) for x in (pos, quat, vel, omega)]
+        lib().orc_set_state(self.ctx, *[_ptr(x) for x in a])
+
+    def get_lambda(self):
+        out = np.zeros(self.R)
+        if self.R:
+            lib().orc_get_lambda(self.ctx, _ptr(out))
+        return out
+
+    def merit_history(self):
+        out = np.zeros(4096)
+        n = lib().orc_get_merit_history(self.ctx, _ptr(out), 4096)
+        return out[:n]
+
+    def linearize(self, n_before=0, lambda0=None):
+        R, D = self.R, self.D
+        out = dict(J=np.zeros((R, D)), Hinv=np.zeros((D, D)), C=np.zeros((R, R)), g=np.zeros(D),
+                   hvec=np.zeros(R), b=np.zeros(R), u=np.zeros(D), lam=np.zeros(R))
+        l0 = None if lambda0 is None else _d(lambda0, (R,))
+        lib().orc_linearize(self.ctx, n_before, _ptr(l0), _ptr(out["J"]), _ptr(out["Hinv"]), _ptr(out["C"]),
+                            _ptr(out["g"]), _ptr(out["hvec"]), _ptr(out["b"]), _ptr(out["u"]), _ptr(out["lam"]))
+        return out
+
+    def apply_A(self, x):
+        x = _d(x, (self.R,))
+        y = np.zeros(self.R)
+        lib().orc_apply_A(self.ctx, _ptr(x), _ptr(y))
+        return y
+
+    def eval_constraints(self, with_jacobian=True):
+        c = np.zeros(self.R)
+        J = np.zeros((self.R, self.D)) if with_jacobian else None
+        lib().orc_eval_constraints(self.ctx, _ptr(c), _ptr(J))
+        return c, J
+
+    def pcr(self, iters):
+        x = np.zeros(self.R)
+        hist = np.zeros(iters + 1)
+        k = lib().orc_pcr(self.ctx, iters, _ptr(x), _ptr(hist))
+        return x, hist[:k + 1]
+
+
+# ---- scalar helpers for pin tests ------------------------------------------------
+
+def fb(a, b):
+    return lib().orc_fb(a, b)
+
+
+def fb_contact(Cn, lam, r):
+    o = [C.c_double() for _ in range(3)]
+    lib().orc_fb_contact(Cn, lam, r, *[C.byref(x) for x in o])
+    return tuple(x.value for x in o)
+
+
+def min_contact(Cn, lam, r):
+    o = [C.c_double() for _ in range(3)]
+    lib().orc_min_contact(Cn, lam, r, *[C.byref(x) for x in o])
+    return tuple(x.value for x in o)
+
+
+def w_fb(vt, lf, mu_ln, r):
+    return lib().orc_w_fb(vt, lf, mu_ln, r)
+
+
+def w_min(vt, lf, mu_ln, r):
+    return lib().orc_w_min(vt, lf, mu_ln, r)
+
+
+def nh_params(E, nu):
+    o = [C.c_double() for _ in range(3)]
+    lib().orc_nh_params(E, nu, *[C.byref(x) for x in o])
+    return tuple(x.value for x in o)
+
+
+def nh_energy(s, C1, D1, alpha):
+    return lib().orc_nh_energy(_ptr(_d(s, (3,))), C1, D1, alpha)
+
+
+def nh_grad_hess(s, C1, D1, alpha):
+    g = np.zeros(3); H = np.zeros(9)
+    lib().orc_nh_grad_hess(_ptr(_d(s, (3,))), C1, D1, alpha, _ptr(g), _ptr(H))
+    return g, H.reshape(3, 3)
+
+
+def svd3(F):
+    U = np.zeros(9); s = np.zeros(3); V = np.zeros(9)
+    lib().orc_svd3(_ptr(_d(F, (9,))), _ptr(U), _ptr(s), _ptr(V))
+    return U.reshape(3, 3), s, V.reshape(3, 3)
+
+
+def basis(n):
+    t1 = np.zeros(3); t2 = np.zeros(3)
+    lib().orc_basis(_ptr(_d(n, (3,))), _ptr(t1), _ptr(t2))
+    return t1, t2
