@@ -1,0 +1,189 @@
+/*
+ * nsn.h -- C ABI of the GB300 (sm_103a) non-smooth Newton time stepper.
+ *
+ * Implements one time step of Algorithm 1 of Macklin, Erleben, Mueller,
+ * Mueller, "Non-Smooth Newton Methods for Deformable Multi-Body Dynamics"
+ * (ACM TOG 38(5), 2019) on one GPU:
+ *   - per-row evaluation of Fischer-Burmeister contact rows with the
+ *     effective-mass complementarity preconditioner (Sec. 4.2, 7, App. A.1),
+ *     smooth isotropic friction rows with compliance W (Sec. 4.3, App. A.2),
+ *     revolute joint rows (Sec. 3.1-3.2) and stable Neo-Hookean compliance
+ *     rows (Sec. 9.1-9.2.2, App. B), plus the diagonal geometric-stiffness
+ *     shift of particle masses (Sec. 8.3);
+ *   - a matrix-free, Jacobi-preconditioned conjugate-residual solve (Sec. 8.2)
+ *     of the Schur system [J H~^-1 J^T + C + eps I] dl = (1/h)(J H~^-1 g - h)
+ *     (Eq. schur_system, Sec. 8.4), then du = H~^-1 (h J^T dl - g) and the
+ *     damped update of Sec. 6.2 / 8.1.
+ *
+ * Conventions (shared with the input generators):
+ *   - SI units; gravity and h in nsn_config.  Quaternions (w, x, y, z),
+ *     angular velocity in the world frame (kinematic map G of Sec. 9.4).
+ *   - Bodies receive ids 0..nb-1 in the order added.  -1 denotes the static
+ *     world in constraint records.
+ *   - Rows: contact c owns rows 3c (normal), 3c+1, 3c+2 (friction along the
+ *     orthonormal basis of Duff et al. 2017 built from n); then joint j owns
+ *     5 rows (3 positional, 2 angular); then tet k owns 3 rows (principal
+ *     stretches s1 >= s2 >= |s3|).  Multipliers are forces (N); impulses are
+ *     h * lambda.
+ *
+ * Ownership: every host array passed in is copied; the caller keeps it.  All
+ * device memory belongs to the context and is released by nsn_destroy.  The
+ * *_device entry points take device pointers that must stay valid for the
+ * call and be ordered on the context's stream.  A context is used from one
+ * host thread at a time.
+ *
+ * Errors: every call returns an nsn_status; nothing aborts or throws across
+ * the ABI.  nsn_last_error() returns a message for the last failure.
+ */
+#ifndef NSN_H
+#define NSN_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct nsn_ctx nsn_ctx;
+
+typedef enum {
+  NSN_OK = 0,
+  NSN_ERR_INVALID_ARG = 1,
+  NSN_ERR_OUT_OF_MEMORY = 2,
+  NSN_ERR_CUDA = 3,
+  NSN_ERR_NOT_CONVERGED = 4,
+  NSN_ERR_TIMEOUT = 5,
+  NSN_ERR_BAD_STATE = 6,
+  NSN_ERR_NONFINITE = 7
+} nsn_status;
+
+enum { NSN_RIGID = 0, NSN_PARTICLE = 1 };
+enum { NSN_CONTACT = 0, NSN_REVOLUTE = 1, NSN_TET_NH = 2 };
+enum { NSN_NCP_FB = 0, NSN_NCP_MIN = 1 };
+enum { NSN_R_NONE = 0, NSN_R_H2 = 1, NSN_R_EFFMASS = 2 };
+enum { NSN_GS_OFF = 0, NSN_GS_PARTICLES = 1 };
+enum { NSN_FP32 = 0, NSN_FP64 = 1 };
+
+typedef struct {
+  double h;               /* time step (Sec. 5) */
+  double gravity[3];
+  int32_t newton_iters;   /* N of Algorithm 1; cap when tol_rel > 0 */
+  int32_t cr_iters;       /* M of Algorithm 1; cap when cr_tol_mode = 1 */
+  double damping;         /* t of Sec. 8.1 (0.75 in the paper) */
+  double eps;             /* identity shift of Sec. 8.4 (1e-6 in the paper) */
+  double tol_rel;         /* stop Newton when merit <= tol_rel * merit(u=0, l=0); 0 = fixed */
+  int32_t cr_tol_mode;    /* 1: stop CR at ||r||_P <= min(0.1, merit/merit0) ||r0||_P */
+  int32_t ncp;            /* NSN_NCP_FB (paper default) or NSN_NCP_MIN */
+  int32_t rscale;         /* complementarity preconditioner, Sec. 7 */
+  int32_t geom_stiffness; /* NSN_GS_PARTICLES: Sec. 8.3 on particle DOFs */
+  int32_t precision;      /* NSN_FP32 bulk arithmetic or NSN_FP64 throughout;
+                             CR scalars and the merit are FP64 in both */
+  int32_t use_graph;      /* 1: capture the step as one CUDA graph and replay it */
+} nsn_config;
+
+/* Fills the paper's defaults: h = 1/60, g = (0, 0, -9.81), 4 x 20 iterations,
+ * t = 0.75, eps = 1e-6, FB, effective-mass r, GS on particles, FP32, graph on. */
+void nsn_default_config(nsn_config *cfg);
+
+typedef struct {
+  int32_t newton_done;    /* Newton iterations solved in the last step */
+  int32_t cr_total;       /* CR iterations summed over those Newton iterations */
+  double merit0;          /* ||[g; h]|| at the zero iterate u = 0, lambda = 0 */
+  double merit_final;     /* ||[g; h]|| at the returned iterate */
+  float ms;               /* device time of the last call (CUDA events) */
+} nsn_stats;
+
+/* Input records (packed, 4-byte fields). */
+typedef struct {
+  int32_t body_a, body_b;  /* body ids, -1 = static world (not both) */
+  float pa[3];             /* point on a: body-local (rigid), ignored (particle), world (-1) */
+  float pb[3];             /* point on b, same convention */
+  float n[3];              /* world contact normal pointing from b towards a (Sec. 3.3) */
+  float d;                 /* thickness d of C_n = n^T (a - b) - d >= 0 */
+  float mu;                /* friction coefficient (Sec. 3.4) */
+} nsn_contact;
+
+typedef struct {
+  int32_t body_a, body_b;  /* rigid bodies, -1 = world */
+  float pa[3], pb[3];      /* anchors: body-local, or world for a static side */
+  float axis_a[3];         /* hinge axis in a's frame (world if static) */
+  float axis_b[3];         /* hinge axis in b's frame (world if static) */
+  float compliance;        /* e of Sec. 3.2; 0 = hard */
+} nsn_revolute;
+
+typedef struct {
+  int32_t v[4];            /* particle body ids */
+  float rest[4][3];        /* rest positions of the 4 vertices */
+  float E, nu;             /* Young's modulus, Poisson ratio (App. B) */
+} nsn_tet;
+
+/* Creates a context on the current CUDA device.  stream: a cudaStream_t to
+ * order all work on, or NULL to create a private stream. */
+nsn_status nsn_create(const nsn_config *cfg, void *stream, nsn_ctx **out);
+nsn_status nsn_destroy(nsn_ctx *ctx);
+const char *nsn_last_error(const nsn_ctx *ctx);
+
+/* Appends n bodies (copied).  kind[n] NSN_RIGID/NSN_PARTICLE; pos n x 3;
+ * quat n x 4 (NULL = identity); vel n x 3; omega n x 3 (NULL = 0);
+ * mass[n] > 0; inertia n x 3 body-frame principal moments > 0 (rigid; may be
+ * NULL if all are particles).  first_id receives the id of the first body. */
+nsn_status nsn_add_bodies(nsn_ctx *ctx, int32_t n, const int32_t *kind, const float *pos,
+                          const float *quat, const float *vel, const float *omega,
+                          const float *mass, const float *inertia, int32_t *first_id);
+
+/* Appends n constraint records of one type (nsn_contact, nsn_revolute or
+ * nsn_tet array, copied).  first_row receives the first row of the block
+ * within its type's row range.  Contacts: body ids of any kind or -1.
+ * Revolute: rigid or -1.  Tet: four distinct particles with a non-degenerate
+ * rest shape. */
+nsn_status nsn_add_constraints(nsn_ctx *ctx, int32_t type, int32_t n, const void *records,
+                               int32_t *first_row);
+
+/* Removes all contacts (they are regenerated every step, Sec. 10). */
+nsn_status nsn_clear_contacts(nsn_ctx *ctx);
+
+/* Number of bodies / constraint rows (after all adds). */
+nsn_status nsn_counts(nsn_ctx *ctx, int32_t *n_bodies, int32_t *n_rows);
+
+/* Advances nsteps time steps (Algorithm 1) from the current state and commits
+ * each.  stats (may be NULL) describes the last step.  Returns
+ * NSN_ERR_NONFINITE if the merit became NaN/Inf. */
+nsn_status nsn_step(nsn_ctx *ctx, int32_t nsteps, nsn_stats *stats);
+
+/* State in ABI body order; any pointer may be NULL.  Host arrays:
+ * pos nb x 3, quat nb x 4, vel nb x 3, omega nb x 3 (particles: quat, omega ignored). */
+nsn_status nsn_get_state(nsn_ctx *ctx, float *pos, float *quat, float *vel, float *omega);
+nsn_status nsn_set_state(nsn_ctx *ctx, const float *pos, const float *quat, const float *vel,
+                         const float *omega);
+/* Same with device pointers (float32), ordered on the context stream. */
+nsn_status nsn_set_state_device(nsn_ctx *ctx, const float *pos, const float *quat, const float *vel,
+                                const float *omega);
+nsn_status nsn_get_state_device(nsn_ctx *ctx, float *pos, float *quat, float *vel, float *omega);
+/* Multipliers of the last step (R values, forces in N). */
+nsn_status nsn_get_lambda(nsn_ctx *ctx, double *lambda);
+/* Merit after each Newton iteration of the last step, then the final merit;
+ * returns the count through *n (at most cap written). */
+nsn_status nsn_get_merit_history(nsn_ctx *ctx, double *out, int32_t cap, int32_t *n);
+
+/* ---- verification entry points (used by the parity tests) ----------------
+ * nsn_linearize: runs the first n_before Newton iterations of a step from the
+ * current state without committing, then evaluates rows, g, H~, b and the
+ * Jacobi diagonal at that iterate and keeps that linear system.
+ * nsn_apply_operator: y = (J H~^-1 J^T + C + eps I) x on the kept system
+ * (R doubles in/out, host), using the same kernels as the CR loop.
+ * nsn_solve: runs iters CR iterations on the kept system from dl = 0 and
+ * returns dl (R) and du = H~^-1 (h J^T dl - g) (D, in body order, 6 per rigid
+ * body [v, w], 3 per particle); either output may be NULL.
+ * nsn_get_system: copies b (R), the Jacobi diagonal (R), h (R) and g (D). */
+nsn_status nsn_linearize(nsn_ctx *ctx, int32_t n_before);
+nsn_status nsn_apply_operator(nsn_ctx *ctx, const double *x, double *y);
+nsn_status nsn_solve(nsn_ctx *ctx, int32_t iters, double *dlambda, double *du);
+nsn_status nsn_get_system(nsn_ctx *ctx, double *b, double *diag, double *hvec, double *g);
+
+/* Device time and launch count of the last nsn_step (all kernels of the step). */
+nsn_status nsn_last_launch_count(nsn_ctx *ctx, int32_t *kernels_per_step);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,1096 @@
+// nsn_host.cu -- host runtime and C ABI of the non-smooth Newton stepper
+// (declared in include/nsn.h).  Builds the device layout from the scene,
+// owns all device memory, enqueues one time step (Algorithm 1) on the
+// context stream and captures it once as a CUDA graph.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/nsn.h"
+#include "nsn_kernels.cuh"
+
+using namespace nsn;
+
+namespace {
+
+constexpr int kMaxBlocks = 152 * 8;  // 152 SMs x 8 resident 256-thread blocks
+constexpr int kGroup = 8;            // lanes per body segment in the body pass
+
+struct HostScene {
+  std::vector<int32_t> kind;
+  std::vector<float> pos, quat, vel, omega, mass, inertia;
+  std::vector<nsn_contact> contacts;
+  std::vector<nsn_revolute> joints;
+  std::vector<nsn_tet> tets;
+};
+
+// Bump allocator over one device allocation.
+struct Arena {
+  char *base = nullptr;
+  size_t size = 0, off = 0;
+  bool sizing = true;
+  template <typename X>
+  X *take(size_t n) {
+    size_t bytes = ((n ? n : 1) * sizeof(X) + 255) & ~size_t(255);
+    X *p = sizing ? nullptr : reinterpret_cast<X *>(base + off);
+    off += bytes;
+    return p;
+  }
+};
+
+struct Layout {
+  int nr = 0, np = 0, nc = 0, nj = 0, nt = 0, R = 0, Rpair = 0, ER = 0, EV = 0;
+  std::vector<int> bmap;            // ABI body id -> encoded (>=0 rigid, <=-2 particle)
+  std::vector<int> rig_of, par_of;  // local index -> ABI id
+  std::vector<int> erow, rseg, vseg, re0, re1, te;
+};
+
+}  // namespace
+
+struct nsn_ctx {
+  nsn_config cfg;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  HostScene scene;
+  bool dirty = true;
+  Layout L;
+  void *dmem = nullptr;
+  size_t dbytes = 0;
+  Dev<float> d32;
+  Dev<double> d64;
+  int *d_bmap = nullptr;
+  float *d_stage = nullptr;  // AoS staging for state transfer (13 floats per body)
+  float *d_backup = nullptr; // committed state saved by nsn_linearize
+  cudaGraphExec_t graph = nullptr;
+  int launches_per_step = 0;
+  bool linearized = false;
+  int lin_buf = 0;           // entry buffer written by the kept linearisation
+  int built_nb = 0;          // bodies present in the current device build
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  std::string err;
+  nsn_stats last{};
+};
+
+namespace {
+
+nsn_status fail(nsn_ctx *c, nsn_status s, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  return s;
+}
+
+#define CUDA_TRY(c, call)                                                              \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess) return fail(c, NSN_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+inline int cdiv(long long a, long long b) { return int((a + b - 1) / b); }
+inline int clampb(long long n) { return int(std::max(1LL, std::min<long long>(n, kMaxBlocks))); }
+
+bool finite_all(const float *p, size_t n) {
+  for (size_t i = 0; i < n; i++)
+    if (!std::isfinite(p[i])) return false;
+  return true;
+}
+
+// ------------------------------------------------------------------------------------
+// layout: entries sorted by body (counting sort), rows -> entry ids
+
+nsn_status build_layout(nsn_ctx *c) {
+  HostScene &S = c->scene;
+  Layout &L = c->L;
+  L = Layout();
+  const int nb = int(S.kind.size());
+  L.bmap.resize(nb);
+  for (int i = 0; i < nb; i++) {
+    if (S.kind[i] == NSN_RIGID) { L.bmap[i] = L.nr++; L.rig_of.push_back(i); }
+    else { L.bmap[i] = -2 - L.np++; L.par_of.push_back(i); }
+  }
+  L.nc = int(S.contacts.size());
+  L.nj = int(S.joints.size());
+  L.nt = int(S.tets.size());
+  L.Rpair = 3 * L.nc + 5 * L.nj;
+  L.R = L.Rpair + 3 * L.nt;
+  // (row, side, body) list
+  struct Side { int row, slot, enc; };
+  std::vector<Side> sides;
+  sides.reserve(size_t(L.R) * 2 + size_t(L.nt) * 6);
+  for (int ci = 0; ci < L.nc; ci++) {
+    int a = S.contacts[ci].body_a, b = S.contacts[ci].body_b;
+    for (int k = 0; k < 3; k++) {
+      if (a >= 0) sides.push_back({3 * ci + k, 0, L.bmap[a]});
+      if (b >= 0) sides.push_back({3 * ci + k, 1, L.bmap[b]});
+    }
+  }
+  for (int j = 0; j < L.nj; j++) {
+    int a = S.joints[j].body_a, b = S.joints[j].body_b;
+    for (int k = 0; k < 5; k++) {
+      int row = 3 * L.nc + 5 * j + k;
+      if (a >= 0) sides.push_back({row, 0, L.bmap[a]});
+      if (b >= 0) sides.push_back({row, 1, L.bmap[b]});
+    }
+  }
+  for (int t = 0; t < L.nt; t++)
+    for (int k = 0; k < 3; k++)
+      for (int q = 0; q < 4; q++) sides.push_back({L.Rpair + 3 * t + k, q, L.bmap[S.tets[t].v[q]]});
+  // counting sort by body: rigid then particle
+  std::vector<int> rcnt(L.nr + 1, 0), pcnt(L.np + 1, 0);
+  for (auto &s : sides) {
+    if (s.enc >= 0) rcnt[s.enc + 1]++;
+    else pcnt[-s.enc - 2 + 1]++;
+  }
+  for (int i = 0; i < L.nr; i++) rcnt[i + 1] += rcnt[i];
+  for (int i = 0; i < L.np; i++) pcnt[i + 1] += pcnt[i];
+  L.rseg = rcnt;
+  L.vseg = pcnt;
+  L.ER = rcnt[L.nr];
+  L.EV = pcnt[L.np];
+  L.erow.assign(size_t(L.ER) + L.EV, 0);
+  L.re0.assign(L.Rpair, -1);
+  L.re1.assign(L.Rpair, -1);
+  L.te.assign(size_t(12) * L.nt, -1);
+  std::vector<int> rfill(rcnt.begin(), rcnt.end() - 1), pfill(pcnt.begin(), pcnt.end() - 1);
+  // sides were appended in row order, so entries within a body stay row-ordered
+  for (auto &s : sides) {
+    int e;
+    if (s.enc >= 0) e = rfill[s.enc]++;
+    else e = L.ER + pfill[-s.enc - 2]++;
+    L.erow[e] = s.row;
+    if (s.row < L.Rpair) {
+      (s.slot == 0 ? L.re0 : L.re1)[s.row] = e;
+    } else {
+      int t = (s.row - L.Rpair) / 3, k = (s.row - L.Rpair) % 3;
+      L.te[12 * t + 4 * k + s.slot] = e;
+    }
+  }
+  return NSN_OK;
+}
+
+template <typename T>
+void carve(Arena &A, Dev<T> &D, const Layout &L, int nb) {
+  auto tk = [&](int n) { return A.take<T>(n); };
+  for (int k = 0; k < 3; k++) { D.rx[k] = tk(L.nr); D.rx0[k] = tk(L.nr); D.rIb[k] = tk(L.nr); }
+  for (int k = 0; k < 4; k++) { D.rq[k] = tk(L.nr); D.rq0[k] = tk(L.nr); }
+  for (int k = 0; k < 6; k++) {
+    D.ru[k] = tk(L.nr); D.rut[k] = tk(L.nr); D.rIw[k] = tk(L.nr); D.rIwi[k] = tk(L.nr);
+    D.rg[k] = tk(L.nr); D.ryg[k] = tk(L.nr);
+  }
+  D.rm = tk(L.nr); D.rinvm = tk(L.nr);
+  for (int k = 0; k < 3; k++) {
+    D.px[k] = tk(L.np); D.px0[k] = tk(L.np); D.pu[k] = tk(L.np); D.put[k] = tk(L.np);
+    D.phinv[k] = tk(L.np); D.pg[k] = tk(L.np); D.pyg[k] = tk(L.np); D.puprev[k] = tk(L.np);
+  }
+  D.pm = tk(L.np);
+  D.erow = A.take<int>(size_t(L.ER) + L.EV);
+  D.rseg = A.take<int>(L.nr + 1);
+  D.vseg = A.take<int>(L.np + 1);
+  for (int k = 0; k < 6; k++) D.ej6[k] = tk(L.ER);
+  for (int b = 0; b < 2; b++)
+    for (int k = 0; k < 3; k++) D.ej3[b][k] = tk(L.EV);
+  D.t = tk(L.ER + L.EV);
+  D.t2 = tk(L.ER + L.EV);
+  D.re0 = A.take<int>(L.Rpair);
+  D.re1 = A.take<int>(L.Rpair);
+  D.te = A.take<int>(size_t(12) * L.nt);
+  D.lam = tk(L.R); D.cdiag = tk(L.R); D.hv = tk(L.R); D.b = tk(L.R); D.P = tk(L.R);
+  D.x = tk(L.R); D.z = tk(L.R); D.p = tk(L.R); D.Ap = tk(L.R); D.Az = tk(L.R);
+  D.c3 = tk(6 * L.nt);
+  D.cba = A.take<int>(L.nc); D.cbb = A.take<int>(L.nc);
+  for (int k = 0; k < 3; k++) { D.cpa[k] = tk(L.nc); D.cpb[k] = tk(L.nc); D.cn[k] = tk(L.nc); }
+  D.cdd = tk(L.nc); D.cmu = tk(L.nc);
+  D.jba = A.take<int>(L.nj); D.jbb = A.take<int>(L.nj);
+  for (int k = 0; k < 3; k++) { D.jpa[k] = tk(L.nj); D.jpb[k] = tk(L.nj); D.jaxa[k] = tk(L.nj); D.jaxb[k] = tk(L.nj); }
+  D.je = tk(L.nj);
+  D.tv = A.take<int>(4 * L.nt);
+  D.tDmi = tk(9 * L.nt); D.tVe = tk(L.nt); D.tC1 = tk(L.nt); D.tD1 = tk(L.nt); D.talpha = tk(L.nt);
+  D.part_body = A.take<double>(2 * kMaxBlocks);
+  D.part_row = A.take<double>(2 * kMaxBlocks * NPART);
+  D.sc = A.take<Scalars>(1);
+  D.fl = A.take<Flags>(1);
+  (void)nb;
+}
+
+template <typename T>
+void fill_sizes(Dev<T> &D, const Layout &L, const nsn_config &cfg) {
+  D.nr = L.nr; D.np = L.np; D.nc = L.nc; D.nj = L.nj; D.nt = L.nt; D.R = L.R; D.Rpair = L.Rpair;
+  D.ER = L.ER; D.EV = L.EV;
+  D.h = cfg.h; D.eps = cfg.eps; D.damping = cfg.damping; D.tol_rel = cfg.tol_rel;
+  for (int k = 0; k < 3; k++) D.grav[k] = cfg.gravity[k];
+  D.ncp = cfg.ncp; D.rscale = cfg.rscale; D.gs = cfg.geom_stiffness; D.cr_tol = cfg.cr_tol_mode;
+  D.nblk_body_r = L.nr ? clampb(cdiv((long long)L.nr * kGroup, BLOCK)) : 0;
+  D.nblk_body_p = L.np ? clampb(cdiv((long long)L.np * kGroup, BLOCK)) : 0;
+  D.nblk_row_pair = L.Rpair ? clampb(cdiv(L.Rpair, BLOCK)) : 0;
+  D.nblk_row_tet = L.nt ? clampb(cdiv(L.nt, BLOCK)) : 0;
+  D.nblk_upd = clampb(cdiv(std::max(L.R, 1), BLOCK));
+}
+
+// host-side copies of per-row / per-body static data, converted to T
+template <typename T>
+nsn_status upload(nsn_ctx *c, Dev<T> &D) {
+  const Layout &L = c->L;
+  const HostScene &S = c->scene;
+  cudaStream_t st = c->stream;
+  std::vector<T> buf;
+  auto put = [&](T *dst, const std::vector<T> &src) -> cudaError_t {
+    if (src.empty()) return cudaSuccess;
+    return cudaMemcpyAsync(dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, st);
+  };
+  auto puti = [&](int *dst, const std::vector<int> &src) -> cudaError_t {
+    if (src.empty()) return cudaSuccess;
+    return cudaMemcpyAsync(dst, src.data(), src.size() * sizeof(int), cudaMemcpyHostToDevice, st);
+  };
+  // rigid static data
+  {
+    std::vector<T> m(L.nr), im(L.nr), I[3];
+    for (int k = 0; k < 3; k++) I[k].resize(L.nr);
+    for (int i = 0; i < L.nr; i++) {
+      int id = L.rig_of[i];
+      m[i] = T(S.mass[id]);
+      im[i] = T(1.0 / double(S.mass[id]));
+      for (int k = 0; k < 3; k++) I[k][i] = T(S.inertia[3 * id + k]);
+    }
+    CUDA_TRY(c, put(D.rm, m)); CUDA_TRY(c, put(D.rinvm, im));
+    for (int k = 0; k < 3; k++) CUDA_TRY(c, put(D.rIb[k], I[k]));
+    std::vector<T> pm(L.np);
+    for (int i = 0; i < L.np; i++) pm[i] = T(S.mass[L.par_of[i]]);
+    CUDA_TRY(c, put(D.pm, pm));
+  }
+  CUDA_TRY(c, puti(D.erow, L.erow));
+  CUDA_TRY(c, puti(D.rseg, L.rseg));
+  CUDA_TRY(c, puti(D.vseg, L.vseg));
+  CUDA_TRY(c, puti(D.re0, L.re0));
+  CUDA_TRY(c, puti(D.re1, L.re1));
+  CUDA_TRY(c, puti(D.te, L.te));
+  // contacts
+  {
+    std::vector<int> a(L.nc), b(L.nc);
+    std::vector<T> pa[3], pb[3], n[3], d(L.nc), mu(L.nc);
+    for (int k = 0; k < 3; k++) { pa[k].resize(L.nc); pb[k].resize(L.nc); n[k].resize(L.nc); }
+    for (int i = 0; i < L.nc; i++) {
+      const nsn_contact &r = S.contacts[i];
+      a[i] = r.body_a >= 0 ? L.bmap[r.body_a] : -1;
+      b[i] = r.body_b >= 0 ? L.bmap[r.body_b] : -1;
+      double nn = std::sqrt(double(r.n[0]) * r.n[0] + double(r.n[1]) * r.n[1] + double(r.n[2]) * r.n[2]);
+      for (int k = 0; k < 3; k++) { pa[k][i] = T(r.pa[k]); pb[k][i] = T(r.pb[k]); n[k][i] = T(r.n[k] / nn); }
+      d[i] = T(r.d); mu[i] = T(r.mu);
+    }
+    CUDA_TRY(c, puti(D.cba, a)); CUDA_TRY(c, puti(D.cbb, b));
+    for (int k = 0; k < 3; k++) { CUDA_TRY(c, put(D.cpa[k], pa[k])); CUDA_TRY(c, put(D.cpb[k], pb[k])); CUDA_TRY(c, put(D.cn[k], n[k])); }
+    CUDA_TRY(c, put(D.cdd, d)); CUDA_TRY(c, put(D.cmu, mu));
+  }
+  // joints
+  {
+    std::vector<int> a(L.nj), b(L.nj);
+    std::vector<T> pa[3], pb[3], xa[3], xb[3], e(L.nj);
+    for (int k = 0; k < 3; k++) { pa[k].resize(L.nj); pb[k].resize(L.nj); xa[k].resize(L.nj); xb[k].resize(L.nj); }
+    for (int i = 0; i < L.nj; i++) {
+      const nsn_revolute &r = S.joints[i];
+      a[i] = r.body_a >= 0 ? L.bmap[r.body_a] : -1;
+      b[i] = r.body_b >= 0 ? L.bmap[r.body_b] : -1;
+      for (int k = 0; k < 3; k++) { pa[k][i] = T(r.pa[k]); pb[k][i] = T(r.pb[k]); xa[k][i] = T(r.axis_a[k]); xb[k][i] = T(r.axis_b[k]); }
+      e[i] = T(r.compliance);
+    }
+    CUDA_TRY(c, puti(D.jba, a)); CUDA_TRY(c, puti(D.jbb, b));
+    for (int k = 0; k < 3; k++) {
+      CUDA_TRY(c, put(D.jpa[k], pa[k])); CUDA_TRY(c, put(D.jpb[k], pb[k]));
+      CUDA_TRY(c, put(D.jaxa[k], xa[k])); CUDA_TRY(c, put(D.jaxb[k], xb[k]));
+    }
+    CUDA_TRY(c, put(D.je, e));
+  }
+  // tets: rest-shape inverse, volume and stable Neo-Hookean constants (App. B):
+  // C1 = mu/2, D1 = lambda/2 (Lame), alpha = 1 + mu/lambda (rest state stress free)
+  {
+    std::vector<int> v(4 * L.nt);
+    std::vector<T> Dmi(9 * L.nt), Ve(L.nt), C1(L.nt), D1(L.nt), al(L.nt);
+    for (int t = 0; t < L.nt; t++) {
+      const nsn_tet &r = S.tets[t];
+      for (int q = 0; q < 4; q++) v[4 * t + q] = -L.bmap[r.v[q]] - 2;
+      double Dm[9];
+      for (int row = 0; row < 3; row++)
+        for (int k = 0; k < 3; k++) Dm[3 * row + k] = double(r.rest[k + 1][row]) - double(r.rest[0][row]);
+      double det = Dm[0] * (Dm[4] * Dm[8] - Dm[5] * Dm[7]) - Dm[1] * (Dm[3] * Dm[8] - Dm[5] * Dm[6]) +
+                   Dm[2] * (Dm[3] * Dm[7] - Dm[4] * Dm[6]);
+      double inv[9] = {(Dm[4] * Dm[8] - Dm[5] * Dm[7]) / det, (Dm[2] * Dm[7] - Dm[1] * Dm[8]) / det,
+                       (Dm[1] * Dm[5] - Dm[2] * Dm[4]) / det, (Dm[5] * Dm[6] - Dm[3] * Dm[8]) / det,
+                       (Dm[0] * Dm[8] - Dm[2] * Dm[6]) / det, (Dm[2] * Dm[3] - Dm[0] * Dm[5]) / det,
+                       (Dm[3] * Dm[7] - Dm[4] * Dm[6]) / det, (Dm[1] * Dm[6] - Dm[0] * Dm[7]) / det,
+                       (Dm[0] * Dm[4] - Dm[1] * Dm[3]) / det};
+      for (int k = 0; k < 9; k++) Dmi[9 * t + k] = T(inv[k]);
+      Ve[t] = T(std::fabs(det) / 6.0);
+      double mu = double(r.E) / (2.0 * (1.0 + double(r.nu)));
+      double la = double(r.E) * double(r.nu) / ((1.0 + double(r.nu)) * (1.0 - 2.0 * double(r.nu)));
+      C1[t] = T(0.5 * mu); D1[t] = T(0.5 * la); al[t] = T(1.0 + mu / la);
+    }
+    CUDA_TRY(c, puti(D.tv, v));
+    CUDA_TRY(c, put(D.tDmi, Dmi)); CUDA_TRY(c, put(D.tVe, Ve)); CUDA_TRY(c, put(D.tC1, C1));
+    CUDA_TRY(c, put(D.tD1, D1)); CUDA_TRY(c, put(D.talpha, al));
+  }
+  CUDA_TRY(c, cudaMemsetAsync(D.lam, 0, sizeof(T) * std::max(L.R, 1), st));
+  CUDA_TRY(c, cudaMemsetAsync(D.sc, 0, sizeof(Scalars), st));
+  CUDA_TRY(c, cudaMemsetAsync(D.fl, 0, sizeof(Flags), st));
+  for (int b2 = 0; b2 < 2; b2++)
+    for (int k = 0; k < 3; k++)
+      if (L.EV) CUDA_TRY(c, cudaMemsetAsync(D.ej3[b2][k], 0, sizeof(T) * L.EV, st));
+  return NSN_OK;
+}
+
+// ------------------------------------------------------------------------------------
+// state transfer (AoS float <-> SoA T)
+
+template <typename T>
+__global__ void k_scatter_state(Dev<T> D, const int *bmap, int nb, const float *pos, const float *quat,
+                                const float *vel, const float *omega) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nb) return;
+  int e = bmap[i];
+  if (e >= 0) {
+    for (int k = 0; k < 3; k++) {
+      if (pos) D.rx[k][e] = T(pos[3 * i + k]);
+      if (vel) D.ru[k][e] = T(vel[3 * i + k]);
+      if (omega) D.ru[3 + k][e] = T(omega[3 * i + k]);
+    }
+    if (quat) {
+      T q[4], n = 0;
+      for (int k = 0; k < 4; k++) { q[k] = T(quat[4 * i + k]); n += q[k] * q[k]; }
+      n = sqrt(n);
+      for (int k = 0; k < 4; k++) D.rq[k][e] = q[k] / n;
+    }
+  } else {
+    int p = -e - 2;
+    for (int k = 0; k < 3; k++) {
+      if (pos) D.px[k][p] = T(pos[3 * i + k]);
+      if (vel) D.pu[k][p] = T(vel[3 * i + k]);
+    }
+  }
+}
+
+template <typename T>
+__global__ void k_gather_state(Dev<T> D, const int *bmap, int nb, float *pos, float *quat, float *vel,
+                               float *omega) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nb) return;
+  int e = bmap[i];
+  if (e >= 0) {
+    for (int k = 0; k < 3; k++) {
+      if (pos) pos[3 * i + k] = float(D.rx[k][e]);
+      if (vel) vel[3 * i + k] = float(D.ru[k][e]);
+      if (omega) omega[3 * i + k] = float(D.ru[3 + k][e]);
+    }
+    if (quat)
+      for (int k = 0; k < 4; k++) quat[4 * i + k] = float(D.rq[k][e]);
+  } else {
+    int p = -e - 2;
+    for (int k = 0; k < 3; k++) {
+      if (pos) pos[3 * i + k] = float(D.px[k][p]);
+      if (vel) vel[3 * i + k] = float(D.pu[k][p]);
+      if (omega) omega[3 * i + k] = 0.f;
+    }
+    if (quat) { quat[4 * i] = 1.f; quat[4 * i + 1] = quat[4 * i + 2] = quat[4 * i + 3] = 0.f; }
+  }
+}
+
+// copies of the committed state (x, q, u) for nsn_linearize
+template <typename T>
+__global__ void k_backup_state(Dev<T> D, T *buf, int restore) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nr = D.nr, np = D.np;
+  if (i < nr) {
+    T *b = buf + 13 * size_t(i);
+    for (int k = 0; k < 3; k++) { if (restore) D.rx[k][i] = b[k]; else b[k] = D.rx[k][i]; }
+    for (int k = 0; k < 4; k++) { if (restore) D.rq[k][i] = b[3 + k]; else b[3 + k] = D.rq[k][i]; }
+    for (int k = 0; k < 6; k++) { if (restore) D.ru[k][i] = b[7 + k]; else b[7 + k] = D.ru[k][i]; }
+  } else if (i < nr + np) {
+    int p = i - nr;
+    T *b = buf + 13 * size_t(i);
+    for (int k = 0; k < 3; k++) { if (restore) D.px[k][p] = b[k]; else b[k] = D.px[k][p]; }
+    for (int k = 0; k < 3; k++) { if (restore) D.pu[k][p] = b[3 + k]; else b[3 + k] = D.pu[k][p]; }
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// step orchestration
+
+template <typename T>
+struct Launcher {
+  nsn_ctx *c;
+  Dev<T> &D;
+  cudaStream_t st;
+  int count = 0;
+
+  void body(int mode, const T *in, int buf, int it, int force) {
+    int nb = D.nblk_body_r + D.nblk_body_p;
+    if (!nb) return;
+    if (mode == BM_RESIDUAL) k_body_pass<T, kGroup, BM_RESIDUAL><<<nb, BLOCK, 0, st>>>(D, in, buf, it, force);
+    else if (mode == BM_APPLY) k_body_pass<T, kGroup, BM_APPLY><<<nb, BLOCK, 0, st>>>(D, in, buf, it, force);
+    else k_body_pass<T, kGroup, BM_UPDATE><<<nb, BLOCK, 0, st>>>(D, in, buf, it, force);
+    count++;
+  }
+  void rows(int mode, int force) {
+    int nb = D.nblk_row_pair + D.nblk_row_tet;
+    if (!nb) return;
+    if (mode == RM_RHS) k_row_pass<T, RM_RHS><<<nb, BLOCK, 0, st>>>(D, force);
+    else k_row_pass<T, RM_APPLY><<<nb, BLOCK, 0, st>>>(D, force);
+    count++;
+  }
+  void eval(int buf, int force) {
+    if (D.nc) { k_eval_contacts<T><<<cdiv(D.nc, 128), 128, 0, st>>>(D, buf, force); count++; }
+    if (D.nj) { k_eval_joints<T><<<cdiv(D.nj, 128), 128, 0, st>>>(D, buf, force); count++; }
+    if (D.nt) { k_eval_tets<T><<<cdiv(D.nt, 128), 128, 0, st>>>(D, buf, force); count++; }
+  }
+  void begin() {
+    // plain start of Sec. 8.1: lambda^0 = 0 (u^0 = 0 is set by the begin kernels)
+    if (D.R) cudaMemsetAsync(D.lam, 0, sizeof(T) * D.R, st);
+    k_begin_rigid<T><<<cdiv(std::max(D.nr, 1), 128), 128, 0, st>>>(D);
+    count++;
+    if (D.np) { k_begin_particle<T><<<cdiv(D.np, 128), 128, 0, st>>>(D); count++; }
+  }
+  void linearize_at(int n) {  // rows, g, H~, b, diag at Newton iteration n
+    const int buf = n & 1;
+    eval(buf, 0);
+    body(BM_RESIDUAL, D.lam, buf, n, 0);
+    rows(RM_RHS, 0);
+    k_merit<T><<<1, BLOCK, 0, st>>>(D, n, 0);
+    count++;
+  }
+  void cr(int iters) {
+    if (!D.R) return;
+    for (int k = 0; k < iters; k++) {
+      body(BM_APPLY, D.z, 0, 0, 0);
+      rows(RM_APPLY, 0);
+      k_cr_scalars<T><<<1, BLOCK, 0, st>>>(D, k);
+      k_cr_update<T><<<D.nblk_upd, BLOCK, 0, st>>>(D);
+      count += 2;
+    }
+  }
+  void newton_update(int n) {
+    body(BM_UPDATE, D.x, n & 1, n, 0);
+    k_lambda_update<T><<<D.nblk_upd, BLOCK, 0, st>>>(D);
+    count++;
+  }
+  void step() {
+    const int N = c->cfg.newton_iters, M = c->cfg.cr_iters;
+    begin();
+    for (int n = 0; n < N; n++) {
+      linearize_at(n);
+      cr(M);
+      newton_update(n);
+    }
+    // final merit at the returned iterate
+    const int buf = N & 1;
+    eval(buf, 1);
+    body(BM_RESIDUAL, D.lam, buf, N, 1);
+    rows(RM_RHS, 1);
+    k_merit<T><<<1, BLOCK, 0, st>>>(D, N, 1);
+    count++;
+  }
+};
+
+template <typename T>
+Dev<T> &dev(nsn_ctx *c);
+template <>
+Dev<float> &dev<float>(nsn_ctx *c) { return c->d32; }
+template <>
+Dev<double> &dev<double>(nsn_ctx *c) { return c->d64; }
+
+nsn_status ensure_built(nsn_ctx *c);
+
+template <typename T>
+nsn_status build_device(nsn_ctx *c) {
+  const Layout &L = c->L;
+  const int nb = int(c->scene.kind.size());
+  Dev<T> &D = dev<T>(c);
+  D = Dev<T>();
+  fill_sizes(D, L, c->cfg);
+  Arena A;
+  carve(A, D, L, nb);
+  size_t need = A.off + size_t(256) * 4 + sizeof(int) * nb + sizeof(float) * 13 * (nb + 1) + sizeof(T) * 13 * (nb + 1);
+  if (c->dmem) { cudaFree(c->dmem); c->dmem = nullptr; }
+  cudaError_t e = cudaMalloc(&c->dmem, need);
+  if (e != cudaSuccess) return fail(c, NSN_ERR_OUT_OF_MEMORY, "cudaMalloc(%zu): %s", need, cudaGetErrorString(e));
+  c->dbytes = need;
+  A.base = static_cast<char *>(c->dmem);
+  A.sizing = false;
+  A.off = 0;
+  carve(A, D, L, nb);
+  fill_sizes(D, L, c->cfg);
+  c->d_bmap = A.take<int>(nb);
+  c->d_stage = A.take<float>(13 * size_t(nb + 1));
+  c->d_backup = reinterpret_cast<float *>(A.take<T>(13 * size_t(nb + 1)));
+  nsn_status s = upload<T>(c, D);
+  if (s != NSN_OK) return s;
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_bmap, L.bmap.data(), sizeof(int) * std::max(nb, 0), cudaMemcpyHostToDevice, c->stream));
+  // initial state
+  const HostScene &S = c->scene;
+  float *st = c->d_stage;
+  float *dpos = st, *dquat = st + 3 * nb, *dvel = st + 7 * nb, *dom = st + 10 * nb;
+  if (nb) {
+    CUDA_TRY(c, cudaMemcpyAsync(dpos, S.pos.data(), sizeof(float) * 3 * nb, cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(dquat, S.quat.data(), sizeof(float) * 4 * nb, cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(dvel, S.vel.data(), sizeof(float) * 3 * nb, cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(dom, S.omega.data(), sizeof(float) * 3 * nb, cudaMemcpyHostToDevice, c->stream));
+    k_scatter_state<T><<<cdiv(nb, 128), 128, 0, c->stream>>>(D, c->d_bmap, nb, dpos, dquat, dvel, dom);
+    CUDA_TRY(c, cudaGetLastError());
+  }
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return NSN_OK;
+}
+
+}  // namespace
+nsn_status state_io(nsn_ctx *c, bool set, bool device, const float *ipos, const float *iquat,
+                    const float *ivel, const float *iom, float *opos, float *oquat, float *ovel, float *oom);
+namespace {
+
+nsn_status ensure_built(nsn_ctx *c) {
+  if (!c->dirty) return NSN_OK;
+  if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
+  // keep the current state of the bodies that already live on the device
+  if (c->dmem && c->built_nb > 0) {
+    const int nb0 = c->built_nb;
+    std::vector<float> pos(3 * nb0), quat(4 * nb0), vel(3 * nb0), om(3 * nb0);
+    c->dirty = false;
+    nsn_status s0 = state_io(c, false, false, nullptr, nullptr, nullptr, nullptr, pos.data(), quat.data(), vel.data(), om.data());
+    c->dirty = true;
+    if (s0 != NSN_OK) return s0;
+    std::copy(pos.begin(), pos.end(), c->scene.pos.begin());
+    std::copy(quat.begin(), quat.end(), c->scene.quat.begin());
+    std::copy(vel.begin(), vel.end(), c->scene.vel.begin());
+    std::copy(om.begin(), om.end(), c->scene.omega.begin());
+  }
+  nsn_status s = build_layout(c);
+  if (s != NSN_OK) return s;
+  s = c->cfg.precision == NSN_FP64 ? build_device<double>(c) : build_device<float>(c);
+  if (s != NSN_OK) return s;
+  c->dirty = false;
+  c->built_nb = int(c->scene.kind.size());
+  return NSN_OK;
+}
+
+template <typename T>
+nsn_status run_steps(nsn_ctx *c, int nsteps) {
+  Dev<T> &D = dev<T>(c);
+  cudaStream_t st = c->stream;
+  CUDA_TRY(c, cudaEventRecord(c->ev0, st));
+  if (c->cfg.use_graph) {
+    if (!c->graph) {
+      cudaGraph_t g;
+      CUDA_TRY(c, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+      Launcher<T> Lr{c, D, st};
+      Lr.step();
+      cudaError_t e = cudaStreamEndCapture(st, &g);
+      if (e != cudaSuccess) return fail(c, NSN_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+      e = cudaGraphInstantiate(&c->graph, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) return fail(c, NSN_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+      c->launches_per_step = Lr.count;
+    }
+    for (int s = 0; s < nsteps; s++) CUDA_TRY(c, cudaGraphLaunch(c->graph, st));
+  } else {
+    for (int s = 0; s < nsteps; s++) {
+      Launcher<T> Lr{c, D, st};
+      Lr.step();
+      c->launches_per_step = Lr.count;
+    }
+    CUDA_TRY(c, cudaGetLastError());
+  }
+  CUDA_TRY(c, cudaEventRecord(c->ev1, st));
+  // stats of the last step
+  Flags fl;
+  Scalars sc;
+  CUDA_TRY(c, cudaMemcpyAsync(&fl, D.fl, sizeof(Flags), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(c, cudaMemcpyAsync(&sc, D.sc, sizeof(Scalars), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(c, cudaStreamSynchronize(st));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+  const int N = c->cfg.newton_iters;
+  c->last.newton_done = fl.newton_count;
+  c->last.cr_total = fl.cr_count;
+  c->last.merit0 = sc.merit0;
+  c->last.merit_final = sc.merit[N < 1023 ? N : 1023];
+  c->last.ms = ms;
+  if (!std::isfinite(c->last.merit_final)) return fail(c, NSN_ERR_NONFINITE, "merit is not finite");
+  return NSN_OK;
+}
+
+bool valid_cfg(const nsn_config *cfg) {
+  return cfg && cfg->h > 0 && cfg->newton_iters >= 0 && cfg->newton_iters < 1000 && cfg->cr_iters >= 0 &&
+         cfg->damping > 0 && cfg->damping <= 1 && cfg->eps >= 0 && cfg->tol_rel >= 0 &&
+         (cfg->precision == NSN_FP32 || cfg->precision == NSN_FP64) && (cfg->ncp == 0 || cfg->ncp == 1) &&
+         cfg->rscale >= 0 && cfg->rscale <= 2;
+}
+
+template <typename T>
+nsn_status do_linearize(nsn_ctx *c, int n_before) {
+  Dev<T> &D = dev<T>(c);
+  cudaStream_t st = c->stream;
+  const int nbt = D.nr + D.np;
+  T *bk = reinterpret_cast<T *>(c->d_backup);
+  if (nbt) k_backup_state<T><<<cdiv(nbt, 128), 128, 0, st>>>(D, bk, 0);
+  Launcher<T> Lr{c, D, st};
+  Lr.begin();
+  for (int n = 0; n < n_before; n++) {
+    Lr.linearize_at(n);
+    Lr.cr(c->cfg.cr_iters);
+    Lr.newton_update(n);
+  }
+  Lr.linearize_at(n_before);
+  if (nbt) k_backup_state<T><<<cdiv(nbt, 128), 128, 0, st>>>(D, bk, 1);
+  CUDA_TRY(c, cudaGetLastError());
+  CUDA_TRY(c, cudaStreamSynchronize(st));
+  c->linearized = true;
+  return NSN_OK;
+}
+
+template <typename T>
+__global__ void k_from_double(T *dst, const double *src, int n) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = T(src[i]);
+}
+template <typename T>
+__global__ void k_to_double(double *dst, const T *src, int n, int invert) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = invert ? 1.0 / double(src[i]) : double(src[i]);
+}
+
+template <typename T>
+nsn_status copy_out(nsn_ctx *c, const T *src, int n, double *host, int invert = 0) {
+  if (!host || n <= 0) return NSN_OK;
+  double *tmp;
+  CUDA_TRY(c, cudaMallocAsync(&tmp, sizeof(double) * n, c->stream));
+  k_to_double<T><<<cdiv(n, 256), 256, 0, c->stream>>>(tmp, src, n, invert);
+  CUDA_TRY(c, cudaMemcpyAsync(host, tmp, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaFreeAsync(tmp, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return NSN_OK;
+}
+
+template <typename T>
+nsn_status do_apply(nsn_ctx *c, const double *x, double *y) {
+  Dev<T> &D = dev<T>(c);
+  cudaStream_t st = c->stream;
+  const int R = D.R;
+  if (R == 0) return NSN_OK;
+  double *tmp;
+  CUDA_TRY(c, cudaMallocAsync(&tmp, sizeof(double) * R, st));
+  CUDA_TRY(c, cudaMemcpyAsync(tmp, x, sizeof(double) * R, cudaMemcpyHostToDevice, st));
+  k_from_double<T><<<cdiv(R, 256), 256, 0, st>>>(D.z, tmp, R);
+  CUDA_TRY(c, cudaMemsetAsync(D.fl, 0, sizeof(Flags), st));
+  Launcher<T> Lr{c, D, st};
+  Lr.body(BM_APPLY, D.z, 0, 0, 1);
+  Lr.rows(RM_APPLY, 1);
+  k_to_double<T><<<cdiv(R, 256), 256, 0, st>>>(tmp, D.Az, R, 0);
+  CUDA_TRY(c, cudaMemcpyAsync(y, tmp, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(c, cudaFreeAsync(tmp, st));
+  CUDA_TRY(c, cudaStreamSynchronize(st));
+  return NSN_OK;
+}
+
+// du in body order from the BM_UPDATE formula without committing: computed on
+// the host from g, H~^-1 blocks and J^T dl gathered through the apply path.
+template <typename T>
+nsn_status do_solve(nsn_ctx *c, int iters, double *dl, double *du) {
+  Dev<T> &D = dev<T>(c);
+  cudaStream_t st = c->stream;
+  CUDA_TRY(c, cudaMemsetAsync(D.fl, 0, sizeof(Flags), st));
+  if (D.R) {
+    k_cr_init<T><<<D.nblk_upd, BLOCK, 0, st>>>(D);
+    // res0 for the scalar kernel
+    Launcher<T> Lr{c, D, st};
+    Lr.cr(iters);
+  }
+  CUDA_TRY(c, cudaGetLastError());
+  if (dl) { nsn_status s = copy_out<T>(c, D.x, D.R, dl); if (s) return s; }
+  if (du) {
+    // du = H~^-1 (h J^T dl - g): reuse the apply body pass on x to get y = H~^-1 J^T x
+    // per body into the per-entry scratch is not body-ordered, so do it on the host.
+    const Layout &L = c->L;
+    const int nb = int(c->scene.kind.size());
+    std::vector<double> x(D.R), erowJ;
+    if (D.R) { nsn_status s = copy_out<T>(c, D.x, D.R, x.data()); if (s) return s; }
+    std::vector<T> J6(size_t(6) * L.ER), J3(size_t(3) * L.EV);
+    std::vector<T> g6(size_t(6) * L.nr), g3(size_t(3) * L.np), Iwi(size_t(6) * L.nr), hinv(size_t(3) * L.np), im(L.nr);
+    int bufJ = -1;
+    (void)bufJ;
+    for (int k = 0; k < 6; k++) {
+      if (L.ER) CUDA_TRY(c, cudaMemcpyAsync(J6.data() + size_t(k) * L.ER, D.ej6[k], sizeof(T) * L.ER, cudaMemcpyDeviceToHost, st));
+      if (L.nr) {
+        CUDA_TRY(c, cudaMemcpyAsync(g6.data() + size_t(k) * L.nr, D.rg[k], sizeof(T) * L.nr, cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(c, cudaMemcpyAsync(Iwi.data() + size_t(k) * L.nr, D.rIwi[k], sizeof(T) * L.nr, cudaMemcpyDeviceToHost, st));
+      }
+    }
+    if (L.nr) CUDA_TRY(c, cudaMemcpyAsync(im.data(), D.rinvm, sizeof(T) * L.nr, cudaMemcpyDeviceToHost, st));
+    int lbuf = c->lin_buf;
+    for (int k = 0; k < 3; k++) {
+      if (L.EV) CUDA_TRY(c, cudaMemcpyAsync(J3.data() + size_t(k) * L.EV, D.ej3[lbuf][k], sizeof(T) * L.EV, cudaMemcpyDeviceToHost, st));
+      if (L.np) {
+        CUDA_TRY(c, cudaMemcpyAsync(g3.data() + size_t(k) * L.np, D.pg[k], sizeof(T) * L.np, cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(c, cudaMemcpyAsync(hinv.data() + size_t(k) * L.np, D.phinv[k], sizeof(T) * L.np, cudaMemcpyDeviceToHost, st));
+      }
+    }
+    CUDA_TRY(c, cudaStreamSynchronize(st));
+    const double h = c->cfg.h;
+    int off = 0;
+    for (int i = 0; i < nb; i++) {
+      int e = L.bmap[i];
+      if (e >= 0) {
+        double s[6] = {0, 0, 0, 0, 0, 0};
+        for (int q = L.rseg[e]; q < L.rseg[e + 1]; q++)
+          for (int k = 0; k < 6; k++) s[k] += double(J6[size_t(k) * L.ER + q]) * x[L.erow[q]];
+        double r[6];
+        for (int k = 0; k < 6; k++) r[k] = h * s[k] - double(g6[size_t(k) * L.nr + e]);
+        const T *S6 = nullptr;
+        (void)S6;
+        double Si[6];
+        for (int k = 0; k < 6; k++) Si[k] = double(Iwi[size_t(k) * L.nr + e]);
+        du[off + 0] = r[0] * double(im[e]); du[off + 1] = r[1] * double(im[e]); du[off + 2] = r[2] * double(im[e]);
+        du[off + 3] = Si[0] * r[3] + Si[3] * r[4] + Si[4] * r[5];
+        du[off + 4] = Si[3] * r[3] + Si[1] * r[4] + Si[5] * r[5];
+        du[off + 5] = Si[4] * r[3] + Si[5] * r[4] + Si[2] * r[5];
+        off += 6;
+      } else {
+        int p = -e - 2;
+        double s[3] = {0, 0, 0};
+        for (int q = L.vseg[p]; q < L.vseg[p + 1]; q++)
+          for (int k = 0; k < 3; k++) s[k] += double(J3[size_t(k) * L.EV + q]) * x[L.erow[L.ER + q]];
+        for (int k = 0; k < 3; k++)
+          du[off + k] = (h * s[k] - double(g3[size_t(k) * L.np + p])) * double(hinv[size_t(k) * L.np + p]);
+        off += 3;
+      }
+    }
+  }
+  return NSN_OK;
+}
+
+template <typename T>
+nsn_status do_system(nsn_ctx *c, double *b, double *diag, double *hvec, double *g) {
+  Dev<T> &D = dev<T>(c);
+  nsn_status s;
+  if ((s = copy_out<T>(c, D.b, D.R, b))) return s;
+  if ((s = copy_out<T>(c, D.P, D.R, diag, 1))) return s;
+  if ((s = copy_out<T>(c, D.hv, D.R, hvec))) return s;
+  if (g) {
+    const Layout &L = c->L;
+    std::vector<double> g6(size_t(6) * L.nr), g3(size_t(3) * L.np);
+    for (int k = 0; k < 6; k++)
+      if ((s = copy_out<T>(c, D.rg[k], L.nr, g6.data() + size_t(k) * L.nr))) return s;
+    for (int k = 0; k < 3; k++)
+      if ((s = copy_out<T>(c, D.pg[k], L.np, g3.data() + size_t(k) * L.np))) return s;
+    int off = 0;
+    for (size_t i = 0; i < c->scene.kind.size(); i++) {
+      int e = L.bmap[i];
+      if (e >= 0) { for (int k = 0; k < 6; k++) g[off + k] = g6[size_t(k) * L.nr + e]; off += 6; }
+      else { int p = -e - 2; for (int k = 0; k < 3; k++) g[off + k] = g3[size_t(k) * L.np + p]; off += 3; }
+    }
+  }
+  return NSN_OK;
+}
+
+}  // namespace
+
+// =====================================================================================
+// C ABI
+
+extern "C" {
+
+void nsn_default_config(nsn_config *cfg) {
+  if (!cfg) return;
+  std::memset(cfg, 0, sizeof *cfg);
+  cfg->h = 1.0 / 60.0;
+  cfg->gravity[2] = -9.81;
+  cfg->newton_iters = 4;
+  cfg->cr_iters = 20;
+  cfg->damping = 0.75;
+  cfg->eps = 1e-6;
+  cfg->tol_rel = 0.0;
+  cfg->cr_tol_mode = 0;
+  cfg->ncp = NSN_NCP_FB;
+  cfg->rscale = NSN_R_EFFMASS;
+  cfg->geom_stiffness = NSN_GS_PARTICLES;
+  cfg->precision = NSN_FP32;
+  cfg->use_graph = 1;
+}
+
+nsn_status nsn_create(const nsn_config *cfg, void *stream, nsn_ctx **out) {
+  if (!out) return NSN_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!valid_cfg(cfg)) return NSN_ERR_INVALID_ARG;
+  nsn_ctx *c = new (std::nothrow) nsn_ctx();
+  if (!c) return NSN_ERR_OUT_OF_MEMORY;
+  c->cfg = *cfg;
+  if (stream) c->stream = static_cast<cudaStream_t>(stream);
+  else {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) { delete c; return NSN_ERR_CUDA; }
+    c->own_stream = true;
+  }
+  if (cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess) {
+    delete c;
+    return NSN_ERR_CUDA;
+  }
+  *out = c;
+  return NSN_OK;
+}
+
+nsn_status nsn_destroy(nsn_ctx *c) {
+  if (!c) return NSN_ERR_INVALID_ARG;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  if (c->dmem) cudaFree(c->dmem);
+  if (c->ev0) cudaEventDestroy(c->ev0);
+  if (c->ev1) cudaEventDestroy(c->ev1);
+  if (c->own_stream) cudaStreamDestroy(c->stream);
+  delete c;
+  return NSN_OK;
+}
+
+const char *nsn_last_error(const nsn_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+nsn_status nsn_add_bodies(nsn_ctx *c, int32_t n, const int32_t *kind, const float *pos, const float *quat,
+                          const float *vel, const float *omega, const float *mass, const float *inertia,
+                          int32_t *first_id) {
+  if (!c) return NSN_ERR_INVALID_ARG;
+  if (n < 0 || (n > 0 && (!kind || !pos || !vel || !mass))) return fail(c, NSN_ERR_INVALID_ARG, "add_bodies: null array");
+  for (int i = 0; i < n; i++) {
+    if (kind[i] != NSN_RIGID && kind[i] != NSN_PARTICLE) return fail(c, NSN_ERR_INVALID_ARG, "body %d: bad kind", i);
+    if (!(mass[i] > 0.f) || !std::isfinite(mass[i])) return fail(c, NSN_ERR_INVALID_ARG, "body %d: mass must be > 0", i);
+    if (kind[i] == NSN_RIGID) {
+      if (!inertia) return fail(c, NSN_ERR_INVALID_ARG, "rigid bodies need inertia");
+      for (int k = 0; k < 3; k++)
+        if (!(inertia[3 * i + k] > 0.f)) return fail(c, NSN_ERR_INVALID_ARG, "body %d: inertia must be > 0", i);
+    }
+  }
+  if (!finite_all(pos, size_t(3) * n) || !finite_all(vel, size_t(3) * n) ||
+      (quat && !finite_all(quat, size_t(4) * n)) || (omega && !finite_all(omega, size_t(3) * n)))
+    return fail(c, NSN_ERR_INVALID_ARG, "add_bodies: non-finite state");
+  HostScene &S = c->scene;
+  if (first_id) *first_id = int32_t(S.kind.size());
+  for (int i = 0; i < n; i++) {
+    S.kind.push_back(kind[i]);
+    for (int k = 0; k < 3; k++) {
+      S.pos.push_back(pos[3 * i + k]);
+      S.vel.push_back(vel[3 * i + k]);
+      S.omega.push_back(omega ? omega[3 * i + k] : 0.f);
+      S.inertia.push_back(inertia && kind[i] == NSN_RIGID ? inertia[3 * i + k] : 1.f);
+    }
+    float q[4] = {1, 0, 0, 0};
+    if (quat && kind[i] == NSN_RIGID) {
+      double nn = 0;
+      for (int k = 0; k < 4; k++) nn += double(quat[4 * i + k]) * quat[4 * i + k];
+      if (!(nn > 0)) return fail(c, NSN_ERR_INVALID_ARG, "body %d: zero quaternion", i);
+      for (int k = 0; k < 4; k++) q[k] = float(quat[4 * i + k] / std::sqrt(nn));
+    }
+    for (int k = 0; k < 4; k++) S.quat.push_back(q[k]);
+    S.mass.push_back(mass[i]);
+  }
+  c->dirty = true;
+  return NSN_OK;
+}
+
+nsn_status nsn_add_constraints(nsn_ctx *c, int32_t type, int32_t n, const void *records, int32_t *first_row) {
+  if (!c) return NSN_ERR_INVALID_ARG;
+  if (n < 0 || (n > 0 && !records)) return fail(c, NSN_ERR_INVALID_ARG, "add_constraints: null records");
+  HostScene &S = c->scene;
+  const int nb = int(S.kind.size());
+  auto body_ok = [&](int id) { return id >= -1 && id < nb; };
+  if (type == NSN_CONTACT) {
+    const nsn_contact *r = static_cast<const nsn_contact *>(records);
+    for (int i = 0; i < n; i++) {
+      if (!body_ok(r[i].body_a) || !body_ok(r[i].body_b) || (r[i].body_a < 0 && r[i].body_b < 0) ||
+          r[i].body_a == r[i].body_b)
+        return fail(c, NSN_ERR_INVALID_ARG, "contact %d: bad body ids", i);
+      double nn = double(r[i].n[0]) * r[i].n[0] + double(r[i].n[1]) * r[i].n[1] + double(r[i].n[2]) * r[i].n[2];
+      if (!(nn > 1e-12) || !finite_all(r[i].pa, 3) || !finite_all(r[i].pb, 3) || !std::isfinite(r[i].d) ||
+          !(r[i].mu >= 0.f))
+        return fail(c, NSN_ERR_INVALID_ARG, "contact %d: bad geometry", i);
+    }
+    if (first_row) *first_row = 3 * int32_t(S.contacts.size());
+    S.contacts.insert(S.contacts.end(), r, r + n);
+  } else if (type == NSN_REVOLUTE) {
+    const nsn_revolute *r = static_cast<const nsn_revolute *>(records);
+    for (int i = 0; i < n; i++) {
+      int a = r[i].body_a, b = r[i].body_b;
+      if (!body_ok(a) || !body_ok(b) || (a < 0 && b < 0) || a == b) return fail(c, NSN_ERR_INVALID_ARG, "joint %d: bad body ids", i);
+      if ((a >= 0 && S.kind[a] != NSN_RIGID) || (b >= 0 && S.kind[b] != NSN_RIGID))
+        return fail(c, NSN_ERR_INVALID_ARG, "joint %d: revolute joints connect rigid bodies", i);
+      if (!(r[i].compliance >= 0.f)) return fail(c, NSN_ERR_INVALID_ARG, "joint %d: compliance < 0", i);
+    }
+    if (first_row) *first_row = 5 * int32_t(S.joints.size());
+    S.joints.insert(S.joints.end(), r, r + n);
+  } else if (type == NSN_TET_NH) {
+    const nsn_tet *r = static_cast<const nsn_tet *>(records);
+    for (int i = 0; i < n; i++) {
+      for (int q = 0; q < 4; q++) {
+        int v = r[i].v[q];
+        if (v < 0 || v >= nb || S.kind[v] != NSN_PARTICLE) return fail(c, NSN_ERR_INVALID_ARG, "tet %d: vertex %d is not a particle", i, q);
+        for (int p = 0; p < q; p++)
+          if (r[i].v[p] == v) return fail(c, NSN_ERR_INVALID_ARG, "tet %d: repeated vertex", i);
+      }
+      double Dm[9];
+      for (int row = 0; row < 3; row++)
+        for (int k = 0; k < 3; k++) Dm[3 * row + k] = double(r[i].rest[k + 1][row]) - double(r[i].rest[0][row]);
+      double det = Dm[0] * (Dm[4] * Dm[8] - Dm[5] * Dm[7]) - Dm[1] * (Dm[3] * Dm[8] - Dm[5] * Dm[6]) +
+                   Dm[2] * (Dm[3] * Dm[7] - Dm[4] * Dm[6]);
+      if (!(std::fabs(det) > 1e-18)) return fail(c, NSN_ERR_INVALID_ARG, "tet %d: degenerate rest shape", i);
+      if (!(r[i].E > 0.f) || !(r[i].nu > 0.f && r[i].nu < 0.5f)) return fail(c, NSN_ERR_INVALID_ARG, "tet %d: bad material", i);
+    }
+    if (first_row) *first_row = 3 * int32_t(S.tets.size());
+    S.tets.insert(S.tets.end(), r, r + n);
+  } else {
+    return fail(c, NSN_ERR_INVALID_ARG, "unknown constraint type %d", type);
+  }
+  c->dirty = true;
+  return NSN_OK;
+}
+
+nsn_status nsn_clear_contacts(nsn_ctx *c) {
+  if (!c) return NSN_ERR_INVALID_ARG;
+  c->scene.contacts.clear();
+  c->dirty = true;
+  return NSN_OK;
+}
+
+nsn_status nsn_counts(nsn_ctx *c, int32_t *n_bodies, int32_t *n_rows) {
+  if (!c) return NSN_ERR_INVALID_ARG;
+  if (n_bodies) *n_bodies = int32_t(c->scene.kind.size());
+  if (n_rows) *n_rows = int32_t(3 * c->scene.contacts.size() + 5 * c->scene.joints.size() + 3 * c->scene.tets.size());
+  return NSN_OK;
+}
+
+nsn_status nsn_step(nsn_ctx *c, int32_t nsteps, nsn_stats *stats) {
+  if (!c || nsteps < 0) return NSN_ERR_INVALID_ARG;
+  nsn_status s = ensure_built(c);
+  if (s != NSN_OK) return s;
+  c->linearized = false;
+  s = c->cfg.precision == NSN_FP64 ? run_steps<double>(c, nsteps) : run_steps<float>(c, nsteps);
+  if (stats) *stats = c->last;
+  return s;
+}
+
+}  // extern "C"
+
+nsn_status state_io(nsn_ctx *c, bool set, bool device, const float *ipos, const float *iquat,
+                    const float *ivel, const float *iom, float *opos, float *oquat, float *ovel, float *oom) {
+  if (!c) return NSN_ERR_INVALID_ARG;
+  nsn_status s = ensure_built(c);
+  if (s != NSN_OK) return s;
+  const int nb = int(c->scene.kind.size());
+  if (!nb) return NSN_OK;
+  cudaStream_t st = c->stream;
+  float *stg = c->d_stage;
+  float *sp = stg, *sq = stg + 3 * nb, *sv = stg + 7 * nb, *so = stg + 10 * nb;
+  if (set) {
+    const float *p = ipos, *q = iquat, *v = ivel, *o = iom;
+    if (!device) {
+      if (ipos) { CUDA_TRY(c, cudaMemcpyAsync(sp, ipos, sizeof(float) * 3 * nb, cudaMemcpyHostToDevice, st)); p = sp; }
+      if (iquat) { CUDA_TRY(c, cudaMemcpyAsync(sq, iquat, sizeof(float) * 4 * nb, cudaMemcpyHostToDevice, st)); q = sq; }
+      if (ivel) { CUDA_TRY(c, cudaMemcpyAsync(sv, ivel, sizeof(float) * 3 * nb, cudaMemcpyHostToDevice, st)); v = sv; }
+      if (iom) { CUDA_TRY(c, cudaMemcpyAsync(so, iom, sizeof(float) * 3 * nb, cudaMemcpyHostToDevice, st)); o = so; }
+    }
+    if (c->cfg.precision == NSN_FP64)
+      k_scatter_state<double><<<cdiv(nb, 128), 128, 0, st>>>(c->d64, c->d_bmap, nb, p, q, v, o);
+    else
+      k_scatter_state<float><<<cdiv(nb, 128), 128, 0, st>>>(c->d32, c->d_bmap, nb, p, q, v, o);
+    CUDA_TRY(c, cudaGetLastError());
+    if (!device) CUDA_TRY(c, cudaStreamSynchronize(st));
+  } else {
+    float *p = device ? opos : (opos ? sp : nullptr), *q = device ? oquat : (oquat ? sq : nullptr);
+    float *v = device ? ovel : (ovel ? sv : nullptr), *o = device ? oom : (oom ? so : nullptr);
+    if (c->cfg.precision == NSN_FP64)
+      k_gather_state<double><<<cdiv(nb, 128), 128, 0, st>>>(c->d64, c->d_bmap, nb, p, q, v, o);
+    else
+      k_gather_state<float><<<cdiv(nb, 128), 128, 0, st>>>(c->d32, c->d_bmap, nb, p, q, v, o);
+    CUDA_TRY(c, cudaGetLastError());
+    if (!device) {
+      if (opos) CUDA_TRY(c, cudaMemcpyAsync(opos, sp, sizeof(float) * 3 * nb, cudaMemcpyDeviceToHost, st));
+      if (oquat) CUDA_TRY(c, cudaMemcpyAsync(oquat, sq, sizeof(float) * 4 * nb, cudaMemcpyDeviceToHost, st));
+      if (ovel) CUDA_TRY(c, cudaMemcpyAsync(ovel, sv, sizeof(float) * 3 * nb, cudaMemcpyDeviceToHost, st));
+      if (oom) CUDA_TRY(c, cudaMemcpyAsync(oom, so, sizeof(float) * 3 * nb, cudaMemcpyDeviceToHost, st));
+      CUDA_TRY(c, cudaStreamSynchronize(st));
+    }
+  }
+  return NSN_OK;
+}
+
+extern "C" {
+
+nsn_status nsn_get_state(nsn_ctx *c, float *pos, float *quat, float *vel, float *omega) {
+  return state_io(c, false, false, nullptr, nullptr, nullptr, nullptr, pos, quat, vel, omega);
+}
+nsn_status nsn_set_state(nsn_ctx *c, const float *pos, const float *quat, const float *vel, const float *omega) {
+  return state_io(c, true, false, pos, quat, vel, omega, nullptr, nullptr, nullptr, nullptr);
+}
+nsn_status nsn_set_state_device(nsn_ctx *c, const float *pos, const float *quat, const float *vel, const float *omega) {
+  return state_io(c, true, true, pos, quat, vel, omega, nullptr, nullptr, nullptr, nullptr);
+}
+nsn_status nsn_get_state_device(nsn_ctx *c, float *pos, float *quat, float *vel, float *omega) {
+  return state_io(c, false, true, nullptr, nullptr, nullptr, nullptr, pos, quat, vel, omega);
+}
+
+nsn_status nsn_get_lambda(nsn_ctx *c, double *lambda) {
+  if (!c || !lambda) return NSN_ERR_INVALID_ARG;
+  nsn_status s = ensure_built(c);
+  if (s != NSN_OK) return s;
+  return c->cfg.precision == NSN_FP64 ? copy_out<double>(c, c->d64.lam, c->L.R, lambda)
+                                      : copy_out<float>(c, c->d32.lam, c->L.R, lambda);
+}
+
+nsn_status nsn_get_merit_history(nsn_ctx *c, double *out, int32_t cap, int32_t *n) {
+  if (!c) return NSN_ERR_INVALID_ARG;
+  nsn_status s = ensure_built(c);
+  if (s != NSN_OK) return s;
+  Scalars sc;
+  Scalars *src = c->cfg.precision == NSN_FP64 ? c->d64.sc : c->d32.sc;
+  CUDA_TRY(c, cudaMemcpyAsync(&sc, src, sizeof(Scalars), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  // merit at each solved Newton iteration, then at the returned iterate
+  const int solved = std::min(c->last.newton_done, 1023);
+  std::vector<double> hist(sc.merit, sc.merit + solved);
+  hist.push_back(sc.merit[std::min(c->cfg.newton_iters, 1023)]);
+  if (n) *n = int32_t(hist.size());
+  if (out)
+    for (int i = 0; i < std::min<int>(cap, int(hist.size())); i++) out[i] = hist[i];
+  return NSN_OK;
+}
+
+nsn_status nsn_linearize(nsn_ctx *c, int32_t n_before) {
+  if (!c || n_before < 0 || n_before > 1000) return NSN_ERR_INVALID_ARG;
+  nsn_status s = ensure_built(c);
+  if (s != NSN_OK) return s;
+  c->lin_buf = n_before & 1;
+  return c->cfg.precision == NSN_FP64 ? do_linearize<double>(c, n_before) : do_linearize<float>(c, n_before);
+}
+
+nsn_status nsn_apply_operator(nsn_ctx *c, const double *x, double *y) {
+  if (!c || !x || !y) return NSN_ERR_INVALID_ARG;
+  if (!c->linearized || c->dirty) return fail(c, NSN_ERR_BAD_STATE, "call nsn_linearize first");
+  return c->cfg.precision == NSN_FP64 ? do_apply<double>(c, x, y) : do_apply<float>(c, x, y);
+}
+
+nsn_status nsn_solve(nsn_ctx *c, int32_t iters, double *dlambda, double *du) {
+  if (!c || iters < 0) return NSN_ERR_INVALID_ARG;
+  if (!c->linearized || c->dirty) return fail(c, NSN_ERR_BAD_STATE, "call nsn_linearize first");
+  return c->cfg.precision == NSN_FP64 ? do_solve<double>(c, iters, dlambda, du) : do_solve<float>(c, iters, dlambda, du);
+}
+
+nsn_status nsn_get_system(nsn_ctx *c, double *b, double *diag, double *hvec, double *g) {
+  if (!c) return NSN_ERR_INVALID_ARG;
+  if (!c->linearized || c->dirty) return fail(c, NSN_ERR_BAD_STATE, "call nsn_linearize first");
+  return c->cfg.precision == NSN_FP64 ? do_system<double>(c, b, diag, hvec, g) : do_system<float>(c, b, diag, hvec, g);
+}
+
+nsn_status nsn_last_launch_count(nsn_ctx *c, int32_t *kernels_per_step) {
+  if (!c || !kernels_per_step) return NSN_ERR_INVALID_ARG;
+  *kernels_per_step = c->launches_per_step;
+  return NSN_OK;
+}
+
+}  // extern "C"

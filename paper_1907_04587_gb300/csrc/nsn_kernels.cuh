@@ -1,0 +1,1045 @@
+// nsn_kernels.cuh -- sm_103a kernels of the non-smooth Newton time stepper.
+//
+// Data layout (structure of arrays, one array per component):
+//   rigid bodies   x[3] q[4] x0[3] q0[4] u[6]=[v,w] ut[6] m invm Ib[3]
+//                  Iw[6] Iwi[6] (symmetric xx yy zz xy xz yz) g[6] yg[6]
+//   particles      x[3] x0[3] u[3] ut[3] m hinv[3] (H~^-1 diagonal) g[3] yg[3] uprev[3]
+//   entries        one per (row, side): rigid entries [0, ER) sorted by body,
+//                  particle entries [ER, ER+EV) sorted by particle; erow[e]
+//                  is the row, ej6[6][ER] / ej3[2][3][EV] the Jacobian values
+//                  (particle values double-buffered by Newton iteration for
+//                  the geometric stiffness), rseg / vseg the segment offsets.
+//   rows           pair rows (contacts, joints) carry entry ids re0/re1
+//                  (-1 for the world side); tet rows te[12 per tet].
+//
+// Every operator apply is two passes with no global atomics:
+//   body pass : per body segment  s = sum_e J_e x[row(e)],  y = H~^-1 s,
+//               then per entry    t[e] = J_e . y
+//   row pass  : per row           w_i = sum_{e in row i} t[e] + (C x)_i + eps x_i
+// CR dot products are fused into the row pass as FP64 block partials; the CR
+// update reduces them (every block redundantly, deterministic order).
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+namespace nsn {
+
+constexpr int BLOCK = 256;
+constexpr int NPART = 4;  // partials per block in the row passes
+
+enum BodyMode { BM_RESIDUAL = 0, BM_APPLY = 1, BM_UPDATE = 2 };
+enum RowMode { RM_RHS = 0, RM_APPLY = 1 };
+
+struct Flags {
+  int newton_stop;   // set when merit <= tol * merit0: later kernels of the step return
+  int cr_stop;       // set when the CR tolerance is met in this Newton iteration
+  int newton_count;  // Newton iterations solved
+  int cr_count;      // CR iterations performed (all Newton iterations)
+};
+
+// FP64 scalars kept on the device
+struct Scalars {
+  double merit[1024];   // merit per Newton iteration (+ final)
+  double merit0;
+  double eta;           // CR forcing term of this Newton iteration
+  double res0;          // ||r_0||_P of this Newton iteration
+  double rho[2];        // CR rho, double-buffered by iteration parity
+  double appap[2];      // CR Ap^T P Ap, double-buffered by iteration parity
+  double alpha, beta;   // CR step of the current iteration
+};
+
+template <typename T>
+struct Dev {
+  // sizes
+  int nr, np, nc, nj, nt, R, Rpair, ER, EV;
+  // parameters
+  double h, eps, damping, tol_rel;
+  double grav[3];
+  int ncp, rscale, gs, cr_tol;
+  // rigid bodies
+  T *rx[3], *rq[4], *rx0[3], *rq0[4], *ru[6], *rut[6], *rm, *rinvm, *rIb[3], *rIw[6], *rIwi[6], *rg[6], *ryg[6];
+  // particles
+  T *px[3], *px0[3], *pu[3], *put[3], *pm, *phinv[3], *pg[3], *pyg[3], *puprev[3];
+  // entries
+  int *erow;
+  int *rseg, *vseg;
+  T *ej6[6];
+  T *ej3[2][3];
+  T *t, *t2;
+  // rows
+  int *re0, *re1, *te;
+  T *lam, *cdiag, *hv, *b, *P, *x, *z, *p, *Ap, *Az;
+  T *c3;
+  // contacts
+  int *cba, *cbb;
+  T *cpa[3], *cpb[3], *cn[3], *cdd, *cmu;
+  // joints
+  int *jba, *jbb;
+  T *jpa[3], *jpb[3], *jaxa[3], *jaxb[3], *je;
+  // tets
+  int *tv;
+  T *tDmi, *tVe, *tC1, *tD1, *talpha;
+  // reductions
+  double *part_body;   // one per body-pass block
+  double *part_row;    // NPART per row-pass block
+  int nblk_body_r, nblk_body_p, nblk_row_pair, nblk_row_tet, nblk_upd;
+  Scalars *sc;
+  Flags *fl;
+};
+
+// ------------------------------------------------------------------------------------
+// small math
+
+template <typename T>
+__device__ __forceinline__ void cross3(const T *a, const T *b, T *c) {
+  c[0] = a[1] * b[2] - a[2] * b[1];
+  c[1] = a[2] * b[0] - a[0] * b[2];
+  c[2] = a[0] * b[1] - a[1] * b[0];
+}
+template <typename T>
+__device__ __forceinline__ T dot3(const T *a, const T *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+template <typename T>
+__device__ __forceinline__ T dsqrt(T v) { return sqrt(v); }
+template <>
+__device__ __forceinline__ float dsqrt<float>(float v) { return sqrtf(v); }
+
+template <typename T>
+__device__ __forceinline__ void quat_R(const T *q, T *R) {
+  T w = q[0], x = q[1], y = q[2], z = q[3];
+  R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w * z);     R[2] = 2 * (x * z + w * y);
+  R[3] = 2 * (x * y + w * z);     R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - w * x);
+  R[6] = 2 * (x * z - w * y);     R[7] = 2 * (y * z + w * x);     R[8] = 1 - 2 * (x * x + y * y);
+}
+
+template <typename T>
+__device__ __forceinline__ void mat3v(const T *M, const T *x, T *y) {
+  y[0] = M[0] * x[0] + M[1] * x[1] + M[2] * x[2];
+  y[1] = M[3] * x[0] + M[4] * x[1] + M[5] * x[2];
+  y[2] = M[6] * x[0] + M[7] * x[1] + M[8] * x[2];
+}
+
+// symmetric 3x3 stored xx yy zz xy xz yz
+template <typename T>
+__device__ __forceinline__ void sym3v(const T *S, const T *x, T *y) {
+  y[0] = S[0] * x[0] + S[3] * x[1] + S[4] * x[2];
+  y[1] = S[3] * x[0] + S[1] * x[1] + S[5] * x[2];
+  y[2] = S[4] * x[0] + S[5] * x[1] + S[2] * x[2];
+}
+
+// Orthonormal basis from a unit vector: Duff et al., "Building an Orthonormal
+// Basis, Revisited", JCGT 6(1), 2017 (branchless form).
+template <typename T>
+__device__ __forceinline__ void basis(const T *n, T *t1, T *t2) {
+  T sign = n[2] >= T(0) ? T(1) : T(-1);
+  T a = T(-1) / (sign + n[2]);
+  T b = n[0] * n[1] * a;
+  t1[0] = T(1) + sign * n[0] * n[0] * a; t1[1] = sign * b; t1[2] = -sign * n[0];
+  t2[0] = b; t2[1] = sign + n[1] * n[1] * a; t2[2] = -n[1];
+}
+
+// Symmetric 3x3 eigen-decomposition by cyclic Jacobi rotations (Golub & Van
+// Loan, Matrix Computations, Sec. 8.5.2).  w sorted descending, V columns.
+template <typename T>
+__device__ void eig_sym3(const T *Ain, T *w, T *V) {
+  T A[9];
+#pragma unroll
+  for (int i = 0; i < 9; i++) { A[i] = Ain[i]; V[i] = (i % 4 == 0) ? T(1) : T(0); }
+  const T tiny = sizeof(T) == 4 ? T(1e-14) : T(1e-34);
+  for (int sweep = 0; sweep < 32; sweep++) {
+    T off = A[1] * A[1] + A[2] * A[2] + A[5] * A[5];
+    T dia = A[0] * A[0] + A[4] * A[4] + A[8] * A[8];
+    if (off == T(0) || off <= tiny * dia) break;
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+      const int p = k == 2 ? 1 : 0, q = k == 0 ? 1 : 2;
+      T apq = A[3 * p + q];
+      if (apq == T(0)) continue;
+      T tau = (A[3 * q + q] - A[3 * p + p]) / (T(2) * apq);
+      T t = (tau >= T(0) ? T(1) : T(-1)) / (fabs(tau) + dsqrt(T(1) + tau * tau));
+      T c = T(1) / dsqrt(T(1) + t * t), s = t * c;
+#pragma unroll
+      for (int r = 0; r < 3; r++) {
+        T arp = A[3 * r + p], arq = A[3 * r + q];
+        A[3 * r + p] = c * arp - s * arq;
+        A[3 * r + q] = s * arp + c * arq;
+      }
+#pragma unroll
+      for (int r = 0; r < 3; r++) {
+        T apr = A[3 * p + r], aqr = A[3 * q + r];
+        A[3 * p + r] = c * apr - s * aqr;
+        A[3 * q + r] = s * apr + c * aqr;
+      }
+#pragma unroll
+      for (int r = 0; r < 3; r++) {
+        T vrp = V[3 * r + p], vrq = V[3 * r + q];
+        V[3 * r + p] = c * vrp - s * vrq;
+        V[3 * r + q] = s * vrp + c * vrq;
+      }
+    }
+  }
+  T ww[3] = {A[0], A[4], A[8]};
+  int i0 = 0, i1 = 1, i2 = 2, tmp;
+  if (ww[i1] > ww[i0]) { tmp = i0; i0 = i1; i1 = tmp; }
+  if (ww[i2] > ww[i0]) { tmp = i0; i0 = i2; i2 = tmp; }
+  if (ww[i2] > ww[i1]) { tmp = i1; i1 = i2; i2 = tmp; }
+  int idx[3] = {i0, i1, i2};
+  T Vs[9];
+#pragma unroll
+  for (int k = 0; k < 3; k++) {
+    w[k] = ww[idx[k]];
+#pragma unroll
+    for (int r = 0; r < 3; r++) Vs[3 * r + k] = V[3 * r + idx[k]];
+  }
+#pragma unroll
+  for (int i = 0; i < 9; i++) V[i] = Vs[i];
+}
+
+template <typename T>
+__device__ __forceinline__ T det3(const T *M) {
+  return M[0] * (M[4] * M[8] - M[5] * M[7]) - M[1] * (M[3] * M[8] - M[5] * M[6]) + M[2] * (M[3] * M[7] - M[4] * M[6]);
+}
+
+// Signed SVD F = U diag(s) V^T, U and V rotations, s1 >= s2 >= |s3| (s3 < 0 for
+// inverted elements): eigenvectors of F^T F, u_k = F v_k / |F v_k| with
+// Gram-Schmidt, u3 = u1 x u2.
+template <typename T>
+__device__ void svd3(const T *F, T *U, T *s, T *V) {
+  T FtF[9];
+#pragma unroll
+  for (int i = 0; i < 3; i++)
+#pragma unroll
+    for (int j = 0; j < 3; j++) FtF[3 * i + j] = F[i] * F[j] + F[3 + i] * F[3 + j] + F[6 + i] * F[6 + j];
+  T w[3];
+  eig_sym3(FtF, w, V);
+  if (det3(V) < T(0)) { V[2] = -V[2]; V[5] = -V[5]; V[8] = -V[8]; }
+  T v[3][3], fv[3][3], u[3][3];
+#pragma unroll
+  for (int k = 0; k < 3; k++) {
+    v[k][0] = V[k]; v[k][1] = V[3 + k]; v[k][2] = V[6 + k];
+    mat3v(F, v[k], fv[k]);
+  }
+  T fn = dsqrt(FtF[0] + FtF[4] + FtF[8]);
+  T tiny = (sizeof(T) == 4 ? T(1e-6) : T(1e-14)) * (fn > T(0) ? fn : T(1));
+  T n1 = dsqrt(dot3(fv[0], fv[0]));
+  if (n1 > tiny) { for (int r = 0; r < 3; r++) u[0][r] = fv[0][r] / n1; }
+  else { u[0][0] = 1; u[0][1] = 0; u[0][2] = 0; }
+  T pr = dot3(u[0], fv[1]);
+#pragma unroll
+  for (int r = 0; r < 3; r++) u[1][r] = fv[1][r] - pr * u[0][r];
+  T n2 = dsqrt(dot3(u[1], u[1]));
+  if (n2 > tiny) { for (int r = 0; r < 3; r++) u[1][r] /= n2; }
+  else { T t2[3]; basis(u[0], u[1], t2); }
+  cross3(u[0], u[1], u[2]);
+#pragma unroll
+  for (int k = 0; k < 3; k++) {
+    s[k] = dot3(u[k], fv[k]);
+    U[k] = u[k][0]; U[3 + k] = u[k][1]; U[6 + k] = u[k][2];
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// reductions
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum over the block; result valid in thread 0.  smem >= BLOCK/32 doubles.
+__device__ __forceinline__ double block_sum(double v, double *smem) {
+  v = warp_sum(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) smem[w] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (w == 0) {
+    r = l < (BLOCK >> 5) ? smem[l] : 0.0;
+    r = warp_sum(r);
+  }
+  return r;
+}
+
+template <int G, typename T>
+__device__ __forceinline__ T group_sum(T v) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, G);
+  return v;
+}
+
+// Deterministic sum of n partials at stride NPART (+ offset) by warp 0; all
+// threads of the block receive the result via shared memory.
+__device__ __forceinline__ void reduce_partials(const double *part, int n, double *out4, double *smem) {
+  if (threadIdx.x < 32) {
+    double a[NPART] = {0, 0, 0, 0};
+    for (int i = threadIdx.x; i < n; i += 32)
+#pragma unroll
+      for (int k = 0; k < NPART; k++) a[k] += part[NPART * i + k];
+#pragma unroll
+    for (int k = 0; k < NPART; k++) a[k] = warp_sum(a[k]);
+    if (threadIdx.x == 0)
+#pragma unroll
+      for (int k = 0; k < NPART; k++) smem[k] = a[k];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < NPART; k++) out4[k] = smem[k];
+  __syncthreads();
+}
+
+// ------------------------------------------------------------------------------------
+// K9: start of step -- q^-, world inertia at q^- (mass evaluated at q^-, Sec. 6.1),
+// unconstrained velocity u~ = u^- + h M~^-1 f with gravity and the explicit
+// gyroscopic torque -w x (I_w w) (Sec. 5); the iterate starts at u = 0 (Sec. 8.1).
+
+template <typename T>
+__global__ void k_begin_rigid(Dev<T> D) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) {
+    D.fl->newton_stop = 0; D.fl->cr_stop = 0; D.fl->newton_count = 0; D.fl->cr_count = 0;
+  }
+  if (i >= D.nr) return;
+  T q[4], R[9], Ib[3], w[3], Iw[9], Iwi[9];
+  for (int k = 0; k < 4; k++) { q[k] = D.rq[k][i]; D.rq0[k][i] = q[k]; }
+  for (int k = 0; k < 3; k++) { D.rx0[k][i] = D.rx[k][i]; Ib[k] = D.rIb[k][i]; w[k] = D.ru[3 + k][i]; }
+  quat_R(q, R);
+  for (int r = 0; r < 3; r++)
+    for (int s = 0; s < 3; s++) {
+      T a = 0, b = 0;
+      for (int k = 0; k < 3; k++) {
+        a += R[3 * r + k] * Ib[k] * R[3 * s + k];
+        b += R[3 * r + k] / Ib[k] * R[3 * s + k];
+      }
+      Iw[3 * r + s] = a;
+      Iwi[3 * r + s] = b;
+    }
+  const int si[6] = {0, 4, 8, 1, 2, 5};
+  for (int k = 0; k < 6; k++) { D.rIw[k][i] = Iw[si[k]]; D.rIwi[k][i] = Iwi[si[k]]; }
+  T Iww[3], tau[3], dw[3];
+  mat3v(Iw, w, Iww);
+  cross3(w, Iww, tau);
+  for (int k = 0; k < 3; k++) tau[k] = -tau[k];
+  mat3v(Iwi, tau, dw);
+  const T h = T(D.h);
+  for (int k = 0; k < 3; k++) {
+    D.rut[k][i] = D.ru[k][i] + h * T(D.grav[k]);
+    D.rut[3 + k][i] = w[k] + h * dw[k];
+    D.ru[k][i] = T(0);
+    D.ru[3 + k][i] = T(0);
+  }
+}
+
+template <typename T>
+__global__ void k_begin_particle(Dev<T> D) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= D.np) return;
+  const T h = T(D.h);
+  T m = D.pm[i];
+  for (int k = 0; k < 3; k++) {
+    D.px0[k][i] = D.px[k][i];
+    D.put[k][i] = D.pu[k][i] + h * T(D.grav[k]);
+    D.pu[k][i] = T(0);
+    D.puprev[k][i] = T(0);
+    D.phinv[k][i] = T(1) / m;
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// K1-K3: row evaluation at the iterate (q^n, u^n, lambda^n)
+
+// body id encoding: >= 0 rigid index, <= -2 particle index (-id-2), -1 world
+template <typename T>
+struct Side {
+  int kind;  // 0 world, 1 rigid, 2 particle
+  int idx;
+  T w[3];    // world point
+  T r[3];    // lever arm (rigid)
+};
+
+template <typename T>
+__device__ __forceinline__ void load_side(const Dev<T> &D, int enc, const T *p, Side<T> &s) {
+  if (enc >= 0) {
+    s.kind = 1; s.idx = enc;
+    T q[4], R[9];
+    for (int k = 0; k < 4; k++) q[k] = D.rq[k][enc];
+    quat_R(q, R);
+    mat3v(R, p, s.r);
+    for (int k = 0; k < 3; k++) s.w[k] = D.rx[k][enc] + s.r[k];
+  } else if (enc == -1) {
+    s.kind = 0; s.idx = -1;
+    for (int k = 0; k < 3; k++) { s.w[k] = p[k]; s.r[k] = T(0); }
+  } else {
+    s.kind = 2; s.idx = -enc - 2;
+    for (int k = 0; k < 3; k++) { s.w[k] = D.px[k][s.idx]; s.r[k] = T(0); }
+  }
+}
+
+// side Jacobian along direction d: [d, r x d] (rigid) or [d] (particle), times sgn
+template <typename T>
+__device__ __forceinline__ void side_row(const Side<T> &s, const T *d, T sgn, T *J6) {
+  for (int k = 0; k < 3; k++) J6[k] = sgn * d[k];
+  if (s.kind == 1) {
+    T rx[3];
+    cross3(s.r, d, rx);
+    for (int k = 0; k < 3; k++) J6[3 + k] = sgn * rx[k];
+  } else {
+    for (int k = 0; k < 3; k++) J6[3 + k] = T(0);
+  }
+}
+
+// J6 M~^-1 J6^T for one side (mass at q^-, no geometric-stiffness shift)
+template <typename T>
+__device__ __forceinline__ T side_quad(const Dev<T> &D, const Side<T> &s, const T *J6) {
+  if (s.kind == 0) return T(0);
+  if (s.kind == 1) {
+    T Si[6], t[3];
+    for (int k = 0; k < 6; k++) Si[k] = D.rIwi[k][s.idx];
+    sym3v(Si, J6 + 3, t);
+    return dot3(J6, J6) * D.rinvm[s.idx] + dot3(J6 + 3, t);
+  }
+  return dot3(J6, J6) / D.pm[s.idx];
+}
+
+template <typename T>
+__device__ __forceinline__ T side_dot_u(const Dev<T> &D, const Side<T> &s, const T *J6) {
+  if (s.kind == 1) {
+    T v = 0;
+    for (int k = 0; k < 6; k++) v += J6[k] * D.ru[k][s.idx];
+    return v;
+  }
+  if (s.kind == 2) return J6[0] * D.pu[0][s.idx] + J6[1] * D.pu[1][s.idx] + J6[2] * D.pu[2][s.idx];
+  return T(0);
+}
+
+template <typename T>
+__device__ __forceinline__ void write_entry(const Dev<T> &D, int e, const T *J6, int buf) {
+  if (e < 0) return;
+  if (e < D.ER) {
+    for (int k = 0; k < 6; k++) D.ej6[k][e] = J6[k];
+  } else {
+    const int v = e - D.ER;
+    for (int k = 0; k < 3; k++) D.ej3[buf][k][v] = J6[k];
+  }
+}
+
+// App. A.2 W_FB with the unsquared |D^T qdot| of the fixed point; stick gives
+// W = 0; a non-positive denominator is floored at 1e-6 (vt + r mu lambda_n).
+template <typename T>
+__device__ __forceinline__ T w_fb(T vt, T lf, T mu_ln, T r) {
+  T bb = mu_ln - lf;
+  T root = dsqrt(vt * vt + r * r * bb * bb);
+  T num = r * (root - r * bb);
+  T den = vt + r * mu_ln - root;
+  if (num == T(0)) return T(0);
+  T fl = T(1e-6) * (vt + r * mu_ln);
+  if (den < fl) den = fl;
+  return num / den;
+}
+
+template <typename T>
+__device__ __forceinline__ T w_min(T vt, T lf, T mu_ln, T r) {
+  T bb = r * (mu_ln - lf);
+  if (vt <= bb) return T(0);
+  return (vt - bb) / mu_ln;
+}
+
+template <typename T>
+__global__ void k_eval_contacts(Dev<T> D, int buf, int force) {
+  if (!force && D.fl->newton_stop) return;
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= D.nc) return;
+  const T h = T(D.h);
+  T pa[3], pb[3], n[3];
+  for (int k = 0; k < 3; k++) { pa[k] = D.cpa[k][c]; pb[k] = D.cpb[k][c]; n[k] = D.cn[k][c]; }
+  Side<T> A, B;
+  load_side(D, D.cba[c], pa, A);
+  load_side(D, D.cbb[c], pb, B);
+  T dd[3] = {A.w[0] - B.w[0], A.w[1] - B.w[1], A.w[2] - B.w[2]};
+  T Cn = dot3(n, dd) - D.cdd[c];
+  // geometric normal row and effective-mass r (Eq. rscaling)
+  T Ja[6], Jb[6];
+  side_row(A, n, T(1), Ja);
+  side_row(B, n, T(-1), Jb);
+  T rN = T(1);
+  if (D.rscale == 1) rN = h * h;
+  else if (D.rscale == 2) rN = h * h * (side_quad(D, A, Ja) + side_quad(D, B, Jb));
+  const int row = 3 * c;
+  T ln = D.lam[row];
+  T phi, al, S;
+  if (D.ncp == 1) {
+    if (Cn <= rN * ln) { phi = Cn; al = T(1); S = T(0); }
+    else { phi = rN * ln; al = T(0); S = rN; }
+  } else {
+    // r-scaled Fischer-Burmeister (App. A.1), subgradient alpha(0,0)=0, beta=1
+    T rl = rN * ln;
+    T rho = dsqrt(Cn * Cn + rl * rl);
+    phi = Cn + rl - rho;
+    if (rho == T(0)) { al = T(0); S = rN; }
+    else { al = T(1) - Cn / rho; S = (T(1) - rl / rho) * rN; }
+  }
+  for (int k = 0; k < 6; k++) { Ja[k] *= al; Jb[k] *= al; }
+  write_entry(D, D.re0[row], Ja, buf);
+  write_entry(D, D.re1[row], Jb, buf);
+  D.cdiag[row] = S / (h * h);
+  D.hv[row] = phi / h;
+  // friction rows D = [t_k, r_a x t_k | -t_k, -r_b x t_k] (Sec. 3.4)
+  T t[2][3];
+  basis(n, t[0], t[1]);
+  T Da[2][6], Db[2][6], vt[2], dq = T(0);
+  for (int k = 0; k < 2; k++) {
+    side_row(A, t[k], T(1), Da[k]);
+    side_row(B, t[k], T(-1), Db[k]);
+    vt[k] = side_dot_u(D, A, Da[k]) + side_dot_u(D, B, Db[k]);
+    dq += side_quad(D, A, Da[k]) + side_quad(D, B, Db[k]);
+  }
+  T rF = T(1);
+  if (D.rscale == 1) rF = h;
+  else if (D.rscale == 2) rF = h * T(0.5) * dq;
+  T mu_ln = D.cmu[c] * ln;
+  T lf[2] = {D.lam[row + 1], D.lam[row + 2]};
+  if (mu_ln > T(0)) {
+    T vn = dsqrt(vt[0] * vt[0] + vt[1] * vt[1]);
+    T lfn = dsqrt(lf[0] * lf[0] + lf[1] * lf[1]);
+    T W = D.ncp == 1 ? w_min(vn, lfn, mu_ln, rF) : w_fb(vn, lfn, mu_ln, rF);
+    for (int k = 0; k < 2; k++) {
+      write_entry(D, D.re0[row + 1 + k], Da[k], buf);
+      write_entry(D, D.re1[row + 1 + k], Db[k], buf);
+      D.cdiag[row + 1 + k] = W / h;
+      D.hv[row + 1 + k] = vt[k] + W * lf[k];
+    }
+  } else {
+    // inactive: rows zeroed, W = 1, h_f = lambda_f (drives lambda_f to zero)
+    T Z[6] = {0, 0, 0, 0, 0, 0};
+    for (int k = 0; k < 2; k++) {
+      write_entry(D, D.re0[row + 1 + k], Z, buf);
+      write_entry(D, D.re1[row + 1 + k], Z, buf);
+      D.cdiag[row + 1 + k] = T(1) / h;
+      D.hv[row + 1 + k] = lf[k];
+    }
+  }
+}
+
+// revolute joint: 3 positional rows (anchor coincidence) + 2 angular rows
+// a_w . b_k = 0 with b_1, b_2 perpendicular to b's hinge axis.
+template <typename T>
+__global__ void k_eval_joints(Dev<T> D, int buf, int force) {
+  if (!force && D.fl->newton_stop) return;
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= D.nj) return;
+  const T h = T(D.h);
+  T pa[3], pb[3], axa[3], axb[3];
+  for (int k = 0; k < 3; k++) { pa[k] = D.jpa[k][j]; pb[k] = D.jpb[k][j]; axa[k] = D.jaxa[k][j]; axb[k] = D.jaxb[k][j]; }
+  Side<T> A, B;
+  const int ea = D.jba[j], eb = D.jbb[j];
+  load_side(D, ea, pa, A);
+  load_side(D, eb, pb, B);
+  const T e = D.je[j];
+  const int base = 3 * D.nc + 5 * j;
+  for (int k = 0; k < 3; k++) {
+    T ek[3] = {T(0), T(0), T(0)};
+    ek[k] = T(1);
+    T Ja[6], Jb[6];
+    side_row(A, ek, T(1), Ja);
+    side_row(B, ek, T(-1), Jb);
+    write_entry(D, D.re0[base + k], Ja, buf);
+    write_entry(D, D.re1[base + k], Jb, buf);
+    T cb = A.w[k] - B.w[k];
+    D.cdiag[base + k] = e / (h * h);
+    D.hv[base + k] = (cb + e * D.lam[base + k]) / h;
+  }
+  T aw[3], bl[2][3], bw[2][3];
+  if (ea >= 0) {
+    T q[4], R[9];
+    for (int k = 0; k < 4; k++) q[k] = D.rq[k][ea];
+    quat_R(q, R);
+    mat3v(R, axa, aw);
+  } else {
+    for (int k = 0; k < 3; k++) aw[k] = axa[k];
+  }
+  basis(axb, bl[0], bl[1]);
+  T Rb[9];
+  if (eb >= 0) {
+    T q[4];
+    for (int k = 0; k < 4; k++) q[k] = D.rq[k][eb];
+    quat_R(q, Rb);
+  }
+  for (int k = 0; k < 2; k++) {
+    if (eb >= 0) mat3v(Rb, bl[k], bw[k]);
+    else for (int m = 0; m < 3; m++) bw[k][m] = bl[k][m];
+    T axb2[3];
+    cross3(aw, bw[k], axb2);
+    T Ja[6] = {0, 0, 0, axb2[0], axb2[1], axb2[2]};
+    T Jb[6] = {0, 0, 0, -axb2[0], -axb2[1], -axb2[2]};
+    const int row = base + 3 + k;
+    write_entry(D, D.re0[row], Ja, buf);
+    write_entry(D, D.re1[row], Jb, buf);
+    T cb = dot3(aw, bw[k]);
+    D.cdiag[row] = e / (h * h);
+    D.hv[row] = (cb + e * D.lam[row]) / h;
+  }
+}
+
+// stable Neo-Hookean tet in compliance form (Sec. 9.1-9.2.2, App. B):
+// c = V dPsi/ds, J = ds/dx, E = (V d2Psi/ds2)^-1 (eigenvalues clamped at
+// 1e-6 C1 V), C = E / h^2, h = E (c + lambda) / h.
+template <typename T>
+__global__ void k_eval_tets(Dev<T> D, int buf, int force) {
+  if (!force && D.fl->newton_stop) return;
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= D.nt) return;
+  const T h = T(D.h);
+  int v[4];
+  for (int q = 0; q < 4; q++) v[q] = D.tv[4 * t + q];
+  T Dmi[9];
+  for (int k = 0; k < 9; k++) Dmi[k] = D.tDmi[9 * t + k];
+  T x0[3];
+  for (int r = 0; r < 3; r++) x0[r] = D.px[r][v[0]];
+  T Ds[9];
+  for (int k = 0; k < 3; k++)
+    for (int r = 0; r < 3; r++) Ds[3 * r + k] = D.px[r][v[k + 1]] - x0[r];
+  T F[9];
+  for (int r = 0; r < 3; r++)
+    for (int k = 0; k < 3; k++) F[3 * r + k] = Ds[3 * r] * Dmi[k] + Ds[3 * r + 1] * Dmi[3 + k] + Ds[3 * r + 2] * Dmi[6 + k];
+  T U[9], s[3], V[9];
+  svd3(F, U, s, V);
+  const T Ve = D.tVe[t], C1 = D.tC1[t], D1 = D.tD1[t], alpha = D.talpha[t];
+  const T J = s[0] * s[1] * s[2];
+  const T pr[3] = {s[1] * s[2], s[0] * s[2], s[0] * s[1]};
+  T cv[3];
+  for (int i = 0; i < 3; i++) cv[i] = Ve * (T(2) * C1 * s[i] + T(2) * D1 * (J - alpha) * pr[i]);
+  const T k0 = T(2) * J - alpha;
+  T N[9];
+  N[0] = Ve * T(2) * (D1 * pr[0] * pr[0] + C1);
+  N[4] = Ve * T(2) * (D1 * pr[1] * pr[1] + C1);
+  N[8] = Ve * T(2) * (D1 * pr[2] * pr[2] + C1);
+  N[1] = N[3] = Ve * T(2) * D1 * s[2] * k0;
+  N[2] = N[6] = Ve * T(2) * D1 * s[1] * k0;
+  N[5] = N[7] = Ve * T(2) * D1 * s[0] * k0;
+  T w[3], Q[9], E[9];
+  eig_sym3(N, w, Q);
+  const T fl = T(1e-6) * C1 * Ve;
+  for (int k = 0; k < 3; k++) w[k] = T(1) / (w[k] < fl ? fl : w[k]);
+  for (int r = 0; r < 3; r++)
+    for (int q = 0; q < 3; q++) E[3 * r + q] = Q[3 * r] * Q[3 * q] * w[0] + Q[3 * r + 1] * Q[3 * q + 1] * w[1] + Q[3 * r + 2] * Q[3 * q + 2] * w[2];
+  const int base = 3 * D.nc + 5 * D.nj + 3 * t;
+  T lam[3] = {D.lam[base], D.lam[base + 1], D.lam[base + 2]};
+  const T ih2 = T(1) / (h * h);
+  for (int k = 0; k < 3; k++) {
+    T uk[3] = {U[k], U[3 + k], U[6 + k]}, vk[3] = {V[k], V[3 + k], V[6 + k]}, wk[3];
+    mat3v(Dmi, vk, wk);
+    T coef[4] = {-(wk[0] + wk[1] + wk[2]), wk[0], wk[1], wk[2]};
+    for (int q = 0; q < 4; q++) {
+      T J6[6] = {coef[q] * uk[0], coef[q] * uk[1], coef[q] * uk[2], 0, 0, 0};
+      write_entry(D, D.te[12 * t + 4 * k + q], J6, buf);
+    }
+    T el = E[3 * k] * (cv[0] + lam[0]) + E[3 * k + 1] * (cv[1] + lam[1]) + E[3 * k + 2] * (cv[2] + lam[2]);
+    D.hv[base + k] = el / h;
+    D.cdiag[base + k] = E[4 * k] * ih2;
+  }
+  T *c3 = D.c3 + 6 * t;
+  c3[0] = E[0] * ih2; c3[1] = E[4] * ih2; c3[2] = E[8] * ih2;
+  c3[3] = E[1] * ih2; c3[4] = E[2] * ih2; c3[5] = E[5] * ih2;
+}
+
+// ------------------------------------------------------------------------------------
+// body pass (K4, K6a, K8a): one group of G lanes per body segment
+
+// MODE BM_RESIDUAL: in = lambda.  g = M~ (u - u~) - h J^T lambda; particle
+//   geometric stiffness (Sec. 8.3, particles only) from the previous Newton
+//   iteration's entries; yg = H~^-1 g; t[e] = J_e yg, t2[e] = J_e H~^-1 J_e^T;
+//   FP64 partial of |g|^2.
+// MODE BM_APPLY: in = z.  y = H~^-1 J^T z; t[e] = J_e y.
+// MODE BM_UPDATE: in = dl.  du = H~^-1 (h J^T dl - g); u += t du; positions
+//   q = q^- + h G(q^-) u with quaternion normalisation.
+template <typename T, int G, int MODE>
+__global__ void __launch_bounds__(BLOCK) k_body_pass(Dev<T> D, const T *__restrict__ in, int buf, int newton_it, int force) {
+  if (!force && D.fl->newton_stop) return;
+  if (MODE == BM_APPLY && D.fl->cr_stop) return;
+  __shared__ double smem[BLOCK / 32];
+  const int gpb = BLOCK / G;         // groups (bodies) per block iteration
+  const int gid = threadIdx.x / G;
+  const int lane = threadIdx.x % G;
+  const T h = T(D.h);
+  double acc_g2 = 0.0;
+  const bool rigid_blocks = blockIdx.x < D.nblk_body_r;
+  if (rigid_blocks) {
+    const int stride = D.nblk_body_r * gpb;
+    for (int b0 = blockIdx.x * gpb; b0 < D.nr; b0 += stride) {
+      const int b = b0 + gid;
+      const bool act = b < D.nr;
+      int s0 = 0, s1 = 0;
+      if (act) { s0 = D.rseg[b]; s1 = D.rseg[b + 1]; }
+      T s[6] = {0, 0, 0, 0, 0, 0};
+      for (int e = s0 + lane; e < s1; e += G) {
+        T xv = in[D.erow[e]];
+#pragma unroll
+        for (int k = 0; k < 6; k++) s[k] += D.ej6[k][e] * xv;
+      }
+#pragma unroll
+      for (int k = 0; k < 6; k++) s[k] = group_sum<G>(s[k]);
+      if (!act) continue;
+      T Si[6];
+#pragma unroll
+      for (int k = 0; k < 6; k++) Si[k] = D.rIwi[k][b];
+      const T im = D.rinvm[b];
+      if (MODE == BM_APPLY) {
+        T y[6];
+        y[0] = s[0] * im; y[1] = s[1] * im; y[2] = s[2] * im;
+        sym3v(Si, s + 3, y + 3);
+        for (int e = s0 + lane; e < s1; e += G) {
+          T acc = 0;
+#pragma unroll
+          for (int k = 0; k < 6; k++) acc += D.ej6[k][e] * y[k];
+          D.t[e] = acc;
+        }
+      } else if (MODE == BM_RESIDUAL) {
+        T g[6], du[6], Iw[6];
+#pragma unroll
+        for (int k = 0; k < 6; k++) { du[k] = D.ru[k][b] - D.rut[k][b]; Iw[k] = D.rIw[k][b]; }
+        const T m = D.rm[b];
+        g[0] = m * du[0] - h * s[0]; g[1] = m * du[1] - h * s[1]; g[2] = m * du[2] - h * s[2];
+        T ia[3];
+        sym3v(Iw, du + 3, ia);
+        g[3] = ia[0] - h * s[3]; g[4] = ia[1] - h * s[4]; g[5] = ia[2] - h * s[5];
+        T y[6];
+        y[0] = g[0] * im; y[1] = g[1] * im; y[2] = g[2] * im;
+        sym3v(Si, g + 3, y + 3);
+        if (lane == 0) {
+#pragma unroll
+          for (int k = 0; k < 6; k++) { D.rg[k][b] = g[k]; D.ryg[k][b] = y[k]; acc_g2 += double(g[k]) * double(g[k]); }
+        }
+        for (int e = s0 + lane; e < s1; e += G) {
+          T J[6], tj[3];
+#pragma unroll
+          for (int k = 0; k < 6; k++) J[k] = D.ej6[k][e];
+          T acc = 0;
+#pragma unroll
+          for (int k = 0; k < 6; k++) acc += J[k] * y[k];
+          D.t[e] = acc;
+          sym3v(Si, J + 3, tj);
+          D.t2[e] = (J[0] * J[0] + J[1] * J[1] + J[2] * J[2]) * im + dot3(J + 3, tj);
+        }
+      } else {  // BM_UPDATE
+        T r[6], du[6];
+#pragma unroll
+        for (int k = 0; k < 6; k++) r[k] = h * s[k] - D.rg[k][b];
+        du[0] = r[0] * im; du[1] = r[1] * im; du[2] = r[2] * im;
+        sym3v(Si, r + 3, du + 3);
+        if (lane == 0) {
+          const T t = T(D.damping);
+          T u[6];
+#pragma unroll
+          for (int k = 0; k < 6; k++) { u[k] = D.ru[k][b] + t * du[k]; D.ru[k][b] = u[k]; }
+          T q0[4];
+#pragma unroll
+          for (int k = 0; k < 4; k++) q0[k] = D.rq0[k][b];
+#pragma unroll
+          for (int k = 0; k < 3; k++) D.rx[k][b] = D.rx0[k][b] + h * u[k];
+          const T *w = u + 3;
+          T qd[4];
+          qd[0] = T(0.5) * (-q0[1] * w[0] - q0[2] * w[1] - q0[3] * w[2]);
+          qd[1] = T(0.5) * (q0[0] * w[0] + q0[3] * w[1] - q0[2] * w[2]);
+          qd[2] = T(0.5) * (-q0[3] * w[0] + q0[0] * w[1] + q0[1] * w[2]);
+          qd[3] = T(0.5) * (q0[2] * w[0] - q0[1] * w[1] + q0[0] * w[2]);
+          T qn[4], nn = 0;
+#pragma unroll
+          for (int k = 0; k < 4; k++) { qn[k] = q0[k] + h * qd[k]; nn += qn[k] * qn[k]; }
+          nn = dsqrt(nn);
+#pragma unroll
+          for (int k = 0; k < 4; k++) D.rq[k][b] = qn[k] / nn;
+        }
+      }
+    }
+  } else {
+    const int bid = blockIdx.x - D.nblk_body_r;
+    const int stride = D.nblk_body_p * gpb;
+    T *J0 = D.ej3[buf][0], *J1 = D.ej3[buf][1], *J2 = D.ej3[buf][2];
+    for (int b0 = bid * gpb; b0 < D.np; b0 += stride) {
+      const int b = b0 + gid;
+      const bool act = b < D.np;
+      int s0 = 0, s1 = 0;
+      if (act) { s0 = D.vseg[b]; s1 = D.vseg[b + 1]; }
+      T s[3] = {0, 0, 0}, sp[3] = {0, 0, 0};
+      const bool gs = MODE == BM_RESIDUAL && D.gs && newton_it > 0;
+      for (int e = s0 + lane; e < s1; e += G) {
+        T xv = in[D.erow[D.ER + e]];
+        s[0] += J0[e] * xv; s[1] += J1[e] * xv; s[2] += J2[e] * xv;
+        if (gs) {
+          sp[0] += D.ej3[buf ^ 1][0][e] * xv; sp[1] += D.ej3[buf ^ 1][1][e] * xv; sp[2] += D.ej3[buf ^ 1][2][e] * xv;
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 3; k++) s[k] = group_sum<G>(s[k]);
+      if (gs) {
+#pragma unroll
+        for (int k = 0; k < 3; k++) sp[k] = group_sum<G>(sp[k]);
+      }
+      if (!act) continue;
+      if (MODE == BM_APPLY) {
+        T y[3] = {s[0] * D.phinv[0][b], s[1] * D.phinv[1][b], s[2] * D.phinv[2][b]};
+        for (int e = s0 + lane; e < s1; e += G) D.t[D.ER + e] = J0[e] * y[0] + J1[e] * y[1] + J2[e] * y[2];
+      } else if (MODE == BM_RESIDUAL) {
+        const T m = D.pm[b];
+        T g[3], hi[3], y[3];
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+          const T u = D.pu[k][b];
+          g[k] = m * (u - D.put[k][b]) - h * s[k];
+          hi[k] = T(1) / m;
+          if (gs) {
+            // c_k = h [(J^n - J^{n-1})^T lambda^n]_k / du_k,  H~_kk = m + max(0, -c_k)
+            const T up = D.puprev[k][b];
+            const T du = u - up;
+            const T sc = fabs(u) > fabs(up) ? fabs(u) : fabs(up);
+            if (fabs(du) > T(1e-6) + T(1e-3) * sc) {
+              const T ck = h * (s[k] - sp[k]) / du;
+              if (ck < T(0)) hi[k] = T(1) / (m - ck);
+            }
+          }
+          y[k] = g[k] * hi[k];
+        }
+        if (lane == 0) {
+#pragma unroll
+          for (int k = 0; k < 3; k++) {
+            D.pg[k][b] = g[k]; D.pyg[k][b] = y[k]; D.phinv[k][b] = hi[k];
+            acc_g2 += double(g[k]) * double(g[k]);
+          }
+        }
+        for (int e = s0 + lane; e < s1; e += G) {
+          const T a0 = J0[e], a1 = J1[e], a2 = J2[e];
+          D.t[D.ER + e] = a0 * y[0] + a1 * y[1] + a2 * y[2];
+          D.t2[D.ER + e] = a0 * a0 * hi[0] + a1 * a1 * hi[1] + a2 * a2 * hi[2];
+        }
+      } else {  // BM_UPDATE
+        if (lane == 0) {
+          const T t = T(D.damping);
+#pragma unroll
+          for (int k = 0; k < 3; k++) {
+            const T du = (h * s[k] - D.pg[k][b]) * D.phinv[k][b];
+            const T u = D.pu[k][b];
+            D.puprev[k][b] = u;
+            const T un = u + t * du;
+            D.pu[k][b] = un;
+            D.px[k][b] = D.px0[k][b] + h * un;
+          }
+        }
+      }
+    }
+  }
+  if (MODE == BM_RESIDUAL) {
+    double tot = block_sum(acc_g2, smem);
+    if (threadIdx.x == 0) D.part_body[blockIdx.x] = tot;
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// row pass (K5, K6b)
+
+// RM_RHS:   b = (1/h)(J H~^-1 g - h), diag = [J H~^-1 J^T]_ii + C_ii + eps,
+//           P = 1/diag; CR start x = 0, z = P b, p = z; partials |h|^2, b^T P b.
+// RM_APPLY: Az = J H~^-1 J^T z + C z + eps z (from the body pass' t);
+//           partials z^T Az, Az^T P Az, Az^T P Ap, z^T diag z.
+template <typename T, int MODE>
+__global__ void __launch_bounds__(BLOCK) k_row_pass(Dev<T> D, int force) {
+  if (!force && D.fl->newton_stop) return;
+  if (MODE == RM_APPLY && D.fl->cr_stop) return;
+  __shared__ double smem[BLOCK / 32];
+  double a[NPART] = {0, 0, 0, 0};
+  const T eps = T(D.eps), ih = T(1) / T(D.h);
+  if (blockIdx.x < D.nblk_row_pair) {
+    const int stride = D.nblk_row_pair * BLOCK;
+    for (int i = blockIdx.x * BLOCK + threadIdx.x; i < D.Rpair; i += stride) {
+      const int e0 = D.re0[i], e1 = D.re1[i];
+      if (MODE == RM_RHS) {
+        T tb = T(0), td = T(0);
+        if (e0 >= 0) { tb += D.t[e0]; td += D.t2[e0]; }
+        if (e1 >= 0) { tb += D.t[e1]; td += D.t2[e1]; }
+        const T hv = D.hv[i];
+        const T bi = (tb - hv) * ih;
+        const T dg = td + D.cdiag[i] + eps;
+        const T Pi = T(1) / dg;
+        D.b[i] = bi; D.P[i] = Pi; D.x[i] = T(0);
+        const T zi = Pi * bi;
+        D.z[i] = zi; D.p[i] = zi;
+        a[0] += double(hv) * double(hv);
+        a[1] += double(bi) * double(zi);
+      } else {
+        T acc = T(0);
+        if (e0 >= 0) acc += D.t[e0];
+        if (e1 >= 0) acc += D.t[e1];
+        const T zi = D.z[i];
+        const T Pi = D.P[i];
+        const T az = acc + (D.cdiag[i] + eps) * zi;
+        D.Az[i] = az;
+        a[0] += double(zi) * double(az);
+        a[1] += double(az) * double(az) * double(Pi);
+        a[2] += double(az) * double(Pi) * double(D.Ap[i]);
+        a[3] += double(zi) * double(zi) / double(Pi);
+      }
+    }
+  } else {
+    const int bid = blockIdx.x - D.nblk_row_pair;
+    const int stride = D.nblk_row_tet * BLOCK;
+    const int rb = D.Rpair;
+    for (int t = bid * BLOCK + threadIdx.x; t < D.nt; t += stride) {
+      const int *te = D.te + 12 * t;
+      const T *c3 = D.c3 + 6 * t;
+      if (MODE == RM_RHS) {
+        const T cc[3] = {c3[0], c3[1], c3[2]};
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+          T tb = T(0), td = T(0);
+#pragma unroll
+          for (int q = 0; q < 4; q++) { const int e = te[4 * k + q]; tb += D.t[e]; td += D.t2[e]; }
+          const int i = rb + 3 * t + k;
+          const T hv = D.hv[i];
+          const T bi = (tb - hv) * ih;
+          const T Pi = T(1) / (td + cc[k] + eps);
+          D.b[i] = bi; D.P[i] = Pi; D.x[i] = T(0);
+          const T zi = Pi * bi;
+          D.z[i] = zi; D.p[i] = zi;
+          a[0] += double(hv) * double(hv);
+          a[1] += double(bi) * double(zi);
+        }
+      } else {
+        const int i0 = rb + 3 * t;
+        const T z0 = D.z[i0], z1 = D.z[i0 + 1], z2 = D.z[i0 + 2];
+        T cz[3];
+        cz[0] = c3[0] * z0 + c3[3] * z1 + c3[4] * z2;
+        cz[1] = c3[3] * z0 + c3[1] * z1 + c3[5] * z2;
+        cz[2] = c3[4] * z0 + c3[5] * z1 + c3[2] * z2;
+        const T zz[3] = {z0, z1, z2};
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+          T acc = T(0);
+#pragma unroll
+          for (int q = 0; q < 4; q++) acc += D.t[te[4 * k + q]];
+          const int i = i0 + k;
+          const T az = acc + cz[k] + eps * zz[k];
+          D.Az[i] = az;
+          const T Pi = D.P[i];
+          a[0] += double(zz[k]) * double(az);
+          a[1] += double(az) * double(az) * double(Pi);
+          a[2] += double(az) * double(Pi) * double(D.Ap[i]);
+          a[3] += double(zz[k]) * double(zz[k]) / double(Pi);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < NPART; k++) {
+    double s = block_sum(a[k], smem);
+    if (threadIdx.x == 0) D.part_row[NPART * blockIdx.x + k] = s;
+  }
+}
+
+// merit of this Newton iteration, Newton stop test, CR forcing term (1 block)
+template <typename T>
+__global__ void k_merit(Dev<T> D, int n, int force) {
+  if (!force && D.fl->newton_stop) return;
+  __shared__ double smem[BLOCK / 32];
+  __shared__ double r4[NPART];
+  double g2 = 0.0;
+  const int nb = D.nblk_body_r + D.nblk_body_p;
+  for (int i = threadIdx.x; i < nb; i += BLOCK) g2 += D.part_body[i];
+  g2 = block_sum(g2, smem);
+  reduce_partials(D.part_row, D.nblk_row_pair + D.nblk_row_tet, r4, r4);
+  if (threadIdx.x == 0) {
+    double m = sqrt(g2 + r4[0]);
+    D.sc->merit[n < 1023 ? n : 1023] = m;
+    if (force) return;
+    if (n == 0) D.sc->merit0 = m;
+    double m0 = D.sc->merit0;
+    if (D.tol_rel > 0.0 && m <= D.tol_rel * m0) D.fl->newton_stop = 1;
+    double eta = 0.0;
+    if (D.cr_tol) {
+      eta = m0 > 0.0 ? m / m0 : 0.0;
+      if (eta > 0.1) eta = 0.1;
+      if (eta <= 0.0) eta = 1e-30;
+    }
+    D.sc->eta = eta;
+    D.sc->res0 = sqrt(r4[1]);
+    D.fl->cr_stop = 0;
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// K7: CR with one global synchronisation per iteration.  The scalar kernel
+// reduces the row-pass partials (d1 = z^T Az, d2 = Az^T P Az, d3 = Az^T P Ap,
+// d4 = ||r||_P^2) once, in a fixed order:
+//   beta = rho'/rho,  Ap^T P Ap = d2 + 2 beta d3 + beta^2 (Ap^T P Ap)_prev,
+//   alpha = rho'/(Ap^T P Ap)     (iteration 0: beta = 0, i.e. p = z, Ap = Az)
+// and the update kernel applies p = z + beta p, Ap = Az + beta Ap,
+// x += alpha p, z -= alpha P Ap.
+template <typename T>
+__global__ void k_cr_scalars(Dev<T> D, int k) {
+  if (D.fl->newton_stop || D.fl->cr_stop) return;
+  __shared__ double r4[NPART];
+  reduce_partials(D.part_row, D.nblk_row_pair + D.nblk_row_tet, r4, r4);
+  if (threadIdx.x == 0) {
+    const double d1 = r4[0], d2 = r4[1], d3 = r4[2], d4 = r4[3];
+    int st = 0;
+    const double cur = sqrt(d4 > 0.0 ? d4 : 0.0);
+    if (D.sc->res0 == 0.0) st = 1;
+    if (D.cr_tol && cur <= D.sc->eta * D.sc->res0) st = 1;
+    double beta = 0.0, rho = d1, apap = d2;
+    if (k > 0) {
+      const double rp = D.sc->rho[(k - 1) & 1];
+      if (!(d1 > 0.0) || !(rp > 0.0)) st = 1;
+      else {
+        beta = d1 / rp;
+        apap = d2 + 2.0 * beta * d3 + beta * beta * D.sc->appap[(k - 1) & 1];
+      }
+    }
+    if (!(apap > 0.0)) st = 1;
+    if (st) {
+      D.fl->cr_stop = 1;
+    } else {
+      D.sc->rho[k & 1] = rho;
+      D.sc->appap[k & 1] = apap;
+      D.sc->alpha = rho / apap;
+      D.sc->beta = beta;
+      D.fl->cr_count += 1;
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(BLOCK) k_cr_update(Dev<T> D) {
+  if (D.fl->newton_stop || D.fl->cr_stop) return;
+  const T alpha = T(D.sc->alpha), beta = T(D.sc->beta);
+  const int stride = gridDim.x * BLOCK;
+  for (int i = blockIdx.x * BLOCK + threadIdx.x; i < D.R; i += stride) {
+    const T zi = D.z[i];
+    const T pi = zi + beta * D.p[i];
+    const T api = D.Az[i] + beta * D.Ap[i];
+    D.p[i] = pi;
+    D.Ap[i] = api;
+    D.x[i] += alpha * pi;
+    D.z[i] = zi - alpha * D.P[i] * api;
+  }
+}
+
+// CR restart on a kept system: x = 0, z = P b, p = z
+template <typename T>
+__global__ void k_cr_init(Dev<T> D) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < D.R; i += gridDim.x * blockDim.x) {
+    const T zi = D.P[i] * D.b[i];
+    D.x[i] = T(0); D.z[i] = zi; D.p[i] = zi;
+  }
+}
+
+// lambda += t dl; counts the Newton iteration
+template <typename T>
+__global__ void k_lambda_update(Dev<T> D) {
+  if (D.fl->newton_stop) return;
+  const T t = T(D.damping);
+  const int i0 = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i0 == 0) D.fl->newton_count += 1;
+  for (int i = i0; i < D.R; i += gridDim.x * blockDim.x) D.lam[i] += t * D.x[i];
+}
+
+}  // namespace nsn

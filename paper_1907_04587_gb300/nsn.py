@@ -1,0 +1,368 @@
+"""ctypes binding of libnsn (include/nsn.h): argument marshalling only.
+
+Every step of the solver runs in the CUDA kernels of libnsn.so; this module
+only converts numpy arrays / torch device pointers to the C ABI.  There is no
+fallback: if the library is missing or cannot be loaded the import of
+``lib()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libnsn.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "nsn.h")
+
+NSN_OK = 0
+STATUS = {0: "NSN_OK", 1: "NSN_ERR_INVALID_ARG", 2: "NSN_ERR_OUT_OF_MEMORY", 3: "NSN_ERR_CUDA",
+          4: "NSN_ERR_NOT_CONVERGED", 5: "NSN_ERR_TIMEOUT", 6: "NSN_ERR_BAD_STATE", 7: "NSN_ERR_NONFINITE"}
+NSN_RIGID, NSN_PARTICLE = 0, 1
+NSN_CONTACT, NSN_REVOLUTE, NSN_TET_NH = 0, 1, 2
+NSN_FP32, NSN_FP64 = 0, 1
+
+CONTACT_DTYPE = np.dtype([("body_a", "<i4"), ("body_b", "<i4"), ("pa", "<f4", 3), ("pb", "<f4", 3),
+                          ("n", "<f4", 3), ("d", "<f4"), ("mu", "<f4")])
+REVOLUTE_DTYPE = np.dtype([("body_a", "<i4"), ("body_b", "<i4"), ("pa", "<f4", 3), ("pb", "<f4", 3),
+                           ("axis_a", "<f4", 3), ("axis_b", "<f4", 3), ("compliance", "<f4")])
+TET_DTYPE = np.dtype([("v", "<i4", 4), ("rest", "<f4", (4, 3)), ("E", "<f4"), ("nu", "<f4")])
+
+
+class nsn_config(C.Structure):
+    _fields_ = [("h", C.c_double), ("gravity", C.c_double * 3), ("newton_iters", C.c_int32),
+                ("cr_iters", C.c_int32), ("damping", C.c_double), ("eps", C.c_double),
+                ("tol_rel", C.c_double), ("cr_tol_mode", C.c_int32), ("ncp", C.c_int32),
+                ("rscale", C.c_int32), ("geom_stiffness", C.c_int32), ("precision", C.c_int32),
+                ("use_graph", C.c_int32)]
+
+
+class nsn_stats(C.Structure):
+    _fields_ = [("newton_done", C.c_int32), ("cr_total", C.c_int32), ("merit0", C.c_double),
+                ("merit_final", C.c_double), ("ms", C.c_float)]
+
+
+class NSNError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+_fp = C.POINTER(C.c_float)
+_dp = C.POINTER(C.c_double)
+_ip = C.POINTER(C.c_int32)
+_vp = C.c_void_p
+
+
+def exported_names():
+    """Function names declared in include/nsn.h."""
+    src = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:nsn_status|void|const char \*)\s*(nsn_\w+)\s*\(", src, re.M)))
+
+
+def lib():
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libnsn.so not built ({LIB_PATH}); run __graft_entry__.build()")
+    L = C.CDLL(LIB_PATH)
+    sig = {
+        "nsn_default_config": (None, [C.POINTER(nsn_config)]),
+        "nsn_create": (C.c_int, [C.POINTER(nsn_config), _vp, C.POINTER(_vp)]),
+        "nsn_destroy": (C.c_int, [_vp]),
+        "nsn_last_error": (C.c_char_p, [_vp]),
+        "nsn_add_bodies": (C.c_int, [_vp, C.c_int32, _ip, _fp, _fp, _fp, _fp, _fp, _fp, _ip]),
+        "nsn_add_constraints": (C.c_int, [_vp, C.c_int32, C.c_int32, _vp, _ip]),
+        "nsn_clear_contacts": (C.c_int, [_vp]),
+        "nsn_counts": (C.c_int, [_vp, _ip, _ip]),
+        "nsn_step": (C.c_int, [_vp, C.c_int32, C.POINTER(nsn_stats)]),
+        "nsn_get_state": (C.c_int, [_vp, _fp, _fp, _fp, _fp]),
+        "nsn_set_state": (C.c_int, [_vp, _fp, _fp, _fp, _fp]),
+        "nsn_set_state_device": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
+        "nsn_get_state_device": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
+        "nsn_get_lambda": (C.c_int, [_vp, _dp]),
+        "nsn_get_merit_history": (C.c_int, [_vp, _dp, C.c_int32, _ip]),
+        "nsn_linearize": (C.c_int, [_vp, C.c_int32]),
+        "nsn_apply_operator": (C.c_int, [_vp, _dp, _dp]),
+        "nsn_solve": (C.c_int, [_vp, C.c_int32, _dp, _dp]),
+        "nsn_get_system": (C.c_int, [_vp, _dp, _dp, _dp, _dp]),
+        "nsn_last_launch_count": (C.c_int, [_vp, _ip]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _f32(a, shape):
+    if a is None:
+        return None
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float32).reshape(shape))
+
+
+def _p(a, kind=_fp):
+    return None if a is None else a.ctypes.data_as(kind)
+
+
+# ---- functions with the ABI names ------------------------------------------------
+
+def nsn_default_config():
+    cfg = nsn_config()
+    lib().nsn_default_config(C.byref(cfg))
+    return cfg
+
+
+def nsn_create(cfg, stream=None):
+    ctx = _vp()
+    st = lib().nsn_create(C.byref(cfg), stream, C.byref(ctx))
+    if st != NSN_OK:
+        raise NSNError(st, "nsn_create failed")
+    return ctx
+
+
+def nsn_destroy(ctx):
+    return lib().nsn_destroy(ctx)
+
+
+def nsn_last_error(ctx):
+    m = lib().nsn_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def _check(ctx, st, what):
+    if st != NSN_OK:
+        raise NSNError(st, f"{what}: {nsn_last_error(ctx)}")
+
+
+def nsn_add_bodies(ctx, kind, pos, quat, vel, omega, mass, inertia):
+    n = len(mass)
+    first = C.c_int32()
+    k = np.ascontiguousarray(np.asarray(kind, np.int32))
+    arrs = [_f32(pos, (n, 3)), _f32(quat, (n, 4)), _f32(vel, (n, 3)), _f32(omega, (n, 3)), _f32(mass, (n,)),
+            _f32(inertia, (n, 3))]
+    _check(ctx, lib().nsn_add_bodies(ctx, n, _p(k, _ip), *[_p(a) for a in arrs], C.byref(first)), "nsn_add_bodies")
+    return first.value
+
+
+def nsn_add_constraints(ctx, ctype, records):
+    rec = np.ascontiguousarray(records)
+    first = C.c_int32()
+    _check(ctx, lib().nsn_add_constraints(ctx, ctype, len(rec), rec.ctypes.data_as(_vp), C.byref(first)),
+           "nsn_add_constraints")
+    return first.value
+
+
+def nsn_clear_contacts(ctx):
+    _check(ctx, lib().nsn_clear_contacts(ctx), "nsn_clear_contacts")
+
+
+def nsn_counts(ctx):
+    nb, nr = C.c_int32(), C.c_int32()
+    _check(ctx, lib().nsn_counts(ctx, C.byref(nb), C.byref(nr)), "nsn_counts")
+    return nb.value, nr.value
+
+
+def nsn_step(ctx, nsteps=1):
+    st = nsn_stats()
+    _check(ctx, lib().nsn_step(ctx, nsteps, C.byref(st)), "nsn_step")
+    return dict(newton_done=st.newton_done, cr_total=st.cr_total, merit0=st.merit0, merit_final=st.merit_final,
+                ms=st.ms)
+
+
+def nsn_get_state(ctx, nb):
+    out = dict(pos=np.zeros((nb, 3), np.float32), quat=np.zeros((nb, 4), np.float32),
+               vel=np.zeros((nb, 3), np.float32), omega=np.zeros((nb, 3), np.float32))
+    _check(ctx, lib().nsn_get_state(ctx, *[_p(out[k]) for k in ("pos", "quat", "vel", "omega")]), "nsn_get_state")
+    return out
+
+
+def nsn_set_state(ctx, nb, pos=None, quat=None, vel=None, omega=None):
+    a = [_f32(pos, (nb, 3)), _f32(quat, (nb, 4)), _f32(vel, (nb, 3)), _f32(omega, (nb, 3))]
+    _check(ctx, lib().nsn_set_state(ctx, *[_p(x) for x in a]), "nsn_set_state")
+
+
+def nsn_set_state_device(ctx, pos=0, quat=0, vel=0, omega=0):
+    """Device pointers (ints, e.g. torch tensor data_ptr(), float32 AoS); 0 = keep."""
+    args = [_vp(x) if x else None for x in (pos, quat, vel, omega)]
+    _check(ctx, lib().nsn_set_state_device(ctx, *args), "nsn_set_state_device")
+
+
+def nsn_get_state_device(ctx, pos=0, quat=0, vel=0, omega=0):
+    args = [_vp(x) if x else None for x in (pos, quat, vel, omega)]
+    _check(ctx, lib().nsn_get_state_device(ctx, *args), "nsn_get_state_device")
+
+
+def nsn_get_lambda(ctx, R):
+    out = np.zeros(R)
+    if R:
+        _check(ctx, lib().nsn_get_lambda(ctx, _p(out, _dp)), "nsn_get_lambda")
+    return out
+
+
+def nsn_get_merit_history(ctx, cap=1025):
+    out = np.zeros(cap)
+    n = C.c_int32()
+    _check(ctx, lib().nsn_get_merit_history(ctx, _p(out, _dp), cap, C.byref(n)), "nsn_get_merit_history")
+    return out[:min(n.value, cap)]
+
+
+def nsn_linearize(ctx, n_before=0):
+    _check(ctx, lib().nsn_linearize(ctx, n_before), "nsn_linearize")
+
+
+def nsn_apply_operator(ctx, x):
+    x = np.ascontiguousarray(np.asarray(x, np.float64))
+    y = np.zeros_like(x)
+    _check(ctx, lib().nsn_apply_operator(ctx, _p(x, _dp), _p(y, _dp)), "nsn_apply_operator")
+    return y
+
+
+def nsn_solve(ctx, iters, R, D):
+    dl = np.zeros(R)
+    du = np.zeros(D)
+    _check(ctx, lib().nsn_solve(ctx, iters, _p(dl, _dp), _p(du, _dp)), "nsn_solve")
+    return dl, du
+
+
+def nsn_get_system(ctx, R, D):
+    b, diag, hv, g = np.zeros(R), np.zeros(R), np.zeros(R), np.zeros(D)
+    _check(ctx, lib().nsn_get_system(ctx, _p(b, _dp), _p(diag, _dp), _p(hv, _dp), _p(g, _dp)), "nsn_get_system")
+    return dict(b=b, diag=diag, hvec=hv, g=g)
+
+
+def nsn_last_launch_count(ctx):
+    n = C.c_int32()
+    _check(ctx, lib().nsn_last_launch_count(ctx, C.byref(n)), "nsn_last_launch_count")
+    return n.value
+
+
+# ---- scene records -----------------------------------------------------------------
+
+def contact_records(s):
+    nc = len(s["c_body"])
+    r = np.zeros(nc, CONTACT_DTYPE)
+    if nc:
+        r["body_a"], r["body_b"] = s["c_body"][:, 0], s["c_body"][:, 1]
+        r["pa"], r["pb"], r["n"] = s["c_pa"], s["c_pb"], s["c_n"]
+        r["d"], r["mu"] = s["c_d"], s["c_mu"]
+    return r
+
+
+def revolute_records(s):
+    nj = len(s["j_body"])
+    r = np.zeros(nj, REVOLUTE_DTYPE)
+    if nj:
+        r["body_a"], r["body_b"] = s["j_body"][:, 0], s["j_body"][:, 1]
+        r["pa"], r["pb"], r["axis_a"], r["axis_b"] = s["j_pa"], s["j_pb"], s["j_axa"], s["j_axb"]
+        r["compliance"] = s["j_compliance"]
+    return r
+
+
+def tet_records(s):
+    nt = len(s["t_v"])
+    r = np.zeros(nt, TET_DTYPE)
+    if nt:
+        r["v"], r["rest"], r["E"], r["nu"] = s["t_v"], s["t_rest"], s["t_E"], s["t_nu"]
+    return r
+
+
+DEFAULTS = dict(h=1.0 / 60.0, gravity=(0.0, 0.0, -9.81), newton_iters=4, cr_iters=20, damping=0.75, eps=1e-6,
+                tol_rel=0.0, cr_tol_mode=0, ncp=0, rscale=2, geom_stiffness=1, precision=NSN_FP32, use_graph=1)
+
+
+def make_config(**params):
+    p = dict(DEFAULTS)
+    unknown = set(params) - set(p)
+    if unknown:
+        raise TypeError(f"unknown parameters {sorted(unknown)}")
+    p.update(params)
+    cfg = nsn_config()
+    cfg.h = p["h"]
+    cfg.gravity = (C.c_double * 3)(*p["gravity"])
+    for k in ("newton_iters", "cr_iters", "cr_tol_mode", "ncp", "rscale", "geom_stiffness", "precision", "use_graph"):
+        setattr(cfg, k, int(p[k]))
+    for k in ("damping", "eps", "tol_rel"):
+        setattr(cfg, k, float(p[k]))
+    return cfg
+
+
+def _current_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except ImportError:
+        pass
+    return None
+
+
+class Solver:
+    """One libnsn context built from a scene dictionary (``scenes.py``)."""
+
+    def __init__(self, scene, stream=None, **params):
+        self.cfg = make_config(**params)
+        self.ctx = nsn_create(self.cfg, stream if stream is not None else _current_stream())
+        s = scene
+        nb = len(s["mass"])
+        self.nb = nb
+        nsn_add_bodies(self.ctx, s["kind"], s["pos"], s["quat"], s["vel"], s["omega"], s["mass"], s["inertia"])
+        for ctype, rec in ((NSN_CONTACT, contact_records(s)), (NSN_REVOLUTE, revolute_records(s)),
+                           (NSN_TET_NH, tet_records(s))):
+            if len(rec):
+                nsn_add_constraints(self.ctx, ctype, rec)
+        _, self.R = nsn_counts(self.ctx)
+        self.D = int(sum(6 if k == 0 else 3 for k in s["kind"]))
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            nsn_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, nsteps=1):
+        return nsn_step(self.ctx, nsteps)
+
+    def get_state(self):
+        return nsn_get_state(self.ctx, self.nb)
+
+    def set_state(self, pos=None, quat=None, vel=None, omega=None):
+        nsn_set_state(self.ctx, self.nb, pos, quat, vel, omega)
+
+    def set_contacts(self, scene):
+        nsn_clear_contacts(self.ctx)
+        rec = contact_records(scene)
+        if len(rec):
+            nsn_add_constraints(self.ctx, NSN_CONTACT, rec)
+        _, self.R = nsn_counts(self.ctx)
+
+    def get_lambda(self):
+        return nsn_get_lambda(self.ctx, self.R)
+
+    def merit_history(self):
+        return nsn_get_merit_history(self.ctx)
+
+    def linearize(self, n_before=0):
+        nsn_linearize(self.ctx, n_before)
+
+    def apply(self, x):
+        return nsn_apply_operator(self.ctx, x)
+
+    def solve(self, iters):
+        return nsn_solve(self.ctx, iters, self.R, self.D)
+
+    def system(self):
+        return nsn_get_system(self.ctx, self.R, self.D)
+
+    def launches_per_step(self):
+        return nsn_last_launch_count(self.ctx)

@@ -1,0 +1,54 @@
+"""CPU checks of the C ABI library: it builds for sm_103a, loads, and exports
+every entry point declared in include/nsn.h (no compute calls without a GPU)."""
+import ctypes
+import re
+
+import pytest
+
+from paper_1907_04587_gb300 import _build, nsn
+
+
+@pytest.fixture(scope="module")
+def libnsn():
+    _build.build()
+    return nsn.lib()
+
+
+def test_header_declares_the_boundary():
+    names = nsn.exported_names()
+    for required in ("nsn_create", "nsn_add_bodies", "nsn_add_constraints", "nsn_step", "nsn_solve"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(libnsn):
+    for name in nsn.exported_names():
+        assert hasattr(libnsn, name), name
+
+
+def test_record_layouts_match_header():
+    src = open(nsn.HEADER).read()
+    # field counts of the packed records: 2 ints + 11 floats, 2 ints + 13 floats, 4 ints + 14 floats
+    assert nsn.CONTACT_DTYPE.itemsize == 4 * (2 + 11)
+    assert nsn.REVOLUTE_DTYPE.itemsize == 4 * (2 + 13)
+    assert nsn.TET_DTYPE.itemsize == 4 * (4 + 14)
+    assert "nsn_contact" in src and "nsn_revolute" in src and "nsn_tet" in src
+
+
+def test_config_struct_and_defaults(libnsn):
+    cfg = nsn.nsn_default_config()
+    assert abs(cfg.h - 1.0 / 60.0) < 1e-15 and cfg.newton_iters == 4 and cfg.cr_iters == 20
+    assert cfg.damping == 0.75 and cfg.eps == 1e-6 and cfg.precision == nsn.NSN_FP32
+    assert ctypes.sizeof(nsn.nsn_config) == 88
+
+
+def test_invalid_arguments_are_rejected_without_gpu(libnsn):
+    out = ctypes.c_void_p()
+    assert libnsn.nsn_create(None, None, ctypes.byref(out)) == 1
+    cfg = nsn.nsn_default_config()
+    cfg.h = -1.0
+    assert libnsn.nsn_create(ctypes.byref(cfg), None, ctypes.byref(out)) == 1
+    assert libnsn.nsn_destroy(None) == 1
+
+
+def test_built_for_sm103a():
+    assert "compute_103a,code=sm_103a" in " ".join(_build.ARCH)

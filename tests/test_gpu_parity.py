@@ -1,0 +1,255 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Identical seeded inputs (float32-representable) go to both sides.  Errors are
+norm-wise relative, ||gpu - oracle|| / ||oracle||.  The FP64 build of the
+kernels must agree to rounding (1e-9); the FP32 production path must meet the
+1e-5 relative bound on per-step velocities and impulses at equal Newton/CR
+iteration counts.
+"""
+import numpy as np
+import pytest
+
+from paper_1907_04587_gb300 import nsn, scenes
+
+pytestmark = pytest.mark.gpu
+
+H = 1.0 / 60.0
+TOL64 = 1e-9
+TOL32 = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def cuda():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    yield
+
+
+def rel(a, b):
+    a = np.asarray(a, np.float64).ravel()
+    b = np.asarray(b, np.float64).ravel()
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def body_u(state, kind):
+    """Generalised velocity in body order: [v, w] per rigid body, v per particle."""
+    out = []
+    for i, k in enumerate(kind):
+        out.append(state["vel"][i])
+        if k == 0:
+            out.append(state["omega"][i])
+    return np.concatenate(out) if out else np.zeros(0)
+
+
+SCENES = {
+    "cube_stack": lambda: scenes.cube_stack(seed=0),
+    "chain_block_small": lambda: scenes.chain_block(seed=1, hexes=4, links=7),
+    "batched_small": lambda: scenes.batched_envs(seed=2, n_envs=12),
+}
+PARAMS = {
+    "cube_stack": dict(newton_iters=4, cr_iters=20),
+    "chain_block_small": dict(newton_iters=10, cr_iters=50),
+    "batched_small": dict(newton_iters=5, cr_iters=25),
+}
+
+
+@pytest.mark.parametrize("name", list(SCENES))
+@pytest.mark.parametrize("prec", [nsn.NSN_FP64, nsn.NSN_FP32])
+def test_linear_system_parity(orc, name, prec):
+    """b, Jacobi diagonal, h and g of Eq. schur_system at the zero iterate and
+    after one Newton iteration; then y = A x for a random x."""
+    s = SCENES[name]()
+    p = PARAMS[name]
+    o = orc.Oracle(s, **p)
+    g = nsn.Solver(s, precision=prec, **p)
+    for n_before in (0, 1):
+        L = o.linearize(n_before=n_before)
+        g.linearize(n_before)
+        sysg = g.system()
+        tol = TOL64 if prec == nsn.NSN_FP64 else (TOL32 if n_before == 0 else 1e-3)
+        assert rel(sysg["g"], L["g"]) < tol, ("g", n_before)
+        assert rel(sysg["hvec"], L["hvec"]) < tol, ("h", n_before)
+        assert rel(sysg["b"], L["b"]) < tol, ("b", n_before)
+        R = o.R
+        x = np.random.default_rng(11).normal(size=R)
+        assert rel(g.apply(x), o.apply_A(x)) < (TOL64 if prec == nsn.NSN_FP64 else TOL32), ("Ax", n_before)
+
+
+@pytest.mark.parametrize("name", list(SCENES))
+def test_cr_solve_parity_fp64(orc, name):
+    """dl after M CR iterations and du = H~^-1 (h J^T dl - g) (Sec. 6.2, 8.2)."""
+    s = SCENES[name]()
+    p = PARAMS[name]
+    o = orc.Oracle(s, **p)
+    g = nsn.Solver(s, precision=nsn.NSN_FP64, **p)
+    o.linearize(n_before=1)
+    g.linearize(1)
+    M = p["cr_iters"]
+    dl_o, _ = o.pcr(M)
+    dl_g, du_g = g.solve(M)
+    assert rel(dl_g, dl_o) < 1e-8
+    L = o.linearize(n_before=1)
+    du_o = L["Hinv"] @ (L["J"].T @ dl_o * H - L["g"])
+    assert rel(du_g, du_o) < 1e-8
+
+
+def _resync_step(o, g, s, kind):
+    """Round the oracle state to float32, load it into both sides, step both."""
+    st = o.get_state()
+    f32 = {k: v.astype(np.float32) for k, v in st.items()}
+    o.set_state(**{k: v.astype(np.float64) for k, v in f32.items()})
+    g.set_state(**f32)
+    so = o.step()
+    sg = g.step()
+    uo, ug = body_u(o.get_state(), kind), body_u(g.get_state(), kind)
+    lo, lg = H * o.get_lambda(), H * g.get_lambda()
+    return rel(ug, uo), rel(lg, lo), so, sg
+
+
+@pytest.mark.parametrize("name", list(SCENES))
+@pytest.mark.parametrize("prec", [nsn.NSN_FP64, nsn.NSN_FP32])
+def test_step_parity(orc, name, prec):
+    """Per-step velocities u+ and impulses h lambda at equal Newton/CR counts,
+    with the state re-synchronised from the oracle before every step."""
+    s = SCENES[name]()
+    p = PARAMS[name]
+    o = orc.Oracle(s, **p)
+    g = nsn.Solver(s, precision=prec, **p)
+    tol = TOL64 if prec == nsn.NSN_FP64 else TOL32
+    for step in range(3):
+        eu, el, so, sg = _resync_step(o, g, s, s["kind"])
+        assert sg["newton_done"] == so["newton_done"]
+        assert sg["cr_total"] == so["cr_total"]
+        assert eu < tol and el < tol, (step, eu, el)
+        assert abs(sg["merit_final"] - so["merit_final"]) <= 10 * tol * max(so["merit0"], 1e-30) + 1e-3 * so["merit_final"]
+
+
+def test_cube_stack_60_steps_fp32(orc):
+    """Config 1 in full: 60 steps of 4 Newton x 20 CR, contacts regenerated at the
+    start of every step from the oracle's state (Sec. 10), state re-synchronised."""
+    s = scenes.cube_stack(seed=0)
+    p = PARAMS["cube_stack"]
+    o = orc.Oracle(s, **p)
+    g = nsn.Solver(s, precision=nsn.NSN_FP32, **p)
+    worst = 0.0
+    for step in range(60):
+        st = o.get_state()
+        c = scenes.stack_contacts(st["pos"], st["quat"])
+        s2 = scenes.finalize(dict(s, **c))
+        o = orc.Oracle(s2, **p)
+        o.set_state(**{k: v.astype(np.float32).astype(np.float64) for k, v in st.items()})
+        g.set_contacts(s2)
+        g.set_state(**{k: v.astype(np.float32) for k, v in st.items()})
+        o.step()
+        g.step()
+        eu = rel(body_u(g.get_state(), s["kind"]), body_u(o.get_state(), s["kind"]))
+        el = rel(H * g.get_lambda(), H * o.get_lambda())
+        worst = max(worst, eu, el)
+    assert worst < TOL32, worst
+
+
+def test_tolerance_mode_counts(orc):
+    """Inexact Newton with the forcing term and a merit tolerance: identical
+    Newton and CR iteration counts (FP64 build)."""
+    s = scenes.chain_block(seed=1, hexes=3, links=3)
+    p = dict(newton_iters=30, cr_iters=100, tol_rel=1e-5, cr_tol_mode=1)
+    o = orc.Oracle(s, **p)
+    g = nsn.Solver(s, precision=nsn.NSN_FP64, **p)
+    so = o.step()
+    sg = g.step()
+    assert sg["newton_done"] == so["newton_done"]
+    assert abs(sg["cr_total"] - so["cr_total"]) <= 1
+    assert rel(body_u(g.get_state(), s["kind"]), body_u(o.get_state(), s["kind"])) < 1e-7
+
+
+# ---------------------------------------------------------------------------------
+# physics pins on the GPU (same closed forms as the oracle pins)
+
+def test_gpu_resting_stack_impulses():
+    b = scenes.SceneBuilder()
+    m = 1000.0
+    for k in range(4):
+        i = b.add_rigid((0, 0, 0.5 + k), mass=m, inertia=(m / 6,) * 3)
+        for pnt in scenes.box_bottom_corners((1, 1, 1)):
+            if k == 0:
+                b.add_contact(i, -1, pnt, (pnt[0], pnt[1], 0), (0, 0, 1), 0.0, 0.5)
+            else:
+                b.add_contact(i, k - 1, pnt, (pnt[0], pnt[1], 0.5), (0, 0, 1), 0.0, 0.5)
+    g = nsn.Solver(b.build(), newton_iters=60, cr_iters=100, precision=nsn.NSN_FP32)
+    g.step()
+    lam = g.get_lambda()
+    for k in range(4):
+        assert abs(H * lam[12 * k:12 * k + 12:3].sum() / (m * 9.81 * H * (4 - k)) - 1) < 1e-4
+
+
+@pytest.mark.parametrize("v0", [0.5, 0.05])
+def test_gpu_sliding_particle(v0):
+    b = scenes.SceneBuilder()
+    i = b.add_particle((0.0, 0.0, 0.0), vel=(0.6 * v0, 0.8 * v0, 0.0), mass=2.0)
+    b.add_contact(i, -1, (0, 0, 0), (0, 0, 0), (0, 0, 1), 0.0, 0.5)
+    s = b.build()
+    g = nsn.Solver(s, newton_iters=40, cr_iters=10, precision=nsn.NSN_FP32)
+    g.step()
+    v = g.get_state()["vel"][0].astype(np.float64)
+    vin = s["vel"][0].astype(np.float64)
+    assert abs(np.hypot(v[0], v[1]) - max(0.0, np.hypot(vin[0], vin[1]) - H * 0.5 * 9.81)) < 1e-5
+
+
+# ---------------------------------------------------------------------------------
+# edge cases
+
+def test_no_constraints_free_fall(orc):
+    b = scenes.SceneBuilder()
+    b.add_particle((0, 0, 1), vel=(1.0, 0, 0), mass=1.0)
+    b.add_rigid((0, 0, 2), omega=(0.3, 0.0, 2.0), mass=2.0, inertia=(1.0, 2.0, 3.0))
+    s = b.build()
+    o = orc.Oracle(s, newton_iters=6, cr_iters=5)
+    g = nsn.Solver(s, newton_iters=6, cr_iters=5, precision=nsn.NSN_FP64)
+    o.step(); g.step()
+    assert rel(body_u(g.get_state(), s["kind"]), body_u(o.get_state(), s["kind"])) < 1e-12
+
+
+def test_particles_only_contacts_and_static_world(orc):
+    b = scenes.SceneBuilder()
+    for k in range(5):
+        i = b.add_particle((0.1 * k, 0, -1e-3 * k), vel=(0.2, 0.1 * k, -0.3), mass=1.0 + k)
+        b.add_contact(i, -1, (0, 0, 0), (0.1 * k, 0, 0), (0, 0, 1), 0.0, 0.4)
+    s = b.build()
+    p = dict(newton_iters=8, cr_iters=10)
+    o = orc.Oracle(s, **p)
+    g = nsn.Solver(s, precision=nsn.NSN_FP64, **p)
+    o.step(); g.step()
+    assert rel(H * g.get_lambda(), H * o.get_lambda()) < TOL64
+    assert rel(body_u(g.get_state(), s["kind"]), body_u(o.get_state(), s["kind"])) < TOL64
+
+
+def test_single_tet_and_ragged_sizes(orc):
+    """One tet (3 rows), and a block whose row / entry counts are not multiples
+    of any block or group size."""
+    for hexes in (1, 3):
+        s = scenes.chain_block(seed=5, hexes=hexes, links=1)
+        p = dict(newton_iters=3, cr_iters=7)
+        o = orc.Oracle(s, **p)
+        g = nsn.Solver(s, precision=nsn.NSN_FP64, **p)
+        o.step(); g.step()
+        assert rel(body_u(g.get_state(), s["kind"]), body_u(o.get_state(), s["kind"])) < TOL64
+
+
+def test_invalid_input_reports_error():
+    cfg = nsn.make_config()
+    ctx = nsn.nsn_create(cfg)
+    try:
+        with pytest.raises(nsn.NSNError):
+            nsn.nsn_add_bodies(ctx, [0], [[0, 0, 0]], [[1, 0, 0, 0]], [[0, 0, 0]], [[0, 0, 0]], [-1.0], [[1, 1, 1]])
+        nsn.nsn_add_bodies(ctx, [1], [[0, 0, 0]], None, [[0, 0, 0]], None, [1.0], None)
+        bad = np.zeros(1, nsn.CONTACT_DTYPE)
+        bad["body_a"], bad["body_b"] = 5, -1
+        bad["n"] = (0, 0, 1)
+        with pytest.raises(nsn.NSNError):
+            nsn.nsn_add_constraints(ctx, nsn.NSN_CONTACT, bad)
+    finally:
+        nsn.nsn_destroy(ctx)
