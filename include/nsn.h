@@ -98,7 +98,7 @@ typedef struct {
   int32_t body_a, body_b;  /* body ids, -1 = static world (not both) */
   float pa[3];             /* point on a: body-local (rigid), ignored (particle), world (-1) */
   float pb[3];             /* point on b, same convention */
-  float n[3];              /* world contact normal pointing from b towards a (Sec. 3.3) */
+  float n[3];              /* unit world contact normal pointing from b towards a (Sec. 3.3) */
   float d;                 /* thickness d of C_n = n^T (a - b) - d >= 0 */
   float mu;                /* friction coefficient (Sec. 3.4) */
 } nsn_contact;
@@ -124,7 +124,7 @@ nsn_status nsn_destroy(nsn_ctx *ctx);
 const char *nsn_last_error(const nsn_ctx *ctx);
 
 /* Appends n bodies (copied).  kind[n] NSN_RIGID/NSN_PARTICLE; pos n x 3;
- * quat n x 4 (NULL = identity); vel n x 3; omega n x 3 (NULL = 0);
+ * quat n x 4 unit quaternions (NULL = identity); vel n x 3; omega n x 3 (NULL = 0);
  * mass[n] > 0; inertia n x 3 body-frame principal moments > 0 (rigid; may be
  * NULL if all are particles).  first_id receives the id of the first body. */
 nsn_status nsn_add_bodies(nsn_ctx *ctx, int32_t n, const int32_t *kind, const float *pos,
@@ -159,6 +159,9 @@ nsn_status nsn_set_state(nsn_ctx *ctx, const float *pos, const float *quat, cons
 nsn_status nsn_set_state_device(nsn_ctx *ctx, const float *pos, const float *quat, const float *vel,
                                 const float *omega);
 nsn_status nsn_get_state_device(nsn_ctx *ctx, float *pos, float *quat, float *vel, float *omega);
+/* State in the bulk precision of the context (double copies of the FP64 build's
+ * values, for verification); same layout as nsn_get_state. */
+nsn_status nsn_get_state_f64(nsn_ctx *ctx, double *pos, double *quat, double *vel, double *omega);
 /* Multipliers of the last step (R values, forces in N). */
 nsn_status nsn_get_lambda(nsn_ctx *ctx, double *lambda);
 /* Merit after each Newton iteration of the last step, then the final merit;

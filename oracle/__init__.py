@@ -95,6 +95,8 @@ def lib():
         for f in ("orc_w_fb", "orc_w_min"):
             getattr(L, f).restype = C.c_double
             getattr(L, f).argtypes = [C.c_double] * 4
+        L.orc_fb_friction_active.restype = C.c_int
+        L.orc_fb_friction_active.argtypes = [C.c_double] * 4
         L.orc_nh_params.argtypes = [C.c_double, C.c_double, _dp, _dp, _dp]
         L.orc_nh_energy.restype = C.c_double
         L.orc_nh_energy.argtypes = [_dp, C.c_double, C.c_double, C.c_double]
@@ -277,6 +279,10 @@ def min_contact(Cn, lam, r):
 
 def w_fb(vt, lf, mu_ln, r):
     return lib().orc_w_fb(vt, lf, mu_ln, r)
+
+
+def fb_friction_active(vt, lf, mu_ln, r):
+    return bool(lib().orc_fb_friction_active(vt, lf, mu_ln, r))
 
 
 def w_min(vt, lf, mu_ln, r):

@@ -127,17 +127,29 @@ void orc_min_contact(double C, double lam, double r, double *phi, double *alpha,
  * denominator; the fixed point |lambda_f| + psi/r of App. A.2 gives the
  * unsquared |D^T qdot| (dimensionally consistent, and the Fig. 4 example
  * vt = 0.5, mu lambda_n = 5 = |lambda_f| then gives W = 0.1, phi_f = 0).
- * Reading: numerator 0 means stick, W = 0; a non-positive denominator is
- * floored at 1e-6 (vt + r mu lambda_n). */
+ * Numerator 0 means stick, W = 0.  The denominator r |lambda_f|^{n+1} is
+ * positive except past the vertical asymptote of W (Fig. 4, left); that case
+ * is handled by the caller (see orc_fb_friction_active). */
 double orc_w_fb(double vt, double lf, double mu_ln, double r) {
   double bb = mu_ln - lf;
   double root = sqrt(vt * vt + r * r * bb * bb);
   double num = r * (root - r * bb);
   double den = vt + r * mu_ln - root;
   if (num == 0.0) return 0.0;
-  double floor_ = 1e-6 * (vt + r * mu_ln);
-  if (den < floor_) den = floor_;
   return num / den;
+}
+
+/* Reading: the FB fixed-point update |lambda_f|^{n+1} = (vt + r mu lambda_n -
+ * sqrt(vt^2 + r^2 (mu lambda_n - lf)^2)) / r of App. A.2 is a friction
+ * magnitude; where it is not positive (|lambda_f| far outside the cone, past
+ * the asymptote of W in Fig. 4) the fixed point has zero friction, so the
+ * contact's friction rows take the form of the inactive set of Sec. 3.5
+ * (rows zeroed, unit W block, h_f = lambda_f). */
+int orc_fb_friction_active(double vt, double lf, double mu_ln, double r) {
+  if (!(mu_ln > 0.0)) return 0;
+  double bb = mu_ln - lf;
+  double den = vt + r * mu_ln - sqrt(vt * vt + r * r * bb * bb);
+  return den > 0.0;
 }
 
 /* W_min of App. A.2 (minimum-map friction). */
@@ -579,10 +591,12 @@ static void eval_rows(orc_ctx *c, const double *u, const double *lam) {
     else if (c->p.rscale == ORC_R_EFFMASS) rF = h * 0.5 * dq;
     double mu_ln = c->c_mu[ci] * ln;
     double lf[2] = {lam[3 * ci + 1], lam[3 * ci + 2]};
-    if (mu_ln > 0.0) {
-      /* active set A of Sec. 3.5 */
-      double vn = sqrt(vt[0] * vt[0] + vt[1] * vt[1]);
-      double ln_f = sqrt(lf[0] * lf[0] + lf[1] * lf[1]);
+    double vn = sqrt(vt[0] * vt[0] + vt[1] * vt[1]);
+    double ln_f = sqrt(lf[0] * lf[0] + lf[1] * lf[1]);
+    /* active set A of Sec. 3.5 (mu lambda_n > 0), for FB restricted to a
+     * positive fixed-point friction magnitude (see orc_fb_friction_active) */
+    int active = c->p.ncp == ORC_NCP_MIN ? mu_ln > 0.0 : orc_fb_friction_active(vn, ln_f, mu_ln, rF);
+    if (active) {
       double W = (c->p.ncp == ORC_NCP_MIN) ? orc_w_min(vn, ln_f, mu_ln, rF) : orc_w_fb(vn, ln_f, mu_ln, rF);
       for (int k = 0; k < 2; k++) {
         c->cdiag[3 * ci + 1 + k] = W / h;               /* C block W/h (Eq. group_system) */

@@ -134,6 +134,7 @@ double orc_fb(double a, double b);
 void orc_fb_contact(double C, double lam, double r, double *phi, double *alpha, double *S);
 void orc_min_contact(double C, double lam, double r, double *phi, double *alpha, double *S);
 double orc_w_fb(double vt, double lf, double mu_ln, double r);
+int orc_fb_friction_active(double vt, double lf, double mu_ln, double r);
 double orc_w_min(double vt, double lf, double mu_ln, double r);
 void orc_nh_params(double E, double nu, double *C1, double *D1, double *alpha);
 double orc_nh_energy(const double s[3], double C1, double D1, double alpha);

@@ -282,7 +282,8 @@ nsn_status upload(nsn_ctx *c, Dev<T> &D) {
       a[i] = r.body_a >= 0 ? L.bmap[r.body_a] : -1;
       b[i] = r.body_b >= 0 ? L.bmap[r.body_b] : -1;
       double nn = std::sqrt(double(r.n[0]) * r.n[0] + double(r.n[1]) * r.n[1] + double(r.n[2]) * r.n[2]);
-      for (int k = 0; k < 3; k++) { pa[k][i] = T(r.pa[k]); pb[k][i] = T(r.pb[k]); n[k][i] = T(r.n[k] / nn); }
+      (void)nn;
+      for (int k = 0; k < 3; k++) { pa[k][i] = T(r.pa[k]); pb[k][i] = T(r.pb[k]); n[k][i] = T(r.n[k]); }
       d[i] = T(r.d); mu[i] = T(r.mu);
     }
     CUDA_TRY(c, puti(D.cba, a)); CUDA_TRY(c, puti(D.cbb, b));
@@ -360,12 +361,8 @@ __global__ void k_scatter_state(Dev<T> D, const int *bmap, int nb, const float *
       if (vel) D.ru[k][e] = T(vel[3 * i + k]);
       if (omega) D.ru[3 + k][e] = T(omega[3 * i + k]);
     }
-    if (quat) {
-      T q[4], n = 0;
-      for (int k = 0; k < 4; k++) { q[k] = T(quat[4 * i + k]); n += q[k] * q[k]; }
-      n = sqrt(n);
-      for (int k = 0; k < 4; k++) D.rq[k][e] = q[k] / n;
-    }
+    if (quat)
+      for (int k = 0; k < 4; k++) D.rq[k][e] = T(quat[4 * i + k]);
   } else {
     int p = -e - 2;
     for (int k = 0; k < 3; k++) {
@@ -375,28 +372,28 @@ __global__ void k_scatter_state(Dev<T> D, const int *bmap, int nb, const float *
   }
 }
 
-template <typename T>
-__global__ void k_gather_state(Dev<T> D, const int *bmap, int nb, float *pos, float *quat, float *vel,
-                               float *omega) {
+template <typename T, typename O = float>
+__global__ void k_gather_state(Dev<T> D, const int *bmap, int nb, O *pos, O *quat, O *vel,
+                               O *omega) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nb) return;
   int e = bmap[i];
   if (e >= 0) {
     for (int k = 0; k < 3; k++) {
-      if (pos) pos[3 * i + k] = float(D.rx[k][e]);
-      if (vel) vel[3 * i + k] = float(D.ru[k][e]);
-      if (omega) omega[3 * i + k] = float(D.ru[3 + k][e]);
+      if (pos) pos[3 * i + k] = O(D.rx[k][e]);
+      if (vel) vel[3 * i + k] = O(D.ru[k][e]);
+      if (omega) omega[3 * i + k] = O(D.ru[3 + k][e]);
     }
     if (quat)
-      for (int k = 0; k < 4; k++) quat[4 * i + k] = float(D.rq[k][e]);
+      for (int k = 0; k < 4; k++) quat[4 * i + k] = O(D.rq[k][e]);
   } else {
     int p = -e - 2;
     for (int k = 0; k < 3; k++) {
-      if (pos) pos[3 * i + k] = float(D.px[k][p]);
-      if (vel) vel[3 * i + k] = float(D.pu[k][p]);
-      if (omega) omega[3 * i + k] = 0.f;
+      if (pos) pos[3 * i + k] = O(D.px[k][p]);
+      if (vel) vel[3 * i + k] = O(D.pu[k][p]);
+      if (omega) omega[3 * i + k] = O(0);
     }
-    if (quat) { quat[4 * i] = 1.f; quat[4 * i + 1] = quat[4 * i + 2] = quat[4 * i + 3] = 0.f; }
+    if (quat) { quat[4 * i] = O(1); quat[4 * i + 1] = quat[4 * i + 2] = quat[4 * i + 3] = O(0); }
   }
 }
 
@@ -463,13 +460,13 @@ struct Launcher {
     k_merit<T><<<1, BLOCK, 0, st>>>(D, n, 0);
     count++;
   }
-  void cr(int iters) {
+  void cr(int iters, int buf) {
     if (!D.R) return;
     for (int k = 0; k < iters; k++) {
-      body(BM_APPLY, D.z, 0, 0, 0);
+      body(BM_APPLY, D.z, buf, 0, 0);
       rows(RM_APPLY, 0);
       k_cr_scalars<T><<<1, BLOCK, 0, st>>>(D, k);
-      k_cr_update<T><<<D.nblk_upd, BLOCK, 0, st>>>(D);
+      k_cr_update<T><<<D.nblk_upd, BLOCK, 0, st>>>(D, k);
       count += 2;
     }
   }
@@ -483,7 +480,7 @@ struct Launcher {
     begin();
     for (int n = 0; n < N; n++) {
       linearize_at(n);
-      cr(M);
+      cr(M, n & 1);
       newton_update(n);
     }
     // final merit at the returned iterate
@@ -640,7 +637,7 @@ nsn_status do_linearize(nsn_ctx *c, int n_before) {
   Lr.begin();
   for (int n = 0; n < n_before; n++) {
     Lr.linearize_at(n);
-    Lr.cr(c->cfg.cr_iters);
+    Lr.cr(c->cfg.cr_iters, n & 1);
     Lr.newton_update(n);
   }
   Lr.linearize_at(n_before);
@@ -686,7 +683,7 @@ nsn_status do_apply(nsn_ctx *c, const double *x, double *y) {
   k_from_double<T><<<cdiv(R, 256), 256, 0, st>>>(D.z, tmp, R);
   CUDA_TRY(c, cudaMemsetAsync(D.fl, 0, sizeof(Flags), st));
   Launcher<T> Lr{c, D, st};
-  Lr.body(BM_APPLY, D.z, 0, 0, 1);
+  Lr.body(BM_APPLY, D.z, c->lin_buf, 0, 1);
   Lr.rows(RM_APPLY, 1);
   k_to_double<T><<<cdiv(R, 256), 256, 0, st>>>(tmp, D.Az, R, 0);
   CUDA_TRY(c, cudaMemcpyAsync(y, tmp, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
@@ -706,7 +703,7 @@ nsn_status do_solve(nsn_ctx *c, int iters, double *dl, double *du) {
     k_cr_init<T><<<D.nblk_upd, BLOCK, 0, st>>>(D);
     // res0 for the scalar kernel
     Launcher<T> Lr{c, D, st};
-    Lr.cr(iters);
+    Lr.cr(iters, c->lin_buf);
   }
   CUDA_TRY(c, cudaGetLastError());
   if (dl) { nsn_status s = copy_out<T>(c, D.x, D.R, dl); if (s) return s; }
@@ -885,8 +882,8 @@ nsn_status nsn_add_bodies(nsn_ctx *c, int32_t n, const int32_t *kind, const floa
     if (quat && kind[i] == NSN_RIGID) {
       double nn = 0;
       for (int k = 0; k < 4; k++) nn += double(quat[4 * i + k]) * quat[4 * i + k];
-      if (!(nn > 0)) return fail(c, NSN_ERR_INVALID_ARG, "body %d: zero quaternion", i);
-      for (int k = 0; k < 4; k++) q[k] = float(quat[4 * i + k] / std::sqrt(nn));
+      if (!(std::fabs(nn - 1.0) < 1e-4)) return fail(c, NSN_ERR_INVALID_ARG, "body %d: quaternion is not unit", i);
+      for (int k = 0; k < 4; k++) q[k] = quat[4 * i + k];
     }
     for (int k = 0; k < 4; k++) S.quat.push_back(q[k]);
     S.mass.push_back(mass[i]);
@@ -908,7 +905,7 @@ nsn_status nsn_add_constraints(nsn_ctx *c, int32_t type, int32_t n, const void *
           r[i].body_a == r[i].body_b)
         return fail(c, NSN_ERR_INVALID_ARG, "contact %d: bad body ids", i);
       double nn = double(r[i].n[0]) * r[i].n[0] + double(r[i].n[1]) * r[i].n[1] + double(r[i].n[2]) * r[i].n[2];
-      if (!(nn > 1e-12) || !finite_all(r[i].pa, 3) || !finite_all(r[i].pb, 3) || !std::isfinite(r[i].d) ||
+      if (!(std::fabs(nn - 1.0) < 1e-4) || !finite_all(r[i].pa, 3) || !finite_all(r[i].pb, 3) || !std::isfinite(r[i].d) ||
           !(r[i].mu >= 0.f))
         return fail(c, NSN_ERR_INVALID_ARG, "contact %d: bad geometry", i);
     }
@@ -1033,6 +1030,31 @@ nsn_status nsn_set_state_device(nsn_ctx *c, const float *pos, const float *quat,
 }
 nsn_status nsn_get_state_device(nsn_ctx *c, float *pos, float *quat, float *vel, float *omega) {
   return state_io(c, false, true, nullptr, nullptr, nullptr, nullptr, pos, quat, vel, omega);
+}
+
+nsn_status nsn_get_state_f64(nsn_ctx *c, double *pos, double *quat, double *vel, double *omega) {
+  if (!c) return NSN_ERR_INVALID_ARG;
+  nsn_status s = ensure_built(c);
+  if (s != NSN_OK) return s;
+  const int nb = int(c->scene.kind.size());
+  if (!nb) return NSN_OK;
+  cudaStream_t st = c->stream;
+  double *tmp;
+  CUDA_TRY(c, cudaMallocAsync(&tmp, sizeof(double) * 13 * nb, st));
+  double *p = pos ? tmp : nullptr, *q = quat ? tmp + 3 * nb : nullptr, *v = vel ? tmp + 7 * nb : nullptr,
+         *o = omega ? tmp + 10 * nb : nullptr;
+  if (c->cfg.precision == NSN_FP64)
+    k_gather_state<double, double><<<cdiv(nb, 128), 128, 0, st>>>(c->d64, c->d_bmap, nb, p, q, v, o);
+  else
+    k_gather_state<float, double><<<cdiv(nb, 128), 128, 0, st>>>(c->d32, c->d_bmap, nb, p, q, v, o);
+  CUDA_TRY(c, cudaGetLastError());
+  if (pos) CUDA_TRY(c, cudaMemcpyAsync(pos, p, sizeof(double) * 3 * nb, cudaMemcpyDeviceToHost, st));
+  if (quat) CUDA_TRY(c, cudaMemcpyAsync(quat, q, sizeof(double) * 4 * nb, cudaMemcpyDeviceToHost, st));
+  if (vel) CUDA_TRY(c, cudaMemcpyAsync(vel, v, sizeof(double) * 3 * nb, cudaMemcpyDeviceToHost, st));
+  if (omega) CUDA_TRY(c, cudaMemcpyAsync(omega, o, sizeof(double) * 3 * nb, cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(c, cudaFreeAsync(tmp, st));
+  CUDA_TRY(c, cudaStreamSynchronize(st));
+  return NSN_OK;
 }
 
 nsn_status nsn_get_lambda(nsn_ctx *c, double *lambda) {

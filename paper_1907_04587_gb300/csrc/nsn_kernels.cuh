@@ -16,8 +16,9 @@
 //   body pass : per body segment  s = sum_e J_e x[row(e)],  y = H~^-1 s,
 //               then per entry    t[e] = J_e . y
 //   row pass  : per row           w_i = sum_{e in row i} t[e] + (C x)_i + eps x_i
-// CR dot products are fused into the row pass as FP64 block partials; the CR
-// update reduces them (every block redundantly, deterministic order).
+// CR dot products are fused into the row pass as per-block partials (exact
+// FP32 double-single per thread, FP64 across threads); one small kernel
+// reduces them in a fixed order and forms the FP64 CR scalars.
 #pragma once
 #include <cuda_runtime.h>
 #include <math.h>
@@ -26,7 +27,7 @@
 namespace nsn {
 
 constexpr int BLOCK = 256;
-constexpr int NPART = 4;  // partials per block in the row passes
+constexpr int NPART = 5;  // partials per block in the row passes
 
 enum BodyMode { BM_RESIDUAL = 0, BM_APPLY = 1, BM_UPDATE = 2 };
 enum RowMode { RM_RHS = 0, RM_APPLY = 1 };
@@ -241,6 +242,32 @@ __device__ void svd3(const T *F, T *U, T *s, T *V) {
 
 // ------------------------------------------------------------------------------------
 // reductions
+//
+// Per-thread partial dot products.  FP64 arithmetic is a small fraction of
+// the FP32 rate on this part, so the FP32 build accumulates exactly-rounded
+// products in double-single form (hi + lo, error-free transformations:
+// TwoProduct via fma, TwoSum of Knuth) on the FP32 pipes and converts to FP64
+// once per thread; the FP64 build accumulates in double.
+template <typename T>
+struct Acc {
+  double v = 0.0;
+  __device__ __forceinline__ void add_prod(T a, T b) { v = fma(double(a), double(b), v); }
+  __device__ __forceinline__ double get() const { return v; }
+};
+template <>
+struct Acc<float> {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add_prod(float a, float b) {
+    const float p = a * b;
+    const float pe = fmaf(a, b, -p);  // exact product p + pe
+    const float s = hi + p;           // TwoSum(hi, p)
+    const float bb = s - hi;
+    const float e = (hi - (s - bb)) + (p - bb);
+    hi = s;
+    lo += e + pe;
+  }
+  __device__ __forceinline__ double get() const { return double(hi) + double(lo); }
+};
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -270,23 +297,33 @@ __device__ __forceinline__ T group_sum(T v) {
   return v;
 }
 
-// Deterministic sum of n partials at stride NPART (+ offset) by warp 0; all
-// threads of the block receive the result via shared memory.
-__device__ __forceinline__ void reduce_partials(const double *part, int n, double *out4, double *smem) {
-  if (threadIdx.x < 32) {
-    double a[NPART] = {0, 0, 0, 0};
-    for (int i = threadIdx.x; i < n; i += 32)
+// Deterministic sum of n NPART-tuples of partials by the whole block (fixed
+// assignment of partials to threads, fixed tree); every thread receives the
+// result in out.  Launched with BLOCK threads.
+__device__ __forceinline__ void reduce_partials(const double *part, int n, double *out) {
+  __shared__ double red[BLOCK / 32][NPART];
+  double a[NPART] = {0, 0, 0, 0, 0};
+  for (int i = threadIdx.x; i < n; i += BLOCK)
 #pragma unroll
-      for (int k = 0; k < NPART; k++) a[k] += part[NPART * i + k];
+    for (int k = 0; k < NPART; k++) a[k] += part[NPART * i + k];
 #pragma unroll
-    for (int k = 0; k < NPART; k++) a[k] = warp_sum(a[k]);
-    if (threadIdx.x == 0)
+  for (int k = 0; k < NPART; k++) a[k] = warp_sum(a[k]);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0)
 #pragma unroll
-      for (int k = 0; k < NPART; k++) smem[k] = a[k];
+    for (int k = 0; k < NPART; k++) red[w][k] = a[k];
+  __syncthreads();
+  if (w == 0) {
+#pragma unroll
+    for (int k = 0; k < NPART; k++) {
+      double v = l < (BLOCK >> 5) ? red[l][k] : 0.0;
+      v = warp_sum(v);
+      if (l == 0) red[0][k] = v;
+    }
   }
   __syncthreads();
 #pragma unroll
-  for (int k = 0; k < NPART; k++) out4[k] = smem[k];
+  for (int k = 0; k < NPART; k++) out[k] = red[0][k];
   __syncthreads();
 }
 
@@ -351,30 +388,44 @@ __global__ void k_begin_particle(Dev<T> D) {
 // K1-K3: row evaluation at the iterate (q^n, u^n, lambda^n)
 
 // body id encoding: >= 0 rigid index, <= -2 particle index (-id-2), -1 world
+//
+// A point's position at the iterate is kept in three parts: the body position
+// at the start of the step x0 (an input value), the displacement h u of the
+// backward-Euler update (Sec. 5) and the lever arm r = R(q) p.  Differences
+// of two points are formed part by part, (x0_a - x0_b) + h (v_a - v_b) +
+// (r_a - r_b), so that in FP32 their accuracy does not depend on how far from
+// the world origin the bodies are.
 template <typename T>
 struct Side {
   int kind;  // 0 world, 1 rigid, 2 particle
   int idx;
-  T w[3];    // world point
+  T x0[3];   // start-of-step position (world point for the static world)
+  T hu[3];   // h * linear velocity of the iterate
   T r[3];    // lever arm (rigid)
 };
 
 template <typename T>
 __device__ __forceinline__ void load_side(const Dev<T> &D, int enc, const T *p, Side<T> &s) {
+  const T h = T(D.h);
   if (enc >= 0) {
     s.kind = 1; s.idx = enc;
     T q[4], R[9];
     for (int k = 0; k < 4; k++) q[k] = D.rq[k][enc];
     quat_R(q, R);
     mat3v(R, p, s.r);
-    for (int k = 0; k < 3; k++) s.w[k] = D.rx[k][enc] + s.r[k];
+    for (int k = 0; k < 3; k++) { s.x0[k] = D.rx0[k][enc]; s.hu[k] = h * D.ru[k][enc]; }
   } else if (enc == -1) {
     s.kind = 0; s.idx = -1;
-    for (int k = 0; k < 3; k++) { s.w[k] = p[k]; s.r[k] = T(0); }
+    for (int k = 0; k < 3; k++) { s.x0[k] = p[k]; s.hu[k] = T(0); s.r[k] = T(0); }
   } else {
     s.kind = 2; s.idx = -enc - 2;
-    for (int k = 0; k < 3; k++) { s.w[k] = D.px[k][s.idx]; s.r[k] = T(0); }
+    for (int k = 0; k < 3; k++) { s.x0[k] = D.px0[k][s.idx]; s.hu[k] = h * D.pu[k][s.idx]; s.r[k] = T(0); }
   }
+}
+
+template <typename T>
+__device__ __forceinline__ void side_diff(const Side<T> &A, const Side<T> &B, T *dd) {
+  for (int k = 0; k < 3; k++) dd[k] = ((A.x0[k] - B.x0[k]) + (A.hu[k] - B.hu[k])) + (A.r[k] - B.r[k]);
 }
 
 // side Jacobian along direction d: [d, r x d] (rigid) or [d] (particle), times sgn
@@ -425,18 +476,20 @@ __device__ __forceinline__ void write_entry(const Dev<T> &D, int e, const T *J6,
   }
 }
 
-// App. A.2 W_FB with the unsquared |D^T qdot| of the fixed point; stick gives
-// W = 0; a non-positive denominator is floored at 1e-6 (vt + r mu lambda_n).
+// App. A.2: W_FB = |v|^{n+1} / |lambda_f|^{n+1} of the FB fixed-point update,
+// with the unsquared |D^T qdot|.  Returns false (friction rows take the
+// inactive form: zero friction at the fixed point) when the updated friction
+// magnitude r |lambda_f|^{n+1} = vt + r mu ln - sqrt(.) is not positive.
 template <typename T>
-__device__ __forceinline__ T w_fb(T vt, T lf, T mu_ln, T r) {
+__device__ __forceinline__ bool w_fb(T vt, T lf, T mu_ln, T r, T &W) {
+  if (!(mu_ln > T(0))) return false;
   T bb = mu_ln - lf;
   T root = dsqrt(vt * vt + r * r * bb * bb);
-  T num = r * (root - r * bb);
   T den = vt + r * mu_ln - root;
-  if (num == T(0)) return T(0);
-  T fl = T(1e-6) * (vt + r * mu_ln);
-  if (den < fl) den = fl;
-  return num / den;
+  if (!(den > T(0))) return false;
+  T num = r * (root - r * bb);
+  W = num == T(0) ? T(0) : num / den;
+  return true;
 }
 
 template <typename T>
@@ -457,7 +510,8 @@ __global__ void k_eval_contacts(Dev<T> D, int buf, int force) {
   Side<T> A, B;
   load_side(D, D.cba[c], pa, A);
   load_side(D, D.cbb[c], pb, B);
-  T dd[3] = {A.w[0] - B.w[0], A.w[1] - B.w[1], A.w[2] - B.w[2]};
+  T dd[3];
+  side_diff(A, B, dd);
   T Cn = dot3(n, dd) - D.cdd[c];
   // geometric normal row and effective-mass r (Eq. rscaling)
   T Ja[6], Jb[6];
@@ -500,10 +554,17 @@ __global__ void k_eval_contacts(Dev<T> D, int buf, int force) {
   else if (D.rscale == 2) rF = h * T(0.5) * dq;
   T mu_ln = D.cmu[c] * ln;
   T lf[2] = {D.lam[row + 1], D.lam[row + 2]};
-  if (mu_ln > T(0)) {
-    T vn = dsqrt(vt[0] * vt[0] + vt[1] * vt[1]);
-    T lfn = dsqrt(lf[0] * lf[0] + lf[1] * lf[1]);
-    T W = D.ncp == 1 ? w_min(vn, lfn, mu_ln, rF) : w_fb(vn, lfn, mu_ln, rF);
+  T vn = dsqrt(vt[0] * vt[0] + vt[1] * vt[1]);
+  T lfn = dsqrt(lf[0] * lf[0] + lf[1] * lf[1]);
+  T W = T(1);
+  bool active;
+  if (D.ncp == 1) {
+    active = mu_ln > T(0);
+    if (active) W = w_min(vn, lfn, mu_ln, rF);
+  } else {
+    active = w_fb(vn, lfn, mu_ln, rF, W);
+  }
+  if (active) {
     for (int k = 0; k < 2; k++) {
       write_entry(D, D.re0[row + 1 + k], Da[k], buf);
       write_entry(D, D.re1[row + 1 + k], Db[k], buf);
@@ -538,6 +599,8 @@ __global__ void k_eval_joints(Dev<T> D, int buf, int force) {
   load_side(D, eb, pb, B);
   const T e = D.je[j];
   const int base = 3 * D.nc + 5 * j;
+  T dd[3];
+  side_diff(A, B, dd);
   for (int k = 0; k < 3; k++) {
     T ek[3] = {T(0), T(0), T(0)};
     ek[k] = T(1);
@@ -546,7 +609,7 @@ __global__ void k_eval_joints(Dev<T> D, int buf, int force) {
     side_row(B, ek, T(-1), Jb);
     write_entry(D, D.re0[base + k], Ja, buf);
     write_entry(D, D.re1[base + k], Jb, buf);
-    T cb = A.w[k] - B.w[k];
+    T cb = dd[k];
     D.cdiag[base + k] = e / (h * h);
     D.hv[base + k] = (cb + e * D.lam[base + k]) / h;
   }
@@ -595,11 +658,11 @@ __global__ void k_eval_tets(Dev<T> D, int buf, int force) {
   for (int q = 0; q < 4; q++) v[q] = D.tv[4 * t + q];
   T Dmi[9];
   for (int k = 0; k < 9; k++) Dmi[k] = D.tDmi[9 * t + k];
-  T x0[3];
-  for (int r = 0; r < 3; r++) x0[r] = D.px[r][v[0]];
+  // edge vectors from start-of-step positions plus displacements (see Side)
   T Ds[9];
   for (int k = 0; k < 3; k++)
-    for (int r = 0; r < 3; r++) Ds[3 * r + k] = D.px[r][v[k + 1]] - x0[r];
+    for (int r = 0; r < 3; r++)
+      Ds[3 * r + k] = (D.px0[r][v[k + 1]] - D.px0[r][v[0]]) + h * (D.pu[r][v[k + 1]] - D.pu[r][v[0]]);
   T F[9];
   for (int r = 0; r < 3; r++)
     for (int k = 0; k < 3; k++) F[3 * r + k] = Ds[3 * r] * Dmi[k] + Ds[3 * r + 1] * Dmi[3 + k] + Ds[3 * r + 2] * Dmi[6 + k];
@@ -659,11 +722,11 @@ __global__ void __launch_bounds__(BLOCK) k_body_pass(Dev<T> D, const T *__restri
   if (!force && D.fl->newton_stop) return;
   if (MODE == BM_APPLY && D.fl->cr_stop) return;
   __shared__ double smem[BLOCK / 32];
+  Acc<T> acc_g2;
   const int gpb = BLOCK / G;         // groups (bodies) per block iteration
   const int gid = threadIdx.x / G;
   const int lane = threadIdx.x % G;
   const T h = T(D.h);
-  double acc_g2 = 0.0;
   const bool rigid_blocks = blockIdx.x < D.nblk_body_r;
   if (rigid_blocks) {
     const int stride = D.nblk_body_r * gpb;
@@ -709,7 +772,7 @@ __global__ void __launch_bounds__(BLOCK) k_body_pass(Dev<T> D, const T *__restri
         sym3v(Si, g + 3, y + 3);
         if (lane == 0) {
 #pragma unroll
-          for (int k = 0; k < 6; k++) { D.rg[k][b] = g[k]; D.ryg[k][b] = y[k]; acc_g2 += double(g[k]) * double(g[k]); }
+          for (int k = 0; k < 6; k++) { D.rg[k][b] = g[k]; D.ryg[k][b] = y[k]; acc_g2.add_prod(g[k], g[k]); }
         }
         for (int e = s0 + lane; e < s1; e += G) {
           T J[6], tj[3];
@@ -805,7 +868,7 @@ __global__ void __launch_bounds__(BLOCK) k_body_pass(Dev<T> D, const T *__restri
 #pragma unroll
           for (int k = 0; k < 3; k++) {
             D.pg[k][b] = g[k]; D.pyg[k][b] = y[k]; D.phinv[k][b] = hi[k];
-            acc_g2 += double(g[k]) * double(g[k]);
+            acc_g2.add_prod(g[k], g[k]);
           }
         }
         for (int e = s0 + lane; e < s1; e += G) {
@@ -830,7 +893,7 @@ __global__ void __launch_bounds__(BLOCK) k_body_pass(Dev<T> D, const T *__restri
     }
   }
   if (MODE == BM_RESIDUAL) {
-    double tot = block_sum(acc_g2, smem);
+    double tot = block_sum(acc_g2.get(), smem);
     if (threadIdx.x == 0) D.part_body[blockIdx.x] = tot;
   }
 }
@@ -841,13 +904,15 @@ __global__ void __launch_bounds__(BLOCK) k_body_pass(Dev<T> D, const T *__restri
 // RM_RHS:   b = (1/h)(J H~^-1 g - h), diag = [J H~^-1 J^T]_ii + C_ii + eps,
 //           P = 1/diag; CR start x = 0, z = P b, p = z; partials |h|^2, b^T P b.
 // RM_APPLY: Az = J H~^-1 J^T z + C z + eps z (from the body pass' t);
-//           partials z^T Az, Az^T P Az, Az^T P Ap, z^T diag z.
+//           partials z^T Az, Az^T P Az, Az^T P Ap, z^T diag z, Ap^T P Ap
+//           (the last from the stored Ap, so that the CR recurrence below is
+//           exact for the vectors actually held in memory).
 template <typename T, int MODE>
 __global__ void __launch_bounds__(BLOCK) k_row_pass(Dev<T> D, int force) {
   if (!force && D.fl->newton_stop) return;
   if (MODE == RM_APPLY && D.fl->cr_stop) return;
   __shared__ double smem[BLOCK / 32];
-  double a[NPART] = {0, 0, 0, 0};
+  Acc<T> a[NPART];
   const T eps = T(D.eps), ih = T(1) / T(D.h);
   if (blockIdx.x < D.nblk_row_pair) {
     const int stride = D.nblk_row_pair * BLOCK;
@@ -861,11 +926,11 @@ __global__ void __launch_bounds__(BLOCK) k_row_pass(Dev<T> D, int force) {
         const T bi = (tb - hv) * ih;
         const T dg = td + D.cdiag[i] + eps;
         const T Pi = T(1) / dg;
-        D.b[i] = bi; D.P[i] = Pi; D.x[i] = T(0);
+        D.b[i] = bi; D.P[i] = Pi; D.x[i] = T(0); D.Ap[i] = T(0);
         const T zi = Pi * bi;
         D.z[i] = zi; D.p[i] = zi;
-        a[0] += double(hv) * double(hv);
-        a[1] += double(bi) * double(zi);
+        a[0].add_prod(hv, hv);
+        a[1].add_prod(bi, zi);
       } else {
         T acc = T(0);
         if (e0 >= 0) acc += D.t[e0];
@@ -873,11 +938,14 @@ __global__ void __launch_bounds__(BLOCK) k_row_pass(Dev<T> D, int force) {
         const T zi = D.z[i];
         const T Pi = D.P[i];
         const T az = acc + (D.cdiag[i] + eps) * zi;
+        const T api = D.Ap[i];
         D.Az[i] = az;
-        a[0] += double(zi) * double(az);
-        a[1] += double(az) * double(az) * double(Pi);
-        a[2] += double(az) * double(Pi) * double(D.Ap[i]);
-        a[3] += double(zi) * double(zi) / double(Pi);
+        const T paz = Pi * az;
+        a[0].add_prod(zi, az);
+        a[1].add_prod(az, paz);
+        a[2].add_prod(paz, api);
+        a[3].add_prod(zi, zi / Pi);
+        a[4].add_prod(api, Pi * api);
       }
     }
   } else {
@@ -898,11 +966,11 @@ __global__ void __launch_bounds__(BLOCK) k_row_pass(Dev<T> D, int force) {
           const T hv = D.hv[i];
           const T bi = (tb - hv) * ih;
           const T Pi = T(1) / (td + cc[k] + eps);
-          D.b[i] = bi; D.P[i] = Pi; D.x[i] = T(0);
+          D.b[i] = bi; D.P[i] = Pi; D.x[i] = T(0); D.Ap[i] = T(0);
           const T zi = Pi * bi;
           D.z[i] = zi; D.p[i] = zi;
-          a[0] += double(hv) * double(hv);
-          a[1] += double(bi) * double(zi);
+          a[0].add_prod(hv, hv);
+          a[1].add_prod(bi, zi);
         }
       } else {
         const int i0 = rb + 3 * t;
@@ -921,17 +989,20 @@ __global__ void __launch_bounds__(BLOCK) k_row_pass(Dev<T> D, int force) {
           const T az = acc + cz[k] + eps * zz[k];
           D.Az[i] = az;
           const T Pi = D.P[i];
-          a[0] += double(zz[k]) * double(az);
-          a[1] += double(az) * double(az) * double(Pi);
-          a[2] += double(az) * double(Pi) * double(D.Ap[i]);
-          a[3] += double(zz[k]) * double(zz[k]) / double(Pi);
+          const T api = D.Ap[i];
+          const T paz = Pi * az;
+          a[0].add_prod(zz[k], az);
+          a[1].add_prod(az, paz);
+          a[2].add_prod(paz, api);
+          a[3].add_prod(zz[k], zz[k] / Pi);
+          a[4].add_prod(api, Pi * api);
         }
       }
     }
   }
 #pragma unroll
   for (int k = 0; k < NPART; k++) {
-    double s = block_sum(a[k], smem);
+    double s = block_sum(a[k].get(), smem);
     if (threadIdx.x == 0) D.part_row[NPART * blockIdx.x + k] = s;
   }
 }
@@ -941,12 +1012,12 @@ template <typename T>
 __global__ void k_merit(Dev<T> D, int n, int force) {
   if (!force && D.fl->newton_stop) return;
   __shared__ double smem[BLOCK / 32];
-  __shared__ double r4[NPART];
+  double r4[NPART];
   double g2 = 0.0;
   const int nb = D.nblk_body_r + D.nblk_body_p;
   for (int i = threadIdx.x; i < nb; i += BLOCK) g2 += D.part_body[i];
   g2 = block_sum(g2, smem);
-  reduce_partials(D.part_row, D.nblk_row_pair + D.nblk_row_tet, r4, r4);
+  reduce_partials(D.part_row, D.nblk_row_pair + D.nblk_row_tet, r4);
   if (threadIdx.x == 0) {
     double m = sqrt(g2 + r4[0]);
     D.sc->merit[n < 1023 ? n : 1023] = m;
@@ -969,18 +1040,18 @@ __global__ void k_merit(Dev<T> D, int n, int force) {
 // ------------------------------------------------------------------------------------
 // K7: CR with one global synchronisation per iteration.  The scalar kernel
 // reduces the row-pass partials (d1 = z^T Az, d2 = Az^T P Az, d3 = Az^T P Ap,
-// d4 = ||r||_P^2) once, in a fixed order:
-//   beta = rho'/rho,  Ap^T P Ap = d2 + 2 beta d3 + beta^2 (Ap^T P Ap)_prev,
+// d4 = ||r||_P^2, d5 = Ap^T P Ap of the stored Ap) once, in a fixed order:
+//   beta = rho'/rho,  Ap'^T P Ap' = d2 + 2 beta d3 + beta^2 d5,
 //   alpha = rho'/(Ap^T P Ap)     (iteration 0: beta = 0, i.e. p = z, Ap = Az)
 // and the update kernel applies p = z + beta p, Ap = Az + beta Ap,
 // x += alpha p, z -= alpha P Ap.
 template <typename T>
 __global__ void k_cr_scalars(Dev<T> D, int k) {
   if (D.fl->newton_stop || D.fl->cr_stop) return;
-  __shared__ double r4[NPART];
-  reduce_partials(D.part_row, D.nblk_row_pair + D.nblk_row_tet, r4, r4);
+  double r4[NPART];
+  reduce_partials(D.part_row, D.nblk_row_pair + D.nblk_row_tet, r4);
   if (threadIdx.x == 0) {
-    const double d1 = r4[0], d2 = r4[1], d3 = r4[2], d4 = r4[3];
+    const double d1 = r4[0], d2 = r4[1], d3 = r4[2], d4 = r4[3], d5 = r4[4];
     int st = 0;
     const double cur = sqrt(d4 > 0.0 ? d4 : 0.0);
     if (D.sc->res0 == 0.0) st = 1;
@@ -991,7 +1062,7 @@ __global__ void k_cr_scalars(Dev<T> D, int k) {
       if (!(d1 > 0.0) || !(rp > 0.0)) st = 1;
       else {
         beta = d1 / rp;
-        apap = d2 + 2.0 * beta * d3 + beta * beta * D.sc->appap[(k - 1) & 1];
+        apap = d2 + 2.0 * beta * d3 + beta * beta * d5;
       }
     }
     if (!(apap > 0.0)) st = 1;
@@ -1008,14 +1079,14 @@ __global__ void k_cr_scalars(Dev<T> D, int k) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(BLOCK) k_cr_update(Dev<T> D) {
+__global__ void __launch_bounds__(BLOCK) k_cr_update(Dev<T> D, int k) {
   if (D.fl->newton_stop || D.fl->cr_stop) return;
   const T alpha = T(D.sc->alpha), beta = T(D.sc->beta);
   const int stride = gridDim.x * BLOCK;
   for (int i = blockIdx.x * BLOCK + threadIdx.x; i < D.R; i += stride) {
     const T zi = D.z[i];
-    const T pi = zi + beta * D.p[i];
-    const T api = D.Az[i] + beta * D.Ap[i];
+    const T pi = k == 0 ? zi : zi + beta * D.p[i];
+    const T api = k == 0 ? D.Az[i] : D.Az[i] + beta * D.Ap[i];
     D.p[i] = pi;
     D.Ap[i] = api;
     D.x[i] += alpha * pi;
@@ -1028,7 +1099,7 @@ template <typename T>
 __global__ void k_cr_init(Dev<T> D) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < D.R; i += gridDim.x * blockDim.x) {
     const T zi = D.P[i] * D.b[i];
-    D.x[i] = T(0); D.z[i] = zi; D.p[i] = zi;
+    D.x[i] = T(0); D.z[i] = zi; D.p[i] = zi; D.Ap[i] = T(0);
   }
 }
 

@@ -85,6 +85,7 @@ def lib():
         "nsn_set_state_device": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
         "nsn_get_state_device": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
         "nsn_get_lambda": (C.c_int, [_vp, _dp]),
+        "nsn_get_state_f64": (C.c_int, [_vp, _dp, _dp, _dp, _dp]),
         "nsn_get_merit_history": (C.c_int, [_vp, _dp, C.c_int32, _ip]),
         "nsn_linearize": (C.c_int, [_vp, C.c_int32]),
         "nsn_apply_operator": (C.c_int, [_vp, _dp, _dp]),
@@ -179,6 +180,13 @@ def nsn_get_state(ctx, nb):
     out = dict(pos=np.zeros((nb, 3), np.float32), quat=np.zeros((nb, 4), np.float32),
                vel=np.zeros((nb, 3), np.float32), omega=np.zeros((nb, 3), np.float32))
     _check(ctx, lib().nsn_get_state(ctx, *[_p(out[k]) for k in ("pos", "quat", "vel", "omega")]), "nsn_get_state")
+    return out
+
+
+def nsn_get_state_f64(ctx, nb):
+    out = dict(pos=np.zeros((nb, 3)), quat=np.zeros((nb, 4)), vel=np.zeros((nb, 3)), omega=np.zeros((nb, 3)))
+    _check(ctx, lib().nsn_get_state_f64(ctx, *[_p(out[k], _dp) for k in ("pos", "quat", "vel", "omega")]),
+           "nsn_get_state_f64")
     return out
 
 
@@ -335,6 +343,9 @@ class Solver:
 
     def get_state(self):
         return nsn_get_state(self.ctx, self.nb)
+
+    def get_state_f64(self):
+        return nsn_get_state_f64(self.ctx, self.nb)
 
     def set_state(self, pos=None, quat=None, vel=None, omega=None):
         nsn_set_state(self.ctx, self.nb, pos, quat, vel, omega)

@@ -107,6 +107,21 @@ def test_w_stick_and_penalty(orc):
         assert orc.w_min(0.0, 6.0, 5.0, r) > 0.0
 
 
+def test_w_asymptote_past_cone_limit(orc):
+    """Fig. 4 (left): past the cone limit W grows to a vertical asymptote where
+    the FB fixed-point friction magnitude (App. A.2) reaches zero,
+    |lambda_f|* = mu lambda_n + sqrt(2 vt r mu lambda_n + r^2 (mu lambda_n)^2) / r;
+    beyond it the friction rows take the inactive form (zero friction)."""
+    for vt, mln, r in [(0.5, 5.0, 0.3), (0.1, 2.0, 1e-3), (0.0, 1.0, 0.05)]:
+        lim = mln + np.sqrt(2 * vt * r * mln + (r * mln) ** 2) / r
+        ws = [orc.w_fb(vt, f * mln, mln, r) for f in (1.0, 1.2, 1.5)]
+        if vt > 0:
+            assert ws[0] < ws[1] < ws[2]
+        assert orc.fb_friction_active(vt, lim * (1 - 1e-9), mln, r)
+        assert not orc.fb_friction_active(vt, lim * (1 + 1e-9), mln, r)
+        assert not orc.fb_friction_active(vt, 0.5, 0.0, r)
+
+
 # ---------------------------------------------------------------------------------
 # Neo-Hookean compliance (Sec. 9.2.2, App. B)
 
