@@ -1,0 +1,342 @@
+#!/usr/bin/env python3
+"""Benchmark of the non-smooth Newton time stepper on one GB300 (per rank).
+
+Workload (default): 4096 independent RL-style environments, each a revolute
+chain of 3-20 links lying on a plane plus 0-64 cubes piled in up to four
+layers, per-environment friction in [0.3, 1.0] (``scenes.batched_envs``),
+solved as one system with the Newton x CR budget the paper uses for its
+many-environment scenes (Table 2, Yumi Cabinet: 5 x 25).
+
+A step is one full time step (Algorithm 1: row evaluation, residual, Schur
+right-hand side, 25 CR iterations of the matrix-free operator, damped update,
+for each of 5 Newton iterations) from the same resident start state.
+  value     env-steps/s with the state already in HBM (device-timed)
+  e2e       env-steps/s through the C ABI with host buffers: host->device copy
+            of the state, the step, device->host copy of the new state
+  roofline  the CR operator apply (body pass + row pass), bytes per launch
+            from the algorithmic count B_apply, timed live with CUDA events
+  cpu_baseline  the FP64 oracle on a 64-environment sample, one host core
+
+``--impl reference`` times the FP64 oracle (the reference arm here) on the
+host cores with the same workload definition, metric and unit.
+Multi-GPU (torchrun): every rank solves its own 4096 environments (weak
+scaling, no data-path collective); rank 0 prints sum(units) / max(time).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_1907_04587_gb300 import scenes  # noqa: E402
+
+METRIC = "env-steps/s (batched plain method, Table 2 many-env budget); CR-apply HBM GB/s"
+UNIT = "env-steps/s"
+WORKLOADS = {
+    "batched4096": dict(make=lambda seed: scenes.batched_envs(seed=seed, n_envs=4096), newton=5, cr=25,
+                        desc="4096 chain+cube-pile environments (3-20 links, 0-64 cubes, mu 0.3-1.0)"),
+    "chain_block": dict(make=lambda seed: scenes.chain_block(seed=seed), newton=10, cr=50,
+                        desc="7-link revolute chain on a 24^3-hex stable Neo-Hookean block (69,120 tets)"),
+    "cube_stack": dict(make=lambda seed: scenes.cube_stack(seed=seed), newton=4, cr=20,
+                       desc="4 unit cubes stacked on a plane (16 contacts)"),
+}
+SAMPLE_ENVS = 64
+
+
+def algorithmic_bytes(sz):
+    """B_apply per operator apply (FP32), per unit:
+    56 per rigid (row, side) entry, 32 per particle entry (J read in both the
+    scatter and the gather pass plus the row index), 12 per row (x, w, C_ii),
+    24 per tet (off-diagonal C block), 76 per rigid body (inverse mass block
+    and z), 36 per particle."""
+    return (56 * sz["rigid_entries"] + 32 * sz["particle_entries"] + 12 * sz["rows"] + 24 * sz["tets"]
+            + 76 * sz["rigid"] + 36 * sz["particles"])
+
+
+def design_bytes(sz):
+    """Bytes the two-pass design itself must move per apply (J read once):
+    36 per rigid entry, 24 per particle entry, 36 per rigid body, 16 per
+    particle, 36 per pair row, 168 per tet (3 rows)."""
+    return (36 * sz["rigid_entries"] + 24 * sz["particle_entries"] + 36 * sz["rigid"] + 16 * sz["particles"]
+            + 36 * sz["pair_rows"] + 168 * sz["tets"])
+
+
+def weak_scaling_value(units_per_rank, seconds_per_rank):
+    """Whole-job throughput: all units processed over the slowest rank's time."""
+    return float(sum(units_per_rank)) / float(max(seconds_per_rank))
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = tempfile.mktemp(suffix=".csv")
+
+    def __enter__(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            self.proc.wait()
+            self.fh.close()
+
+    def summary(self):
+        if not self.proc or not os.path.exists(self.path):
+            return None
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1])); mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def operator_traffic(kernel_hash):
+    """dram bytes per operator apply from the committed ncu summary, if it was
+    taken on the current kernel source; else None."""
+    p = os.path.join(ROOT, "profiles", "operator_apply_batched4096.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    if d.get("kernel_source_sha256") != kernel_hash:
+        return None
+    return d.get("dram_bytes_per_apply")
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("nsn_kernels.cuh", "nsn_host.cu"):
+        h.update(open(os.path.join(ROOT, "paper_1907_04587_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
+def oracle_rate(workload, seed, budget_s, newton, cr):
+    """FP64 oracle env-steps/s on a bounded sample of the workload."""
+    import oracle
+    if workload == "batched4096":
+        s = scenes.batched_envs(seed=seed, n_envs=SAMPLE_ENVS)
+        envs = SAMPLE_ENVS
+        sample = f"{SAMPLE_ENVS} of the 4096 environments' distribution (seed {seed}), same Newton x CR budget"
+    else:
+        s = WORKLOADS[workload]["make"](seed)
+        envs = 1
+        sample = "the full scene"
+    o = oracle.Oracle(s, newton_iters=newton, cr_iters=cr)
+    st0 = o.get_state()
+    n, t0 = 0, time.perf_counter()
+    while True:
+        o.set_state(**st0)
+        o.step()
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s:
+            break
+    return envs * n / el, dict(kind="oracle", cores=1, sample=f"{sample}; {n} steps in {el:.1f} s")
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    W = WORKLOADS[args.workload]
+    value, cb = oracle_rate(args.workload, 0, args.ref_budget, W["newton"], W["cr"])
+    cb["value"] = value
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": args.workload, "description": W["desc"], "newton_iters": W["newton"],
+                      "cr_iters": W["cr"]},
+           "cpu_baseline": cb,
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    from paper_1907_04587_gb300 import nsn
+    import __graft_entry__
+    __graft_entry__.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    W = WORKLOADS[args.workload]
+    newton = args.newton or W["newton"]
+    cr = args.cr or W["cr"]
+    s = W["make"](rank)
+    n_envs = int(s["n_envs"])
+    stream = torch.cuda.Stream(device=dev)
+    solver = nsn.Solver(s, stream=stream.cuda_stream, newton_iters=newton, cr_iters=cr, tol_rel=args.tol,
+                        cr_tol_mode=1 if args.tol > 0 else 0, precision=nsn.NSN_FP32, use_graph=1)
+    nb = solver.nb
+    st0 = {k: torch.from_numpy(np.ascontiguousarray(s[k], dtype=np.float32)).to(dev)
+           for k in ("pos", "quat", "vel", "omega")}
+    ptr = {k: v.data_ptr() for k, v in st0.items()}
+
+    def one_step():
+        nsn.nsn_set_state_device(solver.ctx, ptr["pos"], ptr["quat"], ptr["vel"], ptr["omega"])
+        return solver.step(1)
+
+    torch.cuda.synchronize()
+    for _ in range(max(args.warmup, 1)):
+        st = one_step()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local_rank) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            st = one_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sec = e0.elapsed_time(e1) / 1e3
+    rel_merit = st["merit_final"] / st["merit0"] if st["merit0"] > 0 else 0.0
+    # e2e: host buffers through the C ABI (pinned), copies inside the timed region
+    host_in = {k: torch.from_numpy(np.ascontiguousarray(s[k], dtype=np.float32)).pin_memory()
+               for k in ("pos", "quat", "vel", "omega")}
+    host_out = {k: torch.empty_like(v).pin_memory() for k, v in host_in.items()}
+    fp = lambda t: nsn.C.cast(t.data_ptr(), nsn._fp)  # noqa: E731
+    L = nsn.lib()
+    h2d = sum(v.numel() * 4 for v in host_in.values())
+    d2h = sum(v.numel() * 4 for v in host_out.values())
+    for _ in range(max(args.warmup, 1)):
+        L.nsn_set_state(solver.ctx, *[fp(host_in[k]) for k in ("pos", "quat", "vel", "omega")])
+        solver.step(1)
+        L.nsn_get_state(solver.ctx, *[fp(host_out[k]) for k in ("pos", "quat", "vel", "omega")])
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        L.nsn_set_state(solver.ctx, *[fp(host_in[k]) for k in ("pos", "quat", "vel", "omega")])
+        solver.step(1)
+        L.nsn_get_state(solver.ctx, *[fp(host_out[k]) for k in ("pos", "quat", "vel", "omega")])
+    torch.cuda.synchronize()
+    sec_e2e = time.perf_counter() - t0
+    # roofline of the CR operator apply, timed live on the solver's stream
+    ms_body, ms_row = solver.time_operator(20)
+    sz = solver.sizes()
+    B = algorithmic_bytes(sz)
+    peak, peak_kind = measured_peaks()
+    achieved = B / ((ms_body + ms_row) * 1e-3) / 1e9
+    launches = solver.launches_per_step()
+    units = n_envs * args.steps
+    if dist:
+        t = torch.tensor([sec, sec_e2e, float(units)], device=dev, dtype=torch.float64)
+        tmax = t.clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        tsum = t.clone()
+        dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
+        value = tsum[2].item() / tmax[0].item()
+        value_e2e = tsum[2].item() / tmax[1].item()
+    else:
+        value = weak_scaling_value([units], [sec])
+        value_e2e = weak_scaling_value([units], [sec_e2e])
+    if rank != 0:
+        return
+    cb_value, cb = oracle_rate(args.workload, rank, args.cpu_budget, newton, cr)
+    cb["value"] = cb_value
+    cb["unit"] = UNIT
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": sec * 1e3 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "description": W["desc"], "n_envs": n_envs, "bodies": nb,
+                   "rows": sz["rows"], "newton_iters": newton, "cr_iters": cr, "tol_rel": args.tol,
+                   "relative_merit_last_step": rel_merit, "newton_done": st["newton_done"],
+                   "cr_total": st["cr_total"], "device_bytes": sz["device_bytes"],
+                   "l2": "working set larger than L2 (no flush between steps)",
+                   "parallelism": f"weak, {world} independent replica(s)"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": operator_traffic(kernel_source_hash()),
+                     "kernel": "CR operator apply = k_body_pass<APPLY> + k_row_pass<APPLY>",
+                     "ms_body_pass": ms_body, "ms_row_pass": ms_row, "bytes_algorithmic": B,
+                     "bytes_design": design_bytes(sz), "peak_kind": f"{peak_kind} hbm_gbs (burst)"},
+        "cpu_baseline": cb,
+        "e2e": {"value": value_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": args.steps * (launches + 1),
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="batched4096", choices=list(WORKLOADS))
+    ap.add_argument("--newton", type=int, default=0)
+    ap.add_argument("--cr", type=int, default=0)
+    ap.add_argument("--tol", type=float, default=0.0)
+    ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work for cpu_baseline")
+    ap.add_argument("--ref-budget", type=float, default=60.0, help="seconds of oracle work for --impl reference")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -183,8 +183,19 @@ nsn_status nsn_apply_operator(nsn_ctx *ctx, const double *x, double *y);
 nsn_status nsn_solve(nsn_ctx *ctx, int32_t iters, double *dlambda, double *du);
 nsn_status nsn_get_system(nsn_ctx *ctx, double *b, double *diag, double *hvec, double *g);
 
-/* Device time and launch count of the last nsn_step (all kernels of the step). */
+/* Number of kernel launches in one nsn_step (the captured graph's nodes). */
 nsn_status nsn_last_launch_count(nsn_ctx *ctx, int32_t *kernels_per_step);
+
+/* Times the two kernels of one Schur operator apply (Eq. schur_system,
+ * matrix-free: body-segment pass J^T z, H~^-1, J y per entry; row pass with
+ * C z + eps z and the fused CR dot products) on the context stream with CUDA
+ * events, iters times on the system of the last step, and returns the mean
+ * duration of each in milliseconds.  Requires a prior nsn_step. */
+nsn_status nsn_time_operator(nsn_ctx *ctx, int32_t iters, float *ms_body_pass, float *ms_row_pass);
+
+/* Layout sizes: [rigid bodies, particles, rows, pair rows, tets, rigid
+ * entries, particle entries, device bytes held by the context]. */
+nsn_status nsn_operator_sizes(nsn_ctx *ctx, int64_t *sizes8);
 
 #ifdef __cplusplus
 }

@@ -122,34 +122,38 @@ void orc_min_contact(double C, double lam, double r, double *phi, double *alpha,
 }
 
 /* Friction compliance W_FB of App. A.2 for vt = |D^T qdot|, lf = |lambda_f|,
- * mu_ln = mu lambda_n > 0, r = friction r-factor.
+ * mu_ln = mu lambda_n > 0, r = friction r-factor:
+ *   W = |v|^{n+1} / |lambda_f|^{n+1},  b = mu_ln - lf,  S = sqrt(vt^2 + r^2 b^2)
+ *   |v|^{n+1} = S - r b,   r |lambda_f|^{n+1} = vt + r mu_ln - S.
  * Reading: the printed |lambda_f|^{n+1} and W_FB carry |D^T qdot|^2 in the
  * denominator; the fixed point |lambda_f| + psi/r of App. A.2 gives the
  * unsquared |D^T qdot| (dimensionally consistent, and the Fig. 4 example
  * vt = 0.5, mu lambda_n = 5 = |lambda_f| then gives W = 0.1, phi_f = 0).
- * Numerator 0 means stick, W = 0.  The denominator r |lambda_f|^{n+1} is
- * positive except past the vertical asymptote of W (Fig. 4, left); that case
- * is handled by the caller (see orc_fb_friction_active). */
+ * Both differences are evaluated in the algebraically identical forms
+ *   S - r b = vt^2 / (S + r b)  (b >= 0),
+ *   vt + r mu_ln - S = r [2 vt mu_ln + r lf (2 mu_ln - lf)] / (vt + r mu_ln + S),
+ * which avoid cancellation when vt << r |b| (near stick).  Stick (vt = 0
+ * inside the cone) gives W = 0. */
 double orc_w_fb(double vt, double lf, double mu_ln, double r) {
   double bb = mu_ln - lf;
-  double root = sqrt(vt * vt + r * r * bb * bb);
-  double num = r * (root - r * bb);
-  double den = vt + r * mu_ln - root;
-  if (num == 0.0) return 0.0;
-  return num / den;
+  double S = sqrt(vt * vt + r * r * bb * bb);
+  if (vt == 0.0 && bb >= 0.0) return 0.0;
+  double vnext = bb >= 0.0 ? vt * vt / (S + r * bb) : S - r * bb;          /* |v|^{n+1} */
+  double lnext = (2.0 * vt * mu_ln + r * lf * (2.0 * mu_ln - lf)) / (vt + r * mu_ln + S);  /* |lambda_f|^{n+1} */
+  return vnext / lnext;
 }
 
-/* Reading: the FB fixed-point update |lambda_f|^{n+1} = (vt + r mu lambda_n -
- * sqrt(vt^2 + r^2 (mu lambda_n - lf)^2)) / r of App. A.2 is a friction
- * magnitude; where it is not positive (|lambda_f| far outside the cone, past
- * the asymptote of W in Fig. 4) the fixed point has zero friction, so the
- * contact's friction rows take the form of the inactive set of Sec. 3.5
- * (rows zeroed, unit W block, h_f = lambda_f). */
+/* Reading: the FB update |lambda_f|^{n+1} of App. A.2 is a friction
+ * magnitude; where it is not positive while |v|^{n+1} > 0 (|lambda_f| past
+ * the vertical asymptote of W in Fig. 4, left) the fixed point has zero
+ * friction, so the contact's friction rows take the form of the inactive set
+ * of Sec. 3.5 (rows zeroed, unit W block, h_f = lambda_f).  Stick (vt = 0
+ * inside the cone) stays active with W = 0. */
 int orc_fb_friction_active(double vt, double lf, double mu_ln, double r) {
   if (!(mu_ln > 0.0)) return 0;
   double bb = mu_ln - lf;
-  double den = vt + r * mu_ln - sqrt(vt * vt + r * r * bb * bb);
-  return den > 0.0;
+  if (vt == 0.0 && bb >= 0.0) return 1;
+  return 2.0 * vt * mu_ln + r * lf * (2.0 * mu_ln - lf) > 0.0;
 }
 
 /* W_min of App. A.2 (minimum-map friction). */

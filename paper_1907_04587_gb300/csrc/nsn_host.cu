@@ -794,6 +794,38 @@ nsn_status do_system(nsn_ctx *c, double *b, double *diag, double *hvec, double *
 
 }  // namespace
 
+namespace {
+template <typename T>
+nsn_status do_time_operator(nsn_ctx *c, int iters, float *ms_body, float *ms_row) {
+  Dev<T> &D = dev<T>(c);
+  cudaStream_t st = c->stream;
+  cudaEvent_t e[3];
+  for (auto &x : e) CUDA_TRY(c, cudaEventCreate(&x));
+  CUDA_TRY(c, cudaMemsetAsync(D.fl, 0, sizeof(Flags), st));
+  Launcher<T> Lr{c, D, st};
+  double tb = 0.0, tr = 0.0;
+  const int buf = c->cfg.newton_iters & 1;  // entries written by the final evaluation of the last step
+  for (int i = 0; i < iters; i++) {
+    CUDA_TRY(c, cudaEventRecord(e[0], st));
+    Lr.body(BM_APPLY, D.z, buf, 0, 1);
+    CUDA_TRY(c, cudaEventRecord(e[1], st));
+    Lr.rows(RM_APPLY, 1);
+    CUDA_TRY(c, cudaEventRecord(e[2], st));
+    CUDA_TRY(c, cudaEventSynchronize(e[2]));
+    float a = 0.f, b = 0.f;
+    cudaEventElapsedTime(&a, e[0], e[1]);
+    cudaEventElapsedTime(&b, e[1], e[2]);
+    tb += a; tr += b;
+  }
+  for (auto &x : e) cudaEventDestroy(x);
+  CUDA_TRY(c, cudaGetLastError());
+  if (ms_body) *ms_body = float(tb / std::max(iters, 1));
+  if (ms_row) *ms_row = float(tr / std::max(iters, 1));
+  return NSN_OK;
+}
+
+}  // namespace
+
 // =====================================================================================
 // C ABI
 
@@ -1107,6 +1139,23 @@ nsn_status nsn_get_system(nsn_ctx *c, double *b, double *diag, double *hvec, dou
   if (!c) return NSN_ERR_INVALID_ARG;
   if (!c->linearized || c->dirty) return fail(c, NSN_ERR_BAD_STATE, "call nsn_linearize first");
   return c->cfg.precision == NSN_FP64 ? do_system<double>(c, b, diag, hvec, g) : do_system<float>(c, b, diag, hvec, g);
+}
+
+nsn_status nsn_time_operator(nsn_ctx *c, int32_t iters, float *ms_body_pass, float *ms_row_pass) {
+  if (!c || iters <= 0) return NSN_ERR_INVALID_ARG;
+  if (c->dirty) return fail(c, NSN_ERR_BAD_STATE, "call nsn_step first");
+  return c->cfg.precision == NSN_FP64 ? do_time_operator<double>(c, iters, ms_body_pass, ms_row_pass)
+                                      : do_time_operator<float>(c, iters, ms_body_pass, ms_row_pass);
+}
+
+nsn_status nsn_operator_sizes(nsn_ctx *c, int64_t *sizes) {
+  if (!c || !sizes) return NSN_ERR_INVALID_ARG;
+  nsn_status s = ensure_built(c);
+  if (s != NSN_OK) return s;
+  const Layout &L = c->L;
+  sizes[0] = L.nr; sizes[1] = L.np; sizes[2] = L.R; sizes[3] = L.Rpair; sizes[4] = L.nt;
+  sizes[5] = L.ER; sizes[6] = L.EV; sizes[7] = (int64_t)c->dbytes;
+  return NSN_OK;
 }
 
 nsn_status nsn_last_launch_count(nsn_ctx *c, int32_t *kernels_per_step) {

@@ -476,19 +476,24 @@ __device__ __forceinline__ void write_entry(const Dev<T> &D, int e, const T *J6,
   }
 }
 
-// App. A.2: W_FB = |v|^{n+1} / |lambda_f|^{n+1} of the FB fixed-point update,
-// with the unsquared |D^T qdot|.  Returns false (friction rows take the
-// inactive form: zero friction at the fixed point) when the updated friction
-// magnitude r |lambda_f|^{n+1} = vt + r mu ln - sqrt(.) is not positive.
+// App. A.2: W_FB = |v|^{n+1} / |lambda_f|^{n+1} of the FB fixed-point update
+// (unsquared |D^T qdot|), with b = mu ln - lf, S = sqrt(vt^2 + r^2 b^2):
+//   |v|^{n+1} = S - r b           = vt^2 / (S + r b)  when b >= 0
+//   |lambda_f|^{n+1} = (vt + r mu ln - S) / r
+//                    = (2 vt mu ln + r lf (2 mu ln - lf)) / (vt + r mu ln + S)
+// (cancellation-free forms).  Stick (vt = 0 inside the cone) gives W = 0.
+// Returns false -- friction rows take the inactive form, zero friction at the
+// fixed point -- when mu ln <= 0 or |lambda_f|^{n+1} <= 0 with |v|^{n+1} > 0.
 template <typename T>
 __device__ __forceinline__ bool w_fb(T vt, T lf, T mu_ln, T r, T &W) {
   if (!(mu_ln > T(0))) return false;
-  T bb = mu_ln - lf;
-  T root = dsqrt(vt * vt + r * r * bb * bb);
-  T den = vt + r * mu_ln - root;
-  if (!(den > T(0))) return false;
-  T num = r * (root - r * bb);
-  W = num == T(0) ? T(0) : num / den;
+  const T bb = mu_ln - lf;
+  if (vt == T(0) && bb >= T(0)) { W = T(0); return true; }
+  const T lnum = T(2) * vt * mu_ln + r * lf * (T(2) * mu_ln - lf);
+  if (!(lnum > T(0))) return false;
+  const T S = dsqrt(vt * vt + r * r * bb * bb);
+  const T vnext = bb >= T(0) ? vt * vt / (S + r * bb) : S - r * bb;
+  W = vnext * (vt + r * mu_ln + S) / lnum;
   return true;
 }
 

