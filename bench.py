@@ -46,6 +46,8 @@ UNIT = "env-steps/s"
 WORKLOADS = {
     "batched4096": dict(make=lambda seed: scenes.batched_envs(seed=seed, n_envs=4096), newton=5, cr=25,
                         desc="4096 chain+cube-pile environments (3-20 links, 0-64 cubes, mu 0.3-1.0)"),
+    "batched1024": dict(make=lambda seed: scenes.batched_envs(seed=seed, n_envs=1024), newton=5, cr=25,
+                        desc="1024 chain+cube-pile environments (profiling size: ~0.6 M rows, above L2)"),
     "chain_block": dict(make=lambda seed: scenes.chain_block(seed=seed), newton=10, cr=50,
                         desc="7-link revolute chain on a 24^3-hex stable Neo-Hookean block (69,120 tets)"),
     "cube_stack": dict(make=lambda seed: scenes.cube_stack(seed=seed), newton=4, cr=20,
@@ -157,7 +159,7 @@ def kernel_source_hash():
 def oracle_rate(workload, seed, budget_s, newton, cr):
     """FP64 oracle env-steps/s on a bounded sample of the workload."""
     import oracle
-    if workload == "batched4096":
+    if workload.startswith("batched"):
         s = scenes.batched_envs(seed=seed, n_envs=SAMPLE_ENVS)
         envs = SAMPLE_ENVS
         sample = f"{SAMPLE_ENVS} of the 4096 environments' distribution (seed {seed}), same Newton x CR budget"

@@ -457,7 +457,7 @@ struct Launcher {
     eval(buf, 0);
     body(BM_RESIDUAL, D.lam, buf, n, 0);
     rows(RM_RHS, 0);
-    k_merit<T><<<1, BLOCK, 0, st>>>(D, n, 0);
+    k_merit<T><<<1, RED_THREADS, 0, st>>>(D, n, 0);
     count++;
   }
   void cr(int iters, int buf) {
@@ -465,7 +465,7 @@ struct Launcher {
     for (int k = 0; k < iters; k++) {
       body(BM_APPLY, D.z, buf, 0, 0);
       rows(RM_APPLY, 0);
-      k_cr_scalars<T><<<1, BLOCK, 0, st>>>(D, k);
+      k_cr_scalars<T><<<1, RED_THREADS, 0, st>>>(D, k);
       k_cr_update<T><<<D.nblk_upd, BLOCK, 0, st>>>(D, k);
       count += 2;
     }
@@ -488,7 +488,7 @@ struct Launcher {
     eval(buf, 1);
     body(BM_RESIDUAL, D.lam, buf, N, 1);
     rows(RM_RHS, 1);
-    k_merit<T><<<1, BLOCK, 0, st>>>(D, N, 1);
+    k_merit<T><<<1, RED_THREADS, 0, st>>>(D, N, 1);
     count++;
   }
 };

@@ -16,9 +16,9 @@
 //   body pass : per body segment  s = sum_e J_e x[row(e)],  y = H~^-1 s,
 //               then per entry    t[e] = J_e . y
 //   row pass  : per row           w_i = sum_{e in row i} t[e] + (C x)_i + eps x_i
-// CR dot products are fused into the row pass as per-block partials (exact
-// FP32 double-single per thread, FP64 across threads); one small kernel
-// reduces them in a fixed order and forms the FP64 CR scalars.
+// CR dot products are fused into the row pass as per-block partials (FP32
+// within a thread's few rows, FP64 across threads); one small kernel reduces
+// them in a fixed order and forms the FP64 CR scalars.
 #pragma once
 #include <cuda_runtime.h>
 #include <math.h>
@@ -243,30 +243,15 @@ __device__ void svd3(const T *F, T *U, T *s, T *V) {
 // ------------------------------------------------------------------------------------
 // reductions
 //
-// Per-thread partial dot products.  FP64 arithmetic is a small fraction of
-// the FP32 rate on this part, so the FP32 build accumulates exactly-rounded
-// products in double-single form (hi + lo, error-free transformations:
-// TwoProduct via fma, TwoSum of Knuth) on the FP32 pipes and converts to FP64
-// once per thread; the FP64 build accumulates in double.
+// Per-thread partial dot products.  FP64 arithmetic runs at a small fraction
+// of the FP32 rate on this part, so the FP32 build sums the few rows a thread
+// owns (a handful per launch) in FP32 and converts to FP64 once per thread;
+// all sums across threads and blocks are FP64, in a fixed order.
 template <typename T>
 struct Acc {
-  double v = 0.0;
-  __device__ __forceinline__ void add_prod(T a, T b) { v = fma(double(a), double(b), v); }
-  __device__ __forceinline__ double get() const { return v; }
-};
-template <>
-struct Acc<float> {
-  float hi = 0.f, lo = 0.f;
-  __device__ __forceinline__ void add_prod(float a, float b) {
-    const float p = a * b;
-    const float pe = fmaf(a, b, -p);  // exact product p + pe
-    const float s = hi + p;           // TwoSum(hi, p)
-    const float bb = s - hi;
-    const float e = (hi - (s - bb)) + (p - bb);
-    hi = s;
-    lo += e + pe;
-  }
-  __device__ __forceinline__ double get() const { return double(hi) + double(lo); }
+  T v = T(0);
+  __device__ __forceinline__ void add_prod(T a, T b) { v = fma(a, b, v); }
+  __device__ __forceinline__ double get() const { return double(v); }
 };
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -299,11 +284,13 @@ __device__ __forceinline__ T group_sum(T v) {
 
 // Deterministic sum of n NPART-tuples of partials by the whole block (fixed
 // assignment of partials to threads, fixed tree); every thread receives the
-// result in out.  Launched with BLOCK threads.
+// result in out.  Launched with NT threads.
+constexpr int RED_THREADS = 1024;
+template <int NT>
 __device__ __forceinline__ void reduce_partials(const double *part, int n, double *out) {
-  __shared__ double red[BLOCK / 32][NPART];
+  __shared__ double red[NT / 32][NPART];
   double a[NPART] = {0, 0, 0, 0, 0};
-  for (int i = threadIdx.x; i < n; i += BLOCK)
+  for (int i = threadIdx.x; i < n; i += NT)
 #pragma unroll
     for (int k = 0; k < NPART; k++) a[k] += part[NPART * i + k];
 #pragma unroll
@@ -316,7 +303,7 @@ __device__ __forceinline__ void reduce_partials(const double *part, int n, doubl
   if (w == 0) {
 #pragma unroll
     for (int k = 0; k < NPART; k++) {
-      double v = l < (BLOCK >> 5) ? red[l][k] : 0.0;
+      double v = l < (NT >> 5) ? red[l][k] : 0.0;
       v = warp_sum(v);
       if (l == 0) red[0][k] = v;
     }
@@ -949,7 +936,7 @@ __global__ void __launch_bounds__(BLOCK) k_row_pass(Dev<T> D, int force) {
         a[0].add_prod(zi, az);
         a[1].add_prod(az, paz);
         a[2].add_prod(paz, api);
-        a[3].add_prod(zi, zi / Pi);
+        if (D.cr_tol) a[3].add_prod(zi, zi / Pi);
         a[4].add_prod(api, Pi * api);
       }
     }
@@ -999,7 +986,7 @@ __global__ void __launch_bounds__(BLOCK) k_row_pass(Dev<T> D, int force) {
           a[0].add_prod(zz[k], az);
           a[1].add_prod(az, paz);
           a[2].add_prod(paz, api);
-          a[3].add_prod(zz[k], zz[k] / Pi);
+          if (D.cr_tol) a[3].add_prod(zz[k], zz[k] / Pi);
           a[4].add_prod(api, Pi * api);
         }
       }
@@ -1014,15 +1001,21 @@ __global__ void __launch_bounds__(BLOCK) k_row_pass(Dev<T> D, int force) {
 
 // merit of this Newton iteration, Newton stop test, CR forcing term (1 block)
 template <typename T>
-__global__ void k_merit(Dev<T> D, int n, int force) {
+__global__ void __launch_bounds__(RED_THREADS) k_merit(Dev<T> D, int n, int force) {
   if (!force && D.fl->newton_stop) return;
-  __shared__ double smem[BLOCK / 32];
+  __shared__ double gsum[RED_THREADS / 32];
   double r4[NPART];
   double g2 = 0.0;
   const int nb = D.nblk_body_r + D.nblk_body_p;
-  for (int i = threadIdx.x; i < nb; i += BLOCK) g2 += D.part_body[i];
-  g2 = block_sum(g2, smem);
-  reduce_partials(D.part_row, D.nblk_row_pair + D.nblk_row_tet, r4);
+  for (int i = threadIdx.x; i < nb; i += RED_THREADS) g2 += D.part_body[i];
+  g2 = warp_sum(g2);
+  if ((threadIdx.x & 31) == 0) gsum[threadIdx.x >> 5] = g2;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    g2 = threadIdx.x < RED_THREADS / 32 ? gsum[threadIdx.x] : 0.0;
+    g2 = warp_sum(g2);
+  }
+  reduce_partials<RED_THREADS>(D.part_row, D.nblk_row_pair + D.nblk_row_tet, r4);
   if (threadIdx.x == 0) {
     double m = sqrt(g2 + r4[0]);
     D.sc->merit[n < 1023 ? n : 1023] = m;
@@ -1051,10 +1044,10 @@ __global__ void k_merit(Dev<T> D, int n, int force) {
 // and the update kernel applies p = z + beta p, Ap = Az + beta Ap,
 // x += alpha p, z -= alpha P Ap.
 template <typename T>
-__global__ void k_cr_scalars(Dev<T> D, int k) {
+__global__ void __launch_bounds__(RED_THREADS) k_cr_scalars(Dev<T> D, int k) {
   if (D.fl->newton_stop || D.fl->cr_stop) return;
   double r4[NPART];
-  reduce_partials(D.part_row, D.nblk_row_pair + D.nblk_row_tet, r4);
+  reduce_partials<RED_THREADS>(D.part_row, D.nblk_row_pair + D.nblk_row_tet, r4);
   if (threadIdx.x == 0) {
     const double d1 = r4[0], d2 = r4[1], d3 = r4[2], d4 = r4[3], d5 = r4[4];
     int st = 0;
