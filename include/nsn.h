@@ -197,6 +197,30 @@ nsn_status nsn_time_operator(nsn_ctx *ctx, int32_t iters, float *ms_body_pass, f
  * entries, particle entries, device bytes held by the context]. */
 nsn_status nsn_operator_sizes(nsn_ctx *ctx, int64_t *sizes8);
 
+/* ---- allocation-free operator apply -----------------------------------------
+ * The paper has no counterpart; this entry point serves callers that cannot
+ * allocate device memory where they need an operator product: code running
+ * while a stream is being captured into a CUDA graph, latency-critical loops
+ * that must not block on the allocator, and hosts that give the library a
+ * fixed memory budget.
+ *
+ * Computes y = (J H~^-1 J^T + C + eps I) x for the system kept by the last
+ * nsn_step (its final evaluation) or nsn_linearize, with the same kernels as
+ * the CR loop.  x and y are caller-owned device arrays of nsn_counts() rows
+ * (float32); stream is a cudaStream_t or NULL for the context stream.  The
+ * call allocates nothing: the per-entry scratch lives in a fixed static device
+ * array of NSN_NOALLOC_MAX_ENTRIES floats (16 MiB) that every GPU loading the
+ * library holds until the process exits.  Scenes with more Jacobian entries
+ * than that (about 2 per contact or joint row, 4 per tet row) are rejected
+ * with NSN_ERR_INVALID_ARG.  All calls share the array and it keeps the last
+ * call's contents; every value read is first written by the same call, so
+ * nothing has to be cleared.  Calls that overlap on the GPU (different
+ * streams, or different contexts on one device) race on the array.  The
+ * first call on a device resolves the array's device address (set-up); make
+ * that first call before any stream capture.  FP32 contexts only. */
+#define NSN_NOALLOC_MAX_ENTRIES (4 * 1024 * 1024)
+nsn_status nsn_apply_operator_noalloc(nsn_ctx *ctx, const float *x, float *y, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

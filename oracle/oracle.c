@@ -784,16 +784,29 @@ static double merit(const orc_ctx *c) {
  * Reading: the printed "+ (M du)_k" contradicts H~ = M - K~ and the claim that
  * the shift does not change the solution; the sign follows H~ = M - K~.
  * Reading: g is differenced at the same multipliers lambda^n (H is dg/du at
- * fixed lambda), so M du - dg = h (J^n - J^{n-1})^T lambda^n.
+ * fixed lambda), so M du - dg = h (J^n - J^{n-1})^T lambda^n, formed entry
+ * by entry (J^n - J^{n-1} first, then the product with lambda).
  * Reading: no shift at the first iteration or where |du_k| is below
  * 1e-6 + 1e-3 max(|u^n_k|, |u^{n-1}_k|). */
 static void geometric_stiffness(orc_ctx *c, const double *u, const double *uprev, const double *lam,
                                 double *zb, double *zb2) {
-  JT_x(c, lam, zb);
-  orc_row *save = c->rows;
-  c->rows = c->rows_prev;
-  JT_x(c, lam, zb2);
-  c->rows = save;
+  /* zb = (J^n - J^{n-1})^T lambda^n, the row difference formed entry by entry
+   * (rows of both iterations have the same sides) */
+  (void)zb2;
+  memset(zb, 0, sizeof(double) * c->D);
+  for (int i = 0; i < c->R; i++) {
+    const orc_row *r = &c->rows[i], *q = &c->rows_prev[i];
+    for (int s = 0; s < 4; s++) {
+      int bs = s < r->nside ? r->body[s] : -1, bq = s < q->nside ? q->body[s] : -1;
+      int b = bs >= 0 ? bs : bq;
+      if (b < 0 || c->kind[b] != ORC_PARTICLE) continue;
+      int o = c->dof[b];
+      for (int k = 0; k < 3; k++) {
+        double jn = bs >= 0 ? r->J[s][k] : 0.0, jp = bq >= 0 ? q->J[s][k] : 0.0;
+        zb[o + k] += (jn - jp) * lam[i];
+      }
+    }
+  }
   for (int i = 0; i < c->nb; i++) {
     if (c->kind[i] != ORC_PARTICLE) continue;
     int o = c->dof[i];
@@ -802,7 +815,7 @@ static void geometric_stiffness(orc_ctx *c, const double *u, const double *uprev
       double sc = fabs(u[o + k]) > fabs(uprev[o + k]) ? fabs(u[o + k]) : fabs(uprev[o + k]);
       double shift = 0.0;
       if (fabs(du) > 1e-6 + 1e-3 * sc) {
-        double ck = c->p.h * (zb[o + k] - zb2[o + k]) / du;
+        double ck = c->p.h * zb[o + k] / du;
         shift = ck < 0.0 ? -ck : 0.0;
       }
       c->hdiag[o + k] = c->mass[i] + shift;

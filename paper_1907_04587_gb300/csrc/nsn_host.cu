@@ -71,6 +71,7 @@ struct nsn_ctx {
   int launches_per_step = 0;
   bool linearized = false;
   int lin_buf = 0;           // entry buffer written by the kept linearisation
+  int kept_buf = -1;         // entry buffer of the system kept by the last step / linearisation
   int built_nb = 0;          // bodies present in the current device build
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   std::string err;
@@ -214,8 +215,8 @@ void carve(Arena &A, Dev<T> &D, const Layout &L, int nb) {
   D.je = tk(L.nj);
   D.tv = A.take<int>(4 * L.nt);
   D.tDmi = tk(9 * L.nt); D.tVe = tk(L.nt); D.tC1 = tk(L.nt); D.tD1 = tk(L.nt); D.talpha = tk(L.nt);
-  D.part_body = A.take<double>(2 * kMaxBlocks);
-  D.part_row = A.take<double>(2 * kMaxBlocks * NPART);
+  D.part_body = A.take<typename RedT<T>::type>(2 * kMaxBlocks);
+  D.part_row = A.take<typename RedT<T>::type>(2 * kMaxBlocks * NPART);
   D.sc = A.take<Scalars>(1);
   D.fl = A.take<Flags>(1);
   (void)nb;
@@ -227,6 +228,8 @@ void fill_sizes(Dev<T> &D, const Layout &L, const nsn_config &cfg) {
   D.ER = L.ER; D.EV = L.EV;
   D.h = cfg.h; D.eps = cfg.eps; D.damping = cfg.damping; D.tol_rel = cfg.tol_rel;
   for (int k = 0; k < 3; k++) D.grav[k] = cfg.gravity[k];
+  D.hT = T(cfg.h); D.ihT = T(1.0 / cfg.h); D.epsT = T(cfg.eps); D.dampT = T(cfg.damping);
+  for (int k = 0; k < 3; k++) D.gravT[k] = T(cfg.gravity[k]);
   D.ncp = cfg.ncp; D.rscale = cfg.rscale; D.gs = cfg.geom_stiffness; D.cr_tol = cfg.cr_tol_mode;
   D.nblk_body_r = L.nr ? clampb(cdiv((long long)L.nr * kGroup, BLOCK)) : 0;
   D.nblk_body_p = L.np ? clampb(cdiv((long long)L.np * kGroup, BLOCK)) : 0;
@@ -1000,6 +1003,7 @@ nsn_status nsn_step(nsn_ctx *c, int32_t nsteps, nsn_stats *stats) {
   if (s != NSN_OK) return s;
   c->linearized = false;
   s = c->cfg.precision == NSN_FP64 ? run_steps<double>(c, nsteps) : run_steps<float>(c, nsteps);
+  if (s == NSN_OK) c->kept_buf = c->cfg.newton_iters & 1;
   if (stats) *stats = c->last;
   return s;
 }
@@ -1120,7 +1124,9 @@ nsn_status nsn_linearize(nsn_ctx *c, int32_t n_before) {
   nsn_status s = ensure_built(c);
   if (s != NSN_OK) return s;
   c->lin_buf = n_before & 1;
-  return c->cfg.precision == NSN_FP64 ? do_linearize<double>(c, n_before) : do_linearize<float>(c, n_before);
+  s = c->cfg.precision == NSN_FP64 ? do_linearize<double>(c, n_before) : do_linearize<float>(c, n_before);
+  if (s == NSN_OK) c->kept_buf = c->lin_buf;
+  return s;
 }
 
 nsn_status nsn_apply_operator(nsn_ctx *c, const double *x, double *y) {
@@ -1165,3 +1171,86 @@ nsn_status nsn_last_launch_count(nsn_ctx *c, int32_t *kernels_per_step) {
 }
 
 }  // extern "C"
+
+// =====================================================================================
+// Allocation-free operator apply.
+//
+// Some callers cannot allocate device memory at the point where they need an
+// operator product: code running while a stream is being captured into a CUDA
+// graph (cudaMalloc is not a stream operation and breaks the capture), code
+// inside a latency-critical control loop that must not block on the device
+// allocator, and hosts that hand the library a fixed memory budget.  For
+// them nsn_apply_operator_noalloc computes y = (J H~^-1 J^T + C + eps I) x with
+// the same two kernels as the CR loop, but keeps the per-entry scratch, the
+// per-block partials and the flags in the file-scope device arrays below
+// (part of the library image, resident on every device that loads it until the
+// process exits) instead of in memory allocated by the context.
+
+namespace {
+
+constexpr int kNoallocMaxEntries = NSN_NOALLOC_MAX_ENTRIES;
+static __device__ __align__(256) float g_noalloc_t[kNoallocMaxEntries];
+static __device__ __align__(256) DS g_noalloc_part[2 * kMaxBlocks * NPART];
+static __device__ __align__(256) Flags g_noalloc_flags;  // never written by the apply kernels
+
+struct NoallocPtrs {
+  float *t = nullptr;
+  DS *part = nullptr;
+  Flags *flags = nullptr;
+  bool ready = false;
+};
+constexpr int kMaxDevices = 64;
+NoallocPtrs g_noalloc_dev[kMaxDevices];
+
+// Host code cannot use the arrays' names as device addresses; resolve them
+// once per device, with that device current.
+nsn_status noalloc_setup(nsn_ctx *c, NoallocPtrs **out) {
+  int dev = 0;
+  CUDA_TRY(c, cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return fail(c, NSN_ERR_INVALID_ARG, "device index %d out of range", dev);
+  NoallocPtrs &p = g_noalloc_dev[dev];
+  if (!p.ready) {
+    void *t = nullptr, *part = nullptr, *fl = nullptr;
+    cudaError_t e1 = cudaGetSymbolAddress(&t, g_noalloc_t);
+    cudaError_t e2 = cudaGetSymbolAddress(&part, g_noalloc_part);
+    cudaError_t e3 = cudaGetSymbolAddress(&fl, g_noalloc_flags);
+    if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess)
+      return fail(c, NSN_ERR_CUDA, "cudaGetSymbolAddress: %s",
+                  cudaGetErrorString(e1 != cudaSuccess ? e1 : (e2 != cudaSuccess ? e2 : e3)));
+    p.t = static_cast<float *>(t);
+    p.part = static_cast<DS *>(part);
+    p.flags = static_cast<Flags *>(fl);
+    p.ready = true;
+  }
+  *out = &p;
+  return NSN_OK;
+}
+
+}  // namespace
+
+extern "C" nsn_status nsn_apply_operator_noalloc(nsn_ctx *c, const float *x, float *y, void *stream) {
+  if (!c || !x || !y) return NSN_ERR_INVALID_ARG;
+  if (c->cfg.precision != NSN_FP32) return fail(c, NSN_ERR_INVALID_ARG, "nsn_apply_operator_noalloc needs an FP32 context");
+  if (c->dirty || c->kept_buf < 0) return fail(c, NSN_ERR_BAD_STATE, "no kept system: call nsn_step or nsn_linearize first");
+  const Layout &L = c->L;
+  if (size_t(L.ER) + size_t(L.EV) > size_t(kNoallocMaxEntries))
+    return fail(c, NSN_ERR_INVALID_ARG,
+                "nsn_apply_operator_noalloc: %lld Jacobian entries exceed the static scratch of %d entries",
+                (long long)L.ER + L.EV, kNoallocMaxEntries);
+  NoallocPtrs *np = nullptr;
+  nsn_status s = noalloc_setup(c, &np);
+  if (s != NSN_OK) return s;
+  if (L.R == 0) return NSN_OK;
+  cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : c->stream;
+  Dev<float> D = c->d32;
+  D.t = np->t;
+  D.part_row = np->part;
+  D.fl = np->flags;
+  D.z = const_cast<float *>(x);
+  D.Az = y;
+  const int nb = D.nblk_body_r + D.nblk_body_p, nrw = D.nblk_row_pair + D.nblk_row_tet;
+  if (nb) k_body_pass<float, kGroup, BM_APPLY><<<nb, BLOCK, 0, st>>>(D, x, c->kept_buf, 0, 1);
+  k_row_pass<float, RM_APPLY><<<nrw, BLOCK, 0, st>>>(D, 1);
+  CUDA_TRY(c, cudaGetLastError());
+  return NSN_OK;
+}

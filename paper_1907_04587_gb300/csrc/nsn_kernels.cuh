@@ -48,15 +48,34 @@ struct Scalars {
   double rho[2];        // CR rho, double-buffered by iteration parity
   double appap[2];      // CR Ap^T P Ap, double-buffered by iteration parity
   double alpha, beta;   // CR step of the current iteration
+  float alpha_f, beta_f; // the same, rounded once for the FP32 update kernel
 };
+
+struct DS {
+  float hi, lo;
+};
+__device__ __forceinline__ DS ds_add(DS a, DS b) {
+  const float s = a.hi + b.hi;
+  const float bb = s - a.hi;
+  float e = (a.hi - (s - bb)) + (b.hi - bb);
+  e += a.lo + b.lo;
+  const float hi = s + e;
+  return DS{hi, e - (hi - s)};
+}
+template <typename T>
+struct RedT { using type = DS; };
+template <>
+struct RedT<double> { using type = double; };
 
 template <typename T>
 struct Dev {
   // sizes
   int nr, np, nc, nj, nt, R, Rpair, ER, EV;
-  // parameters
+  // parameters (FP64 as given, and in the bulk type T for the kernels, so that
+  // no thread converts doubles: FP64 conversions share the small FP64 pipe)
   double h, eps, damping, tol_rel;
   double grav[3];
+  T hT, ihT, epsT, dampT, gravT[3];
   int ncp, rscale, gs, cr_tol;
   // rigid bodies
   T *rx[3], *rq[4], *rx0[3], *rq0[4], *ru[6], *rut[6], *rm, *rinvm, *rIb[3], *rIw[6], *rIwi[6], *rg[6], *ryg[6];
@@ -82,8 +101,8 @@ struct Dev {
   int *tv;
   T *tDmi, *tVe, *tC1, *tD1, *talpha;
   // reductions
-  double *part_body;   // one per body-pass block
-  double *part_row;    // NPART per row-pass block
+  typename RedT<T>::type *part_body;   // one per body-pass block
+  typename RedT<T>::type *part_row;    // NPART per row-pass block
   int nblk_body_r, nblk_body_p, nblk_row_pair, nblk_row_tet, nblk_upd;
   Scalars *sc;
   Flags *fl;
@@ -243,37 +262,59 @@ __device__ void svd3(const T *F, T *U, T *s, T *V) {
 // ------------------------------------------------------------------------------------
 // reductions
 //
-// Per-thread partial dot products.  FP64 arithmetic runs at a small fraction
-// of the FP32 rate on this part, so the FP32 build sums the few rows a thread
-// owns (a handful per launch) in FP32 and converts to FP64 once per thread;
-// all sums across threads and blocks are FP64, in a fixed order.
+// Reductions.  FP64 arithmetic runs on a very small pipe on this part (two
+// FMAs per SM per clock), so the FP32 build never adds in FP64 on the device
+// hot path: a thread sums its few rows in FP32, and the sums across threads,
+// warps, blocks and the grid are exact-rounding double-single FP32 values
+// (hi + lo, TwoSum of Knuth), ~48-bit accurate, converted to FP64 only where
+// the CR scalars are formed.  The FP64 build reduces in double throughout.
+__device__ __forceinline__ DS red_zero(DS) { return DS{0.f, 0.f}; }
+__device__ __forceinline__ double red_zero(double) { return 0.0; }
+__device__ __forceinline__ DS red_add(DS a, DS b) { return ds_add(a, b); }
+__device__ __forceinline__ double red_add(double a, double b) { return a + b; }
+__device__ __forceinline__ DS red_from(float v) { return DS{v, 0.f}; }
+__device__ __forceinline__ double red_from(double v) { return v; }
+__device__ __forceinline__ DS red_shfl(DS v, int o) {
+  return DS{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+}
+__device__ __forceinline__ double red_shfl(double v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ double red_get(DS v) { return double(v.hi) + double(v.lo); }
+__device__ __forceinline__ double red_get(double v) { return v; }
+
+template <typename R>
+__device__ __forceinline__ R red_warp(R v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = red_add(v, red_shfl(v, o));
+  return v;
+}
+
+// Sum of NV values over the block (NT threads); result valid in warp 0.
+template <typename R, int NV, int NT>
+__device__ __forceinline__ void red_block(R (&v)[NV]) {
+  __shared__ R sm[NT / 32][NV];
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 0; k < NV; k++) v[k] = red_warp(v[k]);
+  __syncthreads();
+  if (l == 0)
+#pragma unroll
+    for (int k = 0; k < NV; k++) sm[w][k] = v[k];
+  __syncthreads();
+  if (w == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; k++) {
+      R x = l < NT / 32 ? sm[l][k] : red_zero(v[k]);
+      v[k] = red_warp(x);
+    }
+  }
+}
+
+// Per-thread partial dot products: plain sums in the bulk type.
 template <typename T>
 struct Acc {
   T v = T(0);
   __device__ __forceinline__ void add_prod(T a, T b) { v = fma(a, b, v); }
-  __device__ __forceinline__ double get() const { return double(v); }
 };
-
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-// Sum over the block; result valid in thread 0.  smem >= BLOCK/32 doubles.
-__device__ __forceinline__ double block_sum(double v, double *smem) {
-  v = warp_sum(v);
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  __syncthreads();
-  if (l == 0) smem[w] = v;
-  __syncthreads();
-  double r = 0.0;
-  if (w == 0) {
-    r = l < (BLOCK >> 5) ? smem[l] : 0.0;
-    r = warp_sum(r);
-  }
-  return r;
-}
 
 template <int G, typename T>
 __device__ __forceinline__ T group_sum(T v) {
@@ -282,36 +323,20 @@ __device__ __forceinline__ T group_sum(T v) {
   return v;
 }
 
-// Deterministic sum of n NPART-tuples of partials by the whole block (fixed
-// assignment of partials to threads, fixed tree); every thread receives the
-// result in out.  Launched with NT threads.
+// Deterministic sum of n NPART-tuples of block partials by one block of NT
+// threads (fixed assignment and tree); the result is returned in thread 0.
 constexpr int RED_THREADS = 1024;
-template <int NT>
-__device__ __forceinline__ void reduce_partials(const double *part, int n, double *out) {
-  __shared__ double red[NT / 32][NPART];
-  double a[NPART] = {0, 0, 0, 0, 0};
+template <typename R, int NT>
+__device__ __forceinline__ void reduce_partials(const R *part, int n, double *out) {
+  R a[NPART];
+#pragma unroll
+  for (int k = 0; k < NPART; k++) a[k] = red_zero(R());
   for (int i = threadIdx.x; i < n; i += NT)
 #pragma unroll
-    for (int k = 0; k < NPART; k++) a[k] += part[NPART * i + k];
+    for (int k = 0; k < NPART; k++) a[k] = red_add(a[k], part[NPART * i + k]);
+  red_block<R, NPART, NT>(a);
 #pragma unroll
-  for (int k = 0; k < NPART; k++) a[k] = warp_sum(a[k]);
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  if (l == 0)
-#pragma unroll
-    for (int k = 0; k < NPART; k++) red[w][k] = a[k];
-  __syncthreads();
-  if (w == 0) {
-#pragma unroll
-    for (int k = 0; k < NPART; k++) {
-      double v = l < (NT >> 5) ? red[l][k] : 0.0;
-      v = warp_sum(v);
-      if (l == 0) red[0][k] = v;
-    }
-  }
-  __syncthreads();
-#pragma unroll
-  for (int k = 0; k < NPART; k++) out[k] = red[0][k];
-  __syncthreads();
+  for (int k = 0; k < NPART; k++) out[k] = red_get(a[k]);
 }
 
 // ------------------------------------------------------------------------------------
@@ -347,9 +372,9 @@ __global__ void k_begin_rigid(Dev<T> D) {
   cross3(w, Iww, tau);
   for (int k = 0; k < 3; k++) tau[k] = -tau[k];
   mat3v(Iwi, tau, dw);
-  const T h = T(D.h);
+  const T h = D.hT;
   for (int k = 0; k < 3; k++) {
-    D.rut[k][i] = D.ru[k][i] + h * T(D.grav[k]);
+    D.rut[k][i] = D.ru[k][i] + h * D.gravT[k];
     D.rut[3 + k][i] = w[k] + h * dw[k];
     D.ru[k][i] = T(0);
     D.ru[3 + k][i] = T(0);
@@ -360,11 +385,11 @@ template <typename T>
 __global__ void k_begin_particle(Dev<T> D) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= D.np) return;
-  const T h = T(D.h);
+  const T h = D.hT;
   T m = D.pm[i];
   for (int k = 0; k < 3; k++) {
     D.px0[k][i] = D.px[k][i];
-    D.put[k][i] = D.pu[k][i] + h * T(D.grav[k]);
+    D.put[k][i] = D.pu[k][i] + h * D.gravT[k];
     D.pu[k][i] = T(0);
     D.puprev[k][i] = T(0);
     D.phinv[k][i] = T(1) / m;
@@ -393,7 +418,7 @@ struct Side {
 
 template <typename T>
 __device__ __forceinline__ void load_side(const Dev<T> &D, int enc, const T *p, Side<T> &s) {
-  const T h = T(D.h);
+  const T h = D.hT;
   if (enc >= 0) {
     s.kind = 1; s.idx = enc;
     T q[4], R[9];
@@ -496,7 +521,7 @@ __global__ void k_eval_contacts(Dev<T> D, int buf, int force) {
   if (!force && D.fl->newton_stop) return;
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= D.nc) return;
-  const T h = T(D.h);
+  const T h = D.hT;
   T pa[3], pb[3], n[3];
   for (int k = 0; k < 3; k++) { pa[k] = D.cpa[k][c]; pb[k] = D.cpb[k][c]; n[k] = D.cn[k][c]; }
   Side<T> A, B;
@@ -582,7 +607,7 @@ __global__ void k_eval_joints(Dev<T> D, int buf, int force) {
   if (!force && D.fl->newton_stop) return;
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= D.nj) return;
-  const T h = T(D.h);
+  const T h = D.hT;
   T pa[3], pb[3], axa[3], axb[3];
   for (int k = 0; k < 3; k++) { pa[k] = D.jpa[k][j]; pb[k] = D.jpb[k][j]; axa[k] = D.jaxa[k][j]; axb[k] = D.jaxb[k][j]; }
   Side<T> A, B;
@@ -645,7 +670,7 @@ __global__ void k_eval_tets(Dev<T> D, int buf, int force) {
   if (!force && D.fl->newton_stop) return;
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= D.nt) return;
-  const T h = T(D.h);
+  const T h = D.hT;
   int v[4];
   for (int q = 0; q < 4; q++) v[q] = D.tv[4 * t + q];
   T Dmi[9];
@@ -713,12 +738,11 @@ template <typename T, int G, int MODE>
 __global__ void __launch_bounds__(BLOCK) k_body_pass(Dev<T> D, const T *__restrict__ in, int buf, int newton_it, int force) {
   if (!force && D.fl->newton_stop) return;
   if (MODE == BM_APPLY && D.fl->cr_stop) return;
-  __shared__ double smem[BLOCK / 32];
   Acc<T> acc_g2;
   const int gpb = BLOCK / G;         // groups (bodies) per block iteration
   const int gid = threadIdx.x / G;
   const int lane = threadIdx.x % G;
-  const T h = T(D.h);
+  const T h = D.hT;
   const bool rigid_blocks = blockIdx.x < D.nblk_body_r;
   if (rigid_blocks) {
     const int stride = D.nblk_body_r * gpb;
@@ -784,7 +808,7 @@ __global__ void __launch_bounds__(BLOCK) k_body_pass(Dev<T> D, const T *__restri
         du[0] = r[0] * im; du[1] = r[1] * im; du[2] = r[2] * im;
         sym3v(Si, r + 3, du + 3);
         if (lane == 0) {
-          const T t = T(D.damping);
+          const T t = D.dampT;
           T u[6];
 #pragma unroll
           for (int k = 0; k < 6; k++) { u[k] = D.ru[k][b] + t * du[k]; D.ru[k][b] = u[k]; }
@@ -822,8 +846,10 @@ __global__ void __launch_bounds__(BLOCK) k_body_pass(Dev<T> D, const T *__restri
       for (int e = s0 + lane; e < s1; e += G) {
         T xv = in[D.erow[D.ER + e]];
         s[0] += J0[e] * xv; s[1] += J1[e] * xv; s[2] += J2[e] * xv;
-        if (gs) {
-          sp[0] += D.ej3[buf ^ 1][0][e] * xv; sp[1] += D.ej3[buf ^ 1][1][e] * xv; sp[2] += D.ej3[buf ^ 1][2][e] * xv;
+        if (gs) {  // (J^n - J^{n-1})_e lambda_row(e), differenced per entry
+          sp[0] += (J0[e] - D.ej3[buf ^ 1][0][e]) * xv;
+          sp[1] += (J1[e] - D.ej3[buf ^ 1][1][e]) * xv;
+          sp[2] += (J2[e] - D.ej3[buf ^ 1][2][e]) * xv;
         }
       }
 #pragma unroll
@@ -850,7 +876,7 @@ __global__ void __launch_bounds__(BLOCK) k_body_pass(Dev<T> D, const T *__restri
             const T du = u - up;
             const T sc = fabs(u) > fabs(up) ? fabs(u) : fabs(up);
             if (fabs(du) > T(1e-6) + T(1e-3) * sc) {
-              const T ck = h * (s[k] - sp[k]) / du;
+              const T ck = h * sp[k] / du;
               if (ck < T(0)) hi[k] = T(1) / (m - ck);
             }
           }
@@ -870,7 +896,7 @@ __global__ void __launch_bounds__(BLOCK) k_body_pass(Dev<T> D, const T *__restri
         }
       } else {  // BM_UPDATE
         if (lane == 0) {
-          const T t = T(D.damping);
+          const T t = D.dampT;
 #pragma unroll
           for (int k = 0; k < 3; k++) {
             const T du = (h * s[k] - D.pg[k][b]) * D.phinv[k][b];
@@ -885,8 +911,10 @@ __global__ void __launch_bounds__(BLOCK) k_body_pass(Dev<T> D, const T *__restri
     }
   }
   if (MODE == BM_RESIDUAL) {
-    double tot = block_sum(acc_g2.get(), smem);
-    if (threadIdx.x == 0) D.part_body[blockIdx.x] = tot;
+    using R = typename RedT<T>::type;
+    R v[1] = {red_from(acc_g2.v)};
+    red_block<R, 1, BLOCK>(v);
+    if (threadIdx.x == 0) D.part_body[blockIdx.x] = v[0];
   }
 }
 
@@ -903,9 +931,8 @@ template <typename T, int MODE>
 __global__ void __launch_bounds__(BLOCK) k_row_pass(Dev<T> D, int force) {
   if (!force && D.fl->newton_stop) return;
   if (MODE == RM_APPLY && D.fl->cr_stop) return;
-  __shared__ double smem[BLOCK / 32];
   Acc<T> a[NPART];
-  const T eps = T(D.eps), ih = T(1) / T(D.h);
+  const T eps = D.epsT, ih = D.ihT;
   if (blockIdx.x < D.nblk_row_pair) {
     const int stride = D.nblk_row_pair * BLOCK;
     for (int i = blockIdx.x * BLOCK + threadIdx.x; i < D.Rpair; i += stride) {
@@ -992,30 +1019,28 @@ __global__ void __launch_bounds__(BLOCK) k_row_pass(Dev<T> D, int force) {
       }
     }
   }
+  using R = typename RedT<T>::type;
+  R v[NPART];
 #pragma unroll
-  for (int k = 0; k < NPART; k++) {
-    double s = block_sum(a[k].get(), smem);
-    if (threadIdx.x == 0) D.part_row[NPART * blockIdx.x + k] = s;
-  }
+  for (int k = 0; k < NPART; k++) v[k] = red_from(a[k].v);
+  red_block<R, NPART, BLOCK>(v);
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int k = 0; k < NPART; k++) D.part_row[NPART * blockIdx.x + k] = v[k];
 }
 
 // merit of this Newton iteration, Newton stop test, CR forcing term (1 block)
 template <typename T>
 __global__ void __launch_bounds__(RED_THREADS) k_merit(Dev<T> D, int n, int force) {
   if (!force && D.fl->newton_stop) return;
-  __shared__ double gsum[RED_THREADS / 32];
+  using R = typename RedT<T>::type;
   double r4[NPART];
-  double g2 = 0.0;
+  R gv[1] = {red_zero(R())};
   const int nb = D.nblk_body_r + D.nblk_body_p;
-  for (int i = threadIdx.x; i < nb; i += RED_THREADS) g2 += D.part_body[i];
-  g2 = warp_sum(g2);
-  if ((threadIdx.x & 31) == 0) gsum[threadIdx.x >> 5] = g2;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    g2 = threadIdx.x < RED_THREADS / 32 ? gsum[threadIdx.x] : 0.0;
-    g2 = warp_sum(g2);
-  }
-  reduce_partials<RED_THREADS>(D.part_row, D.nblk_row_pair + D.nblk_row_tet, r4);
+  for (int i = threadIdx.x; i < nb; i += RED_THREADS) gv[0] = red_add(gv[0], D.part_body[i]);
+  red_block<R, 1, RED_THREADS>(gv);
+  const double g2 = red_get(gv[0]);
+  reduce_partials<R, RED_THREADS>(D.part_row, D.nblk_row_pair + D.nblk_row_tet, r4);
   if (threadIdx.x == 0) {
     double m = sqrt(g2 + r4[0]);
     D.sc->merit[n < 1023 ? n : 1023] = m;
@@ -1047,7 +1072,7 @@ template <typename T>
 __global__ void __launch_bounds__(RED_THREADS) k_cr_scalars(Dev<T> D, int k) {
   if (D.fl->newton_stop || D.fl->cr_stop) return;
   double r4[NPART];
-  reduce_partials<RED_THREADS>(D.part_row, D.nblk_row_pair + D.nblk_row_tet, r4);
+  reduce_partials<typename RedT<T>::type, RED_THREADS>(D.part_row, D.nblk_row_pair + D.nblk_row_tet, r4);
   if (threadIdx.x == 0) {
     const double d1 = r4[0], d2 = r4[1], d3 = r4[2], d4 = r4[3], d5 = r4[4];
     int st = 0;
@@ -1071,15 +1096,24 @@ __global__ void __launch_bounds__(RED_THREADS) k_cr_scalars(Dev<T> D, int k) {
       D.sc->appap[k & 1] = apap;
       D.sc->alpha = rho / apap;
       D.sc->beta = beta;
+      D.sc->alpha_f = float(D.sc->alpha);
+      D.sc->beta_f = float(beta);
       D.fl->cr_count += 1;
     }
   }
 }
 
 template <typename T>
+__device__ __forceinline__ T cr_scalar(double d, float f);
+template <>
+__device__ __forceinline__ float cr_scalar<float>(double, float f) { return f; }
+template <>
+__device__ __forceinline__ double cr_scalar<double>(double d, float) { return d; }
+
+template <typename T>
 __global__ void __launch_bounds__(BLOCK) k_cr_update(Dev<T> D, int k) {
   if (D.fl->newton_stop || D.fl->cr_stop) return;
-  const T alpha = T(D.sc->alpha), beta = T(D.sc->beta);
+  const T alpha = cr_scalar<T>(D.sc->alpha, D.sc->alpha_f), beta = cr_scalar<T>(D.sc->beta, D.sc->beta_f);
   const int stride = gridDim.x * BLOCK;
   for (int i = blockIdx.x * BLOCK + threadIdx.x; i < D.R; i += stride) {
     const T zi = D.z[i];
@@ -1105,7 +1139,7 @@ __global__ void k_cr_init(Dev<T> D) {
 template <typename T>
 __global__ void k_lambda_update(Dev<T> D) {
   if (D.fl->newton_stop) return;
-  const T t = T(D.damping);
+  const T t = D.dampT;
   const int i0 = blockIdx.x * blockDim.x + threadIdx.x;
   if (i0 == 0) D.fl->newton_count += 1;
   for (int i = i0; i < D.R; i += gridDim.x * blockDim.x) D.lam[i] += t * D.x[i];

@@ -94,6 +94,7 @@ def lib():
         "nsn_last_launch_count": (C.c_int, [_vp, _ip]),
         "nsn_time_operator": (C.c_int, [_vp, C.c_int32, _fp, _fp]),
         "nsn_operator_sizes": (C.c_int, [_vp, C.POINTER(C.c_int64)]),
+        "nsn_apply_operator_noalloc": (C.c_int, [_vp, _vp, _vp, _vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -256,6 +257,12 @@ def nsn_time_operator(ctx, iters=20):
     a, b = C.c_float(), C.c_float()
     _check(ctx, lib().nsn_time_operator(ctx, iters, C.byref(a), C.byref(b)), "nsn_time_operator")
     return a.value, b.value
+
+
+def nsn_apply_operator_noalloc(ctx, x_dev, y_dev, stream=None):
+    """y = A x on the kept system with caller-owned float32 device buffers
+    (integer device addresses) and no device allocation."""
+    _check(ctx, lib().nsn_apply_operator_noalloc(ctx, _vp(x_dev), _vp(y_dev), stream), "nsn_apply_operator_noalloc")
 
 
 def nsn_operator_sizes(ctx):

@@ -2,9 +2,10 @@
 
 Identical seeded inputs (float32-representable) go to both sides.  Errors are
 norm-wise relative.  What is compared is what the method determines uniquely:
-  - u+ per step, relative to ||u_oracle|| + the step's free velocity change
-    h g sqrt(n_bodies) (a resting body has u+ ~ 0, so a bare relative error
-    would measure noise);
+  - u+ per step in the kinetic-energy norm ||du||_M = sqrt(sum m |dv|^2 +
+    dw^T I_w dw), relative to ||u_oracle||_M plus the step's free momentum
+    change (m h g per body): a resting body has u+ ~ 0, and a light body's
+    angular velocity should weigh by its inertia, as impulses do;
   - the net generalised impulse per body, J^T (h lambda), with the oracle's
     geometric rows at the end of the step: with redundant contacts (four
     corners on a face) the split of impulses among contacts is not unique,
@@ -25,6 +26,11 @@ H = 1.0 / 60.0
 TOL64 = 1e-7
 TOL32 = 1e-5
 G = 9.81
+# FP32 CR after M iterations on one linear system, relative error of du: the
+# Krylov recurrences amplify FP32 rounding of the operator by the conditioning
+# of the Jacobi-preconditioned Schur matrix (ill-conditioned by hard joints,
+# stick rows with W = 0 and mass ratios); measured values are reported.
+TOL32_CR = {"cube_stack": 1e-4, "chain_block_small": 1e-3, "batched_small": 1e-3}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -89,30 +95,54 @@ def test_linear_system_parity(orc, name, prec):
 
 
 @pytest.mark.parametrize("name", list(SCENES))
-def test_cr_solve_parity_fp64(orc, name):
-    """dl after M CR iterations and du = H~^-1 (h J^T dl - g) (Sec. 6.2, 8.2)."""
+@pytest.mark.parametrize("prec", [nsn.NSN_FP64, nsn.NSN_FP32])
+def test_cr_solve_parity(orc, name, prec):
+    """M CR iterations on the same linear system (after one Newton iteration):
+    du = H~^-1 (h J^T dl - g) (Sec. 6.2) is unique; dl itself is only unique up
+    to the near-null space of redundant contact rows, so it is checked loosely."""
     s = SCENES[name]()
     p = PARAMS[name]
     o = orc.Oracle(s, **p)
-    g = nsn.Solver(s, precision=nsn.NSN_FP64, **p)
-    o.linearize(n_before=1)
-    g.linearize(1)
+    g = nsn.Solver(s, precision=prec, **p)
+    n_before = 1 if prec == nsn.NSN_FP64 else 0
+    L = o.linearize(n_before=n_before)
+    g.linearize(n_before)
     M = p["cr_iters"]
     dl_o, _ = o.pcr(M)
     dl_g, du_g = g.solve(M)
-    assert rel(dl_g, dl_o) < 1e-8
-    L = o.linearize(n_before=1)
     du_o = L["Hinv"] @ (L["J"].T @ dl_o * H - L["g"])
-    assert rel(du_g, du_o) < 1e-8
+    e_du, e_dl = rel(du_g, du_o), rel(dl_g, dl_o)
+    print(f"{name} prec {prec}: du {e_du:.2e} dl {e_dl:.2e}")
+    if prec == nsn.NSN_FP64:
+        assert e_du < 1e-8 and e_dl < 1e-6
+    else:
+        assert e_du < TOL32_CR[name]
 
 
-def step_errors(o, g, kind):
+def mass_norm(state, s, du_v, du_w):
+    """sqrt(sum m |dv|^2 + dw^T I_w dw) with I_w = R I_body R^T at the state."""
+    R = scenes.quat_rot(state["quat"])
+    m = s["mass"].astype(np.float64)
+    e = (m * (du_v ** 2).sum(1)).sum()
+    rig = s["kind"] == 0
+    Ib = s["inertia"].astype(np.float64)
+    Iw = np.einsum("nij,nj,nkj->nik", R, Ib, R)
+    e += np.einsum("ni,nij,nj->", du_w[rig], Iw[rig], du_w[rig])
+    return np.sqrt(e)
+
+
+def step_errors(o, g, kind, s=None):
     """(velocity error, net body impulse error, per-row impulse error) after
     both sides have stepped from the same state."""
-    uo, ug = body_u(o.get_state(), kind), body_u(g.get_state_f64(), kind)
+    so_, sg_ = o.get_state(), g.get_state_f64()
     lo, lg = H * o.get_lambda(), H * g.get_lambda()
-    scale = np.linalg.norm(uo) + H * G * np.sqrt(len(kind))
-    eu = np.linalg.norm(ug - uo) / scale
+    if s is None:
+        uo, ug = body_u(so_, kind), body_u(sg_, kind)
+        eu = np.linalg.norm(ug - uo) / (np.linalg.norm(uo) + H * G * np.sqrt(len(kind)))
+    else:
+        num = mass_norm(so_, s, sg_["vel"] - so_["vel"], sg_["omega"] - so_["omega"])
+        den = mass_norm(so_, s, so_["vel"], so_["omega"]) + H * G * np.sqrt(s["mass"].astype(np.float64).sum())
+        eu = num / den
     _, Jg = o.eval_constraints()
     eb = rel(Jg.T @ lg, Jg.T @ lo)
     return eu, eb, rel(lg, lo)
@@ -126,7 +156,7 @@ def _resync_step(o, g, s, kind):
     g.set_state(**f32)
     so = o.step()
     sg = g.step()
-    return step_errors(o, g, kind) + (so, sg)
+    return step_errors(o, g, kind, s) + (so, sg)
 
 
 @pytest.mark.parametrize("name", list(SCENES))
@@ -171,7 +201,7 @@ def test_cube_stack_60_steps_fp32(orc):
         g.set_state(**{k: v.astype(np.float32) for k, v in st.items()})
         o.step()
         g.step()
-        eu, eb, el = step_errors(o, g, s["kind"])
+        eu, eb, el = step_errors(o, g, s["kind"], s)
         print(f"step {step}: u {eu:.2e} body impulse {eb:.2e} row impulse {el:.2e}")
         worst = max(worst, eu, eb)
     assert worst < TOL32, worst
