@@ -786,8 +786,11 @@ static double merit(const orc_ctx *c) {
  * Reading: g is differenced at the same multipliers lambda^n (H is dg/du at
  * fixed lambda), so M du - dg = h (J^n - J^{n-1})^T lambda^n, formed entry
  * by entry (J^n - J^{n-1} first, then the product with lambda).
- * Reading: no shift at the first iteration or where |du_k| is below
- * 1e-6 + 1e-3 max(|u^n_k|, |u^{n-1}_k|). */
+ * Reading: no shift at the first iteration; the secant ratio s_k / du_k is
+ * evaluated in the Tikhonov-regularised form s_k du_k / (du_k^2 + tau_k^2),
+ * tau_k = 1e-6 + 1e-3 max(|u^n_k|, |u^{n-1}_k|), which equals the printed ratio
+ * for |du_k| >> tau_k and goes to zero continuously as du_k -> 0 (a hard
+ * cut-off would make H~ jump on rounding-level changes of du). */
 static void geometric_stiffness(orc_ctx *c, const double *u, const double *uprev, const double *lam,
                                 double *zb, double *zb2) {
   /* zb = (J^n - J^{n-1})^T lambda^n, the row difference formed entry by entry
@@ -813,11 +816,9 @@ static void geometric_stiffness(orc_ctx *c, const double *u, const double *uprev
     for (int k = 0; k < 3; k++) {
       double du = u[o + k] - uprev[o + k];
       double sc = fabs(u[o + k]) > fabs(uprev[o + k]) ? fabs(u[o + k]) : fabs(uprev[o + k]);
-      double shift = 0.0;
-      if (fabs(du) > 1e-6 + 1e-3 * sc) {
-        double ck = c->p.h * zb[o + k] / du;
-        shift = ck < 0.0 ? -ck : 0.0;
-      }
+      double tau = 1e-6 + 1e-3 * sc;
+      double ck = c->p.h * zb[o + k] * du / (du * du + tau * tau);
+      double shift = ck < 0.0 ? -ck : 0.0;
       c->hdiag[o + k] = c->mass[i] + shift;
     }
   }

@@ -871,14 +871,14 @@ __global__ void __launch_bounds__(BLOCK) k_body_pass(Dev<T> D, const T *__restri
           g[k] = m * (u - D.put[k][b]) - h * s[k];
           hi[k] = T(1) / m;
           if (gs) {
-            // c_k = h [(J^n - J^{n-1})^T lambda^n]_k / du_k,  H~_kk = m + max(0, -c_k)
+            // c_k = h [(J^n - J^{n-1})^T lambda^n]_k du_k / (du_k^2 + tau_k^2)
+            // (regularised secant), H~_kk = m + max(0, -c_k)
             const T up = D.puprev[k][b];
             const T du = u - up;
             const T sc = fabs(u) > fabs(up) ? fabs(u) : fabs(up);
-            if (fabs(du) > T(1e-6) + T(1e-3) * sc) {
-              const T ck = h * sp[k] / du;
-              if (ck < T(0)) hi[k] = T(1) / (m - ck);
-            }
+            const T tau = T(1e-6) + T(1e-3) * sc;
+            const T ck = h * sp[k] * du / (du * du + tau * tau);
+            if (ck < T(0)) hi[k] = T(1) / (m - ck);
           }
           y[k] = g[k] * hi[k];
         }
