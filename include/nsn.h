@@ -210,12 +210,13 @@ nsn_status nsn_operator_sizes(nsn_ctx *ctx, int64_t *sizes8);
  * (float32); stream is a cudaStream_t or NULL for the context stream.  The
  * call allocates nothing: the per-entry scratch lives in a fixed static device
  * array of NSN_NOALLOC_MAX_ENTRIES floats (16 MiB) that every GPU loading the
- * library holds until the process exits.  Scenes with more Jacobian entries
- * than that (about 2 per contact or joint row, 4 per tet row) are rejected
- * with NSN_ERR_INVALID_ARG.  All calls share the array and it keeps the last
- * call's contents; every value read is first written by the same call, so
- * nothing has to be cleared.  Calls that overlap on the GPU (different
- * streams, or different contexts on one device) race on the array.  The
+ * library holds until the process exits.  Scenes needing more row slots than
+ * that (2 per contact or joint row, 4 per tet row) are rejected with
+ * NSN_ERR_INVALID_ARG.  All calls share the array and it keeps the last call's
+ * contents; each call first clears the slots it uses (the world side of a
+ * contact is read as zero), with a memset on the stream, which allocates
+ * nothing.  Calls that overlap on the GPU (different streams, or different
+ * contexts on one device) race on the array.  The
  * first call on a device resolves the array's device address (set-up); make
  * that first call before any stream capture.  FP32 contexts only. */
 #define NSN_NOALLOC_MAX_ENTRIES (4 * 1024 * 1024)

@@ -48,7 +48,7 @@ struct Layout {
   int nr = 0, np = 0, nc = 0, nj = 0, nt = 0, R = 0, Rpair = 0, ER = 0, EV = 0;
   std::vector<int> bmap;            // ABI body id -> encoded (>=0 rigid, <=-2 particle)
   std::vector<int> rig_of, par_of;  // local index -> ABI id
-  std::vector<int> erow, rseg, vseg, re0, re1, te;
+  std::vector<int> eslot, rseg, vseg, re0, re1, te;
 };
 
 }  // namespace
@@ -157,7 +157,7 @@ nsn_status build_layout(nsn_ctx *c) {
   L.vseg = pcnt;
   L.ER = rcnt[L.nr];
   L.EV = pcnt[L.np];
-  L.erow.assign(size_t(L.ER) + L.EV, 0);
+  L.eslot.assign(size_t(L.ER) + L.EV, 0);
   L.re0.assign(L.Rpair, -1);
   L.re1.assign(L.Rpair, -1);
   L.te.assign(size_t(12) * L.nt, -1);
@@ -167,12 +167,13 @@ nsn_status build_layout(nsn_ctx *c) {
     int e;
     if (s.enc >= 0) e = rfill[s.enc]++;
     else e = L.ER + pfill[-s.enc - 2]++;
-    L.erow[e] = s.row;
     if (s.row < L.Rpair) {
       (s.slot == 0 ? L.re0 : L.re1)[s.row] = e;
+      L.eslot[e] = 2 * s.row + s.slot;
     } else {
       int t = (s.row - L.Rpair) / 3, k = (s.row - L.Rpair) % 3;
       L.te[12 * t + 4 * k + s.slot] = e;
+      L.eslot[e] = 2 * L.Rpair + 12 * t + 4 * k + s.slot;
     }
   }
   return NSN_OK;
@@ -193,14 +194,14 @@ void carve(Arena &A, Dev<T> &D, const Layout &L, int nb) {
     D.phinv[k] = tk(L.np); D.pg[k] = tk(L.np); D.pyg[k] = tk(L.np); D.puprev[k] = tk(L.np);
   }
   D.pm = tk(L.np);
-  D.erow = A.take<int>(size_t(L.ER) + L.EV);
+  D.eslot = A.take<int>(size_t(L.ER) + L.EV);
   D.rseg = A.take<int>(L.nr + 1);
   D.vseg = A.take<int>(L.np + 1);
   for (int k = 0; k < 6; k++) D.ej6[k] = tk(L.ER);
   for (int b = 0; b < 2; b++)
     for (int k = 0; k < 3; k++) D.ej3[b][k] = tk(L.EV);
-  D.t = tk(L.ER + L.EV);
-  D.t2 = tk(L.ER + L.EV);
+  D.t = tk(2 * L.Rpair + 12 * L.nt);
+  D.t2 = tk(2 * L.Rpair + 12 * L.nt);
   D.re0 = A.take<int>(L.Rpair);
   D.re1 = A.take<int>(L.Rpair);
   D.te = A.take<int>(size_t(12) * L.nt);
@@ -269,7 +270,10 @@ nsn_status upload(nsn_ctx *c, Dev<T> &D) {
     for (int i = 0; i < L.np; i++) pm[i] = T(S.mass[L.par_of[i]]);
     CUDA_TRY(c, put(D.pm, pm));
   }
-  CUDA_TRY(c, puti(D.erow, L.erow));
+  CUDA_TRY(c, puti(D.eslot, L.eslot));
+  // slots of world sides are never written and must read as zero
+  CUDA_TRY(c, cudaMemsetAsync(D.t, 0, sizeof(T) * std::max(2 * L.Rpair + 12 * L.nt, 1), st));
+  CUDA_TRY(c, cudaMemsetAsync(D.t2, 0, sizeof(T) * std::max(2 * L.Rpair + 12 * L.nt, 1), st));
   CUDA_TRY(c, puti(D.rseg, L.rseg));
   CUDA_TRY(c, puti(D.vseg, L.vseg));
   CUDA_TRY(c, puti(D.re0, L.re0));
@@ -715,7 +719,8 @@ nsn_status do_solve(nsn_ctx *c, int iters, double *dl, double *du) {
     // per body into the per-entry scratch is not body-ordered, so do it on the host.
     const Layout &L = c->L;
     const int nb = int(c->scene.kind.size());
-    std::vector<double> x(D.R), erowJ;
+    std::vector<double> x(D.R);
+    auto row_of = [&](int slot) { return slot < 2 * L.Rpair ? slot / 2 : L.Rpair + (slot - 2 * L.Rpair) / 4; };
     if (D.R) { nsn_status s = copy_out<T>(c, D.x, D.R, x.data()); if (s) return s; }
     std::vector<T> J6(size_t(6) * L.ER), J3(size_t(3) * L.EV);
     std::vector<T> g6(size_t(6) * L.nr), g3(size_t(3) * L.np), Iwi(size_t(6) * L.nr), hinv(size_t(3) * L.np), im(L.nr);
@@ -745,7 +750,7 @@ nsn_status do_solve(nsn_ctx *c, int iters, double *dl, double *du) {
       if (e >= 0) {
         double s[6] = {0, 0, 0, 0, 0, 0};
         for (int q = L.rseg[e]; q < L.rseg[e + 1]; q++)
-          for (int k = 0; k < 6; k++) s[k] += double(J6[size_t(k) * L.ER + q]) * x[L.erow[q]];
+          for (int k = 0; k < 6; k++) s[k] += double(J6[size_t(k) * L.ER + q]) * x[row_of(L.eslot[q])];
         double r[6];
         for (int k = 0; k < 6; k++) r[k] = h * s[k] - double(g6[size_t(k) * L.nr + e]);
         const T *S6 = nullptr;
@@ -761,7 +766,7 @@ nsn_status do_solve(nsn_ctx *c, int iters, double *dl, double *du) {
         int p = -e - 2;
         double s[3] = {0, 0, 0};
         for (int q = L.vseg[p]; q < L.vseg[p + 1]; q++)
-          for (int k = 0; k < 3; k++) s[k] += double(J3[size_t(k) * L.EV + q]) * x[L.erow[L.ER + q]];
+          for (int k = 0; k < 3; k++) s[k] += double(J3[size_t(k) * L.EV + q]) * x[row_of(L.eslot[L.ER + q])];
         for (int k = 0; k < 3; k++)
           du[off + k] = (h * s[k] - double(g3[size_t(k) * L.np + p])) * double(hinv[size_t(k) * L.np + p]);
         off += 3;
@@ -1233,10 +1238,12 @@ extern "C" nsn_status nsn_apply_operator_noalloc(nsn_ctx *c, const float *x, flo
   if (c->cfg.precision != NSN_FP32) return fail(c, NSN_ERR_INVALID_ARG, "nsn_apply_operator_noalloc needs an FP32 context");
   if (c->dirty || c->kept_buf < 0) return fail(c, NSN_ERR_BAD_STATE, "no kept system: call nsn_step or nsn_linearize first");
   const Layout &L = c->L;
-  if (size_t(L.ER) + size_t(L.EV) > size_t(kNoallocMaxEntries))
+  const size_t nslots = size_t(2) * L.Rpair + size_t(12) * L.nt;
+  if (nslots > size_t(kNoallocMaxEntries))
     return fail(c, NSN_ERR_INVALID_ARG,
-                "nsn_apply_operator_noalloc: %lld Jacobian entries exceed the static scratch of %d entries",
-                (long long)L.ER + L.EV, kNoallocMaxEntries);
+                "nsn_apply_operator_noalloc: %lld row slots (2 per contact or joint row, 4 per tet row) exceed the "
+                "static scratch of %d",
+                (long long)nslots, kNoallocMaxEntries);
   NoallocPtrs *np = nullptr;
   nsn_status s = noalloc_setup(c, &np);
   if (s != NSN_OK) return s;
@@ -1248,6 +1255,8 @@ extern "C" nsn_status nsn_apply_operator_noalloc(nsn_ctx *c, const float *x, flo
   D.fl = np->flags;
   D.z = const_cast<float *>(x);
   D.Az = y;
+  // world-side slots are read but never written: clear the shared scratch
+  CUDA_TRY(c, cudaMemsetAsync(np->t, 0, sizeof(float) * nslots, st));
   const int nb = D.nblk_body_r + D.nblk_body_p, nrw = D.nblk_row_pair + D.nblk_row_tet;
   if (nb) k_body_pass<float, kGroup, BM_APPLY><<<nb, BLOCK, 0, st>>>(D, x, c->kept_buf, 0, 1);
   k_row_pass<float, RM_APPLY><<<nrw, BLOCK, 0, st>>>(D, 1);

@@ -5,8 +5,9 @@
 //                  Iw[6] Iwi[6] (symmetric xx yy zz xy xz yz) g[6] yg[6]
 //   particles      x[3] x0[3] u[3] ut[3] m hinv[3] (H~^-1 diagonal) g[3] yg[3] uprev[3]
 //   entries        one per (row, side): rigid entries [0, ER) sorted by body,
-//                  particle entries [ER, ER+EV) sorted by particle; erow[e]
-//                  is the row, ej6[6][ER] / ej3[2][3][EV] the Jacobian values
+//                  particle entries [ER, ER+EV) sorted by particle; eslot[e]
+//                  is the row-ordered slot of the entry's output (its row
+//                  follows from it), ej6[6][ER] / ej3[2][3][EV] the Jacobian values
 //                  (particle values double-buffered by Newton iteration for
 //                  the geometric stiffness), rseg / vseg the segment offsets.
 //   rows           pair rows (contacts, joints) carry entry ids re0/re1
@@ -14,8 +15,8 @@
 //
 // Every operator apply is two passes with no global atomics:
 //   body pass : per body segment  s = sum_e J_e x[row(e)],  y = H~^-1 s,
-//               then per entry    t[e] = J_e . y
-//   row pass  : per row           w_i = sum_{e in row i} t[e] + (C x)_i + eps x_i
+//               then per entry    t[slot(e)] = J_e . y
+//   row pass  : per row           w_i = sum of row i's slots + (C x)_i + eps x_i
 // CR dot products are fused into the row pass as per-block partials (FP32
 // within a thread's few rows, FP64 across threads); one small kernel reduces
 // them in a fixed order and forms the FP64 CR scalars.
@@ -82,7 +83,7 @@ struct Dev {
   // particles
   T *px[3], *px0[3], *pu[3], *put[3], *pm, *phinv[3], *pg[3], *pyg[3], *puprev[3];
   // entries
-  int *erow;
+  int *eslot;        // row-ordered output slot of each entry (see slot_row)
   int *rseg, *vseg;
   T *ej6[6];
   T *ej3[2][3];
@@ -726,36 +727,70 @@ __global__ void k_eval_tets(Dev<T> D, int buf, int force) {
 
 // ------------------------------------------------------------------------------------
 // body pass (K4, K6a, K8a): one group of G lanes per body segment
+//
+// Per-entry outputs go to row-ordered slots: pair row i, side s -> 2 i + s;
+// tet t, stretch row k, vertex q -> 2 Rpair + 12 t + 4 k + q.  The row pass
+// then reads each row's slots contiguously (world sides keep zeros).
+__device__ __forceinline__ int slot_row(int slot, int Rpair) {
+  return slot < 2 * Rpair ? (slot >> 1) : Rpair + ((slot - 2 * Rpair) >> 2);
+}
 
 // MODE BM_RESIDUAL: in = lambda.  g = M~ (u - u~) - h J^T lambda; particle
-//   geometric stiffness (Sec. 8.3, particles only) from the previous Newton
-//   iteration's entries; yg = H~^-1 g; t[e] = J_e yg, t2[e] = J_e H~^-1 J_e^T;
-//   FP64 partial of |g|^2.
-// MODE BM_APPLY: in = z.  y = H~^-1 J^T z; t[e] = J_e y.
+//   geometric stiffness (Sec. 8.3, particles only) from the per-entry
+//   difference of this and the previous Newton iteration's entries;
+//   yg = H~^-1 g; t[slot] = J_e yg, t2[slot] = J_e H~^-1 J_e^T; partial |g|^2.
+// MODE BM_APPLY: in = z.  y = H~^-1 J^T z; t[slot] = J_e y.
 // MODE BM_UPDATE: in = dl.  du = H~^-1 (h J^T dl - g); u += t du; positions
 //   q = q^- + h G(q^-) u with quaternion normalisation.
+// The first KR entries of each lane stay in registers between the J^T x
+// gather and the per-entry write, so J is read once; longer segments loop.
 template <typename T, int G, int MODE>
 __global__ void __launch_bounds__(BLOCK) k_body_pass(Dev<T> D, const T *__restrict__ in, int buf, int newton_it, int force) {
   if (!force && D.fl->newton_stop) return;
   if (MODE == BM_APPLY && D.fl->cr_stop) return;
+  constexpr int KR = 3;
   Acc<T> acc_g2;
   const int gpb = BLOCK / G;         // groups (bodies) per block iteration
   const int gid = threadIdx.x / G;
   const int lane = threadIdx.x % G;
   const T h = D.hT;
-  const bool rigid_blocks = blockIdx.x < D.nblk_body_r;
-  if (rigid_blocks) {
+  const int Rp = D.Rpair;
+  if (blockIdx.x < D.nblk_body_r) {
     const int stride = D.nblk_body_r * gpb;
     for (int b0 = blockIdx.x * gpb; b0 < D.nr; b0 += stride) {
       const int b = b0 + gid;
       const bool act = b < D.nr;
       int s0 = 0, s1 = 0;
       if (act) { s0 = D.rseg[b]; s1 = D.rseg[b + 1]; }
-      T s[6] = {0, 0, 0, 0, 0, 0};
-      for (int e = s0 + lane; e < s1; e += G) {
-        T xv = in[D.erow[e]];
+      int sl[KR];
 #pragma unroll
-        for (int k = 0; k < 6; k++) s[k] += D.ej6[k][e] * xv;
+      for (int r = 0; r < KR; r++) {
+        const int e = s0 + lane + r * G;
+        sl[r] = e < s1 ? D.eslot[e] : -1;
+      }
+      T J[KR][6], xv[KR];
+#pragma unroll
+      for (int r = 0; r < KR; r++) {
+        const int e = s0 + lane + r * G;
+        if (sl[r] >= 0) {
+#pragma unroll
+          for (int k = 0; k < 6; k++) J[r][k] = D.ej6[k][e];
+          xv[r] = in[slot_row(sl[r], Rp)];
+        } else {
+#pragma unroll
+          for (int k = 0; k < 6; k++) J[r][k] = T(0);
+          xv[r] = T(0);
+        }
+      }
+      T s[6] = {0, 0, 0, 0, 0, 0};
+#pragma unroll
+      for (int r = 0; r < KR; r++)
+#pragma unroll
+        for (int k = 0; k < 6; k++) s[k] += J[r][k] * xv[r];
+      for (int e = s0 + lane + KR * G; e < s1; e += G) {
+        const T x = in[slot_row(D.eslot[e], Rp)];
+#pragma unroll
+        for (int k = 0; k < 6; k++) s[k] += D.ej6[k][e] * x;
       }
 #pragma unroll
       for (int k = 0; k < 6; k++) s[k] = group_sum<G>(s[k]);
@@ -764,49 +799,12 @@ __global__ void __launch_bounds__(BLOCK) k_body_pass(Dev<T> D, const T *__restri
 #pragma unroll
       for (int k = 0; k < 6; k++) Si[k] = D.rIwi[k][b];
       const T im = D.rinvm[b];
-      if (MODE == BM_APPLY) {
-        T y[6];
-        y[0] = s[0] * im; y[1] = s[1] * im; y[2] = s[2] * im;
-        sym3v(Si, s + 3, y + 3);
-        for (int e = s0 + lane; e < s1; e += G) {
-          T acc = 0;
+      if (MODE == BM_UPDATE) {
+        T r6[6], du[6];
 #pragma unroll
-          for (int k = 0; k < 6; k++) acc += D.ej6[k][e] * y[k];
-          D.t[e] = acc;
-        }
-      } else if (MODE == BM_RESIDUAL) {
-        T g[6], du[6], Iw[6];
-#pragma unroll
-        for (int k = 0; k < 6; k++) { du[k] = D.ru[k][b] - D.rut[k][b]; Iw[k] = D.rIw[k][b]; }
-        const T m = D.rm[b];
-        g[0] = m * du[0] - h * s[0]; g[1] = m * du[1] - h * s[1]; g[2] = m * du[2] - h * s[2];
-        T ia[3];
-        sym3v(Iw, du + 3, ia);
-        g[3] = ia[0] - h * s[3]; g[4] = ia[1] - h * s[4]; g[5] = ia[2] - h * s[5];
-        T y[6];
-        y[0] = g[0] * im; y[1] = g[1] * im; y[2] = g[2] * im;
-        sym3v(Si, g + 3, y + 3);
-        if (lane == 0) {
-#pragma unroll
-          for (int k = 0; k < 6; k++) { D.rg[k][b] = g[k]; D.ryg[k][b] = y[k]; acc_g2.add_prod(g[k], g[k]); }
-        }
-        for (int e = s0 + lane; e < s1; e += G) {
-          T J[6], tj[3];
-#pragma unroll
-          for (int k = 0; k < 6; k++) J[k] = D.ej6[k][e];
-          T acc = 0;
-#pragma unroll
-          for (int k = 0; k < 6; k++) acc += J[k] * y[k];
-          D.t[e] = acc;
-          sym3v(Si, J + 3, tj);
-          D.t2[e] = (J[0] * J[0] + J[1] * J[1] + J[2] * J[2]) * im + dot3(J + 3, tj);
-        }
-      } else {  // BM_UPDATE
-        T r[6], du[6];
-#pragma unroll
-        for (int k = 0; k < 6; k++) r[k] = h * s[k] - D.rg[k][b];
-        du[0] = r[0] * im; du[1] = r[1] * im; du[2] = r[2] * im;
-        sym3v(Si, r + 3, du + 3);
+        for (int k = 0; k < 6; k++) r6[k] = h * s[k] - D.rg[k][b];
+        du[0] = r6[0] * im; du[1] = r6[1] * im; du[2] = r6[2] * im;
+        sym3v(Si, r6 + 3, du + 3);
         if (lane == 0) {
           const T t = D.dampT;
           T u[6];
@@ -830,26 +828,106 @@ __global__ void __launch_bounds__(BLOCK) k_body_pass(Dev<T> D, const T *__restri
 #pragma unroll
           for (int k = 0; k < 4; k++) D.rq[k][b] = qn[k] / nn;
         }
+        continue;
+      }
+      T y[6];
+      if (MODE == BM_APPLY) {
+        y[0] = s[0] * im; y[1] = s[1] * im; y[2] = s[2] * im;
+        sym3v(Si, s + 3, y + 3);
+      } else {  // BM_RESIDUAL
+        T g[6], du[6], Iw[6];
+#pragma unroll
+        for (int k = 0; k < 6; k++) { du[k] = D.ru[k][b] - D.rut[k][b]; Iw[k] = D.rIw[k][b]; }
+        const T m = D.rm[b];
+        g[0] = m * du[0] - h * s[0]; g[1] = m * du[1] - h * s[1]; g[2] = m * du[2] - h * s[2];
+        T ia[3];
+        sym3v(Iw, du + 3, ia);
+        g[3] = ia[0] - h * s[3]; g[4] = ia[1] - h * s[4]; g[5] = ia[2] - h * s[5];
+        y[0] = g[0] * im; y[1] = g[1] * im; y[2] = g[2] * im;
+        sym3v(Si, g + 3, y + 3);
+        if (lane == 0) {
+#pragma unroll
+          for (int k = 0; k < 6; k++) { D.rg[k][b] = g[k]; D.ryg[k][b] = y[k]; acc_g2.add_prod(g[k], g[k]); }
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < KR; r++) {
+        if (sl[r] < 0) continue;
+        T acc = T(0);
+#pragma unroll
+        for (int k = 0; k < 6; k++) acc += J[r][k] * y[k];
+        D.t[sl[r]] = acc;
+        if (MODE == BM_RESIDUAL) {
+          T tj[3];
+          sym3v(Si, J[r] + 3, tj);
+          D.t2[sl[r]] = (J[r][0] * J[r][0] + J[r][1] * J[r][1] + J[r][2] * J[r][2]) * im + dot3(J[r] + 3, tj);
+        }
+      }
+      for (int e = s0 + lane + KR * G; e < s1; e += G) {
+        T Je[6];
+#pragma unroll
+        for (int k = 0; k < 6; k++) Je[k] = D.ej6[k][e];
+        T acc = T(0);
+#pragma unroll
+        for (int k = 0; k < 6; k++) acc += Je[k] * y[k];
+        const int slt = D.eslot[e];
+        D.t[slt] = acc;
+        if (MODE == BM_RESIDUAL) {
+          T tj[3];
+          sym3v(Si, Je + 3, tj);
+          D.t2[slt] = (Je[0] * Je[0] + Je[1] * Je[1] + Je[2] * Je[2]) * im + dot3(Je + 3, tj);
+        }
       }
     }
   } else {
     const int bid = blockIdx.x - D.nblk_body_r;
     const int stride = D.nblk_body_p * gpb;
-    T *J0 = D.ej3[buf][0], *J1 = D.ej3[buf][1], *J2 = D.ej3[buf][2];
+    const T *J0 = D.ej3[buf][0], *J1 = D.ej3[buf][1], *J2 = D.ej3[buf][2];
+    const int *eslot = D.eslot + D.ER;
+    const bool gs = MODE == BM_RESIDUAL && D.gs && newton_it > 0;
     for (int b0 = bid * gpb; b0 < D.np; b0 += stride) {
       const int b = b0 + gid;
       const bool act = b < D.np;
       int s0 = 0, s1 = 0;
       if (act) { s0 = D.vseg[b]; s1 = D.vseg[b + 1]; }
+      int sl[KR];
+#pragma unroll
+      for (int r = 0; r < KR; r++) {
+        const int e = s0 + lane + r * G;
+        sl[r] = e < s1 ? eslot[e] : -1;
+      }
+      T J[KR][3], xv[KR];
+#pragma unroll
+      for (int r = 0; r < KR; r++) {
+        const int e = s0 + lane + r * G;
+        if (sl[r] >= 0) {
+          J[r][0] = J0[e]; J[r][1] = J1[e]; J[r][2] = J2[e];
+          xv[r] = in[slot_row(sl[r], Rp)];
+        } else {
+          J[r][0] = J[r][1] = J[r][2] = T(0);
+          xv[r] = T(0);
+        }
+      }
       T s[3] = {0, 0, 0}, sp[3] = {0, 0, 0};
-      const bool gs = MODE == BM_RESIDUAL && D.gs && newton_it > 0;
-      for (int e = s0 + lane; e < s1; e += G) {
-        T xv = in[D.erow[D.ER + e]];
-        s[0] += J0[e] * xv; s[1] += J1[e] * xv; s[2] += J2[e] * xv;
-        if (gs) {  // (J^n - J^{n-1})_e lambda_row(e), differenced per entry
-          sp[0] += (J0[e] - D.ej3[buf ^ 1][0][e]) * xv;
-          sp[1] += (J1[e] - D.ej3[buf ^ 1][1][e]) * xv;
-          sp[2] += (J2[e] - D.ej3[buf ^ 1][2][e]) * xv;
+#pragma unroll
+      for (int r = 0; r < KR; r++) {
+#pragma unroll
+        for (int k = 0; k < 3; k++) s[k] += J[r][k] * xv[r];
+        if (gs && sl[r] >= 0) {  // (J^n - J^{n-1})_e lambda_row(e), differenced per entry
+          const int e = s0 + lane + r * G;
+          sp[0] += (J[r][0] - D.ej3[buf ^ 1][0][e]) * xv[r];
+          sp[1] += (J[r][1] - D.ej3[buf ^ 1][1][e]) * xv[r];
+          sp[2] += (J[r][2] - D.ej3[buf ^ 1][2][e]) * xv[r];
+        }
+      }
+      for (int e = s0 + lane + KR * G; e < s1; e += G) {
+        const T x = in[slot_row(eslot[e], Rp)];
+        const T a0 = J0[e], a1 = J1[e], a2 = J2[e];
+        s[0] += a0 * x; s[1] += a1 * x; s[2] += a2 * x;
+        if (gs) {
+          sp[0] += (a0 - D.ej3[buf ^ 1][0][e]) * x;
+          sp[1] += (a1 - D.ej3[buf ^ 1][1][e]) * x;
+          sp[2] += (a2 - D.ej3[buf ^ 1][2][e]) * x;
         }
       }
 #pragma unroll
@@ -859,12 +937,28 @@ __global__ void __launch_bounds__(BLOCK) k_body_pass(Dev<T> D, const T *__restri
         for (int k = 0; k < 3; k++) sp[k] = group_sum<G>(sp[k]);
       }
       if (!act) continue;
+      if (MODE == BM_UPDATE) {
+        if (lane == 0) {
+          const T t = D.dampT;
+#pragma unroll
+          for (int k = 0; k < 3; k++) {
+            const T du = (h * s[k] - D.pg[k][b]) * D.phinv[k][b];
+            const T u = D.pu[k][b];
+            D.puprev[k][b] = u;
+            const T un = u + t * du;
+            D.pu[k][b] = un;
+            D.px[k][b] = D.px0[k][b] + h * un;
+          }
+        }
+        continue;
+      }
+      T y[3], hi[3];
       if (MODE == BM_APPLY) {
-        T y[3] = {s[0] * D.phinv[0][b], s[1] * D.phinv[1][b], s[2] * D.phinv[2][b]};
-        for (int e = s0 + lane; e < s1; e += G) D.t[D.ER + e] = J0[e] * y[0] + J1[e] * y[1] + J2[e] * y[2];
-      } else if (MODE == BM_RESIDUAL) {
+#pragma unroll
+        for (int k = 0; k < 3; k++) { hi[k] = D.phinv[k][b]; y[k] = s[k] * hi[k]; }
+      } else {  // BM_RESIDUAL
         const T m = D.pm[b];
-        T g[3], hi[3], y[3];
+        T g[3];
 #pragma unroll
         for (int k = 0; k < 3; k++) {
           const T u = D.pu[k][b];
@@ -889,24 +983,19 @@ __global__ void __launch_bounds__(BLOCK) k_body_pass(Dev<T> D, const T *__restri
             acc_g2.add_prod(g[k], g[k]);
           }
         }
-        for (int e = s0 + lane; e < s1; e += G) {
-          const T a0 = J0[e], a1 = J1[e], a2 = J2[e];
-          D.t[D.ER + e] = a0 * y[0] + a1 * y[1] + a2 * y[2];
-          D.t2[D.ER + e] = a0 * a0 * hi[0] + a1 * a1 * hi[1] + a2 * a2 * hi[2];
-        }
-      } else {  // BM_UPDATE
-        if (lane == 0) {
-          const T t = D.dampT;
+      }
 #pragma unroll
-          for (int k = 0; k < 3; k++) {
-            const T du = (h * s[k] - D.pg[k][b]) * D.phinv[k][b];
-            const T u = D.pu[k][b];
-            D.puprev[k][b] = u;
-            const T un = u + t * du;
-            D.pu[k][b] = un;
-            D.px[k][b] = D.px0[k][b] + h * un;
-          }
-        }
+      for (int r = 0; r < KR; r++) {
+        if (sl[r] < 0) continue;
+        D.t[sl[r]] = J[r][0] * y[0] + J[r][1] * y[1] + J[r][2] * y[2];
+        if (MODE == BM_RESIDUAL)
+          D.t2[sl[r]] = J[r][0] * J[r][0] * hi[0] + J[r][1] * J[r][1] * hi[1] + J[r][2] * J[r][2] * hi[2];
+      }
+      for (int e = s0 + lane + KR * G; e < s1; e += G) {
+        const T a0 = J0[e], a1 = J1[e], a2 = J2[e];
+        const int slt = eslot[e];
+        D.t[slt] = a0 * y[0] + a1 * y[1] + a2 * y[2];
+        if (MODE == BM_RESIDUAL) D.t2[slt] = a0 * a0 * hi[0] + a1 * a1 * hi[1] + a2 * a2 * hi[2];
       }
     }
   }
@@ -936,11 +1025,8 @@ __global__ void __launch_bounds__(BLOCK) k_row_pass(Dev<T> D, int force) {
   if (blockIdx.x < D.nblk_row_pair) {
     const int stride = D.nblk_row_pair * BLOCK;
     for (int i = blockIdx.x * BLOCK + threadIdx.x; i < D.Rpair; i += stride) {
-      const int e0 = D.re0[i], e1 = D.re1[i];
       if (MODE == RM_RHS) {
-        T tb = T(0), td = T(0);
-        if (e0 >= 0) { tb += D.t[e0]; td += D.t2[e0]; }
-        if (e1 >= 0) { tb += D.t[e1]; td += D.t2[e1]; }
+        const T tb = D.t[2 * i] + D.t[2 * i + 1], td = D.t2[2 * i] + D.t2[2 * i + 1];
         const T hv = D.hv[i];
         const T bi = (tb - hv) * ih;
         const T dg = td + D.cdiag[i] + eps;
@@ -951,9 +1037,7 @@ __global__ void __launch_bounds__(BLOCK) k_row_pass(Dev<T> D, int force) {
         a[0].add_prod(hv, hv);
         a[1].add_prod(bi, zi);
       } else {
-        T acc = T(0);
-        if (e0 >= 0) acc += D.t[e0];
-        if (e1 >= 0) acc += D.t[e1];
+        const T acc = D.t[2 * i] + D.t[2 * i + 1];
         const T zi = D.z[i];
         const T Pi = D.P[i];
         const T az = acc + (D.cdiag[i] + eps) * zi;
@@ -972,7 +1056,7 @@ __global__ void __launch_bounds__(BLOCK) k_row_pass(Dev<T> D, int force) {
     const int stride = D.nblk_row_tet * BLOCK;
     const int rb = D.Rpair;
     for (int t = bid * BLOCK + threadIdx.x; t < D.nt; t += stride) {
-      const int *te = D.te + 12 * t;
+      const T *ts = D.t + 2 * rb + 12 * t, *ts2 = D.t2 + 2 * rb + 12 * t;
       const T *c3 = D.c3 + 6 * t;
       if (MODE == RM_RHS) {
         const T cc[3] = {c3[0], c3[1], c3[2]};
@@ -980,7 +1064,7 @@ __global__ void __launch_bounds__(BLOCK) k_row_pass(Dev<T> D, int force) {
         for (int k = 0; k < 3; k++) {
           T tb = T(0), td = T(0);
 #pragma unroll
-          for (int q = 0; q < 4; q++) { const int e = te[4 * k + q]; tb += D.t[e]; td += D.t2[e]; }
+          for (int q = 0; q < 4; q++) { tb += ts[4 * k + q]; td += ts2[4 * k + q]; }
           const int i = rb + 3 * t + k;
           const T hv = D.hv[i];
           const T bi = (tb - hv) * ih;
@@ -1003,7 +1087,7 @@ __global__ void __launch_bounds__(BLOCK) k_row_pass(Dev<T> D, int force) {
         for (int k = 0; k < 3; k++) {
           T acc = T(0);
 #pragma unroll
-          for (int q = 0; q < 4; q++) acc += D.t[te[4 * k + q]];
+          for (int q = 0; q < 4; q++) acc += ts[4 * k + q];
           const int i = i0 + k;
           const T az = acc + cz[k] + eps * zz[k];
           D.Az[i] = az;

@@ -66,7 +66,7 @@ def test_noalloc_rejects_too_many_entries(torch_cuda):
     s = scenes.batched_envs(seed=5, n_envs=6000)
     g = nsn.Solver(s, precision=nsn.NSN_FP32, newton_iters=1, cr_iters=1)
     sz = g.sizes()
-    assert sz["rigid_entries"] + sz["particle_entries"] > 4 * 1024 * 1024
+    assert 2 * sz["pair_rows"] + 12 * sz["tets"] > 4 * 1024 * 1024
     g.linearize(0)
     xd = torch.zeros(g.R, dtype=torch.float32, device="cuda")
     yd = torch.zeros_like(xd)
