@@ -46,8 +46,8 @@ UNIT = "env-steps/s"
 WORKLOADS = {
     "batched4096": dict(make=lambda seed: scenes.batched_envs(seed=seed, n_envs=4096), newton=5, cr=25,
                         desc="4096 chain+cube-pile environments (3-20 links, 0-64 cubes, mu 0.3-1.0)"),
-    "batched1024": dict(make=lambda seed: scenes.batched_envs(seed=seed, n_envs=1024), newton=5, cr=25,
-                        desc="1024 chain+cube-pile environments (profiling size: ~0.6 M rows, above L2)"),
+    "batched2048": dict(make=lambda seed: scenes.batched_envs(seed=seed, n_envs=2048), newton=5, cr=25,
+                        desc="2048 chain+cube-pile environments (profiling size: ~1.2 M rows, working set above L2)"),
     "chain_block": dict(make=lambda seed: scenes.chain_block(seed=seed), newton=10, cr=50,
                         desc="7-link revolute chain on a 24^3-hex stable Neo-Hookean block (69,120 tets)"),
     "cube_stack": dict(make=lambda seed: scenes.cube_stack(seed=seed), newton=4, cr=20,
