@@ -197,6 +197,42 @@ nsn_status nsn_time_operator(nsn_ctx *ctx, int32_t iters, float *ms_body_pass, f
  * entries, particle entries, device bytes held by the context]. */
 nsn_status nsn_operator_sizes(nsn_ctx *ctx, int64_t *sizes8);
 
+/* ---- warm starts and the learned warm start ----------------------------------
+ * The paper starts every step from lambda^0 = 0 (Sec. 8.1) and notes that
+ * warm starting can improve efficiency.  NSN_WARM_PREV starts from the
+ * previous step's multipliers; NSN_WARM_LEARNED sets the contact rows'
+ * lambda^0 from a per-contact network (16 features -> 128 -> 128 -> 128 -> 4,
+ * ReLU, BF16 tensor-core GEMMs with FP32 accumulation): outputs are the
+ * normal and two friction multipliers over the contact's gravity-scaled
+ * effective mass |g| / (1/m_a + 1/m_b) and a log preconditioner scale.  In
+ * both modes the warm start is kept only if the merit at (u = 0, lambda^0) is
+ * not above the merit at the zero start; otherwise the step starts from zero.
+ * u^0 = 0 in all modes.  The relative merit is always taken against the zero
+ * start. */
+enum { NSN_WARM_ZERO = 0, NSN_WARM_PREV = 1, NSN_WARM_LEARNED = 2 };
+#define NSN_MLP_NPARAM (128 * 16 + 128 + 128 * 128 + 128 + 128 * 128 + 128 + 4 * 128 + 4)
+nsn_status nsn_set_warm_start(nsn_ctx *ctx, int32_t mode);
+/* Merits of the last warm-started step: zero start, warm start, and whether
+ * the warm start was rejected. */
+nsn_status nsn_get_warm_stats(nsn_ctx *ctx, double *merit_zero, double *merit_warm, int32_t *rejected);
+/* Network parameters (host, NSN_MLP_NPARAM floats): W1[128][16], b1[128],
+ * W2[128][128], b2, W3[128][128], b3, W4[4][128], b4[4]; y = W x + b.  Setting
+ * them resets the Adam state.  get_params also returns the last gradients. */
+nsn_status nsn_mlp_set_params(nsn_ctx *ctx, const float *params, int32_t n);
+nsn_status nsn_mlp_get_params(nsn_ctx *ctx, float *params, float *grads, int32_t n);
+/* Y[n][4] = network(X[n][16]); device pointers, context stream. */
+nsn_status nsn_mlp_forward(nsn_ctx *ctx, const float *X, int32_t n, float *Y);
+/* One training step on a batch (device X[n][16], targets T[n][4], output
+ * weights w[4]): loss 1/(2n) sum w_k (y_k - t_k)^2, backward on the tensor
+ * cores, Adam (lr; lr = 0 only computes the gradients); *loss (host) gets the
+ * batch loss. */
+nsn_status nsn_mlp_train_step(nsn_ctx *ctx, const float *X, const float *T, const float *w, int32_t n, float lr,
+                              float *loss);
+/* Features of every contact at the current (committed) state and, if Ytarget
+ * is not NULL, the current multipliers as training targets (device arrays
+ * X[nc][16], Ytarget[nc][4]). */
+nsn_status nsn_contact_features(nsn_ctx *ctx, float *X, float *Ytarget);
+
 /* ---- allocation-free operator apply -----------------------------------------
  * The paper has no counterpart; this entry point serves callers that cannot
  * allocate device memory where they need an operator product: code running

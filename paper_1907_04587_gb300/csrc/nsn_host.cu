@@ -14,6 +14,7 @@
 
 #include "../../include/nsn.h"
 #include "nsn_kernels.cuh"
+#include "nsn_mlp.cuh"
 
 using namespace nsn;
 
@@ -51,6 +52,21 @@ struct Layout {
   std::vector<int> eslot, rseg, vseg, re0, re1, te;
 };
 
+struct MlpState {
+  bool ready = false;
+  float *pf = nullptr, *gr = nullptr, *m = nullptr, *v = nullptr;  // FP32 master, gradient, Adam moments
+  __nv_bfloat16 *pb = nullptr;                                      // BF16 copy used by the GEMMs
+  int adam_t = 0;
+  // workspace for up to cap rows (inference chunk or training batch)
+  int cap = 0;
+  __nv_bfloat16 *xb = nullptr, *a1b = nullptr, *a2b = nullptr, *a3b = nullptr, *dyb = nullptr, *dzb = nullptr;
+  float *a1f = nullptr, *a2f = nullptr, *a3f = nullptr, *y = nullptr, *dyf = nullptr, *da = nullptr, *dzf = nullptr,
+        *lpart = nullptr;
+  // per-contact features and predictions for the learned warm start
+  int ncap = 0;
+  float *X = nullptr, *Y = nullptr;
+};
+
 }  // namespace
 
 struct nsn_ctx {
@@ -72,6 +88,8 @@ struct nsn_ctx {
   bool linearized = false;
   int lin_buf = 0;           // entry buffer written by the kept linearisation
   int kept_buf = -1;         // entry buffer of the system kept by the last step / linearisation
+  int warm_mode = 0;         // NSN_WARM_*
+  MlpState mlp;
   int built_nb = 0;          // bodies present in the current device build
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   std::string err;
@@ -208,6 +226,7 @@ void carve(Arena &A, Dev<T> &D, const Layout &L, int nb) {
   D.lam = tk(L.R); D.cdiag = tk(L.R); D.hv = tk(L.R); D.b = tk(L.R); D.P = tk(L.R);
   D.x = tk(L.R); D.z = tk(L.R); D.p = tk(L.R); D.Ap = tk(L.R); D.Az = tk(L.R);
   D.c3 = tk(6 * L.nt);
+  D.lam_prev = tk(L.R);
   D.cba = A.take<int>(L.nc); D.cbb = A.take<int>(L.nc);
   for (int k = 0; k < 3; k++) { D.cpa[k] = tk(L.nc); D.cpb[k] = tk(L.nc); D.cn[k] = tk(L.nc); }
   D.cdd = tk(L.nc); D.cmu = tk(L.nc);
@@ -232,6 +251,7 @@ void fill_sizes(Dev<T> &D, const Layout &L, const nsn_config &cfg) {
   D.hT = T(cfg.h); D.ihT = T(1.0 / cfg.h); D.epsT = T(cfg.eps); D.dampT = T(cfg.damping);
   for (int k = 0; k < 3; k++) D.gravT[k] = T(cfg.gravity[k]);
   D.ncp = cfg.ncp; D.rscale = cfg.rscale; D.gs = cfg.geom_stiffness; D.cr_tol = cfg.cr_tol_mode;
+  D.warm = 0;
   D.nblk_body_r = L.nr ? clampb(cdiv((long long)L.nr * kGroup, BLOCK)) : 0;
   D.nblk_body_p = L.np ? clampb(cdiv((long long)L.np * kGroup, BLOCK)) : 0;
   D.nblk_row_pair = L.Rpair ? clampb(cdiv(L.Rpair, BLOCK)) : 0;
@@ -345,6 +365,7 @@ nsn_status upload(nsn_ctx *c, Dev<T> &D) {
     CUDA_TRY(c, put(D.tD1, D1)); CUDA_TRY(c, put(D.talpha, al));
   }
   CUDA_TRY(c, cudaMemsetAsync(D.lam, 0, sizeof(T) * std::max(L.R, 1), st));
+  CUDA_TRY(c, cudaMemsetAsync(D.lam_prev, 0, sizeof(T) * std::max(L.R, 1), st));
   CUDA_TRY(c, cudaMemsetAsync(D.sc, 0, sizeof(Scalars), st));
   CUDA_TRY(c, cudaMemsetAsync(D.fl, 0, sizeof(Flags), st));
   for (int b2 = 0; b2 < 2; b2++)
@@ -425,6 +446,8 @@ __global__ void k_backup_state(Dev<T> D, T *buf, int restore) {
 // ------------------------------------------------------------------------------------
 // step orchestration
 
+nsn_status mlp_infer(nsn_ctx *c, const float *X, int n, float *Y, cudaStream_t st);
+
 template <typename T>
 struct Launcher {
   nsn_ctx *c;
@@ -482,9 +505,37 @@ struct Launcher {
     k_lambda_update<T><<<D.nblk_upd, BLOCK, 0, st>>>(D);
     count++;
   }
+  // warm start of Sec. 8.1's multipliers (previous step or learned), kept only
+  // if the merit at (u = 0, lambda^0) does not exceed the zero start's
+  void warm_start() {
+    eval(0, 1);
+    body(BM_RESIDUAL, D.lam, 0, 0, 1);
+    rows(RM_RHS, 1);
+    k_merit<T><<<1, RED_THREADS, 0, st>>>(D, -1, 1);
+    count++;
+    if (c->warm_mode == NSN_WARM_PREV) {
+      if (D.R) { k_copy<T><<<D.nblk_upd, BLOCK, 0, st>>>(D.lam, D.lam_prev, D.R); count++; }
+    } else if (D.nc) {
+      k_warm_from_pred<T><<<cdiv(D.nc, 128), 128, 0, st>>>(D, c->mlp.Y);
+      count++;
+    }
+    eval(0, 1);
+    body(BM_RESIDUAL, D.lam, 0, 0, 1);
+    rows(RM_RHS, 1);
+    k_merit<T><<<1, RED_THREADS, 0, st>>>(D, -2, 1);
+    k_warm_accept<T><<<D.nblk_upd, BLOCK, 0, st>>>(D);
+    count += 2;
+  }
   void step() {
     const int N = c->cfg.newton_iters, M = c->cfg.cr_iters;
+    if (c->warm_mode == NSN_WARM_LEARNED && D.nc) {
+      k_contact_features<T><<<cdiv(D.nc, 128), 128, 0, st>>>(D, c->mlp.X);
+      count++;
+      mlp_infer(c, c->mlp.X, D.nc, c->mlp.Y, st);
+      count += 5 * ((D.nc + c->mlp.cap - 1) / c->mlp.cap);
+    }
     begin();
+    if (c->warm_mode != NSN_WARM_ZERO) warm_start();
     for (int n = 0; n < N; n++) {
       linearize_at(n);
       cr(M, n & 1);
@@ -497,6 +548,7 @@ struct Launcher {
     rows(RM_RHS, 1);
     k_merit<T><<<1, RED_THREADS, 0, st>>>(D, N, 1);
     count++;
+    if (D.R) { k_copy<T><<<D.nblk_upd, BLOCK, 0, st>>>(D.lam_prev, D.lam, D.R); count++; }
   }
 };
 
@@ -580,10 +632,18 @@ nsn_status ensure_built(nsn_ctx *c) {
   return NSN_OK;
 }
 
+nsn_status mlp_ensure(nsn_ctx *c, int rows_needed);
+
 template <typename T>
 nsn_status run_steps(nsn_ctx *c, int nsteps) {
   Dev<T> &D = dev<T>(c);
   cudaStream_t st = c->stream;
+  D.warm = c->warm_mode;
+  if (c->warm_mode == NSN_WARM_LEARNED) {
+    if (!c->mlp.ready) return fail(c, NSN_ERR_BAD_STATE, "learned warm start without network parameters (nsn_mlp_set_params)");
+    nsn_status s = mlp_ensure(c, D.nc);
+    if (s != NSN_OK) return s;
+  }
   CUDA_TRY(c, cudaEventRecord(c->ev0, st));
   if (c->cfg.use_graph) {
     if (!c->graph) {
@@ -834,6 +894,145 @@ nsn_status do_time_operator(nsn_ctx *c, int iters, float *ms_body, float *ms_row
 
 }  // namespace
 
+
+// ------------------------------------------------------------------------------------
+// learned warm start: network workspace, inference and training
+
+namespace {
+
+template <typename X>
+nsn_status dalloc(nsn_ctx *c, X **p, size_t n) {
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  cudaError_t e = cudaMalloc(reinterpret_cast<void **>(p), sizeof(X) * (n ? n : 1));
+  if (e != cudaSuccess) return fail(c, NSN_ERR_OUT_OF_MEMORY, "cudaMalloc: %s", cudaGetErrorString(e));
+  return NSN_OK;
+}
+
+void mlp_free(MlpState &m) {
+  void *ptrs[] = {m.pf, m.gr, m.m, m.v, m.pb, m.xb, m.a1b, m.a2b, m.a3b, m.dyb, m.dzb, m.a1f, m.a2f, m.a3f,
+                  m.y, m.dyf, m.da, m.dzf, m.lpart, m.X, m.Y};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+  m = MlpState();
+}
+
+constexpr int kMlpChunk = 65536;
+
+nsn_status mlp_workspace(nsn_ctx *c, int cap) {
+  MlpState &m = c->mlp;
+  if (cap <= m.cap) return NSN_OK;
+  nsn_status s;
+  const size_t H = size_t(cap) * mlp::NH;
+  if ((s = dalloc(c, &m.xb, size_t(cap) * mlp::NIN)) || (s = dalloc(c, &m.a1b, H)) || (s = dalloc(c, &m.a2b, H)) ||
+      (s = dalloc(c, &m.a3b, H)) || (s = dalloc(c, &m.dzb, H)) || (s = dalloc(c, &m.a1f, H)) ||
+      (s = dalloc(c, &m.a2f, H)) || (s = dalloc(c, &m.a3f, H)) || (s = dalloc(c, &m.da, H)) ||
+      (s = dalloc(c, &m.dzf, H)) || (s = dalloc(c, &m.y, size_t(cap) * mlp::NOUT)) ||
+      (s = dalloc(c, &m.dyf, size_t(cap) * mlp::NOUT)) || (s = dalloc(c, &m.dyb, size_t(cap) * mlp::NOUT)) ||
+      (s = dalloc(c, &m.lpart, 1024)))
+    return s;
+  m.cap = cap;
+  return NSN_OK;
+}
+
+template <bool TA, bool TB>
+void gemm(const __nv_bfloat16 *A, const __nv_bfloat16 *B, const float *bias, float *Cf, __nv_bfloat16 *Cb, int M, int N,
+          int K, int lda, int ldb, int ldc, int relu, cudaStream_t st) {
+  dim3 grid(cdiv(N, mlp::TN), cdiv(M, mlp::TM));
+  mlp::k_gemm<TA, TB><<<grid, 128, 0, st>>>(A, B, bias, Cf, Cb, M, N, K, lda, ldb, ldc, relu);
+}
+
+// forward pass of n rows (n <= cap); keeps FP32 post-activations when train
+void mlp_forward_rows(MlpState &m, const float *X, int n, float *Y, bool train, cudaStream_t st) {
+  using namespace mlp;
+  k_to_bf16<<<cdiv(size_t(n) * NIN, 256), 256, 0, st>>>(X, m.xb, n * NIN);
+  gemm<false, true>(m.xb, m.pb + OFF_W1, m.pf + OFF_B1, train ? m.a1f : nullptr, m.a1b, n, NH, NIN, NIN, NIN, NH, 1, st);
+  gemm<false, true>(m.a1b, m.pb + OFF_W2, m.pf + OFF_B2, train ? m.a2f : nullptr, m.a2b, n, NH, NH, NH, NH, NH, 1, st);
+  gemm<false, true>(m.a2b, m.pb + OFF_W3, m.pf + OFF_B3, train ? m.a3f : nullptr, m.a3b, n, NH, NH, NH, NH, NH, 1, st);
+  gemm<false, true>(m.a3b, m.pb + OFF_W4, m.pf + OFF_B4, Y, nullptr, n, NOUT, NH, NH, NH, NOUT, 0, st);
+}
+
+nsn_status mlp_ensure(nsn_ctx *c, int rows_needed) {
+  MlpState &m = c->mlp;
+  nsn_status s = mlp_workspace(c, kMlpChunk);
+  if (s != NSN_OK) return s;
+  if (rows_needed > m.ncap) {
+    if ((s = dalloc(c, &m.X, size_t(rows_needed) * mlp::NIN)) || (s = dalloc(c, &m.Y, size_t(rows_needed) * mlp::NOUT)))
+      return s;
+    m.ncap = rows_needed;
+    if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
+  }
+  return NSN_OK;
+}
+
+nsn_status mlp_infer(nsn_ctx *c, const float *X, int n, float *Y, cudaStream_t st) {
+  MlpState &m = c->mlp;
+  for (int r0 = 0; r0 < n; r0 += m.cap) {
+    const int nr = std::min(m.cap, n - r0);
+    mlp_forward_rows(m, X + size_t(r0) * mlp::NIN, nr, Y + size_t(r0) * mlp::NOUT, false, st);
+  }
+  return NSN_OK;
+}
+
+nsn_status mlp_train(nsn_ctx *c, const float *X, const float *Tg, const float *w, int n, float lr, float *loss) {
+  using namespace mlp;
+  MlpState &m = c->mlp;
+  cudaStream_t st = c->stream;
+  nsn_status s = mlp_workspace(c, std::max(n, 64));
+  if (s != NSN_OK) return s;
+  mlp_forward_rows(m, X, n, m.y, true, st);
+  const int nb = std::min(cdiv(size_t(n) * NOUT, 256), 1024);
+  k_loss_grad<<<nb, 256, 0, st>>>(m.y, Tg, w, m.dyb, m.dyf, n, m.lpart);
+  float *g = m.gr;
+  const int cs = 128;
+  // layer 4
+  gemm<true, false>(m.dyb, m.a3b, nullptr, g + OFF_W4, nullptr, NOUT, NH, n, NOUT, NH, NH, 0, st);
+  k_colsum<<<1, cs, 0, st>>>(m.dyf, g + OFF_B4, n, NOUT);
+  gemm<false, false>(m.dyb, m.pb + OFF_W4, nullptr, m.da, nullptr, n, NH, NOUT, NOUT, NH, NH, 0, st);
+  // layer 3
+  k_relu_back<<<cdiv(size_t(n) * NH, 256), 256, 0, st>>>(m.da, m.a3f, m.dzb, m.dzf, n * NH);
+  gemm<true, false>(m.dzb, m.a2b, nullptr, g + OFF_W3, nullptr, NH, NH, n, NH, NH, NH, 0, st);
+  k_colsum<<<1, cs, 0, st>>>(m.dzf, g + OFF_B3, n, NH);
+  gemm<false, false>(m.dzb, m.pb + OFF_W3, nullptr, m.da, nullptr, n, NH, NH, NH, NH, NH, 0, st);
+  // layer 2
+  k_relu_back<<<cdiv(size_t(n) * NH, 256), 256, 0, st>>>(m.da, m.a2f, m.dzb, m.dzf, n * NH);
+  gemm<true, false>(m.dzb, m.a1b, nullptr, g + OFF_W2, nullptr, NH, NH, n, NH, NH, NH, 0, st);
+  k_colsum<<<1, cs, 0, st>>>(m.dzf, g + OFF_B2, n, NH);
+  gemm<false, false>(m.dzb, m.pb + OFF_W2, nullptr, m.da, nullptr, n, NH, NH, NH, NH, NH, 0, st);
+  // layer 1
+  k_relu_back<<<cdiv(size_t(n) * NH, 256), 256, 0, st>>>(m.da, m.a1f, m.dzb, m.dzf, n * NH);
+  gemm<true, false>(m.dzb, m.xb, nullptr, g + OFF_W1, nullptr, NH, NIN, n, NH, NIN, NIN, 0, st);
+  k_colsum<<<1, cs, 0, st>>>(m.dzf, g + OFF_B1, n, NH);
+  if (lr > 0.f) {
+    m.adam_t += 1;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float bc1 = 1.f - std::pow(b1, float(m.adam_t)), bc2 = 1.f - std::pow(b2, float(m.adam_t));
+    k_adam<<<cdiv(NPARAM, 256), 256, 0, st>>>(m.pf, g, m.m, m.v, m.pb, NPARAM, lr, b1, b2, 1e-8f, bc1, bc2);
+  }
+  CUDA_TRY(c, cudaGetLastError());
+  if (loss) {
+    float part[1024];
+    CUDA_TRY(c, cudaMemcpyAsync(part, m.lpart, sizeof(float) * nb, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(c, cudaStreamSynchronize(st));
+    double l = 0.0;
+    for (int i = 0; i < nb; i++) l += part[i];
+    *loss = float(l / n);
+  }
+  return NSN_OK;
+}
+
+template <typename T>
+nsn_status do_features(nsn_ctx *c, float *X, float *Ytarget) {
+  Dev<T> &D = dev<T>(c);
+  if (!D.nc) return NSN_OK;
+  if (X) k_contact_features<T><<<cdiv(D.nc, 128), 128, 0, c->stream>>>(D, X);
+  if (Ytarget) k_contact_targets<T><<<cdiv(D.nc, 128), 128, 0, c->stream>>>(D, Ytarget);
+  CUDA_TRY(c, cudaGetLastError());
+  return NSN_OK;
+}
+
+}  // namespace
+
 // =====================================================================================
 // C ABI
 
@@ -882,6 +1081,7 @@ nsn_status nsn_destroy(nsn_ctx *c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   if (c->graph) cudaGraphExecDestroy(c->graph);
   if (c->dmem) cudaFree(c->dmem);
+  mlp_free(c->mlp);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
   if (c->own_stream) cudaStreamDestroy(c->stream);
@@ -1167,6 +1367,77 @@ nsn_status nsn_operator_sizes(nsn_ctx *c, int64_t *sizes) {
   sizes[0] = L.nr; sizes[1] = L.np; sizes[2] = L.R; sizes[3] = L.Rpair; sizes[4] = L.nt;
   sizes[5] = L.ER; sizes[6] = L.EV; sizes[7] = (int64_t)c->dbytes;
   return NSN_OK;
+}
+
+nsn_status nsn_set_warm_start(nsn_ctx *c, int32_t mode) {
+  if (!c || mode < NSN_WARM_ZERO || mode > NSN_WARM_LEARNED) return NSN_ERR_INVALID_ARG;
+  if (mode != c->warm_mode && c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
+  c->warm_mode = mode;
+  return NSN_OK;
+}
+
+nsn_status nsn_get_warm_stats(nsn_ctx *c, double *merit_zero, double *merit_warm, int32_t *rejected) {
+  if (!c) return NSN_ERR_INVALID_ARG;
+  nsn_status s = ensure_built(c);
+  if (s != NSN_OK) return s;
+  Scalars sc;
+  Scalars *src = c->cfg.precision == NSN_FP64 ? c->d64.sc : c->d32.sc;
+  CUDA_TRY(c, cudaMemcpyAsync(&sc, src, sizeof(Scalars), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  if (merit_zero) *merit_zero = sc.merit0;
+  if (merit_warm) *merit_warm = sc.merit_warm;
+  if (rejected) *rejected = sc.warm_rejected;
+  return NSN_OK;
+}
+
+nsn_status nsn_mlp_set_params(nsn_ctx *c, const float *params, int32_t n) {
+  if (!c || !params || n != mlp::NPARAM) return NSN_ERR_INVALID_ARG;
+  MlpState &m = c->mlp;
+  nsn_status s;
+  if (!m.pf) {
+    if ((s = dalloc(c, &m.pf, mlp::NPARAM)) || (s = dalloc(c, &m.gr, mlp::NPARAM)) || (s = dalloc(c, &m.m, mlp::NPARAM)) ||
+        (s = dalloc(c, &m.v, mlp::NPARAM)) || (s = dalloc(c, &m.pb, mlp::NPARAM)))
+      return s;
+  }
+  CUDA_TRY(c, cudaMemcpyAsync(m.pf, params, sizeof(float) * n, cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaMemsetAsync(m.m, 0, sizeof(float) * n, c->stream));
+  CUDA_TRY(c, cudaMemsetAsync(m.v, 0, sizeof(float) * n, c->stream));
+  CUDA_TRY(c, cudaMemsetAsync(m.gr, 0, sizeof(float) * n, c->stream));
+  mlp::k_to_bf16<<<cdiv(n, 256), 256, 0, c->stream>>>(m.pf, m.pb, n);
+  CUDA_TRY(c, cudaGetLastError());
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  m.adam_t = 0;
+  m.ready = true;
+  return NSN_OK;
+}
+
+nsn_status nsn_mlp_get_params(nsn_ctx *c, float *params, float *grads, int32_t n) {
+  if (!c || n != mlp::NPARAM || !c->mlp.ready) return NSN_ERR_INVALID_ARG;
+  if (params) CUDA_TRY(c, cudaMemcpyAsync(params, c->mlp.pf, sizeof(float) * n, cudaMemcpyDeviceToHost, c->stream));
+  if (grads) CUDA_TRY(c, cudaMemcpyAsync(grads, c->mlp.gr, sizeof(float) * n, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return NSN_OK;
+}
+
+nsn_status nsn_mlp_forward(nsn_ctx *c, const float *X, int32_t n, float *Y) {
+  if (!c || !X || !Y || n < 0 || !c->mlp.ready) return NSN_ERR_INVALID_ARG;
+  nsn_status s = mlp_workspace(c, kMlpChunk);
+  if (s != NSN_OK) return s;
+  mlp_infer(c, X, n, Y, c->stream);
+  CUDA_TRY(c, cudaGetLastError());
+  return NSN_OK;
+}
+
+nsn_status nsn_mlp_train_step(nsn_ctx *c, const float *X, const float *T, const float *w, int32_t n, float lr, float *loss) {
+  if (!c || !X || !T || !w || n <= 0 || !c->mlp.ready) return NSN_ERR_INVALID_ARG;
+  return mlp_train(c, X, T, w, n, lr, loss);
+}
+
+nsn_status nsn_contact_features(nsn_ctx *c, float *X, float *Ytarget) {
+  if (!c) return NSN_ERR_INVALID_ARG;
+  nsn_status s = ensure_built(c);
+  if (s != NSN_OK) return s;
+  return c->cfg.precision == NSN_FP64 ? do_features<double>(c, X, Ytarget) : do_features<float>(c, X, Ytarget);
 }
 
 nsn_status nsn_last_launch_count(nsn_ctx *c, int32_t *kernels_per_step) {

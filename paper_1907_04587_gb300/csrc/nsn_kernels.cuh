@@ -50,6 +50,8 @@ struct Scalars {
   double appap[2];      // CR Ap^T P Ap, double-buffered by iteration parity
   double alpha, beta;   // CR step of the current iteration
   float alpha_f, beta_f; // the same, rounded once for the FP32 update kernel
+  double merit_warm;    // merit at the warm-started iterate (u = 0, lambda^0)
+  int warm_rejected;    // 1 if the warm start was worse than the zero start
 };
 
 struct DS {
@@ -78,6 +80,7 @@ struct Dev {
   double grav[3];
   T hT, ihT, epsT, dampT, gravT[3];
   int ncp, rscale, gs, cr_tol;
+  int warm;          // warm start mode of this step (0 zero, 1 previous step, 2 learned)
   // rigid bodies
   T *rx[3], *rq[4], *rx0[3], *rq0[4], *ru[6], *rut[6], *rm, *rinvm, *rIb[3], *rIw[6], *rIwi[6], *rg[6], *ryg[6];
   // particles
@@ -91,6 +94,7 @@ struct Dev {
   // rows
   int *re0, *re1, *te;
   T *lam, *cdiag, *hv, *b, *P, *x, *z, *p, *Ap, *Az;
+  T *lam_prev;       // multipliers of the previous step (warm starts)
   T *c3;
   // contacts
   int *cba, *cbb;
@@ -1127,9 +1131,11 @@ __global__ void __launch_bounds__(RED_THREADS) k_merit(Dev<T> D, int n, int forc
   reduce_partials<R, RED_THREADS>(D.part_row, D.nblk_row_pair + D.nblk_row_tet, r4);
   if (threadIdx.x == 0) {
     double m = sqrt(g2 + r4[0]);
+    if (n == -1) { D.sc->merit0 = m; return; }          // zero iterate of a warm-started step
+    if (n == -2) { D.sc->merit_warm = m; return; }      // warm-started iterate
     D.sc->merit[n < 1023 ? n : 1023] = m;
     if (force) return;
-    if (n == 0) D.sc->merit0 = m;
+    if (n == 0 && !D.warm) D.sc->merit0 = m;
     double m0 = D.sc->merit0;
     if (D.tol_rel > 0.0 && m <= D.tol_rel * m0) D.fl->newton_stop = 1;
     double eta = 0.0;
@@ -1227,6 +1233,144 @@ __global__ void k_lambda_update(Dev<T> D) {
   const int i0 = blockIdx.x * blockDim.x + threadIdx.x;
   if (i0 == 0) D.fl->newton_count += 1;
   for (int i = i0; i < D.R; i += gridDim.x * blockDim.x) D.lam[i] += t * D.x[i];
+}
+
+// ------------------------------------------------------------------------------------
+// Warm starts (the paper starts from lambda^0 = 0, Sec. 8.1, and notes that
+// warm starting helps).  Features are dimensionless: velocities over g h,
+// penetration over g h^2, multipliers over the contact's gravity-scaled
+// effective mass lambda_s = |g| / (1/m_a + 1/m_b).
+
+template <typename T>
+__device__ __forceinline__ T inv_mass_lin(const Dev<T> &D, const Side<T> &s) {
+  return s.kind == 1 ? D.rinvm[s.idx] : (s.kind == 2 ? T(1) / D.pm[s.idx] : T(0));
+}
+
+// 16 features per contact at the committed state (before k_begin_*):
+// n, relative point velocity, C, inverse-mass shares, previous lambda,
+// mu, normal and friction r over their point-mass values, slip speed.
+template <typename T>
+__global__ void k_contact_features(Dev<T> D, float *X) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= D.nc) return;
+  const T h = D.hT;
+  const T gabs = dsqrt(D.gravT[0] * D.gravT[0] + D.gravT[1] * D.gravT[1] + D.gravT[2] * D.gravT[2]) + T(1e-12);
+  T pa[3], pb[3], n[3];
+  for (int k = 0; k < 3; k++) { pa[k] = D.cpa[k][c]; pb[k] = D.cpb[k][c]; n[k] = D.cn[k][c]; }
+  // positions and velocities of the committed state: x0 := x, u as stored
+  Side<T> A, B;
+  auto load = [&](int enc, const T *p, Side<T> &sd) {
+    if (enc >= 0) {
+      sd.kind = 1; sd.idx = enc;
+      T q[4], R[9];
+      for (int k = 0; k < 4; k++) q[k] = D.rq[k][enc];
+      quat_R(q, R);
+      mat3v(R, p, sd.r);
+      for (int k = 0; k < 3; k++) { sd.x0[k] = D.rx[k][enc]; sd.hu[k] = T(0); }
+    } else if (enc == -1) {
+      sd.kind = 0; sd.idx = -1;
+      for (int k = 0; k < 3; k++) { sd.x0[k] = p[k]; sd.hu[k] = T(0); sd.r[k] = T(0); }
+    } else {
+      sd.kind = 2; sd.idx = -enc - 2;
+      for (int k = 0; k < 3; k++) { sd.x0[k] = D.px[k][sd.idx]; sd.hu[k] = T(0); sd.r[k] = T(0); }
+    }
+  };
+  load(D.cba[c], pa, A);
+  load(D.cbb[c], pb, B);
+  T dd[3];
+  side_diff(A, B, dd);
+  const T Cn = dot3(n, dd) - D.cdd[c];
+  T va[3] = {0, 0, 0}, vb[3] = {0, 0, 0};
+  auto pv = [&](const Side<T> &sd, T *v) {
+    if (sd.kind == 1) {
+      T w[3] = {D.ru[3][sd.idx], D.ru[4][sd.idx], D.ru[5][sd.idx]}, wr[3];
+      cross3(w, sd.r, wr);
+      for (int k = 0; k < 3; k++) v[k] = D.ru[k][sd.idx] + wr[k];
+    } else if (sd.kind == 2) {
+      for (int k = 0; k < 3; k++) v[k] = D.pu[k][sd.idx];
+    }
+  };
+  pv(A, va);
+  pv(B, vb);
+  T vr[3] = {va[0] - vb[0], va[1] - vb[1], va[2] - vb[2]};
+  const T ima = inv_mass_lin(D, A), imb = inv_mass_lin(D, B), ims = ima + imb;
+  const T lscale = gabs / ims;
+  T Ja[6], Jb[6];
+  side_row(A, n, T(1), Ja);
+  side_row(B, n, T(-1), Jb);
+  const T rn = side_quad(D, A, Ja) + side_quad(D, B, Jb);
+  T t[2][3], dq = T(0);
+  basis(n, t[0], t[1]);
+  for (int k = 0; k < 2; k++) {
+    T Da[6], Db[6];
+    side_row(A, t[k], T(1), Da);
+    side_row(B, t[k], T(-1), Db);
+    dq += side_quad(D, A, Da) + side_quad(D, B, Db);
+  }
+  const T vn = dot3(vr, n);
+  const T vt = dsqrt(fmax(dot3(vr, vr) - vn * vn, T(0)));
+  float *x = X + 16 * size_t(c);
+  x[0] = float(n[0]); x[1] = float(n[1]); x[2] = float(n[2]);
+  for (int k = 0; k < 3; k++) x[3 + k] = float(vr[k] / (gabs * h));
+  x[6] = float(Cn / (gabs * h * h));
+  x[7] = float(ima / ims); x[8] = float(imb / ims);
+  for (int k = 0; k < 3; k++) x[9 + k] = float(D.lam_prev[3 * c + k] / lscale);
+  x[12] = float(D.cmu[c]);
+  x[13] = float(rn / ims);
+  x[14] = float(T(0.5) * dq / ims);
+  x[15] = float(vt / (gabs * h));
+}
+
+// lambda_s of each contact (for the training targets and the warm start)
+template <typename T>
+__device__ __forceinline__ T contact_lscale(const Dev<T> &D, int c) {
+  const T gabs = dsqrt(D.gravT[0] * D.gravT[0] + D.gravT[1] * D.gravT[1] + D.gravT[2] * D.gravT[2]) + T(1e-12);
+  const int a = D.cba[c], b = D.cbb[c];
+  T ims = T(0);
+  if (a >= 0) ims += D.rinvm[a]; else if (a <= -2) ims += T(1) / D.pm[-a - 2];
+  if (b >= 0) ims += D.rinvm[b]; else if (b <= -2) ims += T(1) / D.pm[-b - 2];
+  return gabs / ims;
+}
+
+// training targets: the current multipliers of each contact over lambda_s, and
+// a zero log preconditioner scale
+template <typename T>
+__global__ void k_contact_targets(Dev<T> D, float *Y) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= D.nc) return;
+  const T ls = contact_lscale(D, c);
+  for (int k = 0; k < 3; k++) Y[4 * size_t(c) + k] = float(D.lam[3 * c + k] / ls);
+  Y[4 * size_t(c) + 3] = 0.f;
+}
+
+// lambda^0 from the network outputs: lambda_n >= 0, |lambda_f| <= mu lambda_n
+template <typename T>
+__global__ void k_warm_from_pred(Dev<T> D, const float *Y) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= D.nc) return;
+  const T ls = contact_lscale(D, c);
+  T ln = T(Y[4 * size_t(c)]) * ls;
+  if (!(ln > T(0))) ln = T(0);
+  T f1 = T(Y[4 * size_t(c) + 1]) * ls, f2 = T(Y[4 * size_t(c) + 2]) * ls;
+  const T lim = D.cmu[c] * ln, fn = dsqrt(f1 * f1 + f2 * f2);
+  if (fn > lim) { const T s = fn > T(0) ? lim / fn : T(0); f1 *= s; f2 *= s; }
+  D.lam[3 * c] = ln;
+  D.lam[3 * c + 1] = f1;
+  D.lam[3 * c + 2] = f2;
+}
+
+// keep the warm start only if its merit is not above the zero start's
+template <typename T>
+__global__ void k_warm_accept(Dev<T> D) {
+  const bool reject = !(D.sc->merit_warm <= D.sc->merit0);
+  if (blockIdx.x == 0 && threadIdx.x == 0) D.sc->warm_rejected = reject ? 1 : 0;
+  if (!reject) return;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < D.R; i += gridDim.x * blockDim.x) D.lam[i] = T(0);
+}
+
+template <typename T>
+__global__ void k_copy(T *dst, const T *src, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) dst[i] = src[i];
 }
 
 }  // namespace nsn

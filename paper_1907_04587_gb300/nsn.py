@@ -23,6 +23,8 @@ STATUS = {0: "NSN_OK", 1: "NSN_ERR_INVALID_ARG", 2: "NSN_ERR_OUT_OF_MEMORY", 3: 
 NSN_RIGID, NSN_PARTICLE = 0, 1
 NSN_CONTACT, NSN_REVOLUTE, NSN_TET_NH = 0, 1, 2
 NSN_FP32, NSN_FP64 = 0, 1
+NSN_WARM_ZERO, NSN_WARM_PREV, NSN_WARM_LEARNED = 0, 1, 2
+NSN_MLP_NPARAM = 128 * 16 + 128 + 128 * 128 + 128 + 128 * 128 + 128 + 4 * 128 + 4
 
 CONTACT_DTYPE = np.dtype([("body_a", "<i4"), ("body_b", "<i4"), ("pa", "<f4", 3), ("pb", "<f4", 3),
                           ("n", "<f4", 3), ("d", "<f4"), ("mu", "<f4")])
@@ -95,6 +97,13 @@ def lib():
         "nsn_time_operator": (C.c_int, [_vp, C.c_int32, _fp, _fp]),
         "nsn_operator_sizes": (C.c_int, [_vp, C.POINTER(C.c_int64)]),
         "nsn_apply_operator_noalloc": (C.c_int, [_vp, _vp, _vp, _vp]),
+        "nsn_set_warm_start": (C.c_int, [_vp, C.c_int32]),
+        "nsn_get_warm_stats": (C.c_int, [_vp, _dp, _dp, _ip]),
+        "nsn_mlp_set_params": (C.c_int, [_vp, _fp, C.c_int32]),
+        "nsn_mlp_get_params": (C.c_int, [_vp, _fp, _fp, C.c_int32]),
+        "nsn_mlp_forward": (C.c_int, [_vp, _vp, C.c_int32, _vp]),
+        "nsn_mlp_train_step": (C.c_int, [_vp, _vp, _vp, _vp, C.c_int32, C.c_float, C.POINTER(C.c_float)]),
+        "nsn_contact_features": (C.c_int, [_vp, _vp, _vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -265,6 +274,44 @@ def nsn_apply_operator_noalloc(ctx, x_dev, y_dev, stream=None):
     _check(ctx, lib().nsn_apply_operator_noalloc(ctx, _vp(x_dev), _vp(y_dev), stream), "nsn_apply_operator_noalloc")
 
 
+def nsn_set_warm_start(ctx, mode):
+    _check(ctx, lib().nsn_set_warm_start(ctx, mode), "nsn_set_warm_start")
+
+
+def nsn_get_warm_stats(ctx):
+    mz, mw, rj = C.c_double(), C.c_double(), C.c_int32()
+    _check(ctx, lib().nsn_get_warm_stats(ctx, C.byref(mz), C.byref(mw), C.byref(rj)), "nsn_get_warm_stats")
+    return dict(merit_zero=mz.value, merit_warm=mw.value, rejected=bool(rj.value))
+
+
+def nsn_mlp_set_params(ctx, params):
+    p = np.ascontiguousarray(np.asarray(params, np.float32).ravel())
+    _check(ctx, lib().nsn_mlp_set_params(ctx, _p(p), len(p)), "nsn_mlp_set_params")
+
+
+def nsn_mlp_get_params(ctx):
+    p = np.zeros(NSN_MLP_NPARAM, np.float32)
+    g = np.zeros(NSN_MLP_NPARAM, np.float32)
+    _check(ctx, lib().nsn_mlp_get_params(ctx, _p(p), _p(g), NSN_MLP_NPARAM), "nsn_mlp_get_params")
+    return p, g
+
+
+def nsn_mlp_forward(ctx, X_dev, n, Y_dev):
+    _check(ctx, lib().nsn_mlp_forward(ctx, _vp(X_dev), n, _vp(Y_dev)), "nsn_mlp_forward")
+
+
+def nsn_mlp_train_step(ctx, X_dev, T_dev, w_dev, n, lr):
+    loss = C.c_float()
+    _check(ctx, lib().nsn_mlp_train_step(ctx, _vp(X_dev), _vp(T_dev), _vp(w_dev), n, lr, C.byref(loss)),
+           "nsn_mlp_train_step")
+    return loss.value
+
+
+def nsn_contact_features(ctx, X_dev, Y_dev=0):
+    _check(ctx, lib().nsn_contact_features(ctx, _vp(X_dev) if X_dev else None, _vp(Y_dev) if Y_dev else None),
+           "nsn_contact_features")
+
+
 def nsn_operator_sizes(ctx):
     out = (C.c_int64 * 8)()
     _check(ctx, lib().nsn_operator_sizes(ctx, out), "nsn_operator_sizes")
@@ -399,6 +446,12 @@ class Solver:
 
     def launches_per_step(self):
         return nsn_last_launch_count(self.ctx)
+
+    def set_warm_start(self, mode):
+        nsn_set_warm_start(self.ctx, mode)
+
+    def warm_stats(self):
+        return nsn_get_warm_stats(self.ctx)
 
     def time_operator(self, iters=20):
         return nsn_time_operator(self.ctx, iters)

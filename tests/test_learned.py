@@ -1,0 +1,108 @@
+"""Learned warm start on the GPU: tensor-core forward/backward against the
+FP64 reference network, training, and the warm-start modes of nsn_step."""
+import numpy as np
+import pytest
+
+from oracle import mlp_ref
+from paper_1907_04587_gb300 import learn, nsn, scenes
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    return torch
+
+
+def bf16(a):
+    import torch
+    return torch.tensor(np.asarray(a, np.float32)).to(torch.bfloat16).float().numpy().astype(np.float64)
+
+
+def rel(a, b):
+    return np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b)
+
+
+def test_forward_and_gradients_match_fp64_reference(torch_cuda):
+    torch = torch_cuda
+    rng = np.random.default_rng(1)
+    p = bf16(learn.init_params(3))                 # BF16-representable weights on both sides
+    n = 200                                       # not a multiple of the 64-row tile
+    X = bf16(rng.normal(size=(n, 16)))
+    T = rng.normal(size=(n, 4)).astype(np.float32).astype(np.float64)
+    w = np.array([1.0, 1.0, 1.0, 0.1], np.float32)
+    tr = learn.Trainer(params=p.astype(np.float32))
+    Xd = torch.tensor(X, dtype=torch.float32, device="cuda")
+    Yd = torch.empty((n, 4), dtype=torch.float32, device="cuda")
+    nsn.nsn_mlp_forward(tr.host.ctx, Xd.data_ptr(), n, Yd.data_ptr())
+    torch.cuda.synchronize()
+    y_ref, _ = mlp_ref.forward(p, X)
+    assert rel(Yd.cpu().numpy(), y_ref) < 2e-2
+    Td = torch.tensor(T, dtype=torch.float32, device="cuda")
+    wd = torch.tensor(w, device="cuda")
+    loss = nsn.nsn_mlp_train_step(tr.host.ctx, Xd.data_ptr(), Td.data_ptr(), wd.data_ptr(), n, 0.0)
+    l_ref, g_ref = mlp_ref.loss_and_grad(p, X, T, w.astype(np.float64))
+    assert abs(loss - l_ref) < 2e-2 * l_ref
+    _, g = nsn.nsn_mlp_get_params(tr.host.ctx)
+    G, Gr = mlp_ref.unpack(g), mlp_ref.unpack(g_ref)
+    for name in ("W1", "b1", "W2", "b2", "W3", "b3", "W4", "b4"):
+        assert rel(G[name], Gr[name]) < 5e-2, name
+
+
+def test_training_reduces_loss(torch_cuda):
+    torch = torch_cuda
+    rng = np.random.default_rng(2)
+    teacher = learn.init_params(11) * 0.5
+    X = rng.normal(size=(8192, 16)).astype(np.float32)
+    T, _ = mlp_ref.forward(teacher.astype(np.float64), X.astype(np.float64))
+    tr = learn.Trainer(seed=4)
+    Xd = torch.tensor(X, device="cuda")
+    Td = torch.tensor(T.astype(np.float32), device="cuda")
+    hist = tr.train(Xd, Td, epochs=6, batch=1024, lr=3e-3)
+    assert np.mean(hist[-4:]) < 0.3 * np.mean(hist[:4])
+
+
+def test_warm_start_modes_and_fallback(torch_cuda):
+    s = scenes.batched_envs(seed=9, n_envs=16)
+    base = nsn.Solver(s, newton_iters=4, cr_iters=20)
+    base.step()
+    st = base.get_state()
+    ref = nsn.Solver(s, newton_iters=4, cr_iters=20)
+    ref.step(); ref.set_state(**st); r0 = ref.step()
+    h0 = ref.merit_history()
+    # previous-step warm start: accepted or rejected, never worse at the start
+    g = nsn.Solver(s, newton_iters=4, cr_iters=20)
+    g.step(); g.set_state(**st); g.set_warm_start(nsn.NSN_WARM_PREV)
+    r = g.step()
+    ws = g.warm_stats()
+    assert ws["merit_warm"] <= ws["merit_zero"] or ws["rejected"]
+    assert abs(r["merit0"] - r0["merit0"]) <= 1e-6 * r0["merit0"]
+    # a network with huge outputs: the warm start must be rejected and the step
+    # must then equal the zero-start step
+    bad = learn.init_params(0)
+    bad[-4:] = 1e4
+    b = nsn.Solver(s, newton_iters=4, cr_iters=20)
+    nsn.nsn_mlp_set_params(b.ctx, bad)
+    b.step(); b.set_state(**st); b.set_warm_start(nsn.NSN_WARM_LEARNED)
+    b.step()
+    assert b.warm_stats()["rejected"]
+    np.testing.assert_allclose(b.merit_history(), h0, rtol=1e-5)
+
+
+def test_learned_warm_start_after_training(torch_cuda):
+    """Train on solver-generated pairs of two scenes, evaluate on a held-out
+    seed: the learned start is accepted and lowers the initial merit."""
+    X, T = learn.generate(seeds=[100, 101], n_envs=96)
+    tr = learn.Trainer(seed=1)
+    hist = tr.train(X, T, epochs=8, batch=2048, lr=2e-3)
+    assert hist[-1] < hist[0]
+    res = learn.compare_warm_starts(tr.params(), seed=5000, n_envs=96)
+    for k, v in res.items():
+        print(k, "initial merit/zero", v["warm"]["merit_warm"] / max(v["warm"]["merit_zero"], 1e-30) if k != "zero" else 1.0,
+              "final rel", v["final_rel"], "history", np.round(v["rel"], 3))
+    assert res["learned"]["warm"]["merit_warm"] <= res["learned"]["warm"]["merit_zero"] or res["learned"]["warm"]["rejected"]
