@@ -202,7 +202,8 @@ nsn_status nsn_operator_sizes(nsn_ctx *ctx, int64_t *sizes8);
  * warm starting can improve efficiency.  NSN_WARM_PREV starts from the
  * previous step's multipliers; NSN_WARM_LEARNED sets the contact rows'
  * lambda^0 from a per-contact network (16 features -> 128 -> 128 -> 128 -> 4,
- * ReLU, BF16 tensor-core GEMMs with FP32 accumulation): outputs are the
+ * ReLU, BF16 tensor-core GEMMs with FP32 accumulation; contact rows only,
+ * joint and tet rows start at zero): outputs are the
  * normal and two friction multipliers over the contact's gravity-scaled
  * effective mass |g| / (1/m_a + 1/m_b) and a log preconditioner scale.  In
  * both modes the warm start is kept only if the merit at (u = 0, lambda^0) is
@@ -210,6 +211,11 @@ nsn_status nsn_operator_sizes(nsn_ctx *ctx, int64_t *sizes8);
  * u^0 = 0 in all modes.  The relative merit is always taken against the zero
  * start. */
 enum { NSN_WARM_ZERO = 0, NSN_WARM_PREV = 1, NSN_WARM_LEARNED = 2 };
+/* OR-ed into the mode: warm-start the friction rows too.  By default only the
+ * normal and joint rows are warm started and friction starts at zero: the
+ * friction compliance W of Sec. 4.3 is a fixed point in lambda_f, and a stale
+ * friction state seeds the oscillation of that fixed point. */
+#define NSN_WARM_FRICTION 0x100
 #define NSN_MLP_NPARAM (128 * 16 + 128 + 128 * 128 + 128 + 128 * 128 + 128 + 4 * 128 + 4)
 nsn_status nsn_set_warm_start(nsn_ctx *ctx, int32_t mode);
 /* Merits of the last warm-started step: zero start, warm start, and whether

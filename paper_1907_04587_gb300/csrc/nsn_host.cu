@@ -89,6 +89,7 @@ struct nsn_ctx {
   int lin_buf = 0;           // entry buffer written by the kept linearisation
   int kept_buf = -1;         // entry buffer of the system kept by the last step / linearisation
   int warm_mode = 0;         // NSN_WARM_*
+  int warm_friction = 0;     // 1: warm starts also set the friction rows
   MlpState mlp;
   int built_nb = 0;          // bodies present in the current device build
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -514,9 +515,9 @@ struct Launcher {
     k_merit<T><<<1, RED_THREADS, 0, st>>>(D, -1, 1);
     count++;
     if (c->warm_mode == NSN_WARM_PREV) {
-      if (D.R) { k_copy<T><<<D.nblk_upd, BLOCK, 0, st>>>(D.lam, D.lam_prev, D.R); count++; }
+      if (D.R) { k_warm_from_prev<T><<<D.nblk_upd, BLOCK, 0, st>>>(D, c->warm_friction); count++; }
     } else if (D.nc) {
-      k_warm_from_pred<T><<<cdiv(D.nc, 128), 128, 0, st>>>(D, c->mlp.Y);
+      k_warm_from_pred<T><<<cdiv(D.nc, 128), 128, 0, st>>>(D, c->mlp.Y, c->warm_friction);
       count++;
     }
     eval(0, 1);
@@ -1370,9 +1371,12 @@ nsn_status nsn_operator_sizes(nsn_ctx *c, int64_t *sizes) {
 }
 
 nsn_status nsn_set_warm_start(nsn_ctx *c, int32_t mode) {
-  if (!c || mode < NSN_WARM_ZERO || mode > NSN_WARM_LEARNED) return NSN_ERR_INVALID_ARG;
-  if (mode != c->warm_mode && c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
-  c->warm_mode = mode;
+  if (!c) return NSN_ERR_INVALID_ARG;
+  const int base = mode & 0xff, fric = (mode & NSN_WARM_FRICTION) ? 1 : 0;
+  if (base < NSN_WARM_ZERO || base > NSN_WARM_LEARNED || (mode & ~(0xff | NSN_WARM_FRICTION))) return NSN_ERR_INVALID_ARG;
+  if ((base != c->warm_mode || fric != c->warm_friction) && c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
+  c->warm_mode = base;
+  c->warm_friction = fric;
   return NSN_OK;
 }
 

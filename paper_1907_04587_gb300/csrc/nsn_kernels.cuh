@@ -1343,20 +1343,34 @@ __global__ void k_contact_targets(Dev<T> D, float *Y) {
   Y[4 * size_t(c) + 3] = 0.f;
 }
 
-// lambda^0 from the network outputs: lambda_n >= 0, |lambda_f| <= mu lambda_n
+// lambda^0 from the network outputs: lambda_n >= 0; friction rows start at
+// zero unless warm_friction (then |lambda_f| <= mu lambda_n)
 template <typename T>
-__global__ void k_warm_from_pred(Dev<T> D, const float *Y) {
+__global__ void k_warm_from_pred(Dev<T> D, const float *Y, int warm_friction) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= D.nc) return;
   const T ls = contact_lscale(D, c);
   T ln = T(Y[4 * size_t(c)]) * ls;
   if (!(ln > T(0))) ln = T(0);
-  T f1 = T(Y[4 * size_t(c) + 1]) * ls, f2 = T(Y[4 * size_t(c) + 2]) * ls;
-  const T lim = D.cmu[c] * ln, fn = dsqrt(f1 * f1 + f2 * f2);
-  if (fn > lim) { const T s = fn > T(0) ? lim / fn : T(0); f1 *= s; f2 *= s; }
+  T f1 = T(0), f2 = T(0);
+  if (warm_friction) {
+    f1 = T(Y[4 * size_t(c) + 1]) * ls; f2 = T(Y[4 * size_t(c) + 2]) * ls;
+    const T lim = D.cmu[c] * ln, fn = dsqrt(f1 * f1 + f2 * f2);
+    if (fn > lim) { const T s = fn > T(0) ? lim / fn : T(0); f1 *= s; f2 *= s; }
+  }
   D.lam[3 * c] = ln;
   D.lam[3 * c + 1] = f1;
   D.lam[3 * c + 2] = f2;
+}
+
+// previous-step multipliers as lambda^0; friction rows start at zero unless
+// warm_friction
+template <typename T>
+__global__ void k_warm_from_prev(Dev<T> D, int warm_friction) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < D.R; i += gridDim.x * blockDim.x) {
+    const bool fric = i < 3 * D.nc && (i % 3) != 0;
+    D.lam[i] = (fric && !warm_friction) ? T(0) : D.lam_prev[i];
+  }
 }
 
 // keep the warm start only if its merit is not above the zero start's

@@ -92,7 +92,10 @@ def compare_warm_starts(params, seed, n_envs=256, newton=5, cr=25):
     st = g.get_state()
     lam_prev_state = None
     out = {}
-    for name, mode in (("zero", nsn.NSN_WARM_ZERO), ("prev", nsn.NSN_WARM_PREV), ("learned", nsn.NSN_WARM_LEARNED)):
+    modes = (("zero", nsn.NSN_WARM_ZERO), ("prev", nsn.NSN_WARM_PREV), ("learned", nsn.NSN_WARM_LEARNED),
+             ("prev+friction", nsn.NSN_WARM_PREV | nsn.NSN_WARM_FRICTION),
+             ("learned+friction", nsn.NSN_WARM_LEARNED | nsn.NSN_WARM_FRICTION))
+    for name, mode in modes:
         h = nsn.Solver(s, newton_iters=newton, cr_iters=cr)
         nsn.nsn_mlp_set_params(h.ctx, params)
         h.step()                      # same first step: identical previous multipliers
