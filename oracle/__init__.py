@@ -55,7 +55,8 @@ class _Params(C.Structure):
         ("h", C.c_double), ("gravity", C.c_double * 3), ("newton_iters", C.c_int32),
         ("cr_iters", C.c_int32), ("damping", C.c_double), ("eps", C.c_double),
         ("tol_rel", C.c_double), ("cr_tol_mode", C.c_int32), ("ncp", C.c_int32),
-        ("rscale", C.c_int32), ("geom_stiffness", C.c_int32),
+        ("rscale", C.c_int32), ("geom_stiffness", C.c_int32), ("cone_project", C.c_int32),
+        ("island_stop", C.c_int32),
     ]
 
 
@@ -88,6 +89,10 @@ def lib():
         L.orc_pcr.argtypes = [C.c_void_p, C.c_int32, _dp, _dp]
         L.orc_pcr.restype = C.c_int32
         L.orc_eval_constraints.argtypes = [C.c_void_p, _dp, _dp]
+        L.orc_num_islands.argtypes = [C.c_void_p]
+        L.orc_num_islands.restype = C.c_int32
+        L.orc_get_islands.argtypes = [C.c_void_p, _ip, _ip]
+        L.orc_get_island_stats.argtypes = [C.c_void_p, _dp, _dp, _ip]
         L.orc_fb.restype = C.c_double
         L.orc_fb.argtypes = [C.c_double, C.c_double]
         for f in ("orc_fb_contact", "orc_min_contact"):
@@ -123,7 +128,7 @@ def _ptr(a):
 
 DEFAULT_PARAMS = dict(h=1.0 / 60.0, gravity=(0.0, 0.0, -9.81), newton_iters=4, cr_iters=20,
                       damping=0.75, eps=1e-6, tol_rel=0.0, cr_tol_mode=0, ncp=NCP_FB,
-                      rscale=R_EFFMASS, geom_stiffness=GS_PARTICLES)
+                      rscale=R_EFFMASS, geom_stiffness=GS_PARTICLES, cone_project=0, island_stop=0)
 
 
 class Oracle:
@@ -188,6 +193,8 @@ class Oracle:
         pr.ncp = p["ncp"]
         pr.rscale = p["rscale"]
         pr.geom_stiffness = p["geom_stiffness"]
+        pr.cone_project = p["cone_project"]
+        pr.island_stop = p["island_stop"]
         self._s, self._p = s, pr
         self.ctx = L.orc_create(C.byref(s), C.byref(pr))
         if not self.ctx:
@@ -225,6 +232,22 @@ class Oracle:
         if self.R:
             lib().orc_get_lambda(self.ctx, _ptr(out))
         return out
+
+    def islands(self):
+        """(number of islands, island of each body, island of each row)."""
+        n = lib().orc_num_islands(self.ctx)
+        bi = np.zeros(self.nb, np.int32)
+        ri = np.zeros(max(self.R, 1), np.int32)
+        lib().orc_get_islands(self.ctx, _ptr(bi), _ptr(ri))
+        return n, bi, ri[:self.R]
+
+    def island_stats(self):
+        """Per island of the last step: zero-iterate merit, final merit, and the
+        Newton iteration at which it stopped (-1: not stopped)."""
+        n = lib().orc_num_islands(self.ctx)
+        m0, mf, it = np.zeros(n), np.zeros(n), np.zeros(n, np.int32)
+        lib().orc_get_island_stats(self.ctx, _ptr(m0), _ptr(mf), _ptr(it))
+        return dict(merit0=m0, merit_final=mf, stopped_at=it)
 
     def merit_history(self):
         out = np.zeros(4096)

@@ -62,6 +62,11 @@ struct orc_ctx {
   double *hvec, *g, *b, *pdiag;
   double merit_hist[4096];
   int merit_n;
+  /* islands */
+  int ni;
+  int *body_isl, *row_isl;
+  double *isl_m0, *isl_mf, *isl_acc;
+  int *isl_stop;
 };
 
 /* ------------------------------------------------------------------ */
@@ -306,6 +311,56 @@ static void *dupd(const void *src, size_t n) {
   return p;
 }
 
+/* Islands: union-find over bodies, one union per pair of non-world bodies of
+ * each constraint (every vertex of a tet joins the first).  Island ids follow
+ * the order of each island's lowest body; a row belongs to the island of its
+ * constraint's bodies. */
+static int uf_find(int *par, int x) {
+  while (par[x] != x) { par[x] = par[par[x]]; x = par[x]; }
+  return x;
+}
+static void uf_union(int *par, int a, int b) {
+  if (a < 0 || b < 0) return;
+  a = uf_find(par, a); b = uf_find(par, b);
+  if (a == b) return;
+  if (a < b) par[b] = a; else par[a] = b;
+}
+static void build_islands(orc_ctx *c) {
+  int nb = c->nb;
+  int *par = malloc(sizeof(int) * (nb + 1));
+  for (int i = 0; i < nb; i++) par[i] = i;
+  for (int k = 0; k < c->nc; k++) uf_union(par, c->c_body[2 * k], c->c_body[2 * k + 1]);
+  for (int j = 0; j < c->nj; j++) uf_union(par, c->j_body[2 * j], c->j_body[2 * j + 1]);
+  for (int t = 0; t < c->nt; t++)
+    for (int q = 1; q < 4; q++) uf_union(par, c->t_v[4 * t], c->t_v[4 * t + q]);
+  c->body_isl = malloc(sizeof(int) * (nb + 1));
+  int *id = malloc(sizeof(int) * (nb + 1));
+  for (int i = 0; i < nb; i++) id[i] = -1;
+  c->ni = 0;
+  for (int i = 0; i < nb; i++) {
+    int r = uf_find(par, i);
+    if (id[r] < 0) id[r] = c->ni++;
+    c->body_isl[i] = id[r];
+  }
+  c->row_isl = malloc(sizeof(int) * (c->R + 1));
+  for (int k = 0; k < c->nc; k++) {
+    int a = c->c_body[2 * k] >= 0 ? c->c_body[2 * k] : c->c_body[2 * k + 1];
+    for (int q = 0; q < 3; q++) c->row_isl[3 * k + q] = c->body_isl[a];
+  }
+  for (int j = 0; j < c->nj; j++) {
+    int a = c->j_body[2 * j] >= 0 ? c->j_body[2 * j] : c->j_body[2 * j + 1];
+    for (int q = 0; q < 5; q++) c->row_isl[3 * c->nc + 5 * j + q] = c->body_isl[a];
+  }
+  for (int t = 0; t < c->nt; t++)
+    for (int q = 0; q < 3; q++) c->row_isl[3 * c->nc + 5 * c->nj + 3 * t + q] = c->body_isl[c->t_v[4 * t]];
+  c->isl_m0 = calloc(c->ni + 1, sizeof(double));
+  c->isl_mf = calloc(c->ni + 1, sizeof(double));
+  c->isl_acc = calloc(c->ni + 1, sizeof(double));
+  c->isl_stop = malloc(sizeof(int) * (c->ni + 1));
+  for (int i = 0; i < c->ni; i++) c->isl_stop[i] = -1;
+  free(par); free(id);
+}
+
 orc_ctx *orc_create(const orc_scene *s, const orc_params *prm) {
   if (!s || !prm || s->n_bodies < 0 || s->n_contacts < 0 || s->n_joints < 0 || s->n_tets < 0) return NULL;
   if (!(prm->h > 0.0)) return NULL;
@@ -389,6 +444,7 @@ orc_ctx *orc_create(const orc_scene *s, const orc_params *prm) {
   c->b = calloc(c->R + 1, sizeof(double));
   c->pdiag = calloc(c->R + 1, sizeof(double));
   c->g = calloc(D + 1, sizeof(double));
+  build_islands(c);
   return c;
 }
 
@@ -398,12 +454,25 @@ void orc_destroy(orc_ctx *c) {
                   c->j_body, c->j_pa, c->j_pb, c->j_axa, c->j_axb, c->j_e, c->t_v, c->t_Dminv, c->t_Ve,
                   c->t_C1, c->t_D1, c->t_alpha, c->dof, c->pos, c->quat, c->vel, c->omega, c->lambda,
                   c->pos0, c->quat0, c->Iw, c->Iwinv, c->ut, c->hdiag, c->rows, c->rows_prev, c->cdiag,
-                  c->c3, c->hvec, c->b, c->pdiag, c->g};
+                  c->c3, c->hvec, c->b, c->pdiag, c->g, c->body_isl, c->row_isl, c->isl_m0,
+                  c->isl_mf, c->isl_acc, c->isl_stop};
   for (size_t i = 0; i < sizeof ptrs / sizeof ptrs[0]; i++) free(ptrs[i]);
   free(c);
 }
 
 int32_t orc_num_rows(const orc_ctx *c) { return c->R; }
+int32_t orc_num_islands(const orc_ctx *c) { return c->ni; }
+void orc_get_islands(const orc_ctx *c, int32_t *body_island, int32_t *row_island) {
+  if (body_island) for (int i = 0; i < c->nb; i++) body_island[i] = c->body_isl[i];
+  if (row_island) for (int i = 0; i < c->R; i++) row_island[i] = c->row_isl[i];
+}
+void orc_get_island_stats(const orc_ctx *c, double *merit0, double *merit_final, int32_t *stopped_at) {
+  for (int i = 0; i < c->ni; i++) {
+    if (merit0) merit0[i] = c->isl_m0[i];
+    if (merit_final) merit_final[i] = c->isl_mf[i];
+    if (stopped_at) stopped_at[i] = c->isl_stop[i];
+  }
+}
 int32_t orc_num_dofs(const orc_ctx *c) { return c->D; }
 
 void orc_get_state(const orc_ctx *c, double *pos, double *quat, double *vel, double *omega) {
@@ -778,6 +847,37 @@ static double merit(const orc_ctx *c) {
   return sqrt(s);
 }
 
+/* the same norm restricted to each island: out[i] = ||[g; h]|| over the DOFs
+ * of the island's bodies and the island's rows */
+static void island_merits(const orc_ctx *c, double *out) {
+  for (int i = 0; i < c->ni; i++) out[i] = 0.0;
+  for (int b = 0; b < c->nb; b++)
+    for (int k = c->dof[b]; k < c->dof[b + 1]; k++) out[c->body_isl[b]] += c->g[k] * c->g[k];
+  for (int r = 0; r < c->R; r++) out[c->row_isl[r]] += c->hvec[r] * c->hvec[r];
+  for (int i = 0; i < c->ni; i++) out[i] = sqrt(out[i]);
+}
+
+/* Projection of each contact's multipliers onto {lambda_n >= 0,
+ * |lambda_f| <= mu lambda_n}: the normal is clamped, then the friction pair is
+ * scaled radially.  Not part of the paper's method (cone_project option): the
+ * damped update of Sec. 8.1 leaves lambda_n > 0 on separating contacts, where
+ * the lagged W of Eq. friction_w then grows like 1 / lambda_n while
+ * |lambda_f| / (mu lambda_n) grows each iteration.  Every solution of the
+ * NCPs lies in this set, so the projection changes iterates, not solutions. */
+static void cone_project(const orc_ctx *c, double *lam, const int *isl_stop) {
+  for (int k = 0; k < c->nc; k++) {
+    if (isl_stop && isl_stop[c->row_isl[3 * k]] >= 0) continue;   /* stopped island */
+    double *l = lam + 3 * k;
+    if (l[0] < 0.0) l[0] = 0.0;
+    double lim = c->c_mu[k] * l[0];
+    double f = sqrt(l[1] * l[1] + l[2] * l[2]);
+    if (f > lim) {
+      double s = lim / f;
+      l[1] *= s; l[2] *= s;
+    }
+  }
+}
+
 /* Diagonal geometric stiffness of Sec. 8.3 (particles only, Sec. 11).
  * H~ dU = dg from Eq. broyden_update with H~ = M - K~, K~ = diag(c_k):
  *   c_k = [M du - (g(u^n) - g(u^{n-1}))]_k / du_k,  H~_kk = M_kk - min(0, c_k)
@@ -893,6 +993,82 @@ static int pcr(orc_ctx *c, int iters, double eta, double *x, double *res_hist) {
   return k;
 }
 
+/* The same PCR run on every island at once with the island's own scalars
+ * (rho, alpha, beta, stop tests): A is block diagonal by island, so this is
+ * PCR on each island's system by itself, all capped at iters.  eta[i] is the
+ * island's forcing term (0 = fixed count).  Islands whose flag in skip is set
+ * keep x = 0.  Returns the largest iteration count over the islands. */
+static int pcr_islands(orc_ctx *c, int iters, const double *eta, const int *skip, double *x) {
+  int R = c->R, ni = c->ni;
+  if (R == 0) return 0;
+  double *r = calloc(R, sizeof(double)), *z = calloc(R, sizeof(double)), *p = calloc(R, sizeof(double));
+  double *Az = malloc(sizeof(double) * R), *Ap = malloc(sizeof(double) * R);
+  double *zb = malloc(sizeof(double) * (c->D + 1)), *yb = malloc(sizeof(double) * (c->D + 1));
+  double *rho = calloc(ni + 1, sizeof(double)), *res0 = calloc(ni + 1, sizeof(double));
+  double *acc = calloc(ni + 1, sizeof(double)), *alpha = calloc(ni + 1, sizeof(double));
+  int *done = calloc(ni + 1, sizeof(int)), *its = calloc(ni + 1, sizeof(int));
+  const int *isl = c->row_isl;
+  for (int i = 0; i < ni; i++) done[i] = skip && skip[i];
+  for (int i = 0; i < R; i++) {
+    x[i] = 0.0;
+    r[i] = done[isl[i]] ? 0.0 : c->b[i];
+    z[i] = r[i] / c->pdiag[i]; p[i] = z[i];
+  }
+  apply_A(c, z, Az, zb, yb);
+  for (int i = 0; i < R; i++) { Ap[i] = Az[i]; rho[isl[i]] += z[i] * Az[i]; res0[isl[i]] += r[i] * z[i]; }
+  for (int i = 0; i < ni; i++) res0[i] = sqrt(res0[i]);
+  for (int k = 0; k < iters; k++) {
+    /* stop tests at the top of iteration k, per island */
+    for (int i = 0; i < ni; i++) acc[i] = 0.0;
+    for (int i = 0; i < R; i++) acc[isl[i]] += r[i] * z[i];
+    for (int i = 0; i < ni; i++) {
+      if (done[i]) continue;
+      if (res0[i] == 0.0 || (eta && eta[i] > 0.0 && sqrt(acc[i]) <= eta[i] * res0[i])) done[i] = 1;
+    }
+    for (int i = 0; i < ni; i++) acc[i] = 0.0;
+    for (int i = 0; i < R; i++) acc[isl[i]] += Ap[i] * Ap[i] / c->pdiag[i];   /* Ap^T P Ap */
+    int any = 0;
+    for (int i = 0; i < ni; i++) {
+      if (done[i]) continue;
+      if (!(acc[i] > 0.0)) { done[i] = 1; continue; }
+      alpha[i] = rho[i] / acc[i];
+      its[i] = k + 1;
+      any = 1;
+    }
+    if (!any) break;
+    for (int i = 0; i < R; i++) {
+      if (done[isl[i]]) continue;
+      double a = alpha[isl[i]];
+      x[i] += a * p[i];
+      r[i] -= a * Ap[i];
+      z[i] -= a * Ap[i] / c->pdiag[i];
+    }
+    if (k + 1 == iters) break;
+    /* rows of finished islands hold z = 0 from here on (their x is final) */
+    for (int i = 0; i < R; i++) if (done[isl[i]]) z[i] = 0.0;
+    apply_A(c, z, Az, zb, yb);
+    for (int i = 0; i < ni; i++) acc[i] = 0.0;
+    for (int i = 0; i < R; i++) acc[isl[i]] += z[i] * Az[i];
+    for (int i = 0; i < ni; i++) {
+      if (done[i]) continue;
+      if (!(acc[i] > 0.0)) { done[i] = 1; continue; }   /* exact convergence: z = 0 */
+      alpha[i] = acc[i] / rho[i];                        /* beta of this island */
+      rho[i] = acc[i];
+    }
+    for (int i = 0; i < R; i++) {
+      if (done[isl[i]]) continue;
+      double beta = alpha[isl[i]];
+      p[i] = z[i] + beta * p[i];
+      Ap[i] = Az[i] + beta * Ap[i];
+    }
+  }
+  int kmax = 0;
+  for (int i = 0; i < ni; i++) if (its[i] > kmax) kmax = its[i];
+  free(r); free(z); free(p); free(Az); free(Ap); free(zb); free(yb);
+  free(rho); free(res0); free(acc); free(alpha); free(done); free(its);
+  return kmax;
+}
+
 /* ------------------------------------------------------------------ */
 /* Newton loop (Algorithm 1, Sec. 6, Sec. 8)                            */
 
@@ -919,6 +1095,7 @@ static double zero_iterate_merit(orc_ctx *c, orc_work *w) {
   eval_rows(c, w->u, zl);
   compute_g(c, w->u, zl, w->zb);
   double m = merit(c);
+  island_merits(c, c->isl_m0);
   free(zl);
   return m;
 }
@@ -936,6 +1113,8 @@ static int newton(orc_ctx *c, const double *lambda0, int stop_at, orc_stats *st,
   c->merit_n = 0;
   int cr_total = 0, n = 0;
   double mfirst = 0.0;
+  const int isl = c->p.island_stop && c->p.tol_rel > 0.0;
+  for (int i = 0; i < c->ni; i++) c->isl_stop[i] = -1;
   for (n = 0; n < c->p.newton_iters || n == stop_at; n++) {
     eval_rows(c, w->u, lam);
     compute_g(c, w->u, lam, w->zb);
@@ -948,17 +1127,46 @@ static int newton(orc_ctx *c, const double *lambda0, int stop_at, orc_stats *st,
     if (n > 0 && c->p.geom_stiffness == ORC_GS_PARTICLES) geometric_stiffness(c, w->u, w->uprev, lam, w->zb, w->zb2);
     build_rhs(c, w->yb);
     if (n == stop_at) break;
-    if (c->p.tol_rel > 0.0 && mn <= c->p.tol_rel * m0) break;
-    double eta = 0.0;
-    if (c->p.cr_tol_mode) { eta = m0 > 0.0 ? mn / m0 : 0.0; if (eta > 0.1) eta = 0.1; if (eta <= 0.0) eta = 1e-30; }
-    cr_total += pcr(c, c->p.cr_iters, eta, w->dl, NULL);
+    if (isl) {
+      /* per-island stop: an island that reached tol_rel keeps its iterate */
+      island_merits(c, c->isl_acc);
+      int left = 0;
+      for (int i = 0; i < c->ni; i++) {
+        if (c->isl_stop[i] < 0 && c->isl_acc[i] <= c->p.tol_rel * c->isl_m0[i]) c->isl_stop[i] = n;
+        left += c->isl_stop[i] < 0;
+      }
+      if (!left) break;
+    } else if (c->p.tol_rel > 0.0 && mn <= c->p.tol_rel * m0) break;
+    if (isl) {
+      /* per-island CR (island_stop): forcing term from the island's own merit */
+      double *eta_i = calloc(c->ni + 1, sizeof(double));
+      int *skip = calloc(c->ni + 1, sizeof(int));
+      for (int i = 0; i < c->ni; i++) {
+        skip[i] = c->isl_stop[i] >= 0;
+        if (c->p.cr_tol_mode) {
+          double e = c->isl_m0[i] > 0.0 ? c->isl_acc[i] / c->isl_m0[i] : 0.0;
+          eta_i[i] = e > 0.1 ? 0.1 : (e <= 0.0 ? 1e-30 : e);
+        }
+      }
+      cr_total += pcr_islands(c, c->p.cr_iters, eta_i, skip, w->dl);
+      free(eta_i); free(skip);
+    } else {
+      double eta = 0.0;
+      if (c->p.cr_tol_mode) { eta = m0 > 0.0 ? mn / m0 : 0.0; if (eta > 0.1) eta = 0.1; if (eta <= 0.0) eta = 1e-30; }
+      cr_total += pcr(c, c->p.cr_iters, eta, w->dl, NULL);
+    }
     /* du = H~^-1 (h J^T dl - g)  (Sec. 6.2) */
     JT_x(c, w->dl, w->zb);
     for (int k = 0; k < c->D; k++) w->zb[k] = h * w->zb[k] - c->g[k];
     Hinv_z(c, w->zb, w->du);
+    if (isl)
+      for (int b = 0; b < c->nb; b++)
+        if (c->isl_stop[c->body_isl[b]] >= 0)
+          for (int k = c->dof[b]; k < c->dof[b + 1]; k++) w->du[k] = 0.0;
     memcpy(w->uprev, w->u, sizeof(double) * c->D);
     memcpy(c->rows_prev, c->rows, sizeof(orc_row) * c->R);
     for (int i = 0; i < c->R; i++) lam[i] += t * w->dl[i];
+    if (c->p.cone_project) cone_project(c, lam, isl ? c->isl_stop : NULL);
     for (int k = 0; k < c->D; k++) w->u[k] += t * w->du[k];
     positions_from_u(c, w->u);
   }
@@ -966,6 +1174,7 @@ static int newton(orc_ctx *c, const double *lambda0, int stop_at, orc_stats *st,
     eval_rows(c, w->u, lam);
     compute_g(c, w->u, lam, w->zb);
     double mf = merit(c);
+    island_merits(c, c->isl_mf);
     if (c->merit_n < 4096) c->merit_hist[c->merit_n++] = mf;
     if (st) { st->merit_final = mf; }
     /* commit: u^+ and q^+ */

@@ -77,6 +77,14 @@ typedef struct {
   int32_t ncp;              /* ORC_NCP_FB / ORC_NCP_MIN */
   int32_t rscale;           /* ORC_R_* */
   int32_t geom_stiffness;   /* ORC_GS_* */
+  int32_t cone_project;     /* 1: after each damped update, lambda_n := max(lambda_n, 0) and
+                               lambda_f scaled into |lambda_f| <= mu lambda_n (not in the
+                               paper; the printed method is 0) */
+  int32_t island_stop;      /* 1: tol_rel is applied per island (connected component of
+                               bodies through constraints, the static world excluded): an
+                               island whose merit reaches tol_rel times its own zero-iterate
+                               merit keeps its u and lambda from then on; the step ends when
+                               every island has stopped or after newton_iters */
 } orc_params;
 
 typedef struct {
@@ -106,6 +114,15 @@ void orc_set_state(orc_ctx *ctx, const double *pos, const double *quat, const do
 void orc_get_lambda(const orc_ctx *ctx, double *lambda);
 /* Merit after each Newton iteration of the last step (up to newton_iters+1). */
 int32_t orc_get_merit_history(const orc_ctx *ctx, double *out, int32_t cap);
+
+/* Islands: number, the island of each body (nb) and of each row (R), any
+ * pointer may be NULL.  Islands are numbered in order of their lowest body. */
+int32_t orc_num_islands(const orc_ctx *ctx);
+void orc_get_islands(const orc_ctx *ctx, int32_t *body_island, int32_t *row_island);
+/* Per island for the last step: merit at the zero iterate, merit at the
+ * returned iterate, and the Newton iteration at which it stopped (-1 if it
+ * did not reach tol_rel).  Any pointer may be NULL. */
+void orc_get_island_stats(const orc_ctx *ctx, double *merit0, double *merit_final, int32_t *stopped_at);
 
 /* Debug / test access to one linearisation.  Runs the first n_before Newton
  * iterations of a step from the current state (without committing), then

@@ -38,7 +38,9 @@ def test_config_struct_and_defaults(libnsn):
     cfg = nsn.nsn_default_config()
     assert abs(cfg.h - 1.0 / 60.0) < 1e-15 and cfg.newton_iters == 4 and cfg.cr_iters == 20
     assert cfg.damping == 0.75 and cfg.eps == 1e-6 and cfg.precision == nsn.NSN_FP32
-    assert ctypes.sizeof(nsn.nsn_config) == 88
+    assert cfg.cone_project == 0 and cfg.island_stop == 0    # the printed method, one system
+    # h, gravity[3], 2 ints, damping, eps, tol_rel, 8 ints
+    assert ctypes.sizeof(nsn.nsn_config) == 8 * 4 + 4 * 2 + 8 * 3 + 4 * 8
 
 
 def test_invalid_arguments_are_rejected_without_gpu(libnsn):
