@@ -79,10 +79,26 @@ typedef struct {
   int32_t precision;      /* NSN_FP32 bulk arithmetic or NSN_FP64 throughout;
                              CR scalars and the merit are FP64 in both */
   int32_t use_graph;      /* 1: capture the step as one CUDA graph and replay it */
+  int32_t cone_project;   /* 1: after each damped update (Sec. 8.1) set lambda_n :=
+                             max(lambda_n, 0) and scale lambda_f into |lambda_f| <=
+                             mu lambda_n.  Not in the paper (0 = the printed method):
+                             on separating sliding contacts the damped update leaves
+                             lambda_n > 0, the lagged W of Sec. 4.3 grows like
+                             1/lambda_n and |lambda_f|/(mu lambda_n) grows every
+                             iteration.  Solutions of the NCPs already lie in this set. */
+  int32_t island_stop;    /* 1: islands (connected components of the bodies through
+                             constraints, the static world excluded) are solved side by
+                             side: each has its own merit, its own zero-iterate merit
+                             for tol_rel, its own CR scalars (A of Eq. schur_system is
+                             block diagonal by island, so this is CR on each island's
+                             system alone) and its own warm-start acceptance; an island
+                             that reaches tol_rel keeps its u and lambda, and the step
+                             ends when all have stopped or after newton_iters */
 } nsn_config;
 
 /* Fills the paper's defaults: h = 1/60, g = (0, 0, -9.81), 4 x 20 iterations,
- * t = 0.75, eps = 1e-6, FB, effective-mass r, GS on particles, FP32, graph on. */
+ * t = 0.75, eps = 1e-6, FB, effective-mass r, GS on particles, FP32, graph on,
+ * no cone projection, one system (no islands). */
 void nsn_default_config(nsn_config *cfg);
 
 typedef struct {
@@ -218,8 +234,26 @@ enum { NSN_WARM_ZERO = 0, NSN_WARM_PREV = 1, NSN_WARM_LEARNED = 2 };
 #define NSN_WARM_FRICTION 0x100
 #define NSN_MLP_NPARAM (128 * 16 + 128 + 128 * 128 + 128 + 128 * 128 + 128 + 4 * 128 + 4)
 nsn_status nsn_set_warm_start(nsn_ctx *ctx, int32_t mode);
+/* Islands of the current scene: *n_islands, and the island of each body
+ * (host array of the body count, may be NULL).  Islands are numbered in the
+ * order of their lowest body id; they do not depend on island_stop. */
+nsn_status nsn_islands(nsn_ctx *ctx, int32_t *n_islands, int32_t *body_island);
+
+/* Per island, for the last nsn_step with island_stop = 1 (host arrays of cap
+ * >= n_islands entries, any may be NULL): merit at the zero iterate, merit at
+ * the returned iterate, and the Newton iteration at which the island stopped
+ * (-1: it did not reach tol_rel within newton_iters). */
+nsn_status nsn_island_stats(nsn_ctx *ctx, int32_t cap, double *merit0, double *merit_final,
+                            int32_t *stopped_at);
+
+/* Device pointer to the per-island stop iterations above (n_islands int32,
+ * owned by the context, valid until the scene changes; written by each step
+ * on the context stream).  For on-device bookkeeping between steps. */
+nsn_status nsn_island_stop_device(nsn_ctx *ctx, const int32_t **stopped_at);
+
 /* Merits of the last warm-started step: zero start, warm start, and whether
- * the warm start was rejected. */
+ * the warm start was rejected (island_stop = 1: the number of islands where
+ * it was rejected and the zero start kept). */
 nsn_status nsn_get_warm_stats(nsn_ctx *ctx, double *merit_zero, double *merit_warm, int32_t *rejected);
 /* Network parameters (host, NSN_MLP_NPARAM floats): W1[128][16], b1[128],
  * W2[128][128], b2, W3[128][128], b3, W4[4][128], b4[4]; y = W x + b.  Setting

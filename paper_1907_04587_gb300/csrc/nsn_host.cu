@@ -50,6 +50,9 @@ struct Layout {
   std::vector<int> bmap;            // ABI body id -> encoded (>=0 rigid, <=-2 particle)
   std::vector<int> rig_of, par_of;  // local index -> ABI id
   std::vector<int> eslot, rseg, vseg, re0, re1, te;
+  int ni = 0;                       // islands: connected components of bodies through constraints
+  std::vector<int> body_isl;        // ABI body id -> island
+  std::vector<int> risl, bisl_r, bisl_p;  // island of each row / rigid body / particle
 };
 
 struct MlpState {
@@ -125,6 +128,56 @@ bool finite_all(const float *p, size_t n) {
 }
 
 // ------------------------------------------------------------------------------------
+// islands: union-find over the bodies of every constraint (the static world is
+// not a node); ids follow the order of each island's lowest body, and a row
+// belongs to the island of its constraint's bodies
+
+int uf_find(std::vector<int> &par, int x) {
+  while (par[x] != x) { par[x] = par[par[x]]; x = par[x]; }
+  return x;
+}
+void uf_union(std::vector<int> &par, int a, int b) {
+  if (a < 0 || b < 0) return;
+  a = uf_find(par, a); b = uf_find(par, b);
+  if (a == b) return;
+  if (a < b) par[b] = a; else par[a] = b;
+}
+
+void build_islands(const HostScene &S, Layout &L, int nb) {
+  std::vector<int> par(nb);
+  for (int i = 0; i < nb; i++) par[i] = i;
+  for (const auto &r : S.contacts) uf_union(par, r.body_a, r.body_b);
+  for (const auto &r : S.joints) uf_union(par, r.body_a, r.body_b);
+  for (const auto &r : S.tets)
+    for (int q = 1; q < 4; q++) uf_union(par, r.v[0], r.v[q]);
+  std::vector<int> id(nb, -1);
+  L.body_isl.assign(nb, 0);
+  L.ni = 0;
+  for (int i = 0; i < nb; i++) {
+    const int r = uf_find(par, i);
+    if (id[r] < 0) id[r] = L.ni++;
+    L.body_isl[i] = id[r];
+  }
+  L.bisl_r.resize(L.nr);
+  L.bisl_p.resize(L.np);
+  for (int i = 0; i < L.nr; i++) L.bisl_r[i] = L.body_isl[L.rig_of[i]];
+  for (int i = 0; i < L.np; i++) L.bisl_p[i] = L.body_isl[L.par_of[i]];
+  L.risl.assign(L.R, 0);
+  for (int ci = 0; ci < L.nc; ci++) {
+    const auto &r = S.contacts[ci];
+    const int isl = L.body_isl[r.body_a >= 0 ? r.body_a : r.body_b];
+    for (int k = 0; k < 3; k++) L.risl[3 * ci + k] = isl;
+  }
+  for (int j = 0; j < L.nj; j++) {
+    const auto &r = S.joints[j];
+    const int isl = L.body_isl[r.body_a >= 0 ? r.body_a : r.body_b];
+    for (int k = 0; k < 5; k++) L.risl[3 * L.nc + 5 * j + k] = isl;
+  }
+  for (int t = 0; t < L.nt; t++)
+    for (int k = 0; k < 3; k++) L.risl[L.Rpair + 3 * t + k] = L.body_isl[S.tets[t].v[0]];
+}
+
+// ------------------------------------------------------------------------------------
 // layout: entries sorted by body (counting sort), rows -> entry ids
 
 nsn_status build_layout(nsn_ctx *c) {
@@ -195,6 +248,7 @@ nsn_status build_layout(nsn_ctx *c) {
       L.eslot[e] = 2 * L.Rpair + 12 * t + 4 * k + s.slot;
     }
   }
+  build_islands(S, L, nb);
   return NSN_OK;
 }
 
@@ -240,6 +294,16 @@ void carve(Arena &A, Dev<T> &D, const Layout &L, int nb) {
   D.part_row = A.take<typename RedT<T>::type>(2 * kMaxBlocks * NPART);
   D.sc = A.take<Scalars>(1);
   D.fl = A.take<Flags>(1);
+  D.risl = A.take<int>(L.R);
+  D.bisl_r = A.take<int>(L.nr);
+  D.bisl_p = A.take<int>(L.np);
+  const int ni = std::max(L.ni, 1);
+  D.isl.acc = A.take<double>(size_t(ISL_ACC) * ni);
+  D.isl.m0 = A.take<double>(ni); D.isl.mf = A.take<double>(ni); D.isl.mw = A.take<double>(ni);
+  D.isl.eta = A.take<double>(ni); D.isl.res0 = A.take<double>(ni); D.isl.rho = A.take<double>(2 * size_t(ni));
+  D.isl.alpha = A.take<double>(ni); D.isl.beta = A.take<double>(ni);
+  D.isl.alpha_f = A.take<float>(ni); D.isl.beta_f = A.take<float>(ni);
+  D.isl.stop = A.take<int>(ni); D.isl.crdone = A.take<int>(ni);
   (void)nb;
 }
 
@@ -253,6 +317,9 @@ void fill_sizes(Dev<T> &D, const Layout &L, const nsn_config &cfg) {
   for (int k = 0; k < 3; k++) D.gravT[k] = T(cfg.gravity[k]);
   D.ncp = cfg.ncp; D.rscale = cfg.rscale; D.gs = cfg.geom_stiffness; D.cr_tol = cfg.cr_tol_mode;
   D.warm = 0;
+  D.ni = L.ni;
+  D.isl_on = cfg.island_stop ? 1 : 0;
+  D.cone = cfg.cone_project ? 1 : 0;
   D.nblk_body_r = L.nr ? clampb(cdiv((long long)L.nr * kGroup, BLOCK)) : 0;
   D.nblk_body_p = L.np ? clampb(cdiv((long long)L.np * kGroup, BLOCK)) : 0;
   D.nblk_row_pair = L.Rpair ? clampb(cdiv(L.Rpair, BLOCK)) : 0;
@@ -369,6 +436,18 @@ nsn_status upload(nsn_ctx *c, Dev<T> &D) {
   CUDA_TRY(c, cudaMemsetAsync(D.lam_prev, 0, sizeof(T) * std::max(L.R, 1), st));
   CUDA_TRY(c, cudaMemsetAsync(D.sc, 0, sizeof(Scalars), st));
   CUDA_TRY(c, cudaMemsetAsync(D.fl, 0, sizeof(Flags), st));
+  CUDA_TRY(c, puti(D.risl, L.risl));
+  CUDA_TRY(c, puti(D.bisl_r, L.bisl_r));
+  CUDA_TRY(c, puti(D.bisl_p, L.bisl_p));
+  {
+    const size_t ni = size_t(std::max(L.ni, 1));
+    CUDA_TRY(c, cudaMemsetAsync(D.isl.acc, 0, sizeof(double) * ISL_ACC * ni, st));
+    CUDA_TRY(c, cudaMemsetAsync(D.isl.m0, 0, sizeof(double) * ni, st));
+    CUDA_TRY(c, cudaMemsetAsync(D.isl.mf, 0, sizeof(double) * ni, st));
+    CUDA_TRY(c, cudaMemsetAsync(D.isl.mw, 0, sizeof(double) * ni, st));
+    CUDA_TRY(c, cudaMemsetAsync(D.isl.stop, 0xff, sizeof(int) * ni, st));
+    CUDA_TRY(c, cudaMemsetAsync(D.isl.crdone, 0, sizeof(int) * ni, st));
+  }
   for (int b2 = 0; b2 < 2; b2++)
     for (int k = 0; k < 3; k++)
       if (L.EV) CUDA_TRY(c, cudaMemsetAsync(D.ej3[b2][k], 0, sizeof(T) * L.EV, st));
@@ -467,7 +546,10 @@ struct Launcher {
   void rows(int mode, int force) {
     int nb = D.nblk_row_pair + D.nblk_row_tet;
     if (!nb) return;
-    if (mode == RM_RHS) k_row_pass<T, RM_RHS><<<nb, BLOCK, 0, st>>>(D, force);
+    if (D.isl_on) {
+      if (mode == RM_RHS) k_row_pass_isl<T, RM_RHS><<<nb, BLOCK, 0, st>>>(D, force);
+      else k_row_pass_isl<T, RM_APPLY><<<nb, BLOCK, 0, st>>>(D, force);
+    } else if (mode == RM_RHS) k_row_pass<T, RM_RHS><<<nb, BLOCK, 0, st>>>(D, force);
     else k_row_pass<T, RM_APPLY><<<nb, BLOCK, 0, st>>>(D, force);
     count++;
   }
@@ -479,6 +561,10 @@ struct Launcher {
   void begin() {
     // plain start of Sec. 8.1: lambda^0 = 0 (u^0 = 0 is set by the begin kernels)
     if (D.R) cudaMemsetAsync(D.lam, 0, sizeof(T) * D.R, st);
+    if (D.isl_on && D.ni) {
+      cudaMemsetAsync(D.isl.stop, 0xff, sizeof(int) * D.ni, st);
+      cudaMemsetAsync(D.isl.acc, 0, sizeof(double) * ISL_ACC * D.ni, st);
+    }
     k_begin_rigid<T><<<cdiv(std::max(D.nr, 1), 128), 128, 0, st>>>(D);
     count++;
     if (D.np) { k_begin_particle<T><<<cdiv(D.np, 128), 128, 0, st>>>(D); count++; }
@@ -496,8 +582,13 @@ struct Launcher {
     for (int k = 0; k < iters; k++) {
       body(BM_APPLY, D.z, buf, 0, 0);
       rows(RM_APPLY, 0);
-      k_cr_scalars<T><<<1, RED_THREADS, 0, st>>>(D, k);
-      k_cr_update<T><<<D.nblk_upd, BLOCK, 0, st>>>(D, k);
+      if (D.isl_on) {
+        k_cr_scalars_isl<T><<<cdiv(std::max(D.ni, 1), 256), 256, 0, st>>>(D, k);
+        k_cr_update_isl<T><<<D.nblk_upd, BLOCK, 0, st>>>(D, k);
+      } else {
+        k_cr_scalars<T><<<1, RED_THREADS, 0, st>>>(D, k);
+        k_cr_update<T><<<D.nblk_upd, BLOCK, 0, st>>>(D, k);
+      }
       count += 2;
     }
   }
@@ -691,7 +782,8 @@ bool valid_cfg(const nsn_config *cfg) {
   return cfg && cfg->h > 0 && cfg->newton_iters >= 0 && cfg->newton_iters < 1000 && cfg->cr_iters >= 0 &&
          cfg->damping > 0 && cfg->damping <= 1 && cfg->eps >= 0 && cfg->tol_rel >= 0 &&
          (cfg->precision == NSN_FP32 || cfg->precision == NSN_FP64) && (cfg->ncp == 0 || cfg->ncp == 1) &&
-         cfg->rscale >= 0 && cfg->rscale <= 2;
+         cfg->rscale >= 0 && cfg->rscale <= 2 && (cfg->cone_project == 0 || cfg->cone_project == 1) &&
+         (cfg->island_stop == 0 || cfg->island_stop == 1);
 }
 
 template <typename T>
@@ -1055,6 +1147,8 @@ void nsn_default_config(nsn_config *cfg) {
   cfg->geom_stiffness = NSN_GS_PARTICLES;
   cfg->precision = NSN_FP32;
   cfg->use_graph = 1;
+  cfg->cone_project = 0;
+  cfg->island_stop = 0;
 }
 
 nsn_status nsn_create(const nsn_config *cfg, void *stream, nsn_ctx **out) {
@@ -1377,6 +1471,40 @@ nsn_status nsn_set_warm_start(nsn_ctx *c, int32_t mode) {
   if ((base != c->warm_mode || fric != c->warm_friction) && c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
   c->warm_mode = base;
   c->warm_friction = fric;
+  return NSN_OK;
+}
+
+nsn_status nsn_islands(nsn_ctx *c, int32_t *n_islands, int32_t *body_island) {
+  if (!c || !n_islands) return NSN_ERR_INVALID_ARG;
+  nsn_status s = ensure_built(c);
+  if (s != NSN_OK) return s;
+  *n_islands = c->L.ni;
+  if (body_island) std::copy(c->L.body_isl.begin(), c->L.body_isl.end(), body_island);
+  return NSN_OK;
+}
+
+nsn_status nsn_island_stats(nsn_ctx *c, int32_t cap, double *merit0, double *merit_final, int32_t *stopped_at) {
+  if (!c) return NSN_ERR_INVALID_ARG;
+  nsn_status s = ensure_built(c);
+  if (s != NSN_OK) return s;
+  const int ni = c->L.ni;
+  if (cap < ni) return fail(c, NSN_ERR_INVALID_ARG, "nsn_island_stats: cap %d < %d islands", cap, ni);
+  if (!ni) return NSN_OK;
+  const bool f64 = c->cfg.precision == NSN_FP64;
+  const IslState &I = f64 ? c->d64.isl : c->d32.isl;
+  cudaStream_t st = c->stream;
+  if (merit0) CUDA_TRY(c, cudaMemcpyAsync(merit0, I.m0, sizeof(double) * ni, cudaMemcpyDeviceToHost, st));
+  if (merit_final) CUDA_TRY(c, cudaMemcpyAsync(merit_final, I.mf, sizeof(double) * ni, cudaMemcpyDeviceToHost, st));
+  if (stopped_at) CUDA_TRY(c, cudaMemcpyAsync(stopped_at, I.stop, sizeof(int32_t) * ni, cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(c, cudaStreamSynchronize(st));
+  return NSN_OK;
+}
+
+nsn_status nsn_island_stop_device(nsn_ctx *c, const int32_t **stopped_at) {
+  if (!c || !stopped_at) return NSN_ERR_INVALID_ARG;
+  nsn_status s = ensure_built(c);
+  if (s != NSN_OK) return s;
+  *stopped_at = c->cfg.precision == NSN_FP64 ? c->d64.isl.stop : c->d32.isl.stop;
   return NSN_OK;
 }
 

@@ -38,6 +38,24 @@ struct Flags {
   int cr_stop;       // set when the CR tolerance is met in this Newton iteration
   int newton_count;  // Newton iterations solved
   int cr_count;      // CR iterations performed (all Newton iterations)
+  int isl_ticket;    // blocks of the island CR scalar kernel that have finished
+  int isl_active;    // islands still iterating in this CR iteration
+};
+
+// Per-island FP64 state (island mode): islands are the connected components
+// of the bodies through constraints.  Accumulators are indexed [slot * ni + i]:
+//   slot 0: |g|^2 + |h|^2 of the island (merit^2),  slot 1: b^T P b,
+//   slots 2..6: the CR partials d1..d5 of one CR iteration.
+constexpr int ISL_ACC = 7;
+struct IslState {
+  double *acc;
+  double *m0, *mf, *mw;      // zero-iterate, final and warm-start merits
+  double *eta, *res0;        // CR forcing term and ||r_0||_P of the Newton iteration
+  double *rho;               // [2][ni], double-buffered by CR iteration parity
+  double *alpha, *beta;
+  float *alpha_f, *beta_f;
+  int *stop;                 // Newton iteration at which the island stopped, -1 while iterating
+  int *crdone;               // 1: the island's CR is finished in this Newton iteration
 };
 
 // FP64 scalars kept on the device
@@ -51,7 +69,8 @@ struct Scalars {
   double alpha, beta;   // CR step of the current iteration
   float alpha_f, beta_f; // the same, rounded once for the FP32 update kernel
   double merit_warm;    // merit at the warm-started iterate (u = 0, lambda^0)
-  int warm_rejected;    // 1 if the warm start was worse than the zero start
+  int warm_rejected;    // 1 if the warm start was worse than the zero start (island
+                        // mode: the number of islands where it was)
 };
 
 struct DS {
@@ -111,7 +130,42 @@ struct Dev {
   int nblk_body_r, nblk_body_p, nblk_row_pair, nblk_row_tet, nblk_upd;
   Scalars *sc;
   Flags *fl;
+  // islands
+  int ni;            // number of islands
+  int isl_on;        // 1: per-island Newton stop, warm-start acceptance and CR scalars
+  int cone;          // 1: project contact multipliers onto the friction cone after each update
+  int *risl;         // island of each row
+  int *bisl_r, *bisl_p;  // island of each rigid body / particle
+  IslState isl;
 };
+
+// ------------------------------------------------------------------------------------
+// Per-island sums.  The lanes of a warp hold values keyed by island; runs of
+// equal consecutive keys are summed by a segmented suffix scan (Hillis-Steele:
+// after the step of offset o a lane holds the sum of its run over the next 2o
+// lanes) and the first lane of each run adds the run's sum to the island's
+// FP64 accumulator.  Keys < 0 contribute nothing.  Rows and bodies of one
+// island are mostly consecutive, so a warp issues few atomics; a key that
+// recurs in two runs adds twice, which is still the right sum.
+template <typename V, int NV>
+__device__ __forceinline__ void warp_runs_add(int key, V (&v)[NV], double *acc, int stride) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int prev = __shfl_up_sync(full, key, 1);
+  const unsigned head = __ballot_sync(full, lane == 0 || key != prev);
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const bool same = lane + o < 32 && !(head & (((1u << o) - 1u) << (lane + 1)));
+#pragma unroll
+    for (int k = 0; k < NV; k++) {
+      const V w = __shfl_down_sync(full, v[k], o);
+      if (same) v[k] += w;
+    }
+  }
+  if (key >= 0 && ((head >> lane) & 1u))
+#pragma unroll
+    for (int k = 0; k < NV; k++) atomicAdd(acc + size_t(k) * stride + key, double(v[k]));
+}
 
 // ------------------------------------------------------------------------------------
 // small math
@@ -526,6 +580,7 @@ __global__ void k_eval_contacts(Dev<T> D, int buf, int force) {
   if (!force && D.fl->newton_stop) return;
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= D.nc) return;
+  if (!force && D.isl_on && D.isl.stop[D.risl[3 * c]] >= 0) return;   // stopped island
   const T h = D.hT;
   T pa[3], pb[3], n[3];
   for (int k = 0; k < 3; k++) { pa[k] = D.cpa[k][c]; pb[k] = D.cpb[k][c]; n[k] = D.cn[k][c]; }
@@ -612,6 +667,7 @@ __global__ void k_eval_joints(Dev<T> D, int buf, int force) {
   if (!force && D.fl->newton_stop) return;
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= D.nj) return;
+  if (!force && D.isl_on && D.isl.stop[D.risl[3 * D.nc + 5 * j]] >= 0) return;   // stopped island
   const T h = D.hT;
   T pa[3], pb[3], axa[3], axb[3];
   for (int k = 0; k < 3; k++) { pa[k] = D.jpa[k][j]; pb[k] = D.jpb[k][j]; axa[k] = D.jaxa[k][j]; axb[k] = D.jaxb[k][j]; }
@@ -675,6 +731,7 @@ __global__ void k_eval_tets(Dev<T> D, int buf, int force) {
   if (!force && D.fl->newton_stop) return;
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= D.nt) return;
+  if (!force && D.isl_on && D.isl.stop[D.risl[D.Rpair + 3 * t]] >= 0) return;   // stopped island
   const T h = D.hT;
   int v[4];
   for (int q = 0; q < 4; q++) v[q] = D.tv[4 * t + q];
@@ -748,6 +805,15 @@ __device__ __forceinline__ int slot_row(int slot, int Rpair) {
 //   q = q^- + h G(q^-) u with quaternion normalisation.
 // The first KR entries of each lane stay in registers between the J^T x
 // gather and the per-entry write, so J is read once; longer segments loop.
+// island mode: bodies whose island needs no work in this pass (CR finished
+// for the operator apply, island stopped for the residual and the update)
+template <int MODE, typename T>
+__device__ __forceinline__ bool isl_skip(const Dev<T> &D, int is, int force) {
+  if (MODE == BM_APPLY) return D.isl.crdone[is] != 0;
+  if (force) return false;
+  return D.isl.stop[is] >= 0;
+}
+
 template <typename T, int G, int MODE>
 __global__ void __launch_bounds__(BLOCK) k_body_pass(Dev<T> D, const T *__restrict__ in, int buf, int newton_it, int force) {
   if (!force && D.fl->newton_stop) return;
@@ -763,7 +829,8 @@ __global__ void __launch_bounds__(BLOCK) k_body_pass(Dev<T> D, const T *__restri
     const int stride = D.nblk_body_r * gpb;
     for (int b0 = blockIdx.x * gpb; b0 < D.nr; b0 += stride) {
       const int b = b0 + gid;
-      const bool act = b < D.nr;
+      bool act = b < D.nr;
+      if (act && D.isl_on && isl_skip<MODE>(D, D.bisl_r[b], force)) act = false;
       int s0 = 0, s1 = 0;
       if (act) { s0 = D.rseg[b]; s1 = D.rseg[b + 1]; }
       int sl[KR];
@@ -852,6 +919,12 @@ __global__ void __launch_bounds__(BLOCK) k_body_pass(Dev<T> D, const T *__restri
         if (lane == 0) {
 #pragma unroll
           for (int k = 0; k < 6; k++) { D.rg[k][b] = g[k]; D.ryg[k][b] = y[k]; acc_g2.add_prod(g[k], g[k]); }
+          if (D.isl_on) {
+            T gg = T(0);
+#pragma unroll
+            for (int k = 0; k < 6; k++) gg += g[k] * g[k];
+            atomicAdd(D.isl.acc + D.bisl_r[b], double(gg));
+          }
         }
       }
 #pragma unroll
@@ -891,7 +964,8 @@ __global__ void __launch_bounds__(BLOCK) k_body_pass(Dev<T> D, const T *__restri
     const bool gs = MODE == BM_RESIDUAL && D.gs && newton_it > 0;
     for (int b0 = bid * gpb; b0 < D.np; b0 += stride) {
       const int b = b0 + gid;
-      const bool act = b < D.np;
+      bool act = b < D.np;
+      if (act && D.isl_on && isl_skip<MODE>(D, D.bisl_p[b], force)) act = false;
       int s0 = 0, s1 = 0;
       if (act) { s0 = D.vseg[b]; s1 = D.vseg[b + 1]; }
       int sl[KR];
@@ -986,6 +1060,7 @@ __global__ void __launch_bounds__(BLOCK) k_body_pass(Dev<T> D, const T *__restri
             D.pg[k][b] = g[k]; D.pyg[k][b] = y[k]; D.phinv[k][b] = hi[k];
             acc_g2.add_prod(g[k], g[k]);
           }
+          if (D.isl_on) atomicAdd(D.isl.acc + D.bisl_p[b], double(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]));
         }
       }
 #pragma unroll
@@ -1117,36 +1192,202 @@ __global__ void __launch_bounds__(BLOCK) k_row_pass(Dev<T> D, int force) {
     for (int k = 0; k < NPART; k++) D.part_row[NPART * blockIdx.x + k] = v[k];
 }
 
+// Island mode of the row pass: the same per-row arithmetic, with the sums
+// taken per island (warp_runs_add) instead of per block.  The loops step by
+// whole warps so that every lane takes part in the shuffles.
+template <typename T, int MODE>
+__global__ void __launch_bounds__(BLOCK) k_row_pass_isl(Dev<T> D, int force) {
+  if (!force && D.fl->newton_stop) return;
+  if (MODE == RM_APPLY && D.fl->cr_stop) return;
+  const T eps = D.epsT, ih = D.ihT;
+  const int lane = threadIdx.x & 31;
+  const int ni = D.ni;
+  if (blockIdx.x < D.nblk_row_pair) {
+    const int stride = D.nblk_row_pair * BLOCK;
+    for (int w0 = blockIdx.x * BLOCK + (threadIdx.x & ~31); w0 < D.Rpair; w0 += stride) {
+      const int i = w0 + lane;
+      int key = i < D.Rpair ? D.risl[i] : -1;
+      if (key >= 0 && (MODE == RM_APPLY ? D.isl.crdone[key] != 0 : (!force && D.isl.stop[key] >= 0))) key = -1;
+      const bool v = key >= 0;
+      if (MODE == RM_RHS) {
+        T a[2] = {T(0), T(0)};
+        if (v) {
+          const T tb = D.t[2 * i] + D.t[2 * i + 1], td = D.t2[2 * i] + D.t2[2 * i + 1];
+          const T hv = D.hv[i];
+          const T bi = (tb - hv) * ih;
+          const T Pi = T(1) / (td + D.cdiag[i] + eps);
+          D.b[i] = bi; D.P[i] = Pi; D.x[i] = T(0); D.Ap[i] = T(0);
+          const T zi = Pi * bi;
+          D.z[i] = zi; D.p[i] = zi;
+          a[0] = hv * hv; a[1] = bi * zi;
+        }
+        warp_runs_add<T, 2>(key, a, D.isl.acc, ni);
+      } else {
+        T a[5] = {T(0), T(0), T(0), T(0), T(0)};
+        if (v) {
+          const T acc = D.t[2 * i] + D.t[2 * i + 1];
+          const T zi = D.z[i];
+          const T Pi = D.P[i];
+          const T az = acc + (D.cdiag[i] + eps) * zi;
+          const T api = D.Ap[i];
+          D.Az[i] = az;
+          const T paz = Pi * az;
+          a[0] = zi * az; a[1] = az * paz; a[2] = paz * api; a[3] = zi * zi / Pi; a[4] = api * Pi * api;
+        }
+        warp_runs_add<T, 5>(key, a, D.isl.acc + 2 * size_t(ni), ni);
+      }
+    }
+  } else {
+    const int bid = blockIdx.x - D.nblk_row_pair;
+    const int stride = D.nblk_row_tet * BLOCK;
+    const int rb = D.Rpair;
+    for (int w0 = bid * BLOCK + (threadIdx.x & ~31); w0 < D.nt; w0 += stride) {
+      const int t = w0 + lane;
+      int key = t < D.nt ? D.risl[rb + 3 * t] : -1;
+      if (key >= 0 && (MODE == RM_APPLY ? D.isl.crdone[key] != 0 : (!force && D.isl.stop[key] >= 0))) key = -1;
+      const bool v = key >= 0;
+      if (MODE == RM_RHS) {
+        T a[2] = {T(0), T(0)};
+        if (v) {
+          const T *ts = D.t + 2 * rb + 12 * t, *ts2 = D.t2 + 2 * rb + 12 * t;
+          const T *c3 = D.c3 + 6 * t;
+#pragma unroll
+          for (int k = 0; k < 3; k++) {
+            T tb = T(0), td = T(0);
+#pragma unroll
+            for (int q = 0; q < 4; q++) { tb += ts[4 * k + q]; td += ts2[4 * k + q]; }
+            const int i = rb + 3 * t + k;
+            const T hv = D.hv[i];
+            const T bi = (tb - hv) * ih;
+            const T Pi = T(1) / (td + c3[k] + eps);
+            D.b[i] = bi; D.P[i] = Pi; D.x[i] = T(0); D.Ap[i] = T(0);
+            const T zi = Pi * bi;
+            D.z[i] = zi; D.p[i] = zi;
+            a[0] += hv * hv; a[1] += bi * zi;
+          }
+        }
+        warp_runs_add<T, 2>(key, a, D.isl.acc, ni);
+      } else {
+        T a[5] = {T(0), T(0), T(0), T(0), T(0)};
+        if (v) {
+          const T *ts = D.t + 2 * rb + 12 * t;
+          const T *c3 = D.c3 + 6 * t;
+          const int i0 = rb + 3 * t;
+          const T z0 = D.z[i0], z1 = D.z[i0 + 1], z2 = D.z[i0 + 2];
+          T cz[3];
+          cz[0] = c3[0] * z0 + c3[3] * z1 + c3[4] * z2;
+          cz[1] = c3[3] * z0 + c3[1] * z1 + c3[5] * z2;
+          cz[2] = c3[4] * z0 + c3[5] * z1 + c3[2] * z2;
+          const T zz[3] = {z0, z1, z2};
+#pragma unroll
+          for (int k = 0; k < 3; k++) {
+            T acc = T(0);
+#pragma unroll
+            for (int q = 0; q < 4; q++) acc += ts[4 * k + q];
+            const int i = i0 + k;
+            const T az = acc + cz[k] + eps * zz[k];
+            D.Az[i] = az;
+            const T Pi = D.P[i];
+            const T api = D.Ap[i];
+            const T paz = Pi * az;
+            a[0] += zz[k] * az; a[1] += az * paz; a[2] += paz * api; a[3] += zz[k] * zz[k] / Pi;
+            a[4] += api * Pi * api;
+          }
+        }
+        warp_runs_add<T, 5>(key, a, D.isl.acc + 2 * size_t(ni), ni);
+      }
+    }
+  }
+}
+
 // merit of this Newton iteration, Newton stop test, CR forcing term (1 block)
 template <typename T>
 __global__ void __launch_bounds__(RED_THREADS) k_merit(Dev<T> D, int n, int force) {
   if (!force && D.fl->newton_stop) return;
-  using R = typename RedT<T>::type;
-  double r4[NPART];
-  R gv[1] = {red_zero(R())};
-  const int nb = D.nblk_body_r + D.nblk_body_p;
-  for (int i = threadIdx.x; i < nb; i += RED_THREADS) gv[0] = red_add(gv[0], D.part_body[i]);
-  red_block<R, 1, RED_THREADS>(gv);
-  const double g2 = red_get(gv[0]);
-  reduce_partials<R, RED_THREADS>(D.part_row, D.nblk_row_pair + D.nblk_row_tet, r4);
-  if (threadIdx.x == 0) {
-    double m = sqrt(g2 + r4[0]);
-    if (n == -1) { D.sc->merit0 = m; return; }          // zero iterate of a warm-started step
-    if (n == -2) { D.sc->merit_warm = m; return; }      // warm-started iterate
-    D.sc->merit[n < 1023 ? n : 1023] = m;
-    if (force) return;
-    if (n == 0 && !D.warm) D.sc->merit0 = m;
-    double m0 = D.sc->merit0;
-    if (D.tol_rel > 0.0 && m <= D.tol_rel * m0) D.fl->newton_stop = 1;
-    double eta = 0.0;
-    if (D.cr_tol) {
-      eta = m0 > 0.0 ? m / m0 : 0.0;
-      if (eta > 0.1) eta = 0.1;
-      if (eta <= 0.0) eta = 1e-30;
+  const bool final_eval = force && n >= 0;
+  double m = 0.0, res0 = 0.0;
+  if (!D.isl_on) {
+    using R = typename RedT<T>::type;
+    double r4[NPART];
+    R gv[1] = {red_zero(R())};
+    const int nb = D.nblk_body_r + D.nblk_body_p;
+    for (int i = threadIdx.x; i < nb; i += RED_THREADS) gv[0] = red_add(gv[0], D.part_body[i]);
+    red_block<R, 1, RED_THREADS>(gv);
+    const double g2 = red_get(gv[0]);
+    reduce_partials<R, RED_THREADS>(D.part_row, D.nblk_row_pair + D.nblk_row_tet, r4);
+    m = sqrt(g2 + r4[0]);
+    res0 = sqrt(r4[1]);
+  } else {
+    // per island: merit, stop test, forcing term, CR start; the global merit
+    // is the norm over all islands
+    const int ni = D.ni;
+    double *acc = D.isl.acc;
+    double m2 = 0.0;
+    int active = 0;
+    for (int i = threadIdx.x; i < ni; i += RED_THREADS) {
+      const double a = acc[i], bz = acc[ni + i];
+      acc[i] = 0.0; acc[ni + i] = 0.0;
+      const double mi = sqrt(a);
+      if (n == -1) { D.isl.m0[i] = mi; m2 += a; continue; }
+      if (n == -2) { D.isl.mw[i] = mi; m2 += a; continue; }
+      if (final_eval) { D.isl.mf[i] = mi; m2 += a; continue; }
+      int st = D.isl.stop[i];
+      if (st >= 0) {                       // stopped: not evaluated, keeps its last merit
+        m2 += D.isl.mf[i] * D.isl.mf[i];
+        D.isl.crdone[i] = 1;
+        continue;
+      }
+      m2 += a;
+      D.isl.mf[i] = mi;
+      if (n == 0 && !D.warm) D.isl.m0[i] = mi;
+      const double m0 = D.isl.m0[i];
+      if (st < 0 && D.tol_rel > 0.0 && mi <= D.tol_rel * m0) { st = n; D.isl.stop[i] = n; }
+      double eta = 0.0;
+      if (D.cr_tol) {
+        eta = m0 > 0.0 ? mi / m0 : 0.0;
+        if (eta > 0.1) eta = 0.1;
+        if (eta <= 0.0) eta = 1e-30;
+      }
+      D.isl.eta[i] = eta;
+      const double r0 = sqrt(bz);
+      D.isl.res0[i] = r0;
+      D.isl.crdone[i] = (st >= 0 || r0 == 0.0) ? 1 : 0;
+      active |= st < 0;
     }
-    D.sc->eta = eta;
-    D.sc->res0 = sqrt(r4[1]);
-    D.fl->cr_stop = 0;
+    __shared__ double sm[RED_THREADS / 32];
+    for (int o = 16; o > 0; o >>= 1) m2 += __shfl_down_sync(0xffffffffu, m2, o);
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = m2;
+    const int any = __syncthreads_or(active);
+    if (threadIdx.x == 0) {
+      double t2 = 0.0;
+      for (int w = 0; w < RED_THREADS / 32; w++) t2 += sm[w];
+      m = sqrt(t2);
+      if (n >= 0 && !final_eval && !any) D.fl->newton_stop = 1;
+    }
+  }
+  if (threadIdx.x == 0) {
+    if (n == -1) {                                     // zero iterate of a warm-started step
+      D.sc->merit0 = m;
+      D.sc->warm_rejected = 0;
+    } else if (n == -2) {                              // warm-started iterate
+      D.sc->merit_warm = m;
+    } else {
+      D.sc->merit[n < 1023 ? n : 1023] = m;
+      if (!force) {
+        if (n == 0 && !D.warm) D.sc->merit0 = m;
+        const double m0 = D.sc->merit0;
+        if (!D.isl_on && D.tol_rel > 0.0 && m <= D.tol_rel * m0) D.fl->newton_stop = 1;
+        double eta = 0.0;
+        if (D.cr_tol) {
+          eta = m0 > 0.0 ? m / m0 : 0.0;
+          if (eta > 0.1) eta = 0.1;
+          if (eta <= 0.0) eta = 1e-30;
+        }
+        D.sc->eta = eta;
+        D.sc->res0 = res0;
+        D.fl->cr_stop = 0;
+      }
+    }
   }
 }
 
@@ -1216,6 +1457,83 @@ __global__ void __launch_bounds__(BLOCK) k_cr_update(Dev<T> D, int k) {
   }
 }
 
+// Island mode of K7: the same recurrence with each island's own scalars (A
+// is block diagonal by island, so this is CR on every island's system by
+// itself).  One thread per island; the last block to finish sets cr_stop when
+// no island continues.
+template <typename T>
+__global__ void k_cr_scalars_isl(Dev<T> D, int k) {
+  if (D.fl->newton_stop || D.fl->cr_stop) return;
+  const int ni = D.ni;
+  double *acc = D.isl.acc + 2 * size_t(ni);
+  int act = 0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ni; i += gridDim.x * blockDim.x) {
+    const double d1 = acc[i], d2 = acc[ni + i], d3 = acc[2 * ni + i], d4 = acc[3 * ni + i], d5 = acc[4 * ni + i];
+    acc[i] = 0.0; acc[ni + i] = 0.0; acc[2 * ni + i] = 0.0; acc[3 * ni + i] = 0.0; acc[4 * ni + i] = 0.0;
+    if (D.isl.crdone[i]) continue;
+    int st = 0;
+    const double cur = sqrt(d4 > 0.0 ? d4 : 0.0);
+    const double r0 = D.isl.res0[i];
+    if (r0 == 0.0) st = 1;
+    if (D.cr_tol && cur <= D.isl.eta[i] * r0) st = 1;
+    double beta = 0.0, rho = d1, apap = d2;
+    if (k > 0) {
+      const double rp = D.isl.rho[size_t((k - 1) & 1) * ni + i];
+      if (!(d1 > 0.0) || !(rp > 0.0)) st = 1;
+      else {
+        beta = d1 / rp;
+        apap = d2 + 2.0 * beta * d3 + beta * beta * d5;
+      }
+    }
+    if (!(apap > 0.0)) st = 1;
+    if (st) { D.isl.crdone[i] = 1; continue; }
+    D.isl.rho[size_t(k & 1) * ni + i] = rho;
+    const double alpha = rho / apap;
+    D.isl.alpha[i] = alpha; D.isl.beta[i] = beta;
+    D.isl.alpha_f[i] = float(alpha); D.isl.beta_f[i] = float(beta);
+    act = 1;
+  }
+  const int any = __syncthreads_or(act);
+  if (threadIdx.x == 0) {
+    if (any) atomicAdd(&D.fl->isl_active, 1);
+    __threadfence();
+    const int ticket = atomicAdd(&D.fl->isl_ticket, 1);
+    if (ticket == int(gridDim.x) - 1) {
+      __threadfence();
+      const int a = atomicAdd(&D.fl->isl_active, 0);
+      if (a == 0) D.fl->cr_stop = 1;
+      else D.fl->cr_count += 1;
+      D.fl->isl_active = 0;
+      D.fl->isl_ticket = 0;
+    }
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ T isl_scalar(const double *d, const float *f, int i);
+template <>
+__device__ __forceinline__ float isl_scalar<float>(const double *, const float *f, int i) { return f[i]; }
+template <>
+__device__ __forceinline__ double isl_scalar<double>(const double *d, const float *, int i) { return d[i]; }
+
+template <typename T>
+__global__ void __launch_bounds__(BLOCK) k_cr_update_isl(Dev<T> D, int k) {
+  if (D.fl->newton_stop || D.fl->cr_stop) return;
+  const int stride = gridDim.x * BLOCK;
+  for (int i = blockIdx.x * BLOCK + threadIdx.x; i < D.R; i += stride) {
+    const int is = D.risl[i];
+    if (D.isl.crdone[is]) continue;
+    const T alpha = isl_scalar<T>(D.isl.alpha, D.isl.alpha_f, is), beta = isl_scalar<T>(D.isl.beta, D.isl.beta_f, is);
+    const T zi = D.z[i];
+    const T pi = k == 0 ? zi : zi + beta * D.p[i];
+    const T api = k == 0 ? D.Az[i] : D.Az[i] + beta * D.Ap[i];
+    D.p[i] = pi;
+    D.Ap[i] = api;
+    D.x[i] += alpha * pi;
+    D.z[i] = zi - alpha * D.P[i] * api;
+  }
+}
+
 // CR restart on a kept system: x = 0, z = P b, p = z
 template <typename T>
 __global__ void k_cr_init(Dev<T> D) {
@@ -1231,8 +1549,32 @@ __global__ void k_lambda_update(Dev<T> D) {
   if (D.fl->newton_stop) return;
   const T t = D.dampT;
   const int i0 = blockIdx.x * blockDim.x + threadIdx.x;
+  const int stride = gridDim.x * blockDim.x;
   if (i0 == 0) D.fl->newton_count += 1;
-  for (int i = i0; i < D.R; i += gridDim.x * blockDim.x) D.lam[i] += t * D.x[i];
+  if (!D.isl_on && !D.cone) {
+    for (int i = i0; i < D.R; i += stride) D.lam[i] += t * D.x[i];
+    return;
+  }
+  // contact j updates its three rows together (cone projection); rows of
+  // islands that have stopped keep their multipliers
+  const int nc = D.nc, nrest = D.R - 3 * nc;
+  for (int j = i0; j < nc + nrest; j += stride) {
+    if (j < nc) {
+      const int r = 3 * j;
+      if (D.isl_on && D.isl.stop[D.risl[r]] >= 0) continue;
+      T l0 = D.lam[r] + t * D.x[r], l1 = D.lam[r + 1] + t * D.x[r + 1], l2 = D.lam[r + 2] + t * D.x[r + 2];
+      if (D.cone) {
+        if (l0 < T(0)) l0 = T(0);
+        const T lim = D.cmu[j] * l0, f = dsqrt(l1 * l1 + l2 * l2);
+        if (f > lim) { const T sc = lim / f; l1 *= sc; l2 *= sc; }
+      }
+      D.lam[r] = l0; D.lam[r + 1] = l1; D.lam[r + 2] = l2;
+    } else {
+      const int r = 3 * nc + (j - nc);
+      if (D.isl_on && D.isl.stop[D.risl[r]] >= 0) continue;
+      D.lam[r] += t * D.x[r];
+    }
+  }
 }
 
 // ------------------------------------------------------------------------------------
@@ -1376,10 +1718,21 @@ __global__ void k_warm_from_prev(Dev<T> D, int warm_friction) {
 // keep the warm start only if its merit is not above the zero start's
 template <typename T>
 __global__ void k_warm_accept(Dev<T> D) {
+  const int i0 = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+  if (D.isl_on) {
+    // per island: the warm start is kept where its merit is not above the zero start's
+    for (int i = i0; i < D.ni; i += stride)
+      if (!(D.isl.mw[i] <= D.isl.m0[i])) atomicAdd(&D.sc->warm_rejected, 1);
+    for (int i = i0; i < D.R; i += stride) {
+      const int is = D.risl[i];
+      if (!(D.isl.mw[is] <= D.isl.m0[is])) D.lam[i] = T(0);
+    }
+    return;
+  }
   const bool reject = !(D.sc->merit_warm <= D.sc->merit0);
-  if (blockIdx.x == 0 && threadIdx.x == 0) D.sc->warm_rejected = reject ? 1 : 0;
+  if (i0 == 0) D.sc->warm_rejected = reject ? 1 : 0;
   if (!reject) return;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < D.R; i += gridDim.x * blockDim.x) D.lam[i] = T(0);
+  for (int i = i0; i < D.R; i += stride) D.lam[i] = T(0);
 }
 
 template <typename T>

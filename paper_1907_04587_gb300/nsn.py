@@ -39,7 +39,7 @@ class nsn_config(C.Structure):
                 ("cr_iters", C.c_int32), ("damping", C.c_double), ("eps", C.c_double),
                 ("tol_rel", C.c_double), ("cr_tol_mode", C.c_int32), ("ncp", C.c_int32),
                 ("rscale", C.c_int32), ("geom_stiffness", C.c_int32), ("precision", C.c_int32),
-                ("use_graph", C.c_int32)]
+                ("use_graph", C.c_int32), ("cone_project", C.c_int32), ("island_stop", C.c_int32)]
 
 
 class nsn_stats(C.Structure):
@@ -105,6 +105,9 @@ def lib():
         "nsn_mlp_forward": (C.c_int, [_vp, _vp, C.c_int32, _vp]),
         "nsn_mlp_train_step": (C.c_int, [_vp, _vp, _vp, _vp, C.c_int32, C.c_float, C.POINTER(C.c_float)]),
         "nsn_contact_features": (C.c_int, [_vp, _vp, _vp]),
+        "nsn_islands": (C.c_int, [_vp, _ip, _ip]),
+        "nsn_island_stats": (C.c_int, [_vp, C.c_int32, _dp, _dp, _ip]),
+        "nsn_island_stop_device": (C.c_int, [_vp, C.POINTER(_vp)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -279,10 +282,29 @@ def nsn_set_warm_start(ctx, mode):
     _check(ctx, lib().nsn_set_warm_start(ctx, mode), "nsn_set_warm_start")
 
 
+def nsn_islands(ctx, nb):
+    n = C.c_int32()
+    bi = np.zeros(max(nb, 1), np.int32)
+    _check(ctx, lib().nsn_islands(ctx, C.byref(n), _p(bi, _ip)), "nsn_islands")
+    return n.value, bi[:nb]
+
+
+def nsn_island_stats(ctx, ni):
+    m0, mf, it = np.zeros(max(ni, 1)), np.zeros(max(ni, 1)), np.zeros(max(ni, 1), np.int32)
+    _check(ctx, lib().nsn_island_stats(ctx, max(ni, 1), _p(m0, _dp), _p(mf, _dp), _p(it, _ip)), "nsn_island_stats")
+    return dict(merit0=m0[:ni], merit_final=mf[:ni], stopped_at=it[:ni])
+
+
+def nsn_island_stop_device(ctx):
+    ptr = _vp()
+    _check(ctx, lib().nsn_island_stop_device(ctx, C.byref(ptr)), "nsn_island_stop_device")
+    return ptr.value
+
+
 def nsn_get_warm_stats(ctx):
     mz, mw, rj = C.c_double(), C.c_double(), C.c_int32()
     _check(ctx, lib().nsn_get_warm_stats(ctx, C.byref(mz), C.byref(mw), C.byref(rj)), "nsn_get_warm_stats")
-    return dict(merit_zero=mz.value, merit_warm=mw.value, rejected=bool(rj.value))
+    return dict(merit_zero=mz.value, merit_warm=mw.value, rejected=int(rj.value))
 
 
 def nsn_mlp_set_params(ctx, params):
@@ -351,7 +373,8 @@ def tet_records(s):
 
 
 DEFAULTS = dict(h=1.0 / 60.0, gravity=(0.0, 0.0, -9.81), newton_iters=4, cr_iters=20, damping=0.75, eps=1e-6,
-                tol_rel=0.0, cr_tol_mode=0, ncp=0, rscale=2, geom_stiffness=1, precision=NSN_FP32, use_graph=1)
+                tol_rel=0.0, cr_tol_mode=0, ncp=0, rscale=2, geom_stiffness=1, precision=NSN_FP32, use_graph=1,
+                cone_project=0, island_stop=0)
 
 
 def make_config(**params):
@@ -363,7 +386,8 @@ def make_config(**params):
     cfg = nsn_config()
     cfg.h = p["h"]
     cfg.gravity = (C.c_double * 3)(*p["gravity"])
-    for k in ("newton_iters", "cr_iters", "cr_tol_mode", "ncp", "rscale", "geom_stiffness", "precision", "use_graph"):
+    for k in ("newton_iters", "cr_iters", "cr_tol_mode", "ncp", "rscale", "geom_stiffness", "precision", "use_graph",
+              "cone_project", "island_stop"):
         setattr(cfg, k, int(p[k]))
     for k in ("damping", "eps", "tol_rel"):
         setattr(cfg, k, float(p[k]))
@@ -453,6 +477,15 @@ class Solver:
 
     def warm_stats(self):
         return nsn_get_warm_stats(self.ctx)
+
+    def islands(self):
+        """(number of islands, island of each body)."""
+        return nsn_islands(self.ctx, self.nb)
+
+    def island_stats(self):
+        """Per island of the last step (island_stop = 1): zero-iterate merit,
+        final merit, Newton iteration at which it stopped (-1: not stopped)."""
+        return nsn_island_stats(self.ctx, self.islands()[0])
 
     def time_operator(self, iters=20):
         return nsn_time_operator(self.ctx, iters)

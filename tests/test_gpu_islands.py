@@ -1,0 +1,135 @@
+"""GPU parity of island mode and of the friction-cone projection.
+
+Island mode (island_stop = 1) gives every island its own Newton stop test,
+warm-start acceptance and CR scalars; the oracle implements the same and is
+pinned against separate solves of each island.  The FP64 build of the kernels
+must take the same per-island decisions as the oracle (the stop iteration of
+each island is an integer: compared exactly) and reach the same states; the
+FP32 production path must stop the same islands within an iteration or two
+and meet the tolerance where it stops.
+"""
+import numpy as np
+import pytest
+
+from paper_1907_04587_gb300 import nsn, scenes
+
+pytestmark = pytest.mark.gpu
+
+H = 1.0 / 60.0
+G = 9.81
+TOL64 = 1e-7
+
+
+@pytest.fixture(scope="module", autouse=True)
+def cuda():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    yield
+
+
+def mass_norm(state, s, dv, dw):
+    R = scenes.quat_rot(state["quat"])
+    m = s["mass"].astype(np.float64)
+    e = (m * (dv ** 2).sum(1)).sum()
+    rig = s["kind"] == 0
+    Iw = np.einsum("nij,nj,nkj->nik", R, s["inertia"].astype(np.float64), R)
+    e += np.einsum("ni,nij,nj->", dw[rig], Iw[rig], dw[rig])
+    return np.sqrt(e)
+
+
+def vel_error(so, sg, s):
+    num = mass_norm(so, s, sg["vel"] - so["vel"], sg["omega"] - so["omega"])
+    den = mass_norm(so, s, so["vel"], so["omega"]) + H * G * np.sqrt(s["mass"].astype(np.float64).sum())
+    return num / den
+
+
+SCENE = lambda: scenes.batched_envs(seed=5001, n_envs=2, links=(3, 5), boxes=(2, 20))
+PRM = dict(newton_iters=25, cr_iters=60, tol_rel=1e-6, island_stop=1, cone_project=1)
+
+
+def test_islands_match_oracle(orc):
+    s = SCENE()
+    o = orc.Oracle(s, **PRM)
+    g = nsn.Solver(s, **PRM)
+    n_o, bi_o, _ = o.islands()
+    n_g, bi_g = g.islands()
+    assert n_g == n_o and np.array_equal(bi_g, bi_o)
+
+
+def test_island_mode_parity_fp64(orc):
+    s = SCENE()
+    o = orc.Oracle(s, **PRM)
+    g = nsn.Solver(s, precision=nsn.NSN_FP64, **PRM)
+    so_, sg_ = o.step(), g.step()
+    io, ig = o.island_stats(), g.island_stats()
+    print("stop iterations oracle", io["stopped_at"].tolist())
+    print("stop iterations gpu   ", ig["stopped_at"].tolist())
+    assert np.array_equal(ig["stopped_at"], io["stopped_at"])
+    np.testing.assert_allclose(ig["merit0"], io["merit0"], rtol=1e-9)
+    done = io["stopped_at"] >= 0
+    np.testing.assert_allclose(ig["merit_final"][~done], io["merit_final"][~done], rtol=1e-5)
+    assert np.all(ig["merit_final"][done] <= 1e-6 * ig["merit0"][done] * (1 + 1e-6))
+    assert sg_["newton_done"] == so_["newton_done"]
+    e = vel_error(o.get_state(), g.get_state_f64(), s)
+    print("velocity error", e)
+    assert e < TOL64
+
+
+def test_island_mode_fp32(orc):
+    s = SCENE()
+    o = orc.Oracle(s, **PRM)
+    g = nsn.Solver(s, **PRM)
+    o.step(); g.step()
+    io, ig = o.island_stats(), g.island_stats()
+    so, sg = io["stopped_at"], ig["stopped_at"]
+    print("stop iterations oracle", so.tolist())
+    print("stop iterations fp32  ", sg.tolist())
+    both = (so >= 0) & (sg >= 0)
+    assert (sg >= 0).sum() >= (so >= 0).sum() - 1
+    assert np.mean(np.abs(sg[both] - so[both]) <= 2) >= 0.8
+    done = sg >= 0
+    assert np.all(ig["merit_final"][done] <= 1e-6 * ig["merit0"][done] * 1.01)
+    np.testing.assert_allclose(ig["merit0"], io["merit0"], rtol=1e-5)
+
+
+@pytest.mark.parametrize("prec", [nsn.NSN_FP64, nsn.NSN_FP32])
+def test_cone_projection_parity(orc, prec):
+    """Global mode with the projection, equal Newton/CR counts."""
+    s = scenes.batched_envs(seed=2, n_envs=12)
+    p = dict(newton_iters=5, cr_iters=25, cone_project=1)
+    o = orc.Oracle(s, **p)
+    g = nsn.Solver(s, precision=prec, **p)
+    for step in range(2):
+        st = o.get_state()
+        f32 = {k: v.astype(np.float32) for k, v in st.items()}
+        o.set_state(**{k: v.astype(np.float64) for k, v in f32.items()})
+        g.set_state(**f32)
+        o.step(); g.step()
+        e = vel_error(o.get_state(), g.get_state_f64(), s)
+        lam = g.get_lambda()
+        nc = len(s["c_body"])
+        ln, lf = lam[0:3 * nc:3], np.hypot(lam[1:3 * nc:3], lam[2:3 * nc:3])
+        print(f"prec {prec} step {step}: velocity error {e:.2e}")
+        assert np.all(ln >= 0) and np.all(lf <= s["c_mu"] * ln * (1 + 1e-5) + 1e-30)
+        assert e < (TOL64 if prec == nsn.NSN_FP64 else 3e-3)
+
+
+def test_island_warm_start_per_island(orc):
+    """Previous-step warm start in island mode: accepted or rejected island by
+    island; every island that stops meets the tolerance against its own zero
+    start."""
+    s = SCENE()
+    g = nsn.Solver(s, **PRM)
+    g.step()
+    g.set_warm_start(nsn.NSN_WARM_PREV)
+    g.step()
+    ws = g.warm_stats()
+    ni = g.islands()[0]
+    assert 0 <= ws["rejected"] <= ni
+    st = g.island_stats()
+    done = st["stopped_at"] >= 0
+    assert done.sum() >= ni // 2
+    assert np.all(st["merit_final"][done] <= 1e-6 * st["merit0"][done] * 1.01)
