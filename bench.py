@@ -3,19 +3,25 @@
 
 Workload (default): 4096 independent RL-style environments, each a revolute
 chain of 3-20 links lying on a plane plus 0-64 cubes piled in up to four
-layers, per-environment friction in [0.3, 1.0] (``scenes.batched_envs``),
-solved as one system with the Newton x CR budget the paper uses for its
-many-environment scenes (Table 2, Yumi Cabinet: 5 x 25).
+layers, per-environment friction in [0.3, 1.0] (``scenes.batched_envs``).
 
-A step is one full time step (Algorithm 1: row evaluation, residual, Schur
-right-hand side, 25 CR iterations of the matrix-free operator, damped update,
-for each of 5 Newton iterations) from the same resident start state.
-  value     env-steps/s with the state already in HBM (device-timed)
-  e2e       env-steps/s through the C ABI with host buffers: host->device copy
-            of the state, the step, device->host copy of the new state
-  roofline  the CR operator apply (body pass + row pass), bytes per launch
-            from the algorithmic count B_apply, timed live with CUDA events
-  cpu_baseline  the FP64 oracle on a 64-environment sample, one host core
+A step is one time step of Algorithm 1 solved to a relative residual of 1e-6:
+islands (connected components of bodies through constraints) are solved side
+by side, each stops when its merit reaches 1e-6 of its own zero-iterate merit
+(cap: 30 Newton iterations of 50 CR iterations each), and an environment-step
+counts only if every island of the environment reached the tolerance.  The
+trajectory advances from the seeded start state (no reset between steps).
+  value     converged env-steps/s, state resident in HBM (device-timed); the
+            method with the damped update projected onto the friction cone
+            (option cone_project; the printed update is the "as_printed" arm)
+  arms      the same measurement for: the printed update, the previous-step
+            warm start, and the learned warm start (when trained weights exist)
+  e2e       converged env-steps/s through the C ABI with host buffers: host->
+            device copy of the state, the step, device->host copy of the state
+  roofline  the CR operator apply (body pass + row pass, island kernels),
+            bytes per launch from the algorithmic count B_apply, timed live
+  cpu_baseline  the FP64 oracle on a 64-environment sample, one host core,
+            same tolerance, caps and accounting
 
 ``--impl reference`` times the FP64 oracle (the reference arm here) on the
 host cores with the same workload definition, metric and unit.
@@ -41,19 +47,21 @@ import numpy as np  # noqa: E402
 
 from paper_1907_04587_gb300 import scenes  # noqa: E402
 
-METRIC = "env-steps/s (batched plain method, Table 2 many-env budget); CR-apply HBM GB/s"
+METRIC = "env-steps/s at 1e-6 relative residual (batched, islands solved side by side); CR-apply HBM GB/s"
 UNIT = "env-steps/s"
+TOL = 1e-6
 WORKLOADS = {
-    "batched4096": dict(make=lambda seed: scenes.batched_envs(seed=seed, n_envs=4096), newton=5, cr=25,
+    "batched4096": dict(make=lambda seed: scenes.batched_envs(seed=seed, n_envs=4096), newton=30, cr=50,
                         desc="4096 chain+cube-pile environments (3-20 links, 0-64 cubes, mu 0.3-1.0)"),
-    "batched2048": dict(make=lambda seed: scenes.batched_envs(seed=seed, n_envs=2048), newton=5, cr=25,
+    "batched2048": dict(make=lambda seed: scenes.batched_envs(seed=seed, n_envs=2048), newton=30, cr=50,
                         desc="2048 chain+cube-pile environments (profiling size: ~1.2 M rows, working set above L2)"),
-    "chain_block": dict(make=lambda seed: scenes.chain_block(seed=seed), newton=10, cr=50,
+    "chain_block": dict(make=lambda seed: scenes.chain_block(seed=seed), newton=30, cr=50,
                         desc="7-link revolute chain on a 24^3-hex stable Neo-Hookean block (69,120 tets)"),
-    "cube_stack": dict(make=lambda seed: scenes.cube_stack(seed=seed), newton=4, cr=20,
+    "cube_stack": dict(make=lambda seed: scenes.cube_stack(seed=seed), newton=30, cr=20,
                        desc="4 unit cubes stacked on a plane (16 contacts)"),
 }
 SAMPLE_ENVS = 64
+WEIGHTS = os.path.join(ROOT, "paper_1907_04587_gb300", "weights", "warm_start_mlp.npy")
 
 
 def algorithmic_bytes(sz):
@@ -156,28 +164,52 @@ def kernel_source_hash():
     return h.hexdigest()
 
 
+def island_env_map(s, body_island, n_islands):
+    """Environment of each island (that of its lowest body)."""
+    nb = len(body_island)
+    first = np.full(n_islands, nb, np.int64)
+    np.minimum.at(first, body_island, np.arange(nb))
+    env = np.asarray(s.get("env", np.zeros(nb, np.int32)))
+    return env[first].astype(np.int64)
+
+
+def count_converged(stops, isl_env, n_envs):
+    """stops: (steps, islands) stop iterations (-1: not converged).  Returns
+    (converged env-steps, converged island-steps, mean stop iteration)."""
+    stops = np.asarray(stops)
+    fail = np.zeros((stops.shape[0], n_envs), np.int64)
+    for k in range(stops.shape[0]):
+        np.add.at(fail[k], isl_env, (stops[k] < 0).astype(np.int64))
+    ok = stops >= 0
+    return int((fail == 0).sum()), int(ok.sum()), float(stops[ok].mean()) if ok.any() else float("nan")
+
+
 def oracle_rate(workload, seed, budget_s, newton, cr):
-    """FP64 oracle env-steps/s on a bounded sample of the workload."""
+    """FP64 oracle converged env-steps/s on a bounded sample of the workload."""
     import oracle
     if workload.startswith("batched"):
         s = scenes.batched_envs(seed=seed, n_envs=SAMPLE_ENVS)
-        envs = SAMPLE_ENVS
-        sample = f"{SAMPLE_ENVS} of the 4096 environments' distribution (seed {seed}), same Newton x CR budget"
+        sample = f"{SAMPLE_ENVS} environments of the same distribution (seed {seed})"
     else:
         s = WORKLOADS[workload]["make"](seed)
-        envs = 1
         sample = "the full scene"
-    o = oracle.Oracle(s, newton_iters=newton, cr_iters=cr)
-    st0 = o.get_state()
+    n_envs = int(s.get("n_envs", 1))
+    o = oracle.Oracle(s, newton_iters=newton, cr_iters=cr, tol_rel=TOL, island_stop=1, cone_project=1)
+    ni, bi, _ = o.islands()
+    isl_env = island_env_map(s, bi, ni)
+    stops = []
     n, t0 = 0, time.perf_counter()
     while True:
-        o.set_state(**st0)
         o.step()
+        stops.append(o.island_stats()["stopped_at"].copy())
         n += 1
         el = time.perf_counter() - t0
         if el >= budget_s:
             break
-    return envs * n / el, dict(kind="oracle", cores=1, sample=f"{sample}; {n} steps in {el:.1f} s")
+    conv, _, _ = count_converged(stops, isl_env, n_envs)
+    return conv / el, dict(kind="oracle", cores=1,
+                           sample=f"{sample}, same tolerance, caps and accounting; {n} advancing steps in {el:.1f} s, "
+                                  f"{conv} of {n * n_envs} env-steps converged")
 
 
 def run_reference(args, rank, world):
@@ -189,11 +221,56 @@ def run_reference(args, rank, world):
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": args.workload, "description": W["desc"], "newton_iters": W["newton"],
-                      "cr_iters": W["cr"]},
+           "config": {"workload": args.workload, "description": W["desc"], "newton_cap": W["newton"],
+                      "cr_iters": W["cr"], "tol_rel": TOL},
            "cpu_baseline": cb,
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
+
+
+def make_solver(nsn, s, stream, newton, cr, cone, warm=0, params=None):
+    g = nsn.Solver(s, stream=stream.cuda_stream, newton_iters=newton, cr_iters=cr, tol_rel=TOL, island_stop=1,
+                   cone_project=cone, precision=nsn.NSN_FP32, use_graph=1)
+    if params is not None:
+        nsn.nsn_mlp_set_params(g.ctx, params)
+    g.set_warm_start(warm)
+    return g
+
+
+def measure_arm(nsn, torch, g, s, st0, stream, steps, warmup, clk=None):
+    """Device-timed advancing trajectory: reset to the start state, warmup
+    steps, then `steps` timed steps; per-step island stop iterations are copied
+    on the device and counted afterwards."""
+    dev = st0["pos"].device
+    ni, bi = g.islands()
+    isl_env = island_env_map(s, bi, ni)
+    n_envs = int(s.get("n_envs", 1))
+    stops = torch.empty((steps, max(ni, 1)), dtype=torch.int32, device=dev)
+    ptr = {k: v.data_ptr() for k, v in st0.items()}
+    nsn.nsn_set_state_device(g.ctx, ptr["pos"], ptr["quat"], ptr["vel"], ptr["omega"])
+    for _ in range(warmup):
+        g.step(1)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    if clk:
+        clk.__enter__()
+    e0.record(stream)
+    newton = []
+    for k in range(steps):
+        st = g.step(1)
+        nsn.lib().nsn_island_stop_copy(g.ctx, nsn.C.c_void_p(stops[k].data_ptr()))
+        newton.append(st["newton_done"])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if clk:
+        clk.__exit__()
+    sec = e0.elapsed_time(e1) / 1e3
+    conv, conv_isl, mean_stop = count_converged(stops[:, :ni].cpu().numpy(), isl_env, n_envs)
+    return dict(sec=sec, env_steps=conv, env_fraction=conv / (steps * n_envs),
+                island_fraction=conv_isl / max(steps * ni, 1), mean_newton_to_tol=mean_stop,
+                newton_per_step=float(np.mean(newton)), ms_per_step=sec * 1e3 / steps,
+                value=conv / sec, islands=ni)
 
 
 def run_ours(args, rank, world, local_rank):
@@ -208,103 +285,112 @@ def run_ours(args, rank, world, local_rank):
     newton = args.newton or W["newton"]
     cr = args.cr or W["cr"]
     s = W["make"](rank)
-    n_envs = int(s["n_envs"])
+    n_envs = int(s.get("n_envs", 1))
     stream = torch.cuda.Stream(device=dev)
-    solver = nsn.Solver(s, stream=stream.cuda_stream, newton_iters=newton, cr_iters=cr, tol_rel=args.tol,
-                        cr_tol_mode=1 if args.tol > 0 else 0, precision=nsn.NSN_FP32, use_graph=1)
-    nb = solver.nb
     st0 = {k: torch.from_numpy(np.ascontiguousarray(s[k], dtype=np.float32)).to(dev)
            for k in ("pos", "quat", "vel", "omega")}
-    ptr = {k: v.data_ptr() for k, v in st0.items()}
+    params = np.load(WEIGHTS) if os.path.exists(WEIGHTS) else None
+    with torch.cuda.stream(stream):
+        g = make_solver(nsn, s, stream, newton, cr, cone=1)
+        dist = None
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        clk = ClockSampler(local_rank)
+        main_arm = measure_arm(nsn, torch, g, s, st0, stream, args.steps, args.warmup, clk)
+        sec = main_arm["sec"]
+        units = main_arm["env_steps"]
+        if dist:
+            dist.barrier()
+        # e2e: host buffers through the C ABI (pinned), copies inside the timed region
+        host_in = {k: torch.from_numpy(np.ascontiguousarray(s[k], dtype=np.float32)).pin_memory()
+                   for k in ("pos", "quat", "vel", "omega")}
+        host_out = {k: torch.empty_like(v).pin_memory() for k, v in host_in.items()}
+        fp = lambda t: nsn.C.cast(t.data_ptr(), nsn._fp)  # noqa: E731
+        L = nsn.lib()
+        h2d = sum(v.numel() * 4 for v in host_in.values())
+        d2h = sum(v.numel() * 4 for v in host_out.values())
+        ni, bi = g.islands()
+        isl_env = island_env_map(s, bi, ni)
+        stops = torch.empty((args.steps, max(ni, 1)), dtype=torch.int32, device=dev)
 
-    def one_step():
-        nsn.nsn_set_state_device(solver.ctx, ptr["pos"], ptr["quat"], ptr["vel"], ptr["omega"])
-        return solver.step(1)
+        def e2e_step(k):
+            L.nsn_set_state(g.ctx, *[fp(host_in[k2]) for k2 in ("pos", "quat", "vel", "omega")])
+            g.step(1)
+            L.nsn_island_stop_copy(g.ctx, nsn.C.c_void_p(stops[k].data_ptr()))
+            L.nsn_get_state(g.ctx, *[fp(host_out[k2]) for k2 in ("pos", "quat", "vel", "omega")])
 
-    torch.cuda.synchronize()
-    for _ in range(max(args.warmup, 1)):
-        st = one_step()
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.barrier()
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local_rank) as clk:
-        e0.record(stream)
-        for _ in range(args.steps):
-            st = one_step()
-        e1.record(stream)
+        for _ in range(max(args.warmup, 1)):
+            e2e_step(0)
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            e2e_step(k)
         torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    sec = e0.elapsed_time(e1) / 1e3
-    rel_merit = st["merit_final"] / st["merit0"] if st["merit0"] > 0 else 0.0
-    # e2e: host buffers through the C ABI (pinned), copies inside the timed region
-    host_in = {k: torch.from_numpy(np.ascontiguousarray(s[k], dtype=np.float32)).pin_memory()
-               for k in ("pos", "quat", "vel", "omega")}
-    host_out = {k: torch.empty_like(v).pin_memory() for k, v in host_in.items()}
-    fp = lambda t: nsn.C.cast(t.data_ptr(), nsn._fp)  # noqa: E731
-    L = nsn.lib()
-    h2d = sum(v.numel() * 4 for v in host_in.values())
-    d2h = sum(v.numel() * 4 for v in host_out.values())
-    for _ in range(max(args.warmup, 1)):
-        L.nsn_set_state(solver.ctx, *[fp(host_in[k]) for k in ("pos", "quat", "vel", "omega")])
-        solver.step(1)
-        L.nsn_get_state(solver.ctx, *[fp(host_out[k]) for k in ("pos", "quat", "vel", "omega")])
-    if dist:
-        dist.barrier()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        L.nsn_set_state(solver.ctx, *[fp(host_in[k]) for k in ("pos", "quat", "vel", "omega")])
-        solver.step(1)
-        L.nsn_get_state(solver.ctx, *[fp(host_out[k]) for k in ("pos", "quat", "vel", "omega")])
-    torch.cuda.synchronize()
-    sec_e2e = time.perf_counter() - t0
-    # roofline of the CR operator apply, timed live on the solver's stream
-    ms_body, ms_row = solver.time_operator(20)
-    sz = solver.sizes()
+        sec_e2e = time.perf_counter() - t0
+        units_e2e, _, _ = count_converged(stops[:, :ni].cpu().numpy(), isl_env, n_envs)
+        # roofline of the CR operator apply, timed live on the solver's stream
+        ms_body, ms_row = g.time_operator(20)
+        sz = g.sizes()
+        launches = g.launches_per_step()
+        g.close()
+        # the other arms, same trajectory and accounting
+        arms = {}
+        if args.arms:
+            for name, cone, warm in (("as_printed", 0, nsn.NSN_WARM_ZERO), ("prev_warm_start", 1, nsn.NSN_WARM_PREV),
+                                     ("learned_warm_start", 1, nsn.NSN_WARM_LEARNED)):
+                if warm == nsn.NSN_WARM_LEARNED and params is None:
+                    arms[name] = {"unavailable": "no trained weights (paper_1907_04587_gb300/weights)"}
+                    continue
+                ga = make_solver(nsn, s, stream, newton, cr, cone=cone, warm=warm, params=params)
+                r = measure_arm(nsn, torch, ga, s, st0, stream, args.steps, args.warmup)
+                if warm != nsn.NSN_WARM_ZERO:
+                    r["warm_rejected_islands_last_step"] = ga.warm_stats()["rejected"]
+                ga.close()
+                r.pop("sec")
+                arms[name] = r
     B = algorithmic_bytes(sz)
     peak, peak_kind = measured_peaks()
     achieved = B / ((ms_body + ms_row) * 1e-3) / 1e9
-    launches = solver.launches_per_step()
-    units = n_envs * args.steps
     if dist:
-        t = torch.tensor([sec, sec_e2e, float(units)], device=dev, dtype=torch.float64)
+        t = torch.tensor([sec, sec_e2e, float(units), float(units_e2e)], device=dev, dtype=torch.float64)
         tmax = t.clone()
         dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
         tsum = t.clone()
         dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
         value = tsum[2].item() / tmax[0].item()
-        value_e2e = tsum[2].item() / tmax[1].item()
+        value_e2e = tsum[3].item() / tmax[1].item()
     else:
         value = weak_scaling_value([units], [sec])
-        value_e2e = weak_scaling_value([units], [sec_e2e])
+        value_e2e = weak_scaling_value([units_e2e], [sec_e2e])
     if rank != 0:
         return
     cb_value, cb = oracle_rate(args.workload, rank, args.cpu_budget, newton, cr)
     cb["value"] = cb_value
     cb["unit"] = UNIT
+    main_arm.pop("sec")
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": sec * 1e3 / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": args.workload, "description": W["desc"], "n_envs": n_envs, "bodies": nb,
-                   "rows": sz["rows"], "newton_iters": newton, "cr_iters": cr, "tol_rel": args.tol,
-                   "relative_merit_last_step": rel_merit, "newton_done": st["newton_done"],
-                   "cr_total": st["cr_total"], "device_bytes": sz["device_bytes"],
+        "config": {"workload": args.workload, "description": W["desc"], "n_envs": n_envs, "bodies": g.nb,
+                   "rows": sz["rows"], "islands": main_arm["islands"], "newton_cap": newton, "cr_iters": cr,
+                   "tol_rel": TOL, "cone_projection": True, "warm_start": "zero (Sec. 8.1)",
+                   "device_bytes": sz["device_bytes"],
                    "l2": "working set larger than L2 (no flush between steps)",
                    "parallelism": f"weak, {world} independent replica(s)"},
+        "convergence": main_arm,
+        "arms": arms,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": operator_traffic(kernel_source_hash()),
-                     "kernel": "CR operator apply = k_body_pass<APPLY> + k_row_pass<APPLY>",
+                     "kernel": "CR operator apply = k_body_pass<APPLY> + k_row_pass_isl<APPLY>",
                      "ms_body_pass": ms_body, "ms_row_pass": ms_row, "bytes_algorithmic": B,
                      "bytes_design": design_bytes(sz), "peak_kind": f"{peak_kind} hbm_gbs (burst)"},
         "cpu_baseline": cb,
-        "e2e": {"value": value_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": args.steps * (launches + 1),
+        "e2e": {"value": value_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "note": "every e2e step starts from the host copy of the start state"},
+        "gpu_launches": args.steps * launches,
         "clocks": clk.summary(),
     }
     print(json.dumps(out), flush=True)
@@ -319,7 +405,7 @@ def main():
     ap.add_argument("--workload", default="batched4096", choices=list(WORKLOADS))
     ap.add_argument("--newton", type=int, default=0)
     ap.add_argument("--cr", type=int, default=0)
-    ap.add_argument("--tol", type=float, default=0.0)
+    ap.add_argument("--arms", type=int, default=1, help="also measure the as-printed and warm-start arms")
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--ref-budget", type=float, default=60.0, help="seconds of oracle work for --impl reference")
     args = ap.parse_args()

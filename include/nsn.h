@@ -250,6 +250,9 @@ nsn_status nsn_island_stats(nsn_ctx *ctx, int32_t cap, double *merit0, double *m
  * owned by the context, valid until the scene changes; written by each step
  * on the context stream).  For on-device bookkeeping between steps. */
 nsn_status nsn_island_stop_device(nsn_ctx *ctx, const int32_t **stopped_at);
+/* Enqueues on the context stream a device-to-device copy of those n_islands
+ * int32 into dst_device (a device buffer of the caller).  Allocates nothing. */
+nsn_status nsn_island_stop_copy(nsn_ctx *ctx, int32_t *dst_device);
 
 /* Merits of the last warm-started step: zero start, warm start, and whether
  * the warm start was rejected (island_stop = 1: the number of islands where

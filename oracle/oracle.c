@@ -946,6 +946,11 @@ static void build_rhs(orc_ctx *c, double *yb) {
  * Sparse Linear Systems, 2nd ed., Alg. 6.20 with a left Jacobi preconditioner
  * P = diag(A)^-1).  x_0 = 0.  Stops after iters iterations, or when
  * ||r_k||_P <= eta ||r_0||_P if eta > 0.  Returns iterations done. */
+/* CR stops once ||r||_P has fallen to CR_FLOOR of ||r_0||_P: past that the
+ * recurrences run on rounding noise (rho = z^T A z no longer decreases and
+ * beta = rho_k / rho_{k-1} can exceed 1 at every iteration). */
+#define CR_FLOOR 1e-12
+
 static int pcr(orc_ctx *c, int iters, double eta, double *x, double *res_hist) {
   int R = c->R;
   if (R == 0) return 0;
@@ -964,7 +969,7 @@ static int pcr(orc_ctx *c, int iters, double eta, double *x, double *res_hist) {
     for (int i = 0; i < R; i++) cur += r[i] * z[i];
     cur = sqrt(cur);
     if (k > 0 && res_hist) res_hist[k] = cur;
-    if (res0 == 0.0) break;
+    if (res0 == 0.0 || cur <= CR_FLOOR * res0) break;
     if (eta > 0.0 && cur <= eta * res0) break;
     double apq = 0.0;
     for (int i = 0; i < R; i++) apq += Ap[i] * Ap[i] / c->pdiag[i];   /* Ap^T P Ap */
@@ -1023,7 +1028,8 @@ static int pcr_islands(orc_ctx *c, int iters, const double *eta, const int *skip
     for (int i = 0; i < R; i++) acc[isl[i]] += r[i] * z[i];
     for (int i = 0; i < ni; i++) {
       if (done[i]) continue;
-      if (res0[i] == 0.0 || (eta && eta[i] > 0.0 && sqrt(acc[i]) <= eta[i] * res0[i])) done[i] = 1;
+      const double cur = sqrt(acc[i]);
+      if (res0[i] == 0.0 || cur <= CR_FLOOR * res0[i] || (eta && eta[i] > 0.0 && cur <= eta[i] * res0[i])) done[i] = 1;
     }
     for (int i = 0; i < ni; i++) acc[i] = 0.0;
     for (int i = 0; i < R; i++) acc[isl[i]] += Ap[i] * Ap[i] / c->pdiag[i];   /* Ap^T P Ap */

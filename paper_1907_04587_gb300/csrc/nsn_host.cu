@@ -963,6 +963,8 @@ nsn_status do_time_operator(nsn_ctx *c, int iters, float *ms_body, float *ms_row
   cudaEvent_t e[3];
   for (auto &x : e) CUDA_TRY(c, cudaEventCreate(&x));
   CUDA_TRY(c, cudaMemsetAsync(D.fl, 0, sizeof(Flags), st));
+  // island mode: time the apply with every island taking part
+  if (D.isl_on && D.ni) CUDA_TRY(c, cudaMemsetAsync(D.isl.crdone, 0, sizeof(int) * D.ni, st));
   Launcher<T> Lr{c, D, st};
   double tb = 0.0, tr = 0.0;
   const int buf = c->cfg.newton_iters & 1;  // entries written by the final evaluation of the last step
@@ -979,6 +981,7 @@ nsn_status do_time_operator(nsn_ctx *c, int iters, float *ms_body, float *ms_row
     tb += a; tr += b;
   }
   for (auto &x : e) cudaEventDestroy(x);
+  if (D.isl_on && D.ni) CUDA_TRY(c, cudaMemsetAsync(D.isl.acc, 0, sizeof(double) * ISL_ACC * D.ni, st));
   CUDA_TRY(c, cudaGetLastError());
   if (ms_body) *ms_body = float(tb / std::max(iters, 1));
   if (ms_row) *ms_row = float(tr / std::max(iters, 1));
@@ -1497,6 +1500,16 @@ nsn_status nsn_island_stats(nsn_ctx *c, int32_t cap, double *merit0, double *mer
   if (merit_final) CUDA_TRY(c, cudaMemcpyAsync(merit_final, I.mf, sizeof(double) * ni, cudaMemcpyDeviceToHost, st));
   if (stopped_at) CUDA_TRY(c, cudaMemcpyAsync(stopped_at, I.stop, sizeof(int32_t) * ni, cudaMemcpyDeviceToHost, st));
   CUDA_TRY(c, cudaStreamSynchronize(st));
+  return NSN_OK;
+}
+
+nsn_status nsn_island_stop_copy(nsn_ctx *c, int32_t *dst_device) {
+  if (!c || !dst_device) return NSN_ERR_INVALID_ARG;
+  nsn_status s = ensure_built(c);
+  if (s != NSN_OK) return s;
+  if (!c->L.ni) return NSN_OK;
+  const int *src = c->cfg.precision == NSN_FP64 ? c->d64.isl.stop : c->d32.isl.stop;
+  CUDA_TRY(c, cudaMemcpyAsync(dst_device, src, sizeof(int32_t) * c->L.ni, cudaMemcpyDeviceToDevice, c->stream));
   return NSN_OK;
 }
 

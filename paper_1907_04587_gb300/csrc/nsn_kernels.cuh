@@ -499,6 +499,38 @@ __device__ __forceinline__ void side_diff(const Side<T> &A, const Side<T> &B, T 
   for (int k = 0; k < 3; k++) dd[k] = ((A.x0[k] - B.x0[k]) + (A.hu[k] - B.hu[k])) + (A.r[k] - B.r[k]);
 }
 
+// The position-level constraint values (contact gap, joint anchor offset and
+// hinge alignment) are differences of terms of the size of the bodies that
+// nearly cancel; they are evaluated in FP64 from the stored state (FP32 in
+// the production build), so that their rounding stays far below the
+// residual tolerance instead of ~1e-7 of the body size.  This is once per
+// row per Newton iteration, outside the CR loop.
+template <typename T>
+__device__ __forceinline__ void point_parts_f64(const Dev<T> &D, int enc, const T *p, double *x0, double *hu,
+                                                double *r) {
+  const double h = D.h;
+  if (enc >= 0) {
+    double q[4], R[9], pd[3] = {double(p[0]), double(p[1]), double(p[2])};
+    for (int k = 0; k < 4; k++) q[k] = double(D.rq[k][enc]);
+    quat_R(q, R);
+    mat3v(R, pd, r);
+    for (int k = 0; k < 3; k++) { x0[k] = double(D.rx0[k][enc]); hu[k] = h * double(D.ru[k][enc]); }
+  } else if (enc == -1) {
+    for (int k = 0; k < 3; k++) { x0[k] = double(p[k]); hu[k] = 0.0; r[k] = 0.0; }
+  } else {
+    const int i = -enc - 2;
+    for (int k = 0; k < 3; k++) { x0[k] = double(D.px0[k][i]); hu[k] = h * double(D.pu[k][i]); r[k] = 0.0; }
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void gap_f64(const Dev<T> &D, int ea, const T *pa, int eb, const T *pb, double *dd) {
+  double xa[3], ha[3], ra[3], xb[3], hb[3], rb[3];
+  point_parts_f64(D, ea, pa, xa, ha, ra);
+  point_parts_f64(D, eb, pb, xb, hb, rb);
+  for (int k = 0; k < 3; k++) dd[k] = ((xa[k] - xb[k]) + (ha[k] - hb[k])) + (ra[k] - rb[k]);
+}
+
 // side Jacobian along direction d: [d, r x d] (rigid) or [d] (particle), times sgn
 template <typename T>
 __device__ __forceinline__ void side_row(const Side<T> &s, const T *d, T sgn, T *J6) {
@@ -587,9 +619,9 @@ __global__ void k_eval_contacts(Dev<T> D, int buf, int force) {
   Side<T> A, B;
   load_side(D, D.cba[c], pa, A);
   load_side(D, D.cbb[c], pb, B);
-  T dd[3];
-  side_diff(A, B, dd);
-  T Cn = dot3(n, dd) - D.cdd[c];
+  double dd[3];
+  gap_f64(D, D.cba[c], pa, D.cbb[c], pb, dd);
+  const T Cn = T((double(n[0]) * dd[0] + double(n[1]) * dd[1] + double(n[2]) * dd[2]) - double(D.cdd[c]));
   // geometric normal row and effective-mass r (Eq. rscaling)
   T Ja[6], Jb[6];
   side_row(A, n, T(1), Ja);
@@ -677,8 +709,8 @@ __global__ void k_eval_joints(Dev<T> D, int buf, int force) {
   load_side(D, eb, pb, B);
   const T e = D.je[j];
   const int base = 3 * D.nc + 5 * j;
-  T dd[3];
-  side_diff(A, B, dd);
+  double dd[3];
+  gap_f64(D, ea, pa, eb, pb, dd);
   for (int k = 0; k < 3; k++) {
     T ek[3] = {T(0), T(0), T(0)};
     ek[k] = T(1);
@@ -687,29 +719,37 @@ __global__ void k_eval_joints(Dev<T> D, int buf, int force) {
     side_row(B, ek, T(-1), Jb);
     write_entry(D, D.re0[base + k], Ja, buf);
     write_entry(D, D.re1[base + k], Jb, buf);
-    T cb = dd[k];
+    const T cb = T(dd[k]);
     D.cdiag[base + k] = e / (h * h);
     D.hv[base + k] = (cb + e * D.lam[base + k]) / h;
   }
   T aw[3], bl[2][3], bw[2][3];
+  double awd[3], Rbd[9];
   if (ea >= 0) {
     T q[4], R[9];
     for (int k = 0; k < 4; k++) q[k] = D.rq[k][ea];
     quat_R(q, R);
     mat3v(R, axa, aw);
+    double qd[4], Rd[9], ad[3] = {double(axa[0]), double(axa[1]), double(axa[2])};
+    for (int k = 0; k < 4; k++) qd[k] = double(q[k]);
+    quat_R(qd, Rd);
+    mat3v(Rd, ad, awd);
   } else {
-    for (int k = 0; k < 3; k++) aw[k] = axa[k];
+    for (int k = 0; k < 3; k++) { aw[k] = axa[k]; awd[k] = double(axa[k]); }
   }
   basis(axb, bl[0], bl[1]);
   T Rb[9];
   if (eb >= 0) {
     T q[4];
-    for (int k = 0; k < 4; k++) q[k] = D.rq[k][eb];
+    double qd[4];
+    for (int k = 0; k < 4; k++) { q[k] = D.rq[k][eb]; qd[k] = double(q[k]); }
     quat_R(q, Rb);
+    quat_R(qd, Rbd);
   }
   for (int k = 0; k < 2; k++) {
-    if (eb >= 0) mat3v(Rb, bl[k], bw[k]);
-    else for (int m = 0; m < 3; m++) bw[k][m] = bl[k][m];
+    double bwd[3], bld[3] = {double(bl[k][0]), double(bl[k][1]), double(bl[k][2])};
+    if (eb >= 0) { mat3v(Rb, bl[k], bw[k]); mat3v(Rbd, bld, bwd); }
+    else for (int m = 0; m < 3; m++) { bw[k][m] = bl[k][m]; bwd[m] = bld[m]; }
     T axb2[3];
     cross3(aw, bw[k], axb2);
     T Ja[6] = {0, 0, 0, axb2[0], axb2[1], axb2[2]};
@@ -717,7 +757,7 @@ __global__ void k_eval_joints(Dev<T> D, int buf, int force) {
     const int row = base + 3 + k;
     write_entry(D, D.re0[row], Ja, buf);
     write_entry(D, D.re1[row], Jb, buf);
-    T cb = dot3(aw, bw[k]);
+    const T cb = T(awd[0] * bwd[0] + awd[1] * bwd[1] + awd[2] * bwd[2]);
     D.cdiag[row] = e / (h * h);
     D.hv[row] = (cb + e * D.lam[row]) / h;
   }
@@ -1126,7 +1166,7 @@ __global__ void __launch_bounds__(BLOCK) k_row_pass(Dev<T> D, int force) {
         a[0].add_prod(zi, az);
         a[1].add_prod(az, paz);
         a[2].add_prod(paz, api);
-        if (D.cr_tol) a[3].add_prod(zi, zi / Pi);
+        a[3].add_prod(zi, zi / Pi);
         a[4].add_prod(api, Pi * api);
       }
     }
@@ -1176,7 +1216,7 @@ __global__ void __launch_bounds__(BLOCK) k_row_pass(Dev<T> D, int force) {
           a[0].add_prod(zz[k], az);
           a[1].add_prod(az, paz);
           a[2].add_prod(paz, api);
-          if (D.cr_tol) a[3].add_prod(zz[k], zz[k] / Pi);
+          a[3].add_prod(zz[k], zz[k] / Pi);
           a[4].add_prod(api, Pi * api);
         }
       }
@@ -1391,6 +1431,17 @@ __global__ void __launch_bounds__(RED_THREADS) k_merit(Dev<T> D, int n, int forc
   }
 }
 
+// CR stops once ||r||_P has fallen to this fraction of ||r_0||_P: past it the
+// recurrences run on rounding noise of the bulk type (rho = z^T A z stops
+// decreasing and beta = rho_k / rho_{k-1} can exceed 1 at every iteration, so
+// p grows geometrically).  FP32: a little above the rounding of the operator
+// apply; FP64: the oracle's value, well above FP64 rounding so that the
+// iteration at which it is crossed does not depend on summation order.
+template <typename T>
+__device__ __forceinline__ double cr_floor() { return 1e-12; }
+template <>
+__device__ __forceinline__ double cr_floor<float>() { return 1e-6; }
+
 // ------------------------------------------------------------------------------------
 // K7: CR with one global synchronisation per iteration.  The scalar kernel
 // reduces the row-pass partials (d1 = z^T Az, d2 = Az^T P Az, d3 = Az^T P Ap,
@@ -1408,7 +1459,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_cr_scalars(Dev<T> D, int k) {
     const double d1 = r4[0], d2 = r4[1], d3 = r4[2], d4 = r4[3], d5 = r4[4];
     int st = 0;
     const double cur = sqrt(d4 > 0.0 ? d4 : 0.0);
-    if (D.sc->res0 == 0.0) st = 1;
+    if (D.sc->res0 == 0.0 || cur <= cr_floor<T>() * D.sc->res0) st = 1;
     if (D.cr_tol && cur <= D.sc->eta * D.sc->res0) st = 1;
     double beta = 0.0, rho = d1, apap = d2;
     if (k > 0) {
@@ -1474,7 +1525,7 @@ __global__ void k_cr_scalars_isl(Dev<T> D, int k) {
     int st = 0;
     const double cur = sqrt(d4 > 0.0 ? d4 : 0.0);
     const double r0 = D.isl.res0[i];
-    if (r0 == 0.0) st = 1;
+    if (r0 == 0.0 || cur <= cr_floor<T>() * r0) st = 1;
     if (D.cr_tol && cur <= D.isl.eta[i] * r0) st = 1;
     double beta = 0.0, rho = d1, apap = d2;
     if (k > 0) {

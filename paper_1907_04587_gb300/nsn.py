@@ -108,6 +108,7 @@ def lib():
         "nsn_islands": (C.c_int, [_vp, _ip, _ip]),
         "nsn_island_stats": (C.c_int, [_vp, C.c_int32, _dp, _dp, _ip]),
         "nsn_island_stop_device": (C.c_int, [_vp, C.POINTER(_vp)]),
+        "nsn_island_stop_copy": (C.c_int, [_vp, _vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
