@@ -199,7 +199,10 @@ nsn_status nsn_apply_operator(nsn_ctx *ctx, const double *x, double *y);
 nsn_status nsn_solve(nsn_ctx *ctx, int32_t iters, double *dlambda, double *du);
 nsn_status nsn_get_system(nsn_ctx *ctx, double *b, double *diag, double *hvec, double *g);
 
-/* Number of kernel launches in one nsn_step (the captured graph's nodes). */
+/* Number of kernels executed by the last step of nsn_step.  Under the CUDA
+ * graph (use_graph = 1) the Newton and CR loops are conditional WHILE nodes,
+ * so this counts the loop bodies actually run; eager launch (use_graph = 0)
+ * launches every iteration up to the caps, finished ones returning at once. */
 nsn_status nsn_last_launch_count(nsn_ctx *ctx, int32_t *kernels_per_step);
 
 /* Times the two kernels of one Schur operator apply (Eq. schur_system,
@@ -273,7 +276,7 @@ nsn_status nsn_mlp_train_step(nsn_ctx *ctx, const float *X, const float *T, cons
                               float *loss);
 /* Features of every contact at the current (committed) state and, if Ytarget
  * is not NULL, the current multipliers as training targets (device arrays
- * X[nc][16], Ytarget[nc][4]). */
+ * X[nc][16], Ytarget[nc][4], contacts in the order they were added). */
 nsn_status nsn_contact_features(nsn_ctx *ctx, float *X, float *Ytarget);
 
 /* ---- allocation-free operator apply -----------------------------------------
@@ -288,10 +291,13 @@ nsn_status nsn_contact_features(nsn_ctx *ctx, float *X, float *Ytarget);
  * the CR loop.  x and y are caller-owned device arrays of nsn_counts() rows
  * (float32); stream is a cudaStream_t or NULL for the context stream.  The
  * call allocates nothing: the per-entry scratch lives in a fixed static device
- * array of NSN_NOALLOC_MAX_ENTRIES floats (16 MiB) that every GPU loading the
- * library holds until the process exits.  Scenes needing more row slots than
- * that (2 per contact or joint row, 4 per tet row) are rejected with
- * NSN_ERR_INVALID_ARG.  All calls share the array and it keeps the last call's
+ * array of NSN_NOALLOC_MAX_ENTRIES floats (16 MiB), and x and y are permuted
+ * into the context's internal (island) row order through two static arrays of
+ * NSN_NOALLOC_MAX_ENTRIES / 2 floats (8 MiB each); every GPU loading the
+ * library holds them until the process exits.  Scenes needing more row slots
+ * than NSN_NOALLOC_MAX_ENTRIES (2 per contact or joint row, 4 per tet row) are
+ * rejected with NSN_ERR_INVALID_ARG.  All calls share the arrays and they keep
+ * the last call's
  * contents; each call first clears the slots it uses (the world side of a
  * contact is read as zero), with a memset on the stream, which allocates
  * nothing.  Calls that overlap on the GPU (different streams, or different

@@ -946,9 +946,11 @@ static void build_rhs(orc_ctx *c, double *yb) {
  * Sparse Linear Systems, 2nd ed., Alg. 6.20 with a left Jacobi preconditioner
  * P = diag(A)^-1).  x_0 = 0.  Stops after iters iterations, or when
  * ||r_k||_P <= eta ||r_0||_P if eta > 0.  Returns iterations done. */
-/* CR stops once ||r||_P has fallen to CR_FLOOR of ||r_0||_P: past that the
- * recurrences run on rounding noise (rho = z^T A z no longer decreases and
- * beta = rho_k / rho_{k-1} can exceed 1 at every iteration). */
+/* CR stops once ||r||_P has fallen to CR_FLOOR of ||r_0||_P, or when it
+ * grows: preconditioned CR minimises ||r||_P over the Krylov space, so in exact
+ * arithmetic it never increases, and past that point the recurrences run on
+ * rounding noise (rho = z^T A z no longer decreases and beta = rho_k /
+ * rho_{k-1} can exceed 1 at every iteration). */
 #define CR_FLOOR 1e-12
 
 static int pcr(orc_ctx *c, int iters, double eta, double *x, double *res_hist) {
@@ -964,12 +966,14 @@ static int pcr(orc_ctx *c, int iters, double eta, double *x, double *res_hist) {
   double res0 = sqrt(rz);
   if (res_hist) res_hist[0] = res0;
   int k = 0;
+  double prev = res0;
   for (; k < iters; k++) {
     double cur = 0.0;
     for (int i = 0; i < R; i++) cur += r[i] * z[i];
     cur = sqrt(cur);
     if (k > 0 && res_hist) res_hist[k] = cur;
-    if (res0 == 0.0 || cur <= CR_FLOOR * res0) break;
+    if (res0 == 0.0 || cur <= CR_FLOOR * res0 || (k > 0 && cur > prev)) break;
+    prev = cur;
     if (eta > 0.0 && cur <= eta * res0) break;
     double apq = 0.0;
     for (int i = 0; i < R; i++) apq += Ap[i] * Ap[i] / c->pdiag[i];   /* Ap^T P Ap */
@@ -1011,6 +1015,7 @@ static int pcr_islands(orc_ctx *c, int iters, const double *eta, const int *skip
   double *zb = malloc(sizeof(double) * (c->D + 1)), *yb = malloc(sizeof(double) * (c->D + 1));
   double *rho = calloc(ni + 1, sizeof(double)), *res0 = calloc(ni + 1, sizeof(double));
   double *acc = calloc(ni + 1, sizeof(double)), *alpha = calloc(ni + 1, sizeof(double));
+  double *prev = calloc(ni + 1, sizeof(double));
   int *done = calloc(ni + 1, sizeof(int)), *its = calloc(ni + 1, sizeof(int));
   const int *isl = c->row_isl;
   for (int i = 0; i < ni; i++) done[i] = skip && skip[i];
@@ -1021,7 +1026,7 @@ static int pcr_islands(orc_ctx *c, int iters, const double *eta, const int *skip
   }
   apply_A(c, z, Az, zb, yb);
   for (int i = 0; i < R; i++) { Ap[i] = Az[i]; rho[isl[i]] += z[i] * Az[i]; res0[isl[i]] += r[i] * z[i]; }
-  for (int i = 0; i < ni; i++) res0[i] = sqrt(res0[i]);
+  for (int i = 0; i < ni; i++) { res0[i] = sqrt(res0[i]); prev[i] = res0[i]; }
   for (int k = 0; k < iters; k++) {
     /* stop tests at the top of iteration k, per island */
     for (int i = 0; i < ni; i++) acc[i] = 0.0;
@@ -1029,7 +1034,10 @@ static int pcr_islands(orc_ctx *c, int iters, const double *eta, const int *skip
     for (int i = 0; i < ni; i++) {
       if (done[i]) continue;
       const double cur = sqrt(acc[i]);
-      if (res0[i] == 0.0 || cur <= CR_FLOOR * res0[i] || (eta && eta[i] > 0.0 && cur <= eta[i] * res0[i])) done[i] = 1;
+      if (res0[i] == 0.0 || cur <= CR_FLOOR * res0[i] || (k > 0 && cur > prev[i]) ||
+          (eta && eta[i] > 0.0 && cur <= eta[i] * res0[i]))
+        done[i] = 1;
+      prev[i] = cur;
     }
     for (int i = 0; i < ni; i++) acc[i] = 0.0;
     for (int i = 0; i < R; i++) acc[isl[i]] += Ap[i] * Ap[i] / c->pdiag[i];   /* Ap^T P Ap */
@@ -1071,7 +1079,7 @@ static int pcr_islands(orc_ctx *c, int iters, const double *eta, const int *skip
   int kmax = 0;
   for (int i = 0; i < ni; i++) if (its[i] > kmax) kmax = its[i];
   free(r); free(z); free(p); free(Az); free(Ap); free(zb); free(yb);
-  free(rho); free(res0); free(acc); free(alpha); free(done); free(its);
+  free(rho); free(res0); free(acc); free(alpha); free(done); free(its); free(prev);
   return kmax;
 }
 

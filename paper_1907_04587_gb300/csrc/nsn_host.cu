@@ -9,6 +9,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -53,6 +54,10 @@ struct Layout {
   int ni = 0;                       // islands: connected components of bodies through constraints
   std::vector<int> body_isl;        // ABI body id -> island
   std::vector<int> risl, bisl_r, bisl_p;  // island of each row / rigid body / particle
+  // Internal order: bodies, contacts, joints and tets sorted by island (stable),
+  // so that each island's bodies, entries and rows are contiguous.  The ABI
+  // keeps the caller's order; these map internal -> ABI index.
+  std::vector<int> cperm, jperm, tperm, row_abi;
 };
 
 struct MlpState {
@@ -87,7 +92,9 @@ struct nsn_ctx {
   float *d_stage = nullptr;  // AoS staging for state transfer (13 floats per body)
   float *d_backup = nullptr; // committed state saved by nsn_linearize
   cudaGraphExec_t graph = nullptr;
-  int launches_per_step = 0;
+  int launches_per_step = 0;  // kernels executed in the last step
+  struct Segments { int prefix = 0, head = 0, cr = 0, tail = 0, suffix = 0; } seg;  // kernels per graph segment
+  int last_newton_n = 0;     // Newton loop bodies executed in the last step
   bool linearized = false;
   int lin_buf = 0;           // entry buffer written by the kept linearisation
   int kept_buf = -1;         // entry buffer of the system kept by the last step / linearisation
@@ -143,7 +150,7 @@ void uf_union(std::vector<int> &par, int a, int b) {
   if (a < b) par[b] = a; else par[a] = b;
 }
 
-void build_islands(const HostScene &S, Layout &L, int nb) {
+void find_islands(const HostScene &S, Layout &L, int nb) {
   std::vector<int> par(nb);
   for (int i = 0; i < nb; i++) par[i] = i;
   for (const auto &r : S.contacts) uf_union(par, r.body_a, r.body_b);
@@ -158,23 +165,14 @@ void build_islands(const HostScene &S, Layout &L, int nb) {
     if (id[r] < 0) id[r] = L.ni++;
     L.body_isl[i] = id[r];
   }
-  L.bisl_r.resize(L.nr);
-  L.bisl_p.resize(L.np);
-  for (int i = 0; i < L.nr; i++) L.bisl_r[i] = L.body_isl[L.rig_of[i]];
-  for (int i = 0; i < L.np; i++) L.bisl_p[i] = L.body_isl[L.par_of[i]];
-  L.risl.assign(L.R, 0);
-  for (int ci = 0; ci < L.nc; ci++) {
-    const auto &r = S.contacts[ci];
-    const int isl = L.body_isl[r.body_a >= 0 ? r.body_a : r.body_b];
-    for (int k = 0; k < 3; k++) L.risl[3 * ci + k] = isl;
-  }
-  for (int j = 0; j < L.nj; j++) {
-    const auto &r = S.joints[j];
-    const int isl = L.body_isl[r.body_a >= 0 ? r.body_a : r.body_b];
-    for (int k = 0; k < 5; k++) L.risl[3 * L.nc + 5 * j + k] = isl;
-  }
-  for (int t = 0; t < L.nt; t++)
-    for (int k = 0; k < 3; k++) L.risl[L.Rpair + 3 * t + k] = L.body_isl[S.tets[t].v[0]];
+}
+
+// stable order of n items by key
+std::vector<int> order_by(int n, const std::function<int(int)> &key) {
+  std::vector<int> o(n);
+  for (int i = 0; i < n; i++) o[i] = i;
+  std::stable_sort(o.begin(), o.end(), [&](int a, int b) { return key(a) < key(b); });
+  return o;
 }
 
 // ------------------------------------------------------------------------------------
@@ -185,8 +183,10 @@ nsn_status build_layout(nsn_ctx *c) {
   Layout &L = c->L;
   L = Layout();
   const int nb = int(S.kind.size());
+  find_islands(S, L, nb);
+  // bodies in island order (rigid and particle numbered separately)
   L.bmap.resize(nb);
-  for (int i = 0; i < nb; i++) {
+  for (int i : order_by(nb, [&](int b) { return L.body_isl[b]; })) {
     if (S.kind[i] == NSN_RIGID) { L.bmap[i] = L.nr++; L.rig_of.push_back(i); }
     else { L.bmap[i] = -2 - L.np++; L.par_of.push_back(i); }
   }
@@ -195,19 +195,46 @@ nsn_status build_layout(nsn_ctx *c) {
   L.nt = int(S.tets.size());
   L.Rpair = 3 * L.nc + 5 * L.nj;
   L.R = L.Rpair + 3 * L.nt;
+  // constraints in island order
+  auto isl2 = [&](int a, int b) { return L.body_isl[a >= 0 ? a : b]; };
+  L.cperm = order_by(L.nc, [&](int i) { return isl2(S.contacts[i].body_a, S.contacts[i].body_b); });
+  L.jperm = order_by(L.nj, [&](int i) { return isl2(S.joints[i].body_a, S.joints[i].body_b); });
+  L.tperm = order_by(L.nt, [&](int i) { return L.body_isl[S.tets[i].v[0]]; });
+  L.row_abi.resize(L.R);
+  L.risl.resize(L.R);
+  for (int ci = 0; ci < L.nc; ci++) {
+    const auto &r = S.contacts[L.cperm[ci]];
+    for (int k = 0; k < 3; k++) { L.row_abi[3 * ci + k] = 3 * L.cperm[ci] + k; L.risl[3 * ci + k] = isl2(r.body_a, r.body_b); }
+  }
+  for (int j = 0; j < L.nj; j++) {
+    const auto &r = S.joints[L.jperm[j]];
+    for (int k = 0; k < 5; k++) {
+      L.row_abi[3 * L.nc + 5 * j + k] = 3 * L.nc + 5 * L.jperm[j] + k;
+      L.risl[3 * L.nc + 5 * j + k] = isl2(r.body_a, r.body_b);
+    }
+  }
+  for (int t = 0; t < L.nt; t++)
+    for (int k = 0; k < 3; k++) {
+      L.row_abi[L.Rpair + 3 * t + k] = L.Rpair + 3 * L.tperm[t] + k;
+      L.risl[L.Rpair + 3 * t + k] = L.body_isl[S.tets[L.tperm[t]].v[0]];
+    }
+  L.bisl_r.resize(L.nr);
+  L.bisl_p.resize(L.np);
+  for (int i = 0; i < L.nr; i++) L.bisl_r[i] = L.body_isl[L.rig_of[i]];
+  for (int i = 0; i < L.np; i++) L.bisl_p[i] = L.body_isl[L.par_of[i]];
   // (row, side, body) list
   struct Side { int row, slot, enc; };
   std::vector<Side> sides;
   sides.reserve(size_t(L.R) * 2 + size_t(L.nt) * 6);
   for (int ci = 0; ci < L.nc; ci++) {
-    int a = S.contacts[ci].body_a, b = S.contacts[ci].body_b;
+    int a = S.contacts[L.cperm[ci]].body_a, b = S.contacts[L.cperm[ci]].body_b;
     for (int k = 0; k < 3; k++) {
       if (a >= 0) sides.push_back({3 * ci + k, 0, L.bmap[a]});
       if (b >= 0) sides.push_back({3 * ci + k, 1, L.bmap[b]});
     }
   }
   for (int j = 0; j < L.nj; j++) {
-    int a = S.joints[j].body_a, b = S.joints[j].body_b;
+    int a = S.joints[L.jperm[j]].body_a, b = S.joints[L.jperm[j]].body_b;
     for (int k = 0; k < 5; k++) {
       int row = 3 * L.nc + 5 * j + k;
       if (a >= 0) sides.push_back({row, 0, L.bmap[a]});
@@ -216,7 +243,7 @@ nsn_status build_layout(nsn_ctx *c) {
   }
   for (int t = 0; t < L.nt; t++)
     for (int k = 0; k < 3; k++)
-      for (int q = 0; q < 4; q++) sides.push_back({L.Rpair + 3 * t + k, q, L.bmap[S.tets[t].v[q]]});
+      for (int q = 0; q < 4; q++) sides.push_back({L.Rpair + 3 * t + k, q, L.bmap[S.tets[L.tperm[t]].v[q]]});
   // counting sort by body: rigid then particle
   std::vector<int> rcnt(L.nr + 1, 0), pcnt(L.np + 1, 0);
   for (auto &s : sides) {
@@ -248,7 +275,6 @@ nsn_status build_layout(nsn_ctx *c) {
       L.eslot[e] = 2 * L.Rpair + 12 * t + 4 * k + s.slot;
     }
   }
-  build_islands(S, L, nb);
   return NSN_OK;
 }
 
@@ -295,12 +321,15 @@ void carve(Arena &A, Dev<T> &D, const Layout &L, int nb) {
   D.sc = A.take<Scalars>(1);
   D.fl = A.take<Flags>(1);
   D.risl = A.take<int>(L.R);
+  D.cabi = A.take<int>(L.nc);
+  D.row_abi_dev = A.take<int>(L.R);
   D.bisl_r = A.take<int>(L.nr);
   D.bisl_p = A.take<int>(L.np);
   const int ni = std::max(L.ni, 1);
   D.isl.acc = A.take<double>(size_t(ISL_ACC) * ni);
   D.isl.m0 = A.take<double>(ni); D.isl.mf = A.take<double>(ni); D.isl.mw = A.take<double>(ni);
   D.isl.eta = A.take<double>(ni); D.isl.res0 = A.take<double>(ni); D.isl.rho = A.take<double>(2 * size_t(ni));
+  D.isl.res_prev = A.take<double>(ni);
   D.isl.alpha = A.take<double>(ni); D.isl.beta = A.take<double>(ni);
   D.isl.alpha_f = A.take<float>(ni); D.isl.beta_f = A.take<float>(ni);
   D.isl.stop = A.take<int>(ni); D.isl.crdone = A.take<int>(ni);
@@ -373,7 +402,7 @@ nsn_status upload(nsn_ctx *c, Dev<T> &D) {
     std::vector<T> pa[3], pb[3], n[3], d(L.nc), mu(L.nc);
     for (int k = 0; k < 3; k++) { pa[k].resize(L.nc); pb[k].resize(L.nc); n[k].resize(L.nc); }
     for (int i = 0; i < L.nc; i++) {
-      const nsn_contact &r = S.contacts[i];
+      const nsn_contact &r = S.contacts[L.cperm[i]];
       a[i] = r.body_a >= 0 ? L.bmap[r.body_a] : -1;
       b[i] = r.body_b >= 0 ? L.bmap[r.body_b] : -1;
       double nn = std::sqrt(double(r.n[0]) * r.n[0] + double(r.n[1]) * r.n[1] + double(r.n[2]) * r.n[2]);
@@ -391,7 +420,7 @@ nsn_status upload(nsn_ctx *c, Dev<T> &D) {
     std::vector<T> pa[3], pb[3], xa[3], xb[3], e(L.nj);
     for (int k = 0; k < 3; k++) { pa[k].resize(L.nj); pb[k].resize(L.nj); xa[k].resize(L.nj); xb[k].resize(L.nj); }
     for (int i = 0; i < L.nj; i++) {
-      const nsn_revolute &r = S.joints[i];
+      const nsn_revolute &r = S.joints[L.jperm[i]];
       a[i] = r.body_a >= 0 ? L.bmap[r.body_a] : -1;
       b[i] = r.body_b >= 0 ? L.bmap[r.body_b] : -1;
       for (int k = 0; k < 3; k++) { pa[k][i] = T(r.pa[k]); pb[k][i] = T(r.pb[k]); xa[k][i] = T(r.axis_a[k]); xb[k][i] = T(r.axis_b[k]); }
@@ -410,7 +439,7 @@ nsn_status upload(nsn_ctx *c, Dev<T> &D) {
     std::vector<int> v(4 * L.nt);
     std::vector<T> Dmi(9 * L.nt), Ve(L.nt), C1(L.nt), D1(L.nt), al(L.nt);
     for (int t = 0; t < L.nt; t++) {
-      const nsn_tet &r = S.tets[t];
+      const nsn_tet &r = S.tets[L.tperm[t]];
       for (int q = 0; q < 4; q++) v[4 * t + q] = -L.bmap[r.v[q]] - 2;
       double Dm[9];
       for (int row = 0; row < 3; row++)
@@ -437,6 +466,8 @@ nsn_status upload(nsn_ctx *c, Dev<T> &D) {
   CUDA_TRY(c, cudaMemsetAsync(D.sc, 0, sizeof(Scalars), st));
   CUDA_TRY(c, cudaMemsetAsync(D.fl, 0, sizeof(Flags), st));
   CUDA_TRY(c, puti(D.risl, L.risl));
+  CUDA_TRY(c, puti(D.cabi, L.cperm));
+  CUDA_TRY(c, puti(D.row_abi_dev, L.row_abi));
   CUDA_TRY(c, puti(D.bisl_r, L.bisl_r));
   CUDA_TRY(c, puti(D.bisl_p, L.bisl_p));
   {
@@ -569,31 +600,39 @@ struct Launcher {
     count++;
     if (D.np) { k_begin_particle<T><<<cdiv(D.np, 128), 128, 0, st>>>(D); count++; }
   }
-  void linearize_at(int n) {  // rows, g, H~, b, diag at Newton iteration n
-    const int buf = n & 1;
+  void linearize_at(int n) {  // rows, g, H~, b, diag at Newton iteration n (or IT_DEV)
+    const int buf = n == IT_DEV ? IT_DEV : (n & 1);
     eval(buf, 0);
     body(BM_RESIDUAL, D.lam, buf, n, 0);
     rows(RM_RHS, 0);
     k_merit<T><<<1, RED_THREADS, 0, st>>>(D, n, 0);
     count++;
   }
-  void cr(int iters, int buf) {
-    if (!D.R) return;
-    for (int k = 0; k < iters; k++) {
-      body(BM_APPLY, D.z, buf, 0, 0);
-      rows(RM_APPLY, 0);
-      if (D.isl_on) {
-        k_cr_scalars_isl<T><<<cdiv(std::max(D.ni, 1), 256), 256, 0, st>>>(D, k);
-        k_cr_update_isl<T><<<D.nblk_upd, BLOCK, 0, st>>>(D, k);
-      } else {
-        k_cr_scalars<T><<<1, RED_THREADS, 0, st>>>(D, k);
-        k_cr_update<T><<<D.nblk_upd, BLOCK, 0, st>>>(D, k);
-      }
-      count += 2;
+  void cr_begin(int M) {
+    k_cr_begin<T><<<1, 1, 0, st>>>(D, M);
+    count++;
+  }
+  void cr_body(int buf, int M) {  // one CR iteration (index read on the device)
+    body(BM_APPLY, D.z, buf, 0, 0);
+    rows(RM_APPLY, 0);
+    if (D.isl_on) {
+      k_cr_scalars_isl<T><<<cdiv(std::max(D.ni, 1), 256), 256, 0, st>>>(D);
+      k_cr_update_isl<T><<<D.nblk_upd, BLOCK, 0, st>>>(D);
+    } else {
+      k_cr_scalars<T><<<1, RED_THREADS, 0, st>>>(D);
+      k_cr_update<T><<<D.nblk_upd, BLOCK, 0, st>>>(D);
     }
+    k_cr_next<T><<<1, 1, 0, st>>>(D, M);
+    count += 3;
+  }
+  void cr(int iters, int buf) {  // eager CR loop
+    if (!D.R) return;
+    cr_begin(iters);
+    for (int k = 0; k < iters; k++) cr_body(buf, iters);
   }
   void newton_update(int n) {
-    body(BM_UPDATE, D.x, n & 1, n, 0);
+    const int buf = n == IT_DEV ? IT_DEV : (n & 1);
+    body(BM_UPDATE, D.x, buf, n, 0);
     k_lambda_update<T><<<D.nblk_upd, BLOCK, 0, st>>>(D);
     count++;
   }
@@ -618,8 +657,9 @@ struct Launcher {
     k_warm_accept<T><<<D.nblk_upd, BLOCK, 0, st>>>(D);
     count += 2;
   }
-  void step() {
-    const int N = c->cfg.newton_iters, M = c->cfg.cr_iters;
+  // segments of one step (Algorithm 1): prefix, Newton loop body (head, CR
+  // loop body, tail), suffix
+  void prefix() {
     if (c->warm_mode == NSN_WARM_LEARNED && D.nc) {
       k_contact_features<T><<<cdiv(D.nc, 128), 128, 0, st>>>(D, c->mlp.X);
       count++;
@@ -628,19 +668,34 @@ struct Launcher {
     }
     begin();
     if (c->warm_mode != NSN_WARM_ZERO) warm_start();
-    for (int n = 0; n < N; n++) {
-      linearize_at(n);
-      cr(M, n & 1);
-      newton_update(n);
-    }
-    // final merit at the returned iterate
-    const int buf = N & 1;
-    eval(buf, 1);
-    body(BM_RESIDUAL, D.lam, buf, N, 1);
+  }
+  void newton_head(int M) {
+    linearize_at(IT_DEV);
+    if (D.R && M > 0) cr_begin(M);
+  }
+  void newton_tail(int N) {
+    newton_update(IT_DEV);
+    k_newton_next<T><<<1, 1, 0, st>>>(D, N);
+    count++;
+  }
+  void suffix() {  // merit at the returned iterate, multipliers kept for warm starts
+    eval(IT_DEV, 1);
+    body(BM_RESIDUAL, D.lam, IT_DEV, IT_DEV, 1);
     rows(RM_RHS, 1);
-    k_merit<T><<<1, RED_THREADS, 0, st>>>(D, N, 1);
+    k_merit<T><<<1, RED_THREADS, 0, st>>>(D, IT_FINAL, 1);
     count++;
     if (D.R) { k_copy<T><<<D.nblk_upd, BLOCK, 0, st>>>(D.lam_prev, D.lam, D.R); count++; }
+  }
+  void step() {  // eager launch of the whole step
+    const int N = c->cfg.newton_iters, M = c->cfg.cr_iters;
+    prefix();
+    for (int n = 0; n < N; n++) {
+      newton_head(M);
+      if (D.R && M > 0)
+        for (int k = 0; k < M; k++) cr_body(IT_DEV, M);
+      newton_tail(N);
+    }
+    suffix();
   }
 };
 
@@ -726,6 +781,83 @@ nsn_status ensure_built(nsn_ctx *c) {
 
 nsn_status mlp_ensure(nsn_ctx *c, int rows_needed);
 
+// The step as one CUDA graph: prefix, a conditional WHILE node for the Newton
+// loop whose body holds a conditional WHILE node for the CR loop, suffix.
+// The loop-control kernels set each node's condition on the device, so a step
+// runs only the iterations it needs (islands that stop early, CR stopped by
+// its tolerance); both loops stay bounded by their caps.
+template <typename T>
+nsn_status capture_step(nsn_ctx *c, Dev<T> &D) {
+  cudaStream_t st = c->stream;
+  const int N = c->cfg.newton_iters, M = c->cfg.cr_iters;
+  Launcher<T> Lr{c, D, st};
+  cudaGraph_t g = nullptr;
+  CUDA_TRY(c, cudaGraphCreate(&g, 0));
+  struct GraphGuard { cudaGraph_t g; ~GraphGuard() { if (g) cudaGraphDestroy(g); } } guard{g};
+  auto capture = [&](cudaGraph_t graph, const std::vector<cudaGraphNode_t> &in, auto &&fn, int &kernels,
+                     std::vector<cudaGraphNode_t> &out) -> cudaError_t {
+    cudaError_t e = cudaStreamBeginCaptureToGraph(st, graph, in.empty() ? nullptr : in.data(), nullptr, in.size(),
+                                                  cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    const int before = Lr.count;
+    fn();
+    kernels = Lr.count - before;
+    cudaStreamCaptureStatus cs;
+    const cudaGraphNode_t *d = nullptr;
+    size_t nd = 0;
+    e = cudaStreamGetCaptureInfo(st, &cs, nullptr, nullptr, &d, nullptr, &nd);
+    if (e == cudaSuccess) out.assign(d, d + nd);
+    cudaGraph_t gout = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(st, &gout);
+    return e != cudaSuccess ? e : e2;
+  };
+  auto while_node = [&](cudaGraph_t graph, const std::vector<cudaGraphNode_t> &in, cudaGraphConditionalHandle h,
+                        cudaGraphNode_t &node, cudaGraph_t &body) -> cudaError_t {
+    alignas(cudaGraphNodeParams) unsigned char raw[sizeof(cudaGraphNodeParams)];
+    std::memset(raw, 0, sizeof raw);
+    cudaGraphNodeParams &p = *reinterpret_cast<cudaGraphNodeParams *>(raw);
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = h;
+    p.conditional.type = cudaGraphCondTypeWhile;
+    p.conditional.size = 1;
+    cudaError_t e = cudaGraphAddNode(&node, graph, in.empty() ? nullptr : in.data(), nullptr, in.size(), &p);
+    if (e == cudaSuccess) body = p.conditional.phGraph_out[0];
+    return e;
+  };
+  c->seg = nsn_ctx::Segments();
+  std::vector<cudaGraphNode_t> deps, tmp;
+  CUDA_TRY(c, capture(g, deps, [&] { Lr.prefix(); }, c->seg.prefix, deps));
+  if (N > 0) {
+    cudaGraphConditionalHandle hN = 0, hC = 0;
+    CUDA_TRY(c, cudaGraphConditionalHandleCreate(&hN, g, 1, cudaGraphCondAssignDefault));
+    cudaGraphNode_t nN;
+    cudaGraph_t bN = nullptr;
+    CUDA_TRY(c, while_node(g, deps, hN, nN, bN));
+    const bool has_cr = D.R && M > 0;
+    if (has_cr) CUDA_TRY(c, cudaGraphConditionalHandleCreate(&hC, bN, 0, 0));
+    D.hN = hN;
+    D.hC = hC;
+    std::vector<cudaGraphNode_t> body_deps;
+    cudaError_t e = capture(bN, {}, [&] { Lr.newton_head(M); }, c->seg.head, body_deps);
+    if (e == cudaSuccess && has_cr) {
+      cudaGraphNode_t nC;
+      cudaGraph_t bC = nullptr;
+      e = while_node(bN, body_deps, hC, nC, bC);
+      if (e == cudaSuccess) e = capture(bC, {}, [&] { Lr.cr_body(IT_DEV, M); }, c->seg.cr, tmp);
+      body_deps.assign(1, nC);
+    }
+    if (e == cudaSuccess) e = capture(bN, body_deps, [&] { Lr.newton_tail(N); }, c->seg.tail, tmp);
+    D.hN = 0;
+    D.hC = 0;
+    if (e != cudaSuccess) return fail(c, NSN_ERR_CUDA, "graph capture (Newton / CR loops): %s", cudaGetErrorString(e));
+    deps.assign(1, nN);
+  }
+  CUDA_TRY(c, capture(g, deps, [&] { Lr.suffix(); }, c->seg.suffix, tmp));
+  const cudaError_t e = cudaGraphInstantiate(&c->graph, g, 0);
+  if (e != cudaSuccess) return fail(c, NSN_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+  return NSN_OK;
+}
+
 template <typename T>
 nsn_status run_steps(nsn_ctx *c, int nsteps) {
   Dev<T> &D = dev<T>(c);
@@ -739,16 +871,8 @@ nsn_status run_steps(nsn_ctx *c, int nsteps) {
   CUDA_TRY(c, cudaEventRecord(c->ev0, st));
   if (c->cfg.use_graph) {
     if (!c->graph) {
-      cudaGraph_t g;
-      CUDA_TRY(c, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-      Launcher<T> Lr{c, D, st};
-      Lr.step();
-      cudaError_t e = cudaStreamEndCapture(st, &g);
-      if (e != cudaSuccess) return fail(c, NSN_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
-      e = cudaGraphInstantiate(&c->graph, g, 0);
-      cudaGraphDestroy(g);
-      if (e != cudaSuccess) return fail(c, NSN_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
-      c->launches_per_step = Lr.count;
+      nsn_status s = capture_step<T>(c, D);
+      if (s != NSN_OK) return s;
     }
     for (int s = 0; s < nsteps; s++) CUDA_TRY(c, cudaGraphLaunch(c->graph, st));
   } else {
@@ -768,12 +892,16 @@ nsn_status run_steps(nsn_ctx *c, int nsteps) {
   CUDA_TRY(c, cudaStreamSynchronize(st));
   float ms = 0.f;
   cudaEventElapsedTime(&ms, c->ev0, c->ev1);
-  const int N = c->cfg.newton_iters;
   c->last.newton_done = fl.newton_count;
   c->last.cr_total = fl.cr_count;
   c->last.merit0 = sc.merit0;
-  c->last.merit_final = sc.merit[N < 1023 ? N : 1023];
+  c->last.merit_final = sc.merit_final;
   c->last.ms = ms;
+  c->last_newton_n = fl.newton_n;
+  c->kept_buf = fl.newton_n & 1;   // entries of the final evaluation
+  if (c->cfg.use_graph)
+    c->launches_per_step = c->seg.prefix + fl.newton_n * (c->seg.head + c->seg.tail) + fl.cr_exec * c->seg.cr +
+                           c->seg.suffix;
   if (!std::isfinite(c->last.merit_final)) return fail(c, NSN_ERR_NONFINITE, "merit is not finite");
   return NSN_OK;
 }
@@ -831,6 +959,18 @@ nsn_status copy_out(nsn_ctx *c, const T *src, int n, double *host, int invert = 
   return NSN_OK;
 }
 
+// a per-row vector in the caller's (ABI) row order
+template <typename T>
+nsn_status copy_out_rows(nsn_ctx *c, const T *src, double *host, int invert = 0) {
+  const Layout &L = c->L;
+  if (!host || L.R <= 0) return NSN_OK;
+  std::vector<double> tmp(L.R);
+  nsn_status s = copy_out<T>(c, src, L.R, tmp.data(), invert);
+  if (s != NSN_OK) return s;
+  for (int i = 0; i < L.R; i++) host[L.row_abi[i]] = tmp[i];
+  return NSN_OK;
+}
+
 template <typename T>
 nsn_status do_apply(nsn_ctx *c, const double *x, double *y) {
   Dev<T> &D = dev<T>(c);
@@ -838,17 +978,20 @@ nsn_status do_apply(nsn_ctx *c, const double *x, double *y) {
   const int R = D.R;
   if (R == 0) return NSN_OK;
   double *tmp;
+  std::vector<double> xi(R), yi(R);
+  for (int i = 0; i < R; i++) xi[i] = x[c->L.row_abi[i]];
   CUDA_TRY(c, cudaMallocAsync(&tmp, sizeof(double) * R, st));
-  CUDA_TRY(c, cudaMemcpyAsync(tmp, x, sizeof(double) * R, cudaMemcpyHostToDevice, st));
+  CUDA_TRY(c, cudaMemcpyAsync(tmp, xi.data(), sizeof(double) * R, cudaMemcpyHostToDevice, st));
   k_from_double<T><<<cdiv(R, 256), 256, 0, st>>>(D.z, tmp, R);
   CUDA_TRY(c, cudaMemsetAsync(D.fl, 0, sizeof(Flags), st));
   Launcher<T> Lr{c, D, st};
   Lr.body(BM_APPLY, D.z, c->lin_buf, 0, 1);
   Lr.rows(RM_APPLY, 1);
   k_to_double<T><<<cdiv(R, 256), 256, 0, st>>>(tmp, D.Az, R, 0);
-  CUDA_TRY(c, cudaMemcpyAsync(y, tmp, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(c, cudaMemcpyAsync(yi.data(), tmp, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
   CUDA_TRY(c, cudaFreeAsync(tmp, st));
   CUDA_TRY(c, cudaStreamSynchronize(st));
+  for (int i = 0; i < R; i++) y[c->L.row_abi[i]] = yi[i];
   return NSN_OK;
 }
 
@@ -866,7 +1009,7 @@ nsn_status do_solve(nsn_ctx *c, int iters, double *dl, double *du) {
     Lr.cr(iters, c->lin_buf);
   }
   CUDA_TRY(c, cudaGetLastError());
-  if (dl) { nsn_status s = copy_out<T>(c, D.x, D.R, dl); if (s) return s; }
+  if (dl) { nsn_status s = copy_out_rows<T>(c, D.x, dl); if (s) return s; }
   if (du) {
     // du = H~^-1 (h J^T dl - g): reuse the apply body pass on x to get y = H~^-1 J^T x
     // per body into the per-entry scratch is not body-ordered, so do it on the host.
@@ -933,9 +1076,9 @@ template <typename T>
 nsn_status do_system(nsn_ctx *c, double *b, double *diag, double *hvec, double *g) {
   Dev<T> &D = dev<T>(c);
   nsn_status s;
-  if ((s = copy_out<T>(c, D.b, D.R, b))) return s;
-  if ((s = copy_out<T>(c, D.P, D.R, diag, 1))) return s;
-  if ((s = copy_out<T>(c, D.hv, D.R, hvec))) return s;
+  if ((s = copy_out_rows<T>(c, D.b, b))) return s;
+  if ((s = copy_out_rows<T>(c, D.P, diag, 1))) return s;
+  if ((s = copy_out_rows<T>(c, D.hv, hvec))) return s;
   if (g) {
     const Layout &L = c->L;
     std::vector<double> g6(size_t(6) * L.nr), g3(size_t(3) * L.np);
@@ -967,7 +1110,7 @@ nsn_status do_time_operator(nsn_ctx *c, int iters, float *ms_body, float *ms_row
   if (D.isl_on && D.ni) CUDA_TRY(c, cudaMemsetAsync(D.isl.crdone, 0, sizeof(int) * D.ni, st));
   Launcher<T> Lr{c, D, st};
   double tb = 0.0, tr = 0.0;
-  const int buf = c->cfg.newton_iters & 1;  // entries written by the final evaluation of the last step
+  const int buf = c->kept_buf < 0 ? 0 : c->kept_buf;  // entries written by the final evaluation of the last step
   for (int i = 0; i < iters; i++) {
     CUDA_TRY(c, cudaEventRecord(e[0], st));
     Lr.body(BM_APPLY, D.z, buf, 0, 1);
@@ -1306,7 +1449,7 @@ nsn_status nsn_step(nsn_ctx *c, int32_t nsteps, nsn_stats *stats) {
   if (s != NSN_OK) return s;
   c->linearized = false;
   s = c->cfg.precision == NSN_FP64 ? run_steps<double>(c, nsteps) : run_steps<float>(c, nsteps);
-  if (s == NSN_OK) c->kept_buf = c->cfg.newton_iters & 1;
+
   if (stats) *stats = c->last;
   return s;
 }
@@ -1400,8 +1543,8 @@ nsn_status nsn_get_lambda(nsn_ctx *c, double *lambda) {
   if (!c || !lambda) return NSN_ERR_INVALID_ARG;
   nsn_status s = ensure_built(c);
   if (s != NSN_OK) return s;
-  return c->cfg.precision == NSN_FP64 ? copy_out<double>(c, c->d64.lam, c->L.R, lambda)
-                                      : copy_out<float>(c, c->d32.lam, c->L.R, lambda);
+  return c->cfg.precision == NSN_FP64 ? copy_out_rows<double>(c, c->d64.lam, lambda)
+                                      : copy_out_rows<float>(c, c->d32.lam, lambda);
 }
 
 nsn_status nsn_get_merit_history(nsn_ctx *c, double *out, int32_t cap, int32_t *n) {
@@ -1415,7 +1558,7 @@ nsn_status nsn_get_merit_history(nsn_ctx *c, double *out, int32_t cap, int32_t *
   // merit at each solved Newton iteration, then at the returned iterate
   const int solved = std::min(c->last.newton_done, 1023);
   std::vector<double> hist(sc.merit, sc.merit + solved);
-  hist.push_back(sc.merit[std::min(c->cfg.newton_iters, 1023)]);
+  hist.push_back(sc.merit_final);
   if (n) *n = int32_t(hist.size());
   if (out)
     for (int i = 0; i < std::min<int>(cap, int(hist.size())); i++) out[i] = hist[i];
@@ -1610,12 +1753,16 @@ nsn_status nsn_last_launch_count(nsn_ctx *c, int32_t *kernels_per_step) {
 namespace {
 
 constexpr int kNoallocMaxEntries = NSN_NOALLOC_MAX_ENTRIES;
+constexpr int kNoallocMaxRows = NSN_NOALLOC_MAX_ENTRIES / 2;  // a row has at least 2 slots
 static __device__ __align__(256) float g_noalloc_t[kNoallocMaxEntries];
+// x and y in the context's internal (island) row order
+static __device__ __align__(256) float g_noalloc_x[kNoallocMaxRows];
+static __device__ __align__(256) float g_noalloc_y[kNoallocMaxRows];
 static __device__ __align__(256) DS g_noalloc_part[2 * kMaxBlocks * NPART];
 static __device__ __align__(256) Flags g_noalloc_flags;  // never written by the apply kernels
 
 struct NoallocPtrs {
-  float *t = nullptr;
+  float *t = nullptr, *x = nullptr, *y = nullptr;
   DS *part = nullptr;
   Flags *flags = nullptr;
   bool ready = false;
@@ -1631,20 +1778,29 @@ nsn_status noalloc_setup(nsn_ctx *c, NoallocPtrs **out) {
   if (dev < 0 || dev >= kMaxDevices) return fail(c, NSN_ERR_INVALID_ARG, "device index %d out of range", dev);
   NoallocPtrs &p = g_noalloc_dev[dev];
   if (!p.ready) {
-    void *t = nullptr, *part = nullptr, *fl = nullptr;
-    cudaError_t e1 = cudaGetSymbolAddress(&t, g_noalloc_t);
-    cudaError_t e2 = cudaGetSymbolAddress(&part, g_noalloc_part);
-    cudaError_t e3 = cudaGetSymbolAddress(&fl, g_noalloc_flags);
-    if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess)
-      return fail(c, NSN_ERR_CUDA, "cudaGetSymbolAddress: %s",
-                  cudaGetErrorString(e1 != cudaSuccess ? e1 : (e2 != cudaSuccess ? e2 : e3)));
+    void *t = nullptr, *part = nullptr, *fl = nullptr, *x = nullptr, *y = nullptr;
+    const cudaError_t e[5] = {cudaGetSymbolAddress(&t, g_noalloc_t), cudaGetSymbolAddress(&part, g_noalloc_part),
+                              cudaGetSymbolAddress(&fl, g_noalloc_flags), cudaGetSymbolAddress(&x, g_noalloc_x),
+                              cudaGetSymbolAddress(&y, g_noalloc_y)};
+    for (cudaError_t ei : e)
+      if (ei != cudaSuccess) return fail(c, NSN_ERR_CUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(ei));
     p.t = static_cast<float *>(t);
+    p.x = static_cast<float *>(x);
+    p.y = static_cast<float *>(y);
     p.part = static_cast<DS *>(part);
     p.flags = static_cast<Flags *>(fl);
     p.ready = true;
   }
   *out = &p;
   return NSN_OK;
+}
+
+// y[row_abi[i]] = x[i] (scatter) or y[i] = x[row_abi[i]] (gather)
+__global__ void k_permute_rows(float *dst, const float *src, const int *row_abi, int n, int scatter) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (scatter) dst[row_abi[i]] = src[i];
+  else dst[i] = src[row_abi[i]];
 }
 
 }  // namespace
@@ -1669,13 +1825,16 @@ extern "C" nsn_status nsn_apply_operator_noalloc(nsn_ctx *c, const float *x, flo
   D.t = np->t;
   D.part_row = np->part;
   D.fl = np->flags;
-  D.z = const_cast<float *>(x);
-  D.Az = y;
+  D.z = np->x;
+  D.Az = np->y;
+  D.isl_on = 0;  // every row takes part
   // world-side slots are read but never written: clear the shared scratch
   CUDA_TRY(c, cudaMemsetAsync(np->t, 0, sizeof(float) * nslots, st));
+  k_permute_rows<<<cdiv(L.R, 256), 256, 0, st>>>(np->x, x, D.row_abi_dev, L.R, 0);
   const int nb = D.nblk_body_r + D.nblk_body_p, nrw = D.nblk_row_pair + D.nblk_row_tet;
-  if (nb) k_body_pass<float, kGroup, BM_APPLY><<<nb, BLOCK, 0, st>>>(D, x, c->kept_buf, 0, 1);
+  if (nb) k_body_pass<float, kGroup, BM_APPLY><<<nb, BLOCK, 0, st>>>(D, np->x, c->kept_buf, 0, 1);
   k_row_pass<float, RM_APPLY><<<nrw, BLOCK, 0, st>>>(D, 1);
+  k_permute_rows<<<cdiv(L.R, 256), 256, 0, st>>>(y, np->y, D.row_abi_dev, L.R, 1);
   CUDA_TRY(c, cudaGetLastError());
   return NSN_OK;
 }

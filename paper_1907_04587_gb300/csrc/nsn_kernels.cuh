@@ -40,7 +40,20 @@ struct Flags {
   int cr_count;      // CR iterations performed (all Newton iterations)
   int isl_ticket;    // blocks of the island CR scalar kernel that have finished
   int isl_active;    // islands still iterating in this CR iteration
+  // loop state on the device: the Newton and CR iteration indices are read
+  // from here by the kernels, so that one captured loop body serves every
+  // iteration (CUDA graph conditional WHILE nodes)
+  int newton_n;      // current Newton iteration
+  int newton_live;   // 1 while the Newton loop continues
+  int cr_k;          // current CR iteration within this Newton iteration
+  int cr_live;       // 1 while the CR loop continues
+  int cr_exec;       // CR loop bodies executed in this step
 };
+
+// iteration index / entry buffer taken from Flags::newton_n
+constexpr int IT_DEV = -100;
+// k_merit: evaluation at the returned iterate
+constexpr int IT_FINAL = -3;
 
 // Per-island FP64 state (island mode): islands are the connected components
 // of the bodies through constraints.  Accumulators are indexed [slot * ni + i]:
@@ -51,6 +64,7 @@ struct IslState {
   double *acc;
   double *m0, *mf, *mw;      // zero-iterate, final and warm-start merits
   double *eta, *res0;        // CR forcing term and ||r_0||_P of the Newton iteration
+  double *res_prev;          // ||r||_P of the previous CR iteration
   double *rho;               // [2][ni], double-buffered by CR iteration parity
   double *alpha, *beta;
   float *alpha_f, *beta_f;
@@ -64,10 +78,12 @@ struct Scalars {
   double merit0;
   double eta;           // CR forcing term of this Newton iteration
   double res0;          // ||r_0||_P of this Newton iteration
+  double res_prev;      // ||r||_P of the previous CR iteration
   double rho[2];        // CR rho, double-buffered by iteration parity
   double appap[2];      // CR Ap^T P Ap, double-buffered by iteration parity
   double alpha, beta;   // CR step of the current iteration
   float alpha_f, beta_f; // the same, rounded once for the FP32 update kernel
+  double merit_final;   // merit at the returned iterate
   double merit_warm;    // merit at the warm-started iterate (u = 0, lambda^0)
   int warm_rejected;    // 1 if the warm start was worse than the zero start (island
                         // mode: the number of islands where it was)
@@ -136,7 +152,12 @@ struct Dev {
   int cone;          // 1: project contact multipliers onto the friction cone after each update
   int *risl;         // island of each row
   int *bisl_r, *bisl_p;  // island of each rigid body / particle
+  int *cabi;         // ABI index of each (island-ordered) contact: per-contact
+                     // features and predictions are exchanged in ABI order
+  int *row_abi_dev;  // ABI index of each (island-ordered) row
   IslState isl;
+  // conditional handles of the captured Newton / CR WHILE nodes (0: none)
+  cudaGraphConditionalHandle hN, hC;
 };
 
 // ------------------------------------------------------------------------------------
@@ -408,6 +429,7 @@ __global__ void k_begin_rigid(Dev<T> D) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i == 0) {
     D.fl->newton_stop = 0; D.fl->cr_stop = 0; D.fl->newton_count = 0; D.fl->cr_count = 0;
+    D.fl->newton_n = 0; D.fl->newton_live = 1; D.fl->cr_k = 0; D.fl->cr_live = 0; D.fl->cr_exec = 0;
   }
   if (i >= D.nr) return;
   T q[4], R[9], Ib[3], w[3], Iw[9], Iwi[9];
@@ -610,6 +632,7 @@ __device__ __forceinline__ T w_min(T vt, T lf, T mu_ln, T r) {
 template <typename T>
 __global__ void k_eval_contacts(Dev<T> D, int buf, int force) {
   if (!force && D.fl->newton_stop) return;
+  if (buf == IT_DEV) buf = D.fl->newton_n & 1;
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= D.nc) return;
   if (!force && D.isl_on && D.isl.stop[D.risl[3 * c]] >= 0) return;   // stopped island
@@ -697,6 +720,7 @@ __global__ void k_eval_contacts(Dev<T> D, int buf, int force) {
 template <typename T>
 __global__ void k_eval_joints(Dev<T> D, int buf, int force) {
   if (!force && D.fl->newton_stop) return;
+  if (buf == IT_DEV) buf = D.fl->newton_n & 1;
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= D.nj) return;
   if (!force && D.isl_on && D.isl.stop[D.risl[3 * D.nc + 5 * j]] >= 0) return;   // stopped island
@@ -769,6 +793,7 @@ __global__ void k_eval_joints(Dev<T> D, int buf, int force) {
 template <typename T>
 __global__ void k_eval_tets(Dev<T> D, int buf, int force) {
   if (!force && D.fl->newton_stop) return;
+  if (buf == IT_DEV) buf = D.fl->newton_n & 1;
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= D.nt) return;
   if (!force && D.isl_on && D.isl.stop[D.risl[D.Rpair + 3 * t]] >= 0) return;   // stopped island
@@ -857,6 +882,8 @@ __device__ __forceinline__ bool isl_skip(const Dev<T> &D, int is, int force) {
 template <typename T, int G, int MODE>
 __global__ void __launch_bounds__(BLOCK) k_body_pass(Dev<T> D, const T *__restrict__ in, int buf, int newton_it, int force) {
   if (!force && D.fl->newton_stop) return;
+  if (newton_it == IT_DEV) newton_it = D.fl->newton_n;
+  if (buf == IT_DEV) buf = D.fl->newton_n & 1;
   if (MODE == BM_APPLY && D.fl->cr_stop) return;
   constexpr int KR = 3;
   Acc<T> acc_g2;
@@ -1249,6 +1276,7 @@ __global__ void __launch_bounds__(BLOCK) k_row_pass_isl(Dev<T> D, int force) {
       int key = i < D.Rpair ? D.risl[i] : -1;
       if (key >= 0 && (MODE == RM_APPLY ? D.isl.crdone[key] != 0 : (!force && D.isl.stop[key] >= 0))) key = -1;
       const bool v = key >= 0;
+      if (!__any_sync(0xffffffffu, v)) continue;   // the whole warp's islands are finished
       if (MODE == RM_RHS) {
         T a[2] = {T(0), T(0)};
         if (v) {
@@ -1286,6 +1314,7 @@ __global__ void __launch_bounds__(BLOCK) k_row_pass_isl(Dev<T> D, int force) {
       int key = t < D.nt ? D.risl[rb + 3 * t] : -1;
       if (key >= 0 && (MODE == RM_APPLY ? D.isl.crdone[key] != 0 : (!force && D.isl.stop[key] >= 0))) key = -1;
       const bool v = key >= 0;
+      if (!__any_sync(0xffffffffu, v)) continue;
       if (MODE == RM_RHS) {
         T a[2] = {T(0), T(0)};
         if (v) {
@@ -1344,7 +1373,8 @@ __global__ void __launch_bounds__(BLOCK) k_row_pass_isl(Dev<T> D, int force) {
 template <typename T>
 __global__ void __launch_bounds__(RED_THREADS) k_merit(Dev<T> D, int n, int force) {
   if (!force && D.fl->newton_stop) return;
-  const bool final_eval = force && n >= 0;
+  if (n == IT_DEV) n = D.fl->newton_n;
+  const bool final_eval = n == IT_FINAL;
   double m = 0.0, res0 = 0.0;
   if (!D.isl_on) {
     using R = typename RedT<T>::type;
@@ -1371,6 +1401,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_merit(Dev<T> D, int n, int forc
       if (n == -1) { D.isl.m0[i] = mi; m2 += a; continue; }
       if (n == -2) { D.isl.mw[i] = mi; m2 += a; continue; }
       if (final_eval) { D.isl.mf[i] = mi; m2 += a; continue; }
+      if (force) { m2 += a; continue; }     // evaluation without a stop test
       int st = D.isl.stop[i];
       if (st >= 0) {                       // stopped: not evaluated, keeps its last merit
         m2 += D.isl.mf[i] * D.isl.mf[i];
@@ -1402,7 +1433,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_merit(Dev<T> D, int n, int forc
       double t2 = 0.0;
       for (int w = 0; w < RED_THREADS / 32; w++) t2 += sm[w];
       m = sqrt(t2);
-      if (n >= 0 && !final_eval && !any) D.fl->newton_stop = 1;
+      if (n >= 0 && !force && !any) D.fl->newton_stop = 1;
     }
   }
   if (threadIdx.x == 0) {
@@ -1411,6 +1442,8 @@ __global__ void __launch_bounds__(RED_THREADS) k_merit(Dev<T> D, int n, int forc
       D.sc->warm_rejected = 0;
     } else if (n == -2) {                              // warm-started iterate
       D.sc->merit_warm = m;
+    } else if (final_eval) {                           // returned iterate
+      D.sc->merit_final = m;
     } else {
       D.sc->merit[n < 1023 ? n : 1023] = m;
       if (!force) {
@@ -1431,10 +1464,11 @@ __global__ void __launch_bounds__(RED_THREADS) k_merit(Dev<T> D, int n, int forc
   }
 }
 
-// CR stops once ||r||_P has fallen to this fraction of ||r_0||_P: past it the
-// recurrences run on rounding noise of the bulk type (rho = z^T A z stops
-// decreasing and beta = rho_k / rho_{k-1} can exceed 1 at every iteration, so
-// p grows geometrically).  FP32: a little above the rounding of the operator
+// CR stops once ||r||_P has fallen to this fraction of ||r_0||_P, or when
+// ||r||_P grows (preconditioned CR minimises it over the Krylov space, so in
+// exact arithmetic it never increases): past either point the recurrences run
+// on rounding noise of the bulk type (rho = z^T A z stops decreasing and beta =
+// rho_k / rho_{k-1} can exceed 1 at every iteration, so p grows geometrically).  FP32: a little above the rounding of the operator
 // apply; FP64: the oracle's value, well above FP64 rounding so that the
 // iteration at which it is crossed does not depend on summation order.
 template <typename T>
@@ -1451,16 +1485,18 @@ __device__ __forceinline__ double cr_floor<float>() { return 1e-6; }
 // and the update kernel applies p = z + beta p, Ap = Az + beta Ap,
 // x += alpha p, z -= alpha P Ap.
 template <typename T>
-__global__ void __launch_bounds__(RED_THREADS) k_cr_scalars(Dev<T> D, int k) {
+__global__ void __launch_bounds__(RED_THREADS) k_cr_scalars(Dev<T> D) {
   if (D.fl->newton_stop || D.fl->cr_stop) return;
+  const int k = D.fl->cr_k;
   double r4[NPART];
   reduce_partials<typename RedT<T>::type, RED_THREADS>(D.part_row, D.nblk_row_pair + D.nblk_row_tet, r4);
   if (threadIdx.x == 0) {
     const double d1 = r4[0], d2 = r4[1], d3 = r4[2], d4 = r4[3], d5 = r4[4];
     int st = 0;
     const double cur = sqrt(d4 > 0.0 ? d4 : 0.0);
-    if (D.sc->res0 == 0.0 || cur <= cr_floor<T>() * D.sc->res0) st = 1;
+    if (D.sc->res0 == 0.0 || cur <= cr_floor<T>() * D.sc->res0 || (k > 0 && cur > D.sc->res_prev)) st = 1;
     if (D.cr_tol && cur <= D.sc->eta * D.sc->res0) st = 1;
+    D.sc->res_prev = cur;
     double beta = 0.0, rho = d1, apap = d2;
     if (k > 0) {
       const double rp = D.sc->rho[(k - 1) & 1];
@@ -1493,8 +1529,9 @@ template <>
 __device__ __forceinline__ double cr_scalar<double>(double d, float) { return d; }
 
 template <typename T>
-__global__ void __launch_bounds__(BLOCK) k_cr_update(Dev<T> D, int k) {
+__global__ void __launch_bounds__(BLOCK) k_cr_update(Dev<T> D) {
   if (D.fl->newton_stop || D.fl->cr_stop) return;
+  const int k = D.fl->cr_k;
   const T alpha = cr_scalar<T>(D.sc->alpha, D.sc->alpha_f), beta = cr_scalar<T>(D.sc->beta, D.sc->beta_f);
   const int stride = gridDim.x * BLOCK;
   for (int i = blockIdx.x * BLOCK + threadIdx.x; i < D.R; i += stride) {
@@ -1513,8 +1550,9 @@ __global__ void __launch_bounds__(BLOCK) k_cr_update(Dev<T> D, int k) {
 // itself).  One thread per island; the last block to finish sets cr_stop when
 // no island continues.
 template <typename T>
-__global__ void k_cr_scalars_isl(Dev<T> D, int k) {
+__global__ void k_cr_scalars_isl(Dev<T> D) {
   if (D.fl->newton_stop || D.fl->cr_stop) return;
+  const int k = D.fl->cr_k;
   const int ni = D.ni;
   double *acc = D.isl.acc + 2 * size_t(ni);
   int act = 0;
@@ -1525,7 +1563,8 @@ __global__ void k_cr_scalars_isl(Dev<T> D, int k) {
     int st = 0;
     const double cur = sqrt(d4 > 0.0 ? d4 : 0.0);
     const double r0 = D.isl.res0[i];
-    if (r0 == 0.0 || cur <= cr_floor<T>() * r0) st = 1;
+    if (r0 == 0.0 || cur <= cr_floor<T>() * r0 || (k > 0 && cur > D.isl.res_prev[i])) st = 1;
+    D.isl.res_prev[i] = cur;
     if (D.cr_tol && cur <= D.isl.eta[i] * r0) st = 1;
     double beta = 0.0, rho = d1, apap = d2;
     if (k > 0) {
@@ -1568,8 +1607,9 @@ template <>
 __device__ __forceinline__ double isl_scalar<double>(const double *d, const float *, int i) { return d[i]; }
 
 template <typename T>
-__global__ void __launch_bounds__(BLOCK) k_cr_update_isl(Dev<T> D, int k) {
+__global__ void __launch_bounds__(BLOCK) k_cr_update_isl(Dev<T> D) {
   if (D.fl->newton_stop || D.fl->cr_stop) return;
+  const int k = D.fl->cr_k;
   const int stride = gridDim.x * BLOCK;
   for (int i = blockIdx.x * BLOCK + threadIdx.x; i < D.R; i += stride) {
     const int is = D.risl[i];
@@ -1583,6 +1623,40 @@ __global__ void __launch_bounds__(BLOCK) k_cr_update_isl(Dev<T> D, int k) {
     D.x[i] += alpha * pi;
     D.z[i] = zi - alpha * D.P[i] * api;
   }
+}
+
+// Loop control (one thread).  Each loop continues only while its counter is
+// below the cap, so it ends whatever the flags say; under a CUDA graph the
+// kernels also set the condition of the enclosing WHILE node.
+template <typename T>
+__global__ void k_cr_begin(Dev<T> D, int M) {
+  Flags *f = D.fl;
+  f->cr_k = 0;
+  f->cr_live = (!f->newton_stop && !f->cr_stop && M > 0) ? 1 : 0;
+  if (D.hC) cudaGraphSetConditional(D.hC, unsigned(f->cr_live));
+}
+
+template <typename T>
+__global__ void k_cr_next(Dev<T> D, int M) {
+  Flags *f = D.fl;
+  if (f->cr_live) {
+    const int k = f->cr_k + 1;
+    f->cr_k = k;
+    f->cr_exec += 1;
+    if (f->newton_stop || f->cr_stop || k >= M) f->cr_live = 0;
+  }
+  if (D.hC) cudaGraphSetConditional(D.hC, unsigned(f->cr_live));
+}
+
+template <typename T>
+__global__ void k_newton_next(Dev<T> D, int N) {
+  Flags *f = D.fl;
+  if (f->newton_live) {
+    const int n = f->newton_n + 1;
+    f->newton_n = n;
+    if (f->newton_stop || n >= N) f->newton_live = 0;
+  }
+  if (D.hN) cudaGraphSetConditional(D.hN, unsigned(f->newton_live));
 }
 
 // CR restart on a kept system: x = 0, z = P b, p = z
@@ -1702,7 +1776,7 @@ __global__ void k_contact_features(Dev<T> D, float *X) {
   }
   const T vn = dot3(vr, n);
   const T vt = dsqrt(fmax(dot3(vr, vr) - vn * vn, T(0)));
-  float *x = X + 16 * size_t(c);
+  float *x = X + 16 * size_t(D.cabi[c]);
   x[0] = float(n[0]); x[1] = float(n[1]); x[2] = float(n[2]);
   for (int k = 0; k < 3; k++) x[3 + k] = float(vr[k] / (gabs * h));
   x[6] = float(Cn / (gabs * h * h));
@@ -1732,8 +1806,9 @@ __global__ void k_contact_targets(Dev<T> D, float *Y) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= D.nc) return;
   const T ls = contact_lscale(D, c);
-  for (int k = 0; k < 3; k++) Y[4 * size_t(c) + k] = float(D.lam[3 * c + k] / ls);
-  Y[4 * size_t(c) + 3] = 0.f;
+  const size_t o = 4 * size_t(D.cabi[c]);
+  for (int k = 0; k < 3; k++) Y[o + k] = float(D.lam[3 * c + k] / ls);
+  Y[o + 3] = 0.f;
 }
 
 // lambda^0 from the network outputs: lambda_n >= 0; friction rows start at
@@ -1743,11 +1818,12 @@ __global__ void k_warm_from_pred(Dev<T> D, const float *Y, int warm_friction) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= D.nc) return;
   const T ls = contact_lscale(D, c);
-  T ln = T(Y[4 * size_t(c)]) * ls;
+  const size_t o = 4 * size_t(D.cabi[c]);
+  T ln = T(Y[o]) * ls;
   if (!(ln > T(0))) ln = T(0);
   T f1 = T(0), f2 = T(0);
   if (warm_friction) {
-    f1 = T(Y[4 * size_t(c) + 1]) * ls; f2 = T(Y[4 * size_t(c) + 2]) * ls;
+    f1 = T(Y[o + 1]) * ls; f2 = T(Y[o + 2]) * ls;
     const T lim = D.cmu[c] * ln, fn = dsqrt(f1 * f1 + f2 * f2);
     if (fn > lim) { const T s = fn > T(0) ? lim / fn : T(0); f1 *= s; f2 *= s; }
   }
