@@ -237,10 +237,12 @@ def make_solver(nsn, s, stream, newton, cr, cone, warm=0, params=None):
     return g
 
 
-def measure_arm(nsn, torch, g, s, st0, stream, steps, warmup, clk=None):
+def measure_arm(nsn, torch, g, s, st0, stream, steps, warmup, clk=None, reset=False):
     """Device-timed advancing trajectory: reset to the start state, warmup
     steps, then `steps` timed steps; per-step island stop iterations are copied
-    on the device and counted afterwards."""
+    on the device and counted afterwards.  reset=True: every step starts from
+    the start state with no previous-step multipliers (an environment reset,
+    as RL training does at episode starts)."""
     dev = st0["pos"].device
     ni, bi = g.islands()
     isl_env = island_env_map(s, bi, ni)
@@ -248,7 +250,13 @@ def measure_arm(nsn, torch, g, s, st0, stream, steps, warmup, clk=None):
     stops = torch.empty((steps, max(ni, 1)), dtype=torch.int32, device=dev)
     ptr = {k: v.data_ptr() for k, v in st0.items()}
     nsn.nsn_set_state_device(g.ctx, ptr["pos"], ptr["quat"], ptr["vel"], ptr["omega"])
+    def restart():
+        nsn.nsn_set_state_device(g.ctx, ptr["pos"], ptr["quat"], ptr["vel"], ptr["omega"])
+        g.clear_warm_start()
+
     for _ in range(warmup):
+        if reset:
+            restart()
         g.step(1)
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
@@ -258,6 +266,8 @@ def measure_arm(nsn, torch, g, s, st0, stream, steps, warmup, clk=None):
     e0.record(stream)
     newton, launches = [], 0
     for k in range(steps):
+        if reset:
+            restart()
         st = g.step(1)
         nsn.lib().nsn_island_stop_copy(g.ctx, nsn.C.c_void_p(stops[k].data_ptr()))
         newton.append(st["newton_done"])
@@ -338,13 +348,16 @@ def run_ours(args, rank, world, local_rank):
         # the other arms, same trajectory and accounting
         arms = {}
         if args.arms:
-            for name, cone, warm in (("as_printed", 0, nsn.NSN_WARM_ZERO), ("prev_warm_start", 1, nsn.NSN_WARM_PREV),
-                                     ("learned_warm_start", 1, nsn.NSN_WARM_LEARNED)):
+            for name, cone, warm, reset in (("as_printed", 0, nsn.NSN_WARM_ZERO, False),
+                                            ("prev_warm_start", 1, nsn.NSN_WARM_PREV, False),
+                                            ("learned_warm_start", 1, nsn.NSN_WARM_LEARNED, False),
+                                            ("after_reset_zero", 1, nsn.NSN_WARM_ZERO, True),
+                                            ("after_reset_learned", 1, nsn.NSN_WARM_LEARNED, True)):
                 if warm == nsn.NSN_WARM_LEARNED and params is None:
                     arms[name] = {"unavailable": "no trained weights (paper_1907_04587_gb300/weights)"}
                     continue
                 ga = make_solver(nsn, s, stream, newton, cr, cone=cone, warm=warm, params=params)
-                r = measure_arm(nsn, torch, ga, s, st0, stream, args.steps, args.warmup)
+                r = measure_arm(nsn, torch, ga, s, st0, stream, args.steps, args.warmup, reset=reset)
                 if warm != nsn.NSN_WARM_ZERO:
                     r["warm_rejected_islands_last_step"] = ga.warm_stats()["rejected"]
                 ga.close()

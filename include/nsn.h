@@ -224,11 +224,13 @@ nsn_status nsn_operator_sizes(nsn_ctx *ctx, int64_t *sizes8);
  * ReLU, BF16 tensor-core GEMMs with FP32 accumulation; contact rows only,
  * joint and tet rows start at zero): outputs are the
  * normal and two friction multipliers over the contact's gravity-scaled
- * effective mass |g| / (1/m_a + 1/m_b) and a log preconditioner scale.  In
- * both modes the warm start is kept only if the merit at (u = 0, lambda^0) is
- * not above the merit at the zero start; otherwise the step starts from zero.
- * u^0 = 0 in all modes.  The relative merit is always taken against the zero
- * start. */
+ * effective mass |g| / (1/m_a + 1/m_b) and a log preconditioner scale.
+ * NSN_WARM_PREV keeps the previous step's multipliers only if the merit at
+ * (u = 0, lambda^0) is not above the merit at the zero start.  NSN_WARM_LEARNED
+ * falls back on the previous-step start: of the three candidates (network,
+ * previous step, zero) the one of least merit at u = 0 is kept.  With
+ * island_stop = 1 both choices are made island by island.  u^0 = 0 in all
+ * modes.  The relative merit is always taken against the zero start. */
 enum { NSN_WARM_ZERO = 0, NSN_WARM_PREV = 1, NSN_WARM_LEARNED = 2 };
 /* OR-ed into the mode: warm-start the friction rows too.  By default only the
  * normal and joint rows are warm started and friction starts at zero: the
@@ -237,6 +239,10 @@ enum { NSN_WARM_ZERO = 0, NSN_WARM_PREV = 1, NSN_WARM_LEARNED = 2 };
 #define NSN_WARM_FRICTION 0x100
 #define NSN_MLP_NPARAM (128 * 16 + 128 + 128 * 128 + 128 + 128 * 128 + 128 + 4 * 128 + 4)
 nsn_status nsn_set_warm_start(nsn_ctx *ctx, int32_t mode);
+/* Forgets the previous step's multipliers (sets them to zero), e.g. after
+ * the state was reset: the next step's previous-step candidate is then the
+ * zero start.  Enqueued on the context stream; allocates nothing. */
+nsn_status nsn_clear_warm_start(nsn_ctx *ctx);
 /* Islands of the current scene: *n_islands, and the island of each body
  * (host array of the body count, may be NULL).  Islands are numbered in the
  * order of their lowest body id; they do not depend on island_stop. */
@@ -257,9 +263,9 @@ nsn_status nsn_island_stop_device(nsn_ctx *ctx, const int32_t **stopped_at);
  * int32 into dst_device (a device buffer of the caller).  Allocates nothing. */
 nsn_status nsn_island_stop_copy(nsn_ctx *ctx, int32_t *dst_device);
 
-/* Merits of the last warm-started step: zero start, warm start, and whether
- * the warm start was rejected (island_stop = 1: the number of islands where
- * it was rejected and the zero start kept). */
+/* Merits of the last warm-started step: zero start, warm start (the
+ * network's candidate for NSN_WARM_LEARNED), and whether that candidate was
+ * not chosen (island_stop = 1: the number of islands where it was not). */
 nsn_status nsn_get_warm_stats(nsn_ctx *ctx, double *merit_zero, double *merit_warm, int32_t *rejected);
 /* Network parameters (host, NSN_MLP_NPARAM floats): W1[128][16], b1[128],
  * W2[128][128], b2, W3[128][128], b3, W4[4][128], b4[4]; y = W x + b.  Setting

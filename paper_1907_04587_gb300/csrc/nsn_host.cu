@@ -328,6 +328,7 @@ void carve(Arena &A, Dev<T> &D, const Layout &L, int nb) {
   const int ni = std::max(L.ni, 1);
   D.isl.acc = A.take<double>(size_t(ISL_ACC) * ni);
   D.isl.m0 = A.take<double>(ni); D.isl.mf = A.take<double>(ni); D.isl.mw = A.take<double>(ni);
+  D.isl.mw2 = A.take<double>(ni);
   D.isl.eta = A.take<double>(ni); D.isl.res0 = A.take<double>(ni); D.isl.rho = A.take<double>(2 * size_t(ni));
   D.isl.res_prev = A.take<double>(ni);
   D.isl.alpha = A.take<double>(ni); D.isl.beta = A.take<double>(ni);
@@ -644,17 +645,26 @@ struct Launcher {
     rows(RM_RHS, 1);
     k_merit<T><<<1, RED_THREADS, 0, st>>>(D, -1, 1);
     count++;
-    if (c->warm_mode == NSN_WARM_PREV) {
-      if (D.R) { k_warm_from_prev<T><<<D.nblk_upd, BLOCK, 0, st>>>(D, c->warm_friction); count++; }
-    } else if (D.nc) {
-      k_warm_from_pred<T><<<cdiv(D.nc, 128), 128, 0, st>>>(D, c->mlp.Y, c->warm_friction);
-      count++;
-    }
+    // previous-step candidate (also the fallback of the learned start)
+    if (D.R) { k_warm_from_prev<T><<<D.nblk_upd, BLOCK, 0, st>>>(D, c->warm_friction); count++; }
     eval(0, 1);
     body(BM_RESIDUAL, D.lam, 0, 0, 1);
     rows(RM_RHS, 1);
     k_merit<T><<<1, RED_THREADS, 0, st>>>(D, -2, 1);
-    k_warm_accept<T><<<D.nblk_upd, BLOCK, 0, st>>>(D);
+    count++;
+    if (c->warm_mode == NSN_WARM_PREV) {
+      k_warm_accept<T><<<D.nblk_upd, BLOCK, 0, st>>>(D);
+      count++;
+      return;
+    }
+    // learned candidate: contacts from the network, joint and tet rows zero
+    if (D.R) cudaMemsetAsync(D.lam, 0, sizeof(T) * D.R, st);
+    if (D.nc) { k_warm_from_pred<T><<<cdiv(D.nc, 128), 128, 0, st>>>(D, c->mlp.Y, c->warm_friction); count++; }
+    eval(0, 1);
+    body(BM_RESIDUAL, D.lam, 0, 0, 1);
+    rows(RM_RHS, 1);
+    k_merit<T><<<1, RED_THREADS, 0, st>>>(D, -4, 1);
+    k_warm_choose<T><<<D.nblk_upd, BLOCK, 0, st>>>(D, c->warm_friction);
     count += 2;
   }
   // segments of one step (Algorithm 1): prefix, Newton loop body (head, CR
@@ -1664,6 +1674,16 @@ nsn_status nsn_island_stop_device(nsn_ctx *c, const int32_t **stopped_at) {
   return NSN_OK;
 }
 
+nsn_status nsn_clear_warm_start(nsn_ctx *c) {
+  if (!c) return NSN_ERR_INVALID_ARG;
+  nsn_status s = ensure_built(c);
+  if (s != NSN_OK) return s;
+  if (!c->L.R) return NSN_OK;
+  if (c->cfg.precision == NSN_FP64) CUDA_TRY(c, cudaMemsetAsync(c->d64.lam_prev, 0, sizeof(double) * c->L.R, c->stream));
+  else CUDA_TRY(c, cudaMemsetAsync(c->d32.lam_prev, 0, sizeof(float) * c->L.R, c->stream));
+  return NSN_OK;
+}
+
 nsn_status nsn_get_warm_stats(nsn_ctx *c, double *merit_zero, double *merit_warm, int32_t *rejected) {
   if (!c) return NSN_ERR_INVALID_ARG;
   nsn_status s = ensure_built(c);
@@ -1673,7 +1693,7 @@ nsn_status nsn_get_warm_stats(nsn_ctx *c, double *merit_zero, double *merit_warm
   CUDA_TRY(c, cudaMemcpyAsync(&sc, src, sizeof(Scalars), cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   if (merit_zero) *merit_zero = sc.merit0;
-  if (merit_warm) *merit_warm = sc.merit_warm;
+  if (merit_warm) *merit_warm = c->warm_mode == NSN_WARM_LEARNED ? sc.merit_warm2 : sc.merit_warm;
   if (rejected) *rejected = sc.warm_rejected;
   return NSN_OK;
 }

@@ -63,6 +63,7 @@ constexpr int ISL_ACC = 7;
 struct IslState {
   double *acc;
   double *m0, *mf, *mw;      // zero-iterate, final and warm-start merits
+  double *mw2;               // merit of the second warm-start candidate (learned)
   double *eta, *res0;        // CR forcing term and ||r_0||_P of the Newton iteration
   double *res_prev;          // ||r||_P of the previous CR iteration
   double *rho;               // [2][ni], double-buffered by CR iteration parity
@@ -85,6 +86,7 @@ struct Scalars {
   float alpha_f, beta_f; // the same, rounded once for the FP32 update kernel
   double merit_final;   // merit at the returned iterate
   double merit_warm;    // merit at the warm-started iterate (u = 0, lambda^0)
+  double merit_warm2;   // merit at the second candidate (learned, after previous-step)
   int warm_rejected;    // 1 if the warm start was worse than the zero start (island
                         // mode: the number of islands where it was)
 };
@@ -1400,6 +1402,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_merit(Dev<T> D, int n, int forc
       const double mi = sqrt(a);
       if (n == -1) { D.isl.m0[i] = mi; m2 += a; continue; }
       if (n == -2) { D.isl.mw[i] = mi; m2 += a; continue; }
+      if (n == -4) { D.isl.mw2[i] = mi; m2 += a; continue; }
       if (final_eval) { D.isl.mf[i] = mi; m2 += a; continue; }
       if (force) { m2 += a; continue; }     // evaluation without a stop test
       int st = D.isl.stop[i];
@@ -1442,6 +1445,8 @@ __global__ void __launch_bounds__(RED_THREADS) k_merit(Dev<T> D, int n, int forc
       D.sc->warm_rejected = 0;
     } else if (n == -2) {                              // warm-started iterate
       D.sc->merit_warm = m;
+    } else if (n == -4) {                              // second warm-start candidate
+      D.sc->merit_warm2 = m;
     } else if (final_eval) {                           // returned iterate
       D.sc->merit_final = m;
     } else {
@@ -1860,6 +1865,44 @@ __global__ void k_warm_accept(Dev<T> D) {
   if (i0 == 0) D.sc->warm_rejected = reject ? 1 : 0;
   if (!reject) return;
   for (int i = i0; i < D.R; i += stride) D.lam[i] = T(0);
+}
+
+// Learned warm start with the previous-step start as fallback: D.lam holds
+// the network's lambda^0, lam_prev the previous step's multipliers.  Per
+// island (or for the whole system) the candidate of least merit at u = 0 is
+// kept: the network's, the previous step's (friction rows as in
+// k_warm_from_prev), or the zero start.  sc->warm_rejected counts the islands
+// (1 for the whole system) where the network's candidate was not chosen.
+template <typename T>
+__global__ void k_warm_choose(Dev<T> D, int warm_friction) {
+  const int i0 = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+  auto pick = [](double m0, double mp, double ml) {   // 0 zero, 1 previous, 2 learned
+    int c = 0;
+    double best = m0;
+    if (mp < best) { best = mp; c = 1; }
+    if (ml < best) c = 2;
+    return c;
+  };
+  if (D.isl_on)
+    for (int i = i0; i < D.ni; i += stride) {
+      if (pick(D.isl.m0[i], D.isl.mw[i], D.isl.mw2[i]) != 2) atomicAdd(&D.sc->warm_rejected, 1);
+    }
+  else if (i0 == 0)
+    D.sc->warm_rejected = pick(D.sc->merit0, D.sc->merit_warm, D.sc->merit_warm2) != 2 ? 1 : 0;
+  for (int i = i0; i < D.R; i += stride) {
+    int c;
+    if (D.isl_on) {
+      const int is = D.risl[i];
+      c = pick(D.isl.m0[is], D.isl.mw[is], D.isl.mw2[is]);
+    } else {
+      c = pick(D.sc->merit0, D.sc->merit_warm, D.sc->merit_warm2);
+    }
+    if (c == 0) D.lam[i] = T(0);
+    else if (c == 1) {
+      const bool fric = i < 3 * D.nc && (i % 3) != 0;
+      D.lam[i] = (fric && !warm_friction) ? T(0) : D.lam_prev[i];
+    }
+  }
 }
 
 template <typename T>

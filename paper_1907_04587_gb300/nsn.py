@@ -109,6 +109,7 @@ def lib():
         "nsn_island_stats": (C.c_int, [_vp, C.c_int32, _dp, _dp, _ip]),
         "nsn_island_stop_device": (C.c_int, [_vp, C.POINTER(_vp)]),
         "nsn_island_stop_copy": (C.c_int, [_vp, _vp]),
+        "nsn_clear_warm_start": (C.c_int, [_vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -478,6 +479,9 @@ class Solver:
 
     def warm_stats(self):
         return nsn_get_warm_stats(self.ctx)
+
+    def clear_warm_start(self):
+        _check(self.ctx, lib().nsn_clear_warm_start(self.ctx), "nsn_clear_warm_start")
 
     def islands(self):
         """(number of islands, island of each body)."""

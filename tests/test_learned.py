@@ -82,8 +82,8 @@ def test_warm_start_modes_and_fallback(torch_cuda):
     ws = g.warm_stats()
     assert ws["merit_warm"] <= ws["merit_zero"] or ws["rejected"]
     assert abs(r["merit0"] - r0["merit0"]) <= 1e-6 * r0["merit0"]
-    # a network with huge outputs: the warm start must be rejected and the step
-    # must then equal the zero-start step
+    # a network with huge outputs: its candidate must lose to the previous-step
+    # fallback, and the step must then equal the previous-step warm start
     bad = learn.init_params(0)
     bad[-4:] = 1e4
     b = nsn.Solver(s, newton_iters=4, cr_iters=20)
@@ -91,18 +91,18 @@ def test_warm_start_modes_and_fallback(torch_cuda):
     b.step(); b.set_state(**st); b.set_warm_start(nsn.NSN_WARM_LEARNED)
     b.step()
     assert b.warm_stats()["rejected"]
-    np.testing.assert_allclose(b.merit_history(), h0, rtol=1e-5)
+    np.testing.assert_allclose(b.merit_history(), g.merit_history(), rtol=1e-5)
 
 
 def test_learned_warm_start_after_training(torch_cuda):
-    """Train on solver-generated pairs of two scenes, evaluate on a held-out
-    seed: the learned start is accepted and lowers the initial merit."""
-    X, T = learn.generate(seeds=[100, 101], n_envs=96)
-    tr = learn.Trainer(seed=1)
-    hist = tr.train(X, T, epochs=8, batch=2048, lr=2e-3)
-    assert hist[-1] < hist[0]
-    res = learn.compare_warm_starts(tr.params(), seed=5000, n_envs=96)
+    """Train on the solver's converged pairs (two seeds), evaluate on a held-out
+    seed over an advancing trajectory: the learned start (with the previous-step
+    fallback) converges at least as many islands as the zero start, in fewer
+    Newton iterations."""
+    params, hist, n = learn.train_warm_start(seeds=(100, 101), n_envs=64, steps=2, epochs=10, batch=1024)
+    assert n > 1000 and np.mean(hist[-5:]) < np.mean(hist[:5])
+    res = learn.compare_warm_starts(params, seed=5000, n_envs=64, steps=3)
     for k, v in res.items():
-        print(k, "initial merit/zero", v["warm"]["merit_warm"] / max(v["warm"]["merit_zero"], 1e-30) if k != "zero" else 1.0,
-              "final rel", v["final_rel"], "history", np.round(v["rel"], 3))
-    assert res["learned"]["warm"]["merit_warm"] <= res["learned"]["warm"]["merit_zero"] or res["learned"]["warm"]["rejected"]
+        print(k, "islands converged", round(v["island_fraction"], 4), "mean Newton to 1e-6", v["mean_newton"])
+    assert res["learned"]["island_fraction"] >= res["zero"]["island_fraction"] - 0.02
+    assert res["learned"]["mean_newton"] < res["zero"]["mean_newton"]
