@@ -11,17 +11,22 @@ by side, each stops when its merit reaches 1e-6 of its own zero-iterate merit
 (cap: 30 Newton iterations of 50 CR iterations each), and an environment-step
 counts only if every island of the environment reached the tolerance.  The
 trajectory advances from the seeded start state (no reset between steps).
-  value     converged env-steps/s, state resident in HBM (device-timed); the
-            method with the damped update projected onto the friction cone
-            (option cone_project; the printed update is the "as_printed" arm)
-  arms      the same measurement for: the printed update, the previous-step
-            warm start, and the learned warm start (when trained weights exist)
+  value     converged env-steps/s, state resident in HBM (device-timed), of
+            the learned + batched form: per island the least-merit start among
+            the network's lambda^0, the previous step's multipliers (its
+            fallback) and zero; damped update projected onto the friction cone
+            (option cone_project)
+  arms      the same measurement for: the plain batched method (zero start),
+            the printed update, the previous-step start alone, and the first
+            step after an environment reset with the zero / learned start
   e2e       converged env-steps/s through the C ABI with host buffers: host->
             device copy of the state, the step, device->host copy of the state
+            (the state makes that round trip every step)
   roofline  the CR operator apply (body pass + row pass, island kernels),
             bytes per launch from the algorithmic count B_apply, timed live
-  cpu_baseline  the FP64 oracle on a 64-environment sample, one host core,
-            same tolerance, caps and accounting
+  cpu_baseline  the FP64 oracle (plain method: zero start) on a
+            64-environment sample, one host core, same tolerance, caps and
+            accounting
 
 ``--impl reference`` times the FP64 oracle (the reference arm here) on the
 host cores with the same workload definition, metric and unit.
@@ -228,9 +233,12 @@ def run_reference(args, rank, world):
     print(json.dumps(out), flush=True)
 
 
+EAGER = False   # --eager: launch kernel by kernel instead of the CUDA graph (for profilers)
+
+
 def make_solver(nsn, s, stream, newton, cr, cone, warm=0, params=None):
     g = nsn.Solver(s, stream=stream.cuda_stream, newton_iters=newton, cr_iters=cr, tol_rel=TOL, island_stop=1,
-                   cone_project=cone, precision=nsn.NSN_FP32, use_graph=1)
+                   cone_project=cone, precision=nsn.NSN_FP32, use_graph=0 if EAGER else 1)
     if params is not None:
         nsn.nsn_mlp_set_params(g.ctx, params)
     g.set_warm_start(warm)
@@ -301,19 +309,30 @@ def run_ours(args, rank, world, local_rank):
     st0 = {k: torch.from_numpy(np.ascontiguousarray(s[k], dtype=np.float32)).to(dev)
            for k in ("pos", "quat", "vel", "omega")}
     params = np.load(WEIGHTS) if os.path.exists(WEIGHTS) else None
+    warm_names = {"learned": nsn.NSN_WARM_LEARNED, "prev": nsn.NSN_WARM_PREV, "zero": nsn.NSN_WARM_ZERO}
+    warm = args.warm
+    warm_note = {"learned": "learned (per-contact BF16 network) with the previous-step start as fallback: "
+                            "per island the least-merit candidate of network / previous step / zero",
+                 "prev": "previous-step multipliers (per island, kept if not worse than zero)",
+                 "zero": "zero (Sec. 8.1), the plain method"}[warm]
+    if warm == "learned" and params is None:
+        warm, warm_note = "prev", "previous-step multipliers (no trained network weights present)"
     with torch.cuda.stream(stream):
-        g = make_solver(nsn, s, stream, newton, cr, cone=1)
+        g = make_solver(nsn, s, stream, newton, cr, cone=1, warm=warm_names[warm], params=params)
         dist = None
         if world > 1:
             import torch.distributed as dist
             dist.barrier()
         clk = ClockSampler(local_rank)
         main_arm = measure_arm(nsn, torch, g, s, st0, stream, args.steps, args.warmup, clk)
+        if warm != "zero":
+            main_arm["network_or_warm_rejected_islands_last_step"] = g.warm_stats()["rejected"]
         sec = main_arm["sec"]
         units = main_arm["env_steps"]
         if dist:
             dist.barrier()
-        # e2e: host buffers through the C ABI (pinned), copies inside the timed region
+        # e2e: host buffers through the C ABI (pinned), copies inside the timed region; the state
+        # makes a round trip through the host every step (as in an RL loop) and the trajectory advances
         host_in = {k: torch.from_numpy(np.ascontiguousarray(s[k], dtype=np.float32)).pin_memory()
                    for k in ("pos", "quat", "vel", "omega")}
         host_out = {k: torch.empty_like(v).pin_memory() for k, v in host_in.items()}
@@ -324,13 +343,17 @@ def run_ours(args, rank, world, local_rank):
         ni, bi = g.islands()
         isl_env = island_env_map(s, bi, ni)
         stops = torch.empty((args.steps, max(ni, 1)), dtype=torch.int32, device=dev)
+        keys = ("pos", "quat", "vel", "omega")
 
         def e2e_step(k):
-            L.nsn_set_state(g.ctx, *[fp(host_in[k2]) for k2 in ("pos", "quat", "vel", "omega")])
+            L.nsn_set_state(g.ctx, *[fp(host_in[k2]) for k2 in keys])
             g.step(1)
             L.nsn_island_stop_copy(g.ctx, nsn.C.c_void_p(stops[k].data_ptr()))
-            L.nsn_get_state(g.ctx, *[fp(host_out[k2]) for k2 in ("pos", "quat", "vel", "omega")])
+            L.nsn_get_state(g.ctx, *[fp(host_out[k2]) for k2 in keys])
+            for k2 in keys:
+                host_in[k2].copy_(host_out[k2])
 
+        g.clear_warm_start()
         for _ in range(max(args.warmup, 1)):
             e2e_step(0)
         if dist:
@@ -348,18 +371,20 @@ def run_ours(args, rank, world, local_rank):
         # the other arms, same trajectory and accounting
         arms = {}
         if args.arms:
-            for name, cone, warm, reset in (("as_printed", 0, nsn.NSN_WARM_ZERO, False),
-                                            ("prev_warm_start", 1, nsn.NSN_WARM_PREV, False),
-                                            ("learned_warm_start", 1, nsn.NSN_WARM_LEARNED, False),
-                                            ("after_reset_zero", 1, nsn.NSN_WARM_ZERO, True),
-                                            ("after_reset_learned", 1, nsn.NSN_WARM_LEARNED, True)):
-                if warm == nsn.NSN_WARM_LEARNED and params is None:
+            for name, cone, wm, reset in (("plain_zero_start", 1, nsn.NSN_WARM_ZERO, False),
+                                          ("as_printed", 0, nsn.NSN_WARM_ZERO, False),
+                                          ("prev_warm_start", 1, nsn.NSN_WARM_PREV, False),
+                                          ("after_reset_zero", 1, nsn.NSN_WARM_ZERO, True),
+                                          ("after_reset_learned", 1, nsn.NSN_WARM_LEARNED, True)):
+                if wm == warm_names[warm] and not reset and cone == 1:
+                    continue
+                if wm == nsn.NSN_WARM_LEARNED and params is None:
                     arms[name] = {"unavailable": "no trained weights (paper_1907_04587_gb300/weights)"}
                     continue
-                ga = make_solver(nsn, s, stream, newton, cr, cone=cone, warm=warm, params=params)
+                ga = make_solver(nsn, s, stream, newton, cr, cone=cone, warm=wm, params=params)
                 r = measure_arm(nsn, torch, ga, s, st0, stream, args.steps, args.warmup, reset=reset)
-                if warm != nsn.NSN_WARM_ZERO:
-                    r["warm_rejected_islands_last_step"] = ga.warm_stats()["rejected"]
+                if wm != nsn.NSN_WARM_ZERO:
+                    r["network_or_warm_rejected_islands_last_step"] = ga.warm_stats()["rejected"]
                 ga.close()
                 r.pop("sec")
                 arms[name] = r
@@ -389,8 +414,9 @@ def run_ours(args, rank, world, local_rank):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": args.workload, "description": W["desc"], "n_envs": n_envs, "bodies": g.nb,
                    "rows": sz["rows"], "islands": main_arm["islands"], "newton_cap": newton, "cr_iters": cr,
-                   "tol_rel": TOL, "cone_projection": True, "warm_start": "zero (Sec. 8.1)",
-                   "device_bytes": sz["device_bytes"],
+                   "tol_rel": TOL, "cone_projection": True, "warm_start": warm_note,
+                   "device_bytes": sz["device_bytes"], "launch": "kernel by kernel" if EAGER else
+                   "one CUDA graph per step (Newton and CR loops as conditional WHILE nodes)",
                    "l2": "working set larger than L2 (no flush between steps)",
                    "parallelism": f"weak, {world} independent replica(s)"},
         "convergence": main_arm,
@@ -402,7 +428,7 @@ def run_ours(args, rank, world, local_rank):
                      "bytes_design": design_bytes(sz), "peak_kind": f"{peak_kind} hbm_gbs (burst)"},
         "cpu_baseline": cb,
         "e2e": {"value": value_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "note": "every e2e step starts from the host copy of the start state"},
+                "note": "the state makes a host round trip every step; the trajectory advances"},
         "gpu_launches": main_arm["kernels"],
         "clocks": clk.summary(),
     }
@@ -418,10 +444,16 @@ def main():
     ap.add_argument("--workload", default="batched4096", choices=list(WORKLOADS))
     ap.add_argument("--newton", type=int, default=0)
     ap.add_argument("--cr", type=int, default=0)
-    ap.add_argument("--arms", type=int, default=1, help="also measure the as-printed and warm-start arms")
+    ap.add_argument("--arms", type=int, default=1, help="also measure the plain, as-printed and reset arms")
+    ap.add_argument("--warm", default="learned", choices=["learned", "prev", "zero"],
+                    help="warm start of the headline arm (learned: network with previous-step fallback)")
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--ref-budget", type=float, default=60.0, help="seconds of oracle work for --impl reference")
+    ap.add_argument("--eager", type=int, default=0,
+                    help="1: launch kernel by kernel (ncu cannot profile kernels of graphs with conditional nodes)")
     args = ap.parse_args()
+    global EAGER
+    EAGER = bool(args.eager)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
