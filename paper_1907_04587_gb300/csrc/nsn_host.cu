@@ -585,6 +585,15 @@ struct Launcher {
     else k_row_pass<T, RM_APPLY><<<nb, BLOCK, 0, st>>>(D, force);
     count++;
   }
+  // merit of an evaluation (island mode: the per-island pass first); the
+  // k_merit launch itself is counted by the callers
+  void merit(int n, int force) {
+    if (D.isl_on) {
+      k_merit_isl<T><<<cdiv(std::max(D.ni, 1), 256), 256, 0, st>>>(D, n, force);
+      count++;
+    }
+    k_merit<T><<<1, RED_THREADS, 0, st>>>(D, n, force);
+  }
   void eval(int buf, int force) {
     if (D.nc) { k_eval_contacts<T><<<cdiv(D.nc, 128), 128, 0, st>>>(D, buf, force); count++; }
     if (D.nj) { k_eval_joints<T><<<cdiv(D.nj, 128), 128, 0, st>>>(D, buf, force); count++; }
@@ -606,7 +615,7 @@ struct Launcher {
     eval(buf, 0);
     body(BM_RESIDUAL, D.lam, buf, n, 0);
     rows(RM_RHS, 0);
-    k_merit<T><<<1, RED_THREADS, 0, st>>>(D, n, 0);
+    merit(n, 0);
     count++;
   }
   void cr_begin(int M) {
@@ -643,14 +652,14 @@ struct Launcher {
     eval(0, 1);
     body(BM_RESIDUAL, D.lam, 0, 0, 1);
     rows(RM_RHS, 1);
-    k_merit<T><<<1, RED_THREADS, 0, st>>>(D, -1, 1);
+    merit(-1, 1);
     count++;
     // previous-step candidate (also the fallback of the learned start)
     if (D.R) { k_warm_from_prev<T><<<D.nblk_upd, BLOCK, 0, st>>>(D, c->warm_friction); count++; }
     eval(0, 1);
     body(BM_RESIDUAL, D.lam, 0, 0, 1);
     rows(RM_RHS, 1);
-    k_merit<T><<<1, RED_THREADS, 0, st>>>(D, -2, 1);
+    merit(-2, 1);
     count++;
     if (c->warm_mode == NSN_WARM_PREV) {
       k_warm_accept<T><<<D.nblk_upd, BLOCK, 0, st>>>(D);
@@ -663,7 +672,7 @@ struct Launcher {
     eval(0, 1);
     body(BM_RESIDUAL, D.lam, 0, 0, 1);
     rows(RM_RHS, 1);
-    k_merit<T><<<1, RED_THREADS, 0, st>>>(D, -4, 1);
+    merit(-4, 1);
     k_warm_choose<T><<<D.nblk_upd, BLOCK, 0, st>>>(D, c->warm_friction);
     count += 2;
   }
@@ -692,7 +701,7 @@ struct Launcher {
     eval(IT_DEV, 1);
     body(BM_RESIDUAL, D.lam, IT_DEV, IT_DEV, 1);
     rows(RM_RHS, 1);
-    k_merit<T><<<1, RED_THREADS, 0, st>>>(D, IT_FINAL, 1);
+    merit(IT_FINAL, 1);
     count++;
     if (D.R) { k_copy<T><<<D.nblk_upd, BLOCK, 0, st>>>(D.lam_prev, D.lam, D.R); count++; }
   }

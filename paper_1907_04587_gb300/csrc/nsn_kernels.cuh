@@ -48,6 +48,7 @@ struct Flags {
   int cr_k;          // current CR iteration within this Newton iteration
   int cr_live;       // 1 while the CR loop continues
   int cr_exec;       // CR loop bodies executed in this step
+  int isl_any;       // island mode: 1 if an island continues (k_merit_isl)
 };
 
 // iteration index / entry buffer taken from Flags::newton_n
@@ -65,7 +66,7 @@ struct IslState {
   double *m0, *mf, *mw;      // zero-iterate, final and warm-start merits
   double *mw2;               // merit of the second warm-start candidate (learned)
   double *eta, *res0;        // CR forcing term and ||r_0||_P of the Newton iteration
-  double *res_prev;          // ||r||_P of the previous CR iteration
+  double *res_prev;          // ||r||_P^2 of the previous CR iteration
   double *rho;               // [2][ni], double-buffered by CR iteration parity
   double *alpha, *beta;
   float *alpha_f, *beta_f;
@@ -85,6 +86,7 @@ struct Scalars {
   double alpha, beta;   // CR step of the current iteration
   float alpha_f, beta_f; // the same, rounded once for the FP32 update kernel
   double merit_final;   // merit at the returned iterate
+  double isl_m2;        // island mode: sum of the islands' merit^2 (k_merit_isl)
   double merit_warm;    // merit at the warm-started iterate (u = 0, lambda^0)
   double merit_warm2;   // merit at the second candidate (learned, after previous-step)
   int warm_rejected;    // 1 if the warm start was worse than the zero start (island
@@ -1371,6 +1373,63 @@ __global__ void __launch_bounds__(BLOCK) k_row_pass_isl(Dev<T> D, int force) {
   }
 }
 
+// Island mode, before k_merit: per island the merit, the stop test, the CR
+// forcing term and the CR start (one thread per island); the blocks add the
+// islands' merit^2 into sc->isl_m2 and flag in fl->isl_any whether an island
+// continues.  n and force as for k_merit.
+template <typename T>
+__global__ void k_merit_isl(Dev<T> D, int n, int force) {
+  if (!force && D.fl->newton_stop) return;
+  if (n == IT_DEV) n = D.fl->newton_n;
+  const bool final_eval = n == IT_FINAL;
+  const int ni = D.ni;
+  double *acc = D.isl.acc;
+  double m2 = 0.0;
+  int active = 0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ni; i += gridDim.x * blockDim.x) {
+    const double a = acc[i], bz = acc[ni + i];
+    acc[i] = 0.0; acc[ni + i] = 0.0;
+    const double mi = sqrt(a);
+    if (n == -1) { D.isl.m0[i] = mi; m2 += a; continue; }
+    if (n == -2) { D.isl.mw[i] = mi; m2 += a; continue; }
+    if (n == -4) { D.isl.mw2[i] = mi; m2 += a; continue; }
+    if (final_eval) { D.isl.mf[i] = mi; m2 += a; continue; }
+    if (force) { m2 += a; continue; }     // evaluation without a stop test
+    int st = D.isl.stop[i];
+    if (st >= 0) {                       // stopped: not evaluated, keeps its last merit
+      m2 += D.isl.mf[i] * D.isl.mf[i];
+      D.isl.crdone[i] = 1;
+      continue;
+    }
+    m2 += a;
+    D.isl.mf[i] = mi;
+    if (n == 0 && !D.warm) D.isl.m0[i] = mi;
+    const double m0 = D.isl.m0[i];
+    if (D.tol_rel > 0.0 && mi <= D.tol_rel * m0) { st = n; D.isl.stop[i] = n; }
+    double eta = 0.0;
+    if (D.cr_tol) {
+      eta = m0 > 0.0 ? mi / m0 : 0.0;
+      if (eta > 0.1) eta = 0.1;
+      if (eta <= 0.0) eta = 1e-30;
+    }
+    D.isl.eta[i] = eta;
+    const double r0 = sqrt(bz);
+    D.isl.res0[i] = r0;
+    D.isl.crdone[i] = (st >= 0 || r0 == 0.0) ? 1 : 0;
+    active |= st < 0;
+  }
+  __shared__ double sm[32];
+  for (int o = 16; o > 0; o >>= 1) m2 += __shfl_down_sync(0xffffffffu, m2, o);
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = m2;
+  const int any = __syncthreads_or(active);
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < int(blockDim.x) / 32; w++) t += sm[w];
+    atomicAdd(&D.sc->isl_m2, t);
+    if (any) atomicOr(&D.fl->isl_any, 1);
+  }
+}
+
 // merit of this Newton iteration, Newton stop test, CR forcing term (1 block)
 template <typename T>
 __global__ void __launch_bounds__(RED_THREADS) k_merit(Dev<T> D, int n, int force) {
@@ -1390,53 +1449,13 @@ __global__ void __launch_bounds__(RED_THREADS) k_merit(Dev<T> D, int n, int forc
     m = sqrt(g2 + r4[0]);
     res0 = sqrt(r4[1]);
   } else {
-    // per island: merit, stop test, forcing term, CR start; the global merit
-    // is the norm over all islands
-    const int ni = D.ni;
-    double *acc = D.isl.acc;
-    double m2 = 0.0;
-    int active = 0;
-    for (int i = threadIdx.x; i < ni; i += RED_THREADS) {
-      const double a = acc[i], bz = acc[ni + i];
-      acc[i] = 0.0; acc[ni + i] = 0.0;
-      const double mi = sqrt(a);
-      if (n == -1) { D.isl.m0[i] = mi; m2 += a; continue; }
-      if (n == -2) { D.isl.mw[i] = mi; m2 += a; continue; }
-      if (n == -4) { D.isl.mw2[i] = mi; m2 += a; continue; }
-      if (final_eval) { D.isl.mf[i] = mi; m2 += a; continue; }
-      if (force) { m2 += a; continue; }     // evaluation without a stop test
-      int st = D.isl.stop[i];
-      if (st >= 0) {                       // stopped: not evaluated, keeps its last merit
-        m2 += D.isl.mf[i] * D.isl.mf[i];
-        D.isl.crdone[i] = 1;
-        continue;
-      }
-      m2 += a;
-      D.isl.mf[i] = mi;
-      if (n == 0 && !D.warm) D.isl.m0[i] = mi;
-      const double m0 = D.isl.m0[i];
-      if (st < 0 && D.tol_rel > 0.0 && mi <= D.tol_rel * m0) { st = n; D.isl.stop[i] = n; }
-      double eta = 0.0;
-      if (D.cr_tol) {
-        eta = m0 > 0.0 ? mi / m0 : 0.0;
-        if (eta > 0.1) eta = 0.1;
-        if (eta <= 0.0) eta = 1e-30;
-      }
-      D.isl.eta[i] = eta;
-      const double r0 = sqrt(bz);
-      D.isl.res0[i] = r0;
-      D.isl.crdone[i] = (st >= 0 || r0 == 0.0) ? 1 : 0;
-      active |= st < 0;
-    }
-    __shared__ double sm[RED_THREADS / 32];
-    for (int o = 16; o > 0; o >>= 1) m2 += __shfl_down_sync(0xffffffffu, m2, o);
-    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = m2;
-    const int any = __syncthreads_or(active);
+    // the per-island work was done by k_merit_isl; its blocks left the
+    // sum of the islands' merit^2 and whether any island continues
     if (threadIdx.x == 0) {
-      double t2 = 0.0;
-      for (int w = 0; w < RED_THREADS / 32; w++) t2 += sm[w];
-      m = sqrt(t2);
-      if (n >= 0 && !force && !any) D.fl->newton_stop = 1;
+      m = sqrt(D.sc->isl_m2);
+      if (n >= 0 && !force && !D.fl->isl_any) D.fl->newton_stop = 1;
+      D.sc->isl_m2 = 0.0;
+      D.fl->isl_any = 0;
     }
   }
   if (threadIdx.x == 0) {
@@ -1562,15 +1581,17 @@ __global__ void k_cr_scalars_isl(Dev<T> D) {
   double *acc = D.isl.acc + 2 * size_t(ni);
   int act = 0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ni; i += gridDim.x * blockDim.x) {
+    // a finished island's rows add nothing, so its accumulators stay zero
+    if (D.isl.crdone[i]) continue;
     const double d1 = acc[i], d2 = acc[ni + i], d3 = acc[2 * ni + i], d4 = acc[3 * ni + i], d5 = acc[4 * ni + i];
     acc[i] = 0.0; acc[ni + i] = 0.0; acc[2 * ni + i] = 0.0; acc[3 * ni + i] = 0.0; acc[4 * ni + i] = 0.0;
-    if (D.isl.crdone[i]) continue;
     int st = 0;
-    const double cur = sqrt(d4 > 0.0 ? d4 : 0.0);
-    const double r0 = D.isl.res0[i];
-    if (r0 == 0.0 || cur <= cr_floor<T>() * r0 || (k > 0 && cur > D.isl.res_prev[i])) st = 1;
-    D.isl.res_prev[i] = cur;
-    if (D.cr_tol && cur <= D.isl.eta[i] * r0) st = 1;
+    // stop tests on squared norms (no FP64 square root per island)
+    const double cur2 = d4 > 0.0 ? d4 : 0.0;
+    const double r0 = D.isl.res0[i], r02 = r0 * r0, fl = cr_floor<T>();
+    if (r0 == 0.0 || cur2 <= fl * fl * r02 || (k > 0 && cur2 > D.isl.res_prev[i])) st = 1;
+    D.isl.res_prev[i] = cur2;
+    if (D.cr_tol && cur2 <= D.isl.eta[i] * D.isl.eta[i] * r02) st = 1;
     double beta = 0.0, rho = d1, apap = d2;
     if (k > 0) {
       const double rp = D.isl.rho[size_t((k - 1) & 1) * ni + i];
