@@ -54,9 +54,9 @@ struct Layout {
   int ni = 0;                       // islands: connected components of bodies through constraints
   std::vector<int> body_isl;        // ABI body id -> island
   std::vector<int> risl, bisl_r, bisl_p;  // island of each row / rigid body / particle
-  // Internal order: bodies, contacts, joints and tets sorted by island (stable),
-  // so that each island's bodies, entries and rows are contiguous.  The ABI
-  // keeps the caller's order; these map internal -> ABI index.
+  // Internal order: bodies, contacts, joints and tets sorted by island (stable;
+  // islands largest first), so that each island's bodies, entries and rows are
+  // contiguous.  The ABI keeps the caller's order; these map internal -> ABI.
   std::vector<int> cperm, jperm, tperm, row_abi;
 };
 
@@ -184,9 +184,18 @@ nsn_status build_layout(nsn_ctx *c) {
   L = Layout();
   const int nb = int(S.kind.size());
   find_islands(S, L, nb);
+  // Internal island order: largest islands first (ties by id).  Islands that
+  // keep iterating after most have stopped are the large ones (long chains),
+  // so they cluster and blocks of finished islands are skipped as a whole.
+  std::vector<int> isl_size(L.ni, 0), rank(L.ni);
+  for (int b = 0; b < nb; b++) isl_size[L.body_isl[b]]++;
+  {
+    std::vector<int> o = order_by(L.ni, [&](int i) { return -isl_size[i]; });
+    for (int k = 0; k < L.ni; k++) rank[o[k]] = k;
+  }
   // bodies in island order (rigid and particle numbered separately)
   L.bmap.resize(nb);
-  for (int i : order_by(nb, [&](int b) { return L.body_isl[b]; })) {
+  for (int i : order_by(nb, [&](int b) { return rank[L.body_isl[b]]; })) {
     if (S.kind[i] == NSN_RIGID) { L.bmap[i] = L.nr++; L.rig_of.push_back(i); }
     else { L.bmap[i] = -2 - L.np++; L.par_of.push_back(i); }
   }
@@ -197,9 +206,9 @@ nsn_status build_layout(nsn_ctx *c) {
   L.R = L.Rpair + 3 * L.nt;
   // constraints in island order
   auto isl2 = [&](int a, int b) { return L.body_isl[a >= 0 ? a : b]; };
-  L.cperm = order_by(L.nc, [&](int i) { return isl2(S.contacts[i].body_a, S.contacts[i].body_b); });
-  L.jperm = order_by(L.nj, [&](int i) { return isl2(S.joints[i].body_a, S.joints[i].body_b); });
-  L.tperm = order_by(L.nt, [&](int i) { return L.body_isl[S.tets[i].v[0]]; });
+  L.cperm = order_by(L.nc, [&](int i) { return rank[isl2(S.contacts[i].body_a, S.contacts[i].body_b)]; });
+  L.jperm = order_by(L.nj, [&](int i) { return rank[isl2(S.joints[i].body_a, S.joints[i].body_b)]; });
+  L.tperm = order_by(L.nt, [&](int i) { return rank[L.body_isl[S.tets[i].v[0]]]; });
   L.row_abi.resize(L.R);
   L.risl.resize(L.R);
   for (int ci = 0; ci < L.nc; ci++) {
@@ -334,6 +343,9 @@ void carve(Arena &A, Dev<T> &D, const Layout &L, int nb) {
   D.isl.alpha = A.take<double>(ni); D.isl.beta = A.take<double>(ni);
   D.isl.alpha_f = A.take<float>(ni); D.isl.beta_f = A.take<float>(ni);
   D.isl.stop = A.take<int>(ni); D.isl.crdone = A.take<int>(ni);
+  D.fl_row = A.take<unsigned char>(size_t(L.R) / BLOCK + 1);
+  D.fl_br = A.take<unsigned char>(size_t(L.nr) / 32 + 1);
+  D.fl_bp = A.take<unsigned char>(size_t(L.np) / 32 + 1);
   (void)nb;
 }
 
@@ -350,10 +362,24 @@ void fill_sizes(Dev<T> &D, const Layout &L, const nsn_config &cfg) {
   D.ni = L.ni;
   D.isl_on = cfg.island_stop ? 1 : 0;
   D.cone = cfg.cone_project ? 1 : 0;
-  D.nblk_body_r = L.nr ? clampb(cdiv((long long)L.nr * kGroup, BLOCK)) : 0;
-  D.nblk_body_p = L.np ? clampb(cdiv((long long)L.np * kGroup, BLOCK)) : 0;
-  D.nblk_row_pair = L.Rpair ? clampb(cdiv(L.Rpair, BLOCK)) : 0;
-  D.nblk_row_tet = L.nt ? clampb(cdiv(L.nt, BLOCK)) : 0;
+  // grid-stride kernels get at most one wave: SMs x resident blocks per SM of
+  // the kernel (so that no partial second wave trails the first)
+  int dev = 0, nsm = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  auto wave = [&](const void *kern) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BLOCK, 0) != cudaSuccess || per_sm < 1) per_sm = 8;
+    return (long long)nsm * per_sm;
+  };
+  const long long cap_body = wave(reinterpret_cast<const void *>(&k_body_pass<T, kGroup, BM_APPLY>));
+  const long long cap_row = cfg.island_stop ? wave(reinterpret_cast<const void *>(&k_row_pass_isl<T, RM_APPLY>))
+                                            : wave(reinterpret_cast<const void *>(&k_row_pass<T, RM_APPLY>));
+  auto capped = [](long long n, long long cap) { return int(std::max(1LL, std::min({n, cap, (long long)kMaxBlocks}))); };
+  D.nblk_body_r = L.nr ? capped(cdiv((long long)L.nr * kGroup, BLOCK), cap_body) : 0;
+  D.nblk_body_p = L.np ? capped(cdiv((long long)L.np * kGroup, BLOCK), cap_body) : 0;
+  D.nblk_row_pair = L.Rpair ? capped(cdiv(L.Rpair, BLOCK), cap_row) : 0;
+  D.nblk_row_tet = L.nt ? capped(cdiv(L.nt, BLOCK), cap_row) : 0;
   D.nblk_upd = clampb(cdiv(std::max(L.R, 1), BLOCK));
 }
 
@@ -479,6 +505,9 @@ nsn_status upload(nsn_ctx *c, Dev<T> &D) {
     CUDA_TRY(c, cudaMemsetAsync(D.isl.mw, 0, sizeof(double) * ni, st));
     CUDA_TRY(c, cudaMemsetAsync(D.isl.stop, 0xff, sizeof(int) * ni, st));
     CUDA_TRY(c, cudaMemsetAsync(D.isl.crdone, 0, sizeof(int) * ni, st));
+    CUDA_TRY(c, cudaMemsetAsync(D.fl_row, 1, size_t(L.R) / BLOCK + 1, st));
+    CUDA_TRY(c, cudaMemsetAsync(D.fl_br, 1, size_t(L.nr) / 32 + 1, st));
+    CUDA_TRY(c, cudaMemsetAsync(D.fl_bp, 1, size_t(L.np) / 32 + 1, st));
   }
   for (int b2 = 0; b2 < 2; b2++)
     for (int k = 0; k < 3; k++)
@@ -690,6 +719,11 @@ struct Launcher {
   }
   void newton_head(int M) {
     linearize_at(IT_DEV);
+    if (D.isl_on) {
+      const int nblk = std::max({cdiv(std::max(D.R, 1), BLOCK), cdiv(D.nr, 32), cdiv(D.np, 32), 1});
+      k_block_flags<T><<<nblk, BLOCK, 0, st>>>(D);
+      count++;
+    }
     if (D.R && M > 0) cr_begin(M);
   }
   void newton_tail(int N) {
@@ -717,6 +751,16 @@ struct Launcher {
     suffix();
   }
 };
+
+// island mode: every block of rows and bodies takes part (verification paths
+// that run CR without the per-Newton-iteration block flags)
+template <typename T>
+void blocks_all_on(Dev<T> &D, cudaStream_t st) {
+  if (!D.isl_on) return;
+  cudaMemsetAsync(D.fl_row, 1, size_t(D.R) / BLOCK + 1, st);
+  cudaMemsetAsync(D.fl_br, 1, size_t(D.nr) / 32 + 1, st);
+  cudaMemsetAsync(D.fl_bp, 1, size_t(D.np) / 32 + 1, st);
+}
 
 template <typename T>
 Dev<T> &dev(nsn_ctx *c);
@@ -940,6 +984,7 @@ nsn_status do_linearize(nsn_ctx *c, int n_before) {
   const int nbt = D.nr + D.np;
   T *bk = reinterpret_cast<T *>(c->d_backup);
   if (nbt) k_backup_state<T><<<cdiv(nbt, 128), 128, 0, st>>>(D, bk, 0);
+  blocks_all_on(D, st);
   Launcher<T> Lr{c, D, st};
   Lr.begin();
   for (int n = 0; n < n_before; n++) {
@@ -1021,6 +1066,7 @@ nsn_status do_solve(nsn_ctx *c, int iters, double *dl, double *du) {
   Dev<T> &D = dev<T>(c);
   cudaStream_t st = c->stream;
   CUDA_TRY(c, cudaMemsetAsync(D.fl, 0, sizeof(Flags), st));
+  blocks_all_on(D, st);
   if (D.R) {
     k_cr_init<T><<<D.nblk_upd, BLOCK, 0, st>>>(D);
     // res0 for the scalar kernel
@@ -1126,7 +1172,12 @@ nsn_status do_time_operator(nsn_ctx *c, int iters, float *ms_body, float *ms_row
   for (auto &x : e) CUDA_TRY(c, cudaEventCreate(&x));
   CUDA_TRY(c, cudaMemsetAsync(D.fl, 0, sizeof(Flags), st));
   // island mode: time the apply with every island taking part
-  if (D.isl_on && D.ni) CUDA_TRY(c, cudaMemsetAsync(D.isl.crdone, 0, sizeof(int) * D.ni, st));
+  if (D.isl_on && D.ni) {
+    CUDA_TRY(c, cudaMemsetAsync(D.isl.crdone, 0, sizeof(int) * D.ni, st));
+    CUDA_TRY(c, cudaMemsetAsync(D.fl_row, 1, size_t(D.R) / BLOCK + 1, st));
+    CUDA_TRY(c, cudaMemsetAsync(D.fl_br, 1, size_t(D.nr) / 32 + 1, st));
+    CUDA_TRY(c, cudaMemsetAsync(D.fl_bp, 1, size_t(D.np) / 32 + 1, st));
+  }
   Launcher<T> Lr{c, D, st};
   double tb = 0.0, tr = 0.0;
   const int buf = c->kept_buf < 0 ? 0 : c->kept_buf;  // entries written by the final evaluation of the last step

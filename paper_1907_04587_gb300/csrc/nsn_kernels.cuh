@@ -160,6 +160,10 @@ struct Dev {
                      // features and predictions are exchanged in ABI order
   int *row_abi_dev;  // ABI index of each (island-ordered) row
   IslState isl;
+  // island mode: per block of 256 consecutive rows / 32 consecutive bodies, 1
+  // if it holds an island that has not stopped (set each Newton iteration by
+  // k_block_flags; the CR-loop kernels skip blocks whose flag is 0)
+  unsigned char *fl_row, *fl_br, *fl_bp;
   // conditional handles of the captured Newton / CR WHILE nodes (0: none)
   cudaGraphConditionalHandle hN, hC;
 };
@@ -896,9 +900,11 @@ __global__ void __launch_bounds__(BLOCK) k_body_pass(Dev<T> D, const T *__restri
   const int lane = threadIdx.x % G;
   const T h = D.hT;
   const int Rp = D.Rpair;
+  const bool blk_skip = MODE == BM_APPLY && D.isl_on && !force;
   if (blockIdx.x < D.nblk_body_r) {
     const int stride = D.nblk_body_r * gpb;
     for (int b0 = blockIdx.x * gpb; b0 < D.nr; b0 += stride) {
+      if (blk_skip && !D.fl_br[b0 / gpb]) continue;   // no iterating island among these bodies
       const int b = b0 + gid;
       bool act = b < D.nr;
       if (act && D.isl_on && isl_skip<MODE>(D, D.bisl_r[b], force)) act = false;
@@ -1034,6 +1040,7 @@ __global__ void __launch_bounds__(BLOCK) k_body_pass(Dev<T> D, const T *__restri
     const int *eslot = D.eslot + D.ER;
     const bool gs = MODE == BM_RESIDUAL && D.gs && newton_it > 0;
     for (int b0 = bid * gpb; b0 < D.np; b0 += stride) {
+      if (blk_skip && !D.fl_bp[b0 / gpb]) continue;
       const int b = b0 + gid;
       bool act = b < D.np;
       if (act && D.isl_on && isl_skip<MODE>(D, D.bisl_p[b], force)) act = false;
@@ -1276,6 +1283,7 @@ __global__ void __launch_bounds__(BLOCK) k_row_pass_isl(Dev<T> D, int force) {
   if (blockIdx.x < D.nblk_row_pair) {
     const int stride = D.nblk_row_pair * BLOCK;
     for (int w0 = blockIdx.x * BLOCK + (threadIdx.x & ~31); w0 < D.Rpair; w0 += stride) {
+      if (MODE == RM_APPLY && !force && !D.fl_row[w0 / BLOCK]) continue;   // block of finished islands
       const int i = w0 + lane;
       int key = i < D.Rpair ? D.risl[i] : -1;
       if (key >= 0 && (MODE == RM_APPLY ? D.isl.crdone[key] != 0 : (!force && D.isl.stop[key] >= 0))) key = -1;
@@ -1427,6 +1435,32 @@ __global__ void k_merit_isl(Dev<T> D, int n, int force) {
     for (int w = 0; w < int(blockDim.x) / 32; w++) t += sm[w];
     atomicAdd(&D.sc->isl_m2, t);
     if (any) atomicOr(&D.fl->isl_any, 1);
+  }
+}
+
+// Island mode, once per Newton iteration after k_merit_isl: block flags for
+// the CR loop (see Dev::fl_row).  Block j: rows [256 j, 256 j + 256) with its
+// 256 threads; warp 0: rigid bodies [32 j, 32 j + 32); warp 1: particles.
+template <typename T>
+__global__ void __launch_bounds__(BLOCK) k_block_flags(Dev<T> D) {
+  if (D.fl->newton_stop) return;
+  const int j = blockIdx.x;
+  const int r = j * BLOCK + threadIdx.x;
+  const bool live = r < D.R && D.isl.stop[D.risl[r]] < 0;
+  const int any = __syncthreads_or(live);
+  if (threadIdx.x == 0 && j * BLOCK < D.R) D.fl_row[j] = any ? 1 : 0;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (w == 0 && j * 32 < D.nr) {
+    const int b = j * 32 + lane;
+    const bool lb = b < D.nr && D.isl.stop[D.bisl_r[b]] < 0;
+    const unsigned m = __ballot_sync(0xffffffffu, lb);
+    if (lane == 0) D.fl_br[j] = m ? 1 : 0;
+  }
+  if (w == 1 && j * 32 < D.np) {
+    const int b = j * 32 + lane;
+    const bool lb = b < D.np && D.isl.stop[D.bisl_p[b]] < 0;
+    const unsigned m = __ballot_sync(0xffffffffu, lb);
+    if (lane == 0) D.fl_bp[j] = m ? 1 : 0;
   }
 }
 
@@ -1638,6 +1672,7 @@ __global__ void __launch_bounds__(BLOCK) k_cr_update_isl(Dev<T> D) {
   const int k = D.fl->cr_k;
   const int stride = gridDim.x * BLOCK;
   for (int i = blockIdx.x * BLOCK + threadIdx.x; i < D.R; i += stride) {
+    if (!D.fl_row[i / BLOCK]) continue;          // block of finished islands (uniform per block)
     const int is = D.risl[i];
     if (D.isl.crdone[is]) continue;
     const T alpha = isl_scalar<T>(D.isl.alpha, D.isl.alpha_f, is), beta = isl_scalar<T>(D.isl.beta, D.isl.beta_f, is);
