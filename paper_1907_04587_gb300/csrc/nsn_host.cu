@@ -346,6 +346,10 @@ void carve(Arena &A, Dev<T> &D, const Layout &L, int nb) {
   D.fl_row = A.take<unsigned char>(size_t(L.R) / BLOCK + 1);
   D.fl_br = A.take<unsigned char>(size_t(L.nr) / 32 + 1);
   D.fl_bp = A.take<unsigned char>(size_t(L.np) / 32 + 1);
+  D.list_row = A.take<int>(size_t(L.R) / BLOCK + 1);
+  D.list_br = A.take<int>(size_t(L.nr) / 32 + 1);
+  D.list_bp = A.take<int>(size_t(L.np) / 32 + 1);
+  D.list_isl = A.take<int>(ni);
   (void)nb;
 }
 
@@ -618,6 +622,7 @@ struct Launcher {
   // k_merit launch itself is counted by the callers
   void merit(int n, int force) {
     if (D.isl_on) {
+      if (!force) { k_list_reset<T><<<1, 1, 0, st>>>(D); count++; }   // a Newton iteration: new work list
       k_merit_isl<T><<<cdiv(std::max(D.ni, 1), 256), 256, 0, st>>>(D, n, force);
       count++;
     }
@@ -722,7 +727,8 @@ struct Launcher {
     if (D.isl_on) {
       const int nblk = std::max({cdiv(std::max(D.R, 1), BLOCK), cdiv(D.nr, 32), cdiv(D.np, 32), 1});
       k_block_flags<T><<<nblk, BLOCK, 0, st>>>(D);
-      count++;
+      k_block_lists<T><<<1, 1024, 0, st>>>(D, 0);
+      count += 2;
     }
     if (D.R && M > 0) cr_begin(M);
   }
@@ -760,6 +766,7 @@ void blocks_all_on(Dev<T> &D, cudaStream_t st) {
   cudaMemsetAsync(D.fl_row, 1, size_t(D.R) / BLOCK + 1, st);
   cudaMemsetAsync(D.fl_br, 1, size_t(D.nr) / 32 + 1, st);
   cudaMemsetAsync(D.fl_bp, 1, size_t(D.np) / 32 + 1, st);
+  k_block_lists<T><<<1, 1024, 0, st>>>(D, 1);
 }
 
 template <typename T>

@@ -38,8 +38,7 @@ struct Flags {
   int cr_stop;       // set when the CR tolerance is met in this Newton iteration
   int newton_count;  // Newton iterations solved
   int cr_count;      // CR iterations performed (all Newton iterations)
-  int isl_ticket;    // blocks of the island CR scalar kernel that have finished
-  int isl_active;    // islands still iterating in this CR iteration
+  int isl_active;    // set by k_cr_scalars_isl blocks with an island that continues
   // loop state on the device: the Newton and CR iteration indices are read
   // from here by the kernels, so that one captured loop body serves every
   // iteration (CUDA graph conditional WHILE nodes)
@@ -49,6 +48,8 @@ struct Flags {
   int cr_live;       // 1 while the CR loop continues
   int cr_exec;       // CR loop bodies executed in this step
   int isl_any;       // island mode: 1 if an island continues (k_merit_isl)
+  // island mode: lengths of the work lists of this Newton iteration (k_block_lists)
+  int n_list_row, n_list_br, n_list_bp, n_list_isl;
 };
 
 // iteration index / entry buffer taken from Flags::newton_n
@@ -164,6 +165,9 @@ struct Dev {
   // if it holds an island that has not stopped (set each Newton iteration by
   // k_block_flags; the CR-loop kernels skip blocks whose flag is 0)
   unsigned char *fl_row, *fl_br, *fl_bp;
+  // and the same as lists of block indices (ascending), plus the islands that
+  // have not stopped: the CR-loop kernels visit only these
+  int *list_row, *list_br, *list_bp, *list_isl;
   // conditional handles of the captured Newton / CR WHILE nodes (0: none)
   cudaGraphConditionalHandle hN, hC;
 };
@@ -438,6 +442,7 @@ __global__ void k_begin_rigid(Dev<T> D) {
   if (i == 0) {
     D.fl->newton_stop = 0; D.fl->cr_stop = 0; D.fl->newton_count = 0; D.fl->cr_count = 0;
     D.fl->newton_n = 0; D.fl->newton_live = 1; D.fl->cr_k = 0; D.fl->cr_live = 0; D.fl->cr_exec = 0;
+    D.fl->n_list_isl = 0; D.fl->isl_active = 0;
   }
   if (i >= D.nr) return;
   T q[4], R[9], Ib[3], w[3], Iw[9], Iwi[9];
@@ -902,9 +907,10 @@ __global__ void __launch_bounds__(BLOCK) k_body_pass(Dev<T> D, const T *__restri
   const int Rp = D.Rpair;
   const bool blk_skip = MODE == BM_APPLY && D.isl_on && !force;
   if (blockIdx.x < D.nblk_body_r) {
-    const int stride = D.nblk_body_r * gpb;
-    for (int b0 = blockIdx.x * gpb; b0 < D.nr; b0 += stride) {
-      if (blk_skip && !D.fl_br[b0 / gpb]) continue;   // no iterating island among these bodies
+    // chunks of gpb bodies: all of them, or (CR loop, island mode) the listed ones
+    const int nch = blk_skip ? D.fl->n_list_br : (D.nr + gpb - 1) / gpb;
+    for (int j = blockIdx.x; j < nch; j += D.nblk_body_r) {
+      const int b0 = (blk_skip ? D.list_br[j] : j) * gpb;
       const int b = b0 + gid;
       bool act = b < D.nr;
       if (act && D.isl_on && isl_skip<MODE>(D, D.bisl_r[b], force)) act = false;
@@ -1035,12 +1041,12 @@ __global__ void __launch_bounds__(BLOCK) k_body_pass(Dev<T> D, const T *__restri
     }
   } else {
     const int bid = blockIdx.x - D.nblk_body_r;
-    const int stride = D.nblk_body_p * gpb;
     const T *J0 = D.ej3[buf][0], *J1 = D.ej3[buf][1], *J2 = D.ej3[buf][2];
     const int *eslot = D.eslot + D.ER;
     const bool gs = MODE == BM_RESIDUAL && D.gs && newton_it > 0;
-    for (int b0 = bid * gpb; b0 < D.np; b0 += stride) {
-      if (blk_skip && !D.fl_bp[b0 / gpb]) continue;
+    const int nch = blk_skip ? D.fl->n_list_bp : (D.np + gpb - 1) / gpb;
+    for (int j = bid; j < nch; j += D.nblk_body_p) {
+      const int b0 = (blk_skip ? D.list_bp[j] : j) * gpb;
       const int b = b0 + gid;
       bool act = b < D.np;
       if (act && D.isl_on && isl_skip<MODE>(D, D.bisl_p[b], force)) act = false;
@@ -1281,9 +1287,12 @@ __global__ void __launch_bounds__(BLOCK) k_row_pass_isl(Dev<T> D, int force) {
   const int lane = threadIdx.x & 31;
   const int ni = D.ni;
   if (blockIdx.x < D.nblk_row_pair) {
-    const int stride = D.nblk_row_pair * BLOCK;
-    for (int w0 = blockIdx.x * BLOCK + (threadIdx.x & ~31); w0 < D.Rpair; w0 += stride) {
-      if (MODE == RM_APPLY && !force && !D.fl_row[w0 / BLOCK]) continue;   // block of finished islands
+    // blocks of BLOCK rows: all of them, or (CR loop) the listed ones
+    const bool listed = MODE == RM_APPLY && !force;
+    const int nch = listed ? D.fl->n_list_row : (D.Rpair + BLOCK - 1) / BLOCK;
+    for (int j = blockIdx.x; j < nch; j += D.nblk_row_pair) {
+      const int w0 = (listed ? D.list_row[j] : j) * BLOCK + (threadIdx.x & ~31);
+      if (w0 >= D.Rpair) continue;                  // a listed block of tet rows (uniform per warp)
       const int i = w0 + lane;
       int key = i < D.Rpair ? D.risl[i] : -1;
       if (key >= 0 && (MODE == RM_APPLY ? D.isl.crdone[key] != 0 : (!force && D.isl.stop[key] >= 0))) key = -1;
@@ -1381,54 +1390,80 @@ __global__ void __launch_bounds__(BLOCK) k_row_pass_isl(Dev<T> D, int force) {
   }
 }
 
+// one island of k_merit_isl (n and force as for k_merit): merit, stop test,
+// forcing term, CR start; adds the island's merit^2 to m2.  Returns true if the
+// island continues to the CR solve of this Newton iteration.
+template <typename T>
+__device__ __forceinline__ bool isl_merit_one(const Dev<T> &D, int i, int n, int force, bool final_eval, double &m2,
+                                              int &active) {
+  const int ni = D.ni;
+  double *acc = D.isl.acc;
+  const double a = acc[i], bz = acc[ni + i];
+  acc[i] = 0.0; acc[ni + i] = 0.0;
+  const double mi = sqrt(a);
+  if (n == -1) { D.isl.m0[i] = mi; m2 += a; return false; }
+  if (n == -2) { D.isl.mw[i] = mi; m2 += a; return false; }
+  if (n == -4) { D.isl.mw2[i] = mi; m2 += a; return false; }
+  if (final_eval) { D.isl.mf[i] = mi; m2 += a; return false; }
+  if (force) { m2 += a; return false; }     // evaluation without a stop test
+  int st = D.isl.stop[i];
+  if (st >= 0) {                            // stopped: not evaluated, keeps its last merit
+    m2 += D.isl.mf[i] * D.isl.mf[i];
+    D.isl.crdone[i] = 1;
+    return false;
+  }
+  m2 += a;
+  D.isl.mf[i] = mi;
+  if (n == 0 && !D.warm) D.isl.m0[i] = mi;
+  const double m0 = D.isl.m0[i];
+  if (D.tol_rel > 0.0 && mi <= D.tol_rel * m0) { st = n; D.isl.stop[i] = n; }
+  double eta = 0.0;
+  if (D.cr_tol) {
+    eta = m0 > 0.0 ? mi / m0 : 0.0;
+    if (eta > 0.1) eta = 0.1;
+    if (eta <= 0.0) eta = 1e-30;
+  }
+  D.isl.eta[i] = eta;
+  const double r0 = sqrt(bz);
+  D.isl.res0[i] = r0;
+  const bool cont = st < 0 && r0 != 0.0;
+  D.isl.crdone[i] = cont ? 0 : 1;
+  active |= st < 0;
+  return cont;
+}
+
 // Island mode, before k_merit: per island the merit, the stop test, the CR
 // forcing term and the CR start (one thread per island); the blocks add the
 // islands' merit^2 into sc->isl_m2 and flag in fl->isl_any whether an island
-// continues.  n and force as for k_merit.
+// continues.  At a Newton iteration (n >= 0, no force) the islands whose CR
+// runs are appended to list_isl, the work list of k_cr_scalars_isl.
 template <typename T>
 __global__ void k_merit_isl(Dev<T> D, int n, int force) {
   if (!force && D.fl->newton_stop) return;
   if (n == IT_DEV) n = D.fl->newton_n;
   const bool final_eval = n == IT_FINAL;
   const int ni = D.ni;
-  double *acc = D.isl.acc;
   double m2 = 0.0;
   int active = 0;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ni; i += gridDim.x * blockDim.x) {
-    const double a = acc[i], bz = acc[ni + i];
-    acc[i] = 0.0; acc[ni + i] = 0.0;
-    const double mi = sqrt(a);
-    if (n == -1) { D.isl.m0[i] = mi; m2 += a; continue; }
-    if (n == -2) { D.isl.mw[i] = mi; m2 += a; continue; }
-    if (n == -4) { D.isl.mw2[i] = mi; m2 += a; continue; }
-    if (final_eval) { D.isl.mf[i] = mi; m2 += a; continue; }
-    if (force) { m2 += a; continue; }     // evaluation without a stop test
-    int st = D.isl.stop[i];
-    if (st >= 0) {                       // stopped: not evaluated, keeps its last merit
-      m2 += D.isl.mf[i] * D.isl.mf[i];
-      D.isl.crdone[i] = 1;
-      continue;
+  const bool regular = n >= 0 && !force;
+  const int lane = threadIdx.x & 31;
+  // warp-uniform loop: each warp appends its continuing islands with one atomic
+  for (int i0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); i0 < ni; i0 += gridDim.x * blockDim.x) {
+    const int i = i0 + lane;
+    const bool cont = i < ni && isl_merit_one(D, i, n, force, final_eval, m2, active);
+    if (regular) {
+      const unsigned m = __ballot_sync(0xffffffffu, cont);
+      if (m) {
+        int base = 0;
+        if (lane == 0) base = atomicAdd(&D.fl->n_list_isl, __popc(m));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (cont) D.list_isl[base + __popc(m & ((1u << lane) - 1u))] = i;
+      }
     }
-    m2 += a;
-    D.isl.mf[i] = mi;
-    if (n == 0 && !D.warm) D.isl.m0[i] = mi;
-    const double m0 = D.isl.m0[i];
-    if (D.tol_rel > 0.0 && mi <= D.tol_rel * m0) { st = n; D.isl.stop[i] = n; }
-    double eta = 0.0;
-    if (D.cr_tol) {
-      eta = m0 > 0.0 ? mi / m0 : 0.0;
-      if (eta > 0.1) eta = 0.1;
-      if (eta <= 0.0) eta = 1e-30;
-    }
-    D.isl.eta[i] = eta;
-    const double r0 = sqrt(bz);
-    D.isl.res0[i] = r0;
-    D.isl.crdone[i] = (st >= 0 || r0 == 0.0) ? 1 : 0;
-    active |= st < 0;
   }
   __shared__ double sm[32];
   for (int o = 16; o > 0; o >>= 1) m2 += __shfl_down_sync(0xffffffffu, m2, o);
-  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = m2;
+  if (lane == 0) sm[threadIdx.x >> 5] = m2;
   const int any = __syncthreads_or(active);
   if (threadIdx.x == 0) {
     double t = 0.0;
@@ -1462,6 +1497,48 @@ __global__ void __launch_bounds__(BLOCK) k_block_flags(Dev<T> D) {
     const unsigned m = __ballot_sync(0xffffffffu, lb);
     if (lane == 0) D.fl_bp[j] = m ? 1 : 0;
   }
+}
+
+// Compaction of the block flags and of the islands that have not stopped
+// into ascending index lists (one block; once per Newton iteration, after
+// k_block_flags).  Each thread scans a contiguous chunk; a block-wide
+// exclusive scan of the chunk counts gives each thread its output offset.
+__device__ __forceinline__ void compact_list(int n, int (*flag)(const void *, int), const void *src, int *out,
+                                             int *count) {
+  __shared__ int sc[1024];
+  const int nt = blockDim.x, t = threadIdx.x;
+  const int chunk = (n + nt - 1) / nt, lo = min(n, t * chunk), hi = min(n, lo + chunk);
+  int c = 0;
+  for (int i = lo; i < hi; i++) c += flag(src, i);
+  sc[t] = c;
+  __syncthreads();
+  for (int o = 1; o < nt; o <<= 1) {          // inclusive Hillis-Steele scan
+    const int v = t >= o ? sc[t - o] : 0;
+    __syncthreads();
+    sc[t] += v;
+    __syncthreads();
+  }
+  int pos = sc[t] - c;
+  for (int i = lo; i < hi; i++)
+    if (flag(src, i)) out[pos++] = i;
+  if (t == nt - 1) *count = sc[t];
+  __syncthreads();
+}
+
+__device__ int flag_u8(const void *p, int i) { return static_cast<const unsigned char *>(p)[i] != 0; }
+
+__device__ int flag_all(const void *, int) { return 1; }
+
+// all_islands = 1: every island is listed (verification paths that run CR
+// outside a step)
+template <typename T>
+__global__ void __launch_bounds__(1024) k_block_lists(Dev<T> D, int all_islands) {
+  if (!all_islands && D.fl->newton_stop) return;
+  compact_list((D.R + BLOCK - 1) / BLOCK, flag_u8, D.fl_row, D.list_row, &D.fl->n_list_row);
+  compact_list((D.nr + 31) / 32, flag_u8, D.fl_br, D.list_br, &D.fl->n_list_br);
+  compact_list((D.np + 31) / 32, flag_u8, D.fl_bp, D.list_bp, &D.fl->n_list_bp);
+  // in a step the island list comes from k_merit_isl; outside, every island
+  if (all_islands) compact_list(D.ni, flag_all, D.isl.stop, D.list_isl, &D.fl->n_list_isl);
 }
 
 // merit of this Newton iteration, Newton stop test, CR forcing term (1 block)
@@ -1605,8 +1682,8 @@ __global__ void __launch_bounds__(BLOCK) k_cr_update(Dev<T> D) {
 
 // Island mode of K7: the same recurrence with each island's own scalars (A
 // is block diagonal by island, so this is CR on every island's system by
-// itself).  One thread per island; the last block to finish sets cr_stop when
-// no island continues.
+// itself).  One thread per island that has not stopped (the list built by
+// k_merit_isl).
 template <typename T>
 __global__ void k_cr_scalars_isl(Dev<T> D) {
   if (D.fl->newton_stop || D.fl->cr_stop) return;
@@ -1614,7 +1691,9 @@ __global__ void k_cr_scalars_isl(Dev<T> D) {
   const int ni = D.ni;
   double *acc = D.isl.acc + 2 * size_t(ni);
   int act = 0;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ni; i += gridDim.x * blockDim.x) {
+  const int nl = D.fl->n_list_isl;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nl; j += gridDim.x * blockDim.x) {
+    const int i = D.list_isl[j];
     // a finished island's rows add nothing, so its accumulators stay zero
     if (D.isl.crdone[i]) continue;
     const double d1 = acc[i], d2 = acc[ni + i], d3 = acc[2 * ni + i], d4 = acc[3 * ni + i], d5 = acc[4 * ni + i];
@@ -1643,20 +1722,10 @@ __global__ void k_cr_scalars_isl(Dev<T> D) {
     D.isl.alpha_f[i] = float(alpha); D.isl.beta_f[i] = float(beta);
     act = 1;
   }
+  // k_cr_next, which runs after this kernel's blocks have all finished, ends
+  // the CR loop when no block flagged an island that continues
   const int any = __syncthreads_or(act);
-  if (threadIdx.x == 0) {
-    if (any) atomicAdd(&D.fl->isl_active, 1);
-    __threadfence();
-    const int ticket = atomicAdd(&D.fl->isl_ticket, 1);
-    if (ticket == int(gridDim.x) - 1) {
-      __threadfence();
-      const int a = atomicAdd(&D.fl->isl_active, 0);
-      if (a == 0) D.fl->cr_stop = 1;
-      else D.fl->cr_count += 1;
-      D.fl->isl_active = 0;
-      D.fl->isl_ticket = 0;
-    }
-  }
+  if (threadIdx.x == 0 && any) atomicOr(&D.fl->isl_active, 1);
 }
 
 template <typename T>
@@ -1670,9 +1739,10 @@ template <typename T>
 __global__ void __launch_bounds__(BLOCK) k_cr_update_isl(Dev<T> D) {
   if (D.fl->newton_stop || D.fl->cr_stop) return;
   const int k = D.fl->cr_k;
-  const int stride = gridDim.x * BLOCK;
-  for (int i = blockIdx.x * BLOCK + threadIdx.x; i < D.R; i += stride) {
-    if (!D.fl_row[i / BLOCK]) continue;          // block of finished islands (uniform per block)
+  const int nch = D.fl->n_list_row;
+  for (int j = blockIdx.x; j < nch; j += gridDim.x) {
+    const int i = D.list_row[j] * BLOCK + threadIdx.x;
+    if (i >= D.R) continue;
     const int is = D.risl[i];
     if (D.isl.crdone[is]) continue;
     const T alpha = isl_scalar<T>(D.isl.alpha, D.isl.alpha_f, is), beta = isl_scalar<T>(D.isl.beta, D.isl.beta_f, is);
@@ -1701,6 +1771,11 @@ template <typename T>
 __global__ void k_cr_next(Dev<T> D, int M) {
   Flags *f = D.fl;
   if (f->cr_live) {
+    if (D.isl_on) {                    // island mode: did any island continue?
+      if (f->isl_active) f->cr_count += 1;
+      else f->cr_stop = 1;
+      f->isl_active = 0;
+    }
     const int k = f->cr_k + 1;
     f->cr_k = k;
     f->cr_exec += 1;
@@ -1708,6 +1783,10 @@ __global__ void k_cr_next(Dev<T> D, int M) {
   }
   if (D.hC) cudaGraphSetConditional(D.hC, unsigned(f->cr_live));
 }
+
+// empties the island work list before k_merit_isl fills it
+template <typename T>
+__global__ void k_list_reset(Dev<T> D) { D.fl->n_list_isl = 0; }
 
 template <typename T>
 __global__ void k_newton_next(Dev<T> D, int N) {
