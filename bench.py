@@ -92,6 +92,13 @@ def weak_scaling_value(units_per_rank, seconds_per_rank):
     return float(sum(units_per_rank)) / float(max(seconds_per_rank))
 
 
+def measured_bf16_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        return float(json.load(open(p))["bf16_tflops"]), "measured bf16_tflops (burst)"
+    return 1900.0, "fallback"
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -367,6 +374,29 @@ def run_ours(args, rank, world, local_rank):
         # roofline of the CR operator apply, timed live on the solver's stream
         ms_body, ms_row = g.time_operator(20)
         sz = g.sizes()
+        # the network's forward pass over every contact (BF16 tensor cores), timed live
+        mlp = None
+        if params is not None:
+            nc = len(s["c_body"])
+            X = torch.empty((nc, 16), dtype=torch.float32, device=dev)
+            Y = torch.empty((nc, 4), dtype=torch.float32, device=dev)
+            nsn.nsn_contact_features(g.ctx, X.data_ptr())
+            for _ in range(3):
+                nsn.nsn_mlp_forward(g.ctx, X.data_ptr(), nc, Y.data_ptr())
+            f0 = torch.cuda.Event(enable_timing=True)
+            f1 = torch.cuda.Event(enable_timing=True)
+            f0.record(stream)
+            for _ in range(10):
+                nsn.nsn_mlp_forward(g.ctx, X.data_ptr(), nc, Y.data_ptr())
+            f1.record(stream)
+            torch.cuda.synchronize()
+            ms_f = f0.elapsed_time(f1) / 10
+            flop = 2.0 * nc * (16 * 128 + 128 * 128 + 128 * 128 + 128 * 4)
+            bf16 = measured_bf16_peak()
+            mlp = {"bound": "tensor", "achieved": flop / (ms_f * 1e-3) / 1e12, "peak": bf16[0], "unit": "TFLOP/s",
+                   "frac": flop / (ms_f * 1e-3) / 1e12 / bf16[0], "contacts": nc, "ms_forward": ms_f,
+                   "flop_per_contact": flop / nc, "peak_kind": bf16[1],
+                   "kernel": "mlp::k_forward_fused (whole network per 16-row warp tile, weights in shared memory, mma.sync m16n8k16 BF16, FP32 accumulate)"}
         g.close()
         # the other arms, same trajectory and accounting
         arms = {}
@@ -426,6 +456,7 @@ def run_ours(args, rank, world, local_rank):
                      "kernel": "CR operator apply = k_body_pass<APPLY> + k_row_pass_isl<APPLY>",
                      "ms_body_pass": ms_body, "ms_row_pass": ms_row, "bytes_algorithmic": B,
                      "bytes_design": design_bytes(sz), "peak_kind": f"{peak_kind} hbm_gbs (burst)"},
+        "network_roofline": mlp,
         "cpu_baseline": cb,
         "e2e": {"value": value_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "note": "the state makes a host round trip every step; the trajectory advances"},

@@ -717,7 +717,7 @@ struct Launcher {
       k_contact_features<T><<<cdiv(D.nc, 128), 128, 0, st>>>(D, c->mlp.X);
       count++;
       mlp_infer(c, c->mlp.X, D.nc, c->mlp.Y, st);
-      count += 5 * ((D.nc + c->mlp.cap - 1) / c->mlp.cap);
+      count++;
     }
     begin();
     if (c->warm_mode != NSN_WARM_ZERO) warm_start();
@@ -1281,12 +1281,21 @@ nsn_status mlp_ensure(nsn_ctx *c, int rows_needed) {
   return NSN_OK;
 }
 
+// inference: one fused kernel (weights resident in shared memory), one CTA per SM
 nsn_status mlp_infer(nsn_ctx *c, const float *X, int n, float *Y, cudaStream_t st) {
   MlpState &m = c->mlp;
-  for (int r0 = 0; r0 < n; r0 += m.cap) {
-    const int nr = std::min(m.cap, n - r0);
-    mlp_forward_rows(m, X + size_t(r0) * mlp::NIN, nr, Y + size_t(r0) * mlp::NOUT, false, st);
+  if (n <= 0) return NSN_OK;
+  const size_t smem = sizeof(mlp::FusedSmem);
+  static bool attr_set = false;
+  if (!attr_set) {
+    CUDA_TRY(c, cudaFuncSetAttribute(mlp::k_forward_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+    attr_set = true;
   }
+  int dev = 0, nsm = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int tiles = cdiv(n, mlp::FW * 16);
+  mlp::k_forward_fused<<<std::min(tiles, nsm), mlp::FW * 32, smem, st>>>(X, n, m.pb, m.pf, Y);
   return NSN_OK;
 }
 
