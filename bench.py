@@ -374,6 +374,7 @@ def run_ours(args, rank, world, local_rank):
         # roofline of the CR operator apply, timed live on the solver's stream
         ms_body, ms_row = g.time_operator(20)
         sz = g.sizes()
+        tuned_lanes, tuned_ms = g.tuning()
         # the network's forward pass over every contact (BF16 tensor cores), timed live
         mlp = None
         if params is not None:
@@ -455,7 +456,9 @@ def run_ours(args, rank, world, local_rank):
                      "frac": achieved / peak, "traffic": operator_traffic(kernel_source_hash()),
                      "kernel": "CR operator apply = k_body_pass<APPLY> + k_row_pass_isl<APPLY>",
                      "ms_body_pass": ms_body, "ms_row_pass": ms_row, "bytes_algorithmic": B,
-                     "bytes_design": design_bytes(sz), "peak_kind": f"{peak_kind} hbm_gbs (burst)"},
+                     "bytes_design": design_bytes(sz), "peak_kind": f"{peak_kind} hbm_gbs (burst)",
+                     "body_pass_lanes_tuned": tuned_lanes,
+                     "body_pass_ms_for_4_8_16_lanes": [float(x) for x in tuned_ms]},
         "network_roofline": mlp,
         "cpu_baseline": cb,
         "e2e": {"value": value_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,

@@ -205,6 +205,19 @@ nsn_status nsn_get_system(nsn_ctx *ctx, double *b, double *diag, double *hvec, d
  * launches every iteration up to the caps, finished ones returning at once. */
 nsn_status nsn_last_launch_count(nsn_ctx *ctx, int32_t *kernels_per_step);
 
+/* The body pass's segment tile chosen for this scene: *body_lanes lanes per
+ * body (4, 8 or 16).  Scenes of 100,000 rows or more are tuned when the layout
+ * is built: the operator's body pass is timed with each tile on the scene
+ * itself, and another tile replaces 8 only if it is at least 10% faster (8
+ * lanes also give finer skip blocks of bodies late in a step); ms3 (may be
+ * NULL) receives the three measured times in ms (zeros when not tuned).
+ * Smaller scenes use 8. */
+nsn_status nsn_tuning(nsn_ctx *ctx, int32_t *body_lanes, float *ms3);
+/* Forces the body pass's lanes per body (4, 8 or 16; 0 = tuned as above) from
+ * the next use of the context on (the device layout is rebuilt, the state
+ * kept).  Invalid values: NSN_ERR_INVALID_ARG. */
+nsn_status nsn_set_body_lanes(nsn_ctx *ctx, int32_t lanes);
+
 /* Times the two kernels of one Schur operator apply (Eq. schur_system,
  * matrix-free: body-segment pass J^T z, H~^-1, J y per entry; row pass with
  * C z + eps z and the fused CR dot products) on the context stream with CUDA

@@ -22,7 +22,6 @@ using namespace nsn;
 namespace {
 
 constexpr int kMaxBlocks = 152 * 8;  // 152 SMs x 8 resident 256-thread blocks
-constexpr int kGroup = 8;            // lanes per body segment in the body pass
 
 struct HostScene {
   std::vector<int32_t> kind;
@@ -95,6 +94,8 @@ struct nsn_ctx {
   int launches_per_step = 0;  // kernels executed in the last step
   struct Segments { int prefix = 0, head = 0, cr = 0, tail = 0, suffix = 0; } seg;  // kernels per graph segment
   int last_newton_n = 0;     // Newton loop bodies executed in the last step
+  float tune_ms[3] = {0.f, 0.f, 0.f};  // body-pass times measured by the tuner for 4, 8, 16 lanes
+  int forced_lanes = 0;      // nsn_set_body_lanes (0: tuned)
   bool linearized = false;
   int lin_buf = 0;           // entry buffer written by the kept linearisation
   int kept_buf = -1;         // entry buffer of the system kept by the last step / linearisation
@@ -344,11 +345,11 @@ void carve(Arena &A, Dev<T> &D, const Layout &L, int nb) {
   D.isl.alpha_f = A.take<float>(ni); D.isl.beta_f = A.take<float>(ni);
   D.isl.stop = A.take<int>(ni); D.isl.crdone = A.take<int>(ni);
   D.fl_row = A.take<unsigned char>(size_t(L.R) / BLOCK + 1);
-  D.fl_br = A.take<unsigned char>(size_t(L.nr) / 32 + 1);
-  D.fl_bp = A.take<unsigned char>(size_t(L.np) / 32 + 1);
+  D.fl_br = A.take<unsigned char>(size_t(L.nr) / (BLOCK / 16) + 1);
+  D.fl_bp = A.take<unsigned char>(size_t(L.np) / (BLOCK / 16) + 1);
   D.list_row = A.take<int>(size_t(L.R) / BLOCK + 1);
-  D.list_br = A.take<int>(size_t(L.nr) / 32 + 1);
-  D.list_bp = A.take<int>(size_t(L.np) / 32 + 1);
+  D.list_br = A.take<int>(size_t(L.nr) / (BLOCK / 16) + 1);
+  D.list_bp = A.take<int>(size_t(L.np) / (BLOCK / 16) + 1);
   D.list_isl = A.take<int>(ni);
   (void)nb;
 }
@@ -376,12 +377,16 @@ void fill_sizes(Dev<T> &D, const Layout &L, const nsn_config &cfg) {
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BLOCK, 0) != cudaSuccess || per_sm < 1) per_sm = 8;
     return (long long)nsm * per_sm;
   };
-  const long long cap_body = wave(reinterpret_cast<const void *>(&k_body_pass<T, kGroup, BM_APPLY>));
+  if (D.G != 4 && D.G != 16) D.G = 8;
+  const long long cap_body =
+      D.G == 4 ? wave(reinterpret_cast<const void *>(&k_body_pass<T, 4, BM_APPLY>))
+               : (D.G == 16 ? wave(reinterpret_cast<const void *>(&k_body_pass<T, 16, BM_APPLY>))
+                            : wave(reinterpret_cast<const void *>(&k_body_pass<T, 8, BM_APPLY>)));
   const long long cap_row = cfg.island_stop ? wave(reinterpret_cast<const void *>(&k_row_pass_isl<T, RM_APPLY>))
                                             : wave(reinterpret_cast<const void *>(&k_row_pass<T, RM_APPLY>));
   auto capped = [](long long n, long long cap) { return int(std::max(1LL, std::min({n, cap, (long long)kMaxBlocks}))); };
-  D.nblk_body_r = L.nr ? capped(cdiv((long long)L.nr * kGroup, BLOCK), cap_body) : 0;
-  D.nblk_body_p = L.np ? capped(cdiv((long long)L.np * kGroup, BLOCK), cap_body) : 0;
+  D.nblk_body_r = L.nr ? capped(cdiv((long long)L.nr * D.G, BLOCK), cap_body) : 0;
+  D.nblk_body_p = L.np ? capped(cdiv((long long)L.np * D.G, BLOCK), cap_body) : 0;
   D.nblk_row_pair = L.Rpair ? capped(cdiv(L.Rpair, BLOCK), cap_row) : 0;
   D.nblk_row_tet = L.nt ? capped(cdiv(L.nt, BLOCK), cap_row) : 0;
   D.nblk_upd = clampb(cdiv(std::max(L.R, 1), BLOCK));
@@ -510,8 +515,8 @@ nsn_status upload(nsn_ctx *c, Dev<T> &D) {
     CUDA_TRY(c, cudaMemsetAsync(D.isl.stop, 0xff, sizeof(int) * ni, st));
     CUDA_TRY(c, cudaMemsetAsync(D.isl.crdone, 0, sizeof(int) * ni, st));
     CUDA_TRY(c, cudaMemsetAsync(D.fl_row, 1, size_t(L.R) / BLOCK + 1, st));
-    CUDA_TRY(c, cudaMemsetAsync(D.fl_br, 1, size_t(L.nr) / 32 + 1, st));
-    CUDA_TRY(c, cudaMemsetAsync(D.fl_bp, 1, size_t(L.np) / 32 + 1, st));
+    CUDA_TRY(c, cudaMemsetAsync(D.fl_br, 1, size_t(L.nr) / (BLOCK / 16) + 1, st));
+    CUDA_TRY(c, cudaMemsetAsync(D.fl_bp, 1, size_t(L.np) / (BLOCK / 16) + 1, st));
   }
   for (int b2 = 0; b2 < 2; b2++)
     for (int k = 0; k < 3; k++)
@@ -603,10 +608,16 @@ struct Launcher {
   void body(int mode, const T *in, int buf, int it, int force) {
     int nb = D.nblk_body_r + D.nblk_body_p;
     if (!nb) return;
-    if (mode == BM_RESIDUAL) k_body_pass<T, kGroup, BM_RESIDUAL><<<nb, BLOCK, 0, st>>>(D, in, buf, it, force);
-    else if (mode == BM_APPLY) k_body_pass<T, kGroup, BM_APPLY><<<nb, BLOCK, 0, st>>>(D, in, buf, it, force);
-    else k_body_pass<T, kGroup, BM_UPDATE><<<nb, BLOCK, 0, st>>>(D, in, buf, it, force);
+    if (D.G == 4) body_g<4>(mode, nb, in, buf, it, force);
+    else if (D.G == 16) body_g<16>(mode, nb, in, buf, it, force);
+    else body_g<8>(mode, nb, in, buf, it, force);
     count++;
+  }
+  template <int G>
+  void body_g(int mode, int nb, const T *in, int buf, int it, int force) {
+    if (mode == BM_RESIDUAL) k_body_pass<T, G, BM_RESIDUAL><<<nb, BLOCK, 0, st>>>(D, in, buf, it, force);
+    else if (mode == BM_APPLY) k_body_pass<T, G, BM_APPLY><<<nb, BLOCK, 0, st>>>(D, in, buf, it, force);
+    else k_body_pass<T, G, BM_UPDATE><<<nb, BLOCK, 0, st>>>(D, in, buf, it, force);
   }
   void rows(int mode, int force) {
     int nb = D.nblk_row_pair + D.nblk_row_tet;
@@ -725,7 +736,8 @@ struct Launcher {
   void newton_head(int M) {
     linearize_at(IT_DEV);
     if (D.isl_on) {
-      const int nblk = std::max({cdiv(std::max(D.R, 1), BLOCK), cdiv(D.nr, 32), cdiv(D.np, 32), 1});
+      const int gb = BLOCK / D.G;
+      const int nblk = std::max({cdiv(std::max(D.R, 1), BLOCK), cdiv(D.nr, gb), cdiv(D.np, gb), 1});
       k_block_flags<T><<<nblk, BLOCK, 0, st>>>(D);
       k_block_lists<T><<<1, 1024, 0, st>>>(D, 0);
       count += 2;
@@ -764,8 +776,8 @@ template <typename T>
 void blocks_all_on(Dev<T> &D, cudaStream_t st) {
   if (!D.isl_on) return;
   cudaMemsetAsync(D.fl_row, 1, size_t(D.R) / BLOCK + 1, st);
-  cudaMemsetAsync(D.fl_br, 1, size_t(D.nr) / 32 + 1, st);
-  cudaMemsetAsync(D.fl_bp, 1, size_t(D.np) / 32 + 1, st);
+  cudaMemsetAsync(D.fl_br, 1, size_t(D.nr) / (BLOCK / 16) + 1, st);
+  cudaMemsetAsync(D.fl_bp, 1, size_t(D.np) / (BLOCK / 16) + 1, st);
   k_block_lists<T><<<1, 1024, 0, st>>>(D, 1);
 }
 
@@ -777,6 +789,58 @@ template <>
 Dev<double> &dev<double>(nsn_ctx *c) { return c->d64; }
 
 nsn_status ensure_built(nsn_ctx *c);
+
+// Autotuner of the body pass's segment tile: on large scenes, time the
+// operator's body pass (every body active) with 4, 8 and 16 lanes per body on
+// this layout.  8 is kept unless another tile is at least 10% faster: the tile
+// also sets the granularity of the skip blocks of bodies (BLOCK / G), and late
+// in a step, when few islands still iterate, 8 lanes (32-body blocks) skip
+// finer than 4 (64-body blocks).  Small scenes take 8 (launch-bound).
+template <typename T>
+nsn_status tune_body(nsn_ctx *c, Dev<T> &D) {
+  const Layout &L = c->L;
+  cudaStream_t st = c->stream;
+  c->tune_ms[0] = c->tune_ms[1] = c->tune_ms[2] = 0.f;
+  if (c->forced_lanes) {
+    D.G = c->forced_lanes;
+    fill_sizes(D, L, c->cfg);
+    return NSN_OK;
+  }
+  if (L.R < 100000 || (L.nr + L.np) == 0) {
+    D.G = 8;
+    fill_sizes(D, L, c->cfg);
+    return NSN_OK;
+  }
+  if (L.R) CUDA_TRY(c, cudaMemsetAsync(D.z, 0, sizeof(T) * L.R, st));
+  cudaEvent_t e0, e1;
+  CUDA_TRY(c, cudaEventCreate(&e0));
+  CUDA_TRY(c, cudaEventCreate(&e1));
+  const int cand[3] = {4, 8, 16};
+  int best = 8;
+  float best_ms = 1e30f;
+  for (int k = 0; k < 3; k++) {
+    D.G = cand[k];
+    fill_sizes(D, L, c->cfg);
+    Launcher<T> Lr{c, D, st};
+    Lr.body(BM_APPLY, D.z, 0, 0, 1);  // warm-up
+    CUDA_TRY(c, cudaEventRecord(e0, st));
+    for (int r = 0; r < 3; r++) Lr.body(BM_APPLY, D.z, 0, 0, 1);
+    CUDA_TRY(c, cudaEventRecord(e1, st));
+    CUDA_TRY(c, cudaEventSynchronize(e1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    c->tune_ms[k] = ms / 3;
+  }
+  best_ms = c->tune_ms[1];
+  for (int k : {0, 2})
+    if (c->tune_ms[k] < 0.9f * best_ms) { best_ms = c->tune_ms[k]; best = cand[k]; }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  D.G = best;
+  fill_sizes(D, L, c->cfg);
+  CUDA_TRY(c, cudaGetLastError());
+  return NSN_OK;
+}
 
 template <typename T>
 nsn_status build_device(nsn_ctx *c) {
@@ -802,6 +866,7 @@ nsn_status build_device(nsn_ctx *c) {
   c->d_backup = reinterpret_cast<float *>(A.take<T>(13 * size_t(nb + 1)));
   nsn_status s = upload<T>(c, D);
   if (s != NSN_OK) return s;
+  if ((s = tune_body<T>(c, D)) != NSN_OK) return s;
   CUDA_TRY(c, cudaMemcpyAsync(c->d_bmap, L.bmap.data(), sizeof(int) * std::max(nb, 0), cudaMemcpyHostToDevice, c->stream));
   // initial state
   const HostScene &S = c->scene;
@@ -1182,8 +1247,8 @@ nsn_status do_time_operator(nsn_ctx *c, int iters, float *ms_body, float *ms_row
   if (D.isl_on && D.ni) {
     CUDA_TRY(c, cudaMemsetAsync(D.isl.crdone, 0, sizeof(int) * D.ni, st));
     CUDA_TRY(c, cudaMemsetAsync(D.fl_row, 1, size_t(D.R) / BLOCK + 1, st));
-    CUDA_TRY(c, cudaMemsetAsync(D.fl_br, 1, size_t(D.nr) / 32 + 1, st));
-    CUDA_TRY(c, cudaMemsetAsync(D.fl_bp, 1, size_t(D.np) / 32 + 1, st));
+    CUDA_TRY(c, cudaMemsetAsync(D.fl_br, 1, size_t(D.nr) / (BLOCK / 16) + 1, st));
+    CUDA_TRY(c, cudaMemsetAsync(D.fl_bp, 1, size_t(D.np) / (BLOCK / 16) + 1, st));
   }
   Launcher<T> Lr{c, D, st};
   double tb = 0.0, tr = 0.0;
@@ -1824,6 +1889,24 @@ nsn_status nsn_contact_features(nsn_ctx *c, float *X, float *Ytarget) {
   return c->cfg.precision == NSN_FP64 ? do_features<double>(c, X, Ytarget) : do_features<float>(c, X, Ytarget);
 }
 
+nsn_status nsn_tuning(nsn_ctx *c, int32_t *body_lanes, float *ms3) {
+  if (!c) return NSN_ERR_INVALID_ARG;
+  nsn_status s = ensure_built(c);
+  if (s != NSN_OK) return s;
+  if (body_lanes) *body_lanes = c->cfg.precision == NSN_FP64 ? c->d64.G : c->d32.G;
+  if (ms3) for (int k = 0; k < 3; k++) ms3[k] = c->tune_ms[k];
+  return NSN_OK;
+}
+
+nsn_status nsn_set_body_lanes(nsn_ctx *c, int32_t lanes) {
+  if (!c || (lanes != 0 && lanes != 4 && lanes != 8 && lanes != 16)) return NSN_ERR_INVALID_ARG;
+  if (lanes != c->forced_lanes) {
+    c->forced_lanes = lanes;
+    c->dirty = true;   // rebuilt (state kept) before the next use
+  }
+  return NSN_OK;
+}
+
 nsn_status nsn_last_launch_count(nsn_ctx *c, int32_t *kernels_per_step) {
   if (!c || !kernels_per_step) return NSN_ERR_INVALID_ARG;
   *kernels_per_step = c->launches_per_step;
@@ -1928,7 +2011,11 @@ extern "C" nsn_status nsn_apply_operator_noalloc(nsn_ctx *c, const float *x, flo
   CUDA_TRY(c, cudaMemsetAsync(np->t, 0, sizeof(float) * nslots, st));
   k_permute_rows<<<cdiv(L.R, 256), 256, 0, st>>>(np->x, x, D.row_abi_dev, L.R, 0);
   const int nb = D.nblk_body_r + D.nblk_body_p, nrw = D.nblk_row_pair + D.nblk_row_tet;
-  if (nb) k_body_pass<float, kGroup, BM_APPLY><<<nb, BLOCK, 0, st>>>(D, np->x, c->kept_buf, 0, 1);
+  if (nb) {
+    if (D.G == 4) k_body_pass<float, 4, BM_APPLY><<<nb, BLOCK, 0, st>>>(D, np->x, c->kept_buf, 0, 1);
+    else if (D.G == 16) k_body_pass<float, 16, BM_APPLY><<<nb, BLOCK, 0, st>>>(D, np->x, c->kept_buf, 0, 1);
+    else k_body_pass<float, 8, BM_APPLY><<<nb, BLOCK, 0, st>>>(D, np->x, c->kept_buf, 0, 1);
+  }
   k_row_pass<float, RM_APPLY><<<nrw, BLOCK, 0, st>>>(D, 1);
   k_permute_rows<<<cdiv(L.R, 256), 256, 0, st>>>(y, np->y, D.row_abi_dev, L.R, 1);
   CUDA_TRY(c, cudaGetLastError());

@@ -149,6 +149,7 @@ struct Dev {
   typename RedT<T>::type *part_body;   // one per body-pass block
   typename RedT<T>::type *part_row;    // NPART per row-pass block
   int nblk_body_r, nblk_body_p, nblk_row_pair, nblk_row_tet, nblk_upd;
+  int G;             // lanes per body segment in the body pass (4, 8 or 16; tuned per scene)
   Scalars *sc;
   Flags *fl;
   // islands
@@ -161,7 +162,7 @@ struct Dev {
                      // features and predictions are exchanged in ABI order
   int *row_abi_dev;  // ABI index of each (island-ordered) row
   IslState isl;
-  // island mode: per block of 256 consecutive rows / 32 consecutive bodies, 1
+  // island mode: per block of 256 consecutive rows / BLOCK/G consecutive bodies, 1
   // if it holds an island that has not stopped (set each Newton iteration by
   // k_block_flags; the CR-loop kernels skip blocks whose flag is 0)
   unsigned char *fl_row, *fl_br, *fl_bp;
@@ -1474,28 +1475,22 @@ __global__ void k_merit_isl(Dev<T> D, int n, int force) {
 }
 
 // Island mode, once per Newton iteration after k_merit_isl: block flags for
-// the CR loop (see Dev::fl_row).  Block j: rows [256 j, 256 j + 256) with its
-// 256 threads; warp 0: rigid bodies [32 j, 32 j + 32); warp 1: particles.
+// the CR loop (see Dev::fl_row).  Block j: rows [256 j, 256 j + 256); rigid
+// bodies and particles [gb j, gb j + gb), gb = BLOCK / G (the body pass's
+// bodies per block iteration).
 template <typename T>
 __global__ void __launch_bounds__(BLOCK) k_block_flags(Dev<T> D) {
   if (D.fl->newton_stop) return;
-  const int j = blockIdx.x;
-  const int r = j * BLOCK + threadIdx.x;
-  const bool live = r < D.R && D.isl.stop[D.risl[r]] < 0;
-  const int any = __syncthreads_or(live);
-  if (threadIdx.x == 0 && j * BLOCK < D.R) D.fl_row[j] = any ? 1 : 0;
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (w == 0 && j * 32 < D.nr) {
-    const int b = j * 32 + lane;
-    const bool lb = b < D.nr && D.isl.stop[D.bisl_r[b]] < 0;
-    const unsigned m = __ballot_sync(0xffffffffu, lb);
-    if (lane == 0) D.fl_br[j] = m ? 1 : 0;
-  }
-  if (w == 1 && j * 32 < D.np) {
-    const int b = j * 32 + lane;
-    const bool lb = b < D.np && D.isl.stop[D.bisl_p[b]] < 0;
-    const unsigned m = __ballot_sync(0xffffffffu, lb);
-    if (lane == 0) D.fl_bp[j] = m ? 1 : 0;
+  const int j = blockIdx.x, t = threadIdx.x, gb = BLOCK / D.G;
+  const int r = j * BLOCK + t;
+  const int any_r = __syncthreads_or(r < D.R && D.isl.stop[D.risl[r]] < 0);
+  const int br = j * gb + t;
+  const int any_b = __syncthreads_or(t < gb && br < D.nr && D.isl.stop[D.bisl_r[br]] < 0);
+  const int any_p = __syncthreads_or(t < gb && br < D.np && D.isl.stop[D.bisl_p[br]] < 0);
+  if (t == 0) {
+    if (j * BLOCK < D.R) D.fl_row[j] = any_r ? 1 : 0;
+    if (j * gb < D.nr) D.fl_br[j] = any_b ? 1 : 0;
+    if (j * gb < D.np) D.fl_bp[j] = any_p ? 1 : 0;
   }
 }
 
@@ -1535,8 +1530,9 @@ template <typename T>
 __global__ void __launch_bounds__(1024) k_block_lists(Dev<T> D, int all_islands) {
   if (!all_islands && D.fl->newton_stop) return;
   compact_list((D.R + BLOCK - 1) / BLOCK, flag_u8, D.fl_row, D.list_row, &D.fl->n_list_row);
-  compact_list((D.nr + 31) / 32, flag_u8, D.fl_br, D.list_br, &D.fl->n_list_br);
-  compact_list((D.np + 31) / 32, flag_u8, D.fl_bp, D.list_bp, &D.fl->n_list_bp);
+  const int gb = BLOCK / D.G;
+  compact_list((D.nr + gb - 1) / gb, flag_u8, D.fl_br, D.list_br, &D.fl->n_list_br);
+  compact_list((D.np + gb - 1) / gb, flag_u8, D.fl_bp, D.list_bp, &D.fl->n_list_bp);
   // in a step the island list comes from k_merit_isl; outside, every island
   if (all_islands) compact_list(D.ni, flag_all, D.isl.stop, D.list_isl, &D.fl->n_list_isl);
 }

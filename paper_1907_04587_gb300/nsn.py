@@ -110,6 +110,8 @@ def lib():
         "nsn_island_stop_device": (C.c_int, [_vp, C.POINTER(_vp)]),
         "nsn_island_stop_copy": (C.c_int, [_vp, _vp]),
         "nsn_clear_warm_start": (C.c_int, [_vp]),
+        "nsn_tuning": (C.c_int, [_vp, _ip, _fp]),
+        "nsn_set_body_lanes": (C.c_int, [_vp, C.c_int32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -479,6 +481,16 @@ class Solver:
 
     def warm_stats(self):
         return nsn_get_warm_stats(self.ctx)
+
+    def tuning(self):
+        """(lanes per body in the body pass, measured times of 4 / 8 / 16 lanes in ms)."""
+        g = C.c_int32()
+        ms = np.zeros(3, np.float32)
+        _check(self.ctx, lib().nsn_tuning(self.ctx, C.byref(g), _p(ms)), "nsn_tuning")
+        return g.value, ms
+
+    def set_body_lanes(self, lanes):
+        _check(self.ctx, lib().nsn_set_body_lanes(self.ctx, lanes), "nsn_set_body_lanes")
 
     def clear_warm_start(self):
         _check(self.ctx, lib().nsn_clear_warm_start(self.ctx), "nsn_clear_warm_start")

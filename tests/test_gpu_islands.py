@@ -174,3 +174,32 @@ def test_island_stop_device_copy_and_clear_warm_start(orc):
     rg = g.step()
     assert rg["newton_done"] == rz["newton_done"]
     assert np.array_equal(g.island_stats()["stopped_at"], z.island_stats()["stopped_at"])
+
+
+def test_body_pass_tiles_agree(orc):
+    """The body pass with 4, 8 and 16 lanes per body gives the same step and
+    matches the oracle (FP64 build; only the order of the per-body shuffle sums
+    differs).  Global mode: in island mode, islands that never converge amplify
+    any change of summation order within a step."""
+    s = scenes.batched_envs(seed=4, n_envs=6)
+    p = dict(newton_iters=5, cr_iters=25)
+    o = orc.Oracle(s, **p)
+    o.step()
+    for lanes in (4, 8, 16):
+        g = nsn.Solver(s, precision=nsn.NSN_FP64, **p)
+        g.set_body_lanes(lanes)
+        g.step()
+        assert g.tuning()[0] == lanes
+        assert vel_error(o.get_state(), g.get_state_f64(), s) < 1e-7
+
+
+def test_tuner_picks_the_fastest_tile():
+    s = scenes.batched_envs(seed=0, n_envs=256)       # > 100k rows: tuned at build
+    g = nsn.Solver(s, **PRM)
+    lanes, ms = g.tuning()
+    print("body pass ms for 4 / 8 / 16 lanes:", ms, "chosen", lanes)
+    assert lanes in (4, 8, 16) and np.all(ms > 0)
+    # 8 unless another tile is at least 10% faster
+    other = int(np.argmin([ms[0], np.inf, ms[2]]))
+    expect = (4, 8, 16)[other] if min(ms[0], ms[2]) < 0.9 * ms[1] else 8
+    assert lanes == expect
