@@ -64,6 +64,8 @@ WORKLOADS = {
                         desc="7-link revolute chain on a 24^3-hex stable Neo-Hookean block (69,120 tets)"),
     "cube_stack": dict(make=lambda seed: scenes.cube_stack(seed=seed), newton=30, cr=20,
                        desc="4 unit cubes stacked on a plane (16 contacts)"),
+    "mixed_bin": dict(make=lambda seed: scenes.mixed_bin(seed=seed), newton=30, cr=50,
+                      desc="2000 rigid boxes + 8 stable Neo-Hookean balls (36,480 tets) in a bin, one environment"),
 }
 SAMPLE_ENVS = 64
 WEIGHTS = os.path.join(ROOT, "paper_1907_04587_gb300", "weights", "warm_start_mlp.npy")

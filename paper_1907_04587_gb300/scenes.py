@@ -404,3 +404,88 @@ def batched_envs(seed=0, n_envs=4096, links=(3, 20), boxes=(0, 64), box_edge=(0.
     s = dict(kind=kind, pos=pos, quat=quat, vel=vel, omega=omega, mass=mass, inertia=inertia, env=env)
     s.update(joints); s.update(contacts); s.update(_empty_tets())
     return finalize(s)
+
+
+# --------------------------------------------------------------------------------------
+# Workload 5: large mixed scene, rigid boxes and Neo-Hookean spheres in a bin
+
+def sphere_mesh(radius, res, rng, rest_jitter=0.01):
+    """Tet mesh of a ball: the hexes of a res^3 grid over [-radius, radius]^3
+    whose centres lie inside the ball, 5 tets each (hex_tets); vertices
+    renumbered, rest shape jittered by +-rest_jitter of the spacing."""
+    n = res
+    sp = 2.0 * radius / n
+    g = np.arange(n + 1) * sp - radius
+    kk, jj, ii = np.meshgrid(np.arange(n + 1), np.arange(n + 1), np.arange(n + 1), indexing="ij")
+    verts = np.stack([g[ii.ravel()], g[jj.ravel()], g[kk.ravel()]], 1)
+    c = (np.arange(n) + 0.5) * sp - radius
+    ck, cj, ci = np.meshgrid(c, c, c, indexing="ij")
+    inside = (ci ** 2 + cj ** 2 + ck ** 2 <= radius ** 2).ravel()       # hex order matches hex_tets (i fastest)
+    tets = hex_tets(n).reshape(-1, 5, 4)[inside].reshape(-1, 4)
+    used = np.unique(tets)
+    remap = -np.ones(len(verts), np.int64)
+    remap[used] = np.arange(len(used))
+    verts = verts[used]
+    tets = remap[tets].astype(np.int32)
+    rest = verts + rng.uniform(-rest_jitter, rest_jitter, verts.shape) * sp
+    return verts, rest, tets
+
+
+def mixed_bin(seed=0, n_boxes=2000, n_spheres=8, sphere_radius=0.3, sphere_res=12, box_edge=(0.05, 0.3),
+              E=5e4, nu=0.4, density=1000.0, mu=0.5, margin=0.01, cell=0.35):
+    """Config: one environment, a bin (floor z = 0, walls x = 0 and y = 0 used)
+    holding ``n_boxes`` rigid boxes (edge uniform in ``box_edge``) stacked in
+    columns of up to four on a grid of ``cell`` m cells, random yaw, and
+    ``n_spheres`` stable Neo-Hookean balls (``sphere_res``^3-hex voxel meshes,
+    ~4,500 tets each at res 12) resting on the floor against the x = 0 wall.
+    Contacts: 4 bottom corners per box vs the floor or the box below; ball
+    vertices within ``margin`` of the floor or the wall vs that plane."""
+    rng = np.random.default_rng(seed)
+    n_cols = int(np.ceil(n_boxes / 4))
+    side = int(np.ceil(np.sqrt(n_cols)))
+    x_off = 2 * sphere_radius + 0.1                   # the balls' strip along the x = 0 wall
+    B = SceneBuilder()
+    edges = rng.uniform(box_edge[0], box_edge[1], n_boxes)
+    col_top = {}
+    for k in range(n_boxes):
+        col = k % n_cols
+        cx = x_off + (col % side + 0.5) * cell + rng.uniform(-0.01, 0.01)
+        cy = (col // side + 0.5) * cell + rng.uniform(-0.01, 0.01)
+        e = edges[k]
+        below = col_top.get(col)
+        z0 = 0.0 if below is None else below[1]
+        yaw = rng.uniform(-0.3, 0.3)
+        m = density * e ** 3
+        q = quat_yaw(yaw)
+        bid = B.add_rigid((cx, cy, z0 + e / 2), tuple(q), mass=m, inertia=(m * e * e / 6,) * 3)
+        R = quat_rot(np.asarray(q)[None])[0]
+        for u in np.array([[-1, -1, -1], [1, -1, -1], [1, 1, -1], [-1, 1, -1]], np.float64) * 0.5 * e:
+            w = np.array([cx, cy, z0 + e / 2]) + R @ u
+            if below is None:
+                B.add_contact(bid, -1, u, (w[0], w[1], 0.0), (0, 0, 1), 0.0, mu)
+            else:
+                sb, _, sR, sx, se = below
+                loc = sR.T @ (w - sx)
+                loc[2] = se / 2
+                B.add_contact(bid, sb, u, loc, sR[:, 2], 0.0, mu)
+        col_top[col] = (bid, z0 + e, R, np.array([cx, cy, z0 + e / 2]), e)
+    verts, rest, tets = sphere_mesh(sphere_radius, sphere_res, rng)
+    vol = np.abs(np.einsum("ij,ij->i", np.cross(rest[tets[:, 1]] - rest[tets[:, 0]], rest[tets[:, 2]] - rest[tets[:, 0]]),
+                           rest[tets[:, 3]] - rest[tets[:, 0]])) / 6.0
+    vmass = np.zeros(len(verts))
+    np.add.at(vmass, tets.ravel(), np.repeat(vol * density / 4.0, 4))
+    zmin, xmin = verts[:, 2].min(), verts[:, 0].min()
+    for s_ in range(n_spheres):
+        c = np.array([-xmin, (s_ + 0.5) * (2 * sphere_radius + 0.05), -zmin])
+        first = None
+        for v in range(len(verts)):
+            bid = B.add_particle(tuple(verts[v] + c), mass=vmass[v])
+            first = bid if first is None else first
+            p = verts[v] + c
+            if p[2] <= margin:
+                B.add_contact(bid, -1, (0, 0, 0), (p[0], p[1], 0.0), (0, 0, 1), 0.0, mu)
+            if p[0] <= margin:
+                B.add_contact(bid, -1, (0, 0, 0), (0.0, p[1], p[2]), (1, 0, 0), 0.0, mu)
+        for t in range(len(tets)):
+            B.add_tet(tuple(tets[t] + first), rest[tets[t]], E, nu)
+    return B.build()

@@ -203,3 +203,29 @@ def test_tuner_picks_the_fastest_tile():
     other = int(np.argmin([ms[0], np.inf, ms[2]]))
     expect = (4, 8, 16)[other] if min(ms[0], ms[2]) < 0.9 * ms[1] else 8
     assert lanes == expect
+
+
+def test_mixed_bin_parity(orc):
+    """Config 5 shape (rigid boxes and a stable Neo-Hookean ball in a bin),
+    islands to 1e-6 with the geometric stiffness on.  Box islands: the oracle's
+    stop iterations exactly and velocities to FP64 rounding; the ball's
+    island: the secant of Sec. 8.3 amplifies rounding differences between two
+    FP64 implementations iteration by iteration, so it is compared loosely."""
+    s = scenes.mixed_bin(seed=0, n_boxes=40, n_spheres=1, sphere_res=6)
+    p = dict(newton_iters=30, cr_iters=100, tol_rel=1e-6, island_stop=1, cone_project=1)
+    o = orc.Oracle(s, **p)
+    g = nsn.Solver(s, precision=nsn.NSN_FP64, **p)
+    o.step(); g.step()
+    io, ig = o.island_stats(), g.island_stats()
+    n_o, bi, _ = o.islands()
+    rigid_isl = np.unique(bi[s["kind"] == 0])
+    assert np.array_equal(io["stopped_at"][rigid_isl], ig["stopped_at"][rigid_isl])
+    so, sg = o.get_state(), g.get_state_f64()
+    rig = s["kind"] == 0
+    dv = np.linalg.norm(sg["vel"][rig] - so["vel"][rig]) / (np.linalg.norm(so["vel"][rig]) + H * G)
+    dw = np.linalg.norm(sg["omega"][rig] - so["omega"][rig]) / (np.linalg.norm(so["omega"][rig]) + 1e-3)
+    assert dv < 1e-7 and dw < 1e-6, (dv, dw)
+    par = ~rig
+    dp = np.linalg.norm(sg["vel"][par] - so["vel"][par]) / (np.linalg.norm(so["vel"][par]) + H * G)
+    print("ball velocity difference", dp)
+    assert dp < 1e-3
