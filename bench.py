@@ -17,8 +17,12 @@ trajectory advances from the seeded start state (no reset between steps).
             fallback) and zero; damped update projected onto the friction cone
             (option cone_project)
   arms      the same measurement for: the plain batched method (zero start),
-            the printed update, the previous-step start alone, and the first
-            step after an environment reset with the zero / learned start
+            the printed update, the previous-step start alone, the first step
+            after an environment reset with the zero / learned start, and the
+            ablations of Sec. 7 (min-map NCP; r = h^2 and r = 1 instead of the
+            effective-mass r), each on the first step after a reset with the
+            zero start (compare after_reset_zero): on the advancing trajectory
+            the min-map variant diverges, in the FP64 oracle as well
   e2e       converged env-steps/s through the C ABI with host buffers: host->
             device copy of the state, the step, device->host copy of the state
             (the state makes that round trip every step)
@@ -171,6 +175,38 @@ def operator_traffic(kernel_hash):
     return d.get("dram_bytes_per_apply")
 
 
+# shared-memory and FP32 peaks of the part, from its unit counts and the SM clock:
+# 152 SMs x 128 B of shared memory per clock; 152 x 128 FP32 lanes x 2 flop (FMA)
+SMEM_BYTES_PER_SM_CLK = 128
+FP32_FLOP_PER_SM_CLK = 256
+
+
+def resident_roofline(g, clk):
+    """k_cr_resident timed live at full activity (the first Newton iteration
+    of a zero start: every resident island iterates), with its algorithmic
+    shared-memory bytes and flops per row-, entry- and body-iteration."""
+    info = g.resident_info()
+    if info["islands"] == 0:
+        return None
+    ms, w = g.time_resident(10)
+    Ri, Ei, Bi = w["row_iterations"], w["entry_iterations"], w["body_iterations"]
+    smem = 76 * Ri + 80 * Ei + 60 * Bi
+    flop = 28 * Ri + 24 * Ei + 18 * Bi
+    import torch
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    summ = clk.summary() if clk is not None else None
+    mhz = (summ or {}).get("sm_max_mhz") or 2070.0
+    smem_peak = nsm * SMEM_BYTES_PER_SM_CLK * mhz * 1e6 / 1e9
+    fp32_peak = nsm * FP32_FLOP_PER_SM_CLK * mhz * 1e6 / 1e12
+    ach = smem / (ms * 1e-3) / 1e9
+    return {"bound": "smem", "achieved": ach, "peak": smem_peak, "unit": "GB/s", "frac": ach / smem_peak,
+            "kernel": "k_cr_resident (one thread block per island, all CR iterations of a Newton iteration from shared memory)",
+            "ms": ms, "islands": w["islands"], "row_iterations": Ri, "entry_iterations": Ei, "body_iterations": Bi,
+            "bytes_smem": smem, "flop": flop, "tflops": flop / (ms * 1e-3) / 1e12, "fp32_peak_tflops": fp32_peak,
+            "peak_kind": f"derived: {nsm} SMs x {SMEM_BYTES_PER_SM_CLK} B/clk x {mhz:.0f} MHz",
+            "smem_bytes_per_block": info["smem_bytes"], "grid": info["grid"], "max_island_rows": info["max_rows"]}
+
+
 def kernel_source_hash():
     h = hashlib.sha256()
     for f in ("nsn_kernels.cuh", "nsn_host.cu"):
@@ -245,9 +281,9 @@ def run_reference(args, rank, world):
 EAGER = False   # --eager: launch kernel by kernel instead of the CUDA graph (for profilers)
 
 
-def make_solver(nsn, s, stream, newton, cr, cone, warm=0, params=None):
+def make_solver(nsn, s, stream, newton, cr, cone, warm=0, params=None, ncp=0, rscale=2):
     g = nsn.Solver(s, stream=stream.cuda_stream, newton_iters=newton, cr_iters=cr, tol_rel=TOL, island_stop=1,
-                   cone_project=cone, precision=nsn.NSN_FP32, use_graph=0 if EAGER else 1)
+                   cone_project=cone, precision=nsn.NSN_FP32, use_graph=0 if EAGER else 1, ncp=ncp, rscale=rscale)
     if params is not None:
         nsn.nsn_mlp_set_params(g.ctx, params)
     g.set_warm_start(warm)
@@ -376,6 +412,7 @@ def run_ours(args, rank, world, local_rank):
         # roofline of the CR operator apply, timed live on the solver's stream
         ms_body, ms_row = g.time_operator(20)
         sz = g.sizes()
+        resident = resident_roofline(g, clk)
         tuned_lanes, tuned_ms = g.tuning()
         # the network's forward pass over every contact (BF16 tensor cores), timed live
         mlp = None
@@ -404,18 +441,27 @@ def run_ours(args, rank, world, local_rank):
         # the other arms, same trajectory and accounting
         arms = {}
         if args.arms:
-            for name, cone, wm, reset in (("plain_zero_start", 1, nsn.NSN_WARM_ZERO, False),
-                                          ("as_printed", 0, nsn.NSN_WARM_ZERO, False),
-                                          ("prev_warm_start", 1, nsn.NSN_WARM_PREV, False),
-                                          ("after_reset_zero", 1, nsn.NSN_WARM_ZERO, True),
-                                          ("after_reset_learned", 1, nsn.NSN_WARM_LEARNED, True)):
-                if wm == warm_names[warm] and not reset and cone == 1:
+            # (name, cone projection, warm start, reset every step, NCP function, r strategy)
+            for name, cone, wm, reset, ncp, rs in (("plain_zero_start", 1, nsn.NSN_WARM_ZERO, False, 0, 2),
+                                                   ("as_printed", 0, nsn.NSN_WARM_ZERO, False, 0, 2),
+                                                   ("prev_warm_start", 1, nsn.NSN_WARM_PREV, False, 0, 2),
+                                                   ("after_reset_zero", 1, nsn.NSN_WARM_ZERO, True, 0, 2),
+                                                   ("after_reset_learned", 1, nsn.NSN_WARM_LEARNED, True, 0, 2),
+                                                   ("ablation_min_map", 1, nsn.NSN_WARM_ZERO, True, 1, 2),
+                                                   ("ablation_r_h2", 1, nsn.NSN_WARM_ZERO, True, 0, 1),
+                                                   ("ablation_r_identity", 1, nsn.NSN_WARM_ZERO, True, 0, 0)):
+                if wm == warm_names[warm] and not reset and cone == 1 and ncp == 0 and rs == 2:
                     continue
                 if wm == nsn.NSN_WARM_LEARNED and params is None:
                     arms[name] = {"unavailable": "no trained weights (paper_1907_04587_gb300/weights)"}
                     continue
-                ga = make_solver(nsn, s, stream, newton, cr, cone=cone, warm=wm, params=params)
-                r = measure_arm(nsn, torch, ga, s, st0, stream, args.steps, args.warmup, reset=reset)
+                ga = make_solver(nsn, s, stream, newton, cr, cone=cone, warm=wm, params=params, ncp=ncp, rscale=rs)
+                try:
+                    r = measure_arm(nsn, torch, ga, s, st0, stream, args.steps, args.warmup, reset=reset)
+                except nsn.NSNError as e:      # the method failing on this variant is a result
+                    arms[name] = {"failed": str(e)}
+                    ga.close()
+                    continue
                 if wm != nsn.NSN_WARM_ZERO:
                     r["network_or_warm_rejected_islands_last_step"] = ga.warm_stats()["rejected"]
                 ga.close()
@@ -461,6 +507,7 @@ def run_ours(args, rank, world, local_rank):
                      "bytes_design": design_bytes(sz), "peak_kind": f"{peak_kind} hbm_gbs (burst)",
                      "body_pass_lanes_tuned": tuned_lanes,
                      "body_pass_ms_for_4_8_16_lanes": [float(x) for x in tuned_ms]},
+        "resident_roofline": resident,
         "network_roofline": mlp,
         "cpu_baseline": cb,
         "e2e": {"value": value_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,

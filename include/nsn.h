@@ -94,6 +94,14 @@ typedef struct {
                              system alone) and its own warm-start acceptance; an island
                              that reaches tol_rel keeps its u and lambda, and the step
                              ends when all have stopped or after newton_iters */
+  int32_t cr_resident;    /* island mode, 1 (default): islands of rigid bodies, contacts
+                             and joints with at most res_max_rows rows run their CR of a
+                             Newton iteration inside one thread block from shared memory
+                             (the same recurrence and stop rules; HBM read once per
+                             Newton iteration instead of once per CR iteration); 0: every
+                             island in the streamed CR loop */
+  int32_t res_max_rows;   /* row cap of a resident island and of a group of them
+                             (default 512; <= 0: 512) */
 } nsn_config;
 
 /* Fills the paper's defaults: h = 1/60, g = (0, 0, -9.81), 4 x 20 iterations,
@@ -213,6 +221,25 @@ nsn_status nsn_last_launch_count(nsn_ctx *ctx, int32_t *kernels_per_step);
  * NULL) receives the three measured times in ms (zeros when not tuned).
  * Smaller scenes use 8. */
 nsn_status nsn_tuning(nsn_ctx *ctx, int32_t *body_lanes, float *ms3);
+/* Island-resident CR of this scene (nsn_config.cr_resident): info6[0] islands
+ * solved by k_cr_resident (0 when off: not island mode, cr_resident = 0, or no
+ * eligible island), [1] the groups they are packed into (runs of consecutive
+ * eligible islands, at most 32 islands and res_max_rows rows each, one thread
+ * block per group), [2] rows and [3] Jacobian entries of the largest group
+ * (the shared-memory image's capacity), [4] dynamic shared memory per thread
+ * block in bytes, [5] thread blocks of the persistent grid.  NULL:
+ * NSN_ERR_INVALID_ARG. */
+nsn_status nsn_resident_info(nsn_ctx *ctx, int32_t *info6);
+/* Times k_cr_resident alone: the scene is linearized at the zero start of a
+ * step (lambda = 0; the committed x, q, u are kept, lambda is not), so every
+ * resident island takes part, and the kernel runs `iters` timed launches
+ * (after one untimed) of up to cr_iters CR iterations each, on the context's
+ * stream with CUDA events.  *ms: mean launch time; work4 (may be NULL): the
+ * islands solved per launch and the row-, entry- and body-iterations of one
+ * launch (iterations that applied A, summed over islands).  No resident
+ * islands, or iters < 1: NSN_ERR_INVALID_ARG.  Call nsn_linearize again before
+ * the nsn_apply_operator / nsn_solve_linear family. */
+nsn_status nsn_time_resident(nsn_ctx *ctx, int32_t iters, float *ms, double *work4);
 /* Forces the body pass's lanes per body (4, 8 or 16; 0 = tuned as above) from
  * the next use of the context on (the device layout is rebuilt, the state
  * kept).  Invalid values: NSN_ERR_INVALID_ARG. */

@@ -30,6 +30,8 @@
 #include <string.h>
 
 #define MAXSIDE 4
+/* friction compliance above which the rows take the inactive form */
+#define ORC_W_MAX 1e30
 
 typedef struct {
   int nside;
@@ -669,8 +671,15 @@ static void eval_rows(orc_ctx *c, const double *u, const double *lam) {
     /* active set A of Sec. 3.5 (mu lambda_n > 0), for FB restricted to a
      * positive fixed-point friction magnitude (see orc_fb_friction_active) */
     int active = c->p.ncp == ORC_NCP_MIN ? mu_ln > 0.0 : orc_fb_friction_active(vn, ln_f, mu_ln, rF);
+    double W = 1.0;
     if (active) {
-      double W = (c->p.ncp == ORC_NCP_MIN) ? orc_w_min(vn, ln_f, mu_ln, rF) : orc_w_fb(vn, ln_f, mu_ln, rF);
+      W = (c->p.ncp == ORC_NCP_MIN) ? orc_w_min(vn, ln_f, mu_ln, rF) : orc_w_fb(vn, ln_f, mu_ln, rF);
+      /* Reading: a compliance W above 1e30 (mu lambda_n vanishing while the
+       * contact slides) already drives lambda_f to zero; the rows take the
+       * inactive form, which does the same without the overflowing value. */
+      if (!(W <= ORC_W_MAX)) active = 0;
+    }
+    if (active) {
       for (int k = 0; k < 2; k++) {
         c->cdiag[3 * ci + 1 + k] = W / h;               /* C block W/h (Eq. group_system) */
         c->hvec[3 * ci + 1 + k] = vt[k] + W * lf[k];   /* phi_f, Eq. friction_constraint */

@@ -57,6 +57,17 @@ struct Layout {
   // islands largest first), so that each island's bodies, entries and rows are
   // contiguous.  The ABI keeps the caller's order; these map internal -> ABI.
   std::vector<int> cperm, jperm, tperm, row_abi;
+  // island-resident CR: per island {c0, nc, j0, nj, b0, nb, e0, ne} (internal
+  // order), the eligible islands (rigid bodies, contacts and joints only, at
+  // most res_max_rows rows), and the largest eligible island
+  std::vector<int> ires;
+  std::vector<unsigned char> isres;
+  int n_res = 0, res_rows = 0, res_ent = 0, res_bod = 0;
+  // groups of consecutive eligible islands solved by one thread block
+  // ({c0, nc, j0, nj, b0, nb, e0, ne, first slot in gisl, islands} each)
+  std::vector<int> gres, gisl, grp_of;
+  std::vector<int> isl_order;       // island ids in the internal (rank) order
+  int n_streamed = 0;               // islands with rows that the resident CR does not take
 };
 
 struct MlpState {
@@ -193,6 +204,7 @@ nsn_status build_layout(nsn_ctx *c) {
   {
     std::vector<int> o = order_by(L.ni, [&](int i) { return -isl_size[i]; });
     for (int k = 0; k < L.ni; k++) rank[o[k]] = k;
+    L.isl_order = o;
   }
   // bodies in island order (rigid and particle numbered separately)
   L.bmap.resize(nb);
@@ -285,6 +297,67 @@ nsn_status build_layout(nsn_ctx *c) {
       L.eslot[e] = 2 * L.Rpair + 12 * t + 4 * k + s.slot;
     }
   }
+  // per-island ranges (each island's bodies, contacts and joints are
+  // contiguous in the internal order) and eligibility for the resident CR
+  L.ires.assign(size_t(8) * std::max(L.ni, 1), 0);
+  L.isres.assign(std::max(L.ni, 1), 0);
+  {
+    std::vector<int> npar(L.ni, 0), ntet(L.ni, 0);
+    auto first = [&](int i, int slot, int v) { if (L.ires[8 * i + slot + 1] == 0) L.ires[8 * i + slot] = v; L.ires[8 * i + slot + 1]++; };
+    for (int ci = 0; ci < L.nc; ci++) first(L.risl[3 * ci], 0, ci);
+    for (int j = 0; j < L.nj; j++) first(L.risl[3 * L.nc + 5 * j], 2, j);
+    for (int b = 0; b < L.nr; b++) first(L.bisl_r[b], 4, b);
+    for (int b = 0; b < L.np; b++) npar[L.bisl_p[b]]++;
+    for (int t = 0; t < L.nt; t++) ntet[L.risl[L.Rpair + 3 * t]]++;
+    const int cap = c->cfg.res_max_rows > 0 ? c->cfg.res_max_rows : 512;
+    for (int i = 0; i < L.ni; i++) {
+      int *r = &L.ires[8 * size_t(i)];
+      if (r[5] > 0) { r[6] = L.rseg[r[4]]; r[7] = L.rseg[r[4] + r[5]] - r[6]; }
+      const int rows = 3 * r[1] + 5 * r[3];
+      if (!c->cfg.cr_resident || npar[i] || ntet[i] || r[5] == 0 || rows == 0 || rows > cap) {
+        if (rows > 0 || ntet[i]) L.n_streamed++;
+        continue;
+      }
+      L.isres[i] = 1;
+      L.n_res++;
+    }
+    // groups: runs of consecutive eligible islands (in the internal order, so
+    // a group's contacts, joints, bodies and entries are contiguous), at most
+    // RES_MAXI islands and `cap` rows each
+    L.grp_of.assign(std::max(L.ni, 1), -1);
+    std::vector<int> cur;
+    int cur_rows = 0;
+    auto close = [&]() {
+      if (cur.empty()) return;
+      const int g = int(L.gres.size() / 10);
+      int c0 = -1, nc = 0, j0 = -1, nj = 0, nbg = 0, ent = 0;
+      const int b0 = L.ires[8 * size_t(cur[0]) + 4];
+      for (int i : cur) {
+        const int *r = &L.ires[8 * size_t(i)];
+        if (r[1] > 0 && c0 < 0) c0 = r[0];
+        if (r[3] > 0 && j0 < 0) j0 = r[2];
+        nc += r[1]; nj += r[3]; nbg += r[5]; ent += r[7];
+        L.grp_of[i] = g;
+      }
+      const int e0 = L.rseg[b0];
+      const int rec[10] = {std::max(c0, 0), nc, std::max(j0, 0), nj, b0, nbg, e0, ent, int(L.gisl.size()), int(cur.size())};
+      L.gres.insert(L.gres.end(), rec, rec + 10);
+      L.gisl.insert(L.gisl.end(), cur.begin(), cur.end());
+      L.res_rows = std::max(L.res_rows, 3 * nc + 5 * nj);
+      L.res_ent = std::max(L.res_ent, ent);
+      L.res_bod = std::max(L.res_bod, nbg);
+      cur.clear();
+      cur_rows = 0;
+    };
+    for (int i : L.isl_order) {
+      if (!L.isres[i]) { close(); continue; }
+      const int rows = 3 * L.ires[8 * size_t(i) + 1] + 5 * L.ires[8 * size_t(i) + 3];
+      if (int(cur.size()) == RES_MAXI || cur_rows + rows > cap) close();
+      cur.push_back(i);
+      cur_rows += rows;
+    }
+    close();
+  }
   return NSN_OK;
 }
 
@@ -351,6 +424,14 @@ void carve(Arena &A, Dev<T> &D, const Layout &L, int nb) {
   D.list_br = A.take<int>(size_t(L.nr) / (BLOCK / 16) + 1);
   D.list_bp = A.take<int>(size_t(L.np) / (BLOCK / 16) + 1);
   D.list_isl = A.take<int>(ni);
+  D.ires = A.take<int>(size_t(8) * ni);
+  D.isres = A.take<unsigned char>(ni);
+  const size_t ng = std::max<size_t>(L.gres.size() / 10, 1);
+  D.gres = A.take<int>(10 * ng);
+  D.gisl = A.take<int>(std::max<size_t>(L.gisl.size(), 1));
+  D.grp_of = A.take<int>(ni);
+  D.resact = A.take<unsigned char>(ni);
+  D.gact = A.take<unsigned char>(ng);
   (void)nb;
 }
 
@@ -390,6 +471,28 @@ void fill_sizes(Dev<T> &D, const Layout &L, const nsn_config &cfg) {
   D.nblk_row_pair = L.Rpair ? capped(cdiv(L.Rpair, BLOCK), cap_row) : 0;
   D.nblk_row_tet = L.nt ? capped(cdiv(L.nt, BLOCK), cap_row) : 0;
   D.nblk_upd = clampb(cdiv(std::max(L.R, 1), BLOCK));
+  // island-resident CR: a persistent grid of as many CTAs as fit (shared
+  // memory sized for the largest resident island), at most one per island
+  D.res_on = 0;
+  D.nblk_res = 0;
+  D.res_smem = 0;
+  D.ngroups = int(L.gres.size() / 10);
+  D.streamed = 1;
+  if (cfg.island_stop && L.n_res > 0 && D.ngroups > 0) {
+    D.res_rows = L.res_rows; D.res_ent = L.res_ent; D.res_bod = L.res_bod;
+    const size_t smem = res_smem_bytes<T>(L.res_rows, L.res_ent, L.res_bod);
+    int per_sm = 0;
+    const void *kern = reinterpret_cast<const void *>(&k_cr_resident<T>);
+    if (smem <= 200 * 1024 &&
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) == cudaSuccess &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, RES_THREADS, smem) == cudaSuccess && per_sm > 0) {
+      D.res_on = 1;
+      D.res_smem = int(smem);
+      D.nblk_res = int(std::min<long long>((long long)nsm * per_sm, D.ngroups));
+      D.streamed = L.n_streamed > 0 ? 1 : 0;   // 0: no island needs the streamed CR loop
+    }
+    cudaGetLastError();
+  }
 }
 
 // host-side copies of per-row / per-body static data, converted to T
@@ -506,6 +609,13 @@ nsn_status upload(nsn_ctx *c, Dev<T> &D) {
   CUDA_TRY(c, puti(D.row_abi_dev, L.row_abi));
   CUDA_TRY(c, puti(D.bisl_r, L.bisl_r));
   CUDA_TRY(c, puti(D.bisl_p, L.bisl_p));
+  CUDA_TRY(c, puti(D.ires, L.ires));
+  CUDA_TRY(c, cudaMemcpyAsync(D.isres, L.isres.data(), L.isres.size(), cudaMemcpyHostToDevice, st));
+  CUDA_TRY(c, puti(D.gres, L.gres));
+  CUDA_TRY(c, puti(D.gisl, L.gisl));
+  CUDA_TRY(c, puti(D.grp_of, L.grp_of));
+  CUDA_TRY(c, cudaMemsetAsync(D.resact, 0, size_t(std::max(L.ni, 1)), st));
+  CUDA_TRY(c, cudaMemsetAsync(D.gact, 0, std::max<size_t>(L.gres.size() / 10, 1), st));
   {
     const size_t ni = size_t(std::max(L.ni, 1));
     CUDA_TRY(c, cudaMemsetAsync(D.isl.acc, 0, sizeof(double) * ISL_ACC * ni, st));
@@ -633,7 +743,11 @@ struct Launcher {
   // k_merit launch itself is counted by the callers
   void merit(int n, int force) {
     if (D.isl_on) {
-      if (!force) { k_list_reset<T><<<1, 1, 0, st>>>(D); count++; }   // a Newton iteration: new work list
+      if (!force) {   // a Newton iteration: new work lists
+        k_list_reset<T><<<1, 1, 0, st>>>(D);
+        count++;
+        if (D.res_on) cudaMemsetAsync(D.gact, 0, size_t(D.ngroups), st);
+      }
       k_merit_isl<T><<<cdiv(std::max(D.ni, 1), 256), 256, 0, st>>>(D, n, force);
       count++;
     }
@@ -741,8 +855,12 @@ struct Launcher {
       k_block_flags<T><<<nblk, BLOCK, 0, st>>>(D);
       k_block_lists<T><<<1, 1024, 0, st>>>(D, 0);
       count += 2;
+      if (D.res_on && M > 0) {
+        k_cr_resident<T><<<D.nblk_res, RES_THREADS, D.res_smem, st>>>(D, M);
+        count++;
+      }
     }
-    if (D.R && M > 0) cr_begin(M);
+    if (D.R && M > 0 && D.streamed) cr_begin(M);
   }
   void newton_tail(int N) {
     newton_update(IT_DEV);
@@ -762,7 +880,7 @@ struct Launcher {
     prefix();
     for (int n = 0; n < N; n++) {
       newton_head(M);
-      if (D.R && M > 0)
+      if (D.R && M > 0 && D.streamed)
         for (int k = 0; k < M; k++) cr_body(IT_DEV, M);
       newton_tail(N);
     }
@@ -968,7 +1086,7 @@ nsn_status capture_step(nsn_ctx *c, Dev<T> &D) {
     cudaGraphNode_t nN;
     cudaGraph_t bN = nullptr;
     CUDA_TRY(c, while_node(g, deps, hN, nN, bN));
-    const bool has_cr = D.R && M > 0;
+    const bool has_cr = D.R && M > 0 && D.streamed;
     if (has_cr) CUDA_TRY(c, cudaGraphConditionalHandleCreate(&hC, bN, 0, 0));
     D.hN = hN;
     D.hC = hC;
@@ -1046,7 +1164,7 @@ bool valid_cfg(const nsn_config *cfg) {
          cfg->damping > 0 && cfg->damping <= 1 && cfg->eps >= 0 && cfg->tol_rel >= 0 &&
          (cfg->precision == NSN_FP32 || cfg->precision == NSN_FP64) && (cfg->ncp == 0 || cfg->ncp == 1) &&
          cfg->rscale >= 0 && cfg->rscale <= 2 && (cfg->cone_project == 0 || cfg->cone_project == 1) &&
-         (cfg->island_stop == 0 || cfg->island_stop == 1);
+         (cfg->island_stop == 0 || cfg->island_stop == 1) && (cfg->cr_resident == 0 || cfg->cr_resident == 1);
 }
 
 template <typename T>
@@ -1236,6 +1354,47 @@ nsn_status do_system(nsn_ctx *c, double *b, double *diag, double *hvec, double *
 }  // namespace
 
 namespace {
+// k_cr_resident timed alone at the first Newton iteration of a zero start
+// (every resident island continues), the committed state kept
+template <typename T>
+nsn_status do_time_resident(nsn_ctx *c, int iters, float *ms, double *work4) {
+  Dev<T> &D = dev<T>(c);
+  cudaStream_t st = c->stream;
+  if (!D.res_on) return NSN_ERR_INVALID_ARG;
+  nsn_status s = do_linearize<T>(c, 0);
+  if (s != NSN_OK) return s;
+  cudaEvent_t e[2];
+  for (auto &x : e) CUDA_TRY(c, cudaEventCreate(&x));
+  const int M = c->cfg.cr_iters;
+  Flags *f = D.fl;
+  const size_t wofs = offsetof(Flags, res_rowit);
+  float tot = 0.f;
+  Flags fl{};
+  for (int i = 0; i <= iters; i++) {   // launch 0 is a warm-up
+    CUDA_TRY(c, cudaMemsetAsync(&f->res_next, 0, sizeof(int), st));
+    CUDA_TRY(c, cudaMemsetAsync(&f->cr_res_max, 0, sizeof(int), st));
+    CUDA_TRY(c, cudaMemsetAsync(reinterpret_cast<char *>(f) + wofs, 0, 3 * sizeof(unsigned long long), st));
+    CUDA_TRY(c, cudaEventRecord(e[0], st));
+    k_cr_resident<T><<<D.nblk_res, RES_THREADS, D.res_smem, st>>>(D, M);
+    CUDA_TRY(c, cudaEventRecord(e[1], st));
+    CUDA_TRY(c, cudaMemcpyAsync(&fl, f, sizeof(Flags), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(c, cudaStreamSynchronize(st));
+    float t = 0.f;
+    CUDA_TRY(c, cudaEventElapsedTime(&t, e[0], e[1]));
+    if (i > 0) tot += t;
+  }
+  for (auto &x : e) cudaEventDestroy(x);
+  if (ms) *ms = iters > 0 ? tot / iters : 0.f;
+  if (work4) {
+    work4[0] = double(fl.n_list_res);
+    work4[1] = double(fl.res_rowit);
+    work4[2] = double(fl.res_entit);
+    work4[3] = double(fl.res_bodit);
+  }
+  c->linearized = false;
+  return NSN_OK;
+}
+
 template <typename T>
 nsn_status do_time_operator(nsn_ctx *c, int iters, float *ms_body, float *ms_row) {
   Dev<T> &D = dev<T>(c);
@@ -1446,6 +1605,8 @@ void nsn_default_config(nsn_config *cfg) {
   cfg->use_graph = 1;
   cfg->cone_project = 0;
   cfg->island_stop = 0;
+  cfg->cr_resident = 1;
+  cfg->res_max_rows = 512;
 }
 
 nsn_status nsn_create(const nsn_config *cfg, void *stream, nsn_ctx **out) {
@@ -1896,6 +2057,31 @@ nsn_status nsn_tuning(nsn_ctx *c, int32_t *body_lanes, float *ms3) {
   if (body_lanes) *body_lanes = c->cfg.precision == NSN_FP64 ? c->d64.G : c->d32.G;
   if (ms3) for (int k = 0; k < 3; k++) ms3[k] = c->tune_ms[k];
   return NSN_OK;
+}
+
+nsn_status nsn_resident_info(nsn_ctx *c, int32_t *info6) {
+  if (!c || !info6) return NSN_ERR_INVALID_ARG;
+  nsn_status s = ensure_built(c);
+  if (s != NSN_OK) return s;
+  const bool f64 = c->cfg.precision == NSN_FP64;
+  const int on = f64 ? c->d64.res_on : c->d32.res_on;
+  info6[0] = on ? c->L.n_res : 0;
+  info6[1] = on ? int(c->L.gres.size() / 10) : 0;
+  info6[2] = on ? c->L.res_rows : 0;
+  info6[3] = on ? c->L.res_ent : 0;
+  info6[4] = on ? (f64 ? c->d64.res_smem : c->d32.res_smem) : 0;
+  info6[5] = on ? (f64 ? c->d64.nblk_res : c->d32.nblk_res) : 0;
+  return NSN_OK;
+}
+
+nsn_status nsn_time_resident(nsn_ctx *c, int32_t iters, float *ms, double *work4) {
+  if (!c || iters < 1) return NSN_ERR_INVALID_ARG;
+  nsn_status s = ensure_built(c);
+  if (s != NSN_OK) return s;
+  s = c->cfg.precision == NSN_FP64 ? do_time_resident<double>(c, iters, ms, work4)
+                                   : do_time_resident<float>(c, iters, ms, work4);
+  if (s == NSN_ERR_INVALID_ARG) c->err = "nsn_time_resident: no island-resident CR in this context";
+  return s;
 }
 
 nsn_status nsn_set_body_lanes(nsn_ctx *c, int32_t lanes) {

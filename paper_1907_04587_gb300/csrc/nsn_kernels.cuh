@@ -50,6 +50,12 @@ struct Flags {
   int isl_any;       // island mode: 1 if an island continues (k_merit_isl)
   // island mode: lengths of the work lists of this Newton iteration (k_block_lists)
   int n_list_row, n_list_br, n_list_bp, n_list_isl;
+  // island-resident CR: continuing resident islands, the next list slot to
+  // take, the most CR iterations an island ran in this Newton iteration, and
+  // cr_count at the start of the Newton iteration
+  int n_list_res, res_next, cr_res_max, cr_base;   // n_list_res: resident islands continuing
+  // work done by k_cr_resident (row-, entry- and body-iterations), for its roofline
+  unsigned long long res_rowit, res_entit, res_bodit;
 };
 
 // iteration index / entry buffer taken from Flags::newton_n
@@ -169,6 +175,23 @@ struct Dev {
   // and the same as lists of block indices (ascending), plus the islands that
   // have not stopped: the CR-loop kernels visit only these
   int *list_row, *list_br, *list_bp, *list_isl;
+  // island-resident CR (k_cr_resident): per island {first contact, contacts,
+  // first joint, joints, first rigid body, rigid bodies, first entry, entries}
+  // in the internal order; isres[i] = 1 for the islands it solves; their list
+  // of this Newton iteration; the shared-memory image's capacity
+  int res_on;
+  int *ires;
+  unsigned char *isres;
+  // groups of consecutive resident islands: per group {c0, nc, j0, nj, b0, nb,
+  // e0, ne, first slot in gisl, islands}; gisl: their islands; grp_of: group
+  // of each island (-1: streamed); resact: resident and continuing in this
+  // Newton iteration; gact: group has such an island
+  int ngroups;
+  int *gres, *gisl, *grp_of;
+  unsigned char *resact, *gact;
+  int res_rows, res_ent, res_bod;   // capacity of the shared-memory image (largest group)
+  int nblk_res, res_smem;
+  int streamed;      // 1: some island needs the streamed CR loop (else it is not launched)
   // conditional handles of the captured Newton / CR WHILE nodes (0: none)
   cudaGraphConditionalHandle hN, hC;
 };
@@ -444,6 +467,7 @@ __global__ void k_begin_rigid(Dev<T> D) {
     D.fl->newton_stop = 0; D.fl->cr_stop = 0; D.fl->newton_count = 0; D.fl->cr_count = 0;
     D.fl->newton_n = 0; D.fl->newton_live = 1; D.fl->cr_k = 0; D.fl->cr_live = 0; D.fl->cr_exec = 0;
     D.fl->n_list_isl = 0; D.fl->isl_active = 0;
+    D.fl->n_list_res = 0; D.fl->res_next = 0; D.fl->cr_res_max = 0; D.fl->cr_base = 0;
   }
   if (i >= D.nr) return;
   T q[4], R[9], Ib[3], w[3], Iw[9], Iwi[9];
@@ -710,6 +734,10 @@ __global__ void k_eval_contacts(Dev<T> D, int buf, int force) {
   } else {
     active = w_fb(vn, lfn, mu_ln, rF, W);
   }
+  // a compliance above 1e30 (mu lambda_n vanishing while the contact slides)
+  // already drives lambda_f to zero: the inactive form, without the value that
+  // overflows FP32 (W = inf gives P = 0 and 0/0 in the CR products)
+  if (active && !(W <= T(1e30))) active = false;
   if (active) {
     for (int k = 0; k < 2; k++) {
       write_entry(D, D.re0[row + 1 + k], Da[k], buf);
@@ -1453,13 +1481,20 @@ __global__ void k_merit_isl(Dev<T> D, int n, int force) {
     const int i = i0 + lane;
     const bool cont = i < ni && isl_merit_one(D, i, n, force, final_eval, m2, active);
     if (regular) {
-      const unsigned m = __ballot_sync(0xffffffffu, cont);
+      // continuing islands: resident ones to k_cr_resident (marked CR-done for
+      // the streaming kernels), the others to the streaming CR loop
+      const bool res = cont && D.res_on && D.isres[i];
+      if (i < ni && D.res_on) D.resact[i] = res ? 1 : 0;
+      if (res) { D.isl.crdone[i] = 1; D.gact[D.grp_of[i]] = 1; }
+      const unsigned m = __ballot_sync(0xffffffffu, cont && !res);
       if (m) {
         int base = 0;
         if (lane == 0) base = atomicAdd(&D.fl->n_list_isl, __popc(m));
         base = __shfl_sync(0xffffffffu, base, 0);
-        if (cont) D.list_isl[base + __popc(m & ((1u << lane) - 1u))] = i;
+        if (cont && !res) D.list_isl[base + __popc(m & ((1u << lane) - 1u))] = i;
       }
+      const unsigned mr = __ballot_sync(0xffffffffu, res);
+      if (mr && lane == 0) atomicAdd(&D.fl->n_list_res, __popc(mr));
     }
   }
   __shared__ double sm[32];
@@ -1483,10 +1518,12 @@ __global__ void __launch_bounds__(BLOCK) k_block_flags(Dev<T> D) {
   if (D.fl->newton_stop) return;
   const int j = blockIdx.x, t = threadIdx.x, gb = BLOCK / D.G;
   const int r = j * BLOCK + t;
-  const int any_r = __syncthreads_or(r < D.R && D.isl.stop[D.risl[r]] < 0);
+  // an island takes part if it has not stopped and is not solved by k_cr_resident
+  auto streamed = [&](int is) { return D.isl.stop[is] < 0 && !(D.res_on && D.isres[is]); };
+  const int any_r = __syncthreads_or(r < D.R && streamed(D.risl[r]));
   const int br = j * gb + t;
-  const int any_b = __syncthreads_or(t < gb && br < D.nr && D.isl.stop[D.bisl_r[br]] < 0);
-  const int any_p = __syncthreads_or(t < gb && br < D.np && D.isl.stop[D.bisl_p[br]] < 0);
+  const int any_b = __syncthreads_or(t < gb && br < D.nr && streamed(D.bisl_r[br]));
+  const int any_p = __syncthreads_or(t < gb && br < D.np && streamed(D.bisl_p[br]));
   if (t == 0) {
     if (j * BLOCK < D.R) D.fl_row[j] = any_r ? 1 : 0;
     if (j * gb < D.nr) D.fl_br[j] = any_b ? 1 : 0;
@@ -1752,6 +1789,334 @@ __global__ void __launch_bounds__(BLOCK) k_cr_update_isl(Dev<T> D) {
   }
 }
 
+// ------------------------------------------------------------------------------------
+// Island-resident CR (island mode).  Consecutive islands (in the internal,
+// island-sorted order) that have only rigid bodies, contacts and joints are
+// packed into groups of at most RES_MAXI islands whose rows, Jacobian entries
+// and bodies fit in shared memory.  A thread block takes a group that has a
+// continuing island, loads it once per Newton iteration and runs every CR
+// iteration of this Newton iteration there: the recurrence, FP64 scalars and
+// stop rules of k_cr_scalars_isl / k_cr_update_isl, per island, with A applied
+// in the factored form J H~^-1 J^T z + (C + eps) z (Sec. 8.2, Eq.
+// schur_system).  The vector work is spread over the group's rows, entries
+// and bodies; the per-island sums are taken in a fixed order (one warp per
+// island), and the FP64 scalars of all the group's islands are computed
+// lane-parallel by one warp (lane i: island i), so the narrow FP64 pipe sees
+// one instruction stream per group rather than one per island.  HBM is read
+// once per Newton iteration instead of once per CR iteration, and the CR loop
+// costs no kernel launches.  Only x, the solution, is written back.
+constexpr int RES_THREADS = 256;
+constexpr int RES_NW = RES_THREADS / 32;
+constexpr int RES_G = 8;      // lanes per body in the J^T z gather
+constexpr int RES_MAXI = 32;  // islands per group (one lane each in the scalar warp)
+
+__host__ __device__ inline int res_pad(int n) { return (n + 3) & ~3; }
+
+// shared-memory image of one group: RR rows, RE entries, RB bodies, RES_MAXI islands
+template <typename T>
+struct ResSmem {
+  double *r02f, *eta2, *rho_prev, *res_prev;   // [RES_MAXI] per island
+  T *sums;                                      // [5][RES_MAXI] per-island CR products
+  T *z, *p, *Ap, *x, *P, *dg, *Az;              // [RR]
+  T *prod;                                      // [5][RR] per-row CR products
+  T *J[6];                                      // [RE]
+  T *im, *Si[6], *y[6];                         // [RB]
+  T *alpha, *beta;                              // [RES_MAXI]
+  int *le0, *le1, *lb0, *lb1, *risl;            // [RR] local entries / bodies of the two sides, local island
+  int *erow;                                    // [RE] local row of each entry
+  int *seg, *bisl;                              // [RB + 1] entry segments, [RB] local island of each body
+  int *act, *kdone, *cr0, *ncr, *jr0, *njr, *ient, *ibod;  // [RES_MAXI]
+  int *ctl;                                     // group slot, continue flag
+};
+
+template <typename T>
+__host__ __device__ inline size_t res_smem_bytes(int RR, int RE, int RB) {
+  const size_t rr = res_pad(RR), re = res_pad(RE), rb = res_pad(RB + 1);
+  const size_t nT = 12 * rr + 6 * re + 13 * rb + 7 * RES_MAXI;
+  const size_t nI = 5 * rr + re + 2 * rb + 8 * RES_MAXI + 4;
+  return sizeof(double) * 4 * RES_MAXI + sizeof(T) * nT + sizeof(int) * nI;
+}
+
+template <typename T>
+__device__ inline ResSmem<T> res_carve(unsigned char *base, int RR, int RE, int RB) {
+  ResSmem<T> S;
+  const int rr = res_pad(RR), re = res_pad(RE), rb = res_pad(RB + 1);
+  double *d = reinterpret_cast<double *>(base);
+  S.r02f = d; d += RES_MAXI; S.eta2 = d; d += RES_MAXI; S.rho_prev = d; d += RES_MAXI; S.res_prev = d; d += RES_MAXI;
+  T *t = reinterpret_cast<T *>(d);
+  S.sums = t; t += 5 * RES_MAXI;
+  S.z = t; t += rr; S.p = t; t += rr; S.Ap = t; t += rr; S.x = t; t += rr;
+  S.P = t; t += rr; S.dg = t; t += rr; S.Az = t; t += rr;
+  S.prod = t; t += 5 * rr;
+  for (int k = 0; k < 6; k++) { S.J[k] = t; t += re; }
+  S.im = t; t += rb;
+  for (int k = 0; k < 6; k++) { S.Si[k] = t; t += rb; }
+  for (int k = 0; k < 6; k++) { S.y[k] = t; t += rb; }
+  S.alpha = t; t += RES_MAXI; S.beta = t; t += RES_MAXI;
+  int *q = reinterpret_cast<int *>(t);
+  S.le0 = q; q += rr; S.le1 = q; q += rr; S.lb0 = q; q += rr; S.lb1 = q; q += rr; S.risl = q; q += rr;
+  S.erow = q; q += re;
+  S.seg = q; q += rb; S.bisl = q; q += rb;
+  S.act = q; q += RES_MAXI; S.kdone = q; q += RES_MAXI; S.cr0 = q; q += RES_MAXI; S.ncr = q; q += RES_MAXI;
+  S.jr0 = q; q += RES_MAXI; S.njr = q; q += RES_MAXI; S.ient = q; q += RES_MAXI; S.ibod = q; q += RES_MAXI;
+  S.ctl = q;
+  return S;
+}
+
+// local body of local entry e: the last segment that starts at or before e
+__device__ __forceinline__ int res_body_of(const int *seg, int nb, int e) {
+  int lo = 0, hi = nb - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (seg[mid] <= e) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(RES_THREADS) k_cr_resident(Dev<T> D, int M) {
+  if (D.fl->newton_stop) return;
+  extern __shared__ __align__(16) unsigned char res_raw[];
+  const ResSmem<T> S = res_carve<T>(res_raw, D.res_rows, D.res_ent, D.res_bod);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const T eps = D.epsT;
+  const int gc = 3 * D.nc;
+  for (;;) {
+    if (tid == 0) S.ctl[0] = atomicAdd(&D.fl->res_next, 1);
+    __syncthreads();
+    const int g = S.ctl[0];
+    if (g >= D.ngroups) break;
+    if (!D.gact[g]) { __syncthreads(); continue; }   // no island of the group continues
+    const int *gr = D.gres + 10 * size_t(g);
+    const int c0 = gr[0], ncg = gr[1], j0 = gr[2], njg = gr[3], b0 = gr[4], nb = gr[5], e0 = gr[6], ne = gr[7];
+    const int i0 = gr[8], nisl = gr[9];
+    const int ncr_g = 3 * ncg, nrow = ncr_g + 5 * njg;
+    // islands of the group
+    if (tid < nisl) {
+      const int is = D.gisl[i0 + tid];
+      const int *ir = D.ires + 8 * size_t(is);
+      S.cr0[tid] = 3 * (ir[0] - c0); S.ncr[tid] = 3 * ir[1];
+      S.jr0[tid] = ncr_g + 5 * (ir[2] - j0); S.njr[tid] = 5 * ir[3];
+      S.ient[tid] = ir[7]; S.ibod[tid] = ir[5];
+      const int a = D.resact[is];
+      S.act[tid] = a;
+      S.kdone[tid] = 0;
+      const double r0 = D.isl.res0[is], fl = cr_floor<T>();
+      S.r02f[tid] = fl * fl * r0 * r0;
+      S.eta2[tid] = D.cr_tol ? D.isl.eta[is] * D.isl.eta[is] * r0 * r0 : -1.0;
+      S.res_prev[tid] = r0 == 0.0 ? -1.0 : 0.0;   // r0 == 0: the island stops at once
+      S.rho_prev[tid] = 0.0;
+    }
+    for (int b = tid; b < nb; b += RES_THREADS) {
+      const int gb = b0 + b;
+      S.im[b] = D.rinvm[gb];
+#pragma unroll
+      for (int k = 0; k < 6; k++) S.Si[k][b] = D.rIwi[k][gb];
+      S.seg[b] = D.rseg[gb] - e0;
+    }
+    if (tid == 0) S.seg[nb] = ne;
+    for (int e = tid; e < ne; e += RES_THREADS) {
+      const int ge = e0 + e;
+#pragma unroll
+      for (int k = 0; k < 6; k++) S.J[k][e] = D.ej6[k][ge];
+      const int gw = slot_row(D.eslot[ge], D.Rpair);
+      S.erow[e] = gw < gc ? gw - 3 * c0 : ncr_g + (gw - gc - 5 * j0);
+    }
+    for (int r = tid; r < nrow; r += RES_THREADS) {
+      const int gw = r < ncr_g ? 3 * c0 + r : gc + 5 * j0 + (r - ncr_g);
+      const T zi = D.z[gw];                   // P b, from the rhs pass
+      S.z[r] = zi; S.p[r] = zi; S.Ap[r] = T(0); S.x[r] = T(0);
+      S.P[r] = D.P[gw];
+      S.dg[r] = D.cdiag[gw] + eps;
+      const int a0 = D.re0[gw], a1 = D.re1[gw];
+      S.le0[r] = a0 >= 0 ? a0 - e0 : -1;
+      S.le1[r] = a1 >= 0 ? a1 - e0 : -1;
+    }
+    __syncthreads();
+    // island tags of rows and bodies (one warp per island), sides' bodies
+    for (int li = warp; li < nisl; li += RES_NW) {
+      for (int r = lane; r < S.ncr[li]; r += 32) S.risl[S.cr0[li] + r] = li;
+      for (int r = lane; r < S.njr[li]; r += 32) S.risl[S.jr0[li] + r] = li;
+    }
+    for (int r = tid; r < nrow; r += RES_THREADS) {
+      const int a0 = S.le0[r], a1 = S.le1[r];
+      const int q0 = a0 >= 0 ? res_body_of(S.seg, nb, a0) : 0;
+      const int q1 = a1 >= 0 ? res_body_of(S.seg, nb, a1) : 0;
+      S.lb0[r] = q0; S.lb1[r] = q1;
+    }
+    __syncthreads();
+    for (int r = tid; r < nrow; r += RES_THREADS) {
+      // a body's island is that of any row it touches
+      const int a0 = S.le0[r], a1 = S.le1[r], li = S.risl[r];
+      if (a0 >= 0) S.bisl[S.lb0[r]] = li;
+      if (a1 >= 0) S.bisl[S.lb1[r]] = li;
+    }
+    __syncthreads();
+    int k = 0;
+    for (; k < M; k++) {
+      // y = H~^-1 J^T z for the bodies of continuing islands, RES_G lanes per body
+      for (int bb = 0; bb < nb; bb += RES_THREADS / RES_G) {
+        const int b = bb + tid / RES_G, l = tid % RES_G;
+        const bool on = b < nb && S.act[S.bisl[b]];
+        T s6[6] = {0, 0, 0, 0, 0, 0};
+        if (on) {
+          const int s1 = S.seg[b + 1];
+          for (int e = S.seg[b] + l; e < s1; e += RES_G) {
+            const T zr = S.z[S.erow[e]];
+#pragma unroll
+            for (int q = 0; q < 6; q++) s6[q] += S.J[q][e] * zr;
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < 6; q++) s6[q] = group_sum<RES_G>(s6[q]);
+        if (on && l == 0) {
+          const T im = S.im[b];
+          T Si[6], w[3];
+#pragma unroll
+          for (int q = 0; q < 6; q++) Si[q] = S.Si[q][b];
+          sym3v(Si, s6 + 3, w);
+          S.y[0][b] = s6[0] * im; S.y[1][b] = s6[1] * im; S.y[2][b] = s6[2] * im;
+          S.y[3][b] = w[0]; S.y[4][b] = w[1]; S.y[5][b] = w[2];
+        }
+      }
+      __syncthreads();
+      // Az and the five products of k_row_pass_isl, per row
+      for (int r = tid; r < nrow; r += RES_THREADS) {
+        if (!S.act[S.risl[r]]) continue;
+        T t0 = T(0), t1 = T(0);
+        const int e0l = S.le0[r], e1l = S.le1[r];
+        if (e0l >= 0) {
+          const int b = S.lb0[r];
+#pragma unroll
+          for (int q = 0; q < 6; q++) t0 += S.J[q][e0l] * S.y[q][b];
+        }
+        if (e1l >= 0) {
+          const int b = S.lb1[r];
+#pragma unroll
+          for (int q = 0; q < 6; q++) t1 += S.J[q][e1l] * S.y[q][b];
+        }
+        const T zi = S.z[r], Pi = S.P[r], api = S.Ap[r];
+        const T az = (t0 + t1) + S.dg[r] * zi;
+        S.Az[r] = az;
+        const T paz = Pi * az;
+        const int rr = res_pad(D.res_rows);
+        S.prod[r] = zi * az; S.prod[rr + r] = az * paz; S.prod[2 * rr + r] = paz * api;
+        S.prod[3 * rr + r] = zi * zi / Pi; S.prod[4 * rr + r] = api * Pi * api;
+      }
+      __syncthreads();
+      // per-island sums, one warp per island, fixed order
+      for (int li = warp; li < nisl; li += RES_NW) {
+        if (!S.act[li]) continue;
+        const int rr = res_pad(D.res_rows);
+        T a[5] = {T(0), T(0), T(0), T(0), T(0)};
+        const int c0l = S.cr0[li], c1l = c0l + S.ncr[li], j0l = S.jr0[li], j1l = j0l + S.njr[li];
+        for (int r = c0l + lane; r < c1l; r += 32)
+#pragma unroll
+          for (int q = 0; q < 5; q++) a[q] += S.prod[q * rr + r];
+        for (int r = j0l + lane; r < j1l; r += 32)
+#pragma unroll
+          for (int q = 0; q < 5; q++) a[q] += S.prod[q * rr + r];
+#pragma unroll
+        for (int q = 0; q < 5; q++) {
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) a[q] += __shfl_xor_sync(0xffffffffu, a[q], o);
+        }
+        if (lane == 0) {
+#pragma unroll
+          for (int q = 0; q < 5; q++) S.sums[q * RES_MAXI + li] = a[q];
+        }
+      }
+      __syncthreads();
+      // FP64 scalars and stop tests of every island of the group: lane li
+      if (warp == 0) {
+        bool live = false;
+        if (lane < nisl && S.act[lane]) {
+          const int li = lane;
+          double d[5];
+#pragma unroll
+          for (int q = 0; q < 5; q++) d[q] = double(S.sums[q * RES_MAXI + li]);
+          int st = 0;
+          const double cur2 = d[3] > 0.0 ? d[3] : 0.0;
+          const double rp2 = S.res_prev[li];
+          if (rp2 < 0.0 || cur2 <= S.r02f[li] || (k > 0 && cur2 > rp2)) st = 1;
+          if (cur2 <= S.eta2[li]) st = 1;
+          S.res_prev[li] = cur2;
+          double beta = 0.0, apap = d[1];
+          if (k > 0) {
+            const double rp = S.rho_prev[li];
+            if (!(d[0] > 0.0) || !(rp > 0.0)) st = 1;
+            else {
+              beta = d[0] / rp;
+              apap = d[1] + 2.0 * beta * d[2] + beta * beta * d[4];
+            }
+          }
+          if (!(apap > 0.0)) st = 1;
+          if (st) {
+            S.act[li] = 0;
+            S.kdone[li] = k;
+          } else {
+            S.rho_prev[li] = d[0];
+            const double alpha = d[0] / apap;
+            S.alpha[li] = cr_scalar<T>(alpha, float(alpha));
+            S.beta[li] = cr_scalar<T>(beta, float(beta));
+            live = true;
+          }
+        }
+        const unsigned any = __ballot_sync(0xffffffffu, live);
+        if (lane == 0) S.ctl[1] = any != 0u;
+      }
+      __syncthreads();
+      if (!S.ctl[1]) break;
+      for (int r = tid; r < nrow; r += RES_THREADS) {
+        const int li = S.risl[r];
+        if (!S.act[li]) continue;
+        const T alpha = S.alpha[li], beta = S.beta[li];
+        const T zi = S.z[r];
+        const T pi = k == 0 ? zi : zi + beta * S.p[r];
+        const T api = k == 0 ? S.Az[r] : S.Az[r] + beta * S.Ap[r];
+        S.p[r] = pi;
+        S.Ap[r] = api;
+        S.x[r] += alpha * pi;
+        S.z[r] = zi - alpha * S.P[r] * api;
+      }
+      __syncthreads();
+    }
+    // islands that ran to the cap
+    if (tid < nisl && S.act[tid]) S.kdone[tid] = k;
+    __syncthreads();
+    for (int r = tid; r < nrow; r += RES_THREADS) {
+      const int gw = r < ncr_g ? 3 * c0 + r : gc + 5 * j0 + (r - ncr_g);
+      D.x[gw] = S.x[r];
+    }
+    if (warp == 0) {
+      // CR iterations and work of the group's islands that took part
+      unsigned long long wr = 0, we = 0, wb = 0;
+      int kmax = 0;
+      if (lane < nisl && D.resact[D.gisl[i0 + lane]]) {
+        const int kd = S.kdone[lane];
+        const unsigned long long it = (unsigned long long)(kd < M ? kd + 1 : kd);
+        wr = it * unsigned(S.ncr[lane] + S.njr[lane]);
+        we = it * unsigned(S.ient[lane]);
+        wb = it * unsigned(S.ibod[lane]);
+        kmax = kd;
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        wr += __shfl_xor_sync(0xffffffffu, wr, o);
+        we += __shfl_xor_sync(0xffffffffu, we, o);
+        wb += __shfl_xor_sync(0xffffffffu, wb, o);
+        kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
+      }
+      if (lane == 0) {
+        atomicMax(&D.fl->cr_res_max, kmax);
+        atomicAdd(&D.fl->res_rowit, wr);
+        atomicAdd(&D.fl->res_entit, we);
+        atomicAdd(&D.fl->res_bodit, wb);
+      }
+    }
+    __syncthreads();   // the shared image is rebuilt for the next group
+  }
+}
+
 // Loop control (one thread).  Each loop continues only while its counter is
 // below the cap, so it ends whatever the flags say; under a CUDA graph the
 // kernels also set the condition of the enclosing WHILE node.
@@ -1759,7 +2124,10 @@ template <typename T>
 __global__ void k_cr_begin(Dev<T> D, int M) {
   Flags *f = D.fl;
   f->cr_k = 0;
-  f->cr_live = (!f->newton_stop && !f->cr_stop && M > 0) ? 1 : 0;
+  f->cr_base = f->cr_count;
+  // island mode: no streamed island continues (all stopped or resident)
+  const bool none = D.isl_on && f->n_list_isl == 0;
+  f->cr_live = (!f->newton_stop && !f->cr_stop && M > 0 && !none) ? 1 : 0;
   if (D.hC) cudaGraphSetConditional(D.hC, unsigned(f->cr_live));
 }
 
@@ -1782,11 +2150,20 @@ __global__ void k_cr_next(Dev<T> D, int M) {
 
 // empties the island work list before k_merit_isl fills it
 template <typename T>
-__global__ void k_list_reset(Dev<T> D) { D.fl->n_list_isl = 0; }
+__global__ void k_list_reset(Dev<T> D) {
+  D.fl->cr_base = D.fl->cr_count;   // CR iterations before this Newton iteration
+  D.fl->n_list_isl = 0;
+  D.fl->n_list_res = 0;
+  D.fl->res_next = 0;
+}
 
 template <typename T>
 __global__ void k_newton_next(Dev<T> D, int N) {
   Flags *f = D.fl;
+  // CR iterations of this Newton iteration: the streamed loop's or the most
+  // an island ran in k_cr_resident, whichever is larger
+  if (f->cr_res_max > f->cr_count - f->cr_base) f->cr_count = f->cr_base + f->cr_res_max;
+  f->cr_res_max = 0;
   if (f->newton_live) {
     const int n = f->newton_n + 1;
     f->newton_n = n;

@@ -39,7 +39,8 @@ class nsn_config(C.Structure):
                 ("cr_iters", C.c_int32), ("damping", C.c_double), ("eps", C.c_double),
                 ("tol_rel", C.c_double), ("cr_tol_mode", C.c_int32), ("ncp", C.c_int32),
                 ("rscale", C.c_int32), ("geom_stiffness", C.c_int32), ("precision", C.c_int32),
-                ("use_graph", C.c_int32), ("cone_project", C.c_int32), ("island_stop", C.c_int32)]
+                ("use_graph", C.c_int32), ("cone_project", C.c_int32), ("island_stop", C.c_int32),
+                ("cr_resident", C.c_int32), ("res_max_rows", C.c_int32)]
 
 
 class nsn_stats(C.Structure):
@@ -111,6 +112,8 @@ def lib():
         "nsn_island_stop_copy": (C.c_int, [_vp, _vp]),
         "nsn_clear_warm_start": (C.c_int, [_vp]),
         "nsn_tuning": (C.c_int, [_vp, _ip, _fp]),
+        "nsn_resident_info": (C.c_int, [_vp, _ip]),
+        "nsn_time_resident": (C.c_int, [_vp, C.c_int32, _fp, _dp]),
         "nsn_set_body_lanes": (C.c_int, [_vp, C.c_int32]),
     }
     for name, (res, args) in sig.items():
@@ -378,7 +381,7 @@ def tet_records(s):
 
 DEFAULTS = dict(h=1.0 / 60.0, gravity=(0.0, 0.0, -9.81), newton_iters=4, cr_iters=20, damping=0.75, eps=1e-6,
                 tol_rel=0.0, cr_tol_mode=0, ncp=0, rscale=2, geom_stiffness=1, precision=NSN_FP32, use_graph=1,
-                cone_project=0, island_stop=0)
+                cone_project=0, island_stop=0, cr_resident=1, res_max_rows=512)
 
 
 def make_config(**params):
@@ -391,7 +394,7 @@ def make_config(**params):
     cfg.h = p["h"]
     cfg.gravity = (C.c_double * 3)(*p["gravity"])
     for k in ("newton_iters", "cr_iters", "cr_tol_mode", "ncp", "rscale", "geom_stiffness", "precision", "use_graph",
-              "cone_project", "island_stop"):
+              "cone_project", "island_stop", "cr_resident", "res_max_rows"):
         setattr(cfg, k, int(p[k]))
     for k in ("damping", "eps", "tol_rel"):
         setattr(cfg, k, float(p[k]))
@@ -488,6 +491,19 @@ class Solver:
         ms = np.zeros(3, np.float32)
         _check(self.ctx, lib().nsn_tuning(self.ctx, C.byref(g), _p(ms)), "nsn_tuning")
         return g.value, ms
+
+    def resident_info(self):
+        """Island-resident CR: dict of islands, groups, max_rows, max_entries, smem_bytes, grid."""
+        v = np.zeros(6, np.int32)
+        _check(self.ctx, lib().nsn_resident_info(self.ctx, _p(v, _ip)), "nsn_resident_info")
+        return dict(zip(("islands", "groups", "max_rows", "max_entries", "smem_bytes", "grid"), (int(x) for x in v)))
+
+    def time_resident(self, iters=10):
+        """(mean ms of one k_cr_resident launch at full activity, dict of its work)."""
+        ms = C.c_float()
+        w = np.zeros(4, np.float64)
+        _check(self.ctx, lib().nsn_time_resident(self.ctx, iters, C.byref(ms), _p(w, _dp)), "nsn_time_resident")
+        return ms.value, dict(zip(("islands", "row_iterations", "entry_iterations", "body_iterations"), w.tolist()))
 
     def set_body_lanes(self, lanes):
         _check(self.ctx, lib().nsn_set_body_lanes(self.ctx, lanes), "nsn_set_body_lanes")

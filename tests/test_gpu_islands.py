@@ -70,7 +70,11 @@ def test_island_mode_parity_fp64(orc):
     assert np.array_equal(ig["stopped_at"], io["stopped_at"])
     np.testing.assert_allclose(ig["merit0"], io["merit0"], rtol=1e-9)
     done = io["stopped_at"] >= 0
-    np.testing.assert_allclose(ig["merit_final"][~done], io["merit_final"][~done], rtol=1e-5)
+    # an island that did not converge ends on an iterate that depends on the
+    # rounding order; its merit is compared at a tenth of the stop tolerance,
+    # which is relative to its zero-iterate merit (Sec. 8.1)
+    np.testing.assert_array_less(np.abs(ig["merit_final"] - io["merit_final"])[~done],
+                                 1e-7 * io["merit0"][~done] + 1e-300)
     assert np.all(ig["merit_final"][done] <= 1e-6 * ig["merit0"][done] * (1 + 1e-6))
     assert sg_["newton_done"] == so_["newton_done"]
     e = vel_error(o.get_state(), g.get_state_f64(), s)
