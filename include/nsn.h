@@ -100,8 +100,8 @@ typedef struct {
                              (the same recurrence and stop rules; HBM read once per
                              Newton iteration instead of once per CR iteration); 0: every
                              island in the streamed CR loop */
-  int32_t res_max_rows;   /* row cap of a resident island and of a group of them
-                             (default 512; <= 0: 512) */
+  int32_t res_max_rows;   /* row cap of a resident island and of a group of them, at most 2048
+                             (default 384; <= 0: 384) */
 } nsn_config;
 
 /* Fills the paper's defaults: h = 1/60, g = (0, 0, -9.81), 4 x 20 iterations,

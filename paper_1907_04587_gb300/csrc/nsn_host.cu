@@ -309,7 +309,8 @@ nsn_status build_layout(nsn_ctx *c) {
     for (int b = 0; b < L.nr; b++) first(L.bisl_r[b], 4, b);
     for (int b = 0; b < L.np; b++) npar[L.bisl_p[b]]++;
     for (int t = 0; t < L.nt; t++) ntet[L.risl[L.Rpair + 3 * t]]++;
-    const int cap = c->cfg.res_max_rows > 0 ? c->cfg.res_max_rows : 512;
+    // (at most 2048 rows: the reduction task table of a group holds 2 per island + rows / 128)
+    const int cap = std::min(c->cfg.res_max_rows > 0 ? c->cfg.res_max_rows : 384, 2048);
     for (int i = 0; i < L.ni; i++) {
       int *r = &L.ires[8 * size_t(i)];
       if (r[5] > 0) { r[6] = L.rseg[r[4]]; r[7] = L.rseg[r[4] + r[5]] - r[6]; }
@@ -852,9 +853,11 @@ struct Launcher {
     if (D.isl_on) {
       const int gb = BLOCK / D.G;
       const int nblk = std::max({cdiv(std::max(D.R, 1), BLOCK), cdiv(D.nr, gb), cdiv(D.np, gb), 1});
-      k_block_flags<T><<<nblk, BLOCK, 0, st>>>(D);
-      k_block_lists<T><<<1, 1024, 0, st>>>(D, 0);
-      count += 2;
+      if (D.streamed) {   // work lists of the streamed CR loop
+        k_block_flags<T><<<nblk, BLOCK, 0, st>>>(D);
+        k_block_lists<T><<<1, 1024, 0, st>>>(D, 0);
+        count += 2;
+      }
       if (D.res_on && M > 0) {
         k_cr_resident<T><<<D.nblk_res, RES_THREADS, D.res_smem, st>>>(D, M);
         count++;
@@ -1606,7 +1609,7 @@ void nsn_default_config(nsn_config *cfg) {
   cfg->cone_project = 0;
   cfg->island_stop = 0;
   cfg->cr_resident = 1;
-  cfg->res_max_rows = 512;
+  cfg->res_max_rows = 384;
 }
 
 nsn_status nsn_create(const nsn_config *cfg, void *stream, nsn_ctx **out) {

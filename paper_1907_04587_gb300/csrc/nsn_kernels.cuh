@@ -25,6 +25,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace nsn {
 
 constexpr int BLOCK = 256;
@@ -1808,77 +1810,187 @@ __global__ void __launch_bounds__(BLOCK) k_cr_update_isl(Dev<T> D) {
 constexpr int RES_THREADS = 256;
 constexpr int RES_NW = RES_THREADS / 32;
 constexpr int RES_G = 8;      // lanes per body in the J^T z gather
+constexpr int RES_KR = 3;     // entries per lane kept in registers between the gather and t_e = J_e y_b
 constexpr int RES_MAXI = 32;  // islands per group (one lane each in the scalar warp)
+constexpr int RES_TASK = 128; // rows per reduction task (a piece of one island's contact or joint rows)
+constexpr int RES_MAXT = 2 * RES_MAXI + 16;   // reduction tasks per group (groups of at most 2048 rows)
 
 __host__ __device__ inline int res_pad(int n) { return (n + 3) & ~3; }
 
-// shared-memory image of one group: RR rows, RE entries, RB bodies, RES_MAXI islands
+// vectors of the shared-memory image, loaded and stored whole
 template <typename T>
-struct ResSmem {
-  double *r02f, *eta2, *rho_prev, *res_prev;   // [RES_MAXI] per island
-  T *sums;                                      // [5][RES_MAXI] per-island CR products
-  T *z, *p, *Ap, *x, *P, *dg, *Az;              // [RR]
-  T *prod;                                      // [5][RR] per-row CR products
-  T *J[6];                                      // [RE]
-  T *im, *Si[6], *y[6];                         // [RB]
-  T *alpha, *beta;                              // [RES_MAXI]
-  int *le0, *le1, *lb0, *lb1, *risl;            // [RR] local entries / bodies of the two sides, local island
-  int *erow;                                    // [RE] local row of each entry
-  int *seg, *bisl;                              // [RB + 1] entry segments, [RB] local island of each body
-  int *act, *kdone, *cr0, *ncr, *jr0, *njr, *ient, *ibod;  // [RES_MAXI]
-  int *ctl;                                     // group slot, continue flag
+struct alignas(4 * sizeof(T)) RV4 { T a, b, c, d; };
+template <typename T>
+struct alignas(2 * sizeof(T)) RV2 { T a, b; };
+
+// byte offsets of the arrays of the shared-memory image of one group: RR rows,
+// RE entries, RB bodies, RES_MAXI islands (the same on host and device)
+struct ResLayout {
+  size_t rv, jA, bm, bn, jB, p, x, Az, prod, t, part, alpha, beta, dbl, isT, le, risl, erow, seg, bisl, isl, task,
+      ctl, total;
 };
 
 template <typename T>
-__host__ __device__ inline size_t res_smem_bytes(int RR, int RE, int RB) {
-  const size_t rr = res_pad(RR), re = res_pad(RE), rb = res_pad(RB + 1);
-  const size_t nT = 12 * rr + 6 * re + 13 * rb + 7 * RES_MAXI;
-  const size_t nI = 5 * rr + re + 2 * rb + 8 * RES_MAXI + 4;
-  return sizeof(double) * 4 * RES_MAXI + sizeof(T) * nT + sizeof(int) * nI;
+__host__ __device__ inline ResLayout res_layout(int RR, int RE, int RB) {
+  ResLayout L{};
+  size_t off = 0;
+  auto take = [&](size_t bytes, size_t align) {
+    off = (off + align - 1) / align * align;
+    const size_t o = off;
+    off += bytes;
+    return o;
+  };
+  const size_t rr = res_pad(RR), re = res_pad(RE), rb = res_pad(RB + 1), V4 = sizeof(RV4<T>), V2 = sizeof(RV2<T>);
+  L.rv = take(V4 * rr, V4);        // z, P, Ap, C_ii + eps per row
+  L.jA = take(V4 * re, V4);        // J_0..J_3 per entry
+  L.bm = take(V4 * rb, V4);        // 1/m, I_w^-1 (xx, yy, zz) per body
+  L.bn = take(V4 * rb, V4);        // I_w^-1 (xy, xz, yz), unused
+  L.jB = take(V2 * re, V2);        // J_4, J_5 per entry
+  L.p = take(sizeof(T) * rr, sizeof(T));
+  L.x = take(sizeof(T) * rr, sizeof(T));
+  L.Az = take(sizeof(T) * rr, sizeof(T));
+  L.prod = take(sizeof(T) * 5 * rr, sizeof(T));
+  L.t = take(sizeof(T) * re, sizeof(T));
+  L.part = take(sizeof(T) * 5 * RES_MAXT, sizeof(T));
+  L.alpha = take(sizeof(T) * RES_MAXI, sizeof(T));
+  L.beta = take(sizeof(T) * RES_MAXI, sizeof(T));
+  L.dbl = take(sizeof(double) * RES_MAXI, sizeof(double));
+  L.isT = take(sizeof(T) * 3 * RES_MAXI, sizeof(T));
+  L.le = take(sizeof(int2) * rr, sizeof(int2));
+  L.risl = take(sizeof(int) * rr, sizeof(int));
+  L.erow = take(sizeof(int) * re, sizeof(int));
+  L.seg = take(sizeof(int) * rb, sizeof(int));
+  L.bisl = take(sizeof(int) * rb, sizeof(int));
+  L.isl = take(sizeof(int) * 11 * RES_MAXI, sizeof(int));
+  L.task = take(sizeof(int) * 3 * RES_MAXT, sizeof(int));
+  L.ctl = take(sizeof(int) * 4, sizeof(int));
+  L.total = off;
+  return L;
 }
 
 template <typename T>
+__host__ __device__ inline size_t res_smem_bytes(int RR, int RE, int RB) { return res_layout<T>(RR, RE, RB).total; }
+
+template <typename T>
+struct ResSmem {
+  RV4<T> *rv, *jA, *bm, *bn;
+  RV2<T> *jB;
+  T *p, *x, *Az, *prod, *t, *part, *alpha, *beta;   // part: [5][RES_MAXT] task sums
+  T *r02f, *eta2, *res_prev;                    // [RES_MAXI] per island: stop thresholds, ||r||_P^2 of the last iteration
+  double *rho_prev;                             // [RES_MAXI] 1 / rho of the last iteration
+  int2 *le;                                     // local entries of the two sides of each row (-1: none)
+  int *risl, *erow, *seg, *bisl;                // island of each row, row of each entry, body segments, island of each body
+  int *act, *kdone, *cr0, *ncr, *jr0, *njr, *ient, *ibod, *ib0, *it0, *it1;   // [RES_MAXI] per island
+  int *tisl, *tr0, *tn;                         // [RES_MAXT] reduction tasks: island, first row, rows
+  int *ctl;
+};
+
+template <typename T>
 __device__ inline ResSmem<T> res_carve(unsigned char *base, int RR, int RE, int RB) {
+  const ResLayout L = res_layout<T>(RR, RE, RB);
   ResSmem<T> S;
-  const int rr = res_pad(RR), re = res_pad(RE), rb = res_pad(RB + 1);
-  double *d = reinterpret_cast<double *>(base);
-  S.r02f = d; d += RES_MAXI; S.eta2 = d; d += RES_MAXI; S.rho_prev = d; d += RES_MAXI; S.res_prev = d; d += RES_MAXI;
-  T *t = reinterpret_cast<T *>(d);
-  S.sums = t; t += 5 * RES_MAXI;
-  S.z = t; t += rr; S.p = t; t += rr; S.Ap = t; t += rr; S.x = t; t += rr;
-  S.P = t; t += rr; S.dg = t; t += rr; S.Az = t; t += rr;
-  S.prod = t; t += 5 * rr;
-  for (int k = 0; k < 6; k++) { S.J[k] = t; t += re; }
-  S.im = t; t += rb;
-  for (int k = 0; k < 6; k++) { S.Si[k] = t; t += rb; }
-  for (int k = 0; k < 6; k++) { S.y[k] = t; t += rb; }
-  S.alpha = t; t += RES_MAXI; S.beta = t; t += RES_MAXI;
-  int *q = reinterpret_cast<int *>(t);
-  S.le0 = q; q += rr; S.le1 = q; q += rr; S.lb0 = q; q += rr; S.lb1 = q; q += rr; S.risl = q; q += rr;
-  S.erow = q; q += re;
-  S.seg = q; q += rb; S.bisl = q; q += rb;
-  S.act = q; q += RES_MAXI; S.kdone = q; q += RES_MAXI; S.cr0 = q; q += RES_MAXI; S.ncr = q; q += RES_MAXI;
-  S.jr0 = q; q += RES_MAXI; S.njr = q; q += RES_MAXI; S.ient = q; q += RES_MAXI; S.ibod = q; q += RES_MAXI;
-  S.ctl = q;
+  S.rv = reinterpret_cast<RV4<T> *>(base + L.rv);
+  S.jA = reinterpret_cast<RV4<T> *>(base + L.jA);
+  S.bm = reinterpret_cast<RV4<T> *>(base + L.bm);
+  S.bn = reinterpret_cast<RV4<T> *>(base + L.bn);
+  S.jB = reinterpret_cast<RV2<T> *>(base + L.jB);
+  S.p = reinterpret_cast<T *>(base + L.p);
+  S.x = reinterpret_cast<T *>(base + L.x);
+  S.Az = reinterpret_cast<T *>(base + L.Az);
+  S.prod = reinterpret_cast<T *>(base + L.prod);
+  S.t = reinterpret_cast<T *>(base + L.t);
+  S.part = reinterpret_cast<T *>(base + L.part);
+  S.alpha = reinterpret_cast<T *>(base + L.alpha);
+  S.beta = reinterpret_cast<T *>(base + L.beta);
+  S.rho_prev = reinterpret_cast<double *>(base + L.dbl);
+  T *ts = reinterpret_cast<T *>(base + L.isT);
+  S.r02f = ts; S.eta2 = ts + RES_MAXI; S.res_prev = ts + 2 * RES_MAXI;
+  S.le = reinterpret_cast<int2 *>(base + L.le);
+  S.risl = reinterpret_cast<int *>(base + L.risl);
+  S.erow = reinterpret_cast<int *>(base + L.erow);
+  S.seg = reinterpret_cast<int *>(base + L.seg);
+  S.bisl = reinterpret_cast<int *>(base + L.bisl);
+  int *q = reinterpret_cast<int *>(base + L.isl);
+  S.act = q; S.kdone = q + RES_MAXI; S.cr0 = q + 2 * RES_MAXI; S.ncr = q + 3 * RES_MAXI; S.jr0 = q + 4 * RES_MAXI;
+  S.njr = q + 5 * RES_MAXI; S.ient = q + 6 * RES_MAXI; S.ibod = q + 7 * RES_MAXI; S.ib0 = q + 8 * RES_MAXI;
+  S.it0 = q + 9 * RES_MAXI; S.it1 = q + 10 * RES_MAXI;
+  int *tk = reinterpret_cast<int *>(base + L.task);
+  S.tisl = tk; S.tr0 = tk + RES_MAXT; S.tn = tk + 2 * RES_MAXT;
+  S.ctl = reinterpret_cast<int *>(base + L.ctl);
   return S;
 }
 
-// local body of local entry e: the last segment that starts at or before e
-__device__ __forceinline__ int res_body_of(const int *seg, int nb, int e) {
-  int lo = 0, hi = nb - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (seg[mid] <= e) lo = mid; else hi = mid - 1;
+template <typename T>
+__device__ __forceinline__ void res_load_j(const ResSmem<T> &S, int e, T *J) {
+  const RV4<T> a = S.jA[e];
+  const RV2<T> b = S.jB[e];
+  J[0] = a.a; J[1] = a.b; J[2] = a.c; J[3] = a.d; J[4] = b.a; J[5] = b.b;
+}
+
+template <typename T>
+__device__ __forceinline__ T res_dot6(const T *J, const T *y) {
+  T acc = T(0);
+#pragma unroll
+  for (int k = 0; k < 6; k++) acc += J[k] * y[k];
+  return acc;
+}
+
+// The CR scalars of island li at iteration k from its task sums (the
+// recurrence and stop rules of k_cr_scalars_isl).  Returns false when the
+// island's CR stops.  The sums are T values, and so are the stop thresholds:
+// the stop tests compare in T (in FP32 they are exact: a single-precision value
+// and its FP64 image order the same way).  beta, ApTPAp and alpha are FP64;
+// in the FP32 build one FP64 reciprocal of rho * ApTPAp gives both alpha =
+// rho / ApTPAp and 1 / rho for the next iteration's beta, the FP64 build takes
+// the two divisions as they are.
+template <typename T>
+__device__ __forceinline__ bool res_scalars(const ResSmem<T> &S, int li, int k) {
+  T a[5] = {T(0), T(0), T(0), T(0), T(0)};
+  for (int tk = S.it0[li]; tk < S.it1[li]; tk++)
+#pragma unroll
+    for (int q = 0; q < 5; q++) a[q] += S.part[q * RES_MAXT + tk];
+  // ||r||_P^2 = a[3]: floor, growth from the previous iteration, forcing term
+  const T cur2 = a[3] > T(0) ? a[3] : T(0);
+  const T rp2 = S.res_prev[li];
+  bool st = rp2 < T(0) || cur2 <= S.r02f[li] || (k > 0 && cur2 > rp2) || cur2 <= S.eta2[li];
+  S.res_prev[li] = cur2;
+  double beta = 0.0, apap = double(a[1]);
+  if (k > 0) {
+    const double irp = S.rho_prev[li];           // 1 / rho of the previous iteration
+    if (!(a[0] > T(0)) || !(irp > 0.0)) st = true;
+    else {
+      beta = double(a[0]) * irp;
+      apap = double(a[1]) + 2.0 * beta * double(a[2]) + beta * beta * double(a[4]);
+    }
   }
-  return lo;
+  if (st || !(apap > 0.0)) {
+    S.act[li] = 0;
+    S.kdone[li] = k;
+    return false;
+  }
+  const double d0 = double(a[0]);
+  double alpha, inv_rho;
+  if constexpr (std::is_same<T, float>::value) {
+    const double rc = 1.0 / (d0 * apap);
+    alpha = d0 * (d0 * rc);
+    inv_rho = apap * rc;
+  } else {
+    alpha = d0 / apap;
+    inv_rho = 1.0 / d0;
+  }
+  S.rho_prev[li] = a[0] > T(0) ? inv_rho : -1.0;  // rho <= 0: the next iteration stops
+  S.alpha[li] = cr_scalar<T>(alpha, float(alpha));
+  S.beta[li] = cr_scalar<T>(beta, float(beta));
+  return true;
 }
 
 template <typename T>
 __global__ void __launch_bounds__(RES_THREADS) k_cr_resident(Dev<T> D, int M) {
   if (D.fl->newton_stop) return;
-  extern __shared__ __align__(16) unsigned char res_raw[];
+  extern __shared__ __align__(32) unsigned char res_raw[];
   const ResSmem<T> S = res_carve<T>(res_raw, D.res_rows, D.res_ent, D.res_bod);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int rr = res_pad(D.res_rows);
   const T eps = D.epsT;
   const int gc = 3 * D.nc;
   for (;;) {
@@ -1891,129 +2003,139 @@ __global__ void __launch_bounds__(RES_THREADS) k_cr_resident(Dev<T> D, int M) {
     const int c0 = gr[0], ncg = gr[1], j0 = gr[2], njg = gr[3], b0 = gr[4], nb = gr[5], e0 = gr[6], ne = gr[7];
     const int i0 = gr[8], nisl = gr[9];
     const int ncr_g = 3 * ncg, nrow = ncr_g + 5 * njg;
-    // islands of the group
+    // load the group: islands, bodies, entries, rows
     if (tid < nisl) {
       const int is = D.gisl[i0 + tid];
       const int *ir = D.ires + 8 * size_t(is);
       S.cr0[tid] = 3 * (ir[0] - c0); S.ncr[tid] = 3 * ir[1];
       S.jr0[tid] = ncr_g + 5 * (ir[2] - j0); S.njr[tid] = 5 * ir[3];
-      S.ient[tid] = ir[7]; S.ibod[tid] = ir[5];
-      const int a = D.resact[is];
-      S.act[tid] = a;
+      S.ib0[tid] = ir[4] - b0; S.ibod[tid] = ir[5]; S.ient[tid] = ir[7];
+      S.act[tid] = D.resact[is];
       S.kdone[tid] = 0;
       const double r0 = D.isl.res0[is], fl = cr_floor<T>();
-      S.r02f[tid] = fl * fl * r0 * r0;
-      S.eta2[tid] = D.cr_tol ? D.isl.eta[is] * D.isl.eta[is] * r0 * r0 : -1.0;
-      S.res_prev[tid] = r0 == 0.0 ? -1.0 : 0.0;   // r0 == 0: the island stops at once
+      S.r02f[tid] = T(fl * fl * r0 * r0);
+      S.eta2[tid] = D.cr_tol ? T(D.isl.eta[is] * D.isl.eta[is] * r0 * r0) : T(-1);
+      S.res_prev[tid] = r0 == 0.0 ? T(-1) : T(0);   // r0 == 0: the island stops at once
       S.rho_prev[tid] = 0.0;
     }
     for (int b = tid; b < nb; b += RES_THREADS) {
       const int gb = b0 + b;
-      S.im[b] = D.rinvm[gb];
-#pragma unroll
-      for (int k = 0; k < 6; k++) S.Si[k][b] = D.rIwi[k][gb];
+      S.bm[b] = RV4<T>{D.rinvm[gb], D.rIwi[0][gb], D.rIwi[1][gb], D.rIwi[2][gb]};
+      S.bn[b] = RV4<T>{D.rIwi[3][gb], D.rIwi[4][gb], D.rIwi[5][gb], T(0)};
       S.seg[b] = D.rseg[gb] - e0;
     }
     if (tid == 0) S.seg[nb] = ne;
     for (int e = tid; e < ne; e += RES_THREADS) {
       const int ge = e0 + e;
-#pragma unroll
-      for (int k = 0; k < 6; k++) S.J[k][e] = D.ej6[k][ge];
+      S.jA[e] = RV4<T>{D.ej6[0][ge], D.ej6[1][ge], D.ej6[2][ge], D.ej6[3][ge]};
+      S.jB[e] = RV2<T>{D.ej6[4][ge], D.ej6[5][ge]};
       const int gw = slot_row(D.eslot[ge], D.Rpair);
       S.erow[e] = gw < gc ? gw - 3 * c0 : ncr_g + (gw - gc - 5 * j0);
     }
     for (int r = tid; r < nrow; r += RES_THREADS) {
       const int gw = r < ncr_g ? 3 * c0 + r : gc + 5 * j0 + (r - ncr_g);
       const T zi = D.z[gw];                   // P b, from the rhs pass
-      S.z[r] = zi; S.p[r] = zi; S.Ap[r] = T(0); S.x[r] = T(0);
-      S.P[r] = D.P[gw];
-      S.dg[r] = D.cdiag[gw] + eps;
+      S.rv[r] = RV4<T>{zi, D.P[gw], T(0), D.cdiag[gw] + eps};
+      S.p[r] = zi; S.x[r] = T(0);
       const int a0 = D.re0[gw], a1 = D.re1[gw];
-      S.le0[r] = a0 >= 0 ? a0 - e0 : -1;
-      S.le1[r] = a1 >= 0 ? a1 - e0 : -1;
+      S.le[r] = make_int2(a0 >= 0 ? a0 - e0 : -1, a1 >= 0 ? a1 - e0 : -1);
     }
     __syncthreads();
-    // island tags of rows and bodies (one warp per island), sides' bodies
+    // island of each row and body (one warp per island)
     for (int li = warp; li < nisl; li += RES_NW) {
       for (int r = lane; r < S.ncr[li]; r += 32) S.risl[S.cr0[li] + r] = li;
       for (int r = lane; r < S.njr[li]; r += 32) S.risl[S.jr0[li] + r] = li;
+      for (int b = lane; b < S.ibod[li]; b += 32) S.bisl[S.ib0[li] + b] = li;
     }
-    for (int r = tid; r < nrow; r += RES_THREADS) {
-      const int a0 = S.le0[r], a1 = S.le1[r];
-      const int q0 = a0 >= 0 ? res_body_of(S.seg, nb, a0) : 0;
-      const int q1 = a1 >= 0 ? res_body_of(S.seg, nb, a1) : 0;
-      S.lb0[r] = q0; S.lb1[r] = q1;
+    // reduction tasks: each island's contact and joint rows in pieces of at
+    // most RES_TASK rows, island by island (so an island's tasks are contiguous
+    // and its sum is taken in a fixed order)
+    if (tid == 0) {
+      int nt = 0;
+      for (int li = 0; li < nisl; li++) {
+        S.it0[li] = nt;
+        for (int h = 0; h < 2; h++) {
+          const int r0 = h ? S.jr0[li] : S.cr0[li], n = h ? S.njr[li] : S.ncr[li];
+          for (int o = 0; o < n; o += RES_TASK) {
+            S.tisl[nt] = li; S.tr0[nt] = r0 + o; S.tn[nt] = min(RES_TASK, n - o);
+            nt++;
+          }
+        }
+        S.it1[li] = nt;
+      }
+      S.ctl[2] = nt;
     }
     __syncthreads();
-    for (int r = tid; r < nrow; r += RES_THREADS) {
-      // a body's island is that of any row it touches
-      const int a0 = S.le0[r], a1 = S.le1[r], li = S.risl[r];
-      if (a0 >= 0) S.bisl[S.lb0[r]] = li;
-      if (a1 >= 0) S.bisl[S.lb1[r]] = li;
-    }
-    __syncthreads();
+    const int ntask = S.ctl[2];
     int k = 0;
     for (; k < M; k++) {
-      // y = H~^-1 J^T z for the bodies of continuing islands, RES_G lanes per body
+      // y_b = H~^-1 J^T z and t_e = J_e y_b for the bodies of continuing
+      // islands, RES_G lanes per body; the first RES_KR entries of a lane stay
+      // in registers between the two
       for (int bb = 0; bb < nb; bb += RES_THREADS / RES_G) {
         const int b = bb + tid / RES_G, l = tid % RES_G;
         const bool on = b < nb && S.act[S.bisl[b]];
-        T s6[6] = {0, 0, 0, 0, 0, 0};
-        if (on) {
-          const int s1 = S.seg[b + 1];
-          for (int e = S.seg[b] + l; e < s1; e += RES_G) {
-            const T zr = S.z[S.erow[e]];
+        int s0 = 0, s1 = 0;
+        if (on) { s0 = S.seg[b]; s1 = S.seg[b + 1]; }
+        T J[RES_KR][6], s6[6] = {0, 0, 0, 0, 0, 0};
 #pragma unroll
-            for (int q = 0; q < 6; q++) s6[q] += S.J[q][e] * zr;
+        for (int q = 0; q < RES_KR; q++) {
+          const int e = s0 + l + q * RES_G;
+          if (e < s1) {
+            res_load_j(S, e, J[q]);
+            const T zr = S.rv[S.erow[e]].a;
+#pragma unroll
+            for (int m = 0; m < 6; m++) s6[m] += J[q][m] * zr;
           }
         }
+        for (int e = s0 + l + RES_KR * RES_G; e < s1; e += RES_G) {
+          T Je[6];
+          res_load_j(S, e, Je);
+          const T zr = S.rv[S.erow[e]].a;
 #pragma unroll
-        for (int q = 0; q < 6; q++) s6[q] = group_sum<RES_G>(s6[q]);
-        if (on && l == 0) {
-          const T im = S.im[b];
-          T Si[6], w[3];
+          for (int m = 0; m < 6; m++) s6[m] += Je[m] * zr;
+        }
 #pragma unroll
-          for (int q = 0; q < 6; q++) Si[q] = S.Si[q][b];
-          sym3v(Si, s6 + 3, w);
-          S.y[0][b] = s6[0] * im; S.y[1][b] = s6[1] * im; S.y[2][b] = s6[2] * im;
-          S.y[3][b] = w[0]; S.y[4][b] = w[1]; S.y[5][b] = w[2];
+        for (int m = 0; m < 6; m++) s6[m] = group_sum<RES_G>(s6[m]);
+        if (on) {
+          const RV4<T> bm = S.bm[b], bn = S.bn[b];
+          const T Si[6] = {bm.b, bm.c, bm.d, bn.a, bn.b, bn.c};
+          T y[6];
+          y[0] = s6[0] * bm.a; y[1] = s6[1] * bm.a; y[2] = s6[2] * bm.a;
+          sym3v(Si, s6 + 3, y + 3);
+#pragma unroll
+          for (int q = 0; q < RES_KR; q++) {
+            const int e = s0 + l + q * RES_G;
+            if (e < s1) S.t[e] = res_dot6(J[q], y);
+          }
+          for (int e = s0 + l + RES_KR * RES_G; e < s1; e += RES_G) {
+            T Je[6];
+            res_load_j(S, e, Je);
+            S.t[e] = res_dot6(Je, y);
+          }
         }
       }
       __syncthreads();
-      // Az and the five products of k_row_pass_isl, per row
+      // Az = sum of the row's t_e + (C_ii + eps) z and the five products of k_row_pass_isl
       for (int r = tid; r < nrow; r += RES_THREADS) {
         if (!S.act[S.risl[r]]) continue;
-        T t0 = T(0), t1 = T(0);
-        const int e0l = S.le0[r], e1l = S.le1[r];
-        if (e0l >= 0) {
-          const int b = S.lb0[r];
-#pragma unroll
-          for (int q = 0; q < 6; q++) t0 += S.J[q][e0l] * S.y[q][b];
-        }
-        if (e1l >= 0) {
-          const int b = S.lb1[r];
-#pragma unroll
-          for (int q = 0; q < 6; q++) t1 += S.J[q][e1l] * S.y[q][b];
-        }
-        const T zi = S.z[r], Pi = S.P[r], api = S.Ap[r];
-        const T az = (t0 + t1) + S.dg[r] * zi;
+        const int2 le = S.le[r];
+        const T t0 = le.x >= 0 ? S.t[le.x] : T(0);
+        const T t1 = le.y >= 0 ? S.t[le.y] : T(0);
+        const RV4<T> v = S.rv[r];               // z, P, Ap, C_ii + eps
+        const T az = (t0 + t1) + v.d * v.a;
         S.Az[r] = az;
-        const T paz = Pi * az;
-        const int rr = res_pad(D.res_rows);
-        S.prod[r] = zi * az; S.prod[rr + r] = az * paz; S.prod[2 * rr + r] = paz * api;
-        S.prod[3 * rr + r] = zi * zi / Pi; S.prod[4 * rr + r] = api * Pi * api;
+        const T paz = v.b * az;
+        S.prod[r] = v.a * az; S.prod[rr + r] = az * paz; S.prod[2 * rr + r] = paz * v.c;
+        S.prod[3 * rr + r] = v.a * v.a / v.b; S.prod[4 * rr + r] = v.c * v.b * v.c;
       }
       __syncthreads();
-      // per-island sums, one warp per island, fixed order
-      for (int li = warp; li < nisl; li += RES_NW) {
-        if (!S.act[li]) continue;
-        const int rr = res_pad(D.res_rows);
+      // task sums (a task: up to RES_TASK rows of one island), one warp per task
+      for (int tk = warp; tk < ntask; tk += RES_NW) {
+        if (!S.act[S.tisl[tk]]) continue;
         T a[5] = {T(0), T(0), T(0), T(0), T(0)};
-        const int c0l = S.cr0[li], c1l = c0l + S.ncr[li], j0l = S.jr0[li], j1l = j0l + S.njr[li];
-        for (int r = c0l + lane; r < c1l; r += 32)
-#pragma unroll
-          for (int q = 0; q < 5; q++) a[q] += S.prod[q * rr + r];
-        for (int r = j0l + lane; r < j1l; r += 32)
+        const int r1 = S.tr0[tk] + S.tn[tk];
+        for (int r = S.tr0[tk] + lane; r < r1; r += 32)
 #pragma unroll
           for (int q = 0; q < 5; q++) a[q] += S.prod[q * rr + r];
 #pragma unroll
@@ -2023,61 +2145,33 @@ __global__ void __launch_bounds__(RES_THREADS) k_cr_resident(Dev<T> D, int M) {
         }
         if (lane == 0) {
 #pragma unroll
-          for (int q = 0; q < 5; q++) S.sums[q * RES_MAXI + li] = a[q];
+          for (int q = 0; q < 5; q++) S.part[q * RES_MAXT + tk] = a[q];
         }
       }
       __syncthreads();
       // FP64 scalars and stop tests of every island of the group: lane li
       if (warp == 0) {
         bool live = false;
-        if (lane < nisl && S.act[lane]) {
-          const int li = lane;
-          double d[5];
-#pragma unroll
-          for (int q = 0; q < 5; q++) d[q] = double(S.sums[q * RES_MAXI + li]);
-          int st = 0;
-          const double cur2 = d[3] > 0.0 ? d[3] : 0.0;
-          const double rp2 = S.res_prev[li];
-          if (rp2 < 0.0 || cur2 <= S.r02f[li] || (k > 0 && cur2 > rp2)) st = 1;
-          if (cur2 <= S.eta2[li]) st = 1;
-          S.res_prev[li] = cur2;
-          double beta = 0.0, apap = d[1];
-          if (k > 0) {
-            const double rp = S.rho_prev[li];
-            if (!(d[0] > 0.0) || !(rp > 0.0)) st = 1;
-            else {
-              beta = d[0] / rp;
-              apap = d[1] + 2.0 * beta * d[2] + beta * beta * d[4];
-            }
-          }
-          if (!(apap > 0.0)) st = 1;
-          if (st) {
-            S.act[li] = 0;
-            S.kdone[li] = k;
-          } else {
-            S.rho_prev[li] = d[0];
-            const double alpha = d[0] / apap;
-            S.alpha[li] = cr_scalar<T>(alpha, float(alpha));
-            S.beta[li] = cr_scalar<T>(beta, float(beta));
-            live = true;
-          }
-        }
+        if (lane < nisl && S.act[lane]) live = res_scalars<T>(S, lane, k);
         const unsigned any = __ballot_sync(0xffffffffu, live);
         if (lane == 0) S.ctl[1] = any != 0u;
       }
       __syncthreads();
       if (!S.ctl[1]) break;
+      // p = z + beta p, Ap = Az + beta Ap, x += alpha p, z -= alpha P Ap
       for (int r = tid; r < nrow; r += RES_THREADS) {
         const int li = S.risl[r];
         if (!S.act[li]) continue;
         const T alpha = S.alpha[li], beta = S.beta[li];
-        const T zi = S.z[r];
-        const T pi = k == 0 ? zi : zi + beta * S.p[r];
-        const T api = k == 0 ? S.Az[r] : S.Az[r] + beta * S.Ap[r];
+        RV4<T> v = S.rv[r];
+        const T az = S.Az[r];
+        const T pi = k == 0 ? v.a : v.a + beta * S.p[r];
+        const T api = k == 0 ? az : az + beta * v.c;
         S.p[r] = pi;
-        S.Ap[r] = api;
         S.x[r] += alpha * pi;
-        S.z[r] = zi - alpha * S.P[r] * api;
+        v.c = api;
+        v.a = v.a - alpha * v.b * api;
+        S.rv[r] = v;
       }
       __syncthreads();
     }

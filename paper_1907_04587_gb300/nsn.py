@@ -381,7 +381,7 @@ def tet_records(s):
 
 DEFAULTS = dict(h=1.0 / 60.0, gravity=(0.0, 0.0, -9.81), newton_iters=4, cr_iters=20, damping=0.75, eps=1e-6,
                 tol_rel=0.0, cr_tol_mode=0, ncp=0, rscale=2, geom_stiffness=1, precision=NSN_FP32, use_graph=1,
-                cone_project=0, island_stop=0, cr_resident=1, res_max_rows=512)
+                cone_project=0, island_stop=0, cr_resident=1, res_max_rows=384)
 
 
 def make_config(**params):

@@ -145,15 +145,20 @@ def test_graph_loops_equal_eager_launch(orc):
     step: the per-island sums are FP64 atomics whose order is not fixed, and
     islands that never converge amplify that rounding over later steps."""
     s = SCENE()
-    a = nsn.Solver(s, precision=nsn.NSN_FP64, use_graph=1, **PRM)
-    b = nsn.Solver(s, precision=nsn.NSN_FP64, use_graph=0, **PRM)
-    ra, rb = a.step(), b.step()
-    assert ra["newton_done"] == rb["newton_done"]
-    assert np.array_equal(a.island_stats()["stopped_at"], b.island_stats()["stopped_at"])
-    e = vel_error(b.get_state_f64(), a.get_state_f64(), s)
-    assert e < 1e-9, e
-    # the graph runs only the iterations it needs; eager launch runs all
-    assert a.launches_per_step() < b.launches_per_step()
+    for res in (0, 1):   # streamed CR loop (a conditional WHILE node) / island-resident CR
+        a = nsn.Solver(s, precision=nsn.NSN_FP64, use_graph=1, cr_resident=res, **PRM)
+        b = nsn.Solver(s, precision=nsn.NSN_FP64, use_graph=0, cr_resident=res, **PRM)
+        ra, rb = a.step(), b.step()
+        assert ra["newton_done"] == rb["newton_done"]
+        assert np.array_equal(a.island_stats()["stopped_at"], b.island_stats()["stopped_at"])
+        e = vel_error(b.get_state_f64(), a.get_state_f64(), s)
+        assert e < 1e-9, e
+        if res == 0:
+            # the graph runs only the CR iterations it needs; eager launch runs all
+            assert a.launches_per_step() < b.launches_per_step()
+        else:
+            # no CR loop of kernels at all: one resident launch per Newton iteration
+            assert a.launches_per_step() <= b.launches_per_step()
 
 
 def test_island_stop_device_copy_and_clear_warm_start(orc):
