@@ -1812,8 +1812,8 @@ constexpr int RES_NW = RES_THREADS / 32;
 constexpr int RES_G = 8;      // lanes per body in the J^T z gather
 constexpr int RES_KR = 3;     // entries per lane kept in registers between the gather and t_e = J_e y_b
 constexpr int RES_MAXI = 32;  // islands per group (one lane each in the scalar warp)
-constexpr int RES_TASK = 128; // rows per reduction task (a piece of one island's contact or joint rows)
-constexpr int RES_MAXT = 2 * RES_MAXI + 16;   // reduction tasks per group (groups of at most 2048 rows)
+constexpr int RES_TASK = 64;  // rows per task (a piece of one island's contact or joint rows)
+constexpr int RES_MAXT = 2 * RES_MAXI + 32;   // tasks per group (groups of at most 2048 rows)
 
 __host__ __device__ inline int res_pad(int n) { return (n + 3) & ~3; }
 
@@ -1826,7 +1826,7 @@ struct alignas(2 * sizeof(T)) RV2 { T a, b; };
 // byte offsets of the arrays of the shared-memory image of one group: RR rows,
 // RE entries, RB bodies, RES_MAXI islands (the same on host and device)
 struct ResLayout {
-  size_t rv, jA, bm, bn, jB, p, x, Az, prod, t, part, alpha, beta, dbl, isT, le, risl, erow, seg, bisl, isl, task,
+  size_t rv, jA, bm, bn, jB, p, x, Az, t, part, alpha, beta, isT, le, risl, erow, seg, bisl, isl, task,
       ctl, total;
 };
 
@@ -1849,13 +1849,11 @@ __host__ __device__ inline ResLayout res_layout(int RR, int RE, int RB) {
   L.p = take(sizeof(T) * rr, sizeof(T));
   L.x = take(sizeof(T) * rr, sizeof(T));
   L.Az = take(sizeof(T) * rr, sizeof(T));
-  L.prod = take(sizeof(T) * 5 * rr, sizeof(T));
   L.t = take(sizeof(T) * re, sizeof(T));
   L.part = take(sizeof(T) * 5 * RES_MAXT, sizeof(T));
   L.alpha = take(sizeof(T) * RES_MAXI, sizeof(T));
   L.beta = take(sizeof(T) * RES_MAXI, sizeof(T));
-  L.dbl = take(sizeof(double) * RES_MAXI, sizeof(double));
-  L.isT = take(sizeof(T) * 3 * RES_MAXI, sizeof(T));
+  L.isT = take(sizeof(T) * 4 * RES_MAXI, sizeof(T));
   L.le = take(sizeof(int2) * rr, sizeof(int2));
   L.risl = take(sizeof(int) * rr, sizeof(int));
   L.erow = take(sizeof(int) * re, sizeof(int));
@@ -1875,9 +1873,8 @@ template <typename T>
 struct ResSmem {
   RV4<T> *rv, *jA, *bm, *bn;
   RV2<T> *jB;
-  T *p, *x, *Az, *prod, *t, *part, *alpha, *beta;   // part: [5][RES_MAXT] task sums
-  T *r02f, *eta2, *res_prev;                    // [RES_MAXI] per island: stop thresholds, ||r||_P^2 of the last iteration
-  double *rho_prev;                             // [RES_MAXI] 1 / rho of the last iteration
+  T *p, *x, *Az, *t, *part, *alpha, *beta;   // part: [5][RES_MAXT] task sums
+  T *r02f, *eta2, *res_prev, *rho_prev;        // [RES_MAXI] per island: stop thresholds, ||r||_P^2 and rho of the last iteration
   int2 *le;                                     // local entries of the two sides of each row (-1: none)
   int *risl, *erow, *seg, *bisl;                // island of each row, row of each entry, body segments, island of each body
   int *act, *kdone, *cr0, *ncr, *jr0, *njr, *ient, *ibod, *ib0, *it0, *it1;   // [RES_MAXI] per island
@@ -1897,14 +1894,12 @@ __device__ inline ResSmem<T> res_carve(unsigned char *base, int RR, int RE, int 
   S.p = reinterpret_cast<T *>(base + L.p);
   S.x = reinterpret_cast<T *>(base + L.x);
   S.Az = reinterpret_cast<T *>(base + L.Az);
-  S.prod = reinterpret_cast<T *>(base + L.prod);
   S.t = reinterpret_cast<T *>(base + L.t);
   S.part = reinterpret_cast<T *>(base + L.part);
   S.alpha = reinterpret_cast<T *>(base + L.alpha);
   S.beta = reinterpret_cast<T *>(base + L.beta);
-  S.rho_prev = reinterpret_cast<double *>(base + L.dbl);
   T *ts = reinterpret_cast<T *>(base + L.isT);
-  S.r02f = ts; S.eta2 = ts + RES_MAXI; S.res_prev = ts + 2 * RES_MAXI;
+  S.r02f = ts; S.eta2 = ts + RES_MAXI; S.res_prev = ts + 2 * RES_MAXI; S.rho_prev = ts + 3 * RES_MAXI;
   S.le = reinterpret_cast<int2 *>(base + L.le);
   S.risl = reinterpret_cast<int *>(base + L.risl);
   S.erow = reinterpret_cast<int *>(base + L.erow);
@@ -1938,11 +1933,16 @@ __device__ __forceinline__ T res_dot6(const T *J, const T *y) {
 // The CR scalars of island li at iteration k from its task sums (the
 // recurrence and stop rules of k_cr_scalars_isl).  Returns false when the
 // island's CR stops.  The sums are T values, and so are the stop thresholds:
-// the stop tests compare in T (in FP32 they are exact: a single-precision value
-// and its FP64 image order the same way).  beta, ApTPAp and alpha are FP64;
-// in the FP32 build one FP64 reciprocal of rho * ApTPAp gives both alpha =
-// rho / ApTPAp and 1 / rho for the next iteration's beta, the FP64 build takes
-// the two divisions as they are.
+// the stop tests compare in T (in FP32 they are exact: a single-precision
+// value and its FP64 image order the same way).  ApTPAp = d2 + 2 beta d3 +
+// beta^2 d5, the recurrence that cancels, is FP64 in both builds.  In the
+// FP32 build beta and alpha are what the update applies, FP32 values: beta =
+// rho / rho_prev and alpha = rho / ApTPAp are correctly rounded FP32 divisions
+// of FP32-exact operands (rho and rho_prev are FP32 sums), and ApTPAp is taken
+// with that FP32 beta, i.e. for the Ap the update actually forms; the FP64
+// build divides in FP64 as the streamed kernels do.  (One FP64 instruction
+// costs GB300's narrow FP64 pipe a full warp slot, and this step runs once per
+// CR iteration on the critical path of the group.)
 template <typename T>
 __device__ __forceinline__ bool res_scalars(const ResSmem<T> &S, int li, int k) {
   T a[5] = {T(0), T(0), T(0), T(0), T(0)};
@@ -1954,33 +1954,33 @@ __device__ __forceinline__ bool res_scalars(const ResSmem<T> &S, int li, int k) 
   const T rp2 = S.res_prev[li];
   bool st = rp2 < T(0) || cur2 <= S.r02f[li] || (k > 0 && cur2 > rp2) || cur2 <= S.eta2[li];
   S.res_prev[li] = cur2;
-  double beta = 0.0, apap = double(a[1]);
+  const T rho = a[0], rho_prev = S.rho_prev[li];
+  T beta = T(0);
+  double apap = double(a[1]);
   if (k > 0) {
-    const double irp = S.rho_prev[li];           // 1 / rho of the previous iteration
-    if (!(a[0] > T(0)) || !(irp > 0.0)) st = true;
+    if (!(rho > T(0)) || !(rho_prev > T(0))) st = true;
     else {
-      beta = double(a[0]) * irp;
-      apap = double(a[1]) + 2.0 * beta * double(a[2]) + beta * beta * double(a[4]);
+      beta = rho / rho_prev;
+      const double b = double(beta);
+      apap = double(a[1]) + 2.0 * b * double(a[2]) + b * b * double(a[4]);
     }
   }
-  if (st || !(apap > 0.0)) {
+  T alpha = T(0);
+  if (!st && apap > 0.0) {
+    const T ap = T(apap);
+    if (ap > T(0)) alpha = rho / ap;
+    else st = true;                           // ApTPAp below the range of T
+  } else {
+    st = true;
+  }
+  if (st) {
     S.act[li] = 0;
     S.kdone[li] = k;
     return false;
   }
-  const double d0 = double(a[0]);
-  double alpha, inv_rho;
-  if constexpr (std::is_same<T, float>::value) {
-    const double rc = 1.0 / (d0 * apap);
-    alpha = d0 * (d0 * rc);
-    inv_rho = apap * rc;
-  } else {
-    alpha = d0 / apap;
-    inv_rho = 1.0 / d0;
-  }
-  S.rho_prev[li] = a[0] > T(0) ? inv_rho : -1.0;  // rho <= 0: the next iteration stops
-  S.alpha[li] = cr_scalar<T>(alpha, float(alpha));
-  S.beta[li] = cr_scalar<T>(beta, float(beta));
+  S.rho_prev[li] = rho;
+  S.alpha[li] = alpha;
+  S.beta[li] = beta;
   return true;
 }
 
@@ -1990,7 +1990,6 @@ __global__ void __launch_bounds__(RES_THREADS) k_cr_resident(Dev<T> D, int M) {
   extern __shared__ __align__(32) unsigned char res_raw[];
   const ResSmem<T> S = res_carve<T>(res_raw, D.res_rows, D.res_ent, D.res_bod);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int rr = res_pad(D.res_rows);
   const T eps = D.epsT;
   const int gc = 3 * D.nc;
   for (;;) {
@@ -2016,7 +2015,7 @@ __global__ void __launch_bounds__(RES_THREADS) k_cr_resident(Dev<T> D, int M) {
       S.r02f[tid] = T(fl * fl * r0 * r0);
       S.eta2[tid] = D.cr_tol ? T(D.isl.eta[is] * D.isl.eta[is] * r0 * r0) : T(-1);
       S.res_prev[tid] = r0 == 0.0 ? T(-1) : T(0);   // r0 == 0: the island stops at once
-      S.rho_prev[tid] = 0.0;
+      S.rho_prev[tid] = T(0);
     }
     for (int b = tid; b < nb; b += RES_THREADS) {
       const int gb = b0 + b;
@@ -2116,28 +2115,22 @@ __global__ void __launch_bounds__(RES_THREADS) k_cr_resident(Dev<T> D, int M) {
         }
       }
       __syncthreads();
-      // Az = sum of the row's t_e + (C_ii + eps) z and the five products of k_row_pass_isl
-      for (int r = tid; r < nrow; r += RES_THREADS) {
-        if (!S.act[S.risl[r]]) continue;
-        const int2 le = S.le[r];
-        const T t0 = le.x >= 0 ? S.t[le.x] : T(0);
-        const T t1 = le.y >= 0 ? S.t[le.y] : T(0);
-        const RV4<T> v = S.rv[r];               // z, P, Ap, C_ii + eps
-        const T az = (t0 + t1) + v.d * v.a;
-        S.Az[r] = az;
-        const T paz = v.b * az;
-        S.prod[r] = v.a * az; S.prod[rr + r] = az * paz; S.prod[2 * rr + r] = paz * v.c;
-        S.prod[3 * rr + r] = v.a * v.a / v.b; S.prod[4 * rr + r] = v.c * v.b * v.c;
-      }
-      __syncthreads();
-      // task sums (a task: up to RES_TASK rows of one island), one warp per task
+      // Az = t_e0 + t_e1 + (C_ii + eps) z and the five products of
+      // k_row_pass_isl, summed per task (one warp per task, fixed order)
       for (int tk = warp; tk < ntask; tk += RES_NW) {
         if (!S.act[S.tisl[tk]]) continue;
         T a[5] = {T(0), T(0), T(0), T(0), T(0)};
         const int r1 = S.tr0[tk] + S.tn[tk];
-        for (int r = S.tr0[tk] + lane; r < r1; r += 32)
-#pragma unroll
-          for (int q = 0; q < 5; q++) a[q] += S.prod[q * rr + r];
+        for (int r = S.tr0[tk] + lane; r < r1; r += 32) {
+          const int2 le = S.le[r];
+          const T t0 = le.x >= 0 ? S.t[le.x] : T(0);
+          const T t1 = le.y >= 0 ? S.t[le.y] : T(0);
+          const RV4<T> v = S.rv[r];             // z, P, Ap, C_ii + eps
+          const T az = (t0 + t1) + v.d * v.a;
+          S.Az[r] = az;
+          const T paz = v.b * az;
+          a[0] += v.a * az; a[1] += az * paz; a[2] += paz * v.c; a[3] += v.a * v.a / v.b; a[4] += v.c * v.b * v.c;
+        }
 #pragma unroll
         for (int q = 0; q < 5; q++) {
 #pragma unroll

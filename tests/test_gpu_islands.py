@@ -231,9 +231,18 @@ def test_mixed_bin_parity(orc):
     assert np.array_equal(io["stopped_at"][rigid_isl], ig["stopped_at"][rigid_isl])
     so, sg = o.get_state(), g.get_state_f64()
     rig = s["kind"] == 0
-    dv = np.linalg.norm(sg["vel"][rig] - so["vel"][rig]) / (np.linalg.norm(so["vel"][rig]) + H * G)
-    dw = np.linalg.norm(sg["omega"][rig] - so["omega"][rig]) / (np.linalg.norm(so["omega"][rig]) + 1e-3)
-    assert dv < 1e-7 and dw < 1e-6, (dv, dw)
+    # boxes, in the mass-weighted (kinetic energy) norm of the other parity
+    # tests: islands that converged to FP64 rounding, islands that did not
+    # (their last iterate depends on the summation order) to a looser bound
+    conv = (io["stopped_at"] >= 0)[bi]
+    for sel, tol in ((rig & conv, TOL64), (rig & ~conv, 1e-4)):
+        if not sel.any():
+            continue
+        z = lambda a: np.where(sel[:, None], a, 0.0)
+        num = mass_norm(so, s, z(sg["vel"] - so["vel"]), z(sg["omega"] - so["omega"]))
+        den = mass_norm(so, s, z(so["vel"]), z(so["omega"])) + H * G * np.sqrt(s["mass"][sel].astype(np.float64).sum())
+        print("boxes", int(sel.sum()), "velocity difference", num / den)
+        assert num / den < tol
     par = ~rig
     dp = np.linalg.norm(sg["vel"][par] - so["vel"][par]) / (np.linalg.norm(so["vel"][par]) + H * G)
     print("ball velocity difference", dp)
