@@ -22,7 +22,8 @@ trajectory advances from the seeded start state (no reset between steps).
             ablations of Sec. 7 (min-map NCP; r = h^2 and r = 1 instead of the
             effective-mass r), each on the first step after a reset with the
             zero start (compare after_reset_zero): on the advancing trajectory
-            the min-map variant diverges, in the FP64 oracle as well
+            the min-map variant diverges, in the FP64 oracle as well; and the
+            headline arm with the back-tracking line search of Sec. 8.1
   e2e       converged env-steps/s through the C ABI with host buffers: host->
             device copy of the state, the step, device->host copy of the state
             (the state makes that round trip every step)
@@ -282,12 +283,13 @@ def run_reference(args, rank, world):
 
 EAGER = False   # --eager: launch kernel by kernel instead of the CUDA graph (for profilers)
 RESIDENT = 1    # --resident 0: every island in the streamed CR loop
+CR_TOL = 0      # --cr-tol 1: CR of a Newton iteration also stops at the forcing term min(0.1, m/m0)
 
 
-def make_solver(nsn, s, stream, newton, cr, cone, warm=0, params=None, ncp=0, rscale=2):
+def make_solver(nsn, s, stream, newton, cr, cone, warm=0, params=None, ncp=0, rscale=2, ls=0):
     g = nsn.Solver(s, stream=stream.cuda_stream, newton_iters=newton, cr_iters=cr, tol_rel=TOL, island_stop=1,
                    cone_project=cone, precision=nsn.NSN_FP32, use_graph=0 if EAGER else 1, ncp=ncp, rscale=rscale,
-                   cr_resident=RESIDENT)
+                   cr_resident=RESIDENT, cr_tol_mode=CR_TOL, line_search=ls)
     if params is not None:
         nsn.nsn_mlp_set_params(g.ctx, params)
     g.set_warm_start(warm)
@@ -445,21 +447,22 @@ def run_ours(args, rank, world, local_rank):
         # the other arms, same trajectory and accounting
         arms = {}
         if args.arms:
-            # (name, cone projection, warm start, reset every step, NCP function, r strategy)
-            for name, cone, wm, reset, ncp, rs in (("plain_zero_start", 1, nsn.NSN_WARM_ZERO, False, 0, 2),
-                                                   ("as_printed", 0, nsn.NSN_WARM_ZERO, False, 0, 2),
-                                                   ("prev_warm_start", 1, nsn.NSN_WARM_PREV, False, 0, 2),
-                                                   ("after_reset_zero", 1, nsn.NSN_WARM_ZERO, True, 0, 2),
-                                                   ("after_reset_learned", 1, nsn.NSN_WARM_LEARNED, True, 0, 2),
-                                                   ("ablation_min_map", 1, nsn.NSN_WARM_ZERO, True, 1, 2),
-                                                   ("ablation_r_h2", 1, nsn.NSN_WARM_ZERO, True, 0, 1),
-                                                   ("ablation_r_identity", 1, nsn.NSN_WARM_ZERO, True, 0, 0)):
-                if wm == warm_names[warm] and not reset and cone == 1 and ncp == 0 and rs == 2:
+            # (name, cone projection, warm start, reset every step, NCP function, r strategy, line search)
+            for name, cone, wm, reset, ncp, rs, ls in (("line_search", 1, warm_names[warm], False, 0, 2, 1),
+                                                   ("plain_zero_start", 1, nsn.NSN_WARM_ZERO, False, 0, 2, 0),
+                                                   ("as_printed", 0, nsn.NSN_WARM_ZERO, False, 0, 2, 0),
+                                                   ("prev_warm_start", 1, nsn.NSN_WARM_PREV, False, 0, 2, 0),
+                                                   ("after_reset_zero", 1, nsn.NSN_WARM_ZERO, True, 0, 2, 0),
+                                                   ("after_reset_learned", 1, nsn.NSN_WARM_LEARNED, True, 0, 2, 0),
+                                                   ("ablation_min_map", 1, nsn.NSN_WARM_ZERO, True, 1, 2, 0),
+                                                   ("ablation_r_h2", 1, nsn.NSN_WARM_ZERO, True, 0, 1, 0),
+                                                   ("ablation_r_identity", 1, nsn.NSN_WARM_ZERO, True, 0, 0, 0)):
+                if wm == warm_names[warm] and not reset and cone == 1 and ncp == 0 and rs == 2 and not ls:
                     continue
                 if wm == nsn.NSN_WARM_LEARNED and params is None:
                     arms[name] = {"unavailable": "no trained weights (paper_1907_04587_gb300/weights)"}
                     continue
-                ga = make_solver(nsn, s, stream, newton, cr, cone=cone, warm=wm, params=params, ncp=ncp, rscale=rs)
+                ga = make_solver(nsn, s, stream, newton, cr, cone=cone, warm=wm, params=params, ncp=ncp, rscale=rs, ls=ls)
                 try:
                     r = measure_arm(nsn, torch, ga, s, st0, stream, args.steps, args.warmup, reset=reset)
                 except nsn.NSNError as e:      # the method failing on this variant is a result
@@ -505,6 +508,7 @@ def run_ours(args, rank, world, local_rank):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": args.workload, "description": W["desc"], "n_envs": n_envs, "bodies": g.nb,
                    "rows": sz["rows"], "islands": main_arm["islands"], "newton_cap": newton, "cr_iters": cr,
+                   "cr_stop": ("forcing term min(0.1, m/m0), floor, growth, cap" if CR_TOL else "floor, growth, cap"),
                    "tol_rel": TOL, "cone_projection": True, "warm_start": warm_note,
                    "device_bytes": sz["device_bytes"], "launch": "kernel by kernel" if EAGER else
                    "one CUDA graph per step (Newton loop as a conditional WHILE node)",
@@ -546,10 +550,13 @@ def main():
                     help="1: launch kernel by kernel (ncu cannot profile kernels of graphs with conditional nodes)")
     ap.add_argument("--resident", type=int, default=1,
                     help="0: no island-resident CR (every island in the streamed CR loop of four kernels per iteration)")
+    ap.add_argument("--cr-tol", type=int, default=0,
+                    help="1: inexact Newton, CR stops at ||r||_P <= min(0.1, merit/merit0) ||r0||_P (cap --cr)")
     args = ap.parse_args()
-    global EAGER, RESIDENT
+    global EAGER, RESIDENT, CR_TOL
     EAGER = bool(args.eager)
     RESIDENT = int(args.resident)
+    CR_TOL = int(args.cr_tol)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

@@ -102,6 +102,13 @@ typedef struct {
                              island in the streamed CR loop */
   int32_t res_max_rows;   /* row cap of a resident island and of a group of them, at most 2048
                              (default 384; <= 0: 384) */
+  int32_t line_search;    /* 1: back-tracking line search on each Newton step (Sec. 8.1): the
+                             trials t = 1, 1/2, 1/4, 1/8, 1/16 (each a merit evaluation at
+                             lambda + t dlambda, u + t du), the first whose FP64 merit is
+                             below the current iterate's is taken, else the damped step t =
+                             damping; per island in island mode.  0 (default, the paper's
+                             results): the damped step */
+  int32_t reserved;       /* 0 */
 } nsn_config;
 
 /* Fills the paper's defaults: h = 1/60, g = (0, 0, -9.81), 4 x 20 iterations,

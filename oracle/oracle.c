@@ -1123,6 +1123,64 @@ static double zero_iterate_merit(orc_ctx *c, orc_work *w) {
   return m;
 }
 
+/* Back-tracking line search on the Newton step (Sec. 8.1: the step length is
+ * reduced until the merit decreases; Reading: t = 1, 1/2, 1/4, 1/8, 1/16, the
+ * first trial whose merit is below the merit of the current iterate is taken,
+ * and when none is, the damped step t = damping).  The trial iterate is
+ * lambda + t dl (projected onto the cone when cone_project is on) and u + t du,
+ * with the positions from u.  In island mode each island keeps the first t at
+ * which its own merit decreased (A is block diagonal by island, so this is the
+ * search of each island alone); stopped islands keep their iterate.  On
+ * return lam and w->u hold the accepted iterate. */
+static void line_search(orc_ctx *c, int isl, double mn, double *lam, orc_work *w) {
+  const int R = c->R, D = c->D, ni = c->ni;
+  double *lam0 = malloc(sizeof(double) * (R + 1)), *u0 = malloc(sizeof(double) * (D + 1));
+  double *lt = malloc(sizeof(double) * (R + 1)), *ut = malloc(sizeof(double) * (D + 1));
+  double *tacc = malloc(sizeof(double) * (ni + 1)), *mcur = malloc(sizeof(double) * (ni + 1));
+  memcpy(lam0, lam, sizeof(double) * R);
+  memcpy(u0, w->u, sizeof(double) * D);
+  /* merits of the current iterate: c->isl_acc (island mode) or mn */
+  for (int i = 0; i < ni; i++) { tacc[i] = -1.0; mcur[i] = c->isl_acc[i]; }
+  double tg = -1.0;
+  double ts = 1.0;
+  for (int trial = 0; trial < 5; trial++, ts *= 0.5) {
+    for (int i = 0; i < R; i++) lt[i] = lam0[i] + ts * w->dl[i];
+    if (c->p.cone_project) cone_project(c, lt, isl ? c->isl_stop : NULL);
+    for (int k = 0; k < D; k++) ut[k] = u0[k] + ts * w->du[k];
+    positions_from_u(c, ut);
+    eval_rows(c, ut, lt);
+    compute_g(c, ut, lt, w->zb);
+    if (isl) {
+      island_merits(c, c->isl_acc);
+      for (int i = 0; i < ni; i++)
+        if (tacc[i] < 0.0 && c->isl_stop[i] < 0 && c->isl_acc[i] < mcur[i]) tacc[i] = ts;
+    } else if (tg < 0.0 && merit(c) < mn) {
+      tg = ts;
+      break;
+    }
+  }
+  const double td = c->p.damping;
+  if (!isl) {
+    const double t = tg > 0.0 ? tg : td;
+    for (int i = 0; i < R; i++) lam[i] = lam0[i] + t * w->dl[i];
+    if (c->p.cone_project) cone_project(c, lam, NULL);
+    for (int k = 0; k < D; k++) w->u[k] = u0[k] + t * w->du[k];
+  } else {
+    for (int i = 0; i < R; i++) {
+      const int is = c->row_isl[i];
+      const double t = tacc[is] > 0.0 ? tacc[is] : td;
+      lam[i] = lam0[i] + t * w->dl[i];
+    }
+    if (c->p.cone_project) cone_project(c, lam, c->isl_stop);
+    for (int b = 0; b < c->nb; b++) {
+      const int is = c->body_isl[b];
+      const double t = tacc[is] > 0.0 ? tacc[is] : td;
+      for (int k = c->dof[b]; k < c->dof[b + 1]; k++) w->u[k] = u0[k] + t * w->du[k];
+    }
+  }
+  free(lam0); free(u0); free(lt); free(ut); free(tacc); free(mcur);
+}
+
 /* Runs Newton iterations; if stop_at >= 0, returns after evaluating the rows,
  * g, H~ and b at iteration stop_at without solving. */
 static int newton(orc_ctx *c, const double *lambda0, int stop_at, orc_stats *st, orc_work *w, double *lam_out) {
@@ -1188,9 +1246,13 @@ static int newton(orc_ctx *c, const double *lambda0, int stop_at, orc_stats *st,
           for (int k = c->dof[b]; k < c->dof[b + 1]; k++) w->du[k] = 0.0;
     memcpy(w->uprev, w->u, sizeof(double) * c->D);
     memcpy(c->rows_prev, c->rows, sizeof(orc_row) * c->R);
-    for (int i = 0; i < c->R; i++) lam[i] += t * w->dl[i];
-    if (c->p.cone_project) cone_project(c, lam, isl ? c->isl_stop : NULL);
-    for (int k = 0; k < c->D; k++) w->u[k] += t * w->du[k];
+    if (c->p.line_search)
+      line_search(c, isl, mn, lam, w);
+    else {
+      for (int i = 0; i < c->R; i++) lam[i] += t * w->dl[i];
+      if (c->p.cone_project) cone_project(c, lam, isl ? c->isl_stop : NULL);
+      for (int k = 0; k < c->D; k++) w->u[k] += t * w->du[k];
+    }
     positions_from_u(c, w->u);
   }
   if (stop_at < 0) {

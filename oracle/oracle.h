@@ -85,6 +85,11 @@ typedef struct {
                                island whose merit reaches tol_rel times its own zero-iterate
                                merit keeps its u and lambda from then on; the step ends when
                                every island has stopped or after newton_iters */
+  int32_t line_search;      /* 1: back-tracking line search of Sec. 8.1 on the Newton step:
+                               t = 1, 1/2, 1/4, 1/8, 1/16, the first whose merit is below the
+                               merit of the current iterate (per island in island mode);
+                               none: the damped step t = damping.  0 (the paper's results):
+                               always the damped step */
 } orc_params;
 
 typedef struct {

@@ -418,6 +418,11 @@ void carve(Arena &A, Dev<T> &D, const Layout &L, int nb) {
   D.isl.alpha = A.take<double>(ni); D.isl.beta = A.take<double>(ni);
   D.isl.alpha_f = A.take<float>(ni); D.isl.beta_f = A.take<float>(ni);
   D.isl.stop = A.take<int>(ni); D.isl.crdone = A.take<int>(ni);
+  D.isl.tacc = A.take<double>(ni);
+  // line search: du, u and lambda at the head of the Newton iteration, dlambda
+  for (int k = 0; k < 6; k++) { D.rdu[k] = tk(L.nr); D.ru0[k] = tk(L.nr); }
+  for (int k = 0; k < 3; k++) { D.pdu[k] = tk(L.np); D.pu0[k] = tk(L.np); }
+  D.lam0 = tk(L.R); D.xs = tk(L.R);
   D.fl_row = A.take<unsigned char>(size_t(L.R) / BLOCK + 1);
   D.fl_br = A.take<unsigned char>(size_t(L.nr) / (BLOCK / 16) + 1);
   D.fl_bp = A.take<unsigned char>(size_t(L.np) / (BLOCK / 16) + 1);
@@ -449,6 +454,7 @@ void fill_sizes(Dev<T> &D, const Layout &L, const nsn_config &cfg) {
   D.ni = L.ni;
   D.isl_on = cfg.island_stop ? 1 : 0;
   D.cone = cfg.cone_project ? 1 : 0;
+  D.ls = cfg.line_search ? 1 : 0;
   // grid-stride kernels get at most one wave: SMs x resident blocks per SM of
   // the kernel (so that no partial second wave trails the first)
   int dev = 0, nsm = 152;
@@ -735,24 +741,26 @@ struct Launcher {
     if (!nb) return;
     if (D.isl_on) {
       if (mode == RM_RHS) k_row_pass_isl<T, RM_RHS><<<nb, BLOCK, 0, st>>>(D, force);
+      else if (mode == RM_MERIT) k_row_pass_isl<T, RM_MERIT><<<nb, BLOCK, 0, st>>>(D, force);
       else k_row_pass_isl<T, RM_APPLY><<<nb, BLOCK, 0, st>>>(D, force);
     } else if (mode == RM_RHS) k_row_pass<T, RM_RHS><<<nb, BLOCK, 0, st>>>(D, force);
+    else if (mode == RM_MERIT) k_row_pass<T, RM_MERIT><<<nb, BLOCK, 0, st>>>(D, force);
     else k_row_pass<T, RM_APPLY><<<nb, BLOCK, 0, st>>>(D, force);
     count++;
   }
   // merit of an evaluation (island mode: the per-island pass first); the
   // k_merit launch itself is counted by the callers
-  void merit(int n, int force) {
+  void merit(int n, int force, double trial_t = 0.0) {
     if (D.isl_on) {
       if (!force) {   // a Newton iteration: new work lists
         k_list_reset<T><<<1, 1, 0, st>>>(D);
         count++;
         if (D.res_on) cudaMemsetAsync(D.gact, 0, size_t(D.ngroups), st);
       }
-      k_merit_isl<T><<<cdiv(std::max(D.ni, 1), 256), 256, 0, st>>>(D, n, force);
+      k_merit_isl<T><<<cdiv(std::max(D.ni, 1), 256), 256, 0, st>>>(D, n, force, trial_t);
       count++;
     }
-    k_merit<T><<<1, RED_THREADS, 0, st>>>(D, n, force);
+    k_merit<T><<<1, RED_THREADS, 0, st>>>(D, n, force, trial_t);
   }
   void eval(int buf, int force) {
     if (D.nc) { k_eval_contacts<T><<<cdiv(D.nc, 128), 128, 0, st>>>(D, buf, force); count++; }
@@ -865,8 +873,31 @@ struct Launcher {
     }
     if (D.R && M > 0 && D.streamed) cr_begin(M);
   }
+  // back-tracking line search on the Newton step (Sec. 8.1): five trials t = 1,
+  // 1/2, 1/4, 1/8, 1/16, each a merit evaluation at the trial iterate (rows into
+  // the next iteration's entry buffer, no geometric stiffness, |h|^2 only in the
+  // row pass), then the accepted step (or the damping) committed
+  void line_search() {
+    body(BM_UPDATE, D.x, IT_DEV, IT_DEV, 0);   // du and the iterate kept, nothing committed
+    const int nl = D.nr + D.np + D.R;
+    const int gl = clampb(cdiv(std::max(nl, 1), 256));
+    k_ls_begin<T><<<D.nblk_upd, BLOCK, 0, st>>>(D);
+    count++;
+    T t = T(1);
+    for (int j = 0; j < 5; j++, t *= T(0.5)) {
+      k_ls_set<T><<<gl, 256, 0, st>>>(D, t, 0);
+      eval(IT_DEV_NEXT, 0);
+      body(BM_RESIDUAL, D.lam, IT_DEV_NEXT, 0, 0);
+      rows(RM_MERIT, 0);
+      merit(IT_TRIAL, 1, double(t));
+      count += 2;
+    }
+    k_ls_set<T><<<gl, 256, 0, st>>>(D, T(0), 1);
+    count++;
+  }
   void newton_tail(int N) {
-    newton_update(IT_DEV);
+    if (D.ls && D.R) line_search();
+    else newton_update(IT_DEV);
     k_newton_next<T><<<1, 1, 0, st>>>(D, N);
     count++;
   }
@@ -1167,7 +1198,8 @@ bool valid_cfg(const nsn_config *cfg) {
          cfg->damping > 0 && cfg->damping <= 1 && cfg->eps >= 0 && cfg->tol_rel >= 0 &&
          (cfg->precision == NSN_FP32 || cfg->precision == NSN_FP64) && (cfg->ncp == 0 || cfg->ncp == 1) &&
          cfg->rscale >= 0 && cfg->rscale <= 2 && (cfg->cone_project == 0 || cfg->cone_project == 1) &&
-         (cfg->island_stop == 0 || cfg->island_stop == 1) && (cfg->cr_resident == 0 || cfg->cr_resident == 1);
+         (cfg->island_stop == 0 || cfg->island_stop == 1) && (cfg->cr_resident == 0 || cfg->cr_resident == 1) &&
+         (cfg->line_search == 0 || cfg->line_search == 1);
 }
 
 template <typename T>
@@ -1610,6 +1642,7 @@ void nsn_default_config(nsn_config *cfg) {
   cfg->island_stop = 0;
   cfg->cr_resident = 1;
   cfg->res_max_rows = 384;
+  cfg->line_search = 0;
 }
 
 nsn_status nsn_create(const nsn_config *cfg, void *stream, nsn_ctx **out) {

@@ -33,7 +33,7 @@ constexpr int BLOCK = 256;
 constexpr int NPART = 5;  // partials per block in the row passes
 
 enum BodyMode { BM_RESIDUAL = 0, BM_APPLY = 1, BM_UPDATE = 2 };
-enum RowMode { RM_RHS = 0, RM_APPLY = 1 };
+enum RowMode { RM_RHS = 0, RM_APPLY = 1, RM_MERIT = 2 };   // RM_MERIT: |h|^2 only (line search)
 
 struct Flags {
   int newton_stop;   // set when merit <= tol * merit0: later kernels of the step return
@@ -62,6 +62,11 @@ struct Flags {
 
 // iteration index / entry buffer taken from Flags::newton_n
 constexpr int IT_DEV = -100;
+// entry buffer of the next Newton iteration (line-search trials: this
+// iteration's entries stay for the geometric stiffness of the next)
+constexpr int IT_DEV_NEXT = -101;
+// k_merit_isl / k_merit: a line-search trial
+constexpr int IT_TRIAL = -6;
 // k_merit: evaluation at the returned iterate
 constexpr int IT_FINAL = -3;
 
@@ -81,6 +86,7 @@ struct IslState {
   float *alpha_f, *beta_f;
   int *stop;                 // Newton iteration at which the island stopped, -1 while iterating
   int *crdone;               // 1: the island's CR is finished in this Newton iteration
+  double *tacc;              // line search: accepted step of this Newton iteration (-1: none yet)
 };
 
 // FP64 scalars kept on the device
@@ -98,6 +104,7 @@ struct Scalars {
   double isl_m2;        // island mode: sum of the islands' merit^2 (k_merit_isl)
   double merit_warm;    // merit at the warm-started iterate (u = 0, lambda^0)
   double merit_warm2;   // merit at the second candidate (learned, after previous-step)
+  double ls_t;          // line search, global mode: accepted step (-1: none yet)
   int warm_rejected;    // 1 if the warm start was worse than the zero start (island
                         // mode: the number of islands where it was)
 };
@@ -164,6 +171,10 @@ struct Dev {
   int ni;            // number of islands
   int isl_on;        // 1: per-island Newton stop, warm-start acceptance and CR scalars
   int cone;          // 1: project contact multipliers onto the friction cone after each update
+  int ls;            // 1: back-tracking line search on the Newton step (Sec. 8.1)
+  T *rdu[6], *pdu[3];            // line search: du of this Newton iteration
+  T *ru0[6], *pu0[3], *lam0;     // line search: u and lambda at its head
+  T *xs;                         // line search: dlambda of this Newton iteration
   int *risl;         // island of each row
   int *bisl_r, *bisl_p;  // island of each rigid body / particle
   int *cabi;         // ABI index of each (island-ordered) contact: per-contact
@@ -673,6 +684,7 @@ template <typename T>
 __global__ void k_eval_contacts(Dev<T> D, int buf, int force) {
   if (!force && D.fl->newton_stop) return;
   if (buf == IT_DEV) buf = D.fl->newton_n & 1;
+  else if (buf == IT_DEV_NEXT) buf = (D.fl->newton_n + 1) & 1;
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= D.nc) return;
   if (!force && D.isl_on && D.isl.stop[D.risl[3 * c]] >= 0) return;   // stopped island
@@ -765,6 +777,7 @@ template <typename T>
 __global__ void k_eval_joints(Dev<T> D, int buf, int force) {
   if (!force && D.fl->newton_stop) return;
   if (buf == IT_DEV) buf = D.fl->newton_n & 1;
+  else if (buf == IT_DEV_NEXT) buf = (D.fl->newton_n + 1) & 1;
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= D.nj) return;
   if (!force && D.isl_on && D.isl.stop[D.risl[3 * D.nc + 5 * j]] >= 0) return;   // stopped island
@@ -838,6 +851,7 @@ template <typename T>
 __global__ void k_eval_tets(Dev<T> D, int buf, int force) {
   if (!force && D.fl->newton_stop) return;
   if (buf == IT_DEV) buf = D.fl->newton_n & 1;
+  else if (buf == IT_DEV_NEXT) buf = (D.fl->newton_n + 1) & 1;
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= D.nt) return;
   if (!force && D.isl_on && D.isl.stop[D.risl[D.Rpair + 3 * t]] >= 0) return;   // stopped island
@@ -928,6 +942,7 @@ __global__ void __launch_bounds__(BLOCK) k_body_pass(Dev<T> D, const T *__restri
   if (!force && D.fl->newton_stop) return;
   if (newton_it == IT_DEV) newton_it = D.fl->newton_n;
   if (buf == IT_DEV) buf = D.fl->newton_n & 1;
+  else if (buf == IT_DEV_NEXT) buf = (D.fl->newton_n + 1) & 1;
   if (MODE == BM_APPLY && D.fl->cr_stop) return;
   constexpr int KR = 3;
   Acc<T> acc_g2;
@@ -990,7 +1005,10 @@ __global__ void __launch_bounds__(BLOCK) k_body_pass(Dev<T> D, const T *__restri
         for (int k = 0; k < 6; k++) r6[k] = h * s[k] - D.rg[k][b];
         du[0] = r6[0] * im; du[1] = r6[1] * im; du[2] = r6[2] * im;
         sym3v(Si, r6 + 3, du + 3);
-        if (lane == 0) {
+        if (lane == 0 && D.ls) {   // line search: keep du and the iterate; k_ls_set commits
+#pragma unroll
+          for (int k = 0; k < 6; k++) { D.rdu[k][b] = du[k]; D.ru0[k][b] = D.ru[k][b]; }
+        } else if (lane == 0) {
           const T t = D.dampT;
           T u[6];
 #pragma unroll
@@ -1138,6 +1156,11 @@ __global__ void __launch_bounds__(BLOCK) k_body_pass(Dev<T> D, const T *__restri
             const T du = (h * s[k] - D.pg[k][b]) * D.phinv[k][b];
             const T u = D.pu[k][b];
             D.puprev[k][b] = u;
+            if (D.ls) {   // line search: keep du and the iterate; k_ls_set commits
+              D.pdu[k][b] = du;
+              D.pu0[k][b] = u;
+              continue;
+            }
             const T un = u + t * du;
             D.pu[k][b] = un;
             D.px[k][b] = D.px0[k][b] + h * un;
@@ -1219,7 +1242,10 @@ __global__ void __launch_bounds__(BLOCK) k_row_pass(Dev<T> D, int force) {
   if (blockIdx.x < D.nblk_row_pair) {
     const int stride = D.nblk_row_pair * BLOCK;
     for (int i = blockIdx.x * BLOCK + threadIdx.x; i < D.Rpair; i += stride) {
-      if (MODE == RM_RHS) {
+      if (MODE == RM_MERIT) {
+        const T hv = D.hv[i];
+        a[0].add_prod(hv, hv);
+      } else if (MODE == RM_RHS) {
         const T tb = D.t[2 * i] + D.t[2 * i + 1], td = D.t2[2 * i] + D.t2[2 * i + 1];
         const T hv = D.hv[i];
         const T bi = (tb - hv) * ih;
@@ -1252,7 +1278,10 @@ __global__ void __launch_bounds__(BLOCK) k_row_pass(Dev<T> D, int force) {
     for (int t = bid * BLOCK + threadIdx.x; t < D.nt; t += stride) {
       const T *ts = D.t + 2 * rb + 12 * t, *ts2 = D.t2 + 2 * rb + 12 * t;
       const T *c3 = D.c3 + 6 * t;
-      if (MODE == RM_RHS) {
+      if (MODE == RM_MERIT) {
+#pragma unroll
+        for (int k = 0; k < 3; k++) { const T hv = D.hv[rb + 3 * t + k]; a[0].add_prod(hv, hv); }
+      } else if (MODE == RM_RHS) {
         const T cc[3] = {c3[0], c3[1], c3[2]};
 #pragma unroll
         for (int k = 0; k < 3; k++) {
@@ -1329,7 +1358,11 @@ __global__ void __launch_bounds__(BLOCK) k_row_pass_isl(Dev<T> D, int force) {
       if (key >= 0 && (MODE == RM_APPLY ? D.isl.crdone[key] != 0 : (!force && D.isl.stop[key] >= 0))) key = -1;
       const bool v = key >= 0;
       if (!__any_sync(0xffffffffu, v)) continue;   // the whole warp's islands are finished
-      if (MODE == RM_RHS) {
+      if (MODE == RM_MERIT) {
+        T a[1] = {T(0)};
+        if (v) { const T hv = D.hv[i]; a[0] = hv * hv; }
+        warp_runs_add<T, 1>(key, a, D.isl.acc, ni);
+      } else if (MODE == RM_RHS) {
         T a[2] = {T(0), T(0)};
         if (v) {
           const T tb = D.t[2 * i] + D.t[2 * i + 1], td = D.t2[2 * i] + D.t2[2 * i + 1];
@@ -1367,7 +1400,13 @@ __global__ void __launch_bounds__(BLOCK) k_row_pass_isl(Dev<T> D, int force) {
       if (key >= 0 && (MODE == RM_APPLY ? D.isl.crdone[key] != 0 : (!force && D.isl.stop[key] >= 0))) key = -1;
       const bool v = key >= 0;
       if (!__any_sync(0xffffffffu, v)) continue;
-      if (MODE == RM_RHS) {
+      if (MODE == RM_MERIT) {
+        T a[1] = {T(0)};
+        if (v)
+#pragma unroll
+          for (int k = 0; k < 3; k++) { const T hv = D.hv[rb + 3 * t + k]; a[0] += hv * hv; }
+        warp_runs_add<T, 1>(key, a, D.isl.acc, ni);
+      } else if (MODE == RM_RHS) {
         T a[2] = {T(0), T(0)};
         if (v) {
           const T *ts = D.t + 2 * rb + 12 * t, *ts2 = D.t2 + 2 * rb + 12 * t;
@@ -1426,12 +1465,17 @@ __global__ void __launch_bounds__(BLOCK) k_row_pass_isl(Dev<T> D, int force) {
 // island continues to the CR solve of this Newton iteration.
 template <typename T>
 __device__ __forceinline__ bool isl_merit_one(const Dev<T> &D, int i, int n, int force, bool final_eval, double &m2,
-                                              int &active) {
+                                              int &active, double trial_t) {
   const int ni = D.ni;
   double *acc = D.isl.acc;
   const double a = acc[i], bz = acc[ni + i];
   acc[i] = 0.0; acc[ni + i] = 0.0;
   const double mi = sqrt(a);
+  if (n == IT_TRIAL) {   // line search: the first trial below the merit at the head of the iteration
+    if (D.isl.stop[i] < 0 && D.isl.tacc[i] < 0.0 && mi < D.isl.mf[i]) D.isl.tacc[i] = trial_t;
+    m2 += a;
+    return false;
+  }
   if (n == -1) { D.isl.m0[i] = mi; m2 += a; return false; }
   if (n == -2) { D.isl.mw[i] = mi; m2 += a; return false; }
   if (n == -4) { D.isl.mw2[i] = mi; m2 += a; return false; }
@@ -1469,7 +1513,7 @@ __device__ __forceinline__ bool isl_merit_one(const Dev<T> &D, int i, int n, int
 // continues.  At a Newton iteration (n >= 0, no force) the islands whose CR
 // runs are appended to list_isl, the work list of k_cr_scalars_isl.
 template <typename T>
-__global__ void k_merit_isl(Dev<T> D, int n, int force) {
+__global__ void k_merit_isl(Dev<T> D, int n, int force, double trial_t) {
   if (!force && D.fl->newton_stop) return;
   if (n == IT_DEV) n = D.fl->newton_n;
   const bool final_eval = n == IT_FINAL;
@@ -1481,7 +1525,7 @@ __global__ void k_merit_isl(Dev<T> D, int n, int force) {
   // warp-uniform loop: each warp appends its continuing islands with one atomic
   for (int i0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); i0 < ni; i0 += gridDim.x * blockDim.x) {
     const int i = i0 + lane;
-    const bool cont = i < ni && isl_merit_one(D, i, n, force, final_eval, m2, active);
+    const bool cont = i < ni && isl_merit_one(D, i, n, force, final_eval, m2, active, trial_t);
     if (regular) {
       // continuing islands: resident ones to k_cr_resident (marked CR-done for
       // the streaming kernels), the others to the streaming CR loop
@@ -1578,7 +1622,7 @@ __global__ void __launch_bounds__(1024) k_block_lists(Dev<T> D, int all_islands)
 
 // merit of this Newton iteration, Newton stop test, CR forcing term (1 block)
 template <typename T>
-__global__ void __launch_bounds__(RED_THREADS) k_merit(Dev<T> D, int n, int force) {
+__global__ void __launch_bounds__(RED_THREADS) k_merit(Dev<T> D, int n, int force, double trial_t) {
   if (!force && D.fl->newton_stop) return;
   if (n == IT_DEV) n = D.fl->newton_n;
   const bool final_eval = n == IT_FINAL;
@@ -1605,7 +1649,10 @@ __global__ void __launch_bounds__(RED_THREADS) k_merit(Dev<T> D, int n, int forc
     }
   }
   if (threadIdx.x == 0) {
-    if (n == -1) {                                     // zero iterate of a warm-started step
+    if (n == IT_TRIAL) {                               // line-search trial (global mode decides here)
+      const int h = D.fl->newton_n;
+      if (!D.isl_on && D.sc->ls_t < 0.0 && m < D.sc->merit[h < 1023 ? h : 1023]) D.sc->ls_t = trial_t;
+    } else if (n == -1) {                              // zero iterate of a warm-started step
       D.sc->merit0 = m;
       D.sc->warm_rejected = 0;
     } else if (n == -2) {                              // warm-started iterate
@@ -2269,6 +2316,99 @@ __global__ void k_cr_init(Dev<T> D) {
 }
 
 // lambda += t dl; counts the Newton iteration
+// Back-tracking line search on the Newton step (Sec. 8.1; the trials t = 1,
+// 1/2, 1/4, 1/8, 1/16 and the damped fallback are the oracle's).  k_ls_begin
+// keeps lambda and dlambda of this Newton iteration and clears the accepted
+// steps; k_ls_set(t, final) moves the islands still searching (final: every
+// island that has not stopped, with its accepted step or the damping) to
+// lambda + t dlambda (projected onto the friction cone when on) and u + t du,
+// positions from u as in k_body_pass<UPDATE>.
+template <typename T>
+__global__ void k_ls_begin(Dev<T> D) {
+  if (D.fl->newton_stop) return;
+  const int stride = gridDim.x * blockDim.x;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < D.R; i += stride) { D.lam0[i] = D.lam[i]; D.xs[i] = D.x[i]; }
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < D.ni; i += stride) D.isl.tacc[i] = -1.0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) D.sc->ls_t = -1.0;
+}
+
+template <typename T>
+__device__ __forceinline__ bool ls_step(const Dev<T> &D, int is, T t, int final, T &tt) {
+  if (D.isl_on) {
+    if (D.isl.stop[is] >= 0) return false;
+    const double a = D.isl.tacc[is];
+    if (final) { tt = a > 0.0 ? T(a) : D.dampT; return true; }
+    if (a > 0.0) return false;   // already accepted
+    tt = t;
+    return true;
+  }
+  const double a = D.sc->ls_t;
+  if (final) { tt = a > 0.0 ? T(a) : D.dampT; return true; }
+  if (a > 0.0) return false;
+  tt = t;
+  return true;
+}
+
+template <typename T>
+__global__ void k_ls_set(Dev<T> D, T t, int final) {
+  if (D.fl->newton_stop) return;
+  const int i0 = blockIdx.x * blockDim.x + threadIdx.x;
+  const int stride = gridDim.x * blockDim.x;
+  if (final && i0 == 0) D.fl->newton_count += 1;
+  const T h = D.hT;
+  const int nr = D.nr, np = D.np, nc = D.nc, nrest = D.R - 3 * nc;
+  const int n = nr + np + nc + nrest;
+  for (int j = i0; j < n; j += stride) {
+    T tt;
+    if (j < nr) {                       // rigid body
+      const int b = j;
+      if (!ls_step(D, D.isl_on ? D.bisl_r[b] : 0, t, final, tt)) continue;
+      T u[6], q0[4];
+#pragma unroll
+      for (int k = 0; k < 6; k++) { u[k] = D.ru0[k][b] + tt * D.rdu[k][b]; D.ru[k][b] = u[k]; }
+#pragma unroll
+      for (int k = 0; k < 4; k++) q0[k] = D.rq0[k][b];
+#pragma unroll
+      for (int k = 0; k < 3; k++) D.rx[k][b] = D.rx0[k][b] + h * u[k];
+      const T *w = u + 3;
+      T qd[4];
+      qd[0] = T(0.5) * (-q0[1] * w[0] - q0[2] * w[1] - q0[3] * w[2]);
+      qd[1] = T(0.5) * (q0[0] * w[0] + q0[3] * w[1] - q0[2] * w[2]);
+      qd[2] = T(0.5) * (-q0[3] * w[0] + q0[0] * w[1] + q0[1] * w[2]);
+      qd[3] = T(0.5) * (q0[2] * w[0] - q0[1] * w[1] + q0[0] * w[2]);
+      T qn[4], nn = 0;
+#pragma unroll
+      for (int k = 0; k < 4; k++) { qn[k] = q0[k] + h * qd[k]; nn += qn[k] * qn[k]; }
+      nn = dsqrt(nn);
+#pragma unroll
+      for (int k = 0; k < 4; k++) D.rq[k][b] = qn[k] / nn;
+    } else if (j < nr + np) {           // particle
+      const int b = j - nr;
+      if (!ls_step(D, D.isl_on ? D.bisl_p[b] : 0, t, final, tt)) continue;
+#pragma unroll
+      for (int k = 0; k < 3; k++) {
+        const T un = D.pu0[k][b] + tt * D.pdu[k][b];
+        D.pu[k][b] = un;
+        D.px[k][b] = D.px0[k][b] + h * un;
+      }
+    } else if (j < nr + np + nc) {      // contact: its three rows, projected onto the cone
+      const int c = j - nr - np, r = 3 * c;
+      if (!ls_step(D, D.isl_on ? D.risl[r] : 0, t, final, tt)) continue;
+      T l0 = D.lam0[r] + tt * D.xs[r], l1 = D.lam0[r + 1] + tt * D.xs[r + 1], l2 = D.lam0[r + 2] + tt * D.xs[r + 2];
+      if (D.cone) {
+        if (l0 < T(0)) l0 = T(0);
+        const T lim = D.cmu[c] * l0, f = dsqrt(l1 * l1 + l2 * l2);
+        if (f > lim) { const T sc = lim / f; l1 *= sc; l2 *= sc; }
+      }
+      D.lam[r] = l0; D.lam[r + 1] = l1; D.lam[r + 2] = l2;
+    } else {                            // joint and tet rows
+      const int r = 3 * nc + (j - nr - np - nc);
+      if (!ls_step(D, D.isl_on ? D.risl[r] : 0, t, final, tt)) continue;
+      D.lam[r] = D.lam0[r] + tt * D.xs[r];
+    }
+  }
+}
+
 template <typename T>
 __global__ void k_lambda_update(Dev<T> D) {
   if (D.fl->newton_stop) return;

@@ -40,7 +40,8 @@ class nsn_config(C.Structure):
                 ("tol_rel", C.c_double), ("cr_tol_mode", C.c_int32), ("ncp", C.c_int32),
                 ("rscale", C.c_int32), ("geom_stiffness", C.c_int32), ("precision", C.c_int32),
                 ("use_graph", C.c_int32), ("cone_project", C.c_int32), ("island_stop", C.c_int32),
-                ("cr_resident", C.c_int32), ("res_max_rows", C.c_int32)]
+                ("cr_resident", C.c_int32), ("res_max_rows", C.c_int32), ("line_search", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class nsn_stats(C.Structure):
@@ -381,7 +382,8 @@ def tet_records(s):
 
 DEFAULTS = dict(h=1.0 / 60.0, gravity=(0.0, 0.0, -9.81), newton_iters=4, cr_iters=20, damping=0.75, eps=1e-6,
                 tol_rel=0.0, cr_tol_mode=0, ncp=0, rscale=2, geom_stiffness=1, precision=NSN_FP32, use_graph=1,
-                cone_project=0, island_stop=0, cr_resident=1, res_max_rows=384)
+                cone_project=0, island_stop=0, cr_resident=1, res_max_rows=384,
+                line_search=0)
 
 
 def make_config(**params):
@@ -394,7 +396,7 @@ def make_config(**params):
     cfg.h = p["h"]
     cfg.gravity = (C.c_double * 3)(*p["gravity"])
     for k in ("newton_iters", "cr_iters", "cr_tol_mode", "ncp", "rscale", "geom_stiffness", "precision", "use_graph",
-              "cone_project", "island_stop", "cr_resident", "res_max_rows"):
+              "cone_project", "island_stop", "cr_resident", "res_max_rows", "line_search"):
         setattr(cfg, k, int(p[k]))
     for k in ("damping", "eps", "tol_rel"):
         setattr(cfg, k, float(p[k]))

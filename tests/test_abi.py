@@ -40,7 +40,7 @@ def test_config_struct_and_defaults(libnsn):
     assert cfg.damping == 0.75 and cfg.eps == 1e-6 and cfg.precision == nsn.NSN_FP32
     assert cfg.cone_project == 0 and cfg.island_stop == 0    # the printed method, one system
     # h, gravity[3], 2 ints, damping, eps, tol_rel, 8 ints
-    assert ctypes.sizeof(nsn.nsn_config) == 8 * 4 + 4 * 2 + 8 * 3 + 4 * 10
+    assert ctypes.sizeof(nsn.nsn_config) == 8 * 4 + 4 * 2 + 8 * 3 + 4 * 12
 
 
 def test_invalid_arguments_are_rejected_without_gpu(libnsn):
