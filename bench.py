@@ -14,21 +14,27 @@ trajectory advances from the seeded start state (no reset between steps).
   value     converged env-steps/s, state resident in HBM (device-timed), of
             the learned + batched form: per island the least-merit start among
             the network's lambda^0, the previous step's multipliers (its
-            fallback) and zero; damped update projected onto the friction cone
-            (option cone_project)
-  arms      the same measurement for: the plain batched method (zero start),
-            the printed update, the previous-step start alone, the first step
-            after an environment reset with the zero / learned start, and the
-            ablations of Sec. 7 (min-map NCP; r = h^2 and r = 1 instead of the
-            effective-mass r), each on the first step after a reset with the
-            zero start (compare after_reset_zero): on the advancing trajectory
-            the min-map variant diverges, in the FP64 oracle as well; and the
-            headline arm with the back-tracking line search of Sec. 8.1
+            fallback) and zero; Newton steps with the back-tracking line search
+            of Sec. 8.1 (trials t = 1 .. 1/16, else the damped 0.75; --line-search
+            0: the damped step), projected onto the friction cone (option
+            cone_project); CR per island in shared memory where it fits
+  arms      the same measurement for: the headline with the damped step, the
+            plain batched method (zero start; damped and with the line
+            search), the printed update, the previous-step start alone, the
+            first step after an environment reset with the zero / learned
+            start, and the ablations of Sec. 7 (min-map NCP; r = h^2 and r = 1
+            instead of the effective-mass r), each on the first step after a
+            reset with the zero start (compare after_reset_zero): on the
+            advancing trajectory the min-map variant diverges, in the FP64
+            oracle as well
   e2e       converged env-steps/s through the C ABI with host buffers: host->
             device copy of the state, the step, device->host copy of the state
             (the state makes that round trip every step)
-  roofline  the CR operator apply (body pass + row pass, island kernels),
-            bytes per launch from the algorithmic count B_apply, timed live
+  roofline  the dominant kernel of the step: the island-resident CR
+            (k_cr_resident), shared-memory bytes per launch from its
+            algorithmic count, timed live at full activity; the streamed CR
+            operator apply is reported beside it (operator_apply_roofline, HBM)
+            and the network forward (network_roofline, tensor)
   cpu_baseline  the FP64 oracle (plain method: zero start) on a
             64-environment sample, one host core, same tolerance, caps and
             accounting
@@ -247,7 +253,8 @@ def oracle_rate(workload, seed, budget_s, newton, cr):
         s = WORKLOADS[workload]["make"](seed)
         sample = "the full scene"
     n_envs = int(s.get("n_envs", 1))
-    o = oracle.Oracle(s, newton_iters=newton, cr_iters=cr, tol_rel=TOL, island_stop=1, cone_project=1)
+    o = oracle.Oracle(s, newton_iters=newton, cr_iters=cr, tol_rel=TOL, island_stop=1, cone_project=1,
+                      line_search=LS)
     ni, bi, _ = o.islands()
     isl_env = island_env_map(s, bi, ni)
     stops = []
@@ -261,7 +268,8 @@ def oracle_rate(workload, seed, budget_s, newton, cr):
             break
     conv, _, _ = count_converged(stops, isl_env, n_envs)
     return conv / el, dict(kind="oracle", cores=1,
-                           sample=f"{sample}, same tolerance, caps and accounting; {n} advancing steps in {el:.1f} s, "
+                           sample=f"{sample}, same tolerance, caps, Newton step ({'line search' if LS else 'damped'}) "
+                                  f"and accounting, zero start; {n} advancing steps in {el:.1f} s, "
                                   f"{conv} of {n * n_envs} env-steps converged")
 
 
@@ -284,6 +292,7 @@ def run_reference(args, rank, world):
 EAGER = False   # --eager: launch kernel by kernel instead of the CUDA graph (for profilers)
 RESIDENT = 1    # --resident 0: every island in the streamed CR loop
 CR_TOL = 0      # --cr-tol 1: CR of a Newton iteration also stops at the forcing term min(0.1, m/m0)
+LS = 1          # --line-search 0: the headline arm takes the damped step of Sec. 8.1 instead
 
 
 def make_solver(nsn, s, stream, newton, cr, cone, warm=0, params=None, ncp=0, rscale=2, ls=0):
@@ -369,7 +378,7 @@ def run_ours(args, rank, world, local_rank):
     if warm == "learned" and params is None:
         warm, warm_note = "prev", "previous-step multipliers (no trained network weights present)"
     with torch.cuda.stream(stream):
-        g = make_solver(nsn, s, stream, newton, cr, cone=1, warm=warm_names[warm], params=params)
+        g = make_solver(nsn, s, stream, newton, cr, cone=1, warm=warm_names[warm], params=params, ls=LS)
         dist = None
         if world > 1:
             import torch.distributed as dist
@@ -448,8 +457,10 @@ def run_ours(args, rank, world, local_rank):
         arms = {}
         if args.arms:
             # (name, cone projection, warm start, reset every step, NCP function, r strategy, line search)
-            for name, cone, wm, reset, ncp, rs, ls in (("line_search", 1, warm_names[warm], False, 0, 2, 1),
+            for name, cone, wm, reset, ncp, rs, ls in (("damped_update" if LS else "line_search", 1, warm_names[warm],
+                                                    False, 0, 2, 0 if LS else 1),
                                                    ("plain_zero_start", 1, nsn.NSN_WARM_ZERO, False, 0, 2, 0),
+                                                   ("plain_zero_start_line_search", 1, nsn.NSN_WARM_ZERO, False, 0, 2, 1),
                                                    ("as_printed", 0, nsn.NSN_WARM_ZERO, False, 0, 2, 0),
                                                    ("prev_warm_start", 1, nsn.NSN_WARM_PREV, False, 0, 2, 0),
                                                    ("after_reset_zero", 1, nsn.NSN_WARM_ZERO, True, 0, 2, 0),
@@ -457,7 +468,7 @@ def run_ours(args, rank, world, local_rank):
                                                    ("ablation_min_map", 1, nsn.NSN_WARM_ZERO, True, 1, 2, 0),
                                                    ("ablation_r_h2", 1, nsn.NSN_WARM_ZERO, True, 0, 1, 0),
                                                    ("ablation_r_identity", 1, nsn.NSN_WARM_ZERO, True, 0, 0, 0)):
-                if wm == warm_names[warm] and not reset and cone == 1 and ncp == 0 and rs == 2 and not ls:
+                if wm == warm_names[warm] and not reset and cone == 1 and ncp == 0 and rs == 2 and ls == LS:
                     continue
                 if wm == nsn.NSN_WARM_LEARNED and params is None:
                     arms[name] = {"unavailable": "no trained weights (paper_1907_04587_gb300/weights)"}
@@ -509,6 +520,8 @@ def run_ours(args, rank, world, local_rank):
         "config": {"workload": args.workload, "description": W["desc"], "n_envs": n_envs, "bodies": g.nb,
                    "rows": sz["rows"], "islands": main_arm["islands"], "newton_cap": newton, "cr_iters": cr,
                    "cr_stop": ("forcing term min(0.1, m/m0), floor, growth, cap" if CR_TOL else "floor, growth, cap"),
+                   "newton_step": ("back-tracking line search (t = 1 .. 1/16, else the damped 0.75), per island"
+                                   if LS else "damped, t = 0.75"),
                    "tol_rel": TOL, "cone_projection": True, "warm_start": warm_note,
                    "device_bytes": sz["device_bytes"], "launch": "kernel by kernel" if EAGER else
                    "one CUDA graph per step (Newton loop as a conditional WHILE node)",
@@ -552,11 +565,14 @@ def main():
                     help="0: no island-resident CR (every island in the streamed CR loop of four kernels per iteration)")
     ap.add_argument("--cr-tol", type=int, default=0,
                     help="1: inexact Newton, CR stops at ||r||_P <= min(0.1, merit/merit0) ||r0||_P (cap --cr)")
+    ap.add_argument("--line-search", type=int, default=1,
+                    help="1 (default): headline arm with the back-tracking line search of Sec. 8.1; 0: damped step")
     args = ap.parse_args()
-    global EAGER, RESIDENT, CR_TOL
+    global EAGER, RESIDENT, CR_TOL, LS
     EAGER = bool(args.eager)
     RESIDENT = int(args.resident)
     CR_TOL = int(args.cr_tol)
+    LS = int(args.line_search)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

@@ -58,6 +58,10 @@ struct Flags {
   int n_list_res, res_next, cr_res_max, cr_base;   // n_list_res: resident islands continuing
   // work done by k_cr_resident (row-, entry- and body-iterations), for its roofline
   unsigned long long res_rowit, res_entit, res_bodit;
+  // line search: 1 while the trials of a Newton iteration run; 1 while some
+  // island still searches (kernels of a trial skip the islands that accepted,
+  // and return at once when none searches); the OR of this trial's islands
+  int ls_trial, ls_search, ls_next;
 };
 
 // iteration index / entry buffer taken from Flags::newton_n
@@ -673,6 +677,17 @@ __device__ __forceinline__ bool w_fb(T vt, T lf, T mu_ln, T r, T &W) {
   return true;
 }
 
+// line-search trial: island is (island mode) has already accepted a step
+template <typename T>
+__device__ __forceinline__ bool ls_done(const Dev<T> &D, int is) {
+  return D.fl->ls_trial && D.isl_on && D.isl.tacc[is] > 0.0;
+}
+// line-search trial in which no island searches any more: the kernel returns
+template <typename T>
+__device__ __forceinline__ bool ls_idle(const Dev<T> &D) {
+  return D.fl->ls_trial && !D.fl->ls_search;
+}
+
 template <typename T>
 __device__ __forceinline__ T w_min(T vt, T lf, T mu_ln, T r) {
   T bb = r * (mu_ln - lf);
@@ -682,12 +697,13 @@ __device__ __forceinline__ T w_min(T vt, T lf, T mu_ln, T r) {
 
 template <typename T>
 __global__ void k_eval_contacts(Dev<T> D, int buf, int force) {
+  if (ls_idle(D)) return;
   if (!force && D.fl->newton_stop) return;
   if (buf == IT_DEV) buf = D.fl->newton_n & 1;
   else if (buf == IT_DEV_NEXT) buf = (D.fl->newton_n + 1) & 1;
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= D.nc) return;
-  if (!force && D.isl_on && D.isl.stop[D.risl[3 * c]] >= 0) return;   // stopped island
+  if (!force && D.isl_on && (D.isl.stop[D.risl[3 * c]] >= 0 || ls_done(D, D.risl[3 * c]))) return;   // stopped island
   const T h = D.hT;
   T pa[3], pb[3], n[3];
   for (int k = 0; k < 3; k++) { pa[k] = D.cpa[k][c]; pb[k] = D.cpb[k][c]; n[k] = D.cn[k][c]; }
@@ -775,12 +791,13 @@ __global__ void k_eval_contacts(Dev<T> D, int buf, int force) {
 // a_w . b_k = 0 with b_1, b_2 perpendicular to b's hinge axis.
 template <typename T>
 __global__ void k_eval_joints(Dev<T> D, int buf, int force) {
+  if (ls_idle(D)) return;
   if (!force && D.fl->newton_stop) return;
   if (buf == IT_DEV) buf = D.fl->newton_n & 1;
   else if (buf == IT_DEV_NEXT) buf = (D.fl->newton_n + 1) & 1;
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= D.nj) return;
-  if (!force && D.isl_on && D.isl.stop[D.risl[3 * D.nc + 5 * j]] >= 0) return;   // stopped island
+  if (!force && D.isl_on && (D.isl.stop[D.risl[3 * D.nc + 5 * j]] >= 0 || ls_done(D, D.risl[3 * D.nc + 5 * j]))) return;
   const T h = D.hT;
   T pa[3], pb[3], axa[3], axb[3];
   for (int k = 0; k < 3; k++) { pa[k] = D.jpa[k][j]; pb[k] = D.jpb[k][j]; axa[k] = D.jaxa[k][j]; axb[k] = D.jaxb[k][j]; }
@@ -849,12 +866,13 @@ __global__ void k_eval_joints(Dev<T> D, int buf, int force) {
 // 1e-6 C1 V), C = E / h^2, h = E (c + lambda) / h.
 template <typename T>
 __global__ void k_eval_tets(Dev<T> D, int buf, int force) {
+  if (ls_idle(D)) return;
   if (!force && D.fl->newton_stop) return;
   if (buf == IT_DEV) buf = D.fl->newton_n & 1;
   else if (buf == IT_DEV_NEXT) buf = (D.fl->newton_n + 1) & 1;
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= D.nt) return;
-  if (!force && D.isl_on && D.isl.stop[D.risl[D.Rpair + 3 * t]] >= 0) return;   // stopped island
+  if (!force && D.isl_on && (D.isl.stop[D.risl[D.Rpair + 3 * t]] >= 0 || ls_done(D, D.risl[D.Rpair + 3 * t]))) return;
   const T h = D.hT;
   int v[4];
   for (int q = 0; q < 4; q++) v[q] = D.tv[4 * t + q];
@@ -934,11 +952,12 @@ template <int MODE, typename T>
 __device__ __forceinline__ bool isl_skip(const Dev<T> &D, int is, int force) {
   if (MODE == BM_APPLY) return D.isl.crdone[is] != 0;
   if (force) return false;
-  return D.isl.stop[is] >= 0;
+  return D.isl.stop[is] >= 0 || (MODE == BM_RESIDUAL && ls_done(D, is));
 }
 
 template <typename T, int G, int MODE>
 __global__ void __launch_bounds__(BLOCK) k_body_pass(Dev<T> D, const T *__restrict__ in, int buf, int newton_it, int force) {
+  if (ls_idle(D)) return;
   if (!force && D.fl->newton_stop) return;
   if (newton_it == IT_DEV) newton_it = D.fl->newton_n;
   if (buf == IT_DEV) buf = D.fl->newton_n & 1;
@@ -1235,6 +1254,7 @@ __global__ void __launch_bounds__(BLOCK) k_body_pass(Dev<T> D, const T *__restri
 //           exact for the vectors actually held in memory).
 template <typename T, int MODE>
 __global__ void __launch_bounds__(BLOCK) k_row_pass(Dev<T> D, int force) {
+  if (ls_idle(D)) return;
   if (!force && D.fl->newton_stop) return;
   if (MODE == RM_APPLY && D.fl->cr_stop) return;
   Acc<T> a[NPART];
@@ -1341,6 +1361,7 @@ __global__ void __launch_bounds__(BLOCK) k_row_pass(Dev<T> D, int force) {
 // whole warps so that every lane takes part in the shuffles.
 template <typename T, int MODE>
 __global__ void __launch_bounds__(BLOCK) k_row_pass_isl(Dev<T> D, int force) {
+  if (ls_idle(D)) return;
   if (!force && D.fl->newton_stop) return;
   if (MODE == RM_APPLY && D.fl->cr_stop) return;
   const T eps = D.epsT, ih = D.ihT;
@@ -1355,7 +1376,7 @@ __global__ void __launch_bounds__(BLOCK) k_row_pass_isl(Dev<T> D, int force) {
       if (w0 >= D.Rpair) continue;                  // a listed block of tet rows (uniform per warp)
       const int i = w0 + lane;
       int key = i < D.Rpair ? D.risl[i] : -1;
-      if (key >= 0 && (MODE == RM_APPLY ? D.isl.crdone[key] != 0 : (!force && D.isl.stop[key] >= 0))) key = -1;
+      if (key >= 0 && (MODE == RM_APPLY ? D.isl.crdone[key] != 0 : (!force && (D.isl.stop[key] >= 0 || ls_done(D, key))))) key = -1;
       const bool v = key >= 0;
       if (!__any_sync(0xffffffffu, v)) continue;   // the whole warp's islands are finished
       if (MODE == RM_MERIT) {
@@ -1397,7 +1418,7 @@ __global__ void __launch_bounds__(BLOCK) k_row_pass_isl(Dev<T> D, int force) {
     for (int w0 = bid * BLOCK + (threadIdx.x & ~31); w0 < D.nt; w0 += stride) {
       const int t = w0 + lane;
       int key = t < D.nt ? D.risl[rb + 3 * t] : -1;
-      if (key >= 0 && (MODE == RM_APPLY ? D.isl.crdone[key] != 0 : (!force && D.isl.stop[key] >= 0))) key = -1;
+      if (key >= 0 && (MODE == RM_APPLY ? D.isl.crdone[key] != 0 : (!force && (D.isl.stop[key] >= 0 || ls_done(D, key))))) key = -1;
       const bool v = key >= 0;
       if (!__any_sync(0xffffffffu, v)) continue;
       if (MODE == RM_MERIT) {
@@ -1514,6 +1535,7 @@ __device__ __forceinline__ bool isl_merit_one(const Dev<T> &D, int i, int n, int
 // runs are appended to list_isl, the work list of k_cr_scalars_isl.
 template <typename T>
 __global__ void k_merit_isl(Dev<T> D, int n, int force, double trial_t) {
+  if (ls_idle(D)) return;
   if (!force && D.fl->newton_stop) return;
   if (n == IT_DEV) n = D.fl->newton_n;
   const bool final_eval = n == IT_FINAL;
@@ -1526,6 +1548,7 @@ __global__ void k_merit_isl(Dev<T> D, int n, int force, double trial_t) {
   for (int i0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); i0 < ni; i0 += gridDim.x * blockDim.x) {
     const int i = i0 + lane;
     const bool cont = i < ni && isl_merit_one(D, i, n, force, final_eval, m2, active, trial_t);
+    if (n == IT_TRIAL && i < ni && D.isl.stop[i] < 0 && D.isl.tacc[i] < 0.0) active = 1;   // still searching
     if (regular) {
       // continuing islands: resident ones to k_cr_resident (marked CR-done for
       // the streaming kernels), the others to the streaming CR loop
@@ -1551,7 +1574,7 @@ __global__ void k_merit_isl(Dev<T> D, int n, int force, double trial_t) {
     double t = 0.0;
     for (int w = 0; w < int(blockDim.x) / 32; w++) t += sm[w];
     atomicAdd(&D.sc->isl_m2, t);
-    if (any) atomicOr(&D.fl->isl_any, 1);
+    if (any) atomicOr(n == IT_TRIAL ? &D.fl->ls_next : &D.fl->isl_any, 1);
   }
 }
 
@@ -1623,6 +1646,7 @@ __global__ void __launch_bounds__(1024) k_block_lists(Dev<T> D, int all_islands)
 // merit of this Newton iteration, Newton stop test, CR forcing term (1 block)
 template <typename T>
 __global__ void __launch_bounds__(RED_THREADS) k_merit(Dev<T> D, int n, int force, double trial_t) {
+  if (ls_idle(D)) return;
   if (!force && D.fl->newton_stop) return;
   if (n == IT_DEV) n = D.fl->newton_n;
   const bool final_eval = n == IT_FINAL;
@@ -1651,7 +1675,13 @@ __global__ void __launch_bounds__(RED_THREADS) k_merit(Dev<T> D, int n, int forc
   if (threadIdx.x == 0) {
     if (n == IT_TRIAL) {                               // line-search trial (global mode decides here)
       const int h = D.fl->newton_n;
-      if (!D.isl_on && D.sc->ls_t < 0.0 && m < D.sc->merit[h < 1023 ? h : 1023]) D.sc->ls_t = trial_t;
+      if (!D.isl_on) {
+        if (D.sc->ls_t < 0.0 && m < D.sc->merit[h < 1023 ? h : 1023]) D.sc->ls_t = trial_t;
+        D.fl->ls_search = D.sc->ls_t < 0.0 ? 1 : 0;
+      } else {
+        D.fl->ls_search = D.fl->ls_next;                // some island still searches
+        D.fl->ls_next = 0;
+      }
     } else if (n == -1) {                              // zero iterate of a warm-started step
       D.sc->merit0 = m;
       D.sc->warm_rejected = 0;
@@ -2329,7 +2359,10 @@ __global__ void k_ls_begin(Dev<T> D) {
   const int stride = gridDim.x * blockDim.x;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < D.R; i += stride) { D.lam0[i] = D.lam[i]; D.xs[i] = D.x[i]; }
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < D.ni; i += stride) D.isl.tacc[i] = -1.0;
-  if (blockIdx.x == 0 && threadIdx.x == 0) D.sc->ls_t = -1.0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    D.sc->ls_t = -1.0;
+    D.fl->ls_trial = 0; D.fl->ls_search = 1; D.fl->ls_next = 0;
+  }
 }
 
 template <typename T>
@@ -2352,9 +2385,13 @@ __device__ __forceinline__ bool ls_step(const Dev<T> &D, int is, T t, int final,
 template <typename T>
 __global__ void k_ls_set(Dev<T> D, T t, int final) {
   if (D.fl->newton_stop) return;
+  if (!final && ls_idle(D)) return;   // every island has accepted a step
   const int i0 = blockIdx.x * blockDim.x + threadIdx.x;
   const int stride = gridDim.x * blockDim.x;
-  if (final && i0 == 0) D.fl->newton_count += 1;
+  if (i0 == 0) {
+    if (final) D.fl->newton_count += 1;
+    D.fl->ls_trial = final ? 0 : 1;
+  }
   const T h = D.hT;
   const int nr = D.nr, np = D.np, nc = D.nc, nrest = D.R - 3 * nc;
   const int n = nr + np + nc + nrest;

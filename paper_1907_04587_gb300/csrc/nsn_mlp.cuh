@@ -116,11 +116,14 @@ __global__ void __launch_bounds__(128) k_gemm(const __nv_bfloat16 *__restrict__ 
 // Fused inference: the whole network per row tile in one kernel.  The BF16
 // weights (70 KB) stay in shared memory for the CTA's lifetime; each warp
 // takes 16 rows, runs the four layers with mma.sync m16n8k16 (BF16 operands,
-// FP32 accumulation), keeps its activations in a shared-memory ping-pong pair
-// (BF16, as the layered path stores them) and writes only Y.  X is read once.
-// Shared rows are padded by 8 BF16 so that the fragment loads (lane g reads
-// row g, lane tq words tq) fall in 32 distinct banks.
-constexpr int FW = 8;            // warps per CTA, 16 rows each
+// FP32 accumulation) and keeps its activations in one shared-memory tile
+// (BF16, as the layered path stores them), overwritten layer by layer once
+// the layer's fragments are in registers; only Y is written.  X is read once.
+// Fragments are loaded with ldmatrix (one instruction for the A fragment of a
+// k-step, one for the B fragments of two n8 tiles).  Shared rows are padded by
+// 8 BF16 (16 bytes), so that the eight 16-byte rows of each 8x8 matrix fall in
+// distinct bank groups.
+constexpr int FW = 16;           // warps per CTA, 16 rows each
 constexpr int FP1 = NIN + 8;     // padded row lengths (BF16)
 constexpr int FPH = NH + 8;
 constexpr int N4P = 8;           // layer 4 padded to one n8 tile
@@ -128,14 +131,26 @@ struct FusedSmem {
   __nv_bfloat16 W1[NH][FP1], W2[NH][FPH], W3[NH][FPH], W4[N4P][FPH];
   float b1[NH], b2[NH], b3[NH], b4[N4P];
   __nv_bfloat16 x[FW][16][FP1];
-  __nv_bfloat16 act[FW][2][16][FPH];
+  __nv_bfloat16 act[FW][16][FPH];
 };
 
+// four 8x8 BF16 matrices from shared memory (lane l gives the address of row
+// l % 8 of matrix l / 8); register i holds matrix i in the mma fragment layout
+__device__ __forceinline__ void ldsm_x4(const __nv_bfloat16 *p, uint32_t &r0, uint32_t &r1, uint32_t &r2,
+                                        uint32_t &r3) {
+  const unsigned a = static_cast<unsigned>(__cvta_generic_to_shared(p));
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];\n"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+               : "r"(a));
+}
+
 // one dense layer for a warp's 16 rows: out = ReLU(A W^T + b) as BF16 (NT n8 tiles,
-// K = 16 * KS), A and W row-major in shared memory with padded row lengths
+// K = 16 * KS), A and W row-major in shared memory with padded row lengths; out
+// may be A (the stores follow the last fragment load of the warp)
 template <int KS, int NT, int LDA, int LDW>
 __device__ __forceinline__ void fused_layer(const __nv_bfloat16 *A, const __nv_bfloat16 *W, const float *b,
-                                            __nv_bfloat16 *out, int g, int tq) {
+                                            __nv_bfloat16 *out, int lane) {
+  const int g = lane >> 2, tq = lane & 3, m = lane >> 3, r8 = lane & 7;
   float acc[NT][4];
 #pragma unroll
   for (int j = 0; j < NT; j++)
@@ -145,17 +160,19 @@ __device__ __forceinline__ void fused_layer(const __nv_bfloat16 *A, const __nv_b
   for (int ks = 0; ks < KS; ks++) {
     const int k0 = 16 * ks;
     uint32_t a[4];
-    a[0] = pack_bf16(A[g * LDA + k0 + 2 * tq], A[g * LDA + k0 + 2 * tq + 1]);
-    a[1] = pack_bf16(A[(g + 8) * LDA + k0 + 2 * tq], A[(g + 8) * LDA + k0 + 2 * tq + 1]);
-    a[2] = pack_bf16(A[g * LDA + k0 + 2 * tq + 8], A[g * LDA + k0 + 2 * tq + 9]);
-    a[3] = pack_bf16(A[(g + 8) * LDA + k0 + 2 * tq + 8], A[(g + 8) * LDA + k0 + 2 * tq + 9]);
+    // A: matrices (rows 0-7, k0), (rows 8-15, k0), (rows 0-7, k0+8), (rows 8-15, k0+8)
+    ldsm_x4(A + (r8 + 8 * (m & 1)) * LDA + k0 + 8 * (m >> 1), a[0], a[1], a[2], a[3]);
 #pragma unroll
-    for (int j = 0; j < NT; j++) {
-      const __nv_bfloat16 *w = W + (8 * j + g) * LDW + k0;
-      uint32_t bb[2] = {pack_bf16(w[2 * tq], w[2 * tq + 1]), pack_bf16(w[2 * tq + 8], w[2 * tq + 9])};
-      mma_bf16_16816(acc[j], a, bb);
+    for (int j = 0; j < NT; j += 2) {
+      // B of tiles j, j+1: matrices (tile j, k0), (tile j, k0+8), (tile j+1, k0), (tile j+1, k0+8)
+      uint32_t bq[4];
+      ldsm_x4(W + (8 * (j + (m >> 1)) + r8) * LDW + k0 + 8 * (m & 1), bq[0], bq[1], bq[2], bq[3]);
+      uint32_t b0[2] = {bq[0], bq[1]}, b1[2] = {bq[2], bq[3]};
+      mma_bf16_16816(acc[j], a, b0);
+      mma_bf16_16816(acc[j + 1], a, b1);
     }
   }
+  __syncwarp();
 #pragma unroll
   for (int j = 0; j < NT; j++) {
     const int c = 8 * j + 2 * tq;
@@ -187,6 +204,7 @@ __global__ void __launch_bounds__(FW * 32) k_forward_fused(const float *__restri
   if (threadIdx.x < N4P) S.b4[threadIdx.x] = threadIdx.x < NOUT ? pf[OFF_B4 + threadIdx.x] : 0.f;
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, tq = lane & 3;
+  __nv_bfloat16 *act = &S.act[warp][0][0];
   for (int r0 = (blockIdx.x * FW + warp) * 16; r0 < n; r0 += gridDim.x * FW * 16) {
     // 16 rows x 16 features: 8 per lane, coalesced
 #pragma unroll
@@ -196,23 +214,19 @@ __global__ void __launch_bounds__(FW * 32) k_forward_fused(const float *__restri
       S.x[warp][r][k] = __float2bfloat16(v);
     }
     __syncwarp();
-    fused_layer<1, NH / 8, FP1, FP1>(&S.x[warp][0][0], &S.W1[0][0], S.b1, &S.act[warp][0][0][0], g, tq);
+    fused_layer<1, NH / 8, FP1, FP1>(&S.x[warp][0][0], &S.W1[0][0], S.b1, act, lane);
     __syncwarp();
-    fused_layer<NH / 16, NH / 8, FPH, FPH>(&S.act[warp][0][0][0], &S.W2[0][0], S.b2, &S.act[warp][1][0][0], g, tq);
+    fused_layer<NH / 16, NH / 8, FPH, FPH>(act, &S.W2[0][0], S.b2, act, lane);
     __syncwarp();
-    fused_layer<NH / 16, NH / 8, FPH, FPH>(&S.act[warp][1][0][0], &S.W3[0][0], S.b3, &S.act[warp][0][0][0], g, tq);
+    fused_layer<NH / 16, NH / 8, FPH, FPH>(act, &S.W3[0][0], S.b3, act, lane);
     __syncwarp();
     // layer 4 (no ReLU): one n8 tile, columns 0..NOUT-1 kept
     float acc[4] = {0.f, 0.f, 0.f, 0.f};
-    const __nv_bfloat16 *A = &S.act[warp][0][0][0];
 #pragma unroll
     for (int ks = 0; ks < NH / 16; ks++) {
       const int k0 = 16 * ks;
       uint32_t a[4];
-      a[0] = pack_bf16(A[g * FPH + k0 + 2 * tq], A[g * FPH + k0 + 2 * tq + 1]);
-      a[1] = pack_bf16(A[(g + 8) * FPH + k0 + 2 * tq], A[(g + 8) * FPH + k0 + 2 * tq + 1]);
-      a[2] = pack_bf16(A[g * FPH + k0 + 2 * tq + 8], A[g * FPH + k0 + 2 * tq + 9]);
-      a[3] = pack_bf16(A[(g + 8) * FPH + k0 + 2 * tq + 8], A[(g + 8) * FPH + k0 + 2 * tq + 9]);
+      ldsm_x4(act + ((lane & 7) + 8 * ((lane >> 3) & 1)) * FPH + k0 + 8 * (lane >> 4), a[0], a[1], a[2], a[3]);
       uint32_t bb[2] = {pack_bf16(S.W4[g][k0 + 2 * tq], S.W4[g][k0 + 2 * tq + 1]),
                         pack_bf16(S.W4[g][k0 + 2 * tq + 8], S.W4[g][k0 + 2 * tq + 9])};
       mma_bf16_16816(acc, a, bb);
