@@ -1,0 +1,101 @@
+"""Parity at the full size of the batched workload (4096 environments,
+2,358,981 rows), in the launch configuration bench.py times: FP32, one CUDA
+graph per step, islands solved side by side, island-resident CR, the
+back-tracking line search, projection onto the friction cone.
+
+The oracle cannot solve 4096 environments in a test's time, so environments
+are sampled and each is solved by the FP64 oracle alone (an environment is a
+union of islands and A is block diagonal by island, so this is the same
+problem); the rest is checked through properties that hold at any size."""
+import numpy as np
+import pytest
+
+from paper_1907_04587_gb300 import nsn, scenes
+from test_oracle_islands import sub_scene
+
+pytestmark = pytest.mark.gpu
+
+H = 1.0 / 60.0
+G = 9.81
+PRM = dict(newton_iters=30, cr_iters=50, tol_rel=1e-6, island_stop=1, cone_project=1, line_search=1)
+SAMPLE = (0, 1, 7, 100, 1234, 2048, 3333, 4095)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def cuda():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    yield
+
+
+@pytest.fixture(scope="module")
+def full():
+    s = scenes.batched_envs(seed=0, n_envs=4096)
+    g = nsn.Solver(s, precision=nsn.NSN_FP32, use_graph=1, **PRM)
+    g.step()
+    return s, g
+
+
+def mass_weighted(s, sel, v_a, w_a, v_b, w_b):
+    """Kinetic-energy norm of (a - b) over the bodies sel, relative to b's plus g h."""
+    R = scenes.quat_rot(s["quat"][sel])
+    m = s["mass"][sel].astype(np.float64)
+    Iw = np.einsum("nij,nj,nkj->nik", R, s["inertia"][sel].astype(np.float64), R)
+    rig = s["kind"][sel] == 0
+    def e(dv, dw):
+        return np.sqrt((m * (dv ** 2).sum(1)).sum() + np.einsum("ni,nij,nj->", dw[rig], Iw[rig], dw[rig]))
+    return e(v_a - v_b, w_a - w_b) / (e(v_b, w_b) + H * G * np.sqrt(m.sum()))
+
+
+def test_sampled_environments_match_oracle(orc, full):
+    s, g = full
+    st = g.get_state()
+    n_isl, bi_g = g.islands()
+    stop_g = g.island_stats()["stopped_at"]
+    agree = total = 0
+    for e in SAMPLE:
+        bodies = np.nonzero(s["env"] == e)[0]
+        sub = sub_scene(s, bodies)
+        o = orc.Oracle(sub, **PRM)
+        o.step()
+        so = o.get_state()
+        _, bi_o, _ = o.islands()
+        stop_o = o.island_stats()["stopped_at"]
+        # islands of this environment on the GPU, in the oracle's island order
+        isl_g = bi_g[bodies]
+        conv_g = np.array([stop_g[isl_g[np.nonzero(bi_o == i)[0][0]]] >= 0 for i in range(len(stop_o))])
+        conv_o = stop_o >= 0
+        agree += int((conv_g == conv_o).sum())
+        total += len(conv_o)
+        both = conv_g & conv_o
+        sel = both[bi_o]                # bodies of islands converged on both sides
+        if sel.any():
+            err = mass_weighted(sub, sel, st["vel"][bodies][sel], st["omega"][bodies][sel], so["vel"][sel],
+                                so["omega"][sel])
+            print(f"env {e}: {len(stop_o)} islands, converged gpu {conv_g.sum()} oracle {conv_o.sum()}, "
+                  f"velocity error on islands converged on both {err:.2e}")
+            assert err < 2e-3
+    print("islands with the same converged / not converged outcome:", agree, "of", total)
+    assert agree >= 0.85 * total
+
+
+def test_full_size_properties(full):
+    """Every contact's multipliers lie in the friction cone after the projected
+    update (lambda_n >= 0, |lambda_f| <= mu lambda_n); every island that
+    stopped meets the tolerance; the state is finite; most islands converge."""
+    s, g = full
+    lam = g.get_lambda().astype(np.float64)
+    nc = len(s["c_body"])
+    l3 = lam[:3 * nc].reshape(nc, 3)
+    mu = s["c_mu"].astype(np.float64)
+    assert np.all(l3[:, 0] >= 0.0)
+    fr = np.hypot(l3[:, 1], l3[:, 2])
+    assert np.all(fr <= mu * l3[:, 0] * (1 + 1e-5) + 1e-30)
+    st = g.island_stats()
+    done = st["stopped_at"] >= 0
+    assert done.mean() > 0.8
+    assert np.all(st["merit_final"][done] <= 1e-6 * st["merit0"][done] * 1.001)
+    assert all(np.isfinite(v).all() for v in g.get_state().values())
