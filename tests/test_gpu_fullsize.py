@@ -77,7 +77,9 @@ def test_sampled_environments_match_oracle(orc, full):
                                 so["omega"][sel])
             print(f"env {e}: {len(stop_o)} islands, converged gpu {conv_g.sum()} oracle {conv_o.sum()}, "
                   f"velocity error on islands converged on both {err:.2e}")
-            assert err < 2e-3
+            # the FP32 path against FP64 on islands both solved to 1e-6: the 1e-5
+            # relative velocity bar of the specification (measured up to 1.8e-6)
+            assert err < 1e-5
     print("islands with the same converged / not converged outcome:", agree, "of", total)
     assert agree >= 0.85 * total
 
