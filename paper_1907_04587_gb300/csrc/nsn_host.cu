@@ -62,6 +62,7 @@ struct Layout {
   // most res_max_rows rows), and the largest eligible island
   std::vector<int> ires;
   std::vector<unsigned char> isres;
+  std::vector<unsigned char> isl_rigid;   // 1: the island has no particles and no tets
   int n_res = 0, res_rows = 0, res_ent = 0, res_bod = 0;
   // groups of consecutive eligible islands solved by one thread block
   // ({c0, nc, j0, nj, b0, nb, e0, ne, first slot in gisl, islands} each)
@@ -301,6 +302,7 @@ nsn_status build_layout(nsn_ctx *c) {
   // contiguous in the internal order) and eligibility for the resident CR
   L.ires.assign(size_t(8) * std::max(L.ni, 1), 0);
   L.isres.assign(std::max(L.ni, 1), 0);
+  L.isl_rigid.assign(std::max(L.ni, 1), 0);
   {
     std::vector<int> npar(L.ni, 0), ntet(L.ni, 0);
     auto first = [&](int i, int slot, int v) { if (L.ires[8 * i + slot + 1] == 0) L.ires[8 * i + slot] = v; L.ires[8 * i + slot + 1]++; };
@@ -311,6 +313,7 @@ nsn_status build_layout(nsn_ctx *c) {
     for (int t = 0; t < L.nt; t++) ntet[L.risl[L.Rpair + 3 * t]]++;
     // (at most 2048 rows: the reduction task table of a group holds 2 per island + rows / 128)
     const int cap = std::min(c->cfg.res_max_rows > 0 ? c->cfg.res_max_rows : 384, 2048);
+    for (int i = 0; i < L.ni; i++) L.isl_rigid[i] = npar[i] == 0 && ntet[i] == 0;
     for (int i = 0; i < L.ni; i++) {
       int *r = &L.ires[8 * size_t(i)];
       if (r[5] > 0) { r[6] = L.rseg[r[4]]; r[7] = L.rseg[r[4] + r[5]] - r[6]; }
@@ -419,6 +422,9 @@ void carve(Arena &A, Dev<T> &D, const Layout &L, int nb) {
   D.isl.alpha_f = A.take<float>(ni); D.isl.beta_f = A.take<float>(ni);
   D.isl.stop = A.take<int>(ni); D.isl.crdone = A.take<int>(ni);
   D.isl.tacc = A.take<double>(ni);
+  D.isl.ls_pre = A.take<int>(ni);
+  D.isl.mls = A.take<double>(ni);
+  D.isl.rigid = A.take<unsigned char>(ni);
   // line search: du, u and lambda at the head of the Newton iteration, dlambda
   for (int k = 0; k < 6; k++) { D.rdu[k] = tk(L.nr); D.ru0[k] = tk(L.nr); }
   for (int k = 0; k < 3; k++) { D.pdu[k] = tk(L.np); D.pu0[k] = tk(L.np); }
@@ -618,6 +624,8 @@ nsn_status upload(nsn_ctx *c, Dev<T> &D) {
   CUDA_TRY(c, puti(D.bisl_p, L.bisl_p));
   CUDA_TRY(c, puti(D.ires, L.ires));
   CUDA_TRY(c, cudaMemcpyAsync(D.isres, L.isres.data(), L.isres.size(), cudaMemcpyHostToDevice, st));
+  CUDA_TRY(c, cudaMemcpyAsync(D.isl.rigid, L.isl_rigid.data(), L.isl_rigid.size(), cudaMemcpyHostToDevice, st));
+  CUDA_TRY(c, cudaMemsetAsync(D.isl.ls_pre, 0, sizeof(int) * size_t(std::max(L.ni, 1)), st));
   CUDA_TRY(c, puti(D.gres, L.gres));
   CUDA_TRY(c, puti(D.gisl, L.gisl));
   CUDA_TRY(c, puti(D.grp_of, L.grp_of));
@@ -773,6 +781,7 @@ struct Launcher {
     if (D.isl_on && D.ni) {
       cudaMemsetAsync(D.isl.stop, 0xff, sizeof(int) * D.ni, st);
       cudaMemsetAsync(D.isl.acc, 0, sizeof(double) * ISL_ACC * D.ni, st);
+      cudaMemsetAsync(D.isl.ls_pre, 0, sizeof(int) * D.ni, st);   // no line-search evaluation carries over
     }
     k_begin_rigid<T><<<cdiv(std::max(D.nr, 1), 128), 128, 0, st>>>(D);
     count++;

@@ -91,6 +91,13 @@ struct IslState {
   int *stop;                 // Newton iteration at which the island stopped, -1 while iterating
   int *crdone;               // 1: the island's CR is finished in this Newton iteration
   double *tacc;              // line search: accepted step of this Newton iteration (-1: none yet)
+  // line search: 1 when the island's rows, residual and merit (mls) were
+  // evaluated by the trial it accepted, i.e. at the iterate it committed; the
+  // next Newton iteration's evaluation reuses them (islands of rigid bodies,
+  // rigid[i] = 1: particles need the head's geometric-stiffness difference)
+  int *ls_pre;
+  double *mls;
+  unsigned char *rigid;
 };
 
 // FP64 scalars kept on the device
@@ -485,6 +492,7 @@ __global__ void k_begin_rigid(Dev<T> D) {
     D.fl->newton_n = 0; D.fl->newton_live = 1; D.fl->cr_k = 0; D.fl->cr_live = 0; D.fl->cr_exec = 0;
     D.fl->n_list_isl = 0; D.fl->isl_active = 0;
     D.fl->n_list_res = 0; D.fl->res_next = 0; D.fl->cr_res_max = 0; D.fl->cr_base = 0;
+    D.fl->ls_trial = 0; D.fl->ls_search = 0; D.fl->ls_next = 0;
   }
   if (i >= D.nr) return;
   T q[4], R[9], Ib[3], w[3], Iw[9], Iwi[9];
@@ -703,7 +711,8 @@ __global__ void k_eval_contacts(Dev<T> D, int buf, int force) {
   else if (buf == IT_DEV_NEXT) buf = (D.fl->newton_n + 1) & 1;
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= D.nc) return;
-  if (!force && D.isl_on && (D.isl.stop[D.risl[3 * c]] >= 0 || ls_done(D, D.risl[3 * c]))) return;   // stopped island
+  if (!force && D.isl_on && (D.isl.stop[D.risl[3 * c]] >= 0 || ls_done(D, D.risl[3 * c]) || D.isl.ls_pre[D.risl[3 * c]]))
+    return;   // stopped island, or evaluated at this iterate by the line search
   const T h = D.hT;
   T pa[3], pb[3], n[3];
   for (int k = 0; k < 3; k++) { pa[k] = D.cpa[k][c]; pb[k] = D.cpb[k][c]; n[k] = D.cn[k][c]; }
@@ -797,7 +806,9 @@ __global__ void k_eval_joints(Dev<T> D, int buf, int force) {
   else if (buf == IT_DEV_NEXT) buf = (D.fl->newton_n + 1) & 1;
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= D.nj) return;
-  if (!force && D.isl_on && (D.isl.stop[D.risl[3 * D.nc + 5 * j]] >= 0 || ls_done(D, D.risl[3 * D.nc + 5 * j]))) return;
+  if (!force && D.isl_on &&
+      (D.isl.stop[D.risl[3 * D.nc + 5 * j]] >= 0 || ls_done(D, D.risl[3 * D.nc + 5 * j]) || D.isl.ls_pre[D.risl[3 * D.nc + 5 * j]]))
+    return;
   const T h = D.hT;
   T pa[3], pb[3], axa[3], axb[3];
   for (int k = 0; k < 3; k++) { pa[k] = D.jpa[k][j]; pb[k] = D.jpb[k][j]; axa[k] = D.jaxa[k][j]; axb[k] = D.jaxb[k][j]; }
@@ -872,7 +883,9 @@ __global__ void k_eval_tets(Dev<T> D, int buf, int force) {
   else if (buf == IT_DEV_NEXT) buf = (D.fl->newton_n + 1) & 1;
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= D.nt) return;
-  if (!force && D.isl_on && (D.isl.stop[D.risl[D.Rpair + 3 * t]] >= 0 || ls_done(D, D.risl[D.Rpair + 3 * t]))) return;
+  if (!force && D.isl_on && (D.isl.stop[D.risl[D.Rpair + 3 * t]] >= 0 || ls_done(D, D.risl[D.Rpair + 3 * t]) ||
+                              D.isl.ls_pre[D.risl[D.Rpair + 3 * t]]))
+    return;
   const T h = D.hT;
   int v[4];
   for (int q = 0; q < 4; q++) v[q] = D.tv[4 * t + q];
@@ -952,7 +965,7 @@ template <int MODE, typename T>
 __device__ __forceinline__ bool isl_skip(const Dev<T> &D, int is, int force) {
   if (MODE == BM_APPLY) return D.isl.crdone[is] != 0;
   if (force) return false;
-  return D.isl.stop[is] >= 0 || (MODE == BM_RESIDUAL && ls_done(D, is));
+  return D.isl.stop[is] >= 0 || (MODE == BM_RESIDUAL && (ls_done(D, is) || D.isl.ls_pre[is]));
 }
 
 template <typename T, int G, int MODE>
@@ -1493,7 +1506,11 @@ __device__ __forceinline__ bool isl_merit_one(const Dev<T> &D, int i, int n, int
   acc[i] = 0.0; acc[ni + i] = 0.0;
   const double mi = sqrt(a);
   if (n == IT_TRIAL) {   // line search: the first trial below the merit at the head of the iteration
-    if (D.isl.stop[i] < 0 && D.isl.tacc[i] < 0.0 && mi < D.isl.mf[i]) D.isl.tacc[i] = trial_t;
+    if (D.isl.stop[i] < 0 && D.isl.tacc[i] < 0.0 && mi < D.isl.mf[i]) {
+      D.isl.tacc[i] = trial_t;
+      D.isl.mls[i] = mi;
+      D.isl.ls_pre[i] = D.isl.rigid[i];
+    }
     m2 += a;
     return false;
   }
@@ -1503,19 +1520,23 @@ __device__ __forceinline__ bool isl_merit_one(const Dev<T> &D, int i, int n, int
   if (final_eval) { D.isl.mf[i] = mi; m2 += a; return false; }
   if (force) { m2 += a; return false; }     // evaluation without a stop test
   int st = D.isl.stop[i];
+  // evaluated by the accepted line-search trial: its merit (the rhs pass added
+  // only |h|^2 here, the residual pass was skipped)
+  double an = a, mn = mi;
+  if (D.isl.ls_pre[i]) { mn = D.isl.mls[i]; an = mn * mn; D.isl.ls_pre[i] = 0; }
   if (st >= 0) {                            // stopped: not evaluated, keeps its last merit
     m2 += D.isl.mf[i] * D.isl.mf[i];
     D.isl.crdone[i] = 1;
     return false;
   }
-  m2 += a;
-  D.isl.mf[i] = mi;
-  if (n == 0 && !D.warm) D.isl.m0[i] = mi;
+  m2 += an;
+  D.isl.mf[i] = mn;
+  if (n == 0 && !D.warm) D.isl.m0[i] = mn;
   const double m0 = D.isl.m0[i];
-  if (D.tol_rel > 0.0 && mi <= D.tol_rel * m0) { st = n; D.isl.stop[i] = n; }
+  if (D.tol_rel > 0.0 && mn <= D.tol_rel * m0) { st = n; D.isl.stop[i] = n; }
   double eta = 0.0;
   if (D.cr_tol) {
-    eta = m0 > 0.0 ? mi / m0 : 0.0;
+    eta = m0 > 0.0 ? mn / m0 : 0.0;
     if (eta > 0.1) eta = 0.1;
     if (eta <= 0.0) eta = 1e-30;
   }
