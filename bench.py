@@ -18,7 +18,8 @@ trajectory advances from the seeded start state (no reset between steps).
             of Sec. 8.1 (trials t = 1 .. 1/16, else the damped 0.75; --line-search
             0: the damped step), projected onto the friction cone (option
             cone_project); CR per island in shared memory where it fits
-  arms      the same measurement for: the headline with the damped step, the
+  arms      the same measurement for: the headline in the FP64 build, the
+            headline with the damped step, the
             plain batched method (zero start; damped and with the line
             search), the printed update, the previous-step start alone, the
             first step after an environment reset with the zero / learned
@@ -295,9 +296,9 @@ CR_TOL = 0      # --cr-tol 1: CR of a Newton iteration also stops at the forcing
 LS = 1          # --line-search 0: the headline arm takes the damped step of Sec. 8.1 instead
 
 
-def make_solver(nsn, s, stream, newton, cr, cone, warm=0, params=None, ncp=0, rscale=2, ls=0):
+def make_solver(nsn, s, stream, newton, cr, cone, warm=0, params=None, ncp=0, rscale=2, ls=0, fp64=False):
     g = nsn.Solver(s, stream=stream.cuda_stream, newton_iters=newton, cr_iters=cr, tol_rel=TOL, island_stop=1,
-                   cone_project=cone, precision=nsn.NSN_FP32, use_graph=0 if EAGER else 1, ncp=ncp, rscale=rscale,
+                   cone_project=cone, precision=nsn.NSN_FP64 if fp64 else nsn.NSN_FP32, use_graph=0 if EAGER else 1, ncp=ncp, rscale=rscale,
                    cr_resident=RESIDENT, cr_tol_mode=CR_TOL, line_search=ls)
     if params is not None:
         nsn.nsn_mlp_set_params(g.ctx, params)
@@ -457,7 +458,8 @@ def run_ours(args, rank, world, local_rank):
         arms = {}
         if args.arms:
             # (name, cone projection, warm start, reset every step, NCP function, r strategy, line search)
-            for name, cone, wm, reset, ncp, rs, ls in (("damped_update" if LS else "line_search", 1, warm_names[warm],
+            for name, cone, wm, reset, ncp, rs, ls in (("fp64_bulk", 1, warm_names[warm], False, 0, 2, LS),
+                                                   ("damped_update" if LS else "line_search", 1, warm_names[warm],
                                                     False, 0, 2, 0 if LS else 1),
                                                    ("plain_zero_start", 1, nsn.NSN_WARM_ZERO, False, 0, 2, 0),
                                                    ("plain_zero_start_line_search", 1, nsn.NSN_WARM_ZERO, False, 0, 2, 1),
@@ -468,12 +470,14 @@ def run_ours(args, rank, world, local_rank):
                                                    ("ablation_min_map", 1, nsn.NSN_WARM_ZERO, True, 1, 2, 0),
                                                    ("ablation_r_h2", 1, nsn.NSN_WARM_ZERO, True, 0, 1, 0),
                                                    ("ablation_r_identity", 1, nsn.NSN_WARM_ZERO, True, 0, 0, 0)):
-                if wm == warm_names[warm] and not reset and cone == 1 and ncp == 0 and rs == 2 and ls == LS:
+                fp64 = name == "fp64_bulk"
+                if wm == warm_names[warm] and not reset and cone == 1 and ncp == 0 and rs == 2 and ls == LS and not fp64:
                     continue
                 if wm == nsn.NSN_WARM_LEARNED and params is None:
                     arms[name] = {"unavailable": "no trained weights (paper_1907_04587_gb300/weights)"}
                     continue
-                ga = make_solver(nsn, s, stream, newton, cr, cone=cone, warm=wm, params=params, ncp=ncp, rscale=rs, ls=ls)
+                ga = make_solver(nsn, s, stream, newton, cr, cone=cone, warm=wm, params=params, ncp=ncp, rscale=rs, ls=ls,
+                                 fp64=fp64)
                 try:
                     r = measure_arm(nsn, torch, ga, s, st0, stream, args.steps, args.warmup, reset=reset)
                 except nsn.NSNError as e:      # the method failing on this variant is a result
