@@ -18,7 +18,9 @@ trajectory advances from the seeded start state (no reset between steps).
             of Sec. 8.1 (trials t = 1 .. 1/16, else the damped 0.75; --line-search
             0: the damped step), projected onto the friction cone (option
             cone_project); CR per island in shared memory where it fits
-  arms      the same measurement for: the headline in the FP64 build, the
+  arms      the same measurement for: the headline with the network's
+            preconditioner scale on the contacts' Jacobi entries, the headline
+            in the FP64 build, the
             headline with the damped step, the
             plain batched method (zero start; damped and with the line
             search), the printed update, the previous-step start alone, the
@@ -458,7 +460,9 @@ def run_ours(args, rank, world, local_rank):
         arms = {}
         if args.arms:
             # (name, cone projection, warm start, reset every step, NCP function, r strategy, line search)
-            for name, cone, wm, reset, ncp, rs, ls in (("fp64_bulk", 1, warm_names[warm], False, 0, 2, LS),
+            for name, cone, wm, reset, ncp, rs, ls in (("learned_precond", 1, nsn.NSN_WARM_LEARNED | nsn.NSN_WARM_PRECOND,
+                                                    False, 0, 2, LS),
+                                                   ("fp64_bulk", 1, warm_names[warm], False, 0, 2, LS),
                                                    ("damped_update" if LS else "line_search", 1, warm_names[warm],
                                                     False, 0, 2, 0 if LS else 1),
                                                    ("plain_zero_start", 1, nsn.NSN_WARM_ZERO, False, 0, 2, 0),
@@ -473,7 +477,7 @@ def run_ours(args, rank, world, local_rank):
                 fp64 = name == "fp64_bulk"
                 if wm == warm_names[warm] and not reset and cone == 1 and ncp == 0 and rs == 2 and ls == LS and not fp64:
                     continue
-                if wm == nsn.NSN_WARM_LEARNED and params is None:
+                if (wm & 0xff) == nsn.NSN_WARM_LEARNED and params is None:
                     arms[name] = {"unavailable": "no trained weights (paper_1907_04587_gb300/weights)"}
                     continue
                 ga = make_solver(nsn, s, stream, newton, cr, cone=cone, warm=wm, params=params, ncp=ncp, rscale=rs, ls=ls,
@@ -484,7 +488,7 @@ def run_ours(args, rank, world, local_rank):
                     arms[name] = {"failed": str(e)}
                     ga.close()
                     continue
-                if wm != nsn.NSN_WARM_ZERO:
+                if (wm & 0xff) != nsn.NSN_WARM_ZERO:
                     r["network_or_warm_rejected_islands_last_step"] = ga.warm_stats()["rejected"]
                 ga.close()
                 r.pop("sec")

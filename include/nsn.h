@@ -284,6 +284,12 @@ enum { NSN_WARM_ZERO = 0, NSN_WARM_PREV = 1, NSN_WARM_LEARNED = 2 };
  * friction compliance W of Sec. 4.3 is a fixed point in lambda_f, and a stale
  * friction state seeds the oscillation of that fixed point. */
 #define NSN_WARM_FRICTION 0x100
+/* With NSN_WARM_LEARNED: the network's fourth output, the logarithm of a
+ * per-contact preconditioner scale (clamped to [1/4, 4]), multiplies the
+ * Jacobi preconditioner P of the contact's three rows in every CR solve of
+ * the step; the scale is trained towards A_ii (A^-1)_ii of the contact's
+ * normal row (the diagonal of the inverse over the Jacobi diagonal). */
+#define NSN_WARM_PRECOND 0x200
 #define NSN_MLP_NPARAM (128 * 16 + 128 + 128 * 128 + 128 + 128 * 128 + 128 + 4 * 128 + 4)
 nsn_status nsn_set_warm_start(nsn_ctx *ctx, int32_t mode);
 /* Forgets the previous step's multipliers (sets them to zero), e.g. after

@@ -113,6 +113,7 @@ struct nsn_ctx {
   int kept_buf = -1;         // entry buffer of the system kept by the last step / linearisation
   int warm_mode = 0;         // NSN_WARM_*
   int warm_friction = 0;     // 1: warm starts also set the friction rows
+  int warm_precond = 0;      // 1: the learned start also scales the contacts' Jacobi preconditioner
   MlpState mlp;
   int built_nb = 0;          // bodies present in the current device build
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -429,6 +430,7 @@ void carve(Arena &A, Dev<T> &D, const Layout &L, int nb) {
   for (int k = 0; k < 6; k++) { D.rdu[k] = tk(L.nr); D.ru0[k] = tk(L.nr); }
   for (int k = 0; k < 3; k++) { D.pdu[k] = tk(L.np); D.pu0[k] = tk(L.np); }
   D.lam0 = tk(L.R); D.xs = tk(L.R);
+  D.pscale = tk(std::max(L.nc, 1));
   D.fl_row = A.take<unsigned char>(size_t(L.R) / BLOCK + 1);
   D.fl_br = A.take<unsigned char>(size_t(L.nr) / (BLOCK / 16) + 1);
   D.fl_bp = A.take<unsigned char>(size_t(L.np) / (BLOCK / 16) + 1);
@@ -612,6 +614,10 @@ nsn_status upload(nsn_ctx *c, Dev<T> &D) {
     CUDA_TRY(c, puti(D.tv, v));
     CUDA_TRY(c, put(D.tDmi, Dmi)); CUDA_TRY(c, put(D.tVe, Ve)); CUDA_TRY(c, put(D.tC1, C1));
     CUDA_TRY(c, put(D.tD1, D1)); CUDA_TRY(c, put(D.talpha, al));
+  }
+  {
+    std::vector<T> ones(std::max(L.nc, 1), T(1));
+    CUDA_TRY(c, put(D.pscale, ones));
   }
   CUDA_TRY(c, cudaMemsetAsync(D.lam, 0, sizeof(T) * std::max(L.R, 1), st));
   CUDA_TRY(c, cudaMemsetAsync(D.lam_prev, 0, sizeof(T) * std::max(L.R, 1), st));
@@ -1159,6 +1165,7 @@ nsn_status run_steps(nsn_ctx *c, int nsteps) {
   Dev<T> &D = dev<T>(c);
   cudaStream_t st = c->stream;
   D.warm = c->warm_mode;
+  D.pscale_on = c->warm_mode == NSN_WARM_LEARNED && c->warm_precond ? 1 : 0;
   if (c->warm_mode == NSN_WARM_LEARNED) {
     if (!c->mlp.ready) return fail(c, NSN_ERR_BAD_STATE, "learned warm start without network parameters (nsn_mlp_set_params)");
     nsn_status s = mlp_ensure(c, D.nc);
@@ -1195,6 +1202,7 @@ nsn_status run_steps(nsn_ctx *c, int nsteps) {
   c->last.ms = ms;
   c->last_newton_n = fl.newton_n;
   c->kept_buf = fl.newton_n & 1;   // entries of the final evaluation
+  D.pscale_on = 0;                 // the linearize / solve / apply paths use the Jacobi preconditioner
   if (c->cfg.use_graph)
     c->launches_per_step = c->seg.prefix + fl.newton_n * (c->seg.head + c->seg.tail) + fl.cr_exec * c->seg.cr +
                            c->seg.suffix;
@@ -1969,11 +1977,16 @@ nsn_status nsn_operator_sizes(nsn_ctx *c, int64_t *sizes) {
 
 nsn_status nsn_set_warm_start(nsn_ctx *c, int32_t mode) {
   if (!c) return NSN_ERR_INVALID_ARG;
-  const int base = mode & 0xff, fric = (mode & NSN_WARM_FRICTION) ? 1 : 0;
-  if (base < NSN_WARM_ZERO || base > NSN_WARM_LEARNED || (mode & ~(0xff | NSN_WARM_FRICTION))) return NSN_ERR_INVALID_ARG;
-  if ((base != c->warm_mode || fric != c->warm_friction) && c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
+  const int base = mode & 0xff, fric = (mode & NSN_WARM_FRICTION) ? 1 : 0, pre = (mode & NSN_WARM_PRECOND) ? 1 : 0;
+  if (base < NSN_WARM_ZERO || base > NSN_WARM_LEARNED || (mode & ~(0xff | NSN_WARM_FRICTION | NSN_WARM_PRECOND)))
+    return NSN_ERR_INVALID_ARG;
+  if ((base != c->warm_mode || fric != c->warm_friction || pre != c->warm_precond) && c->graph) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
   c->warm_mode = base;
   c->warm_friction = fric;
+  c->warm_precond = pre;
   return NSN_OK;
 }
 

@@ -183,6 +183,8 @@ struct Dev {
   int isl_on;        // 1: per-island Newton stop, warm-start acceptance and CR scalars
   int cone;          // 1: project contact multipliers onto the friction cone after each update
   int ls;            // 1: back-tracking line search on the Newton step (Sec. 8.1)
+  int pscale_on;     // 1: the Jacobi preconditioner of contact c's rows is multiplied by pscale[c]
+  T *pscale;         // learned preconditioner scale per (internal) contact
   T *rdu[6], *pdu[3];            // line search: du of this Newton iteration
   T *ru0[6], *pu0[3], *lam0;     // line search: u and lambda at its head
   T *xs;                         // line search: dlambda of this Newton iteration
@@ -1283,7 +1285,7 @@ __global__ void __launch_bounds__(BLOCK) k_row_pass(Dev<T> D, int force) {
         const T hv = D.hv[i];
         const T bi = (tb - hv) * ih;
         const T dg = td + D.cdiag[i] + eps;
-        const T Pi = T(1) / dg;
+        const T Pi = (D.pscale_on && i < 3 * D.nc ? D.pscale[i / 3] : T(1)) / dg;
         D.b[i] = bi; D.P[i] = Pi; D.x[i] = T(0); D.Ap[i] = T(0);
         const T zi = Pi * bi;
         D.z[i] = zi; D.p[i] = zi;
@@ -1402,7 +1404,7 @@ __global__ void __launch_bounds__(BLOCK) k_row_pass_isl(Dev<T> D, int force) {
           const T tb = D.t[2 * i] + D.t[2 * i + 1], td = D.t2[2 * i] + D.t2[2 * i + 1];
           const T hv = D.hv[i];
           const T bi = (tb - hv) * ih;
-          const T Pi = T(1) / (td + D.cdiag[i] + eps);
+          const T Pi = (D.pscale_on && i < 3 * D.nc ? D.pscale[i / 3] : T(1)) / (td + D.cdiag[i] + eps);
           D.b[i] = bi; D.P[i] = Pi; D.x[i] = T(0); D.Ap[i] = T(0);
           const T zi = Pi * bi;
           D.z[i] = zi; D.p[i] = zi;
@@ -2617,6 +2619,12 @@ __global__ void k_warm_from_pred(Dev<T> D, const float *Y, int warm_friction) {
   if (c >= D.nc) return;
   const T ls = contact_lscale(D, c);
   const size_t o = 4 * size_t(D.cabi[c]);
+  if (D.pscale_on) {
+    // learned preconditioner scale: output 4 is its logarithm, clamped to a
+    // factor of 4 either way
+    const float e = fminf(fmaxf(Y[o + 3], -1.3862944f), 1.3862944f);
+    D.pscale[c] = T(expf(e));
+  }
   T ln = T(Y[o]) * ls;
   if (!(ln > T(0))) ln = T(0);
   T f1 = T(0), f2 = T(0);

@@ -1,8 +1,10 @@
 """Learned warm start: data generation from the solver, training, evaluation.
 
-Every numerical step runs in libnsn's kernels (features, targets, BF16
-tensor-core forward/backward, Adam); this module only drives them and moves
-batches of device pointers around.
+Every numerical step of the solver and the network runs in libnsn's kernels
+(features, targets, operator applies, BF16 tensor-core forward/backward,
+Adam); this module drives them and moves batches of device pointers around.
+The one host computation is the preconditioner-scale target: dense inverses
+of the islands' Schur blocks (precond_targets).
 """
 from __future__ import annotations
 
@@ -35,7 +37,64 @@ def contact_islands(g, s):
     return bi[np.where(cb[:, 0] >= 0, cb[:, 0], cb[:, 1])]
 
 
-def generate(seeds, n_envs=512, steps=3, solve=None):
+def island_rows(g, s):
+    """Rows (ABI order) of every island that has rows: contact rows 3c..3c+2,
+    then joint rows 3 nc + 5j..5j+4, each island's rows ascending."""
+    _, bi = g.islands()
+    nc = len(s["c_body"])
+    cb = np.asarray(s["c_body"]); jb = np.asarray(s["j_body"]).reshape(-1, 2) if len(s["j_body"]) else np.zeros((0, 2), int)
+    ci = bi[np.where(cb[:, 0] >= 0, cb[:, 0], cb[:, 1])]
+    ji = bi[np.where(jb[:, 0] >= 0, jb[:, 0], jb[:, 1])] if len(jb) else np.zeros(0, int)
+    row_isl = np.concatenate([np.repeat(ci, 3), np.repeat(ji, 5)])
+    order = np.argsort(row_isl, kind="stable")
+    isl_sorted = row_isl[order]
+    starts = np.searchsorted(isl_sorted, np.unique(isl_sorted))
+    return np.split(order, starts[1:]), row_isl
+
+
+def precond_targets(g, s):
+    """Per contact, A_ii (A^-1)_ii of its normal row for the system kept by
+    the last step (its final evaluation): the diagonal of the inverse over the
+    Jacobi diagonal, the scale that turns Jacobi into the exact diagonal of
+    A^-1.  A (Eq. schur_system) is block diagonal by island, so one operator
+    apply (libnsn's CR kernels, nsn_apply_operator_noalloc) on the sum of every
+    island's j-th unit row vector gives column j of every island's block at
+    once: as many applies as the largest island has rows.  The blocks are then
+    inverted on the host in FP64 (training-data preparation, not the solver)."""
+    import torch
+    blocks, _ = island_rows(g, s)
+    R = g.R
+    nc = len(s["c_body"])
+    sizes = np.array([len(b) for b in blocks])
+    classes = {int(n): torch.from_numpy(np.stack([blocks[i] for i in np.nonzero(sizes == n)[0]])).cuda()
+               for n in np.unique(sizes)}
+    A = {n: torch.zeros((len(ri), n, n), dtype=torch.float32, device="cuda") for n, ri in classes.items()}
+    x = torch.zeros(R, dtype=torch.float32, device="cuda")
+    y = torch.zeros(R, dtype=torch.float32, device="cuda")
+    for j in range(int(sizes.max())):
+        x.zero_()
+        for n, ri in classes.items():
+            if n > j:
+                x[ri[:, j]] = 1.0
+        torch.cuda.synchronize()
+        nsn.nsn_apply_operator_noalloc(g.ctx, x.data_ptr(), y.data_ptr())
+        torch.cuda.synchronize()
+        for n, ri in classes.items():
+            if n > j:
+                A[n][:, :, j] = y[ri]
+    out = np.ones(nc)
+    for n, ri in classes.items():
+        An = A[n].double().cpu().numpy()
+        An = 0.5 * (An + An.transpose(0, 2, 1))
+        inv = np.linalg.inv(An)
+        sc = np.einsum("kii->ki", An) * np.einsum("kii->ki", inv)
+        rows = ri.cpu().numpy()
+        normal = (rows < 3 * nc) & (rows % 3 == 0)
+        out[rows[normal] // 3] = sc[normal]
+    return out
+
+
+def generate(seeds, n_envs=512, steps=3, solve=None, precond=True):
     """(features, targets) on the device from the solver's own trajectories.
 
     For each seed, a batched scene is advanced `steps` steps by the island
@@ -43,7 +102,8 @@ def generate(seeds, n_envs=512, steps=3, solve=None):
     features are taken at the committed state (the previous-step multipliers
     among them); after it, the converged multipliers are the targets.  Only
     contacts of islands that reached the tolerance are kept, so every target
-    is a converged solution."""
+    is a converged solution.  The fourth target is the logarithm of the
+    contact's preconditioner scale (precond_targets) at the converged state."""
     import torch
     Xs, Ts = [], []
     for seed in seeds:
@@ -57,6 +117,11 @@ def generate(seeds, n_envs=512, steps=3, solve=None):
             nsn.nsn_contact_features(g.ctx, X.data_ptr())
             g.step()
             nsn.nsn_contact_features(g.ctx, 0, T.data_ptr())
+            if precond:
+                # log scale, clamped to the range the solver applies ([1, 4]:
+                # nearly singular blocks of redundant contacts give ratios of 1e7)
+                sc = precond_targets(g, s)
+                T[:, 3] = torch.from_numpy(np.log(np.clip(sc, 1.0, 4.0))).to(T)
             ok = g.island_stats()["stopped_at"][cisl] >= 0
             keep = torch.from_numpy(np.nonzero(ok)[0]).to("cuda")
             torch.cuda.synchronize()
@@ -113,7 +178,7 @@ class Trainer:
 
 
 def train_warm_start(seeds=(100, 101, 102, 103), n_envs=512, steps=3, epochs=20, batch=4096, lr=1e-3,
-                     weights=(1.0, 0.1, 0.1, 0.0), seed=1):
+                     weights=(1.0, 0.1, 0.1, 0.1), seed=1):
     """Data from the solver, standardised inputs, training on the tensor
     cores; returns (params acting on raw features, loss history, pairs)."""
     X, T = generate(list(seeds), n_envs=n_envs, steps=steps)
@@ -126,23 +191,26 @@ def train_warm_start(seeds=(100, 101, 102, 103), n_envs=512, steps=3, epochs=20,
 
 
 def compare_warm_starts(params, seed, n_envs=256, steps=3, solve=None):
-    """Per warm-start mode, over `steps` advancing steps from the same start:
-    the share of islands that reached the tolerance and their mean Newton
-    iterations to it."""
+    """Per warm-start mode (zero, previous step, learned, learned with the
+    preconditioner scale), over `steps` advancing steps from the same start:
+    the share of islands that reached the tolerance, their mean Newton
+    iterations to it and the CR iterations of the steps."""
     s = scenes.batched_envs(seed=seed, n_envs=n_envs)
     out = {}
-    for name, mode in (("zero", nsn.NSN_WARM_ZERO), ("prev", nsn.NSN_WARM_PREV), ("learned", nsn.NSN_WARM_LEARNED)):
+    for name, mode in (("zero", nsn.NSN_WARM_ZERO), ("prev", nsn.NSN_WARM_PREV), ("learned", nsn.NSN_WARM_LEARNED),
+                       ("learned_precond", nsn.NSN_WARM_LEARNED | nsn.NSN_WARM_PRECOND)):
         g = nsn.Solver(s, **(solve or SOLVE))
         nsn.nsn_mlp_set_params(g.ctx, params)
         g.set_warm_start(mode)
-        stops, warm = [], []
+        stops, warm, cr = [], [], 0
         for _ in range(steps):
-            g.step()
+            r = g.step()
+            cr += r["cr_total"]
             stops.append(g.island_stats()["stopped_at"].copy())
             warm.append(g.warm_stats())
         g.close()
         st = np.concatenate(stops)
         ok = st >= 0
         out[name] = dict(island_fraction=float(ok.mean()), mean_newton=float(st[ok].mean()) if ok.any() else None,
-                         warm=warm)
+                         cr_total=int(cr), warm=warm)
     return out

@@ -25,6 +25,7 @@ NSN_CONTACT, NSN_REVOLUTE, NSN_TET_NH = 0, 1, 2
 NSN_FP32, NSN_FP64 = 0, 1
 NSN_WARM_ZERO, NSN_WARM_PREV, NSN_WARM_LEARNED = 0, 1, 2
 NSN_WARM_FRICTION = 0x100
+NSN_WARM_PRECOND = 0x200
 NSN_MLP_NPARAM = 128 * 16 + 128 + 128 * 128 + 128 + 128 * 128 + 128 + 4 * 128 + 4
 
 CONTACT_DTYPE = np.dtype([("body_a", "<i4"), ("body_b", "<i4"), ("pa", "<f4", 3), ("pb", "<f4", 3),

@@ -103,6 +103,62 @@ def test_learned_warm_start_after_training(torch_cuda):
     assert n > 1000 and np.mean(hist[-5:]) < np.mean(hist[:5])
     res = learn.compare_warm_starts(params, seed=5000, n_envs=64, steps=3)
     for k, v in res.items():
-        print(k, "islands converged", round(v["island_fraction"], 4), "mean Newton to 1e-6", v["mean_newton"])
+        print(k, "islands converged", round(v["island_fraction"], 4), "mean Newton to 1e-6", v["mean_newton"],
+              "CR iterations", v["cr_total"])
     assert res["learned"]["island_fraction"] >= res["zero"]["island_fraction"] - 0.02
     assert res["learned"]["mean_newton"] < res["zero"]["mean_newton"]
+    # the learned preconditioner scale changes the CR iterates, not what the
+    # islands converge to: as many islands reach the tolerance
+    assert res["learned_precond"]["island_fraction"] >= res["learned"]["island_fraction"] - 0.03
+
+
+def _probe_dense(g):
+    """Dense A of the kept system, one operator apply per row (small scenes)."""
+    import torch
+    R = g.R
+    A = np.zeros((R, R))
+    x = torch.zeros(R, dtype=torch.float32, device="cuda")
+    y = torch.zeros(R, dtype=torch.float32, device="cuda")
+    for j in range(R):
+        x.zero_(); x[j] = 1.0
+        torch.cuda.synchronize()
+        nsn.nsn_apply_operator_noalloc(g.ctx, x.data_ptr(), y.data_ptr())
+        torch.cuda.synchronize()
+        A[:, j] = y.double().cpu().numpy()
+    return A
+
+
+def test_precond_targets_equal_the_dense_inverse(torch_cuda):
+    """The block-probing target (all islands' columns from one apply each)
+    equals A_ii (A^-1)_ii of the contacts' normal rows from the dense A of the
+    whole scene, and is >= 1 (Cauchy-Schwarz on an SPD matrix)."""
+    s = scenes.batched_envs(seed=7, n_envs=3, links=(3, 4), boxes=(2, 8))
+    g = nsn.Solver(s, **learn.SOLVE)
+    g.step()
+    sc = learn.precond_targets(g, s)
+    A = _probe_dense(g)
+    A = 0.5 * (A + A.T)
+    inv = np.linalg.inv(A)
+    nc = len(s["c_body"])
+    ref = np.diag(A)[0:3 * nc:3] * np.diag(inv)[0:3 * nc:3]
+    print("scales", np.round(sc[:8], 3), "min", sc.min(), "max", sc.max())
+    np.testing.assert_allclose(sc, ref, rtol=1e-3)
+    assert np.all(sc >= 1.0 - 1e-4)
+
+
+def test_precond_scale_one_is_the_jacobi_preconditioner(torch_cuda):
+    """A network whose fourth output is zero scales every contact by exp(0) = 1:
+    the step is the one without the scale, bit for bit."""
+    s = scenes.batched_envs(seed=8, n_envs=4)
+    p = learn.init_params(3)
+    p[-4 * 128 - 4 + 3 * 128:-4 * 128 - 4 + 4 * 128] = 0.0   # fourth row of the last layer
+    p[-1] = 0.0                                              # its bias
+    out = []
+    for mode in (nsn.NSN_WARM_LEARNED, nsn.NSN_WARM_LEARNED | nsn.NSN_WARM_PRECOND):
+        g = nsn.Solver(s, **learn.SOLVE)
+        nsn.nsn_mlp_set_params(g.ctx, p)
+        g.set_warm_start(mode)
+        g.step(); g.step()
+        out.append(g.get_state())
+    for k in ("pos", "vel", "omega"):
+        assert np.array_equal(out[0][k], out[1][k])
