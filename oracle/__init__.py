@@ -17,6 +17,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
+_SRC_COLLIDE = os.path.join(_HERE, "collide.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
 NCP_FB, NCP_MIN = 0, 1
@@ -27,9 +28,10 @@ GS_OFF, GS_PARTICLES = 0, 1
 def build(force: bool = False) -> str:
     """Compile liboracle.so with gcc (plain C99, -O2, no fast-math)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(
-            os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "oracle.h"))):
+            os.path.getmtime(_SRC), os.path.getmtime(_SRC_COLLIDE), os.path.getmtime(os.path.join(_HERE, "oracle.h"))):
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp,
+                               _SRC, _SRC_COLLIDE, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -63,6 +65,22 @@ class _Params(C.Structure):
 class _Stats(C.Structure):
     _fields_ = [("newton_done", C.c_int32), ("cr_total", C.c_int32), ("merit0", C.c_double),
                 ("merit_first", C.c_double), ("merit_final", C.c_double)]
+
+
+_fp = C.POINTER(C.c_float)
+
+
+class _CollideIn(C.Structure):
+    _fields_ = [
+        ("n_bodies", C.c_int32), ("kind", _ip), ("pos", _fp), ("quat", _fp), ("vel", _fp), ("omega", _fp),
+        ("half", _fp), ("env", _ip), ("n_planes", C.c_int32), ("planes", _fp), ("n_exclude", C.c_int32),
+        ("exclude", _ip), ("mu_env", _fp), ("margin", C.c_float), ("h", C.c_float),
+    ]
+
+
+class _Contacts(C.Structure):
+    _fields_ = [("capacity", C.c_int32), ("c_body", _ip), ("c_pa", _dp), ("c_pb", _dp), ("c_n", _dp),
+                ("c_d", _dp), ("c_mu", _dp)]
 
 
 _lib = None
@@ -108,6 +126,8 @@ def lib():
         L.orc_nh_grad_hess.argtypes = [_dp, C.c_double, C.c_double, C.c_double, _dp, _dp]
         L.orc_svd3.argtypes = [_dp, _dp, _dp, _dp]
         L.orc_basis.argtypes = [_dp, _dp, _dp]
+        L.orc_collide.restype = C.c_int32
+        L.orc_collide.argtypes = [C.POINTER(_CollideIn), C.POINTER(_Contacts)]
     return _lib
 
 
@@ -340,3 +360,39 @@ def basis(n):
     t1 = np.zeros(3); t2 = np.zeros(3)
     lib().orc_basis(_ptr(_d(n, (3,))), _ptr(t1), _ptr(t2))
     return t1, t2
+
+
+def collide(kind, pos, quat, vel, omega, half, env, planes, exclude, mu_env, margin, h):
+    """Contact generation of Sec. 3.3 / Sec. 10 (collide.c): candidates of body
+    vertices against static planes and the boxes of their environment within
+    ``margin``, at the start of the step or at the position predicted with the
+    unconstrained velocity (vel, omega), over a step h.  Inputs are rounded to
+    FP32 (what the GPU path receives); returns the contact arrays of a scene
+    dictionary (c_body, c_pa, c_pb, c_n, c_d, c_mu), geometry in FP64."""
+    f32 = lambda a, c: np.ascontiguousarray(np.asarray(a, np.float32).reshape(-1, c))
+    i32 = lambda a: np.ascontiguousarray(np.asarray(a, np.int32).ravel())
+    kind, env = i32(kind), i32(env)
+    pos, quat, vel, omega, half = f32(pos, 3), f32(quat, 4), f32(vel, 3), f32(omega, 3), f32(half, 3)
+    planes = f32(planes, 4) if planes is not None and len(planes) else np.zeros((0, 4), np.float32)
+    exclude = (np.ascontiguousarray(np.asarray(exclude, np.int32).reshape(-1, 2))
+               if exclude is not None and len(exclude) else np.zeros((0, 2), np.int32))
+    mu_env = np.ascontiguousarray(np.asarray(mu_env, np.float32).ravel())
+    nb = len(kind)
+    assert len(env) == nb and (nb == 0 or (np.all(np.diff(env) >= 0) and env.max() < len(mu_env)))
+    fp = lambda a: a.ctypes.data_as(_fp)
+    ip = lambda a: a.ctypes.data_as(_ip)
+    ci = _CollideIn(nb, ip(kind), fp(pos), fp(quat), fp(vel), fp(omega), fp(half), ip(env), len(planes), fp(planes),
+                    len(exclude), ip(exclude), fp(mu_env), float(margin), float(h))
+    cap = 0
+    while True:
+        out = dict(c_body=np.zeros((cap, 2), np.int32), c_pa=np.zeros((cap, 3)), c_pb=np.zeros((cap, 3)),
+                   c_n=np.zeros((cap, 3)), c_d=np.zeros(cap), c_mu=np.zeros(cap))
+        dp = lambda a: a.ctypes.data_as(_dp)
+        co = _Contacts(cap, ip(out["c_body"]), dp(out["c_pa"]), dp(out["c_pb"]), dp(out["c_n"]), dp(out["c_d"]),
+                       dp(out["c_mu"]))
+        n = lib().orc_collide(C.byref(ci), C.byref(co))
+        if n < 0:
+            raise ValueError("orc_collide: excluded pair out of range")
+        if n <= cap:
+            return {k: v[:n] for k, v in out.items()}
+        cap = n

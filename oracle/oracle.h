@@ -164,6 +164,40 @@ void orc_nh_grad_hess(const double s[3], double C1, double D1, double alpha, dou
 void orc_svd3(const double F[9], double U[9], double s[3], double V[9]);
 void orc_basis(const double n[3], double t1[3], double t2[3]);
 
+/* Contact generation (Sec. 3.3 contact constraints, Sec. 10 collision
+ * detection), in collide.c.  Inputs are FP32, as the GPU path receives them:
+ * bodies (kind, pos nb x 3, quat nb x 4 scalar first, the unconstrained
+ * velocity vel / omega nb x 3, box half extents nb x 3 -- a rigid body with a
+ * non-positive extent has no shape --, environment id nb, non-decreasing),
+ * static planes (n_planes x 4: unit normal, offset; the plane is n.x = offset,
+ * its solid side n.x < offset), excluded body pairs (n_exclude x 2, both ids
+ * >= 0, e.g. the bodies of a joint), friction per environment, the margin
+ * (> 0) and the time step h.  Output records as the contact arrays of
+ * orc_scene (b = -1 and a world point pb for a plane); at most capacity are
+ * written.  Returns the number of contacts found (may exceed capacity), or -1
+ * on a bad excluded pair. */
+typedef struct {
+  int32_t n_bodies;
+  const int32_t *kind;
+  const float *pos, *quat, *vel, *omega, *half;
+  const int32_t *env;
+  int32_t n_planes;
+  const float *planes;
+  int32_t n_exclude;
+  const int32_t *exclude;
+  const float *mu_env;
+  float margin, h;
+} orc_collide_in;
+
+typedef struct {
+  int32_t capacity;
+  int32_t *c_body;          /* capacity x 2 */
+  double *c_pa, *c_pb, *c_n; /* capacity x 3 */
+  double *c_d, *c_mu;       /* capacity */
+} orc_contacts;
+
+int32_t orc_collide(const orc_collide_in *in, orc_contacts *out);
+
 #ifdef __cplusplus
 }
 #endif

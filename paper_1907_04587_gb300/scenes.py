@@ -8,7 +8,8 @@ float32 so that the FP32 device path and the FP64 oracle see identical values.
 Scene dictionary (numpy arrays):
   kind[nb] (0 rigid, 1 particle), pos[nb,3], quat[nb,4] (w,x,y,z), vel[nb,3],
   omega[nb,3] (world frame), mass[nb], inertia[nb,3] (body-frame principal),
-  env[nb] (environment id, 0 for single scenes)
+  env[nb] (environment id, 0 for single scenes), half[nb,3] (box half extents
+  of a rigid body's collision shape; zeros: no shape, and for particles)
   c_body[nc,2] (-1 = static world), c_pa[nc,3], c_pb[nc,3] (body-local, or a
   world point for the world side), c_n[nc,3] (world normal from b to a),
   c_d[nc], c_mu[nc]
@@ -175,7 +176,8 @@ def cube_stack(seed=0, n=4, edge=1.0, density=1000.0, mu=0.5, jitter=1e-3, yaw_d
                   edge / 2 + i * edge + rng.uniform(-jitter, jitter))
         quat[i] = quat_yaw(np.deg2rad(rng.uniform(-yaw_deg, yaw_deg)))
     s = dict(kind=np.zeros(n, np.int32), pos=pos, quat=quat, vel=np.zeros((n, 3)), omega=np.zeros((n, 3)),
-             mass=np.full(n, m), inertia=np.tile(I, (n, 1)), env=np.zeros(n, np.int32))
+             mass=np.full(n, m), inertia=np.tile(I, (n, 1)), env=np.zeros(n, np.int32),
+             half=np.full((n, 3), edge / 2))
     s.update(stack_contacts(pos, quat, edge, mu))
     s.update(_empty_joints()); s.update(_empty_tets())
     return finalize(s)
@@ -283,7 +285,8 @@ def chain_block(seed=0, hexes=24, edge=0.5, E=1e5, nu=0.45, density=1000.0, link
                     c_d=np.zeros(kc), c_mu=np.full(kc, mu))
     t_rest = rest[tets]
     s = dict(kind=kind, pos=pos, quat=quat, vel=np.zeros((len(kind), 3)), omega=np.zeros((len(kind), 3)),
-             mass=mass, inertia=inertia, env=np.zeros(len(kind), np.int32), t_v=(tets + links).astype(np.int32),
+             mass=mass, inertia=inertia, env=np.zeros(len(kind), np.int32),
+             half=np.concatenate([np.tile(L / 2, (links, 1)), np.zeros((nv, 3))]), t_v=(tets + links).astype(np.int32),
              t_rest=t_rest, t_E=np.full(len(tets), E), t_nu=np.full(len(tets), nu))
     s.update(joints); s.update(contacts)
     return finalize(s)
@@ -401,7 +404,10 @@ def batched_envs(seed=0, n_envs=4096, links=(3, 20), boxes=(0, 64), box_edge=(0.
                     c_pa=np.concatenate([c_pa_l, c_pa_b]), c_pb=np.concatenate([c_pb_l, c_pb_b]),
                     c_n=np.concatenate([c_n_l, c_n_b]), c_d=np.zeros(4 * (n_l + len(bi))),
                     c_mu=np.concatenate([c_mu_l, c_mu_b]))
-    s = dict(kind=kind, pos=pos, quat=quat, vel=vel, omega=omega, mass=mass, inertia=inertia, env=env)
+    half = np.zeros((NB, 3))
+    half[li] = L / 2
+    half[bi] = edge[:, None] / 2
+    s = dict(kind=kind, pos=pos, quat=quat, vel=vel, omega=omega, mass=mass, inertia=inertia, env=env, half=half)
     s.update(joints); s.update(contacts); s.update(_empty_tets())
     return finalize(s)
 
@@ -488,4 +494,8 @@ def mixed_bin(seed=0, n_boxes=2000, n_spheres=8, sphere_radius=0.3, sphere_res=1
                 B.add_contact(bid, -1, (0, 0, 0), (0.0, p[1], p[2]), (1, 0, 0), 0.0, mu)
         for t in range(len(tets)):
             B.add_tet(tuple(tets[t] + first), rest[tets[t]], E, nu)
-    return B.build()
+    s = B.build()
+    half = np.zeros((len(s["mass"]), 3), F32)        # the boxes are bodies 0 .. n_boxes-1
+    half[:n_boxes] = (edges[:, None] / 2).astype(F32)
+    s["half"] = half
+    return s

@@ -13,7 +13,7 @@ import pytest
 
 from paper_1907_04587_gb300 import scenes
 
-BODY_KEYS = ("kind", "pos", "quat", "vel", "omega", "mass", "inertia", "env")
+BODY_KEYS = ("kind", "pos", "quat", "vel", "omega", "mass", "inertia", "env", "half")
 
 
 def sub_scene(s, bodies):
