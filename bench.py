@@ -219,6 +219,93 @@ def resident_roofline(g, clk):
             "smem_bytes_per_block": info["smem_bytes"], "grid": info["grid"], "max_island_rows": info["max_rows"]}
 
 
+# FP32 operations counted from the collider's source (every operation is a
+# separately rounded instruction): the rotation of a body's quaternion, once
+# per rigid body, 30; one vertex-box test -- lever arm 3, velocity at the
+# vertex 12, relative prediction 12, two box-frame transforms 30, two squared
+# distances 28, two compares 2 -- 87; one vertex-plane test -- two plane
+# distances 12, two compares 2 -- 14, plus the prediction, 6 per vertex.
+OPS_ROTATION = 30
+OPS_BOX_TEST = 87
+OPS_PLANE_TEST = 14
+OPS_VERTEX = 6
+
+
+def contact_generation(nsn, torch, s, stream, clk, iters=20):
+    """Contact generation (Sec. 3.3, Sec. 10) on the workload's bodies with
+    the ground plane: the collider's five kernels timed with CUDA events on
+    device buffers, and end to end through nsn_collider_run
+    (host arrays in and out).  Bound: FP32 ALU (the tests are independent
+    arithmetic on L2-resident body data)."""
+    if "half" not in s:
+        return None
+    n_envs = int(s["n_envs"])
+    planes = ((0.0, 0.0, 1.0, 0.0),)
+    col = nsn.Collider(s, planes=planes, mu_env=np.full(n_envs, 0.5, np.float32), stream=stream.cuda_stream)
+    ref = col.run(s["pos"], s["quat"], s["vel"], s["omega"])
+    n = len(ref["c_body"])
+    dev = torch.device("cuda", torch.cuda.current_device())
+    d = {k: torch.from_numpy(np.ascontiguousarray(s[k], dtype=np.float32)).to(dev) for k in ("pos", "quat", "vel", "omega")}
+    cap = n + 1024
+    out_t = dict(c_body=torch.empty((cap, 2), dtype=torch.int32, device=dev),
+                 **{k: torch.empty((cap, 3), device=dev) for k in ("c_pa", "c_pb", "c_n")},
+                 **{k: torch.empty(cap, device=dev) for k in ("c_d", "c_mu")})
+    out = {k: v.data_ptr() for k, v in out_t.items()}
+    out["capacity"] = cap
+    found = torch.zeros(1, dtype=torch.int32, device=dev)
+    args = [d[k].data_ptr() for k in ("pos", "quat", "vel", "omega")]
+    torch.cuda.synchronize()
+    for _ in range(3):
+        col.run_async(*args, out, found.data_ptr())
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(iters):
+        col.run_async(*args, out, found.data_ptr())
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / iters
+    assert int(found.item()) == n
+    t0 = time.perf_counter()
+    for _ in range(3):
+        col.run(s["pos"], s["quat"], s["vel"], s["omega"])
+    ms_e2e = (time.perf_counter() - t0) * 1e3 / 3
+    # tests per vertex: every plane, and the boxes of its environment other
+    # than its own body and the bodies it shares a joint with
+    kind, half, env = s["kind"], s["half"], s["env"]
+    box = (kind == 0) & np.all(half > 0, axis=1)
+    nvert = np.where(kind == 1, 1, np.where(box, 8, 0))
+    nbox_env = np.bincount(env, weights=box, minlength=n_envs)
+    excl = np.zeros(len(kind))
+    for a, b in col.exclude:
+        excl[a] += box[b]
+        excl[b] += box[a]
+    box_tests = nbox_env[env] - box - excl
+    tests_box = float((nvert * box_tests).sum())
+    tests_plane = float(nvert.sum() * len(planes))
+    # the emit pass repeats the tests of the vertices with contacts
+    vid = ref["c_body"][:, 0].astype(np.int64) * 8 + np.dot(ref["c_pa"] > 0, [1, 2, 4])
+    hit_body = np.unique(vid) // 8
+    hit = np.bincount(hit_body, minlength=len(kind))
+    per_vertex = OPS_BOX_TEST * box_tests + OPS_PLANE_TEST * len(planes) + OPS_VERTEX
+    ops = OPS_ROTATION * float((kind == 0).sum()) + per_vertex @ nvert + per_vertex @ hit
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    summ = clk.summary() if clk is not None else None
+    mhz = (summ or {}).get("sm_max_mhz") or 2070.0
+    peak = nsm * 128 * mhz * 1e6 / 1e12
+    ach = ops / (ms * 1e-3) / 1e12
+    info = col.info()
+    return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "Tops/s", "frac": ach / peak,
+            "peak_kind": f"derived: {nsm} SMs x 128 FP32 lanes x {mhz:.0f} MHz, one rounded op per lane per clock",
+            "kernel": ("k_col_prep + k_col_count + k_col_scan + k_col_emit (FP32, one thread per vertex over its "
+                       "environment's shapes) + k_col_geom (FP64 closest points and normals, one thread per contact); "
+                       "achieved = FP32 operations of the tests over the whole call"),
+            "ms": ms, "ms_e2e_host_arrays": ms_e2e, "contacts": n, "vertices": info["vertices"],
+            "tests": tests_box + tests_plane, "ops_per_box_test": OPS_BOX_TEST,
+            "ops_per_plane_test": OPS_PLANE_TEST, "fp32_ops": ops, "tests_per_s": (tests_box + tests_plane) / (ms * 1e-3),
+            "hand_built_scene_contacts": int(len(s["c_body"]))}
+
+
 def kernel_source_hash():
     h = hashlib.sha256()
     for f in ("nsn_kernels.cuh", "nsn_host.cu"):
@@ -493,6 +580,7 @@ def run_ours(args, rank, world, local_rank):
                 ga.close()
                 r.pop("sec")
                 arms[name] = r
+    contacts_rf = contact_generation(nsn, torch, s, stream, clk)
     B = algorithmic_bytes(sz)
     peak, peak_kind = measured_peaks()
     achieved = B / ((ms_body + ms_row) * 1e-3) / 1e9
@@ -544,6 +632,7 @@ def run_ours(args, rank, world, local_rank):
         "roofline": resident if resident is not None else apply_rf,
         "operator_apply_roofline": apply_rf,
         "network_roofline": mlp,
+        "contact_generation": contacts_rf,
         "cpu_baseline": cb,
         "e2e": {"value": value_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "note": "the state makes a host round trip every step; the trajectory advances"},

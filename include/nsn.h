@@ -366,6 +366,73 @@ nsn_status nsn_contact_features(nsn_ctx *ctx, float *X, float *Ytarget);
 #define NSN_NOALLOC_MAX_ENTRIES (4 * 1024 * 1024)
 nsn_status nsn_apply_operator_noalloc(nsn_ctx *ctx, const float *x, float *y, void *stream);
 
+/* ---- contact generation (Sec. 3.3, Sec. 10) ---------------------------------
+ * The paper creates a contact constraint when two features come within a
+ * fixed distance of each other (Sec. 3.3), runs collision detection once per
+ * time step with the unconstrained velocity to find candidates, and takes the
+ * normal as the normalised vector between the closest points at the start of
+ * the step (Sec. 10).  The collider does this for box and particle scenes:
+ *   vertices: the 8 corners of every rigid body with a box shape (corner k has
+ *             coordinate +half[i] on axis i where bit i of k is set, -half[i]
+ *             otherwise), and every particle;
+ *   shapes:   the static planes (all environments), and the rigid boxes of the
+ *             vertex's own environment other than its own body and the
+ *             excluded pairs (e.g. the two bodies of a joint).
+ * Vertex p of body A is a candidate against shape B when p, or its predicted
+ * position p + h (u_A(p) - u_B(p)) with u the unconstrained velocity field of
+ * each body (v + omega x r), lies within `margin` of B (inside a box counts as
+ * distance 0).  A contact record (the CONTACT layout of the scene arrays):
+ * body_a = A, body_b = B or -1 for a plane; pa = the corner in A's frame (0
+ * for a particle); pb = the closest point of B at the start of the step, in
+ * B's frame, or the world foot point on a plane; n = the world normal from B
+ * towards A: the plane normal, (p - closest point) / distance outside a box,
+ * the outward normal of the face of least penetration inside it; d = 0; mu =
+ * mu_env of A's environment.  Order: by vertex (body, then corner), then the
+ * planes in order, then the boxes in body order.  Candidate, outside/inside
+ * and nearest-face decisions are taken in FP32 with one rounding per
+ * operation; closest points and normals in FP64, rounded to FP32.
+ *
+ * nsn_collider_create: the static scene.  kind (0 rigid, 1 particle), half
+ * (n x 3 box half extents; a rigid body with any extent <= 0 has no shape and
+ * no vertices) and env (environment id per body, non-decreasing, in
+ * [0, n_envs)) for n_bodies bodies; mu_env (n_envs); planes (n_planes x 4:
+ * unit normal n and offset o of the plane n.x = o, solid side n.x < o);
+ * exclude (n_exclude x 2 body ids); margin > 0; h >= 0 the step of the
+ * prediction; stream: a cudaStream_t for all work of the collider, or NULL.
+ * Host arrays are copied; the caller keeps them.  Bad sizes, ids, order or
+ * values: NSN_ERR_INVALID_ARG; device memory: NSN_ERR_OUT_OF_MEMORY.
+ *
+ * nsn_collider_run: host arrays.  pos (n x 3), quat (n x 4, w x y z), vel and
+ * omega (n x 3, the unconstrained velocity, world frame) are copied in; at
+ * most `capacity` contacts are copied out to c_body (capacity x 2), c_pa,
+ * c_pb, c_n (capacity x 3), c_d, c_mu (capacity); *n_found = the number of
+ * contacts found.  Returns when the results are on the host.  More contacts
+ * than capacity: the first `capacity` are written and the call returns
+ * NSN_ERR_OUT_OF_MEMORY with *n_found set (call again with a larger buffer).
+ *
+ * nsn_collider_run_async: the same with device arrays on the collider's
+ * stream, nothing copied and nothing synchronised: the count goes to the
+ * device int32 *found_dev (may be NULL), contacts past `capacity` are not
+ * written.  The collider's scratch is shared by its calls: calls on one
+ * collider are serialised by its stream.
+ *
+ * nsn_collider_info: info4 = {bodies, vertices, planes, thread blocks per
+ * launch}.  Errors of a collider call: nsn_collider_last_error. */
+typedef struct nsn_collider nsn_collider;
+nsn_status nsn_collider_create(int32_t n_bodies, const int32_t *kind, const float *half, const int32_t *env,
+                               int32_t n_envs, const float *mu_env, int32_t n_planes, const float *planes,
+                               int32_t n_exclude, const int32_t *exclude, float margin, float h, void *stream,
+                               nsn_collider **out);
+nsn_status nsn_collider_destroy(nsn_collider *c);
+nsn_status nsn_collider_run(nsn_collider *c, const float *pos, const float *quat, const float *vel,
+                            const float *omega, int32_t capacity, int32_t *c_body, float *c_pa, float *c_pb,
+                            float *c_n, float *c_d, float *c_mu, int32_t *n_found);
+nsn_status nsn_collider_run_async(nsn_collider *c, const float *pos, const float *quat, const float *vel,
+                                  const float *omega, int32_t capacity, int32_t *c_body, float *c_pa, float *c_pb,
+                                  float *c_n, float *c_d, float *c_mu, int32_t *found_dev);
+nsn_status nsn_collider_info(const nsn_collider *c, int32_t *info4);
+const char *nsn_collider_last_error(const nsn_collider *c);
+
 #ifdef __cplusplus
 }
 #endif

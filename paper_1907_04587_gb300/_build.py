@@ -7,7 +7,7 @@ import subprocess
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libnsn.so")
-SOURCES = [os.path.join(CSRC, "nsn_host.cu")]
+SOURCES = [os.path.join(CSRC, "nsn_host.cu"), os.path.join(CSRC, "nsn_collide.cu")]
 DEPS = SOURCES + [os.path.join(CSRC, "nsn_kernels.cuh"),
                   os.path.join(os.path.dirname(HERE), "include", "nsn.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

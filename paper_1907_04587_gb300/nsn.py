@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libnsn.so")
 HEADER = os.path.join(os.path.dirname(_HERE), "include", "nsn.h")
 
 NSN_OK = 0
+NSN_ERR_INVALID_ARG, NSN_ERR_OUT_OF_MEMORY = 1, 2
 STATUS = {0: "NSN_OK", 1: "NSN_ERR_INVALID_ARG", 2: "NSN_ERR_OUT_OF_MEMORY", 3: "NSN_ERR_CUDA",
           4: "NSN_ERR_NOT_CONVERGED", 5: "NSN_ERR_TIMEOUT", 6: "NSN_ERR_BAD_STATE", 7: "NSN_ERR_NONFINITE"}
 NSN_RIGID, NSN_PARTICLE = 0, 1
@@ -117,6 +118,14 @@ def lib():
         "nsn_resident_info": (C.c_int, [_vp, _ip]),
         "nsn_time_resident": (C.c_int, [_vp, C.c_int32, _fp, _dp]),
         "nsn_set_body_lanes": (C.c_int, [_vp, C.c_int32]),
+        "nsn_collider_create": (C.c_int, [C.c_int32, _ip, _fp, _ip, C.c_int32, _fp, C.c_int32, _fp, C.c_int32,
+                                          _ip, C.c_float, C.c_float, _vp, C.POINTER(_vp)]),
+        "nsn_collider_destroy": (C.c_int, [_vp]),
+        "nsn_collider_run": (C.c_int, [_vp, _fp, _fp, _fp, _fp, C.c_int32, _ip, _fp, _fp, _fp, _fp, _fp, _ip]),
+        "nsn_collider_run_async": (C.c_int, [_vp, _vp, _vp, _vp, _vp, C.c_int32, _vp, _vp, _vp, _vp, _vp, _vp,
+                                             _vp]),
+        "nsn_collider_info": (C.c_int, [_vp, _ip]),
+        "nsn_collider_last_error": (C.c_char_p, [_vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -528,3 +537,115 @@ class Solver:
 
     def sizes(self):
         return nsn_operator_sizes(self.ctx)
+
+
+# ---- contact generation (Sec. 3.3, Sec. 10) ----------------------------------------
+
+class ColliderError(NSNError):
+    pass
+
+
+def nsn_collider_create(kind, half, env, n_envs, mu_env, planes, exclude, margin, h, stream=None):
+    kind = np.ascontiguousarray(np.asarray(kind, np.int32).ravel())
+    env = np.ascontiguousarray(np.asarray(env, np.int32).ravel())
+    n = len(kind)
+    half = _f32(half, (n, 3))
+    mu_env = _f32(mu_env, (-1,))
+    planes = _f32(planes, (-1, 4)) if planes is not None and len(planes) else np.zeros((0, 4), np.float32)
+    exclude = (np.ascontiguousarray(np.asarray(exclude, np.int32).reshape(-1, 2))
+               if exclude is not None and len(exclude) else np.zeros((0, 2), np.int32))
+    out = _vp()
+    st = lib().nsn_collider_create(n, _p(kind, _ip), _p(half), _p(env, _ip), int(n_envs), _p(mu_env), len(planes),
+                                   _p(planes), len(exclude), _p(exclude, _ip), float(margin), float(h), stream,
+                                   C.byref(out))
+    if st != NSN_OK:
+        raise ColliderError(st, "nsn_collider_create failed")
+    return out
+
+
+def nsn_collider_destroy(col):
+    return lib().nsn_collider_destroy(col)
+
+
+def nsn_collider_last_error(col):
+    m = lib().nsn_collider_last_error(col)
+    return m.decode() if m else ""
+
+
+def nsn_collider_info(col):
+    v = np.zeros(4, np.int32)
+    st = lib().nsn_collider_info(col, _p(v, _ip))
+    if st != NSN_OK:
+        raise ColliderError(st, "nsn_collider_info")
+    return dict(zip(("bodies", "vertices", "planes", "blocks"), (int(x) for x in v)))
+
+
+def nsn_collider_run(col, pos, quat, vel, omega, capacity):
+    """Host arrays in, contact arrays (a scene's c_* keys) out; grows the
+    buffers once if more than ``capacity`` contacts are found."""
+    n = len(pos)
+    arrs = [_f32(pos, (n, 3)), _f32(quat, (n, 4)), _f32(vel, (n, 3)), _f32(omega, (n, 3))]
+    for _ in range(2):
+        cap = int(capacity)
+        out = dict(c_body=np.zeros((cap, 2), np.int32), c_pa=np.zeros((cap, 3), np.float32),
+                   c_pb=np.zeros((cap, 3), np.float32), c_n=np.zeros((cap, 3), np.float32),
+                   c_d=np.zeros(cap, np.float32), c_mu=np.zeros(cap, np.float32))
+        found = C.c_int32()
+        st = lib().nsn_collider_run(col, *[_p(a) for a in arrs], cap, _p(out["c_body"], _ip), _p(out["c_pa"]),
+                                    _p(out["c_pb"]), _p(out["c_n"]), _p(out["c_d"]), _p(out["c_mu"]),
+                                    C.byref(found))
+        if st == NSN_ERR_OUT_OF_MEMORY and found.value > cap:
+            capacity = found.value
+            continue
+        if st != NSN_OK:
+            raise ColliderError(st, f"nsn_collider_run: {nsn_collider_last_error(col)}")
+        return {k: v[:found.value] for k, v in out.items()}
+    raise ColliderError(NSN_ERR_OUT_OF_MEMORY, "nsn_collider_run: contact count changed between calls")
+
+
+def nsn_collider_run_async(col, pos, quat, vel, omega, capacity, c_body, c_pa, c_pb, c_n, c_d, c_mu, found_dev):
+    """Device pointers (ints) in and out, on the collider's stream."""
+    st = lib().nsn_collider_run_async(col, pos, quat, vel, omega, int(capacity), c_body, c_pa, c_pb, c_n, c_d, c_mu,
+                                      found_dev)
+    if st != NSN_OK:
+        raise ColliderError(st, f"nsn_collider_run_async: {nsn_collider_last_error(col)}")
+
+
+class Collider:
+    """Contact generation for a scene dictionary with box half extents
+    (``half``): body corners and particles against ``planes`` (k x 4: normal,
+    offset) and the boxes of their environment; the bodies of every joint are
+    excluded from each other.  ``mu_env`` defaults to 0.5 per environment."""
+
+    def __init__(self, scene, planes=((0.0, 0.0, 1.0, 0.0),), margin=0.01, h=1.0 / 60.0, mu_env=None,
+                 exclude=None, stream=None):
+        s = scene
+        n_envs = int(s.get("n_envs", int(np.max(s["env"])) + 1 if len(s["env"]) else 1))
+        if exclude is None:
+            jb = np.asarray(s.get("j_body", np.zeros((0, 2), np.int32)))
+            exclude = jb[(jb[:, 0] >= 0) & (jb[:, 1] >= 0)] if len(jb) else jb
+        self.mu_env = np.full(n_envs, 0.5, np.float32) if mu_env is None else np.asarray(mu_env, np.float32)
+        self.planes, self.exclude = np.asarray(planes, np.float32).reshape(-1, 4), np.asarray(exclude, np.int32)
+        self.margin, self.h, self.n_envs = float(margin), float(h), n_envs
+        self.ptr = nsn_collider_create(s["kind"], s["half"], s["env"], n_envs, self.mu_env, self.planes,
+                                       self.exclude, margin, h, stream)
+        self.capacity = 8 * len(s["kind"]) + 16
+
+    def __del__(self):
+        if getattr(self, "ptr", None) is not None and _lib is not None:
+            nsn_collider_destroy(self.ptr)
+            self.ptr = None
+
+    def info(self):
+        return nsn_collider_info(self.ptr)
+
+    def run(self, pos, quat, vel, omega):
+        r = nsn_collider_run(self.ptr, pos, quat, vel, omega, self.capacity)
+        self.capacity = max(self.capacity, len(r["c_body"]))
+        return r
+
+    def run_async(self, pos, quat, vel, omega, out, found_dev):
+        """Device pointers: ``out`` maps c_body, c_pa, c_pb, c_n, c_d, c_mu to
+        (pointer) with room for ``out['capacity']`` contacts."""
+        nsn_collider_run_async(self.ptr, pos, quat, vel, omega, out["capacity"], out["c_body"], out["c_pa"],
+                               out["c_pb"], out["c_n"], out["c_d"], out["c_mu"], found_dev)

@@ -54,3 +54,15 @@ def test_invalid_arguments_are_rejected_without_gpu(libnsn):
 
 def test_built_for_sm103a():
     assert "compute_103a,code=sm_103a" in " ".join(_build.ARCH)
+
+
+def test_collider_rejects_invalid_scenes_without_gpu(libnsn):
+    """nsn_collider_create checks its arguments on the host before any CUDA
+    call: margin <= 0, environments out of order, excluded ids out of range."""
+    base = dict(kind=[0, 0], half=[[.1, .1, .1]] * 2, env=[0, 1], n_envs=2, mu_env=[.5, .5],
+                planes=[[0, 0, 1, 0]], exclude=None, margin=0.01, h=1 / 60)
+    for bad in (dict(margin=0.0), dict(env=[1, 0]), dict(exclude=[[0, 5]]), dict(n_envs=1), dict(kind=[0, 2])):
+        with pytest.raises(nsn.ColliderError) as e:
+            nsn.nsn_collider_create(**{**base, **bad})
+        assert e.value.status == nsn.NSN_ERR_INVALID_ARG
+    assert libnsn.nsn_collider_destroy(None) == nsn.NSN_ERR_INVALID_ARG
