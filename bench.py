@@ -231,7 +231,7 @@ OPS_PLANE_TEST = 14
 OPS_VERTEX = 6
 
 
-def contact_generation(nsn, torch, s, stream, clk, iters=20):
+def contact_generation(nsn, torch, s, stream, clk, rank=0, iters=20):
     """Contact generation (Sec. 3.3, Sec. 10) on the workload's bodies with
     the ground plane: the collider's five kernels timed with CUDA events on
     device buffers, and end to end through nsn_collider_run
@@ -289,6 +289,9 @@ def contact_generation(nsn, torch, s, stream, clk, iters=20):
     hit = np.bincount(hit_body, minlength=len(kind))
     per_vertex = OPS_BOX_TEST * box_tests + OPS_PLANE_TEST * len(planes) + OPS_VERTEX
     ops = OPS_ROTATION * float((kind == 0).sum()) + per_vertex @ nvert + per_vertex @ hit
+    orc = oracle_collide_rate(s, planes, col.exclude) if rank == 0 else None
+    if orc is not None:
+        orc["ms_scaled_to_scene"] = (tests_box + tests_plane) / orc["tests_per_s"] * 1e3
     nsm = torch.cuda.get_device_properties(0).multi_processor_count
     summ = clk.summary() if clk is not None else None
     mhz = (summ or {}).get("sm_max_mhz") or 2070.0
@@ -303,7 +306,36 @@ def contact_generation(nsn, torch, s, stream, clk, iters=20):
             "ms": ms, "ms_e2e_host_arrays": ms_e2e, "contacts": n, "vertices": info["vertices"],
             "tests": tests_box + tests_plane, "ops_per_box_test": OPS_BOX_TEST,
             "ops_per_plane_test": OPS_PLANE_TEST, "fp32_ops": ops, "tests_per_s": (tests_box + tests_plane) / (ms * 1e-3),
-            "hand_built_scene_contacts": int(len(s["c_body"]))}
+            "hand_built_scene_contacts": int(len(s["c_body"])), "oracle": orc}
+
+
+def oracle_collide_rate(s, planes, exclude, margin=0.01, h=1.0 / 60.0, n_envs_sample=512):
+    """The oracle's contact generation (oracle/collide.c, one host core) on the
+    first ``n_envs_sample`` environments of the scene: tests per second and
+    the time scaled to the whole scene by its share of the tests."""
+    import oracle
+    env = s["env"]
+    nb = int(np.searchsorted(env, n_envs_sample))     # environments are contiguous body ranges
+    ex = np.asarray(exclude).reshape(-1, 2)
+    ex = ex[(ex[:, 0] < nb) & (ex[:, 1] < nb)]
+    kind, half = s["kind"][:nb], s["half"][:nb]
+    box = (kind == 0) & np.all(half > 0, axis=1)
+    nvert = np.where(kind == 1, 1, np.where(box, 8, 0))
+    nbox_env = np.bincount(env[:nb], weights=box, minlength=n_envs_sample)
+    excl = np.zeros(nb)
+    for a, b in ex:
+        excl[a] += box[b]
+        excl[b] += box[a]
+    tests = float((nvert * (nbox_env[env[:nb]] - box - excl)).sum() + nvert.sum() * len(planes))
+    args = (kind, s["pos"][:nb], s["quat"][:nb], s["vel"][:nb], s["omega"][:nb], half, env[:nb], planes, ex,
+            np.full(n_envs_sample, 0.5), margin, h)
+    t0 = time.perf_counter()
+    r = oracle.collide(*args)
+    sec = time.perf_counter() - t0
+    return {"kind": "oracle", "cores": 1, "tests_per_s": tests / sec, "ms_sample": sec * 1e3,
+            "contacts_sample": int(len(r["c_body"])),
+            "sample": f"the first {n_envs_sample} environments ({nb} bodies, {tests:.0f} tests), FP32 decisions "
+                      f"and FP64 geometry in plain C; the call counts the contacts, then writes them"}
 
 
 def kernel_source_hash():
@@ -580,7 +612,7 @@ def run_ours(args, rank, world, local_rank):
                 ga.close()
                 r.pop("sec")
                 arms[name] = r
-    contacts_rf = contact_generation(nsn, torch, s, stream, clk)
+    contacts_rf = contact_generation(nsn, torch, s, stream, clk, rank)
     B = algorithmic_bytes(sz)
     peak, peak_kind = measured_peaks()
     achieved = B / ((ms_body + ms_row) * 1e-3) / 1e9
