@@ -165,3 +165,42 @@ def test_generated_contacts_drive_the_solver(orc):
     # the two contact sets agree to FP32 rounding (a few 1e-8 m): the states
     # to far below the step's velocity change g h = 0.16 m/s
     assert dv < 1e-6
+
+
+def test_trajectory_with_contacts_generated_every_step(orc):
+    """Sec. 10's loop: collision detection once per step from the start-of-step
+    state and the unconstrained velocity (here v + h g and omega), then the
+    step.  The GPU runs its collider on its own FP64 state and refills its
+    solver's contacts; the oracle does the same with its own collider and
+    solver.  Over 10 steps of the cube stack (4 Newton x 20 CR) the contact
+    sets stay identical and the states agree to FP64 rounding (each step
+    starting from the FP32-rounded state, as the GPU context's rebuild does)."""
+    s = scenes.cube_stack(seed=2)
+    prm = dict(newton_iters=4, cr_iters=20)
+    grav = np.array([0.0, 0.0, -9.81])
+    col = nsn.Collider(s, mu_env=np.full(1, 0.5, np.float32))
+    g = None
+    st_g = st_o = {k: s[k].astype(np.float64) for k in ("pos", "quat", "vel", "omega")}
+    worst = 0.0
+    for step in range(10):
+        f32 = {k: v.astype(np.float32) for k, v in st_g.items()}
+        cg = col.run(f32["pos"], f32["quat"], (st_g["vel"] + H * grav).astype(np.float32), f32["omega"])
+        o32 = {k: v.astype(np.float32) for k, v in st_o.items()}
+        co = orc.collide(s["kind"], o32["pos"], o32["quat"], (st_o["vel"] + H * grav).astype(np.float32),
+                         o32["omega"], s["half"], s["env"], Z, None, [0.5], 0.01, H)
+        np.testing.assert_array_equal(cg["c_body"], co["c_body"])
+        sg = scenes.finalize({**s, **cg})
+        if g is None:
+            g = nsn.Solver(sg, precision=nsn.NSN_FP64, **prm)
+        else:
+            g.set_contacts(sg)
+        o = orc.Oracle(scenes.finalize({**s, **co}), **prm)
+        # refilling the contacts rebuilds the GPU context from its state in
+        # FP32 (the ABI's state arrays): the oracle starts from the same values
+        o.set_state(**{k: v.astype(np.float32).astype(np.float64) for k, v in st_o.items()})
+        g.step(); o.step()
+        st_g, st_o = g.get_state_f64(), o.get_state()
+        dv = np.abs(st_g["vel"] - st_o["vel"]).max()
+        worst = max(worst, dv)
+        print(f"step {step}: {len(cg['c_body'])} contacts, velocity difference {dv:.2e}")
+    assert worst < 1e-9
