@@ -414,7 +414,8 @@ nsn_status nsn_apply_operator_noalloc(nsn_ctx *ctx, const float *x, float *y, vo
  * stream, nothing copied and nothing synchronised: the count goes to the
  * device int32 *found_dev (may be NULL), contacts past `capacity` are not
  * written.  The collider's scratch is shared by its calls: calls on one
- * collider are serialised by its stream.
+ * collider are serialised by its stream, and a collider is used from one
+ * host thread at a time.
  *
  * nsn_collider_info: info4 = {bodies, vertices, planes, thread blocks per
  * launch}.  Errors of a collider call: nsn_collider_last_error. */

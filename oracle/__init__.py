@@ -2,7 +2,7 @@
 
 TEST INFRASTRUCTURE ONLY.  The oracle is the plain, slow, double-precision C
 implementation in ``oracle.c`` of Macklin et al. 2019 (Algorithm 1, Sec. 6-9,
-App. A-B).  Only the test suite, ``__graft_entry__.smoke()`` and the CPU
+App. A-B), with contact generation (Sec. 3.3, Sec. 10) in ``collide.c``.  Only the test suite, ``__graft_entry__.smoke()`` and the CPU
 baseline leg of ``bench.py`` may import this package.  It shares no code with
 the CUDA library in ``paper_1907_04587_gb300``; both consume the same scene
 dictionaries produced by ``paper_1907_04587_gb300.scenes``.
