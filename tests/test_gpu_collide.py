@@ -4,8 +4,9 @@ since both sides take every candidate, inside/outside and nearest-face
 decision in FP32 with the same rounded operations -- and closest points and
 normals (FP64 on both sides, rounded to FP32 on the GPU) within half an FP32
 ulp.  Scenes: the cube stack, a random box and particle scene with random
-velocities, the chain on the Neo-Hookean block, the batched environments at
-64 and at the full 4096."""
+velocities, the chain on the Neo-Hookean block, the bin of 2000 boxes and 8
+particle balls against three planes, the batched environments at 64 and at
+the full 4096."""
 import ctypes
 import numpy as np
 import pytest
@@ -70,7 +71,7 @@ def run_both(orc, s, planes=Z, margin=0.01, mu_env=None, exclude=None):
     return g, o, col
 
 
-@pytest.mark.parametrize("name", ["cube_stack", "random", "chain_block", "batched64"])
+@pytest.mark.parametrize("name", ["cube_stack", "random", "chain_block", "batched64", "mixed_bin"])
 def test_contacts_match_oracle(orc, name):
     if name == "cube_stack":
         s, kw = scenes.cube_stack(seed=0), {}
@@ -78,8 +79,10 @@ def test_contacts_match_oracle(orc, name):
         s, kw = random_scene(7), dict(margin=0.02, planes=((0, 0, 1, 0), (0.6, 0.8, 0.0, -0.3)))
     elif name == "chain_block":
         s, kw = scenes.chain_block(seed=0, hexes=6), dict(margin=0.005)
-    else:
+    elif name == "batched64":
         s, kw = scenes.batched_envs(seed=2, n_envs=64), {}
+    else:     # one environment: 2000 boxes, 8 balls of particles, floor and two walls
+        s, kw = scenes.mixed_bin(seed=0), dict(planes=((0, 0, 1, 0), (1, 0, 0, 0), (0, 1, 0, 0)))
     g, o, col = run_both(orc, s, **kw)
     print(name, col.info(), "contacts", len(g["c_body"]))
     assert len(g["c_body"]) > 0
