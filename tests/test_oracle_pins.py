@@ -522,3 +522,27 @@ def test_pendulum_drift_and_period(orc):
     Ip = I[1] + m * (Lx / 2) ** 2
     T = 2 * np.pi * np.sqrt(Ip / (m * G * Lx / 2))
     assert abs(period - T) / T < 0.05
+
+
+@pytest.mark.parametrize("e", [0.0, 1e-5, 1e-4, 1e-3, 1e6])
+def test_compliant_joint_one_step_closed_form(orc, e):
+    """Compliant joint rows (Sec. 3.2: C = e / h^2, h = (c + e lambda) / h): a
+    body of mass m hanging at rest from a world anchor at its centre.  The
+    vertical row is implicit Euler on a spring of stiffness 1/e, so one step
+    gives m v = h lambda - m g h with h v + e lambda = 0, i.e.
+    v = -m g h / (m + h^2 / e): 0 for a hard joint, free fall as e grows."""
+    m = 3.0
+    b = scenes.SceneBuilder()
+    i = b.add_rigid((0.2, -0.1, 1.0), (1, 0, 0, 0), mass=m, inertia=(0.2, 0.3, 0.4))
+    b.add_revolute(i, -1, (0, 0, 0), (0.2, -0.1, 1.0), (0, 1, 0), (0, 1, 0), e)
+    s = b.build()
+    o = orc.Oracle(s, newton_iters=30, cr_iters=30, line_search=1)
+    o.step()
+    v = o.get_state()["vel"][0]
+    x0 = np.asarray(s["pos"][0], np.float64)
+    anchor = np.asarray(s["j_pb"][0], np.float64)
+    assert np.array_equal(x0, anchor)
+    ef = float(np.float32(e))
+    expect = 0.0 if ef == 0.0 else -m * G * H / (m + H * H / ef)
+    assert abs(v[2] - expect) < 1e-9 * G * H, (v, expect)
+    assert np.all(np.abs(v[:2]) < 1e-12) and np.all(np.abs(o.get_state()["omega"][0]) < 1e-12)
