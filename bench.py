@@ -272,15 +272,8 @@ def contact_generation(nsn, torch, s, stream, clk, rank=0, iters=20):
     ms_e2e = (time.perf_counter() - t0) * 1e3 / 3
     # tests per vertex: every plane, and the boxes of its environment other
     # than its own body and the bodies it shares a joint with
-    kind, half, env = s["kind"], s["half"], s["env"]
-    box = (kind == 0) & np.all(half > 0, axis=1)
-    nvert = np.where(kind == 1, 1, np.where(box, 8, 0))
-    nbox_env = np.bincount(env, weights=box, minlength=n_envs)
-    excl = np.zeros(len(kind))
-    for a, b in col.exclude:
-        excl[a] += box[b]
-        excl[b] += box[a]
-    box_tests = nbox_env[env] - box - excl
+    kind = s["kind"]
+    nvert, box_tests = collide_tests(kind, s["half"], s["env"], col.exclude, n_envs)
     tests_box = float((nvert * box_tests).sum())
     tests_plane = float(nvert.sum() * len(planes))
     # the emit pass repeats the tests of the vertices with contacts
@@ -309,6 +302,21 @@ def contact_generation(nsn, torch, s, stream, clk, rank=0, iters=20):
             "hand_built_scene_contacts": int(len(s["c_body"])), "oracle": orc}
 
 
+def collide_tests(kind, half, env, exclude, n_envs):
+    """Per body: its vertex count (8 per box, 1 per particle) and the boxes
+    each of its vertices is tested against (the boxes of its environment
+    other than itself and its joint partners).  Plane tests are one per
+    vertex and plane."""
+    box = (kind == 0) & np.all(half > 0, axis=1)
+    nvert = np.where(kind == 1, 1, np.where(box, 8, 0))
+    nbox_env = np.bincount(env, weights=box, minlength=n_envs)
+    excl = np.zeros(len(kind))
+    for a, b in np.asarray(exclude).reshape(-1, 2):
+        excl[a] += box[b]
+        excl[b] += box[a]
+    return nvert, nbox_env[env] - box - excl
+
+
 def oracle_collide_rate(s, planes, exclude, margin=0.01, h=1.0 / 60.0, n_envs_sample=512):
     """The oracle's contact generation (oracle/collide.c, one host core) on the
     first ``n_envs_sample`` environments of the scene: tests per second and
@@ -319,14 +327,8 @@ def oracle_collide_rate(s, planes, exclude, margin=0.01, h=1.0 / 60.0, n_envs_sa
     ex = np.asarray(exclude).reshape(-1, 2)
     ex = ex[(ex[:, 0] < nb) & (ex[:, 1] < nb)]
     kind, half = s["kind"][:nb], s["half"][:nb]
-    box = (kind == 0) & np.all(half > 0, axis=1)
-    nvert = np.where(kind == 1, 1, np.where(box, 8, 0))
-    nbox_env = np.bincount(env[:nb], weights=box, minlength=n_envs_sample)
-    excl = np.zeros(nb)
-    for a, b in ex:
-        excl[a] += box[b]
-        excl[b] += box[a]
-    tests = float((nvert * (nbox_env[env[:nb]] - box - excl)).sum() + nvert.sum() * len(planes))
+    nvert, box_tests = collide_tests(kind, half, env[:nb], ex, n_envs_sample)
+    tests = float((nvert * box_tests).sum() + nvert.sum() * len(planes))
     args = (kind, s["pos"][:nb], s["quat"][:nb], s["vel"][:nb], s["omega"][:nb], half, env[:nb], planes, ex,
             np.full(n_envs_sample, 0.5), margin, h)
     t0 = time.perf_counter()
@@ -612,7 +614,10 @@ def run_ours(args, rank, world, local_rank):
                 ga.close()
                 r.pop("sec")
                 arms[name] = r
-    contacts_rf = contact_generation(nsn, torch, s, stream, clk, rank)
+    try:      # a side measurement: its failure is reported, the step's line stands
+        contacts_rf = contact_generation(nsn, torch, s, stream, clk, rank)
+    except Exception as e:  # noqa: BLE001
+        contacts_rf = {"failed": repr(e)}
     B = algorithmic_bytes(sz)
     peak, peak_kind = measured_peaks()
     achieved = B / ((ms_body + ms_row) * 1e-3) / 1e9

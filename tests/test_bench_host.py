@@ -58,3 +58,31 @@ def test_reference_arm_prints_one_json_line():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["unit"] == bench.UNIT and d["value"] > 0
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_collider_test_count_matches_enumeration():
+    """The contact-generation roofline counts the tests in closed form
+    (planes, plus the boxes of the vertex's environment other than its own
+    body and its joint partners); check it against the enumeration the
+    oracle's loops perform, on batched environments with particles added."""
+    import numpy as np
+    from paper_1907_04587_gb300 import scenes
+    s = scenes.batched_envs(seed=9, n_envs=5)
+    kind = s["kind"].copy()
+    kind[::7] = 1                         # some particles among the bodies
+    half = s["half"].copy()
+    half[::11] = 0.0                      # and some rigid bodies without a shape
+    env = s["env"]
+    jb = s["j_body"][(s["j_body"][:, 0] >= 0) & (s["j_body"][:, 1] >= 0)]
+    nvert, box_tests = bench.collide_tests(kind, half, env, jb, 5)
+    pairs = {(int(a), int(b)) for a, b in jb} | {(int(b), int(a)) for a, b in jb}
+    is_box = [(k == 0 and np.all(h > 0)) for k, h in zip(kind, half)]
+    brute = 0
+    for a in range(len(kind)):
+        nv = 1 if kind[a] == 1 else (8 if is_box[a] else 0)
+        for b in range(len(kind)):
+            if b != a and env[b] == env[a] and is_box[b] and (a, b) not in pairs:
+                brute += nv
+    assert brute == int((nvert * box_tests).sum())
+    r = bench.oracle_collide_rate(s, ((0.0, 0.0, 1.0, 0.0),), jb, n_envs_sample=2)
+    assert r["tests_per_s"] > 0 and r["contacts_sample"] > 0
