@@ -400,7 +400,9 @@ nsn_status nsn_apply_operator_noalloc(nsn_ctx *ctx, const float *x, float *y, vo
  * exclude (n_exclude x 2 body ids); margin > 0; h >= 0 the step of the
  * prediction; stream: a cudaStream_t for all work of the collider, or NULL.
  * Host arrays are copied; the caller keeps them.  Bad sizes, ids, order or
- * values: NSN_ERR_INVALID_ARG; device memory: NSN_ERR_OUT_OF_MEMORY.
+ * values, or more than 2^31 - 1 vertex-shape pairs (the sum over environments
+ * of vertices x (planes + boxes)): NSN_ERR_INVALID_ARG; device memory:
+ * NSN_ERR_OUT_OF_MEMORY.
  *
  * nsn_collider_run: host arrays.  pos (n x 3), quat (n x 4, w x y z), vel and
  * omega (n x 3, the unconstrained velocity, world frame) are copied in; at

@@ -572,6 +572,15 @@ nsn_status nsn_collider_create(int32_t n_bodies, const int32_t *kind, const floa
     }
   }
   if (vbody.size() > (size_t)INT32_MAX / 2) return NSN_ERR_INVALID_ARG;
+  {   // contacts are counted in int32: every vertex against every shape of its
+      // environment must fit
+    std::vector<int64_t> nbox(n_envs, 0), nvert(n_envs, 0);
+    for (int b = 0; b < n_bodies; b++) nbox[env[b]] += shape[b];
+    for (int32_t b : vbody) nvert[env[b]]++;
+    int64_t bound = 0;
+    for (int e = 0; e < n_envs; e++) bound += nvert[e] * (n_planes + nbox[e]);
+    if (bound > (int64_t)INT32_MAX) return NSN_ERR_INVALID_ARG;
+  }
   nsn_collider *c = new nsn_collider();
   c->nb = n_bodies;
   c->nv = (int)vbody.size();

@@ -66,3 +66,9 @@ def test_collider_rejects_invalid_scenes_without_gpu(libnsn):
             nsn.nsn_collider_create(**{**base, **bad})
         assert e.value.status == nsn.NSN_ERR_INVALID_ARG
     assert libnsn.nsn_collider_destroy(None) == nsn.NSN_ERR_INVALID_ARG
+    # 17,000 boxes in one environment: 8 x 17,000 x 17,001 pairs overflow the
+    # int32 contact count, rejected before any device work
+    n = 17000
+    with pytest.raises(nsn.ColliderError) as e:
+        nsn.nsn_collider_create([0] * n, [[.1, .1, .1]] * n, [0] * n, 1, [.5], [[0, 0, 1, 0]], None, 0.01, 1 / 60)
+    assert e.value.status == nsn.NSN_ERR_INVALID_ARG
