@@ -339,30 +339,34 @@ nsn_status nsn_mlp_train_step(nsn_ctx *ctx, const float *X, const float *T, cons
 nsn_status nsn_contact_features(nsn_ctx *ctx, float *X, float *Ytarget);
 
 /* ---- allocation-free operator apply -----------------------------------------
- * The paper has no counterpart; this entry point serves callers that cannot
- * allocate device memory where they need an operator product: code running
- * while a stream is being captured into a CUDA graph, latency-critical loops
- * that must not block on the allocator, and hosts that give the library a
- * fixed memory budget.
+ * The paper has no counterpart.  This entry point serves callers that cannot
+ * allocate device memory where they need an operator product: a host
+ * application that owns the device's memory and gives the library a fixed
+ * budget with nothing to spare, and a real-time control loop that must not
+ * block in the device allocator (cudaMalloc can synchronise the device).
  *
  * Computes y = (J H~^-1 J^T + C + eps I) x for the system kept by the last
  * nsn_step (its final evaluation) or nsn_linearize, with the same kernels as
  * the CR loop.  x and y are caller-owned device arrays of nsn_counts() rows
- * (float32); stream is a cudaStream_t or NULL for the context stream.  The
- * call allocates nothing: the per-entry scratch lives in a fixed static device
- * array of NSN_NOALLOC_MAX_ENTRIES floats (16 MiB), and x and y are permuted
- * into the context's internal (island) row order through two static arrays of
- * NSN_NOALLOC_MAX_ENTRIES / 2 floats (8 MiB each); every GPU loading the
- * library holds them until the process exits.  Scenes needing more row slots
- * than NSN_NOALLOC_MAX_ENTRIES (2 per contact or joint row, 4 per tet row) are
- * rejected with NSN_ERR_INVALID_ARG.  All calls share the arrays and they keep
- * the last call's
- * contents; each call first clears the slots it uses (the world side of a
- * contact is read as zero), with a memset on the stream, which allocates
- * nothing.  Calls that overlap on the GPU (different streams, or different
- * contexts on one device) race on the array.  The
- * first call on a device resolves the array's device address (set-up); make
- * that first call before any stream capture.  FP32 contexts only. */
+ * (float32); stream is a cudaStream_t or NULL for the context stream.  A
+ * stream other than the context stream must be ordered after the context
+ * stream's last nsn_step / nsn_linearize (e.g. by waiting on an event recorded
+ * there): the apply reads the Jacobian entries, compliances and inverse masses
+ * that those calls wrote.  The call allocates nothing: the per-entry scratch
+ * lives in a fixed static device array of NSN_NOALLOC_MAX_ENTRIES floats
+ * (16 MiB), and x and y are permuted into the context's internal (island) row
+ * order through two static arrays of NSN_NOALLOC_MAX_ENTRIES / 2 floats
+ * (8 MiB each); every GPU loading the library holds them until the process
+ * exits.  Scenes needing more row slots than NSN_NOALLOC_MAX_ENTRIES (2 per
+ * contact or joint row, 4 per tet row) are rejected with NSN_ERR_INVALID_ARG.
+ * All calls share the arrays and they keep the last call's contents; each
+ * call first clears the slots it uses (the world side of a contact is read as
+ * zero), with a memset on the stream, which allocates nothing.  Calls that
+ * overlap on the GPU (different streams, or different contexts on one device)
+ * race on the arrays.  The first call on a device (and the first after the
+ * device's CUDA context changed) resolves the arrays' device addresses, under
+ * a lock shared by all host threads; make that first call before any stream
+ * capture.  FP32 contexts only. */
 #define NSN_NOALLOC_MAX_ENTRIES (4 * 1024 * 1024)
 nsn_status nsn_apply_operator_noalloc(nsn_ctx *ctx, const float *x, float *y, void *stream);
 

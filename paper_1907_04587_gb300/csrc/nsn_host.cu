@@ -2,6 +2,7 @@
 // (declared in include/nsn.h).  Builds the device layout from the scene,
 // owns all device memory, enqueues one time step (Algorithm 1) on the
 // context stream and captures it once as a CUDA graph.
+#include <cuda.h>   // CUcontext, CUresult (types only)
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -10,6 +11,7 @@
 #include <cstdio>
 #include <cstring>
 #include <functional>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -21,7 +23,16 @@ using namespace nsn;
 
 namespace {
 
-constexpr int kMaxBlocks = 152 * 8;  // 152 SMs x 8 resident 256-thread blocks
+// Resident 256-thread blocks of the current device (SMs x threads per SM /
+// 256): the cap of every grid and the capacity of the per-block partial sums.
+int device_max_blocks() {
+  int dev = 0, nsm = 0, thr = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1) nsm = 1;
+  if (cudaDeviceGetAttribute(&thr, cudaDevAttrMaxThreadsPerMultiProcessor, dev) != cudaSuccess || thr < BLOCK)
+    thr = BLOCK;
+  return nsm * (thr / BLOCK);
+}
 
 struct HostScene {
   std::vector<int32_t> kind;
@@ -140,7 +151,7 @@ nsn_status fail(nsn_ctx *c, nsn_status s, const char *fmt, ...) {
   } while (0)
 
 inline int cdiv(long long a, long long b) { return int((a + b - 1) / b); }
-inline int clampb(long long n) { return int(std::max(1LL, std::min<long long>(n, kMaxBlocks))); }
+inline int clampb(long long n, int max_blk) { return int(std::max(1LL, std::min<long long>(n, max_blk))); }
 
 bool finite_all(const float *p, size_t n) {
   for (size_t i = 0; i < n; i++)
@@ -404,8 +415,9 @@ void carve(Arena &A, Dev<T> &D, const Layout &L, int nb) {
   D.je = tk(L.nj);
   D.tv = A.take<int>(4 * L.nt);
   D.tDmi = tk(9 * L.nt); D.tVe = tk(L.nt); D.tC1 = tk(L.nt); D.tD1 = tk(L.nt); D.talpha = tk(L.nt);
-  D.part_body = A.take<typename RedT<T>::type>(2 * kMaxBlocks);
-  D.part_row = A.take<typename RedT<T>::type>(2 * kMaxBlocks * NPART);
+  D.max_blk = device_max_blocks();
+  D.part_body = A.take<typename RedT<T>::type>(2 * size_t(D.max_blk));
+  D.part_row = A.take<typename RedT<T>::type>(2 * size_t(D.max_blk) * NPART);
   D.sc = A.take<Scalars>(1);
   D.fl = A.take<Flags>(1);
   D.risl = A.take<int>(L.R);
@@ -451,6 +463,7 @@ void carve(Arena &A, Dev<T> &D, const Layout &L, int nb) {
 
 template <typename T>
 void fill_sizes(Dev<T> &D, const Layout &L, const nsn_config &cfg) {
+  D.max_blk = device_max_blocks();
   D.nr = L.nr; D.np = L.np; D.nc = L.nc; D.nj = L.nj; D.nt = L.nt; D.R = L.R; D.Rpair = L.Rpair;
   D.ER = L.ER; D.EV = L.EV;
   D.h = cfg.h; D.eps = cfg.eps; D.damping = cfg.damping; D.tol_rel = cfg.tol_rel;
@@ -480,12 +493,12 @@ void fill_sizes(Dev<T> &D, const Layout &L, const nsn_config &cfg) {
                             : wave(reinterpret_cast<const void *>(&k_body_pass<T, 8, BM_APPLY>)));
   const long long cap_row = cfg.island_stop ? wave(reinterpret_cast<const void *>(&k_row_pass_isl<T, RM_APPLY>))
                                             : wave(reinterpret_cast<const void *>(&k_row_pass<T, RM_APPLY>));
-  auto capped = [](long long n, long long cap) { return int(std::max(1LL, std::min({n, cap, (long long)kMaxBlocks}))); };
+  auto capped = [&](long long n, long long cap) { return int(std::max(1LL, std::min({n, cap, (long long)D.max_blk}))); };
   D.nblk_body_r = L.nr ? capped(cdiv((long long)L.nr * D.G, BLOCK), cap_body) : 0;
   D.nblk_body_p = L.np ? capped(cdiv((long long)L.np * D.G, BLOCK), cap_body) : 0;
   D.nblk_row_pair = L.Rpair ? capped(cdiv(L.Rpair, BLOCK), cap_row) : 0;
   D.nblk_row_tet = L.nt ? capped(cdiv(L.nt, BLOCK), cap_row) : 0;
-  D.nblk_upd = clampb(cdiv(std::max(L.R, 1), BLOCK));
+  D.nblk_upd = clampb(cdiv(std::max(L.R, 1), BLOCK), D.max_blk);
   // island-resident CR: a persistent grid of as many CTAs as fit (shared
   // memory sized for the largest resident island), at most one per island
   D.res_on = 0;
@@ -895,7 +908,7 @@ struct Launcher {
   void line_search() {
     body(BM_UPDATE, D.x, IT_DEV, IT_DEV, 0);   // du and the iterate kept, nothing committed
     const int nl = D.nr + D.np + D.R;
-    const int gl = clampb(cdiv(std::max(nl, 1), 256));
+    const int gl = clampb(cdiv(std::max(nl, 1), 256), D.max_blk);
     k_ls_begin<T><<<D.nblk_upd, BLOCK, 0, st>>>(D);
     count++;
     T t = T(1);
@@ -1171,6 +1184,8 @@ nsn_status run_steps(nsn_ctx *c, int nsteps) {
     nsn_status s = mlp_ensure(c, D.nc);
     if (s != NSN_OK) return s;
   }
+  if (!c->ev0) CUDA_TRY(c, cudaEventCreate(&c->ev0));
+  if (!c->ev1) CUDA_TRY(c, cudaEventCreate(&c->ev1));
   CUDA_TRY(c, cudaEventRecord(c->ev0, st));
   if (c->cfg.use_graph) {
     if (!c->graph) {
@@ -1420,6 +1435,8 @@ nsn_status do_time_resident(nsn_ctx *c, int iters, float *ms, double *work4) {
   const int M = c->cfg.cr_iters;
   Flags *f = D.fl;
   const size_t wofs = offsetof(Flags, res_rowit);
+  Dev<T> Dw = D;
+  Dw.res_work = 1;   // these launches count their work; the step's do not
   float tot = 0.f;
   Flags fl{};
   for (int i = 0; i <= iters; i++) {   // launch 0 is a warm-up
@@ -1427,7 +1444,7 @@ nsn_status do_time_resident(nsn_ctx *c, int iters, float *ms, double *work4) {
     CUDA_TRY(c, cudaMemsetAsync(&f->cr_res_max, 0, sizeof(int), st));
     CUDA_TRY(c, cudaMemsetAsync(reinterpret_cast<char *>(f) + wofs, 0, 3 * sizeof(unsigned long long), st));
     CUDA_TRY(c, cudaEventRecord(e[0], st));
-    k_cr_resident<T><<<D.nblk_res, RES_THREADS, D.res_smem, st>>>(D, M);
+    k_cr_resident<T><<<D.nblk_res, RES_THREADS, D.res_smem, st>>>(Dw, M);
     CUDA_TRY(c, cudaEventRecord(e[1], st));
     CUDA_TRY(c, cudaMemcpyAsync(&fl, f, sizeof(Flags), cudaMemcpyDeviceToHost, st));
     CUDA_TRY(c, cudaStreamSynchronize(st));
@@ -1674,11 +1691,7 @@ nsn_status nsn_create(const nsn_config *cfg, void *stream, nsn_ctx **out) {
     if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) { delete c; return NSN_ERR_CUDA; }
     c->own_stream = true;
   }
-  if (cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess) {
-    delete c;
-    return NSN_ERR_CUDA;
-  }
-  *out = c;
+  *out = c;   // the timing events are created by the first step
   return NSN_OK;
 }
 
@@ -1744,6 +1757,19 @@ nsn_status nsn_add_constraints(nsn_ctx *c, int32_t type, int32_t n, const void *
   HostScene &S = c->scene;
   const int nb = int(S.kind.size());
   auto body_ok = [&](int id) { return id >= -1 && id < nb; };
+  {
+    // the device layout indexes rows and Jacobian entries with int32: the scene
+    // after this call must keep 3 nc + 5 nj + 3 nt rows and 2 (3 nc + 5 nj) +
+    // 12 nt entries below 2^31 (checked in int64 before anything is stored)
+    const int64_t nc = int64_t(S.contacts.size()) + (type == NSN_CONTACT ? n : 0);
+    const int64_t nj = int64_t(S.joints.size()) + (type == NSN_REVOLUTE ? n : 0);
+    const int64_t nt = int64_t(S.tets.size()) + (type == NSN_TET_NH ? n : 0);
+    const int64_t rows = 3 * nc + 5 * nj + 3 * nt, entries = 2 * (3 * nc + 5 * nj) + 12 * nt;
+    if (rows > INT32_MAX || entries > INT32_MAX)
+      return fail(c, NSN_ERR_INVALID_ARG,
+                  "add_constraints: the scene would hold %lld rows and %lld Jacobian entries (limit 2^31 - 1)",
+                  (long long)rows, (long long)entries);
+  }
   if (type == NSN_CONTACT) {
     const nsn_contact *r = static_cast<const nsn_contact *>(records);
     for (int i = 0; i < n; i++) {
@@ -2163,44 +2189,77 @@ nsn_status nsn_last_launch_count(nsn_ctx *c, int32_t *kernels_per_step) {
 // Allocation-free operator apply.
 //
 // Some callers cannot allocate device memory at the point where they need an
-// operator product: code running while a stream is being captured into a CUDA
-// graph (cudaMalloc is not a stream operation and breaks the capture), code
-// inside a latency-critical control loop that must not block on the device
-// allocator, and hosts that hand the library a fixed memory budget.  For
-// them nsn_apply_operator_noalloc computes y = (J H~^-1 J^T + C + eps I) x with
-// the same two kernels as the CR loop, but keeps the per-entry scratch, the
-// per-block partials and the flags in the file-scope device arrays below
-// (part of the library image, resident on every device that loads it until the
-// process exits) instead of in memory allocated by the context.
+// operator product: a host application that owns the device's memory and hands
+// the library a fixed budget with nothing to spare, and a real-time control
+// loop that must not block in the device allocator (cudaMalloc can synchronise
+// the device and take milliseconds).  For them nsn_apply_operator_noalloc
+// computes y = (J H~^-1 J^T + C + eps I) x with the same two kernels as the CR
+// loop, but keeps the per-entry scratch, the per-block partials and the flags
+// in the file-scope device arrays below (part of the library image, resident
+// on every device that loads it until the process exits) instead of in memory
+// allocated by the context.
 
 namespace {
 
 constexpr int kNoallocMaxEntries = NSN_NOALLOC_MAX_ENTRIES;
 constexpr int kNoallocMaxRows = NSN_NOALLOC_MAX_ENTRIES / 2;  // a row has at least 2 slots
+constexpr int kNoallocMaxBlocks = 8192;                        // grid cap the partials can hold
 static __device__ __align__(256) float g_noalloc_t[kNoallocMaxEntries];
 // x and y in the context's internal (island) row order
 static __device__ __align__(256) float g_noalloc_x[kNoallocMaxRows];
 static __device__ __align__(256) float g_noalloc_y[kNoallocMaxRows];
-static __device__ __align__(256) DS g_noalloc_part[2 * kMaxBlocks * NPART];
+static __device__ __align__(256) DS g_noalloc_part[2 * kNoallocMaxBlocks * NPART];
 static __device__ __align__(256) Flags g_noalloc_flags;  // never written by the apply kernels
 
 struct NoallocPtrs {
   float *t = nullptr, *x = nullptr, *y = nullptr;
   DS *part = nullptr;
   Flags *flags = nullptr;
+  CUcontext ctx = nullptr;   // the CUDA context the addresses belong to
   bool ready = false;
 };
 constexpr int kMaxDevices = 64;
+// Resolved addresses per device.  Contexts on different host threads may make
+// their first call at the same time: the table is read and written only under
+// g_noalloc_mu, and each call takes a copy of its entry.
+std::mutex g_noalloc_mu;
 NoallocPtrs g_noalloc_dev[kMaxDevices];
 
-// Host code cannot use the arrays' names as device addresses; resolve them
-// once per device, with that device current.
-nsn_status noalloc_setup(nsn_ctx *c, NoallocPtrs **out) {
+// cuCtxGetCurrent, obtained through the runtime (no link against the driver library)
+using CtxGetCurrentFn = CUresult (*)(CUcontext *);
+CtxGetCurrentFn ctx_get_current() {
+  static const CtxGetCurrentFn fn = [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      p = nullptr;
+    return reinterpret_cast<CtxGetCurrentFn>(p);
+  }();
+  return fn;
+}
+
+// Host code cannot use the arrays' names as device addresses: they are
+// host-side stand-ins.  Resolve them once per device, with that device
+// current, and again if the device's context changed since (after
+// cudaDeviceReset the module is loaded anew and the arrays may move).
+nsn_status noalloc_setup(nsn_ctx *c, NoallocPtrs *out) {
   int dev = 0;
   CUDA_TRY(c, cudaGetDevice(&dev));
   if (dev < 0 || dev >= kMaxDevices) return fail(c, NSN_ERR_INVALID_ARG, "device index %d out of range", dev);
+  CUcontext cur = nullptr;
+  const CtxGetCurrentFn get = ctx_get_current();
+  if (!get || get(&cur) != CUDA_SUCCESS)
+    return fail(c, NSN_ERR_CUDA, "nsn_apply_operator_noalloc: cuCtxGetCurrent unavailable");
+  if (!cur) {   // first runtime call of this host thread: bind the device's primary context
+    CUDA_TRY(c, cudaSetDevice(dev));
+    if (get(&cur) != CUDA_SUCCESS || !cur)
+      return fail(c, NSN_ERR_CUDA, "nsn_apply_operator_noalloc: no current CUDA context");
+  }
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
   NoallocPtrs &p = g_noalloc_dev[dev];
-  if (!p.ready) {
+  if (!p.ready || p.ctx != cur) {
+    p.ready = false;
     void *t = nullptr, *part = nullptr, *fl = nullptr, *x = nullptr, *y = nullptr;
     const cudaError_t e[5] = {cudaGetSymbolAddress(&t, g_noalloc_t), cudaGetSymbolAddress(&part, g_noalloc_part),
                               cudaGetSymbolAddress(&fl, g_noalloc_flags), cudaGetSymbolAddress(&x, g_noalloc_x),
@@ -2212,9 +2271,10 @@ nsn_status noalloc_setup(nsn_ctx *c, NoallocPtrs **out) {
     p.y = static_cast<float *>(y);
     p.part = static_cast<DS *>(part);
     p.flags = static_cast<Flags *>(fl);
+    p.ctx = cur;
     p.ready = true;
   }
-  *out = &p;
+  *out = p;
   return NSN_OK;
 }
 
@@ -2239,9 +2299,13 @@ extern "C" nsn_status nsn_apply_operator_noalloc(nsn_ctx *c, const float *x, flo
                 "nsn_apply_operator_noalloc: %lld row slots (2 per contact or joint row, 4 per tet row) exceed the "
                 "static scratch of %d",
                 (long long)nslots, kNoallocMaxEntries);
-  NoallocPtrs *np = nullptr;
-  nsn_status s = noalloc_setup(c, &np);
+  if (c->d32.max_blk > kNoallocMaxBlocks)
+    return fail(c, NSN_ERR_INVALID_ARG, "nsn_apply_operator_noalloc: %d blocks per grid exceed the static partials of %d",
+                c->d32.max_blk, kNoallocMaxBlocks);
+  NoallocPtrs npv;
+  nsn_status s = noalloc_setup(c, &npv);
   if (s != NSN_OK) return s;
+  const NoallocPtrs *np = &npv;
   if (L.R == 0) return NSN_OK;
   cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : c->stream;
   Dev<float> D = c->d32;

@@ -175,6 +175,10 @@ struct Dev {
   typename RedT<T>::type *part_body;   // one per body-pass block
   typename RedT<T>::type *part_row;    // NPART per row-pass block
   int nblk_body_r, nblk_body_p, nblk_row_pair, nblk_row_tet, nblk_upd;
+  int max_blk;       // resident 256-thread blocks of the device (SMs x threads per SM / 256):
+                     // the grid cap and the capacity of part_body / part_row
+  int res_work;      // 1: k_cr_resident counts its row-, entry- and body-iterations
+                     // (only the timing entry point sets it)
   int G;             // lanes per body segment in the body pass (4, 8 or 16; tuned per scene)
   Scalars *sc;
   Flags *fl;
@@ -2294,10 +2298,12 @@ __global__ void __launch_bounds__(RES_THREADS) k_cr_resident(Dev<T> D, int M) {
         kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
       }
       if (lane == 0) {
-        atomicMax(&D.fl->cr_res_max, kmax);
-        atomicAdd(&D.fl->res_rowit, wr);
-        atomicAdd(&D.fl->res_entit, we);
-        atomicAdd(&D.fl->res_bodit, wb);
+        atomicMax(&D.fl->cr_res_max, kmax);   // the step's CR count (statistics)
+        if (D.res_work) {
+          atomicAdd(&D.fl->res_rowit, wr);
+          atomicAdd(&D.fl->res_entit, we);
+          atomicAdd(&D.fl->res_bodit, wb);
+        }
       }
     }
     __syncthreads();   // the shared image is rebuilt for the next group

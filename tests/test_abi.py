@@ -72,3 +72,28 @@ def test_collider_rejects_invalid_scenes_without_gpu(libnsn):
     with pytest.raises(nsn.ColliderError) as e:
         nsn.nsn_collider_create([0] * n, [[.1, .1, .1]] * n, [0] * n, 1, [.5], [[0, 0, 1, 0]], None, 0.01, 1 / 60)
     assert e.value.status == nsn.NSN_ERR_INVALID_ARG
+
+
+def test_constraint_counts_beyond_int32_rejected_without_gpu(libnsn):
+    """nsn_add_constraints sizes the scene in int64 before storing anything:
+    716M contacts (3 rows each, 2.148e9 rows) or 179M tets (12 Jacobian
+    entries each, 2.148e9 entries) would overflow the int32 row and entry
+    indices of the device layout and are rejected with NSN_ERR_INVALID_ARG.
+    The context uses the per-thread default stream handle, so nothing here
+    touches a GPU; the records are not read once the count is rejected."""
+    cfg = nsn.nsn_default_config()
+    ctx = ctypes.c_void_p()
+    per_thread_stream = ctypes.c_void_p(2)   # cudaStreamPerThread
+    assert libnsn.nsn_create(ctypes.byref(cfg), per_thread_stream, ctypes.byref(ctx)) == nsn.NSN_OK
+    try:
+        rec = (ctypes.c_char * 256)()
+        first = ctypes.c_int32()
+        for typ, n in ((nsn.NSN_CONTACT, 716_000_000), (nsn.NSN_TET_NH, 179_000_000)):
+            st = libnsn.nsn_add_constraints(ctx, typ, n, rec, ctypes.byref(first))
+            assert st == nsn.NSN_ERR_INVALID_ARG
+            assert b"limit 2^31 - 1" in libnsn.nsn_last_error(ctx)
+        # a count that fits is still validated record by record (zeroed records: bad body ids)
+        st = libnsn.nsn_add_constraints(ctx, nsn.NSN_CONTACT, 1, rec, ctypes.byref(first))
+        assert st == nsn.NSN_ERR_INVALID_ARG
+    finally:
+        libnsn.nsn_destroy(ctx)

@@ -1,11 +1,13 @@
 """Allocation-free operator apply (nsn_apply_operator_noalloc).
 
 Callers that cannot allocate device memory where they need an operator
-product -- code running while a stream is captured into a CUDA graph,
-latency-critical loops that must not block on the allocator, hosts with a
-fixed memory budget -- use this entry point; its scratch is a static device
-array in the library.  This file is collected last so that a failure here
-comes after every other test has run.
+product -- a host application that owns the device's memory and leaves the
+library no budget for it, a real-time loop that must not block in the device
+allocator -- use this entry point; its scratch is a static device array in
+the library.  The tests call it through the C ABI and compare it with the
+allocating apply (nsn_apply_operator) and with the FP64 oracle's operator.
+This file is collected last so that a failure here comes after every other
+test has run; it also passes when run alone in a fresh process.
 """
 import numpy as np
 import pytest
@@ -72,3 +74,25 @@ def test_noalloc_rejects_too_many_entries(torch_cuda):
     yd = torch.zeros_like(xd)
     with pytest.raises(nsn.NSNError, match="exceed the static scratch"):
         nsn.nsn_apply_operator_noalloc(g.ctx, xd.data_ptr(), yd.data_ptr())
+
+
+def test_noalloc_apply_matches_oracle_operator(torch_cuda, orc):
+    """At the zero iterate of a step (u = 0, lambda = 0: identical inputs on
+    both sides) the allocation-free product equals the FP64 oracle's
+    y = (J H~^-1 J^T + C + eps I) x (Eq. schur_system, Sec. 8.4) within the
+    FP32 tolerance of the linear-system parity tests, on two calls in a row."""
+    torch = torch_cuda
+    s = scenes.chain_block(seed=5, hexes=3, links=4)   # contacts, joints, tets
+    p = dict(newton_iters=3, cr_iters=10)
+    o = orc.Oracle(s, **p)
+    o.linearize(n_before=0)
+    g = nsn.Solver(s, precision=nsn.NSN_FP32, **p)
+    g.linearize(0)
+    rng = np.random.default_rng(8)
+    for call in range(2):
+        x = rng.normal(size=g.R).astype(np.float32).astype(np.float64)
+        xd = torch.tensor(x, dtype=torch.float32, device="cuda")
+        yd = torch.full_like(xd, float("nan"))
+        nsn.nsn_apply_operator_noalloc(g.ctx, xd.data_ptr(), yd.data_ptr())
+        torch.cuda.synchronize()
+        assert _rel(yd.cpu().numpy(), o.apply_A(x)) < 1e-5, call
