@@ -111,6 +111,9 @@ def lib():
         L.orc_num_islands.restype = C.c_int32
         L.orc_get_islands.argtypes = [C.c_void_p, _ip, _ip]
         L.orc_get_island_stats.argtypes = [C.c_void_p, _dp, _dp, _ip]
+        L.orc_record_decisions.argtypes = [C.c_void_p, C.c_int32]
+        L.orc_record_decisions.restype = C.c_int
+        L.orc_get_decisions.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
         L.orc_fb.restype = C.c_double
         L.orc_fb.argtypes = [C.c_double, C.c_double]
         for f in ("orc_fb_contact", "orc_min_contact"):
@@ -126,8 +129,9 @@ def lib():
         L.orc_nh_grad_hess.argtypes = [_dp, C.c_double, C.c_double, C.c_double, _dp, _dp]
         L.orc_svd3.argtypes = [_dp, _dp, _dp, _dp]
         L.orc_basis.argtypes = [_dp, _dp, _dp]
-        L.orc_collide.restype = C.c_int32
-        L.orc_collide.argtypes = [C.POINTER(_CollideIn), C.POINTER(_Contacts)]
+        for f in ("orc_collide", "orc_collide_f64"):
+            getattr(L, f).restype = C.c_int32
+            getattr(L, f).argtypes = [C.POINTER(_CollideIn), C.POINTER(_Contacts)]
     return _lib
 
 
@@ -271,6 +275,21 @@ class Oracle:
         lib().orc_get_island_stats(self.ctx, _ptr(m0), _ptr(mf), _ptr(it))
         return dict(merit0=m0, merit_final=mf, stopped_at=it)
 
+    def record_decisions(self, iters):
+        """Keep the discrete decisions of the next steps' first `iters` Newton
+        iterations (see oracle.h, orc_record_decisions)."""
+        if lib().orc_record_decisions(self.ctx, int(iters)) != 0:
+            raise MemoryError("orc_record_decisions")
+        self._dlog_iters = int(iters)
+
+    def decisions(self):
+        """(rows: iters x R uint8, islands: iters x n_islands uint8) of the last step."""
+        n = lib().orc_num_islands(self.ctx)
+        rows = np.zeros((self._dlog_iters, self.R), np.uint8)
+        isl = np.zeros((self._dlog_iters, n), np.uint8)
+        lib().orc_get_decisions(self.ctx, rows.ctypes.data_as(C.c_void_p), isl.ctypes.data_as(C.c_void_p))
+        return rows, isl
+
     def merit_history(self):
         out = np.zeros(4096)
         n = lib().orc_get_merit_history(self.ctx, _ptr(out), 4096)
@@ -362,13 +381,16 @@ def basis(n):
     return t1, t2
 
 
-def collide(kind, pos, quat, vel, omega, half, env, planes, exclude, mu_env, margin, h):
+def collide(kind, pos, quat, vel, omega, half, env, planes, exclude, mu_env, margin, h, fp64_decisions=False):
     """Contact generation of Sec. 3.3 / Sec. 10 (collide.c): candidates of body
     vertices against static planes and the boxes of their environment within
     ``margin``, at the start of the step or at the position predicted with the
     unconstrained velocity (vel, omega), over a step h.  Inputs are rounded to
     FP32 (what the GPU path receives); returns the contact arrays of a scene
-    dictionary (c_body, c_pa, c_pb, c_n, c_d, c_mu), geometry in FP64."""
+    dictionary (c_body, c_pa, c_pb, c_n, c_d, c_mu), geometry in FP64.
+    fp64_decisions=False: candidate and face decisions in FP32 in a fixed
+    order of rounded operations (orc_collide); True: the plain FP64 definition
+    throughout (orc_collide_f64)."""
     f32 = lambda a, c: np.ascontiguousarray(np.asarray(a, np.float32).reshape(-1, c))
     i32 = lambda a: np.ascontiguousarray(np.asarray(a, np.int32).ravel())
     kind, env = i32(kind), i32(env)
@@ -390,7 +412,7 @@ def collide(kind, pos, quat, vel, omega, half, env, planes, exclude, mu_env, mar
         dp = lambda a: a.ctypes.data_as(_dp)
         co = _Contacts(cap, ip(out["c_body"]), dp(out["c_pa"]), dp(out["c_pb"]), dp(out["c_n"]), dp(out["c_d"]),
                        dp(out["c_mu"]))
-        n = lib().orc_collide(C.byref(ci), C.byref(co))
+        n = (lib().orc_collide_f64 if fp64_decisions else lib().orc_collide)(C.byref(ci), C.byref(co))
         if n < 0:
             raise ValueError("orc_collide: excluded pair out of range")
         if n <= cap:

@@ -18,14 +18,23 @@
  * (u the unconstrained velocity field of each body), its distance to B is
  * below the margin (a point inside a box is at distance 0).
  *
- * The candidate decision and the inside / outside / nearest-face decisions
- * are integers decided by floating point: they are taken in FP32, in the
- * fixed order of operations written below (no contraction: the file is
- * compiled in ISO C mode, where GCC does not fuse multiply-adds), the
- * precision of the GPU kernels.  Everything else -- closest points and normals
- * -- is FP64.  Output order: bodies A ascending (environments are contiguous
- * ranges of bodies), their vertices in corner order, then the planes in order,
- * then the boxes B of A's environment ascending.
+ * Two versions of the same definition:
+ *   orc_collide      the candidate decision and the inside / outside /
+ *                    nearest-face decisions are integers decided by floating
+ *                    point; they are taken in FP32, in the fixed order of
+ *                    operations written below (no contraction: the file is
+ *                    compiled in ISO C mode, where GCC does not fuse
+ *                    multiply-adds), the precision of the GPU kernels, so that
+ *                    the GPU's contact lists can be compared element by
+ *                    element.  Closest points and normals are FP64.
+ *   orc_collide_f64  everything in FP64 from the definition above (unit
+ *                    quaternions, exact distances): the plain reference.  The
+ *                    two differ only on vertex-shape pairs whose distance lies
+ *                    within FP32 rounding of the margin, or whose nearest faces
+ *                    are tied to rounding; the tests bound that band.
+ * Output order (both): bodies A ascending (environments are contiguous ranges
+ * of bodies), their vertices in corner order, then the planes in order, then
+ * the boxes B of A's environment ascending.
  */
 #include <math.h>
 #include <stdint.h>
@@ -291,6 +300,119 @@ int32_t orc_collide(const orc_collide_in *in, orc_contacts *out) {
         }
         nn = sqrt(nn);
         for (int i = 0; i < 3; i++) nw[i] /= nn;
+        n = emit(out, n, a, b, cl, cp, nw, c.mu_env[e]);
+      }
+    }
+  }
+  free(X.start);
+  free(X.list);
+  return n;
+}
+
+/* ---- the plain FP64 version ------------------------------------------------- */
+
+/* rotation of the quaternion q / |q| (FP64) */
+static void rot_unit64(const float *qf, double *R) {
+  double w = qf[0], x = qf[1], y = qf[2], z = qf[3];
+  double n = sqrt(w * w + x * x + y * y + z * z);
+  w /= n; x /= n; y /= n; z /= n;
+  R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w * z); R[2] = 2 * (x * z + w * y);
+  R[3] = 2 * (x * y + w * z); R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - w * x);
+  R[6] = 2 * (x * z - w * y); R[7] = 2 * (y * z + w * x); R[8] = 1 - 2 * (x * x + y * y);
+}
+
+/* squared distance of a point to the box [-e, e] (box frame), 0 inside */
+static double dist2_box64(const double *q, const float *e) {
+  double s = 0.0;
+  for (int i = 0; i < 3; i++) {
+    double d = fabs(q[i]) - e[i];
+    if (d > 0.0) s += d * d;
+  }
+  return s;
+}
+
+/* velocity of the point at lever arm r of a body: v + w x r */
+static void vel_at64(const float *v, const float *w, const double *r, double *o) {
+  o[0] = v[0] + (w[1] * r[2] - w[2] * r[1]);
+  o[1] = v[1] + (w[2] * r[0] - w[0] * r[2]);
+  o[2] = v[2] + (w[0] * r[1] - w[1] * r[0]);
+}
+
+int32_t orc_collide_f64(const orc_collide_in *in, orc_contacts *out) {
+  col_in c = {in->n_bodies, in->kind, in->pos, in->quat, in->vel, in->omega, in->half, in->env,
+              in->n_planes, in->planes, in->n_exclude, in->exclude, in->mu_env, in->margin, in->h};
+  for (int k = 0; k < 2 * c.nx; k++)
+    if (c.excl[k] < 0 || c.excl[k] >= c.nb) return -1;
+  const double margin = c.margin, h = c.h;
+  excl_lists X = make_excl(&c);
+  int n = 0;
+  for (int a = 0; a < c.nb; a++) {
+    int nv = n_vertices(&c, a);
+    if (nv == 0) continue;
+    int e = c.env[a];
+    int lo = a, hi = a;
+    while (lo > 0 && c.env[lo - 1] == e) lo--;
+    while (hi < c.nb && c.env[hi] == e) hi++;
+    double RA[9];
+    if (c.kind[a] == ORC_RIGID) rot_unit64(c.quat + 4 * a, RA);
+    for (int k = 0; k < nv; k++) {
+      float cl[3] = {0, 0, 0};
+      double r[3] = {0, 0, 0}, p[3], ua[3];
+      if (c.kind[a] == ORC_RIGID) {
+        corner(&c, a, k, cl);
+        for (int i = 0; i < 3; i++) r[i] = RA[3 * i] * cl[0] + RA[3 * i + 1] * cl[1] + RA[3 * i + 2] * cl[2];
+        vel_at64(c.vel + 3 * a, c.omega + 3 * a, r, ua);
+      } else {
+        for (int i = 0; i < 3; i++) ua[i] = c.vel[3 * a + i];
+      }
+      for (int i = 0; i < 3; i++) p[i] = c.pos[3 * a + i] + r[i];
+      /* planes: signed distance n.p - o at p and at p + h u_A */
+      for (int j = 0; j < c.np; j++) {
+        const float *pl = c.planes + 4 * j;
+        double s0 = pl[0] * p[0] + pl[1] * p[1] + pl[2] * p[2] - pl[3];
+        double s1 = s0 + h * (pl[0] * ua[0] + pl[1] * ua[1] + pl[2] * ua[2]);
+        if (!(s0 < margin || s1 < margin)) continue;
+        double pb[3], nw[3];
+        for (int i = 0; i < 3; i++) { nw[i] = pl[i]; pb[i] = p[i] - s0 * nw[i]; }
+        n = emit(out, n, a, -1, cl, pb, nw, c.mu_env[e]);
+      }
+      /* boxes of the same environment: distance at p and at p + h (u_A(p) - u_B(p)) */
+      for (int b = lo; b < hi; b++) {
+        if (b == a || !is_box(&c, b) || excluded(&X, a, b)) continue;
+        const float *xb = c.pos + 3 * b, *eb = c.half + 3 * b;
+        double RB[9], rb[3], ub[3], r1[3], q0[3], q1[3];
+        rot_unit64(c.quat + 4 * b, RB);
+        for (int i = 0; i < 3; i++) rb[i] = p[i] - xb[i];
+        vel_at64(c.vel + 3 * b, c.omega + 3 * b, rb, ub);
+        for (int i = 0; i < 3; i++) r1[i] = rb[i] + h * (ua[i] - ub[i]);
+        for (int i = 0; i < 3; i++) {   /* box frame: R_B^T r */
+          q0[i] = RB[i] * rb[0] + RB[3 + i] * rb[1] + RB[6 + i] * rb[2];
+          q1[i] = RB[i] * r1[0] + RB[3 + i] * r1[1] + RB[6 + i] * r1[2];
+        }
+        if (!(dist2_box64(q0, eb) < margin * margin || dist2_box64(q1, eb) < margin * margin)) continue;
+        int outside = 0, face = 0;
+        double best = 0.0;
+        for (int i = 0; i < 3; i++) {
+          if (fabs(q0[i]) > eb[i]) outside = 1;
+          double depth = eb[i] - fabs(q0[i]);
+          if (i == 0 || depth < best) { best = depth; face = i; }
+        }
+        double cp[3], nl[3] = {0, 0, 0}, nw[3], len = 0.0;
+        if (outside) {
+          for (int i = 0; i < 3; i++) {
+            cp[i] = q0[i] > eb[i] ? eb[i] : (q0[i] < -eb[i] ? -eb[i] : q0[i]);
+            nl[i] = q0[i] - cp[i];
+            len += nl[i] * nl[i];
+          }
+          len = sqrt(len);
+          for (int i = 0; i < 3; i++) nl[i] /= len;
+        } else {
+          double sg = q0[face] >= 0.0 ? 1.0 : -1.0;
+          for (int i = 0; i < 3; i++) cp[i] = q0[i];
+          cp[face] = sg * eb[face];
+          nl[face] = sg;
+        }
+        for (int i = 0; i < 3; i++) nw[i] = RB[3 * i] * nl[0] + RB[3 * i + 1] * nl[1] + RB[3 * i + 2] * nl[2];
         n = emit(out, n, a, b, cl, cp, nw, c.mu_env[e]);
       }
     }

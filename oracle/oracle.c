@@ -64,6 +64,11 @@ struct orc_ctx {
   double *hvec, *g, *b, *pdiag;
   double merit_hist[4096];
   int merit_n;
+  /* decision log (orc_record_decisions): per Newton iteration n < dlog_iters,
+   * one code per row (dlog[n R + i]) and per island (dlog_ls[n ni + i]);
+   * dlog_n is the iteration whose main evaluation is running (-1: none) */
+  uint8_t *dlog, *dlog_ls;
+  int dlog_iters, dlog_n, dlog_rec;
   /* islands */
   int ni;
   int *body_isl, *row_isl;
@@ -457,12 +462,33 @@ void orc_destroy(orc_ctx *c) {
                   c->t_C1, c->t_D1, c->t_alpha, c->dof, c->pos, c->quat, c->vel, c->omega, c->lambda,
                   c->pos0, c->quat0, c->Iw, c->Iwinv, c->ut, c->hdiag, c->rows, c->rows_prev, c->cdiag,
                   c->c3, c->hvec, c->b, c->pdiag, c->g, c->body_isl, c->row_isl, c->isl_m0,
-                  c->isl_mf, c->isl_acc, c->isl_stop};
+                  c->isl_mf, c->isl_acc, c->isl_stop, c->dlog, c->dlog_ls};
   for (size_t i = 0; i < sizeof ptrs / sizeof ptrs[0]; i++) free(ptrs[i]);
   free(c);
 }
 
 int32_t orc_num_rows(const orc_ctx *c) { return c->R; }
+
+int orc_record_decisions(orc_ctx *c, int32_t iters) {
+  free(c->dlog);
+  free(c->dlog_ls);
+  c->dlog = NULL;
+  c->dlog_ls = NULL;
+  c->dlog_iters = 0;
+  if (iters <= 0) return 0;
+  c->dlog = malloc((size_t)iters * c->R + 1);
+  c->dlog_ls = malloc((size_t)iters * c->ni + 1);
+  if (!c->dlog || !c->dlog_ls) return -1;
+  memset(c->dlog, 255, (size_t)iters * c->R + 1);
+  memset(c->dlog_ls, 255, (size_t)iters * c->ni + 1);
+  c->dlog_iters = iters;
+  return 0;
+}
+
+void orc_get_decisions(const orc_ctx *c, uint8_t *rows, uint8_t *isl) {
+  if (rows && c->dlog) memcpy(rows, c->dlog, (size_t)c->dlog_iters * c->R);
+  if (isl && c->dlog_ls) memcpy(isl, c->dlog_ls, (size_t)c->dlog_iters * c->ni);
+}
 int32_t orc_num_islands(const orc_ctx *c) { return c->ni; }
 void orc_get_islands(const orc_ctx *c, int32_t *body_island, int32_t *row_island) {
   if (body_island) for (int i = 0; i < c->nb; i++) body_island[i] = c->body_isl[i];
@@ -645,6 +671,7 @@ static void eval_rows(orc_ctx *c, const double *u, const double *lam) {
     double ln = lam[3 * ci], phi, al, S;
     if (c->p.ncp == ORC_NCP_MIN) orc_min_contact(Cn, ln, rN, &phi, &al, &S);
     else orc_fb_contact(Cn, ln, rN, &phi, &al, &S);
+    const uint8_t ncode = c->p.ncp == ORC_NCP_MIN ? (Cn <= rN * ln) : (Cn == 0.0 && ln == 0.0);
     scale_row(rn, al);
     c->cdiag[3 * ci] = S / (h * h);
     c->hvec[3 * ci] = phi / h;
@@ -679,6 +706,13 @@ static void eval_rows(orc_ctx *c, const double *u, const double *lam) {
        * inactive form, which does the same without the overflowing value. */
       if (!(W <= ORC_W_MAX)) active = 0;
     }
+    if (c->dlog && c->dlog_rec && c->dlog_n < c->dlog_iters) {
+      /* friction: 0 inactive (mu lambda_n <= 0), 1 inactive past the
+       * asymptote of W, 2 stick (W = 0), 3 sliding (W > 0) */
+      const uint8_t fcode = !(mu_ln > 0.0) ? 0 : (!active ? 1 : (W == 0.0 ? 2 : 3));
+      uint8_t *L = c->dlog + (size_t)c->dlog_n * c->R + 3 * ci;
+      L[0] = ncode; L[1] = fcode; L[2] = fcode;
+    }
     if (active) {
       for (int k = 0; k < 2; k++) {
         c->cdiag[3 * ci + 1 + k] = W / h;               /* C block W/h (Eq. group_system) */
@@ -699,6 +733,8 @@ static void eval_rows(orc_ctx *c, const double *u, const double *lam) {
    * (anchor coincidence) and 2 angular rows a_w . b_k = 0 with b_1, b_2 an
    * orthonormal pair perpendicular to the hinge axis of b. */
   int base = 3 * c->nc;
+  if (c->dlog && c->dlog_rec && c->dlog_n < c->dlog_iters)
+    memset(c->dlog + (size_t)c->dlog_n * c->R + base, 0, 5 * (size_t)c->nj);
   for (int j = 0; j < c->nj; j++) {
     int a = c->j_body[2 * j], b = c->j_body[2 * j + 1];
     double wa[3], ra[3], wb[3], rb[3];
@@ -766,7 +802,10 @@ static void eval_rows(orc_ctx *c, const double *u, const double *lam) {
     double w[3], Q[9], E[9];
     eig_sym3(N, w, Q);
     double fl = 1e-6 * c->t_C1[t] * Ve;
-    for (int k = 0; k < 3; k++) if (w[k] < fl) w[k] = fl;
+    uint8_t tcode = s[2] < 0.0 ? 4 : 0;   /* inverted, plus the number of clamped eigenvalues */
+    for (int k = 0; k < 3; k++) if (w[k] < fl) { w[k] = fl; tcode++; }
+    if (c->dlog && c->dlog_rec && c->dlog_n < c->dlog_iters)
+      memset(c->dlog + (size_t)c->dlog_n * c->R + base + 3 * t, tcode, 3);
     for (int r = 0; r < 3; r++)
       for (int q = 0; q < 3; q++) {
         double acc = 0.0;
@@ -873,17 +912,20 @@ static void island_merits(const orc_ctx *c, double *out) {
  * the lagged W of Eq. friction_w then grows like 1 / lambda_n while
  * |lambda_f| / (mu lambda_n) grows each iteration.  Every solution of the
  * NCPs lies in this set, so the projection changes iterates, not solutions. */
-static void cone_project(const orc_ctx *c, double *lam, const int *isl_stop) {
+static void cone_project(const orc_ctx *c, double *lam, const int *isl_stop, int rec_n) {
   for (int k = 0; k < c->nc; k++) {
     if (isl_stop && isl_stop[c->row_isl[3 * k]] >= 0) continue;   /* stopped island */
     double *l = lam + 3 * k;
-    if (l[0] < 0.0) l[0] = 0.0;
+    uint8_t bits = 0;
+    if (l[0] < 0.0) { l[0] = 0.0; bits |= 2; }
     double lim = c->c_mu[k] * l[0];
     double f = sqrt(l[1] * l[1] + l[2] * l[2]);
     if (f > lim) {
       double s = lim / f;
       l[1] *= s; l[2] *= s;
+      bits |= 4;
     }
+    if (c->dlog && rec_n >= 0 && rec_n < c->dlog_iters) c->dlog[(size_t)rec_n * c->R + 3 * k] |= bits;
   }
 }
 
@@ -1145,7 +1187,7 @@ static void line_search(orc_ctx *c, int isl, double mn, double *lam, orc_work *w
   double ts = 1.0;
   for (int trial = 0; trial < 5; trial++, ts *= 0.5) {
     for (int i = 0; i < R; i++) lt[i] = lam0[i] + ts * w->dl[i];
-    if (c->p.cone_project) cone_project(c, lt, isl ? c->isl_stop : NULL);
+    if (c->p.cone_project) cone_project(c, lt, isl ? c->isl_stop : NULL, -1);
     for (int k = 0; k < D; k++) ut[k] = u0[k] + ts * w->du[k];
     positions_from_u(c, ut);
     eval_rows(c, ut, lt);
@@ -1160,10 +1202,20 @@ static void line_search(orc_ctx *c, int isl, double mn, double *lam, orc_work *w
     }
   }
   const double td = c->p.damping;
+  if (c->dlog && c->dlog_n < c->dlog_iters) {
+    /* accepted trial per island: 0..4 for t = 1 .. 1/16, 5 the damped step,
+     * 255 a stopped island */
+    uint8_t *L = c->dlog_ls + (size_t)c->dlog_n * ni;
+    for (int i = 0; i < ni; i++) {
+      const double a = isl ? tacc[i] : tg;
+      if (isl && c->isl_stop[i] >= 0) L[i] = 255;
+      else L[i] = a > 0.0 ? (uint8_t)lround(-log2(a)) : 5;
+    }
+  }
   if (!isl) {
     const double t = tg > 0.0 ? tg : td;
     for (int i = 0; i < R; i++) lam[i] = lam0[i] + t * w->dl[i];
-    if (c->p.cone_project) cone_project(c, lam, NULL);
+    if (c->p.cone_project) cone_project(c, lam, NULL, c->dlog_n);
     for (int k = 0; k < D; k++) w->u[k] = u0[k] + t * w->du[k];
   } else {
     for (int i = 0; i < R; i++) {
@@ -1171,7 +1223,7 @@ static void line_search(orc_ctx *c, int isl, double mn, double *lam, orc_work *w
       const double t = tacc[is] > 0.0 ? tacc[is] : td;
       lam[i] = lam0[i] + t * w->dl[i];
     }
-    if (c->p.cone_project) cone_project(c, lam, c->isl_stop);
+    if (c->p.cone_project) cone_project(c, lam, c->isl_stop, c->dlog_n);
     for (int b = 0; b < c->nb; b++) {
       const int is = c->body_isl[b];
       const double t = tacc[is] > 0.0 ? tacc[is] : td;
@@ -1197,7 +1249,10 @@ static int newton(orc_ctx *c, const double *lambda0, int stop_at, orc_stats *st,
   const int isl = c->p.island_stop && c->p.tol_rel > 0.0;
   for (int i = 0; i < c->ni; i++) c->isl_stop[i] = -1;
   for (n = 0; n < c->p.newton_iters || n == stop_at; n++) {
+    c->dlog_n = n;
+    c->dlog_rec = 1;
     eval_rows(c, w->u, lam);
+    c->dlog_rec = 0;
     compute_g(c, w->u, lam, w->zb);
     double mn = merit(c);
     if (n == 0) mfirst = mn;
@@ -1250,7 +1305,7 @@ static int newton(orc_ctx *c, const double *lambda0, int stop_at, orc_stats *st,
       line_search(c, isl, mn, lam, w);
     else {
       for (int i = 0; i < c->R; i++) lam[i] += t * w->dl[i];
-      if (c->p.cone_project) cone_project(c, lam, isl ? c->isl_stop : NULL);
+      if (c->p.cone_project) cone_project(c, lam, isl ? c->isl_stop : NULL, n);
       for (int k = 0; k < c->D; k++) w->u[k] += t * w->du[k];
     }
     positions_from_u(c, w->u);
@@ -1277,6 +1332,10 @@ static int newton(orc_ctx *c, const double *lambda0, int stop_at, orc_stats *st,
 }
 
 int orc_step(orc_ctx *c, const double *lambda0, orc_stats *st) {
+  if (c->dlog) {
+    memset(c->dlog, 255, (size_t)c->dlog_iters * c->R);
+    memset(c->dlog_ls, 255, (size_t)c->dlog_iters * c->ni);
+  }
   orc_work w;
   work_alloc(c, &w);
   newton(c, lambda0, -1, st, &w, NULL);

@@ -128,6 +128,21 @@ void orc_get_islands(const orc_ctx *ctx, int32_t *body_island, int32_t *row_isla
  * returned iterate, and the Newton iteration at which it stopped (-1 if it
  * did not reach tol_rel).  Any pointer may be NULL. */
 void orc_get_island_stats(const orc_ctx *ctx, double *merit0, double *merit_final, int32_t *stopped_at);
+/* Decision log of the following steps, for precision-aware comparisons: the
+ * discrete choices the method makes at each Newton iteration n < iters, one
+ * byte per row (row order of the scene) and per island:
+ *   contact normal row: bit 0 the FB kink (C = lambda = 0; min-map: the
+ *     branch C <= r lambda), bit 1 / bit 2 the cone projection clamped
+ *     lambda_n / scaled lambda_f after the update;
+ *   friction rows: 0 inactive (mu lambda_n <= 0), 1 inactive past the
+ *     asymptote of W, 2 stick (W = 0), 3 sliding;
+ *   joint rows: 0;  tet rows: clamped eigenvalues of the Hessian (+4 inverted);
+ *   island: the accepted line-search trial (0..4: t = 1 .. 1/16, 5: damped
+ *     step, 255: stopped).
+ * 255 marks an iteration that did not run.  orc_record_decisions(iters <= 0)
+ * turns the log off; returns -1 if it cannot allocate. */
+int orc_record_decisions(orc_ctx *ctx, int32_t iters);
+void orc_get_decisions(const orc_ctx *ctx, uint8_t *rows, uint8_t *islands);
 
 /* Debug / test access to one linearisation.  Runs the first n_before Newton
  * iterations of a step from the current state (without committing), then
@@ -197,6 +212,11 @@ typedef struct {
 } orc_contacts;
 
 int32_t orc_collide(const orc_collide_in *in, orc_contacts *out);
+/* The same contacts with every decision and all geometry in FP64 (unit
+ * quaternions): the plain definition, against which the FP32 decisions of
+ * orc_collide (and of the GPU) differ only within rounding of the margin or
+ * of a tie between nearest faces. */
+int32_t orc_collide_f64(const orc_collide_in *in, orc_contacts *out);
 
 #ifdef __cplusplus
 }

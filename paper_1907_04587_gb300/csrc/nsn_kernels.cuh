@@ -596,15 +596,56 @@ __device__ __forceinline__ void side_diff(const Side<T> &A, const Side<T> &B, T 
 // the production build), so that their rounding stays far below the
 // residual tolerance instead of ~1e-7 of the body size.  This is once per
 // row per Newton iteration, outside the CR loop.
+//
+// A body-frame vector v at the iterate is R(q(u)) v, with the kinematic
+// update of Sec. 9.4 q(u) = normalize(q0 + (h/2) [0, w] q0) from the
+// orientation q0 at the start of the step and the iterate's world-frame
+// angular velocity w.  It factors as q(u) = e(s) (q0 / |q0|) with s = (h/2) w
+// and the unit quaternion e(s) = (1, s) / sqrt(1 + |s|^2), so
+//   R(q(u)) v = r0 + 2 / (1 + |s|^2) (s x r0 + s x (s x r0)),  r0 = R(q0 / |q0|) v.
+// r0 depends on the start of the step only and is formed in FP64; the
+// increment, of the size h |w| |v|, is formed in the bulk type.  The values
+// are then smooth functions of u to FP64 accuracy, where the quaternion
+// stored in FP32 (rq) would carry its rounding -- different at every
+// iterate -- into every constraint value.  The FP64 build stores rq in FP64
+// and rotates with it directly, in the oracle's order of operations.
+template <typename T>
+__device__ __forceinline__ void rot_iter_f64(const Dev<T> &D, int b, const double *v, double *out) {
+  if (sizeof(T) == sizeof(double)) {
+    double q[4], R[9];
+    for (int k = 0; k < 4; k++) q[k] = double(D.rq[k][b]);
+    quat_R(q, R);
+    mat3v(R, v, out);
+    return;
+  }
+  const double w = D.rq0[0][b], x = D.rq0[1][b], y = D.rq0[2][b], z = D.rq0[3][b];
+  const double ww = w * w, xx = x * x, yy = y * y, zz = z * z;
+  const double n2 = (ww + xx) + (yy + zz);
+  // 1 / |q0|^2: an FP32 quaternion is unit to its rounding (n2 = 1 + d,
+  // |d| ~ 1e-7), where 2 - n2 equals 1 / n2 to d^2
+  const double inv = 2.0 - n2;
+  const double R[9] = {(ww + xx) - (yy + zz), 2 * (x * y - w * z), 2 * (x * z + w * y),
+                       2 * (x * y + w * z), (ww - xx) + (yy - zz), 2 * (y * z - w * x),
+                       2 * (x * z - w * y), 2 * (y * z + w * x), (ww - xx) - (yy - zz)};
+  double r0[3];
+  mat3v(R, v, r0);
+  const T hh = T(0.5) * D.hT;
+  const T s[3] = {hh * D.ru[3][b], hh * D.ru[4][b], hh * D.ru[5][b]};
+  const T r0t[3] = {T(r0[0] * inv), T(r0[1] * inv), T(r0[2] * inv)};
+  T c1[3], c2[3];
+  cross3(s, r0t, c1);
+  cross3(s, c1, c2);
+  const T f = T(2) / (T(1) + dot3(s, s));
+  for (int k = 0; k < 3; k++) out[k] = r0[k] * inv + double(f * (c1[k] + c2[k]));
+}
+
 template <typename T>
 __device__ __forceinline__ void point_parts_f64(const Dev<T> &D, int enc, const T *p, double *x0, double *hu,
                                                 double *r) {
   const double h = D.h;
   if (enc >= 0) {
-    double q[4], R[9], pd[3] = {double(p[0]), double(p[1]), double(p[2])};
-    for (int k = 0; k < 4; k++) q[k] = double(D.rq[k][enc]);
-    quat_R(q, R);
-    mat3v(R, pd, r);
+    const double pd[3] = {double(p[0]), double(p[1]), double(p[2])};
+    rot_iter_f64(D, enc, pd, r);
     for (int k = 0; k < 3; k++) { x0[k] = double(D.rx0[k][enc]); hu[k] = h * double(D.ru[k][enc]); }
   } else if (enc == -1) {
     for (int k = 0; k < 3; k++) { x0[k] = double(p[k]); hu[k] = 0.0; r[k] = 0.0; }
@@ -838,17 +879,16 @@ __global__ void k_eval_joints(Dev<T> D, int buf, int force) {
     D.cdiag[base + k] = e / (h * h);
     D.hv[base + k] = (cb + e * D.lam[base + k]) / h;
   }
+  // axes at the iterate: bulk type for the rows, FP64 (rot_iter_f64) for the values
   T aw[3], bl[2][3], bw[2][3];
-  double awd[3], Rbd[9];
+  double awd[3];
   if (ea >= 0) {
     T q[4], R[9];
     for (int k = 0; k < 4; k++) q[k] = D.rq[k][ea];
     quat_R(q, R);
     mat3v(R, axa, aw);
-    double qd[4], Rd[9], ad[3] = {double(axa[0]), double(axa[1]), double(axa[2])};
-    for (int k = 0; k < 4; k++) qd[k] = double(q[k]);
-    quat_R(qd, Rd);
-    mat3v(Rd, ad, awd);
+    const double ad[3] = {double(axa[0]), double(axa[1]), double(axa[2])};
+    rot_iter_f64(D, ea, ad, awd);
   } else {
     for (int k = 0; k < 3; k++) { aw[k] = axa[k]; awd[k] = double(axa[k]); }
   }
@@ -856,14 +896,12 @@ __global__ void k_eval_joints(Dev<T> D, int buf, int force) {
   T Rb[9];
   if (eb >= 0) {
     T q[4];
-    double qd[4];
-    for (int k = 0; k < 4; k++) { q[k] = D.rq[k][eb]; qd[k] = double(q[k]); }
+    for (int k = 0; k < 4; k++) q[k] = D.rq[k][eb];
     quat_R(q, Rb);
-    quat_R(qd, Rbd);
   }
   for (int k = 0; k < 2; k++) {
     double bwd[3], bld[3] = {double(bl[k][0]), double(bl[k][1]), double(bl[k][2])};
-    if (eb >= 0) { mat3v(Rb, bl[k], bw[k]); mat3v(Rbd, bld, bwd); }
+    if (eb >= 0) { mat3v(Rb, bl[k], bw[k]); rot_iter_f64(D, eb, bld, bwd); }
     else for (int m = 0; m < 3; m++) { bw[k][m] = bl[k][m]; bwd[m] = bld[m]; }
     T axb2[3];
     cross3(aw, bw[k], axb2);
@@ -1745,10 +1783,13 @@ __global__ void __launch_bounds__(RED_THREADS) k_merit(Dev<T> D, int n, int forc
 // rho_k / rho_{k-1} can exceed 1 at every iteration, so p grows geometrically).  FP32: a little above the rounding of the operator
 // apply; FP64: the oracle's value, well above FP64 rounding so that the
 // iteration at which it is crossed does not depend on summation order.
+#ifndef NSN_CR_FLOOR_F32
+#define NSN_CR_FLOOR_F32 1e-9
+#endif
 template <typename T>
 __device__ __forceinline__ double cr_floor() { return 1e-12; }
 template <>
-__device__ __forceinline__ double cr_floor<float>() { return 1e-6; }
+__device__ __forceinline__ double cr_floor<float>() { return NSN_CR_FLOOR_F32; }
 
 // ------------------------------------------------------------------------------------
 // K7: CR with one global synchronisation per iteration.  The scalar kernel

@@ -207,3 +207,27 @@ def test_trajectory_with_contacts_generated_every_step(orc):
         worst = max(worst, dv)
         print(f"step {step}: {len(cg['c_body'])} contacts, velocity difference {dv:.2e}")
     assert worst < 1e-9
+
+
+@pytest.mark.parametrize("name", ["random", "batched4096"])
+def test_contacts_within_rounding_of_the_fp64_definition(orc, name):
+    """The GPU's contacts against the oracle's plain FP64 definition of
+    contact generation (orc_collide_f64): lists differ only on vertex-shape
+    pairs whose distance is within 4 FP32 units of the coordinates' scale of
+    the margin, normals change face only on nearest-face ties within that
+    band, and other normals differ only by the rotation's rounding."""
+    import collide_band
+    if name == "random":
+        s, planes, margin = random_scene(7), ((0, 0, 1, 0), (0.6, 0.8, 0.0, -0.3)), 0.02
+    else:
+        s, planes, margin = scenes.batched_envs(seed=0, n_envs=4096), Z, 0.01
+    n_envs = int(s["env"].max()) + 1
+    mu = np.full(n_envs, 0.5, np.float32)
+    col = nsn.Collider(s, planes=planes, margin=margin, h=H, mu_env=mu)
+    g = col.run(s["pos"], s["quat"], s["vel"], s["omega"])
+    o = orc.collide(s["kind"], s["pos"], s["quat"], s["vel"], s["omega"], s["half"], s["env"], planes, col.exclude,
+                    mu, margin, H, fp64_decisions=True)
+    r = collide_band.compare(s, g, o, [list(p) for p in planes], margin, H)
+    print(name, r)
+    assert r["membership"] <= 4 and r["face"] <= 4 and r["normal"] <= 8, r
+    assert r["n_common"] >= 0.999 * max(len(g["c_body"]), len(o["c_body"])), r

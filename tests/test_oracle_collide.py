@@ -12,6 +12,18 @@ from paper_1907_04587_gb300 import scenes
 
 H = 1.0 / 60.0
 Z_PLANE = [[0.0, 0.0, 1.0, 0.0]]
+FP64_DECISIONS = False
+
+
+@pytest.fixture(autouse=True, params=[False, True], ids=["fp32-decisions", "fp64-decisions"])
+def decisions(request):
+    """Every pin below holds for both versions of the oracle's contact
+    generation: decisions in FP32 (the GPU's order of rounded operations) and
+    the plain FP64 definition."""
+    global FP64_DECISIONS
+    FP64_DECISIONS = request.param
+    yield request.param
+    FP64_DECISIONS = False
 
 
 def run(bodies, planes=Z_PLANE, exclude=None, mu=(0.5,), margin=0.01, h=H):
@@ -20,7 +32,8 @@ def run(bodies, planes=Z_PLANE, exclude=None, mu=(0.5,), margin=0.01, h=H):
     z3 = np.zeros((nb, 3))
     return oracle.collide(b["kind"], b["pos"], b.get("quat", np.tile([1.0, 0, 0, 0], (nb, 1))),
                           b.get("vel", z3), b.get("omega", z3), b.get("half", z3),
-                          b.get("env", np.zeros(nb, np.int32)), planes, exclude, mu, margin, h)
+                          b.get("env", np.zeros(nb, np.int32)), planes, exclude, mu, margin, h,
+                          fp64_decisions=FP64_DECISIONS)
 
 
 def world(pos, quat, local):
@@ -143,7 +156,7 @@ def test_scene_contacts_are_reproduced():
     s = scenes.batched_envs(seed=5, n_envs=8)
     jb = s["j_body"][s["j_body"][:, 1] >= 0]
     r = oracle.collide(s["kind"], s["pos"], s["quat"], s["vel"], s["omega"], s["half"], s["env"], Z_PLANE, jb,
-                       np.full(8, 0.5), 0.01, H)
+                       np.full(8, 0.5), 0.01, H, fp64_decisions=FP64_DECISIONS)
     gen = {}
     for i, ((a, b), pa) in enumerate(zip(r["c_body"], r["c_pa"])):
         gen[(int(a), int(b), tuple(np.sign(pa).astype(int)))] = i
@@ -231,3 +244,48 @@ def test_relative_velocity_and_plane_offset():
     r = run(dict(kind=[1], pos=[[0.3, 0.4, 0.105]]), planes=[[0, 0, 1, 0.1]])
     np.testing.assert_allclose(r["c_pb"], [[0.3, 0.4, 0.1]], atol=1e-7)
     assert len(run(dict(kind=[1], pos=[[0.3, 0.4, 0.115]]), planes=[[0, 0, 1, 0.1]])["c_body"]) == 0
+
+
+@pytest.mark.parametrize("which", ["batched", "particles_and_boxes"])
+def test_fp32_decisions_differ_from_the_fp64_definition_only_within_rounding(which, decisions):
+    """The FP32 decisions (the GPU's) against the plain FP64 definition on
+    scenes whose vertices rest on planes and boxes (many decisions sit near
+    the margin or on a face tie): a pair present in one list only lies within
+    4 FP32 units of the coordinates' scale of the margin, a normal that changes
+    face belongs to a tie within the same band, other normals differ only by
+    the rotation's rounding, and geometry of the common pairs agrees."""
+    if decisions:
+        pytest.skip("compares the two versions once")
+    import collide_band
+    if which == "batched":
+        s = scenes.batched_envs(seed=1, n_envs=512)
+        planes = Z_PLANE
+        n_envs = 512
+    else:
+        rng = np.random.default_rng(11)
+        b = scenes.SceneBuilder()
+        for i in range(300):
+            if i % 3:
+                b.add_particle(rng.uniform([-1, -1, -0.01], [1, 1, 0.3]), vel=rng.normal(scale=0.3, size=3))
+            else:
+                q = scenes.quat_axis_angle(rng.normal(size=3), rng.uniform(0, np.pi))
+                b.add_rigid(rng.uniform([-1, -1, 0.0], [1, 1, 0.3]), q, vel=rng.normal(scale=0.3, size=3),
+                            omega=rng.normal(scale=1.0, size=3))
+        s = b.build()
+        s["half"] = np.where((s["kind"] == 0)[:, None], rng.uniform(0.05, 0.2, (len(s["kind"]), 3)), 0.0)
+        planes = [[0.0, 0.0, 1.0, 0.0], [0.6, 0.0, 0.8, 0.3]]
+        n_envs = 1
+    ex = s["j_body"][(s["j_body"] >= 0).all(1)] if len(s["j_body"]) else None
+    args = (s["kind"], s["pos"], s["quat"], s["vel"], s["omega"], s["half"], s["env"], planes, ex,
+            np.full(n_envs, 0.5), 0.01, H)
+    A = oracle.collide(*args)
+    B = oracle.collide(*args, fp64_decisions=True)
+    r = collide_band.compare(s, A, B, planes, 0.01, H)
+    assert r["membership"] <= 4 and r["face"] <= 4 and r["normal"] <= 4, r
+    assert r["n_common"] >= 0.999 * max(len(A["c_body"]), len(B["c_body"])), r
+    ka, kb = collide_band.contact_keys(A, planes), collide_band.contact_keys(B, planes)
+    same = [(ka[k], kb[k]) for k in set(ka) & set(kb)
+            if np.abs(A["c_n"][ka[k]] - B["c_n"][kb[k]]).max() < 1e-6]
+    ia, ib = np.array(same).T
+    np.testing.assert_allclose(A["c_pb"][ia], B["c_pb"][ib], rtol=0, atol=1e-6)
+    print(which, r)
