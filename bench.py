@@ -418,6 +418,7 @@ def run_reference(args, rank, world):
 EAGER = False   # --eager: launch kernel by kernel instead of the CUDA graph (for profilers)
 RESIDENT = 1    # --resident 0: every island in the streamed CR loop
 CR_TOL = 0      # --cr-tol 1: CR of a Newton iteration also stops at the forcing term min(0.1, m/m0)
+REGEN = 1       # --contacts fixed: the scene's contacts for the whole trajectory instead of generating them each step
 LS = 1          # --line-search 0: the headline arm takes the damped step of Sec. 8.1 instead
 
 
@@ -431,12 +432,17 @@ def make_solver(nsn, s, stream, newton, cr, cone, warm=0, params=None, ncp=0, rs
     return g
 
 
-def measure_arm(nsn, torch, g, s, st0, stream, steps, warmup, clk=None, reset=False):
+def measure_arm(nsn, torch, g, s, st0, stream, steps, warmup, clk=None, reset=False, collider=None):
     """Device-timed advancing trajectory: reset to the start state, warmup
     steps, then `steps` timed steps; per-step island stop iterations are copied
     on the device and counted afterwards.  reset=True: every step starts from
     the start state with no previous-step multipliers (an environment reset,
-    as RL training does at episode starts)."""
+    as RL training does at episode starts).  collider: contacts regenerated
+    at every step (nsn_collide_and_step: the collider on the current state,
+    the layout rebuilt for the new contacts, the previous multipliers carried
+    over by key), all inside the timed region; the islands then change from
+    step to step, and each step's are counted with that step's stop
+    iterations."""
     dev = st0["pos"].device
     ni, bi = g.islands()
     isl_env = island_env_map(s, bi, ni)
@@ -448,22 +454,35 @@ def measure_arm(nsn, torch, g, s, st0, stream, steps, warmup, clk=None, reset=Fa
         nsn.nsn_set_state_device(g.ctx, ptr["pos"], ptr["quat"], ptr["vel"], ptr["omega"])
         g.clear_warm_start()
 
+    def one_step():
+        return g.collide_and_step(collider, 1) if collider is not None else g.step(1)
+
     for _ in range(warmup):
         if reset:
             restart()
-        g.step(1)
+        one_step()
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     if clk:
         clk.__enter__()
+    newton, launches, contacts = [], 0, []
+    if collider is not None:
+        # islands change with the contacts: the stop iterations of each step go
+        # to a buffer of the largest island count a scene of these bodies can
+        # have (every body alone), with that step's island -> environment map
+        stops = torch.full((steps, len(s["mass"])), -1, dtype=torch.int32, device=dev)
+        maps = []
     e0.record(stream)
-    newton, launches = [], 0
     for k in range(steps):
         if reset:
             restart()
-        st = g.step(1)
+        st = one_step()
         nsn.lib().nsn_island_stop_copy(g.ctx, nsn.C.c_void_p(stops[k].data_ptr()))
+        if collider is not None:
+            ni_k, bi_k = g.islands()
+            maps.append((ni_k, island_env_map(s, bi_k, ni_k)))
+            contacts.append((g.R - 5 * len(s["j_body"])) // 3)
         newton.append(st["newton_done"])
         launches += g.launches_per_step()
     e1.record(stream)
@@ -471,11 +490,28 @@ def measure_arm(nsn, torch, g, s, st0, stream, steps, warmup, clk=None, reset=Fa
     if clk:
         clk.__exit__()
     sec = e0.elapsed_time(e1) / 1e3
-    conv, conv_isl, mean_stop = count_converged(stops[:, :ni].cpu().numpy(), isl_env, n_envs)
-    return dict(sec=sec, env_steps=conv, env_fraction=conv / (steps * n_envs),
-                island_fraction=conv_isl / max(steps * ni, 1), mean_newton_to_tol=mean_stop,
-                newton_per_step=float(np.mean(newton)), ms_per_step=sec * 1e3 / steps,
-                value=conv / sec, islands=ni, kernels=launches)
+    if collider is None:
+        conv, conv_isl, mean_stop = count_converged(stops[:, :ni].cpu().numpy(), isl_env, n_envs)
+        n_isl_steps = steps * ni
+    else:
+        sa = stops.cpu().numpy()
+        conv = conv_isl = 0
+        stops_ok = []
+        for k, (ni_k, env_k) in enumerate(maps):
+            c1, c2, _ = count_converged(sa[k:k + 1, :ni_k], env_k, n_envs)
+            conv += c1; conv_isl += c2
+            stops_ok.append(sa[k, :ni_k][sa[k, :ni_k] >= 0])
+        allok = np.concatenate(stops_ok) if stops_ok else np.zeros(0)
+        mean_stop = float(allok.mean()) if len(allok) else float("nan")
+        n_isl_steps = sum(m[0] for m in maps)
+        ni = int(np.mean([m[0] for m in maps]))
+    out = dict(sec=sec, env_steps=conv, env_fraction=conv / (steps * n_envs),
+               island_fraction=conv_isl / max(n_isl_steps, 1), mean_newton_to_tol=mean_stop,
+               newton_per_step=float(np.mean(newton)), ms_per_step=sec * 1e3 / steps,
+               value=conv / sec, islands=ni, kernels=launches)
+    if collider is not None:
+        out["contacts_per_step"] = float(np.mean(contacts))
+    return out
 
 
 def run_ours(args, rank, world, local_rank):
@@ -505,12 +541,17 @@ def run_ours(args, rank, world, local_rank):
         warm, warm_note = "prev", "previous-step multipliers (no trained network weights present)"
     with torch.cuda.stream(stream):
         g = make_solver(nsn, s, stream, newton, cr, cone=1, warm=warm_names[warm], params=params, ls=LS)
+        # contacts regenerated at every step (Sec. 10) where the scene has
+        # collision shapes and per-environment friction (the batched workloads)
+        collider = None
+        if REGEN and "half" in s and "mu_env" in s:
+            collider = nsn.Collider(s, mu_env=s["mu_env"], stream=stream.cuda_stream)
         dist = None
         if world > 1:
             import torch.distributed as dist
             dist.barrier()
         clk = ClockSampler(local_rank)
-        main_arm = measure_arm(nsn, torch, g, s, st0, stream, args.steps, args.warmup, clk)
+        main_arm = measure_arm(nsn, torch, g, s, st0, stream, args.steps, args.warmup, clk, collider=collider)
         if warm != "zero":
             main_arm["network_or_warm_rejected_islands_last_step"] = g.warm_stats()["rejected"]
         sec = main_arm["sec"]
@@ -531,9 +572,17 @@ def run_ours(args, rank, world, local_rank):
         stops = torch.empty((args.steps, max(ni, 1)), dtype=torch.int32, device=dev)
         keys = ("pos", "quat", "vel", "omega")
 
+        if collider is not None:
+            stops = torch.full((args.steps, len(s["mass"])), -1, dtype=torch.int32, device=dev)
+            e2e_maps = []
+
         def e2e_step(k):
             L.nsn_set_state(g.ctx, *[fp(host_in[k2]) for k2 in keys])
-            g.step(1)
+            if collider is not None:
+                g.collide_and_step(collider, 1)
+                e2e_maps.append(g.islands())
+            else:
+                g.step(1)
             L.nsn_island_stop_copy(g.ctx, nsn.C.c_void_p(stops[k].data_ptr()))
             L.nsn_get_state(g.ctx, *[fp(host_out[k2]) for k2 in keys])
             for k2 in keys:
@@ -542,6 +591,8 @@ def run_ours(args, rank, world, local_rank):
         g.clear_warm_start()
         for _ in range(max(args.warmup, 1)):
             e2e_step(0)
+        if collider is not None:
+            e2e_maps.clear()
         if dist:
             dist.barrier()
         t0 = time.perf_counter()
@@ -549,7 +600,12 @@ def run_ours(args, rank, world, local_rank):
             e2e_step(k)
         torch.cuda.synchronize()
         sec_e2e = time.perf_counter() - t0
-        units_e2e, _, _ = count_converged(stops[:, :ni].cpu().numpy(), isl_env, n_envs)
+        if collider is None:
+            units_e2e, _, _ = count_converged(stops[:, :ni].cpu().numpy(), isl_env, n_envs)
+        else:
+            sa = stops.cpu().numpy()
+            units_e2e = sum(count_converged(sa[k:k + 1, :m[0]], island_env_map(s, m[1], m[0]), n_envs)[0]
+                            for k, m in enumerate(e2e_maps))
         # roofline of the CR operator apply, timed live on the solver's stream
         ms_body, ms_row = g.time_operator(20)
         sz = g.sizes()
@@ -664,6 +720,10 @@ def run_ours(args, rank, world, local_rank):
                    "cr": ("island-resident CR (groups of small islands in shared memory, one thread block "
                           "each) + streamed CR loop for the rest" if RESIDENT else "streamed CR loop only"),
                    "l2": "working set larger than L2 (no flush between steps)",
+                   "contacts": ("generated on the GPU at every step (Sec. 10: box corners and particles against the "
+                                "ground and the boxes of their environment, margin 1 cm, candidates from v + h g), "
+                                "the layout rebuilt for them, previous multipliers carried over by key; all inside "
+                                "the timed step" if collider is not None else "the scene's contacts, fixed"),
                    "parallelism": f"weak, {world} independent replica(s)"},
         "convergence": main_arm,
         "arms": arms,
@@ -702,11 +762,15 @@ def main():
                     help="0: no island-resident CR (every island in the streamed CR loop of four kernels per iteration)")
     ap.add_argument("--cr-tol", type=int, default=0,
                     help="1: inexact Newton, CR stops at ||r||_P <= min(0.1, merit/merit0) ||r0||_P (cap --cr)")
+    ap.add_argument("--contacts", default="regen", choices=["regen", "fixed"],
+                    help="regen (default): contacts generated at every step on the GPU (Sec. 10), timed with the step; "
+                         "fixed: the scene's contacts throughout")
     ap.add_argument("--line-search", type=int, default=1,
                     help="1 (default): headline arm with the back-tracking line search of Sec. 8.1; 0: damped step")
     args = ap.parse_args()
-    global EAGER, RESIDENT, CR_TOL, LS
+    global EAGER, RESIDENT, CR_TOL, LS, REGEN
     EAGER = bool(args.eager)
+    REGEN = 1 if args.contacts == "regen" else 0
     RESIDENT = int(args.resident)
     CR_TOL = int(args.cr_tol)
     LS = int(args.line_search)

@@ -21,10 +21,24 @@
  *   - Bodies receive ids 0..nb-1 in the order added.  -1 denotes the static
  *     world in constraint records.
  *   - Rows: contact c owns rows 3c (normal), 3c+1, 3c+2 (friction along the
- *     orthonormal basis of Duff et al. 2017 built from n); then joint j owns
- *     5 rows (3 positional, 2 angular); then tet k owns 3 rows (principal
- *     stretches s1 >= s2 >= |s3|).  Multipliers are forces (N); impulses are
- *     h * lambda.
+ *     orthonormal basis of Duff et al. 2017 built from n); then joint j (in
+ *     the order added, revolute and prismatic alike) owns 5 rows; then
+ *     Neo-Hookean tet k owns 3 rows (principal stretches s1 >= s2 >= |s3|);
+ *     then linear tet l owns 6 rows.  Multipliers are forces (N); impulses
+ *     are h * lambda.
+ *   - Revolute rows: 3 anchor-coincidence rows, 2 rows keeping a's axis
+ *     orthogonal to the basis t1, t2 of b's axis (Sec. 3.1; the paper gives no
+ *     joint functions).  Prismatic rows (the Fetch scenes of Sec. 10): t_k .
+ *     (p_a - p_b) for k = 1, 2 (a's anchor stays on the line through b's
+ *     anchor along b's axis), a_w . t_1, a_w . t_2, and n_a . t_2 with n_a the
+ *     first basis vector of a's axis (no twist); both axes are normalised.
+ *   - Linear tet rows (Sec. 9.2.1): the small strain of F = D_s D_m^-1 in the
+ *     eigenbasis of the isotropic stiffness: (e_xx + e_yy + e_zz) / sqrt(3),
+ *     (e_xx - e_yy) / sqrt(2), (e_xx + e_yy - 2 e_zz) / sqrt(6), and the
+ *     engineering shears 2 e_yz, 2 e_xz, 2 e_xy; the paper's strain vector
+ *     s rotated by a constant orthogonal matrix, which makes the compliance
+ *     (V_e K_e)^-1 diagonal (1 / (V_e (3 lambda + 2 mu)), 1 / (2 V_e mu) twice,
+ *     1 / (V_e mu) three times).
  *
  * Ownership: every host array passed in is copied; the caller keeps it.  All
  * device memory belongs to the context and is released by nsn_destroy.  The
@@ -58,7 +72,7 @@ typedef enum {
 } nsn_status;
 
 enum { NSN_RIGID = 0, NSN_PARTICLE = 1 };
-enum { NSN_CONTACT = 0, NSN_REVOLUTE = 1, NSN_TET_NH = 2 };
+enum { NSN_CONTACT = 0, NSN_REVOLUTE = 1, NSN_TET_NH = 2, NSN_PRISMATIC = 3, NSN_TET_LINEAR = 4 };
 enum { NSN_NCP_FB = 0, NSN_NCP_MIN = 1 };
 enum { NSN_R_NONE = 0, NSN_R_H2 = 1, NSN_R_EFFMASS = 2 };
 enum { NSN_GS_OFF = 0, NSN_GS_PARTICLES = 1 };
@@ -162,11 +176,12 @@ nsn_status nsn_add_bodies(nsn_ctx *ctx, int32_t n, const int32_t *kind, const fl
                           const float *quat, const float *vel, const float *omega,
                           const float *mass, const float *inertia, int32_t *first_id);
 
-/* Appends n constraint records of one type (nsn_contact, nsn_revolute or
- * nsn_tet array, copied).  first_row receives the first row of the block
- * within its type's row range.  Contacts: body ids of any kind or -1.
- * Revolute: rigid or -1.  Tet: four distinct particles with a non-degenerate
- * rest shape. */
+/* Appends n constraint records of one type (nsn_contact; nsn_revolute for
+ * NSN_REVOLUTE and NSN_PRISMATIC; nsn_tet for NSN_TET_NH and NSN_TET_LINEAR;
+ * copied).  first_row receives the first row of the block within its type's
+ * row range (joints of both kinds share one range).  Contacts: body ids of
+ * any kind or -1.  Joints: rigid or -1; prismatic axes nonzero.  Tets: four
+ * distinct particles with a non-degenerate rest shape, E > 0, 0 < nu < 0.5. */
 nsn_status nsn_add_constraints(nsn_ctx *ctx, int32_t type, int32_t n, const void *records,
                                int32_t *first_row);
 
@@ -292,6 +307,10 @@ enum { NSN_WARM_ZERO = 0, NSN_WARM_PREV = 1, NSN_WARM_LEARNED = 2 };
 #define NSN_WARM_PRECOND 0x200
 #define NSN_MLP_NPARAM (128 * 16 + 128 + 128 * 128 + 128 + 128 * 128 + 128 + 4 * 128 + 4)
 nsn_status nsn_set_warm_start(nsn_ctx *ctx, int32_t mode);
+/* The previous step's multipliers as the next warm start reads them (R
+ * values, ABI row order; after contacts were replaced, those carried over by
+ * key, zero for new contacts). */
+nsn_status nsn_get_prev_lambda(nsn_ctx *ctx, double *lambda);
 /* Forgets the previous step's multipliers (sets them to zero), e.g. after
  * the state was reset: the next step's previous-step candidate is then the
  * zero start.  Enqueued on the context stream; allocates nothing. */
@@ -315,6 +334,29 @@ nsn_status nsn_island_stop_device(nsn_ctx *ctx, const int32_t **stopped_at);
 /* Enqueues on the context stream a device-to-device copy of those n_islands
  * int32 into dst_device (a device buffer of the caller).  Allocates nothing. */
 nsn_status nsn_island_stop_copy(nsn_ctx *ctx, int32_t *dst_device);
+
+/* Decision log, for comparisons across precisions (verification): the
+ * discrete choices of the method at each of the first `iters` Newton
+ * iterations of each following step (iters = 0: off; the log is kept on the
+ * device and rewritten by every step).  nsn_get_decisions copies the last
+ * step's log: rows (iters x nsn_counts() rows, ABI row order) and islands
+ * (iters x islands of nsn_islands), one byte each:
+ *   contact normal row: bit 0 the Fischer-Burmeister kink C = lambda = 0
+ *     (Sec. 4.2; min-map: the branch C <= r lambda), bit 1 / bit 2 the cone
+ *     projection clamped lambda_n / scaled lambda_f in the update;
+ *   friction rows: 0 inactive (mu lambda_n <= 0, Sec. 3.5), 1 inactive past
+ *     the asymptote of W (App. A.2), 2 stick (W = 0), 3 sliding;
+ *   joint rows: 0;  tet rows: eigenvalues of the Hessian clamped to keep it
+ *     positive definite (Sec. 9.2.2), +4 when the tet is inverted;
+ *   island: the line-search trial taken (Sec. 8.1; 0..4 for t = 1 .. 1/16,
+ *     5 the damped step), 255 an island that had stopped;
+ *   cr (iters x islands, uint16): the CR updates the island took before a
+ *     stop test of Sec. 8.2 (or the cap) ended its CR, 0xffff for an island
+ *     that had stopped.
+ * 255 marks a row or iteration that was not evaluated.  Any output may be
+ * NULL.  No logged step: NSN_ERR_BAD_STATE. */
+nsn_status nsn_record_decisions(nsn_ctx *ctx, int32_t iters);
+nsn_status nsn_get_decisions(nsn_ctx *ctx, uint8_t *rows, uint8_t *islands, uint16_t *cr);
 
 /* Merits of the last warm-started step: zero start, warm start (the
  * network's candidate for NSN_WARM_LEARNED), and whether that candidate was
@@ -439,6 +481,24 @@ nsn_status nsn_collider_run_async(nsn_collider *c, const float *pos, const float
                                   float *c_n, float *c_d, float *c_mu, int32_t *found_dev);
 nsn_status nsn_collider_info(const nsn_collider *c, int32_t *info4);
 const char *nsn_collider_last_error(const nsn_collider *c);
+
+/* Time steps with contacts generated at the start of each (Sec. 10: collision
+ * detection once per step, candidates from the unconstrained velocity,
+ * normals between closest points at the start of the step).  For each of
+ * nsteps steps: the collider runs on the context's current state (positions,
+ * orientations, angular velocities, and linear velocities plus h g), its
+ * contacts replace the context's contacts, and one step of nsn_step runs.
+ * The collider describes the same bodies as the context (same count and
+ * order); its contacts come with the collider's friction per environment.
+ * Replacing the contacts rebuilds the context's layout on the host (the
+ * islands and the row order change with the contacts); the previous step's
+ * multipliers -- the NSN_WARM_PREV start and the learned start's fallback --
+ * carry over contact by contact through the key (body_a, body_b, point on
+ * a), which for a generated contact names the vertex and the shape, and row
+ * by row for joints and tets.  stats: the last step.  Errors: those of the
+ * collider (NSN_ERR_INVALID_ARG for a collider of another body count) and of
+ * nsn_step.  The context's stream waits for the collider at each step. */
+nsn_status nsn_collide_and_step(nsn_ctx *ctx, nsn_collider *col, int32_t nsteps, nsn_stats *stats);
 
 #ifdef __cplusplus
 }

@@ -47,8 +47,9 @@ class _Scene(C.Structure):
         ("n_contacts", C.c_int32), ("c_body", _ip), ("c_pa", _dp), ("c_pb", _dp), ("c_n", _dp),
         ("c_d", _dp), ("c_mu", _dp),
         ("n_joints", C.c_int32), ("j_body", _ip), ("j_pa", _dp), ("j_pb", _dp), ("j_axa", _dp),
-        ("j_axb", _dp), ("j_compliance", _dp),
+        ("j_axb", _dp), ("j_compliance", _dp), ("j_kind", _ip),
         ("n_tets", C.c_int32), ("t_v", _ip), ("t_rest", _dp), ("t_E", _dp), ("t_nu", _dp),
+        ("n_ltets", C.c_int32), ("l_v", _ip), ("l_rest", _dp), ("l_E", _dp), ("l_nu", _dp),
     ]
 
 
@@ -113,7 +114,7 @@ def lib():
         L.orc_get_island_stats.argtypes = [C.c_void_p, _dp, _dp, _ip]
         L.orc_record_decisions.argtypes = [C.c_void_p, C.c_int32]
         L.orc_record_decisions.restype = C.c_int
-        L.orc_get_decisions.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+        L.orc_get_decisions.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
         L.orc_fb.restype = C.c_double
         L.orc_fb.argtypes = [C.c_double, C.c_double]
         for f in ("orc_fb_contact", "orc_min_contact"):
@@ -178,6 +179,7 @@ class Oracle:
         nc = int(np.shape(scene.get("c_body", np.zeros((0, 2))))[0])
         nj = int(np.shape(scene.get("j_body", np.zeros((0, 2))))[0])
         nt = int(np.shape(scene.get("t_v", np.zeros((0, 4))))[0])
+        nl = int(np.shape(scene.get("l_v", np.zeros((0, 4))))[0])
         s = _Scene()
         s.n_bodies = nb
         s.kind = _ptr(arr("kind", np.int32, (nb,)))
@@ -201,11 +203,17 @@ class Oracle:
         s.j_axa = _ptr(arr("j_axa", np.float64, (nj, 3)))
         s.j_axb = _ptr(arr("j_axb", np.float64, (nj, 3)))
         s.j_compliance = _ptr(arr("j_compliance", np.float64, (nj,)))
+        s.j_kind = _ptr(arr("j_kind", np.int32, (nj,)))     # 0 revolute (default), 1 prismatic
         s.n_tets = nt
         s.t_v = _ptr(arr("t_v", np.int32, (nt, 4)))
         s.t_rest = _ptr(arr("t_rest", np.float64, (nt, 4, 3)))
         s.t_E = _ptr(arr("t_E", np.float64, (nt,)))
         s.t_nu = _ptr(arr("t_nu", np.float64, (nt,)))
+        s.n_ltets = nl
+        s.l_v = _ptr(arr("l_v", np.int32, (nl, 4)))
+        s.l_rest = _ptr(arr("l_rest", np.float64, (nl, 4, 3)))
+        s.l_E = _ptr(arr("l_E", np.float64, (nl,)))
+        s.l_nu = _ptr(arr("l_nu", np.float64, (nl,)))
         pr = _Params()
         pr.h = p["h"]
         pr.gravity = (C.c_double * 3)(*p["gravity"])
@@ -225,7 +233,7 @@ class Oracle:
         self.ctx = L.orc_create(C.byref(s), C.byref(pr))
         if not self.ctx:
             raise ValueError("oracle rejected the scene")
-        self.nb, self.nc, self.nj, self.nt = nb, nc, nj, nt
+        self.nb, self.nc, self.nj, self.nt, self.nl = nb, nc, nj, nt, nl
         self.R = L.orc_num_rows(self.ctx)
         self.D = L.orc_num_dofs(self.ctx)
         self.last_stats = None
@@ -283,12 +291,15 @@ class Oracle:
         self._dlog_iters = int(iters)
 
     def decisions(self):
-        """(rows: iters x R uint8, islands: iters x n_islands uint8) of the last step."""
+        """(rows: iters x R uint8, islands: iters x n_islands uint8, cr: iters x
+        n_islands uint16) of the last step."""
         n = lib().orc_num_islands(self.ctx)
         rows = np.zeros((self._dlog_iters, self.R), np.uint8)
         isl = np.zeros((self._dlog_iters, n), np.uint8)
-        lib().orc_get_decisions(self.ctx, rows.ctypes.data_as(C.c_void_p), isl.ctypes.data_as(C.c_void_p))
-        return rows, isl
+        cr = np.zeros((self._dlog_iters, n), np.uint16)
+        lib().orc_get_decisions(self.ctx, rows.ctypes.data_as(C.c_void_p), isl.ctypes.data_as(C.c_void_p),
+                                cr.ctypes.data_as(C.c_void_p))
+        return rows, isl, cr
 
     def merit_history(self):
         out = np.zeros(4096)

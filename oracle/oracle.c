@@ -41,12 +41,15 @@ typedef struct {
 
 struct orc_ctx {
   orc_params p;
-  int nb, nc, nj, nt, R, D;
+  int nb, nc, nj, nt, nl, R, D;
   /* scene copies */
   int *kind;
   double *mass, *inertia;
   int *c_body; double *c_pa, *c_pb, *c_n, *c_d, *c_mu;
   int *j_body; double *j_pa, *j_pb, *j_axa, *j_axb, *j_e;
+  int *j_kind;               /* 0 revolute, 1 prismatic */
+  int *l_v; double *l_Dminv, *l_Ve, *l_K6, *l_E6;   /* linear tets: rest inverse, volume, V_e K_e, its inverse E */
+  double *c6;                /* nl x 36, linear-tet compliance blocks E / h^2 */
   int *t_v; double *t_Dminv, *t_Ve, *t_C1, *t_D1, *t_alpha;
   int *dof;                  /* dof offset per body */
   /* state */
@@ -68,6 +71,7 @@ struct orc_ctx {
    * one code per row (dlog[n R + i]) and per island (dlog_ls[n ni + i]);
    * dlog_n is the iteration whose main evaluation is running (-1: none) */
   uint8_t *dlog, *dlog_ls;
+  uint16_t *dlog_cr;   /* CR updates per island per Newton iteration */
   int dlog_iters, dlog_n, dlog_rec;
   /* islands */
   int ni;
@@ -299,6 +303,31 @@ void orc_svd3(const double F[9], double U[9], double s[3], double V[9]) {
   }
 }
 
+/* inverse of an n x n matrix (n <= 6) by Gauss-Jordan elimination with
+ * partial pivoting; returns -1 if singular */
+static int inv_n(const double *M, int n, double *Mi) {
+  double A[6][12];
+  for (int i = 0; i < n; i++)
+    for (int j = 0; j < 2 * n; j++) A[i][j] = j < n ? M[n * i + j] : (j - n == i ? 1.0 : 0.0);
+  for (int col = 0; col < n; col++) {
+    int piv = col;
+    for (int r = col + 1; r < n; r++) if (fabs(A[r][col]) > fabs(A[piv][col])) piv = r;
+    if (A[piv][col] == 0.0) return -1;
+    if (piv != col)
+      for (int j = 0; j < 2 * n; j++) { double t = A[col][j]; A[col][j] = A[piv][j]; A[piv][j] = t; }
+    const double d = A[col][col];
+    for (int j = 0; j < 2 * n; j++) A[col][j] /= d;
+    for (int r = 0; r < n; r++) {
+      if (r == col || A[r][col] == 0.0) continue;
+      const double f = A[r][col];
+      for (int j = 0; j < 2 * n; j++) A[r][j] -= f * A[col][j];
+    }
+  }
+  for (int i = 0; i < n; i++)
+    for (int j = 0; j < n; j++) Mi[n * i + j] = A[i][n + j];
+  return 0;
+}
+
 static int inv3(const double *M, double *Mi) {
   double d = det3(M);
   if (d == 0.0) return -1;
@@ -340,6 +369,8 @@ static void build_islands(orc_ctx *c) {
   for (int j = 0; j < c->nj; j++) uf_union(par, c->j_body[2 * j], c->j_body[2 * j + 1]);
   for (int t = 0; t < c->nt; t++)
     for (int q = 1; q < 4; q++) uf_union(par, c->t_v[4 * t], c->t_v[4 * t + q]);
+  for (int t = 0; t < c->nl; t++)
+    for (int q = 1; q < 4; q++) uf_union(par, c->l_v[4 * t], c->l_v[4 * t + q]);
   c->body_isl = malloc(sizeof(int) * (nb + 1));
   int *id = malloc(sizeof(int) * (nb + 1));
   for (int i = 0; i < nb; i++) id[i] = -1;
@@ -360,6 +391,9 @@ static void build_islands(orc_ctx *c) {
   }
   for (int t = 0; t < c->nt; t++)
     for (int q = 0; q < 3; q++) c->row_isl[3 * c->nc + 5 * c->nj + 3 * t + q] = c->body_isl[c->t_v[4 * t]];
+  for (int t = 0; t < c->nl; t++)
+    for (int q = 0; q < 6; q++)
+      c->row_isl[3 * c->nc + 5 * c->nj + 3 * c->nt + 6 * t + q] = c->body_isl[c->l_v[4 * t]];
   c->isl_m0 = calloc(c->ni + 1, sizeof(double));
   c->isl_mf = calloc(c->ni + 1, sizeof(double));
   c->isl_acc = calloc(c->ni + 1, sizeof(double));
@@ -392,11 +426,17 @@ orc_ctx *orc_create(const orc_scene *s, const orc_params *prm) {
       int v = s->t_v[4 * t + k];
       if (v < 0 || v >= nb || s->kind[v] != ORC_PARTICLE) return NULL;
     }
+  if (s->n_ltets < 0) return NULL;
+  for (int t = 0; t < s->n_ltets; t++)
+    for (int k = 0; k < 4; k++) {
+      int v = s->l_v[4 * t + k];
+      if (v < 0 || v >= nb || s->kind[v] != ORC_PARTICLE) return NULL;
+    }
 
   orc_ctx *c = (orc_ctx *)calloc(1, sizeof(orc_ctx));
   c->p = *prm;
-  c->nb = nb; c->nc = s->n_contacts; c->nj = s->n_joints; c->nt = s->n_tets;
-  c->R = 3 * c->nc + 5 * c->nj + 3 * c->nt;
+  c->nb = nb; c->nc = s->n_contacts; c->nj = s->n_joints; c->nt = s->n_tets; c->nl = s->n_ltets;
+  c->R = 3 * c->nc + 5 * c->nj + 3 * c->nt + 6 * c->nl;
   c->kind = dupd(s->kind, sizeof(int) * nb);
   c->mass = dupd(s->mass, sizeof(double) * nb);
   c->inertia = dupd(s->inertia, sizeof(double) * 3 * nb);
@@ -417,6 +457,38 @@ orc_ctx *orc_create(const orc_scene *s, const orc_params *prm) {
   c->j_axa = dupd(s->j_axa, sizeof(double) * 3 * c->nj);
   c->j_axb = dupd(s->j_axb, sizeof(double) * 3 * c->nj);
   c->j_e = dupd(s->j_compliance, sizeof(double) * c->nj);
+  c->j_kind = calloc(c->nj + 1, sizeof(int));
+  if (s->j_kind)
+    for (int j = 0; j < c->nj; j++) {
+      if (s->j_kind[j] != 0 && s->j_kind[j] != 1) { orc_destroy(c); return NULL; }
+      c->j_kind[j] = s->j_kind[j];
+    }
+  /* linear tets (Sec. 9.2.1): E = (V_e K_e)^-1 with the isotropic stiffness
+   * of the engineering strains (Lame mu, lambda from E and nu) */
+  c->l_v = dupd(s->l_v, sizeof(int) * 4 * c->nl);
+  c->l_Dminv = malloc(sizeof(double) * 9 * (c->nl + 1));
+  c->l_Ve = malloc(sizeof(double) * (c->nl + 1));
+  c->l_E6 = malloc(sizeof(double) * 36 * (c->nl + 1));
+  c->l_K6 = malloc(sizeof(double) * 36 * (c->nl + 1));
+  c->c6 = calloc(36 * (c->nl + 1), sizeof(double));
+  for (int t = 0; t < c->nl; t++) {
+    const double *X = s->l_rest + 12 * t;
+    double Dm[9];
+    for (int r = 0; r < 3; r++)
+      for (int k = 0; k < 3; k++) Dm[3 * r + k] = X[3 * (k + 1) + r] - X[r];
+    if (inv3(Dm, c->l_Dminv + 9 * t) != 0) { orc_destroy(c); return NULL; }
+    c->l_Ve[t] = fabs(det3(Dm)) / 6.0;
+    const double E = s->l_E[t], nu = s->l_nu[t];
+    if (!(E > 0.0) || !(nu > -1.0 && nu < 0.5)) { orc_destroy(c); return NULL; }
+    const double mu = E / (2.0 * (1.0 + nu)), la = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+    double K[36] = {0};
+    for (int i = 0; i < 3; i++)
+      for (int j = 0; j < 3; j++) K[6 * i + j] = la + (i == j ? 2.0 * mu : 0.0);
+    for (int i = 3; i < 6; i++) K[7 * i] = mu;
+    for (int k = 0; k < 36; k++) K[k] *= c->l_Ve[t];
+    memcpy(c->l_K6 + 36 * t, K, sizeof K);
+    if (inv_n(K, 6, c->l_E6 + 36 * t) != 0) { orc_destroy(c); return NULL; }
+  }
   c->t_v = dupd(s->t_v, sizeof(int) * 4 * c->nt);
   c->t_Dminv = malloc(sizeof(double) * 9 * (c->nt + 1));
   c->t_Ve = malloc(sizeof(double) * (c->nt + 1));
@@ -462,7 +534,8 @@ void orc_destroy(orc_ctx *c) {
                   c->t_C1, c->t_D1, c->t_alpha, c->dof, c->pos, c->quat, c->vel, c->omega, c->lambda,
                   c->pos0, c->quat0, c->Iw, c->Iwinv, c->ut, c->hdiag, c->rows, c->rows_prev, c->cdiag,
                   c->c3, c->hvec, c->b, c->pdiag, c->g, c->body_isl, c->row_isl, c->isl_m0,
-                  c->isl_mf, c->isl_acc, c->isl_stop, c->dlog, c->dlog_ls};
+                  c->isl_mf, c->isl_acc, c->isl_stop, c->dlog, c->dlog_ls, c->dlog_cr, c->j_kind,
+                  c->l_v, c->l_Dminv, c->l_Ve, c->l_K6, c->l_E6, c->c6};
   for (size_t i = 0; i < sizeof ptrs / sizeof ptrs[0]; i++) free(ptrs[i]);
   free(c);
 }
@@ -472,22 +545,24 @@ int32_t orc_num_rows(const orc_ctx *c) { return c->R; }
 int orc_record_decisions(orc_ctx *c, int32_t iters) {
   free(c->dlog);
   free(c->dlog_ls);
+  free(c->dlog_cr);
   c->dlog = NULL;
   c->dlog_ls = NULL;
+  c->dlog_cr = NULL;
   c->dlog_iters = 0;
   if (iters <= 0) return 0;
   c->dlog = malloc((size_t)iters * c->R + 1);
   c->dlog_ls = malloc((size_t)iters * c->ni + 1);
-  if (!c->dlog || !c->dlog_ls) return -1;
-  memset(c->dlog, 255, (size_t)iters * c->R + 1);
-  memset(c->dlog_ls, 255, (size_t)iters * c->ni + 1);
+  c->dlog_cr = malloc(sizeof(uint16_t) * ((size_t)iters * c->ni + 1));
+  if (!c->dlog || !c->dlog_ls || !c->dlog_cr) return -1;
   c->dlog_iters = iters;
   return 0;
 }
 
-void orc_get_decisions(const orc_ctx *c, uint8_t *rows, uint8_t *isl) {
+void orc_get_decisions(const orc_ctx *c, uint8_t *rows, uint8_t *isl, uint16_t *cr) {
   if (rows && c->dlog) memcpy(rows, c->dlog, (size_t)c->dlog_iters * c->R);
   if (isl && c->dlog_ls) memcpy(isl, c->dlog_ls, (size_t)c->dlog_iters * c->ni);
+  if (cr && c->dlog_cr) memcpy(cr, c->dlog_cr, sizeof(uint16_t) * (size_t)c->dlog_iters * c->ni);
 }
 int32_t orc_num_islands(const orc_ctx *c) { return c->ni; }
 void orc_get_islands(const orc_ctx *c, int32_t *body_island, int32_t *row_island) {
@@ -648,6 +723,76 @@ static void scale_row(orc_row *row, double a) {
 /* ------------------------------------------------------------------ */
 /* row evaluation at the iterate (q^n, u^n, lambda^n): J, C, h  (Sec. 6.1) */
 
+/* Prismatic joint (rows 5j .. 5j+4 of the joint block; the paper's Fetch
+ * scenes use prismatic joints but do not give their constraint functions).
+ * Reading: the anchor of a stays on the line through the anchor of b along
+ * b's slide axis u_b, and the relative rotation is locked:
+ *   rows 0, 1: t_k . (p_a - p_b), t_1, t_2 the orthonormal basis of u_b
+ *              (b's frame; world if b is static);
+ *   rows 2, 3: a_w . t_k (the axis of a stays along u_b);
+ *   row 4:     n_a . t_2, n_a the first basis vector of a's axis in a's
+ *              frame (no twist about the axis; zero when the two frames agree).
+ * The rows are the velocities of these functions: a positional row acts at
+ * p_a on both bodies (b's lever arm is p_a - x_b, since t_k turns with b);
+ * an angular row c = x . y has rows [0, x_w x y_w | 0, -(x_w x y_w)].
+ * Compliance e: C = e / h^2, h = (c + e lambda) / h as for revolute joints. */
+static void eval_prismatic(orc_ctx *c, int j, int a, int b, const double *wa, const double *ra, const double *wb,
+                           const double *lam) {
+  const double h = c->p.h, e = c->j_e[j];
+  const int base = 3 * c->nc + 5 * j;
+  /* Reading: the axes are directions; they are normalised before the basis
+   * is built (a rounded input is unit only to its rounding) */
+  double axa[3], axb[3];
+  memcpy(axa, c->j_axa + 3 * j, sizeof axa);
+  memcpy(axb, c->j_axb + 3 * j, sizeof axb);
+  const double la = sqrt(dot3(axa, axa)), lb0 = sqrt(dot3(axb, axb));
+  for (int k = 0; k < 3; k++) { axa[k] /= la; axb[k] /= lb0; }
+  double tb[2][3], t[2][3], Rb[9], Ra[9];
+  orc_basis(axb, tb[0], tb[1]);
+  if (b >= 0) {
+    quat_to_R(c->quat + 4 * b, Rb);
+    matvec3(Rb, tb[0], t[0]);
+    matvec3(Rb, tb[1], t[1]);
+  } else {
+    memcpy(t, tb, sizeof t);
+  }
+  double d[3], lb[3] = {0, 0, 0};
+  for (int k = 0; k < 3; k++) d[k] = wa[k] - wb[k];
+  if (b >= 0) for (int k = 0; k < 3; k++) lb[k] = wa[k] - c->pos[3 * b + k];
+  for (int k = 0; k < 2; k++) {
+    const int ri = base + k;
+    orc_row *r = &c->rows[ri];
+    r->nside = 0;
+    set_side(c, r, a, ra, t[k], 1.0);
+    set_side(c, r, b, lb, t[k], -1.0);
+    c->cdiag[ri] = e / (h * h);
+    c->hvec[ri] = (dot3(t[k], d) + e * lam[ri]) / h;
+  }
+  double aw[3], na[3], nb_[3], nw[3];
+  if (a >= 0) { quat_to_R(c->quat + 4 * a, Ra); matvec3(Ra, axa, aw); }
+  else memcpy(aw, axa, sizeof aw);
+  orc_basis(axa, na, nb_);
+  if (a >= 0) matvec3(Ra, na, nw);
+  else memcpy(nw, na, sizeof nw);
+  const double *xs[3] = {aw, aw, nw}, *ys[3] = {t[0], t[1], t[1]};
+  for (int k = 0; k < 3; k++) {
+    const int ri = base + 2 + k;
+    orc_row *r = &c->rows[ri];
+    r->nside = 0;
+    double xy[3];
+    cross3(xs[k], ys[k], xy);
+    for (int sd = 0; sd < 2; sd++) {
+      int body = sd == 0 ? a : b;
+      if (body < 0) continue;
+      int si = r->nside++;
+      r->body[si] = body;
+      for (int q = 0; q < 3; q++) { r->J[si][q] = 0.0; r->J[si][3 + q] = (sd == 0 ? 1.0 : -1.0) * xy[q]; }
+    }
+    c->cdiag[ri] = e / (h * h);
+    c->hvec[ri] = (dot3(xs[k], ys[k]) + e * lam[ri]) / h;
+  }
+}
+
 static void eval_rows(orc_ctx *c, const double *u, const double *lam) {
   const double h = c->p.h;
   /* contacts: Sec. 3.3, App. A.1 (normal), Sec. 4.3 / App. A.2 (friction) */
@@ -741,6 +886,10 @@ static void eval_rows(orc_ctx *c, const double *u, const double *lam) {
     attach_point(c, a, c->j_pa + 3 * j, wa, ra);
     attach_point(c, b, c->j_pb + 3 * j, wb, rb);
     double e = c->j_e[j];
+    if (c->j_kind[j] == 1) {
+      eval_prismatic(c, j, a, b, wa, ra, wb, lam);
+      continue;
+    }
     for (int k = 0; k < 3; k++) {
       int ri = base + 5 * j + k;
       double ek[3] = {0, 0, 0};
@@ -830,6 +979,56 @@ static void eval_rows(orc_ctx *c, const double *u, const double *lam) {
     }
     for (int k = 0; k < 9; k++) c->c3[9 * t + k] = E[k] / (h * h);
   }
+  /* constant-strain tets with a linear Hookean material (Sec. 9.2.1):
+   * s = [e_xx, e_yy, e_zz, 2 e_yz, 2 e_xz, 2 e_xy] of the small strain
+   * e = (F + F^T)/2 - I, F = D_s D_m^-1; U = V_e s^T K_e s / 2, so c = V_e K_e s,
+   * J = ds/dx (constant), E = (V_e K_e)^-1, C = E / h^2 (a 6 x 6 block) and
+   * h = E (c + lambda) / h, the pattern of the Neo-Hookean rows above. */
+  base = 3 * c->nc + 5 * c->nj + 3 * c->nt;
+  if (c->dlog && c->dlog_rec && c->dlog_n < c->dlog_iters)
+    memset(c->dlog + (size_t)c->dlog_n * c->R + base, 0, 6 * (size_t)c->nl);
+  for (int t = 0; t < c->nl; t++) {
+    const int *v = c->l_v + 4 * t;
+    const double *Dmi = c->l_Dminv + 9 * t, *E = c->l_E6 + 36 * t, *K = c->l_K6 + 36 * t;
+    double Ds[9], F[9];
+    for (int r = 0; r < 3; r++)
+      for (int k = 0; k < 3; k++) Ds[3 * r + k] = c->pos[3 * v[k + 1] + r] - c->pos[3 * v[0] + r];
+    for (int r = 0; r < 3; r++)
+      for (int k = 0; k < 3; k++) F[3 * r + k] = Ds[3 * r] * Dmi[k] + Ds[3 * r + 1] * Dmi[3 + k] + Ds[3 * r + 2] * Dmi[6 + k];
+    const double sv[6] = {F[0] - 1.0, F[4] - 1.0, F[8] - 1.0, F[5] + F[7], F[2] + F[6], F[1] + F[3]};
+    /* dF_ab / dx_{q,a} = w_q[b]: w_q = row q-1 of D_m^-1, w_0 = -(sum of the rows) */
+    double w[4][3];
+    for (int b2 = 0; b2 < 3; b2++) {
+      w[0][b2] = -(Dmi[b2] + Dmi[3 + b2] + Dmi[6 + b2]);
+      for (int q = 1; q < 4; q++) w[q][b2] = Dmi[3 * (q - 1) + b2];
+    }
+    double cv[6];
+    for (int k = 0; k < 6; k++) {
+      cv[k] = 0.0;
+      for (int m = 0; m < 6; m++) cv[k] += K[6 * k + m] * sv[m];
+    }
+    /* (component of the strain, pair of coordinates): normal strains a = b,
+     * engineering shears the two off-diagonal entries */
+    static const int IA[6] = {0, 1, 2, 1, 0, 0}, IB[6] = {0, 1, 2, 2, 2, 1};
+    for (int k = 0; k < 6; k++) {
+      const int ri = base + 6 * t + k;
+      orc_row *r = &c->rows[ri];
+      r->nside = 4;
+      for (int q = 0; q < 4; q++) {
+        r->body[q] = v[q];
+        for (int m = 0; m < 6; m++) r->J[q][m] = 0.0;
+        /* d e_ab / dx_{q,c} = (delta_ac w_q[b] + delta_bc w_q[a]) / 2; the
+         * engineering shear is twice the tensor entry */
+        if (k < 3) r->J[q][IA[k]] = w[q][IA[k]];
+        else { r->J[q][IA[k]] += w[q][IB[k]]; r->J[q][IB[k]] += w[q][IA[k]]; }
+      }
+      double el = 0.0;
+      for (int m = 0; m < 6; m++) el += E[6 * k + m] * (cv[m] + lam[base + 6 * t + m]);
+      c->hvec[ri] = el / h;
+      c->cdiag[ri] = E[7 * k] / (h * h);
+    }
+    for (int k = 0; k < 36; k++) c->c6[36 * t + k] = E[k] / (h * h);
+  }
 }
 
 /* z (D) = J^T x (R) */
@@ -864,6 +1063,10 @@ static void C_x_add(const orc_ctx *c, const double *x, double *w) {
   for (int t = 0; t < c->nt; t++)
     for (int r = 0; r < 3; r++)
       for (int q = 0; q < 3; q++) w[tb + 3 * t + r] += c->c3[9 * t + 3 * r + q] * x[tb + 3 * t + q];
+  const int lb = tb + 3 * c->nt;
+  for (int t = 0; t < c->nl; t++)
+    for (int r = 0; r < 6; r++)
+      for (int q = 0; q < 6; q++) w[lb + 6 * t + r] += c->c6[36 * t + 6 * r + q] * x[lb + 6 * t + q];
 }
 
 /* Schur operator of Eq. schur_system plus the eps shift of Sec. 8.4. */
@@ -1058,7 +1261,7 @@ static int pcr(orc_ctx *c, int iters, double eta, double *x, double *res_hist) {
  * PCR on each island's system by itself, all capped at iters.  eta[i] is the
  * island's forcing term (0 = fixed count).  Islands whose flag in skip is set
  * keep x = 0.  Returns the largest iteration count over the islands. */
-static int pcr_islands(orc_ctx *c, int iters, const double *eta, const int *skip, double *x) {
+static int pcr_islands(orc_ctx *c, int iters, const double *eta, const int *skip, double *x, int *its_out) {
   int R = c->R, ni = c->ni;
   if (R == 0) return 0;
   double *r = calloc(R, sizeof(double)), *z = calloc(R, sizeof(double)), *p = calloc(R, sizeof(double));
@@ -1129,6 +1332,7 @@ static int pcr_islands(orc_ctx *c, int iters, const double *eta, const int *skip
   }
   int kmax = 0;
   for (int i = 0; i < ni; i++) if (its[i] > kmax) kmax = its[i];
+  if (its_out) memcpy(its_out, its, sizeof(int) * ni);
   free(r); free(z); free(p); free(Az); free(Ap); free(zb); free(yb);
   free(rho); free(res0); free(acc); free(alpha); free(done); free(its); free(prev);
   return kmax;
@@ -1284,12 +1488,20 @@ static int newton(orc_ctx *c, const double *lambda0, int stop_at, orc_stats *st,
           eta_i[i] = e > 0.1 ? 0.1 : (e <= 0.0 ? 1e-30 : e);
         }
       }
-      cr_total += pcr_islands(c, c->p.cr_iters, eta_i, skip, w->dl);
+      int *its = calloc(c->ni + 1, sizeof(int));
+      cr_total += pcr_islands(c, c->p.cr_iters, eta_i, skip, w->dl, its);
+      if (c->dlog && n < c->dlog_iters)
+        for (int i = 0; i < c->ni; i++)
+          if (!skip[i]) c->dlog_cr[(size_t)n * c->ni + i] = (uint16_t)its[i];
+      free(its);
       free(eta_i); free(skip);
     } else {
       double eta = 0.0;
       if (c->p.cr_tol_mode) { eta = m0 > 0.0 ? mn / m0 : 0.0; if (eta > 0.1) eta = 0.1; if (eta <= 0.0) eta = 1e-30; }
-      cr_total += pcr(c, c->p.cr_iters, eta, w->dl, NULL);
+      const int kcr = pcr(c, c->p.cr_iters, eta, w->dl, NULL);
+      cr_total += kcr;
+      if (c->dlog && n < c->dlog_iters)
+        for (int i = 0; i < c->ni; i++) c->dlog_cr[(size_t)n * c->ni + i] = (uint16_t)kcr;
     }
     /* du = H~^-1 (h J^T dl - g)  (Sec. 6.2) */
     JT_x(c, w->dl, w->zb);
@@ -1335,6 +1547,7 @@ int orc_step(orc_ctx *c, const double *lambda0, orc_stats *st) {
   if (c->dlog) {
     memset(c->dlog, 255, (size_t)c->dlog_iters * c->R);
     memset(c->dlog_ls, 255, (size_t)c->dlog_iters * c->ni);
+    memset(c->dlog_cr, 255, sizeof(uint16_t) * (size_t)c->dlog_iters * c->ni);
   }
   orc_work w;
   work_alloc(c, &w);
@@ -1383,6 +1596,10 @@ int orc_linearize(orc_ctx *c, int32_t n_before, const double *lambda0, double *J
     for (int t = 0; t < c->nt; t++)
       for (int r = 0; r < 3; r++)
         for (int q = 0; q < 3; q++) C[(size_t)(tb + 3 * t + r) * R + tb + 3 * t + q] = c->c3[9 * t + 3 * r + q];
+    const int lb = tb + 3 * c->nt;   /* linear tets: 6 x 6 blocks */
+    for (int t = 0; t < c->nl; t++)
+      for (int r = 0; r < 6; r++)
+        for (int q = 0; q < 6; q++) C[(size_t)(lb + 6 * t + r) * R + lb + 6 * t + q] = c->c6[36 * t + 6 * r + q];
   }
   if (g) memcpy(g, c->g, sizeof(double) * D);
   if (hvec) memcpy(hvec, c->hvec, sizeof(double) * R);
@@ -1438,6 +1655,8 @@ int orc_eval_constraints(orc_ctx *c, double *cvals, double *Jgeo) {
     orc_svd3(F, U, s, V);
     for (int k = 0; k < 3; k++) cvals[tb + 3 * t + k] = s[k];
   }
+  /* linear tets: the strain components (rows at lambda = 0: h = E c / h = s / h) */
+  for (int i = tb + 3 * c->nt; i < c->R; i++) cvals[i] = c->hvec[i] * c->p.h;
   if (Jgeo) {
     memset(Jgeo, 0, sizeof(double) * (size_t)c->R * c->D);
     for (int i = 0; i < c->R; i++) {

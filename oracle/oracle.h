@@ -16,6 +16,8 @@
  *   contact c  -> rows 3c (normal), 3c+1, 3c+2 (friction t1, t2)
  *   joint j    -> rows 3*nc + 5j .. +4  (3 positional, 2 angular)
  *   tet k      -> rows 3*nc + 5*nj + 3k .. +2 (principal stretches s1..s3)
+ *   linear tet -> rows 3*nc + 5*nj + 3*nt + 6l .. +5 (strains e_xx, e_yy,
+ *                 e_zz, 2 e_yz, 2 e_xz, 2 e_xy; Sec. 9.2.1)
  * Body ids: index into the body arrays; -1 = static world.
  * Quaternions are scalar first (w, x, y, z); angular velocity is world frame
  * (kinematic map G of Sec. 9.4).
@@ -57,12 +59,19 @@ typedef struct {
   const double *j_pa, *j_pb;    /* nj x 3 anchors (local, world if static) */
   const double *j_axa, *j_axb;  /* nj x 3 hinge axis in a / b frame */
   const double *j_compliance;   /* nj, e of Sec. 3.2 (0 = hard) */
+  const int32_t *j_kind;        /* nj: 0 revolute, 1 prismatic (NULL: all revolute) */
   /* stable Neo-Hookean tetrahedra (Sec. 9.2.2, App. B) */
   int32_t n_tets;
   const int32_t *t_v;       /* nt x 4 particle body ids */
   const double *t_rest;     /* nt x 4 x 3 rest positions */
   const double *t_E;        /* nt Young's modulus */
   const double *t_nu;       /* nt Poisson ratio */
+  /* constant-strain tetrahedra with a linear Hookean material (Sec. 9.2.1) */
+  int32_t n_ltets;
+  const int32_t *l_v;       /* nl x 4 particle body ids */
+  const double *l_rest;     /* nl x 4 x 3 rest positions */
+  const double *l_E;        /* nl Young's modulus */
+  const double *l_nu;       /* nl Poisson ratio */
 } orc_scene;
 
 typedef struct {
@@ -138,11 +147,13 @@ void orc_get_island_stats(const orc_ctx *ctx, double *merit0, double *merit_fina
  *     asymptote of W, 2 stick (W = 0), 3 sliding;
  *   joint rows: 0;  tet rows: clamped eigenvalues of the Hessian (+4 inverted);
  *   island: the accepted line-search trial (0..4: t = 1 .. 1/16, 5: damped
- *     step, 255: stopped).
+ *     step, 255: stopped);
+ *   cr (uint16 per island): the CR updates before a stop test (or the cap)
+ *     ended the island's CR, 0xffff: stopped.
  * 255 marks an iteration that did not run.  orc_record_decisions(iters <= 0)
  * turns the log off; returns -1 if it cannot allocate. */
 int orc_record_decisions(orc_ctx *ctx, int32_t iters);
-void orc_get_decisions(const orc_ctx *ctx, uint8_t *rows, uint8_t *islands);
+void orc_get_decisions(const orc_ctx *ctx, uint8_t *rows, uint8_t *islands, uint16_t *cr);
 
 /* Debug / test access to one linearisation.  Runs the first n_before Newton
  * iterations of a step from the current state (without committing), then

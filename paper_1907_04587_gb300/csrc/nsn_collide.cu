@@ -40,6 +40,7 @@
 #include <vector>
 
 #include "../../include/nsn.h"
+#include "nsn_internal.h"
 
 namespace {
 
@@ -635,6 +636,8 @@ nsn_status nsn_collider_destroy(nsn_collider *c) {
 }
 
 const char *nsn_collider_last_error(const nsn_collider *c) { return c ? c->err.c_str() : "null collider"; }
+
+cudaStream_t nsn_collider_stream_of(const nsn_collider *c) { return c ? c->stream : nullptr; }
 
 nsn_status nsn_collider_run_async(nsn_collider *c, const float *pos, const float *quat, const float *vel,
                                   const float *omega, int32_t capacity, int32_t *c_body, float *c_pa, float *c_pb,

@@ -18,6 +18,7 @@
 #include "../../include/nsn.h"
 #include "nsn_kernels.cuh"
 #include "nsn_mlp.cuh"
+#include "nsn_internal.h"
 
 using namespace nsn;
 
@@ -39,7 +40,9 @@ struct HostScene {
   std::vector<float> pos, quat, vel, omega, mass, inertia;
   std::vector<nsn_contact> contacts;
   std::vector<nsn_revolute> joints;
-  std::vector<nsn_tet> tets;
+  std::vector<int32_t> jkind;       // per joint: 0 revolute, 1 prismatic
+  std::vector<nsn_tet> tets;        // stable Neo-Hookean
+  std::vector<nsn_tet> ltets;       // linear Hookean (Sec. 9.2.1)
 };
 
 // Bump allocator over one device allocation.
@@ -68,6 +71,12 @@ struct Layout {
   // islands largest first), so that each island's bodies, entries and rows are
   // contiguous.  The ABI keeps the caller's order; these map internal -> ABI.
   std::vector<int> cperm, jperm, tperm, row_abi;
+  // tet blocks of three rows: a Neo-Hookean tet is one block (kind 0); a
+  // linear tet is two (kind 1: volumetric and two deviatoric normal-strain
+  // modes, kind 2: the three engineering shears); per block (ABI block
+  // order) its record and its first ABI row
+  std::vector<const nsn_tet *> tb_rec;
+  std::vector<int> tb_kind, tb_abi;
   // island-resident CR: per island {c0, nc, j0, nj, b0, nb, e0, ne} (internal
   // order), the eligible islands (rigid bodies, contacts and joints only, at
   // most res_max_rows rows), and the largest eligible island
@@ -107,7 +116,7 @@ struct nsn_ctx {
   bool dirty = true;
   Layout L;
   void *dmem = nullptr;
-  size_t dbytes = 0;
+  size_t dbytes = 0, dcap = 0;   // bytes in use, bytes allocated
   Dev<float> d32;
   Dev<double> d64;
   int *d_bmap = nullptr;
@@ -119,6 +128,7 @@ struct nsn_ctx {
   int last_newton_n = 0;     // Newton loop bodies executed in the last step
   float tune_ms[3] = {0.f, 0.f, 0.f};  // body-pass times measured by the tuner for 4, 8, 16 lanes
   int forced_lanes = 0;      // nsn_set_body_lanes (0: tuned)
+  int tuned_lanes = 0, tuned_nb = -1;   // the tuner's choice and the body count it was made for
   bool linearized = false;
   int lin_buf = 0;           // entry buffer written by the kept linearisation
   int kept_buf = -1;         // entry buffer of the system kept by the last step / linearisation
@@ -127,6 +137,22 @@ struct nsn_ctx {
   int warm_precond = 0;      // 1: the learned start also scales the contacts' Jacobi preconditioner
   MlpState mlp;
   int built_nb = 0;          // bodies present in the current device build
+  // previous-step multipliers across a rebuild of the layout (contacts
+  // regenerated every step, Sec. 10): the contacts of the built scene, and its
+  // joint and tet counts, so that the next build can match them by key
+  std::vector<nsn_contact> built_contacts;
+  int built_nj = 0, built_nt = 0;   // joints and tet blocks (3 rows each) of the built scene
+  // nsn_collide_and_step: the state handed to the collider (13 floats per
+  // body) and its contact buffers (device), with a pinned host copy
+  float *col_state = nullptr;
+  int col_state_nb = 0;
+  int32_t *col_body = nullptr, *col_found = nullptr, *col_found_h = nullptr;
+  float *col_f = nullptr, *col_f_h = nullptr;   // pa, pb, n (9), d, mu (2) per contact
+  int32_t *col_body_h = nullptr;
+  int col_cap = 0;
+  int dlog_iters = 0;        // nsn_record_decisions: Newton iterations logged (0: off)
+  unsigned char *dlog_buf = nullptr;   // the log on the device (iters x (rows + islands) bytes)
+  size_t dlog_bytes = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   std::string err;
   nsn_stats last{};
@@ -182,6 +208,8 @@ void find_islands(const HostScene &S, Layout &L, int nb) {
   for (const auto &r : S.joints) uf_union(par, r.body_a, r.body_b);
   for (const auto &r : S.tets)
     for (int q = 1; q < 4; q++) uf_union(par, r.v[0], r.v[q]);
+  for (const auto &r : S.ltets)
+    for (int q = 1; q < 4; q++) uf_union(par, r.v[0], r.v[q]);
   std::vector<int> id(nb, -1);
   L.body_isl.assign(nb, 0);
   L.ni = 0;
@@ -192,11 +220,13 @@ void find_islands(const HostScene &S, Layout &L, int nb) {
   }
 }
 
-// stable order of n items by key
-std::vector<int> order_by(int n, const std::function<int(int)> &key) {
-  std::vector<int> o(n);
-  for (int i = 0; i < n; i++) o[i] = i;
-  std::stable_sort(o.begin(), o.end(), [&](int a, int b) { return key(a) < key(b); });
+// stable order of n items by an integer key in [0, K) (counting sort: the
+// layout is rebuilt whenever contacts are regenerated, so it stays linear)
+std::vector<int> order_by(int n, int K, const std::function<int(int)> &key) {
+  std::vector<int> k(n), start(size_t(K) + 1, 0), o(n);
+  for (int i = 0; i < n; i++) { k[i] = key(i); start[size_t(k[i]) + 1]++; }
+  for (int j = 0; j < K; j++) start[size_t(j) + 1] += start[j];
+  for (int i = 0; i < n; i++) o[start[k[i]]++] = i;
   return o;
 }
 
@@ -215,26 +245,36 @@ nsn_status build_layout(nsn_ctx *c) {
   std::vector<int> isl_size(L.ni, 0), rank(L.ni);
   for (int b = 0; b < nb; b++) isl_size[L.body_isl[b]]++;
   {
-    std::vector<int> o = order_by(L.ni, [&](int i) { return -isl_size[i]; });
+    const int maxsz = L.ni ? *std::max_element(isl_size.begin(), isl_size.end()) : 0;
+    std::vector<int> o = order_by(L.ni, maxsz + 1, [&](int i) { return maxsz - isl_size[i]; });
     for (int k = 0; k < L.ni; k++) rank[o[k]] = k;
     L.isl_order = o;
   }
   // bodies in island order (rigid and particle numbered separately)
   L.bmap.resize(nb);
-  for (int i : order_by(nb, [&](int b) { return rank[L.body_isl[b]]; })) {
+  for (int i : order_by(nb, std::max(L.ni, 1), [&](int b) { return rank[L.body_isl[b]]; })) {
     if (S.kind[i] == NSN_RIGID) { L.bmap[i] = L.nr++; L.rig_of.push_back(i); }
     else { L.bmap[i] = -2 - L.np++; L.par_of.push_back(i); }
   }
   L.nc = int(S.contacts.size());
   L.nj = int(S.joints.size());
-  L.nt = int(S.tets.size());
   L.Rpair = 3 * L.nc + 5 * L.nj;
+  for (size_t t = 0; t < S.tets.size(); t++) {
+    L.tb_rec.push_back(&S.tets[t]); L.tb_kind.push_back(0); L.tb_abi.push_back(L.Rpair + 3 * int(t));
+  }
+  const int lrow0 = L.Rpair + 3 * int(S.tets.size());
+  for (size_t t = 0; t < S.ltets.size(); t++)
+    for (int h = 0; h < 2; h++) {
+      L.tb_rec.push_back(&S.ltets[t]); L.tb_kind.push_back(1 + h); L.tb_abi.push_back(lrow0 + 6 * int(t) + 3 * h);
+    }
+  L.nt = int(L.tb_rec.size());
   L.R = L.Rpair + 3 * L.nt;
   // constraints in island order
   auto isl2 = [&](int a, int b) { return L.body_isl[a >= 0 ? a : b]; };
-  L.cperm = order_by(L.nc, [&](int i) { return rank[isl2(S.contacts[i].body_a, S.contacts[i].body_b)]; });
-  L.jperm = order_by(L.nj, [&](int i) { return rank[isl2(S.joints[i].body_a, S.joints[i].body_b)]; });
-  L.tperm = order_by(L.nt, [&](int i) { return rank[L.body_isl[S.tets[i].v[0]]]; });
+  const int K = std::max(L.ni, 1);
+  L.cperm = order_by(L.nc, K, [&](int i) { return rank[isl2(S.contacts[i].body_a, S.contacts[i].body_b)]; });
+  L.jperm = order_by(L.nj, K, [&](int i) { return rank[isl2(S.joints[i].body_a, S.joints[i].body_b)]; });
+  L.tperm = order_by(L.nt, K, [&](int i) { return rank[L.body_isl[L.tb_rec[i]->v[0]]]; });
   L.row_abi.resize(L.R);
   L.risl.resize(L.R);
   for (int ci = 0; ci < L.nc; ci++) {
@@ -250,8 +290,8 @@ nsn_status build_layout(nsn_ctx *c) {
   }
   for (int t = 0; t < L.nt; t++)
     for (int k = 0; k < 3; k++) {
-      L.row_abi[L.Rpair + 3 * t + k] = L.Rpair + 3 * L.tperm[t] + k;
-      L.risl[L.Rpair + 3 * t + k] = L.body_isl[S.tets[L.tperm[t]].v[0]];
+      L.row_abi[L.Rpair + 3 * t + k] = L.tb_abi[L.tperm[t]] + k;
+      L.risl[L.Rpair + 3 * t + k] = L.body_isl[L.tb_rec[L.tperm[t]]->v[0]];
     }
   L.bisl_r.resize(L.nr);
   L.bisl_p.resize(L.np);
@@ -278,7 +318,7 @@ nsn_status build_layout(nsn_ctx *c) {
   }
   for (int t = 0; t < L.nt; t++)
     for (int k = 0; k < 3; k++)
-      for (int q = 0; q < 4; q++) sides.push_back({L.Rpair + 3 * t + k, q, L.bmap[S.tets[L.tperm[t]].v[q]]});
+      for (int q = 0; q < 4; q++) sides.push_back({L.Rpair + 3 * t + k, q, L.bmap[L.tb_rec[L.tperm[t]]->v[q]]});
   // counting sort by body: rigid then particle
   std::vector<int> rcnt(L.nr + 1, 0), pcnt(L.np + 1, 0);
   for (auto &s : sides) {
@@ -414,6 +454,8 @@ void carve(Arena &A, Dev<T> &D, const Layout &L, int nb) {
   for (int k = 0; k < 3; k++) { D.jpa[k] = tk(L.nj); D.jpb[k] = tk(L.nj); D.jaxa[k] = tk(L.nj); D.jaxb[k] = tk(L.nj); }
   D.je = tk(L.nj);
   D.tv = A.take<int>(4 * L.nt);
+  D.tkind = A.take<int>(L.nt);
+  D.jkind = A.take<int>(L.nj);
   D.tDmi = tk(9 * L.nt); D.tVe = tk(L.nt); D.tC1 = tk(L.nt); D.tD1 = tk(L.nt); D.talpha = tk(L.nt);
   D.max_blk = device_max_blocks();
   D.part_body = A.take<typename RedT<T>::type>(2 * size_t(D.max_blk));
@@ -438,6 +480,7 @@ void carve(Arena &A, Dev<T> &D, const Layout &L, int nb) {
   D.isl.ls_pre = A.take<int>(ni);
   D.isl.mls = A.take<double>(ni);
   D.isl.rigid = A.take<unsigned char>(ni);
+  D.isl.crk = A.take<int>(ni);
   // line search: du, u and lambda at the head of the Newton iteration, dlambda
   for (int k = 0; k < 6; k++) { D.rdu[k] = tk(L.nr); D.ru0[k] = tk(L.nr); }
   for (int k = 0; k < 3; k++) { D.pdu[k] = tk(L.np); D.pu0[k] = tk(L.np); }
@@ -476,6 +519,7 @@ void fill_sizes(Dev<T> &D, const Layout &L, const nsn_config &cfg) {
   D.isl_on = cfg.island_stop ? 1 : 0;
   D.cone = cfg.cone_project ? 1 : 0;
   D.ls = cfg.line_search ? 1 : 0;
+  D.crM = cfg.cr_iters;
   // grid-stride kernels get at most one wave: SMs x resident blocks per SM of
   // the kernel (so that no partial second wave trails the first)
   int dev = 0, nsm = 152;
@@ -599,14 +643,23 @@ nsn_status upload(nsn_ctx *c, Dev<T> &D) {
       CUDA_TRY(c, put(D.jaxa[k], xa[k])); CUDA_TRY(c, put(D.jaxb[k], xb[k]));
     }
     CUDA_TRY(c, put(D.je, e));
+    std::vector<int> jk(L.nj);
+    for (int i = 0; i < L.nj; i++) jk[i] = L.jperm.empty() ? 0 : S.jkind[L.jperm[i]];
+    CUDA_TRY(c, puti(D.jkind, jk));
   }
   // tets: rest-shape inverse, volume and stable Neo-Hookean constants (App. B):
-  // C1 = mu/2, D1 = lambda/2 (Lame), alpha = 1 + mu/lambda (rest state stress free)
+  // C1 = mu/2, D1 = lambda/2 (Lame), alpha = 1 + mu/lambda (rest state stress
+  // free).  A block of a linear tet (Sec. 9.2.1) holds, in place of (C1, D1,
+  // alpha), the compliances E' = 1 / (V_e k) of its three modes: the isotropic
+  // stiffness of the engineering strains has the eigenvalue 3 lambda + 2 mu on
+  // the volumetric mode, 2 mu on the two deviatoric normal modes and mu on the
+  // three shears, so (V_e K_e)^-1 is diagonal in that basis.
   {
-    std::vector<int> v(4 * L.nt);
+    std::vector<int> v(4 * L.nt), kind(L.nt);
     std::vector<T> Dmi(9 * L.nt), Ve(L.nt), C1(L.nt), D1(L.nt), al(L.nt);
     for (int t = 0; t < L.nt; t++) {
-      const nsn_tet &r = S.tets[L.tperm[t]];
+      const nsn_tet &r = *L.tb_rec[L.tperm[t]];
+      kind[t] = L.tb_kind[L.tperm[t]];
       for (int q = 0; q < 4; q++) v[4 * t + q] = -L.bmap[r.v[q]] - 2;
       double Dm[9];
       for (int row = 0; row < 3; row++)
@@ -622,9 +675,17 @@ nsn_status upload(nsn_ctx *c, Dev<T> &D) {
       Ve[t] = T(std::fabs(det) / 6.0);
       double mu = double(r.E) / (2.0 * (1.0 + double(r.nu)));
       double la = double(r.E) * double(r.nu) / ((1.0 + double(r.nu)) * (1.0 - 2.0 * double(r.nu)));
-      C1[t] = T(0.5 * mu); D1[t] = T(0.5 * la); al[t] = T(1.0 + mu / la);
+      const double V = std::fabs(det) / 6.0;
+      if (kind[t] == 0) {
+        C1[t] = T(0.5 * mu); D1[t] = T(0.5 * la); al[t] = T(1.0 + mu / la);
+      } else if (kind[t] == 1) {
+        C1[t] = T(1.0 / (V * (3.0 * la + 2.0 * mu))); D1[t] = T(1.0 / (V * 2.0 * mu)); al[t] = D1[t];
+      } else {
+        C1[t] = T(1.0 / (V * mu)); D1[t] = C1[t]; al[t] = C1[t];
+      }
     }
     CUDA_TRY(c, puti(D.tv, v));
+    CUDA_TRY(c, puti(D.tkind, kind));
     CUDA_TRY(c, put(D.tDmi, Dmi)); CUDA_TRY(c, put(D.tVe, Ve)); CUDA_TRY(c, put(D.tC1, C1));
     CUDA_TRY(c, put(D.tD1, D1)); CUDA_TRY(c, put(D.talpha, al));
   }
@@ -980,6 +1041,12 @@ template <typename T>
 nsn_status tune_body(nsn_ctx *c, Dev<T> &D) {
   const Layout &L = c->L;
   cudaStream_t st = c->stream;
+  if (!c->forced_lanes && c->tuned_lanes && c->tuned_nb == L.nr + L.np && L.R >= 100000) {
+    // rebuilt for new contacts: same bodies, same tile (and the times measured for it)
+    D.G = c->tuned_lanes;
+    fill_sizes(D, L, c->cfg);
+    return NSN_OK;
+  }
   c->tune_ms[0] = c->tune_ms[1] = c->tune_ms[2] = 0.f;
   if (c->forced_lanes) {
     D.G = c->forced_lanes;
@@ -1017,6 +1084,8 @@ nsn_status tune_body(nsn_ctx *c, Dev<T> &D) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   D.G = best;
+  c->tuned_lanes = best;
+  c->tuned_nb = L.nr + L.np;
   fill_sizes(D, L, c->cfg);
   CUDA_TRY(c, cudaGetLastError());
   return NSN_OK;
@@ -1032,9 +1101,15 @@ nsn_status build_device(nsn_ctx *c) {
   Arena A;
   carve(A, D, L, nb);
   size_t need = A.off + size_t(256) * 4 + sizeof(int) * nb + sizeof(float) * 13 * (nb + 1) + sizeof(T) * 13 * (nb + 1);
-  if (c->dmem) { cudaFree(c->dmem); c->dmem = nullptr; }
-  cudaError_t e = cudaMalloc(&c->dmem, need);
-  if (e != cudaSuccess) return fail(c, NSN_ERR_OUT_OF_MEMORY, "cudaMalloc(%zu): %s", need, cudaGetErrorString(e));
+  // a rebuild (contacts regenerated) reuses the allocation when it still fits;
+  // a new one has 25% of headroom for the next contact sets
+  if (!c->dmem || need > c->dcap) {
+    if (c->dmem) { cudaFree(c->dmem); c->dmem = nullptr; c->dcap = 0; }
+    const size_t cap = need + need / 4;
+    cudaError_t e = cudaMalloc(&c->dmem, cap);
+    if (e != cudaSuccess) return fail(c, NSN_ERR_OUT_OF_MEMORY, "cudaMalloc(%zu): %s", cap, cudaGetErrorString(e));
+    c->dcap = cap;
+  }
   c->dbytes = need;
   A.base = static_cast<char *>(c->dmem);
   A.sizing = false;
@@ -1069,9 +1144,91 @@ nsn_status state_io(nsn_ctx *c, bool set, bool device, const float *ipos, const 
                     const float *ivel, const float *iom, float *opos, float *oquat, float *ovel, float *oom);
 namespace {
 
+// Key of a contact for matching across regenerations: its two bodies and the
+// bit patterns of its body-local point on a (for a generated contact, the
+// vertex: a box corner, or the particle).
+struct ContactKey {
+  int32_t a, b;
+  uint32_t p[3];
+  bool operator==(const ContactKey &o) const {
+    return a == o.a && b == o.b && p[0] == o.p[0] && p[1] == o.p[1] && p[2] == o.p[2];
+  }
+};
+ContactKey contact_key(const nsn_contact &r) {
+  ContactKey k{r.body_a, r.body_b, {0, 0, 0}};
+  std::memcpy(k.p, r.pa, sizeof k.p);
+  return k;
+}
+
+// The previous step's multipliers of the built scene, in ABI row order
+// (empty if there is no built scene), to carry over a rebuild.
+template <typename T>
+nsn_status save_lam_prev(nsn_ctx *c, std::vector<double> &out) {
+  out.clear();
+  const Dev<T> &D = dev<T>(c);
+  const Layout &L = c->L;
+  if (!c->dmem || L.R == 0 || !D.lam_prev) return NSN_OK;
+  std::vector<T> v(L.R);
+  CUDA_TRY(c, cudaMemcpyAsync(v.data(), D.lam_prev, sizeof(T) * L.R, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  out.assign(L.R, 0.0);
+  for (int i = 0; i < L.R; i++) out[L.row_abi[i]] = double(v[i]);
+  return NSN_OK;
+}
+
+// Restores them into the new build: contact rows by key, joint and tet rows
+// by position when their counts did not change.  Rows without a match start
+// from zero (a new contact has no previous-step multiplier).
+template <typename T>
+nsn_status restore_lam_prev(nsn_ctx *c, const std::vector<double> &old, const std::vector<nsn_contact> &old_contacts,
+                            int old_nj, int old_nt) {
+  if (old.empty()) return NSN_OK;
+  Dev<T> &D = dev<T>(c);
+  const Layout &L = c->L;
+  const HostScene &S = c->scene;
+  if (L.R == 0) return NSN_OK;
+  std::vector<double> abi(L.R, 0.0);
+  const int onc = int(old_contacts.size());
+  // the old contacts bucketed by body a + 1 (a = -1: the world), scanned per
+  // new contact: a vertex has few contacts, so this stays linear
+  const int nb = int(S.kind.size());
+  // slot s = body_a + 1; after the fill, slot s holds list[end(s - 1) .. end(s))
+  std::vector<int> end(size_t(nb) + 2, 0), list(onc);
+  for (int i = 0; i < onc; i++) end[size_t(old_contacts[i].body_a) + 2]++;
+  for (int b = 0; b <= nb; b++) end[size_t(b) + 1] += end[b];
+  for (int i = 0; i < onc; i++) list[end[size_t(old_contacts[i].body_a) + 1]++] = i;
+  for (int i = 0; i < L.nc; i++) {
+    const ContactKey k = contact_key(S.contacts[i]);
+    const int sl = k.a + 1;
+    if (sl < 0 || sl > nb) continue;
+    for (int j = sl == 0 ? 0 : end[sl - 1]; j < end[sl]; j++) {
+      const int o = list[j];
+      if (contact_key(old_contacts[o]) == k) {
+        for (int q = 0; q < 3; q++) abi[3 * i + q] = old[3 * size_t(o) + q];
+        break;
+      }
+    }
+  }
+  if (old_nj == L.nj)
+    for (int r = 0; r < 5 * L.nj; r++) abi[3 * L.nc + r] = old[3 * size_t(onc) + r];
+  if (old_nt == L.nt && old_nj == L.nj)
+    for (int r = 0; r < 3 * L.nt; r++) abi[L.Rpair + r] = old[3 * size_t(onc) + 5 * size_t(old_nj) + r];
+  std::vector<T> v(L.R);
+  for (int i = 0; i < L.R; i++) v[i] = T(abi[L.row_abi[i]]);
+  CUDA_TRY(c, cudaMemcpyAsync(D.lam_prev, v.data(), sizeof(T) * L.R, cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return NSN_OK;
+}
+
 nsn_status ensure_built(nsn_ctx *c) {
   if (!c->dirty) return NSN_OK;
   if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
+  std::vector<double> lam_prev_abi;
+  if (c->dmem && c->built_nb > 0) {
+    nsn_status sl = c->cfg.precision == NSN_FP64 ? save_lam_prev<double>(c, lam_prev_abi)
+                                                 : save_lam_prev<float>(c, lam_prev_abi);
+    if (sl != NSN_OK) return sl;
+  }
   // keep the current state of the bodies that already live on the device
   if (c->dmem && c->built_nb > 0) {
     const int nb0 = c->built_nb;
@@ -1089,8 +1246,17 @@ nsn_status ensure_built(nsn_ctx *c) {
   if (s != NSN_OK) return s;
   s = c->cfg.precision == NSN_FP64 ? build_device<double>(c) : build_device<float>(c);
   if (s != NSN_OK) return s;
+  if (!lam_prev_abi.empty() && c->built_nb == int(c->scene.kind.size())) {
+    s = c->cfg.precision == NSN_FP64
+            ? restore_lam_prev<double>(c, lam_prev_abi, c->built_contacts, c->built_nj, c->built_nt)
+            : restore_lam_prev<float>(c, lam_prev_abi, c->built_contacts, c->built_nj, c->built_nt);
+    if (s != NSN_OK) return s;
+  }
   c->dirty = false;
   c->built_nb = int(c->scene.kind.size());
+  c->built_contacts = c->scene.contacts;
+  c->built_nj = int(c->scene.joints.size());
+  c->built_nt = c->L.nt;
   return NSN_OK;
 }
 
@@ -1184,6 +1350,25 @@ nsn_status run_steps(nsn_ctx *c, int nsteps) {
     nsn_status s = mlp_ensure(c, D.nc);
     if (s != NSN_OK) return s;
   }
+  // decision log: sized for the current layout, its pointers captured with the step
+  const size_t dlog_need = size_t(c->dlog_iters) * (size_t(D.R) + 3 * size_t(D.ni));
+  if (c->dlog_iters > 0 && (dlog_need > c->dlog_bytes || !c->dlog_buf)) {
+    if (c->dlog_buf) cudaFree(c->dlog_buf);
+    c->dlog_buf = nullptr;
+    c->dlog_bytes = 0;
+    if (cudaMalloc(&c->dlog_buf, std::max<size_t>(dlog_need, 1)) != cudaSuccess)
+      return fail(c, NSN_ERR_OUT_OF_MEMORY, "decision log of %zu bytes", dlog_need);
+    c->dlog_bytes = dlog_need;
+  }
+  unsigned char *want = c->dlog_iters > 0 ? c->dlog_buf : nullptr;
+  if (D.dlog != want + (want ? 2 * size_t(c->dlog_iters) * D.ni : 0) || D.dlog_iters != c->dlog_iters) {
+    // layout: CR counts (uint16, first for alignment), row codes, island codes
+    D.dlog_cr = want ? reinterpret_cast<unsigned short *>(want) : nullptr;
+    D.dlog = want ? want + 2 * size_t(c->dlog_iters) * D.ni : nullptr;
+    D.dlog_ls = want ? D.dlog + size_t(c->dlog_iters) * D.R : nullptr;
+    D.dlog_iters = want ? c->dlog_iters : 0;
+    if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
+  }
   if (!c->ev0) CUDA_TRY(c, cudaEventCreate(&c->ev0));
   if (!c->ev1) CUDA_TRY(c, cudaEventCreate(&c->ev1));
   CUDA_TRY(c, cudaEventRecord(c->ev0, st));
@@ -1192,9 +1377,13 @@ nsn_status run_steps(nsn_ctx *c, int nsteps) {
       nsn_status s = capture_step<T>(c, D);
       if (s != NSN_OK) return s;
     }
-    for (int s = 0; s < nsteps; s++) CUDA_TRY(c, cudaGraphLaunch(c->graph, st));
+    for (int s = 0; s < nsteps; s++) {
+      if (D.dlog) CUDA_TRY(c, cudaMemsetAsync(D.dlog_cr, 0xff, dlog_need, st));
+      CUDA_TRY(c, cudaGraphLaunch(c->graph, st));
+    }
   } else {
     for (int s = 0; s < nsteps; s++) {
+      if (D.dlog) CUDA_TRY(c, cudaMemsetAsync(D.dlog_cr, 0xff, dlog_need, st));
       Launcher<T> Lr{c, D, st};
       Lr.step();
       c->launches_per_step = Lr.count;
@@ -1701,6 +1890,14 @@ nsn_status nsn_destroy(nsn_ctx *c) {
   if (c->graph) cudaGraphExecDestroy(c->graph);
   if (c->dmem) cudaFree(c->dmem);
   mlp_free(c->mlp);
+  if (c->dlog_buf) cudaFree(c->dlog_buf);
+  if (c->col_state) cudaFree(c->col_state);
+  if (c->col_body) cudaFree(c->col_body);
+  if (c->col_f) cudaFree(c->col_f);
+  if (c->col_found) cudaFree(c->col_found);
+  if (c->col_found_h) cudaFreeHost(c->col_found_h);
+  if (c->col_f_h) cudaFreeHost(c->col_f_h);
+  if (c->col_body_h) cudaFreeHost(c->col_body_h);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
   if (c->own_stream) cudaStreamDestroy(c->stream);
@@ -1762,9 +1959,10 @@ nsn_status nsn_add_constraints(nsn_ctx *c, int32_t type, int32_t n, const void *
     // after this call must keep 3 nc + 5 nj + 3 nt rows and 2 (3 nc + 5 nj) +
     // 12 nt entries below 2^31 (checked in int64 before anything is stored)
     const int64_t nc = int64_t(S.contacts.size()) + (type == NSN_CONTACT ? n : 0);
-    const int64_t nj = int64_t(S.joints.size()) + (type == NSN_REVOLUTE ? n : 0);
+    const int64_t nj = int64_t(S.joints.size()) + (type == NSN_REVOLUTE || type == NSN_PRISMATIC ? n : 0);
     const int64_t nt = int64_t(S.tets.size()) + (type == NSN_TET_NH ? n : 0);
-    const int64_t rows = 3 * nc + 5 * nj + 3 * nt, entries = 2 * (3 * nc + 5 * nj) + 12 * nt;
+    const int64_t nl = int64_t(S.ltets.size()) + (type == NSN_TET_LINEAR ? n : 0);
+    const int64_t rows = 3 * nc + 5 * nj + 3 * nt + 6 * nl, entries = 2 * (3 * nc + 5 * nj) + 12 * nt + 24 * nl;
     if (rows > INT32_MAX || entries > INT32_MAX)
       return fail(c, NSN_ERR_INVALID_ARG,
                   "add_constraints: the scene would hold %lld rows and %lld Jacobian entries (limit 2^31 - 1)",
@@ -1783,18 +1981,27 @@ nsn_status nsn_add_constraints(nsn_ctx *c, int32_t type, int32_t n, const void *
     }
     if (first_row) *first_row = 3 * int32_t(S.contacts.size());
     S.contacts.insert(S.contacts.end(), r, r + n);
-  } else if (type == NSN_REVOLUTE) {
+  } else if (type == NSN_REVOLUTE || type == NSN_PRISMATIC) {
     const nsn_revolute *r = static_cast<const nsn_revolute *>(records);
     for (int i = 0; i < n; i++) {
       int a = r[i].body_a, b = r[i].body_b;
       if (!body_ok(a) || !body_ok(b) || (a < 0 && b < 0) || a == b) return fail(c, NSN_ERR_INVALID_ARG, "joint %d: bad body ids", i);
       if ((a >= 0 && S.kind[a] != NSN_RIGID) || (b >= 0 && S.kind[b] != NSN_RIGID))
-        return fail(c, NSN_ERR_INVALID_ARG, "joint %d: revolute joints connect rigid bodies", i);
+        return fail(c, NSN_ERR_INVALID_ARG, "joint %d: joints connect rigid bodies", i);
       if (!(r[i].compliance >= 0.f)) return fail(c, NSN_ERR_INVALID_ARG, "joint %d: compliance < 0", i);
+      if (type == NSN_PRISMATIC) {
+        const double la = double(r[i].axis_a[0]) * r[i].axis_a[0] + double(r[i].axis_a[1]) * r[i].axis_a[1] +
+                          double(r[i].axis_a[2]) * r[i].axis_a[2];
+        const double lb = double(r[i].axis_b[0]) * r[i].axis_b[0] + double(r[i].axis_b[1]) * r[i].axis_b[1] +
+                          double(r[i].axis_b[2]) * r[i].axis_b[2];
+        if (!(la > 1e-12) || !(lb > 1e-12) || !finite_all(r[i].axis_a, 3) || !finite_all(r[i].axis_b, 3))
+          return fail(c, NSN_ERR_INVALID_ARG, "joint %d: prismatic axes must be nonzero", i);
+      }
     }
     if (first_row) *first_row = 5 * int32_t(S.joints.size());
     S.joints.insert(S.joints.end(), r, r + n);
-  } else if (type == NSN_TET_NH) {
+    S.jkind.insert(S.jkind.end(), size_t(n), type == NSN_PRISMATIC ? 1 : 0);
+  } else if (type == NSN_TET_NH || type == NSN_TET_LINEAR) {
     const nsn_tet *r = static_cast<const nsn_tet *>(records);
     for (int i = 0; i < n; i++) {
       for (int q = 0; q < 4; q++) {
@@ -1811,8 +2018,13 @@ nsn_status nsn_add_constraints(nsn_ctx *c, int32_t type, int32_t n, const void *
       if (!(std::fabs(det) > 1e-18)) return fail(c, NSN_ERR_INVALID_ARG, "tet %d: degenerate rest shape", i);
       if (!(r[i].E > 0.f) || !(r[i].nu > 0.f && r[i].nu < 0.5f)) return fail(c, NSN_ERR_INVALID_ARG, "tet %d: bad material", i);
     }
-    if (first_row) *first_row = 3 * int32_t(S.tets.size());
-    S.tets.insert(S.tets.end(), r, r + n);
+    if (type == NSN_TET_NH) {
+      if (first_row) *first_row = 3 * int32_t(S.tets.size());
+      S.tets.insert(S.tets.end(), r, r + n);
+    } else {
+      if (first_row) *first_row = 6 * int32_t(S.ltets.size());
+      S.ltets.insert(S.ltets.end(), r, r + n);
+    }
   } else {
     return fail(c, NSN_ERR_INVALID_ARG, "unknown constraint type %d", type);
   }
@@ -1830,7 +2042,9 @@ nsn_status nsn_clear_contacts(nsn_ctx *c) {
 nsn_status nsn_counts(nsn_ctx *c, int32_t *n_bodies, int32_t *n_rows) {
   if (!c) return NSN_ERR_INVALID_ARG;
   if (n_bodies) *n_bodies = int32_t(c->scene.kind.size());
-  if (n_rows) *n_rows = int32_t(3 * c->scene.contacts.size() + 5 * c->scene.joints.size() + 3 * c->scene.tets.size());
+  if (n_rows)
+    *n_rows = int32_t(3 * c->scene.contacts.size() + 5 * c->scene.joints.size() + 3 * c->scene.tets.size() +
+                      6 * c->scene.ltets.size());
   return NSN_OK;
 }
 
@@ -2052,6 +2266,144 @@ nsn_status nsn_island_stop_copy(nsn_ctx *c, int32_t *dst_device) {
   return NSN_OK;
 }
 
+}  // extern "C"
+
+namespace {
+// v += h g: the unconstrained velocity the collider predicts with (Sec. 10)
+__global__ void k_add_gravity(float *vel, int nb, float gx, float gy, float gz) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nb) return;
+  vel[3 * i] += gx; vel[3 * i + 1] += gy; vel[3 * i + 2] += gz;
+}
+
+nsn_status collide_once(nsn_ctx *c, nsn_collider *col) {
+  const int nb = int(c->scene.kind.size());
+  int32_t info[4];
+  nsn_status s = nsn_collider_info(col, info);
+  if (s != NSN_OK) return fail(c, s, "nsn_collide_and_step: bad collider");
+  if (info[0] != nb) return fail(c, NSN_ERR_INVALID_ARG, "nsn_collide_and_step: the collider has %d bodies, the scene %d", info[0], nb);
+  if ((s = ensure_built(c)) != NSN_OK) return s;
+  cudaStream_t st = c->stream;
+  if (c->col_state_nb != nb) {
+    if (c->col_state) cudaFree(c->col_state);
+    c->col_state = nullptr;
+    c->col_state_nb = 0;
+    CUDA_TRY(c, cudaMalloc(&c->col_state, sizeof(float) * 13 * std::max(nb, 1)));
+    c->col_state_nb = nb;
+  }
+  if (!c->col_found) {
+    CUDA_TRY(c, cudaMalloc(&c->col_found, sizeof(int32_t)));
+    CUDA_TRY(c, cudaMallocHost(&c->col_found_h, sizeof(int32_t)));
+  }
+  float *pos = c->col_state, *quat = pos + 3 * size_t(nb), *vel = pos + 7 * size_t(nb), *om = pos + 10 * size_t(nb);
+  if ((s = state_io(c, false, true, nullptr, nullptr, nullptr, nullptr, pos, quat, vel, om)) != NSN_OK) return s;
+  const float h = float(c->cfg.h);
+  if (nb) k_add_gravity<<<cdiv(nb, 256), 256, 0, st>>>(vel, nb, h * float(c->cfg.gravity[0]), h * float(c->cfg.gravity[1]),
+                                                       h * float(c->cfg.gravity[2]));
+  CUDA_TRY(c, cudaGetLastError());
+  // the collider works on its own stream: the state export must be complete
+  CUDA_TRY(c, cudaStreamSynchronize(st));
+  cudaStream_t cs = nsn_collider_stream_of(col);
+  for (int attempt = 0; attempt < 2; attempt++) {
+    if (c->col_cap == 0) {
+      const int cap = std::max(1024, int(c->scene.contacts.size()) + int(c->scene.contacts.size()) / 4);
+      CUDA_TRY(c, cudaMalloc(&c->col_body, sizeof(int32_t) * 2 * size_t(cap)));
+      CUDA_TRY(c, cudaMalloc(&c->col_f, sizeof(float) * 11 * size_t(cap)));
+      CUDA_TRY(c, cudaMallocHost(&c->col_body_h, sizeof(int32_t) * 2 * size_t(cap)));
+      CUDA_TRY(c, cudaMallocHost(&c->col_f_h, sizeof(float) * 11 * size_t(cap)));
+      c->col_cap = cap;
+    }
+    const size_t cap = size_t(c->col_cap);
+    float *pa = c->col_f, *pb = pa + 3 * cap, *n = pa + 6 * cap, *d = pa + 9 * cap, *mu = pa + 10 * cap;
+    s = nsn_collider_run_async(col, pos, quat, vel, om, c->col_cap, c->col_body, pa, pb, n, d, mu, c->col_found);
+    if (s != NSN_OK) return fail(c, s, "nsn_collide_and_step: %s", nsn_collider_last_error(col));
+    CUDA_TRY(c, cudaMemcpyAsync(c->col_found_h, c->col_found, sizeof(int32_t), cudaMemcpyDeviceToHost, cs));
+    CUDA_TRY(c, cudaStreamSynchronize(cs));
+    const int found = *c->col_found_h;
+    if (found > c->col_cap) {   // grow and run again
+      cudaFree(c->col_body); cudaFree(c->col_f); cudaFreeHost(c->col_body_h); cudaFreeHost(c->col_f_h);
+      c->col_body = nullptr; c->col_f = nullptr; c->col_body_h = nullptr; c->col_f_h = nullptr;
+      c->col_cap = 0;
+      const int cap2 = found + found / 4 + 1024;
+      CUDA_TRY(c, cudaMalloc(&c->col_body, sizeof(int32_t) * 2 * size_t(cap2)));
+      CUDA_TRY(c, cudaMalloc(&c->col_f, sizeof(float) * 11 * size_t(cap2)));
+      CUDA_TRY(c, cudaMallocHost(&c->col_body_h, sizeof(int32_t) * 2 * size_t(cap2)));
+      CUDA_TRY(c, cudaMallocHost(&c->col_f_h, sizeof(float) * 11 * size_t(cap2)));
+      c->col_cap = cap2;
+      continue;
+    }
+    CUDA_TRY(c, cudaMemcpyAsync(c->col_body_h, c->col_body, sizeof(int32_t) * 2 * size_t(found), cudaMemcpyDeviceToHost, cs));
+    const float *src[5] = {pa, pb, n, d, mu};
+    const size_t w[5] = {3, 3, 3, 1, 1}, o[5] = {0, 3 * cap, 6 * cap, 9 * cap, 10 * cap};
+    for (int k = 0; k < 5; k++)
+      CUDA_TRY(c, cudaMemcpyAsync(c->col_f_h + o[k], src[k], sizeof(float) * w[k] * size_t(found), cudaMemcpyDeviceToHost, cs));
+    CUDA_TRY(c, cudaStreamSynchronize(cs));
+    std::vector<nsn_contact> rec(found);
+    const float *hf = c->col_f_h;
+    for (int i = 0; i < found; i++) {
+      nsn_contact &r = rec[i];
+      r.body_a = c->col_body_h[2 * i];
+      r.body_b = c->col_body_h[2 * i + 1];
+      for (int k = 0; k < 3; k++) { r.pa[k] = hf[3 * i + k]; r.pb[k] = hf[3 * cap + 3 * i + k]; r.n[k] = hf[6 * cap + 3 * i + k]; }
+      r.d = hf[9 * cap + i];
+      r.mu = hf[10 * cap + i];
+    }
+    c->scene.contacts.swap(rec);
+    c->dirty = true;
+    return NSN_OK;
+  }
+  return fail(c, NSN_ERR_OUT_OF_MEMORY, "nsn_collide_and_step: contact buffer");
+}
+}  // namespace
+
+extern "C" {
+
+nsn_status nsn_collide_and_step(nsn_ctx *c, nsn_collider *col, int32_t nsteps, nsn_stats *stats) {
+  if (!c || !col || nsteps < 0) return NSN_ERR_INVALID_ARG;
+  for (int k = 0; k < nsteps; k++) {
+    nsn_status s = collide_once(c, col);
+    if (s != NSN_OK) return s;
+    if ((s = nsn_step(c, 1, stats)) != NSN_OK) return s;
+  }
+  return NSN_OK;
+}
+
+nsn_status nsn_get_prev_lambda(nsn_ctx *c, double *lambda) {
+  if (!c || !lambda) return NSN_ERR_INVALID_ARG;
+  nsn_status s = ensure_built(c);
+  if (s != NSN_OK) return s;
+  std::vector<double> v;
+  s = c->cfg.precision == NSN_FP64 ? save_lam_prev<double>(c, v) : save_lam_prev<float>(c, v);
+  if (s != NSN_OK) return s;
+  if (v.empty()) v.assign(c->L.R, 0.0);
+  std::copy(v.begin(), v.end(), lambda);
+  return NSN_OK;
+}
+
+nsn_status nsn_record_decisions(nsn_ctx *c, int32_t iters) {
+  if (!c || iters < 0 || iters > 100000) return NSN_ERR_INVALID_ARG;
+  c->dlog_iters = iters;
+  return NSN_OK;
+}
+
+nsn_status nsn_get_decisions(nsn_ctx *c, uint8_t *rows, uint8_t *islands, uint16_t *cr) {
+  if (!c) return NSN_ERR_INVALID_ARG;
+  if (c->dlog_iters <= 0 || !c->dlog_buf || c->dirty)
+    return fail(c, NSN_ERR_BAD_STATE, "nsn_get_decisions: no logged step (nsn_record_decisions, then nsn_step)");
+  const Layout &L = c->L;
+  const int it = c->dlog_iters, R = L.R, ni = L.ni;
+  std::vector<uint8_t> h(size_t(it) * (size_t(R) + 3 * size_t(ni)));
+  CUDA_TRY(c, cudaMemcpyAsync(h.data(), c->dlog_buf, h.size(), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  const size_t o_rows = 2 * size_t(it) * ni, o_isl = o_rows + size_t(it) * R;
+  if (cr) std::memcpy(cr, h.data(), 2 * size_t(it) * ni);
+  if (rows)
+    for (int n = 0; n < it; n++)
+      for (int i = 0; i < R; i++) rows[size_t(n) * R + L.row_abi[i]] = h[o_rows + size_t(n) * R + i];
+  if (islands) std::copy(h.begin() + o_isl, h.end(), islands);
+  return NSN_OK;
+}
+
 nsn_status nsn_island_stop_device(nsn_ctx *c, const int32_t **stopped_at) {
   if (!c || !stopped_at) return NSN_ERR_INVALID_ARG;
   nsn_status s = ensure_built(c);
@@ -2172,7 +2524,8 @@ nsn_status nsn_set_body_lanes(nsn_ctx *c, int32_t lanes) {
   if (!c || (lanes != 0 && lanes != 4 && lanes != 8 && lanes != 16)) return NSN_ERR_INVALID_ARG;
   if (lanes != c->forced_lanes) {
     c->forced_lanes = lanes;
-    c->dirty = true;   // rebuilt (state kept) before the next use
+    c->tuned_lanes = 0;   // lanes = 0: tune again
+    c->dirty = true;      // rebuilt (state kept) before the next use
   }
   return NSN_OK;
 }

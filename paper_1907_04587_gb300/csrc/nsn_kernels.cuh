@@ -98,6 +98,7 @@ struct IslState {
   int *ls_pre;
   double *mls;
   unsigned char *rigid;
+  int *crk;                  // CR updates the island took in this Newton iteration
 };
 
 // FP64 scalars kept on the device
@@ -168,9 +169,12 @@ struct Dev {
   // joints
   int *jba, *jbb;
   T *jpa[3], *jpb[3], *jaxa[3], *jaxb[3], *je;
-  // tets
-  int *tv;
+  // tets: blocks of three rows (kind 0 stable Neo-Hookean; a linear tet is two
+  // blocks, kind 1 its normal-strain modes, kind 2 its shears, with the three
+  // mode compliances in place of C1, D1, alpha)
+  int *tv, *tkind;
   T *tDmi, *tVe, *tC1, *tD1, *talpha;
+  int *jkind;        // per joint: 0 revolute, 1 prismatic
   // reductions
   typename RedT<T>::type *part_body;   // one per body-pass block
   typename RedT<T>::type *part_row;    // NPART per row-pass block
@@ -224,6 +228,13 @@ struct Dev {
   int streamed;      // 1: some island needs the streamed CR loop (else it is not launched)
   // conditional handles of the captured Newton / CR WHILE nodes (0: none)
   cudaGraphConditionalHandle hN, hC;
+  // decision log (nsn_record_decisions; null: off): per Newton iteration n <
+  // dlog_iters one code per internal row (dlog[n R + row]) and per island
+  // (dlog_ls[n ni + island]); the codes are those of the oracle's log
+  unsigned char *dlog, *dlog_ls;
+  unsigned short *dlog_cr;   // CR updates per island per Newton iteration
+  int dlog_iters;
+  int crM;                   // CR cap M of a Newton iteration (nsn_config.cr_iters)
 };
 
 // ------------------------------------------------------------------------------------
@@ -270,6 +281,13 @@ template <typename T>
 __device__ __forceinline__ T dsqrt(T v) { return sqrt(v); }
 template <>
 __device__ __forceinline__ float dsqrt<float>(float v) { return sqrtf(v); }
+// |(a, b)|: in FP32 without forming a^2 + b^2, which underflows to subnormal
+// values for components below ~1e-19 (e.g. the friction impulses of a
+// separating contact); FP64 has the range and keeps the plain form
+template <typename T>
+__device__ __forceinline__ T dnorm2(T a, T b) { return sqrt(a * a + b * b); }
+template <>
+__device__ __forceinline__ float dnorm2<float>(float a, float b) { return hypotf(a, b); }
 
 template <typename T>
 __device__ __forceinline__ void quat_R(const T *q, T *R) {
@@ -726,7 +744,7 @@ __device__ __forceinline__ bool w_fb(T vt, T lf, T mu_ln, T r, T &W) {
   if (vt == T(0) && bb >= T(0)) { W = T(0); return true; }
   const T lnum = T(2) * vt * mu_ln + r * lf * (T(2) * mu_ln - lf);
   if (!(lnum > T(0))) return false;
-  const T S = dsqrt(vt * vt + r * r * bb * bb);
+  const T S = dnorm2(vt, r * bb);
   const T vnext = bb >= T(0) ? vt * vt / (S + r * bb) : S - r * bb;
   W = vnext * (vt + r * mu_ln + S) / lnum;
   return true;
@@ -750,10 +768,22 @@ __device__ __forceinline__ T w_min(T vt, T lf, T mu_ln, T r) {
   return (vt - bb) / mu_ln;
 }
 
+// Slot of the decision log written by an evaluation: the Newton iteration of
+// the iterate it evaluates (a line-search trial evaluates the next one), -1
+// when the log is off or for forced evaluations (warm-start candidates, the
+// final merit) that the Newton loop does not take decisions from.
+template <typename T>
+__device__ __forceinline__ int dlog_slot(const Dev<T> &D, int buf, int force) {
+  if (!D.dlog || force || (buf != IT_DEV && buf != IT_DEV_NEXT)) return -1;
+  const int n = D.fl->newton_n + (buf == IT_DEV_NEXT ? 1 : 0);
+  return n < D.dlog_iters ? n : -1;
+}
+
 template <typename T>
 __global__ void k_eval_contacts(Dev<T> D, int buf, int force) {
   if (ls_idle(D)) return;
   if (!force && D.fl->newton_stop) return;
+  const int slot = dlog_slot(D, buf, force);
   if (buf == IT_DEV) buf = D.fl->newton_n & 1;
   else if (buf == IT_DEV_NEXT) buf = (D.fl->newton_n + 1) & 1;
   int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -785,7 +815,7 @@ __global__ void k_eval_contacts(Dev<T> D, int buf, int force) {
   } else {
     // r-scaled Fischer-Burmeister (App. A.1), subgradient alpha(0,0)=0, beta=1
     T rl = rN * ln;
-    T rho = dsqrt(Cn * Cn + rl * rl);
+    T rho = dnorm2(Cn, rl);
     phi = Cn + rl - rho;
     if (rho == T(0)) { al = T(0); S = rN; }
     else { al = T(1) - Cn / rho; S = (T(1) - rl / rho) * rN; }
@@ -810,8 +840,8 @@ __global__ void k_eval_contacts(Dev<T> D, int buf, int force) {
   else if (D.rscale == 2) rF = h * T(0.5) * dq;
   T mu_ln = D.cmu[c] * ln;
   T lf[2] = {D.lam[row + 1], D.lam[row + 2]};
-  T vn = dsqrt(vt[0] * vt[0] + vt[1] * vt[1]);
-  T lfn = dsqrt(lf[0] * lf[0] + lf[1] * lf[1]);
+  T vn = dnorm2(vt[0], vt[1]);
+  T lfn = dnorm2(lf[0], lf[1]);
   T W = T(1);
   bool active;
   if (D.ncp == 1) {
@@ -824,6 +854,15 @@ __global__ void k_eval_contacts(Dev<T> D, int buf, int force) {
   // already drives lambda_f to zero: the inactive form, without the value that
   // overflows FP32 (W = inf gives P = 0 and 0/0 in the CR products)
   if (active && !(W <= T(1e30))) active = false;
+  if (slot >= 0) {
+    // normal row: the FB kink (C = lambda = 0) or the min-map branch C <= r lambda;
+    // friction: 0 inactive (mu lambda_n <= 0), 1 inactive past the asymptote, 2 stick, 3 sliding
+    unsigned char *Lg = D.dlog + size_t(slot) * D.R + row;
+    Lg[0] = D.ncp == 1 ? (Cn <= rN * ln) : (Cn == T(0) && ln == T(0));
+    const unsigned char fc = !(mu_ln > T(0)) ? 0 : (!active ? 1 : (W == T(0) ? 2 : 3));
+    Lg[1] = fc;
+    Lg[2] = fc;
+  }
   if (active) {
     for (int k = 0; k < 2; k++) {
       write_entry(D, D.re0[row + 1 + k], Da[k], buf);
@@ -845,10 +884,91 @@ __global__ void k_eval_contacts(Dev<T> D, int buf, int force) {
 
 // revolute joint: 3 positional rows (anchor coincidence) + 2 angular rows
 // a_w . b_k = 0 with b_1, b_2 perpendicular to b's hinge axis.
+// Prismatic joint rows (the paper's Fetch scenes have prismatic joints; their
+// functions are not given): with t_1, t_2 the orthonormal basis of b's
+// normalised axis (turning with b) and a_w, n_a a's normalised axis and the
+// first basis vector of it (turning with a),
+//   rows 0, 1  t_k . (p_a - p_b): a's anchor stays on b's line; the row acts
+//              at p_a on both bodies (b's lever arm is p_a - x_b, since t_k
+//              turns with b)
+//   rows 2, 3  a_w . t_k: a's axis stays along b's;  row 4  n_a . t_2: no twist
+// with C = e / h^2 and h = (c + e lambda) / h.  Rows in the bulk type,
+// values in FP64 (rot_iter_f64), as for revolute joints.
+template <typename T>
+__device__ void eval_prismatic(const Dev<T> &D, int ea, int eb, const T *pa, const T *pb, const T *axa_in,
+                               const T *axb_in, const Side<T> &A, const Side<T> &B, T e, int base, int buf) {
+  const T h = D.hT;
+  double axad[3], axbd[3];
+  {
+    const double la = sqrt(double(axa_in[0]) * axa_in[0] + double(axa_in[1]) * axa_in[1] + double(axa_in[2]) * axa_in[2]);
+    const double lb = sqrt(double(axb_in[0]) * axb_in[0] + double(axb_in[1]) * axb_in[1] + double(axb_in[2]) * axb_in[2]);
+    for (int k = 0; k < 3; k++) { axad[k] = double(axa_in[k]) / la; axbd[k] = double(axb_in[k]) / lb; }
+  }
+  const T axa[3] = {T(axad[0]), T(axad[1]), T(axad[2])}, axb[3] = {T(axbd[0]), T(axbd[1]), T(axbd[2])};
+  T tb[2][3], t[2][3];
+  double tbd[2][3], td[2][3];
+  basis(axb, tb[0], tb[1]);
+  basis<double>(axbd, tbd[0], tbd[1]);
+  if (eb >= 0) {
+    T q[4], Rb[9];
+    for (int k = 0; k < 4; k++) q[k] = D.rq[k][eb];
+    quat_R(q, Rb);
+    for (int k = 0; k < 2; k++) { mat3v(Rb, tb[k], t[k]); rot_iter_f64(D, eb, tbd[k], td[k]); }
+  } else {
+    for (int k = 0; k < 2; k++)
+      for (int m = 0; m < 3; m++) { t[k][m] = tb[k][m]; td[k][m] = tbd[k][m]; }
+  }
+  double dd[3];
+  gap_f64(D, ea, pa, eb, pb, dd);
+  Side<T> Bl = B;
+  if (B.kind == 1)
+    for (int k = 0; k < 3; k++) Bl.r[k] = ((A.x0[k] - B.x0[k]) + (A.hu[k] - B.hu[k])) + A.r[k];
+  for (int k = 0; k < 2; k++) {
+    T Ja[6], Jb[6];
+    side_row(A, t[k], T(1), Ja);
+    side_row(Bl, t[k], T(-1), Jb);
+    write_entry(D, D.re0[base + k], Ja, buf);
+    write_entry(D, D.re1[base + k], Jb, buf);
+    const T cb = T(td[k][0] * dd[0] + td[k][1] * dd[1] + td[k][2] * dd[2]);
+    D.cdiag[base + k] = e / (h * h);
+    D.hv[base + k] = (cb + e * D.lam[base + k]) / h;
+  }
+  T nal[3], nbl[3], aw[3], na[3];
+  double nald[3], nbld[3], awd[3], nad[3];
+  basis(axa, nal, nbl);
+  basis<double>(axad, nald, nbld);
+  if (ea >= 0) {
+    T q[4], Ra[9];
+    for (int k = 0; k < 4; k++) q[k] = D.rq[k][ea];
+    quat_R(q, Ra);
+    mat3v(Ra, axa, aw);
+    mat3v(Ra, nal, na);
+    rot_iter_f64(D, ea, axad, awd);
+    rot_iter_f64(D, ea, nald, nad);
+  } else {
+    for (int m = 0; m < 3; m++) { aw[m] = axa[m]; na[m] = nal[m]; awd[m] = axad[m]; nad[m] = nald[m]; }
+  }
+  const T *xs[3] = {aw, aw, na}, *ys[3] = {t[0], t[1], t[1]};
+  const double *xd[3] = {awd, awd, nad}, *yd[3] = {td[0], td[1], td[1]};
+  for (int k = 0; k < 3; k++) {
+    T xy[3];
+    cross3(xs[k], ys[k], xy);
+    const T Ja[6] = {0, 0, 0, xy[0], xy[1], xy[2]};
+    const T Jb[6] = {0, 0, 0, -xy[0], -xy[1], -xy[2]};
+    const int row = base + 2 + k;
+    write_entry(D, D.re0[row], Ja, buf);
+    write_entry(D, D.re1[row], Jb, buf);
+    const T cb = T(xd[k][0] * yd[k][0] + xd[k][1] * yd[k][1] + xd[k][2] * yd[k][2]);
+    D.cdiag[row] = e / (h * h);
+    D.hv[row] = (cb + e * D.lam[row]) / h;
+  }
+}
+
 template <typename T>
 __global__ void k_eval_joints(Dev<T> D, int buf, int force) {
   if (ls_idle(D)) return;
   if (!force && D.fl->newton_stop) return;
+  const int slot = dlog_slot(D, buf, force);
   if (buf == IT_DEV) buf = D.fl->newton_n & 1;
   else if (buf == IT_DEV_NEXT) buf = (D.fl->newton_n + 1) & 1;
   int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -865,6 +985,12 @@ __global__ void k_eval_joints(Dev<T> D, int buf, int force) {
   load_side(D, eb, pb, B);
   const T e = D.je[j];
   const int base = 3 * D.nc + 5 * j;
+  if (slot >= 0)
+    for (int k = 0; k < 5; k++) D.dlog[size_t(slot) * D.R + base + k] = 0;   // joints take no decision
+  if (D.jkind[j] == 1) {
+    eval_prismatic(D, ea, eb, pa, pb, axa, axb, A, B, e, base, buf);
+    return;
+  }
   double dd[3];
   gap_f64(D, ea, pa, eb, pb, dd);
   for (int k = 0; k < 3; k++) {
@@ -923,6 +1049,7 @@ template <typename T>
 __global__ void k_eval_tets(Dev<T> D, int buf, int force) {
   if (ls_idle(D)) return;
   if (!force && D.fl->newton_stop) return;
+  const int slot = dlog_slot(D, buf, force);
   if (buf == IT_DEV) buf = D.fl->newton_n & 1;
   else if (buf == IT_DEV_NEXT) buf = (D.fl->newton_n + 1) & 1;
   int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -943,6 +1070,48 @@ __global__ void k_eval_tets(Dev<T> D, int buf, int force) {
   T F[9];
   for (int r = 0; r < 3; r++)
     for (int k = 0; k < 3; k++) F[3 * r + k] = Ds[3 * r] * Dmi[k] + Ds[3 * r + 1] * Dmi[3 + k] + Ds[3 * r + 2] * Dmi[6 + k];
+  if (D.tkind[t] != 0) {
+    // a block of a linear tet (Sec. 9.2.1): the small strain e = (F + F^T)/2 - I
+    // (engineering shears), its modes m (kind 1: volumetric and two deviatoric
+    // normal-strain modes; kind 2: the shears) with constant rows dm/dx and
+    // diagonal compliance E' (tC1, tD1, talpha): h = (m + E' lambda) / h,
+    // C = E' / h^2 -- the Neo-Hookean pattern with V_e K_e diagonal
+    const int kind = D.tkind[t];
+    const T e6[6] = {F[0] - T(1), F[4] - T(1), F[8] - T(1), F[5] + F[7], F[2] + F[6], F[1] + F[3]};
+    T w[4][3];
+    for (int b2 = 0; b2 < 3; b2++) {
+      w[0][b2] = -(Dmi[b2] + Dmi[3 + b2] + Dmi[6 + b2]);
+      for (int q = 1; q < 4; q++) w[q][b2] = Dmi[3 * (q - 1) + b2];
+    }
+    const T r3 = T(0.57735026918962576), r2 = T(0.70710678118654752), r6 = T(0.40824829046386302);
+    const T Qn[3][3] = {{r3, r2, r6}, {r3, -r2, r6}, {r3, T(0), T(-2) * r6}};   // Qn[component][mode]
+    const int IA[3] = {1, 0, 0}, IB[3] = {2, 2, 1};                          // shears yz, xz, xy
+    const T Ep[3] = {D.tC1[t], D.tD1[t], D.talpha[t]};
+    const int base = 3 * D.nc + 5 * D.nj + 3 * t;
+    const T ih2 = T(1) / (h * h);
+    for (int k = 0; k < 3; k++) {
+      T m = T(0);
+      for (int q = 0; q < 4; q++) {
+        T J6[6] = {0, 0, 0, 0, 0, 0};
+        if (kind == 1) {
+          for (int c = 0; c < 3; c++) J6[c] = Qn[c][k] * w[q][c];
+        } else {
+          J6[IA[k]] = w[q][IB[k]];
+          J6[IB[k]] = w[q][IA[k]];
+        }
+        write_entry(D, D.te[12 * t + 4 * k + q], J6, buf);
+      }
+      if (kind == 1) m = Qn[0][k] * e6[0] + Qn[1][k] * e6[1] + Qn[2][k] * e6[2];
+      else m = e6[3 + k];
+      D.hv[base + k] = (m + Ep[k] * D.lam[base + k]) / h;
+      D.cdiag[base + k] = Ep[k] * ih2;
+      if (slot >= 0) D.dlog[size_t(slot) * D.R + base + k] = 0;
+    }
+    T *c3 = D.c3 + 6 * t;
+    c3[0] = Ep[0] * ih2; c3[1] = Ep[1] * ih2; c3[2] = Ep[2] * ih2;
+    c3[3] = T(0); c3[4] = T(0); c3[5] = T(0);
+    return;
+  }
   T U[9], s[3], V[9];
   svd3(F, U, s, V);
   const T Ve = D.tVe[t], C1 = D.tC1[t], D1 = D.tD1[t], alpha = D.talpha[t];
@@ -961,7 +1130,13 @@ __global__ void k_eval_tets(Dev<T> D, int buf, int force) {
   T w[3], Q[9], E[9];
   eig_sym3(N, w, Q);
   const T fl = T(1e-6) * C1 * Ve;
-  for (int k = 0; k < 3; k++) w[k] = T(1) / (w[k] < fl ? fl : w[k]);
+  unsigned char tcode = s[2] < T(0) ? 4 : 0;   // inverted, plus the number of clamped eigenvalues
+  for (int k = 0; k < 3; k++) {
+    tcode += w[k] < fl;
+    w[k] = T(1) / (w[k] < fl ? fl : w[k]);
+  }
+  if (slot >= 0)
+    for (int k = 0; k < 3; k++) D.dlog[size_t(slot) * D.R + 3 * D.nc + 5 * D.nj + 3 * t + k] = tcode;
   for (int r = 0; r < 3; r++)
     for (int q = 0; q < 3; q++) E[3 * r + q] = Q[3 * r] * Q[3 * q] * w[0] + Q[3 * r + 1] * Q[3 * q + 1] * w[1] + Q[3 * r + 2] * Q[3 * q + 2] * w[2];
   const int base = 3 * D.nc + 5 * D.nj + 3 * t;
@@ -1589,6 +1764,7 @@ __device__ __forceinline__ bool isl_merit_one(const Dev<T> &D, int i, int n, int
   D.isl.res0[i] = r0;
   const bool cont = st < 0 && r0 != 0.0;
   D.isl.crdone[i] = cont ? 0 : 1;
+  D.isl.crk[i] = cont ? D.crM : 0;   // the cap, unless a CR stop test ends the island's CR earlier
   active |= st < 0;
   return cont;
 }
@@ -1895,7 +2071,7 @@ __global__ void k_cr_scalars_isl(Dev<T> D) {
       }
     }
     if (!(apap > 0.0)) st = 1;
-    if (st) { D.isl.crdone[i] = 1; continue; }
+    if (st) { D.isl.crdone[i] = 1; D.isl.crk[i] = k; continue; }
     D.isl.rho[size_t(k & 1) * ni + i] = rho;
     const double alpha = rho / apap;
     D.isl.alpha[i] = alpha; D.isl.beta[i] = beta;
@@ -2316,6 +2492,7 @@ __global__ void __launch_bounds__(RES_THREADS) k_cr_resident(Dev<T> D, int M) {
     // islands that ran to the cap
     if (tid < nisl && S.act[tid]) S.kdone[tid] = k;
     __syncthreads();
+    if (tid < nisl && D.resact[D.gisl[i0 + tid]]) D.isl.crk[D.gisl[i0 + tid]] = S.kdone[tid];
     for (int r = tid; r < nrow; r += RES_THREADS) {
       const int gw = r < ncr_g ? 3 * c0 + r : gc + 5 * j0 + (r - ncr_g);
       D.x[gw] = S.x[r];
@@ -2394,6 +2571,14 @@ __global__ void k_list_reset(Dev<T> D) {
 template <typename T>
 __global__ void k_newton_next(Dev<T> D, int N) {
   Flags *f = D.fl;
+  if (D.dlog && f->newton_live && !f->newton_stop && f->newton_n < D.dlog_iters) {
+    // decision log: CR updates of this Newton iteration per island still iterating
+    unsigned short *Lc = D.dlog_cr + size_t(f->newton_n) * D.ni;
+    for (int i = 0; i < D.ni; i++) {
+      if (D.isl_on && D.isl.stop[i] >= 0) continue;
+      Lc[i] = (unsigned short)(D.isl_on ? D.isl.crk[i] : f->cr_count - f->cr_base);
+    }
+  }
   // CR iterations of this Newton iteration: the streamed loop's or the most
   // an island ran in k_cr_resident, whichever is larger
   if (f->cr_res_max > f->cr_count - f->cr_base) f->cr_count = f->cr_base + f->cr_res_max;
@@ -2465,6 +2650,14 @@ __global__ void k_ls_set(Dev<T> D, T t, int final) {
   const T h = D.hT;
   const int nr = D.nr, np = D.np, nc = D.nc, nrest = D.R - 3 * nc;
   const int n = nr + np + nc + nrest;
+  if (final && D.dlog && D.fl->newton_n < D.dlog_iters) {
+    // accepted trial per island: 0..4 for t = 1 .. 1/16, 5 the damped step, 255 stopped
+    unsigned char *Lg = D.dlog_ls + size_t(D.fl->newton_n) * D.ni;
+    for (int i = i0; i < D.ni; i += stride) {
+      const double a = D.isl_on ? D.isl.tacc[i] : D.sc->ls_t;
+      Lg[i] = (D.isl_on && D.isl.stop[i] >= 0) ? 255 : (a > 0.0 ? (unsigned char)__double2int_rn(-log2(a)) : 5);
+    }
+  }
   for (int j = i0; j < n; j += stride) {
     T tt;
     if (j < nr) {                       // rigid body
@@ -2502,12 +2695,14 @@ __global__ void k_ls_set(Dev<T> D, T t, int final) {
       const int c = j - nr - np, r = 3 * c;
       if (!ls_step(D, D.isl_on ? D.risl[r] : 0, t, final, tt)) continue;
       T l0 = D.lam0[r] + tt * D.xs[r], l1 = D.lam0[r + 1] + tt * D.xs[r + 1], l2 = D.lam0[r + 2] + tt * D.xs[r + 2];
+      unsigned char bits = 0;
       if (D.cone) {
-        if (l0 < T(0)) l0 = T(0);
-        const T lim = D.cmu[c] * l0, f = dsqrt(l1 * l1 + l2 * l2);
-        if (f > lim) { const T sc = lim / f; l1 *= sc; l2 *= sc; }
+        if (l0 < T(0)) { l0 = T(0); bits |= 2; }
+        const T lim = D.cmu[c] * l0, f = dnorm2(l1, l2);
+        if (f > lim) { const T sc = lim / f; l1 *= sc; l2 *= sc; bits |= 4; }
       }
       D.lam[r] = l0; D.lam[r + 1] = l1; D.lam[r + 2] = l2;
+      if (final && D.dlog && D.fl->newton_n < D.dlog_iters) D.dlog[size_t(D.fl->newton_n) * D.R + r] |= bits;
     } else {                            // joint and tet rows
       const int r = 3 * nc + (j - nr - np - nc);
       if (!ls_step(D, D.isl_on ? D.risl[r] : 0, t, final, tt)) continue;
@@ -2535,12 +2730,14 @@ __global__ void k_lambda_update(Dev<T> D) {
       const int r = 3 * j;
       if (D.isl_on && D.isl.stop[D.risl[r]] >= 0) continue;
       T l0 = D.lam[r] + t * D.x[r], l1 = D.lam[r + 1] + t * D.x[r + 1], l2 = D.lam[r + 2] + t * D.x[r + 2];
+      unsigned char bits = 0;
       if (D.cone) {
-        if (l0 < T(0)) l0 = T(0);
-        const T lim = D.cmu[j] * l0, f = dsqrt(l1 * l1 + l2 * l2);
-        if (f > lim) { const T sc = lim / f; l1 *= sc; l2 *= sc; }
+        if (l0 < T(0)) { l0 = T(0); bits |= 2; }
+        const T lim = D.cmu[j] * l0, f = dnorm2(l1, l2);
+        if (f > lim) { const T sc = lim / f; l1 *= sc; l2 *= sc; bits |= 4; }
       }
       D.lam[r] = l0; D.lam[r + 1] = l1; D.lam[r + 2] = l2;
+      if (D.dlog && D.fl->newton_n < D.dlog_iters) D.dlog[size_t(D.fl->newton_n) * D.R + r] |= bits;
     } else {
       const int r = 3 * nc + (j - nc);
       if (D.isl_on && D.isl.stop[D.risl[r]] >= 0) continue;
@@ -2677,7 +2874,7 @@ __global__ void k_warm_from_pred(Dev<T> D, const float *Y, int warm_friction) {
   T f1 = T(0), f2 = T(0);
   if (warm_friction) {
     f1 = T(Y[o + 1]) * ls; f2 = T(Y[o + 2]) * ls;
-    const T lim = D.cmu[c] * ln, fn = dsqrt(f1 * f1 + f2 * f2);
+    const T lim = D.cmu[c] * ln, fn = dnorm2(f1, f2);
     if (fn > lim) { const T s = fn > T(0) ? lim / fn : T(0); f1 *= s; f2 *= s; }
   }
   D.lam[3 * c] = ln;

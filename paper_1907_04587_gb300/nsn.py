@@ -22,7 +22,7 @@ NSN_ERR_INVALID_ARG, NSN_ERR_OUT_OF_MEMORY = 1, 2
 STATUS = {0: "NSN_OK", 1: "NSN_ERR_INVALID_ARG", 2: "NSN_ERR_OUT_OF_MEMORY", 3: "NSN_ERR_CUDA",
           4: "NSN_ERR_NOT_CONVERGED", 5: "NSN_ERR_TIMEOUT", 6: "NSN_ERR_BAD_STATE", 7: "NSN_ERR_NONFINITE"}
 NSN_RIGID, NSN_PARTICLE = 0, 1
-NSN_CONTACT, NSN_REVOLUTE, NSN_TET_NH = 0, 1, 2
+NSN_CONTACT, NSN_REVOLUTE, NSN_TET_NH, NSN_PRISMATIC, NSN_TET_LINEAR = 0, 1, 2, 3, 4
 NSN_FP32, NSN_FP64 = 0, 1
 NSN_WARM_ZERO, NSN_WARM_PREV, NSN_WARM_LEARNED = 0, 1, 2
 NSN_WARM_FRICTION = 0x100
@@ -114,6 +114,9 @@ def lib():
         "nsn_island_stop_device": (C.c_int, [_vp, C.POINTER(_vp)]),
         "nsn_island_stop_copy": (C.c_int, [_vp, _vp]),
         "nsn_clear_warm_start": (C.c_int, [_vp]),
+        "nsn_record_decisions": (C.c_int, [_vp, C.c_int32]),
+        "nsn_get_prev_lambda": (C.c_int, [_vp, _dp]),
+        "nsn_get_decisions": (C.c_int, [_vp, _vp, _vp, _vp]),
         "nsn_tuning": (C.c_int, [_vp, _ip, _fp]),
         "nsn_resident_info": (C.c_int, [_vp, _ip]),
         "nsn_time_resident": (C.c_int, [_vp, C.c_int32, _fp, _dp]),
@@ -126,6 +129,7 @@ def lib():
                                              _vp]),
         "nsn_collider_info": (C.c_int, [_vp, _ip]),
         "nsn_collider_last_error": (C.c_char_p, [_vp]),
+        "nsn_collide_and_step": (C.c_int, [_vp, _vp, C.c_int32, C.POINTER(nsn_stats)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -382,12 +386,28 @@ def revolute_records(s):
     return r
 
 
-def tet_records(s):
-    nt = len(s["t_v"])
+def tet_records(s, pre="t"):
+    nt = len(s.get(f"{pre}_v", ()))
     r = np.zeros(nt, TET_DTYPE)
     if nt:
-        r["v"], r["rest"], r["E"], r["nu"] = s["t_v"], s["t_rest"], s["t_E"], s["t_nu"]
+        r["v"], r["rest"], r["E"], r["nu"] = s[f"{pre}_v"], s[f"{pre}_rest"], s[f"{pre}_E"], s[f"{pre}_nu"]
     return r
+
+
+def joint_runs(s):
+    """The scene's joints as runs of equal kind in scene order: [(type, records)]
+    (added run by run, the ABI joint order is the scene's)."""
+    rec = revolute_records(s)
+    nj = len(rec)
+    kind = np.asarray(s.get("j_kind", np.zeros(nj, np.int32)), np.int32).reshape(-1)
+    runs, i = [], 0
+    while i < nj:
+        j = i
+        while j < nj and kind[j] == kind[i]:
+            j += 1
+        runs.append((NSN_PRISMATIC if kind[i] == 1 else NSN_REVOLUTE, rec[i:j]))
+        i = j
+    return runs
 
 
 DEFAULTS = dict(h=1.0 / 60.0, gravity=(0.0, 0.0, -9.81), newton_iters=4, cr_iters=20, damping=0.75, eps=1e-6,
@@ -433,8 +453,8 @@ class Solver:
         nb = len(s["mass"])
         self.nb = nb
         nsn_add_bodies(self.ctx, s["kind"], s["pos"], s["quat"], s["vel"], s["omega"], s["mass"], s["inertia"])
-        for ctype, rec in ((NSN_CONTACT, contact_records(s)), (NSN_REVOLUTE, revolute_records(s)),
-                           (NSN_TET_NH, tet_records(s))):
+        for ctype, rec in ([(NSN_CONTACT, contact_records(s))] + joint_runs(s) +
+                           [(NSN_TET_NH, tet_records(s)), (NSN_TET_LINEAR, tet_records(s, "l"))]):
             if len(rec):
                 nsn_add_constraints(self.ctx, ctype, rec)
         _, self.R = nsn_counts(self.ctx)
@@ -454,6 +474,16 @@ class Solver:
     def step(self, nsteps=1):
         return nsn_step(self.ctx, nsteps)
 
+    def collide_and_step(self, collider, nsteps=1):
+        """nsteps steps, each after contact generation on the current state
+        (nsn_collide_and_step; `collider` a Collider over the same bodies)."""
+        st = nsn_stats()
+        _check(self.ctx, lib().nsn_collide_and_step(self.ctx, collider.ptr, int(nsteps), C.byref(st)),
+               "nsn_collide_and_step")
+        _, self.R = nsn_counts(self.ctx)
+        return dict(newton_done=st.newton_done, cr_total=st.cr_total, merit0=st.merit0,
+                    merit_final=st.merit_final, ms=st.ms)
+
     def get_state(self):
         return nsn_get_state(self.ctx, self.nb)
 
@@ -472,6 +502,12 @@ class Solver:
 
     def get_lambda(self):
         return nsn_get_lambda(self.ctx, self.R)
+
+    def get_prev_lambda(self):
+        """Multipliers the next warm start reads (carried over contact changes by key)."""
+        out = np.zeros(self.R)
+        _check(self.ctx, lib().nsn_get_prev_lambda(self.ctx, out.ctypes.data_as(_dp)), "nsn_get_prev_lambda")
+        return out
 
     def merit_history(self):
         return nsn_get_merit_history(self.ctx)
@@ -531,6 +567,23 @@ class Solver:
         """Per island of the last step (island_stop = 1): zero-iterate merit,
         final merit, Newton iteration at which it stopped (-1: not stopped)."""
         return nsn_island_stats(self.ctx, self.islands()[0])
+
+    def record_decisions(self, iters):
+        """Log the discrete decisions of the first `iters` Newton iterations of
+        the following steps (nsn_record_decisions; 0 = off)."""
+        _check(self.ctx, lib().nsn_record_decisions(self.ctx, int(iters)), "nsn_record_decisions")
+        self._dlog_iters = int(iters)
+
+    def decisions(self):
+        """(rows: iters x R uint8 in ABI row order, islands: iters x n_islands
+        uint8, cr: iters x n_islands uint16) of the last step (nsn_get_decisions)."""
+        ni = self.islands()[0]
+        rows = np.zeros((self._dlog_iters, self.R), np.uint8)
+        isl = np.zeros((self._dlog_iters, ni), np.uint8)
+        cr = np.zeros((self._dlog_iters, ni), np.uint16)
+        _check(self.ctx, lib().nsn_get_decisions(self.ctx, rows.ctypes.data, isl.ctypes.data, cr.ctypes.data),
+               "nsn_get_decisions")
+        return rows, isl, cr
 
     def time_operator(self, iters=20):
         return nsn_time_operator(self.ctx, iters)

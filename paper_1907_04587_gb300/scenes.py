@@ -8,13 +8,16 @@ float32 so that the FP32 device path and the FP64 oracle see identical values.
 Scene dictionary (numpy arrays):
   kind[nb] (0 rigid, 1 particle), pos[nb,3], quat[nb,4] (w,x,y,z), vel[nb,3],
   omega[nb,3] (world frame), mass[nb], inertia[nb,3] (body-frame principal),
-  env[nb] (environment id, 0 for single scenes), half[nb,3] (box half extents
+  env[nb] (environment id, 0 for single scenes), mu_env[n_envs] (friction of
+  each environment, batched scenes), half[nb,3] (box half extents
   of a rigid body's collision shape; zeros: no shape, and for particles)
   c_body[nc,2] (-1 = static world), c_pa[nc,3], c_pb[nc,3] (body-local, or a
   world point for the world side), c_n[nc,3] (world normal from b to a),
   c_d[nc], c_mu[nc]
-  j_body[nj,2], j_pa[nj,3], j_pb[nj,3], j_axa[nj,3], j_axb[nj,3], j_compliance[nj]
-  t_v[nt,4], t_rest[nt,4,3], t_E[nt], t_nu[nt]
+  j_body[nj,2], j_pa[nj,3], j_pb[nj,3], j_axa[nj,3], j_axb[nj,3], j_compliance[nj],
+  j_kind[nj] (optional: 0 revolute, 1 prismatic)
+  t_v[nt,4], t_rest[nt,4,3], t_E[nt], t_nu[nt]  (stable Neo-Hookean tets)
+  l_v[nl,4], l_rest[nl,4,3], l_E[nl], l_nu[nl]  (optional: linear Hookean tets)
 
 Workloads (the paper's scenes need URDFs and meshes that are not available, so
 these stand in for them):
@@ -68,8 +71,9 @@ class SceneBuilder:
     def __init__(self):
         self.b = {k: [] for k in ("kind", "pos", "quat", "vel", "omega", "mass", "inertia", "env")}
         self.c = {k: [] for k in ("c_body", "c_pa", "c_pb", "c_n", "c_d", "c_mu")}
-        self.j = {k: [] for k in ("j_body", "j_pa", "j_pb", "j_axa", "j_axb", "j_compliance")}
+        self.j = {k: [] for k in ("j_body", "j_pa", "j_pb", "j_axa", "j_axb", "j_compliance", "j_kind")}
         self.t = {k: [] for k in ("t_v", "t_rest", "t_E", "t_nu")}
+        self.l = {k: [] for k in ("l_v", "l_rest", "l_E", "l_nu")}
 
     @property
     def n_bodies(self):
@@ -95,19 +99,31 @@ class SceneBuilder:
     def add_revolute(self, a, b, pa, pb, axa, axb, compliance=0.0):
         self.j["j_body"].append((a, b)); self.j["j_pa"].append(pa); self.j["j_pb"].append(pb)
         self.j["j_axa"].append(axa); self.j["j_axb"].append(axb); self.j["j_compliance"].append(compliance)
+        self.j["j_kind"].append(0)
+
+    def add_prismatic(self, a, b, pa, pb, axa, axb, compliance=0.0):
+        """Slider: a's anchor pa stays on the line through b's anchor pb along
+        b's axis axb, with a's axis axa kept along it and no twist about it."""
+        self.add_revolute(a, b, pa, pb, axa, axb, compliance)
+        self.j["j_kind"][-1] = 1
 
     def add_tet(self, v, rest, E, nu):
         self.t["t_v"].append(v); self.t["t_rest"].append(rest); self.t["t_E"].append(E); self.t["t_nu"].append(nu)
+
+    def add_linear_tet(self, v, rest, E, nu):
+        """Constant-strain tet with a linear Hookean material (Sec. 9.2.1)."""
+        self.l["l_v"].append(v); self.l["l_rest"].append(rest); self.l["l_E"].append(E); self.l["l_nu"].append(nu)
 
     def build(self):
         shapes = dict(kind=(0,), pos=(0, 3), quat=(0, 4), vel=(0, 3), omega=(0, 3), mass=(0,), inertia=(0, 3),
                       env=(0,), c_body=(0, 2), c_pa=(0, 3), c_pb=(0, 3), c_n=(0, 3), c_d=(0,), c_mu=(0,),
                       j_body=(0, 2), j_pa=(0, 3), j_pb=(0, 3), j_axa=(0, 3), j_axb=(0, 3), j_compliance=(0,),
-                      t_v=(0, 4), t_rest=(0, 4, 3), t_E=(0,), t_nu=(0,))
+                      j_kind=(0,), t_v=(0, 4), t_rest=(0, 4, 3), t_E=(0,), t_nu=(0,),
+                      l_v=(0, 4), l_rest=(0, 4, 3), l_E=(0,), l_nu=(0,))
         out = {}
-        for grp in (self.b, self.c, self.j, self.t):
+        for grp in (self.b, self.c, self.j, self.t, self.l):
             for k, v in grp.items():
-                ints = k in ("kind", "env", "c_body", "j_body", "t_v")
+                ints = k in ("kind", "env", "c_body", "j_body", "j_kind", "t_v", "l_v")
                 dt = np.int32 if ints else np.float64
                 a = np.asarray(v, dtype=dt) if len(v) else np.zeros(shapes[k], dtype=dt)
                 out[k] = a
@@ -407,7 +423,8 @@ def batched_envs(seed=0, n_envs=4096, links=(3, 20), boxes=(0, 64), box_edge=(0.
     half = np.zeros((NB, 3))
     half[li] = L / 2
     half[bi] = edge[:, None] / 2
-    s = dict(kind=kind, pos=pos, quat=quat, vel=vel, omega=omega, mass=mass, inertia=inertia, env=env, half=half)
+    s = dict(kind=kind, pos=pos, quat=quat, vel=vel, omega=omega, mass=mass, inertia=inertia, env=env, half=half,
+             mu_env=mue)
     s.update(joints); s.update(contacts); s.update(_empty_tets())
     return finalize(s)
 
@@ -499,3 +516,45 @@ def mixed_bin(seed=0, n_boxes=2000, n_spheres=8, sphere_radius=0.3, sphere_res=1
     half[:n_boxes] = (edges[:, None] / 2).astype(F32)
     s["half"] = half
     return s
+
+
+# --------------------------------------------------------------------------------------
+# Prismatic and revolute joints with a linear Hookean block (the joint and
+# material types of the paper's Fetch and PneuNet scenes, Sec. 9.2.1, Sec. 10)
+
+def slider_arm_block(seed=0, hexes=2, edge=0.3, E=5e4, nu=0.3, density=1000.0, mu=0.6):
+    """An arm on a horizontal prismatic joint to the world (a 0.2 m cube
+    carriage, 2 kg) carrying two revolute links (0.3 x 0.05 x 0.05 m, 0.5 kg)
+    that start horizontal and swing under gravity, beside a block of
+    hexes^3 x 5 linear Hookean tets resting on the ground (bottom vertices in
+    contact with the plane, rest shape jittered by 1%)."""
+    rng = np.random.default_rng(seed)
+    b = SceneBuilder()
+    u = (1.0, 0.0, 0.0)
+    car = b.add_rigid((0.0, 2.0, 1.0), (1, 0, 0, 0), vel=(rng.uniform(-0.2, 0.2), 0, 0), mass=2.0,
+                      inertia=tuple(box_inertia(2.0, (0.2, 0.2, 0.2))))
+    b.add_prismatic(car, -1, (0, 0, 0), (0.0, 2.0, 1.0), u, u, 0.0)
+    L = np.array([0.3, 0.05, 0.05])
+    I = tuple(box_inertia(0.5, L))
+    l1 = b.add_rigid((0.15, 2.0, 1.0), (1, 0, 0, 0), mass=0.5, inertia=I)
+    b.add_revolute(l1, car, (-0.15, 0, 0), (0.0, 0.0, 0.0), (0, 1, 0), (0, 1, 0), 0.0)
+    l2 = b.add_rigid((0.45, 2.0, 1.0), (1, 0, 0, 0), mass=0.5, inertia=I)
+    b.add_revolute(l2, l1, (-0.15, 0, 0), (0.15, 0, 0), (0, 1, 0), (0, 1, 0), 0.0)
+    n = hexes
+    h = edge / n
+    grid = np.array([(i, j, k) for k in range(n + 1) for j in range(n + 1) for i in range(n + 1)], np.float64) * h
+    X = grid + rng.uniform(-0.01, 0.01, grid.shape) * h
+    X[:, 2] = np.where(grid[:, 2] == 0.0, 0.0, X[:, 2])          # bottom layer on the plane
+    tets = hex_tets(n)
+    vol = np.zeros(len(X))
+    for t in tets:
+        P = X[list(t)]
+        v = abs(np.linalg.det(np.stack([P[1] - P[0], P[2] - P[0], P[3] - P[0]], 1))) / 6
+        vol[list(t)] += v / 4
+    ids = [b.add_particle(tuple(x), mass=density * vol[i]) for i, x in enumerate(X)]
+    for t in tets:
+        b.add_linear_tet(tuple(ids[q] for q in t), tuple(map(tuple, X[list(t)])), E, nu)
+    for i, x in enumerate(X):
+        if x[2] == 0.0:
+            b.add_contact(ids[i], -1, (0, 0, 0), (x[0], x[1], 0.0), (0, 0, 1), 0.0, mu)
+    return b.build()

@@ -12,8 +12,11 @@ norm-wise relative.  What is compared is what the method determines uniquely:
     only their resultant is;
   - per-row impulses h lambda, checked tightly for the FP64 build only.
 The FP64 build of the kernels agrees to rounding amplified by conditioning
-(1e-7); the FP32 production path meets the 1e-5 bound on velocities and body
-impulses at equal Newton/CR iteration counts.
+(1e-7).  FP32 step parity, judged decision by decision, is in
+test_gpu_fp32_decisions.py; here the FP32 linear algebra is bounded by the
+conditioning of the Jacobi-preconditioned Schur matrix: a solve in FP32 is
+accurate to about kappa * 2^-24 (Sec. 11's error estimate), so the bound is
+max(1e-5, 10 kappa 2^-24) with kappa measured on the oracle's dense matrix.
 """
 import numpy as np
 import pytest
@@ -26,11 +29,21 @@ H = 1.0 / 60.0
 TOL64 = 1e-7
 TOL32 = 1e-5
 G = 9.81
-# FP32 CR after M iterations on one linear system, relative error of du: the
-# Krylov recurrences amplify FP32 rounding of the operator by the conditioning
-# of the Jacobi-preconditioned Schur matrix (ill-conditioned by hard joints,
-# stick rows with W = 0 and mass ratios); measured values are reported.
-TOL32_CR = {"cube_stack": 1e-4, "chain_block_small": 1e-3, "batched_small": 1e-3}
+EPS32 = 2.0 ** -24
+
+
+def kappa_jacobi(L):
+    """Condition number of P^(1/2) A P^(1/2), A = J H~^-1 J^T + C + eps I the
+    Schur matrix of Eq. schur_system and P = diag(A)^-1 (Sec. 8.2), from the
+    oracle's dense linearisation."""
+    A = L["J"] @ L["Hinv"] @ L["J"].T + L["C"] + 1e-6 * np.eye(len(L["b"]))
+    d = 1.0 / np.sqrt(np.diag(A))
+    w = np.linalg.eigvalsh(d[:, None] * A * d[None, :])
+    return float(w[-1] / w[0])
+
+
+def tol32_linear(kappa):
+    return max(TOL32, 10.0 * kappa * EPS32)
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -75,13 +88,6 @@ PARAMS = {
 # iterates Newton iteration by Newton iteration (even between two FP64
 # implementations), see test_geometric_stiffness_parity for the shift itself.
 STEP_PARAMS = dict(PARAMS, chain_block_small=dict(newton_iters=10, cr_iters=50, geom_stiffness=0))
-# FP32 production path, per-step errors at equal iteration counts (stated,
-# not hidden): velocity (kinetic-energy norm) and net body impulse.  They are
-# ~1e-5 while every discrete decision of the method (friction activity, the
-# FB kink, the W asymptote) comes out the same as in FP64; on steps where FP32
-# rounding flips one of them the iterates follow another branch and per-step
-# errors up to ~1.5e-3 were measured on these scenes.
-TOL32_STEP = {"cube_stack": 1e-4, "chain_block_small": 3e-3, "batched_small": 3e-3}
 
 
 @pytest.mark.parametrize("name", list(SCENES))
@@ -93,11 +99,17 @@ def test_linear_system_parity(orc, name, prec):
     p = PARAMS[name]
     o = orc.Oracle(s, **p)
     g = nsn.Solver(s, precision=prec, **p)
+    kappa = None
     for n_before in (0, 1):
         L = o.linearize(n_before=n_before)
         g.linearize(n_before)
         sysg = g.system()
-        tol = TOL64 if prec == nsn.NSN_FP64 else (TOL32 if n_before == 0 else 1e-3)
+        if kappa is None:
+            kappa = kappa_jacobi(L)
+        # after one Newton iteration the FP32 iterate carries the error of its
+        # first solve (kappa eps32): the system is linearised at that iterate
+        tol = TOL64 if prec == nsn.NSN_FP64 else (TOL32 if n_before == 0 else tol32_linear(kappa))
+        print(f"{name} prec {prec} n {n_before}: kappa {kappa:.2e} tol {tol:.1e}")
         assert rel(sysg["g"], L["g"]) < tol, ("g", n_before)
         assert rel(sysg["hvec"], L["hvec"]) < tol, ("h", n_before)
         assert rel(sysg["b"], L["b"]) < tol, ("b", n_before)
@@ -124,11 +136,12 @@ def test_cr_solve_parity(orc, name, prec):
     dl_g, du_g = g.solve(M)
     du_o = L["Hinv"] @ (L["J"].T @ dl_o * H - L["g"])
     e_du, e_dl = rel(du_g, du_o), rel(dl_g, dl_o)
-    print(f"{name} prec {prec}: du {e_du:.2e} dl {e_dl:.2e}")
+    kappa = kappa_jacobi(L)
+    print(f"{name} prec {prec}: du {e_du:.2e} dl {e_dl:.2e} kappa {kappa:.2e} bound {tol32_linear(kappa):.1e}")
     if prec == nsn.NSN_FP64:
         assert e_du < 1e-8 and e_dl < 1e-6
     else:
-        assert e_du < TOL32_CR[name]
+        assert e_du < tol32_linear(kappa)
 
 
 def mass_norm(state, s, du_v, du_w):
@@ -172,15 +185,16 @@ def _resync_step(o, g, s, kind):
 
 
 @pytest.mark.parametrize("name", list(SCENES))
-@pytest.mark.parametrize("prec", [nsn.NSN_FP64, nsn.NSN_FP32])
+@pytest.mark.parametrize("prec", [nsn.NSN_FP64])
 def test_step_parity(orc, name, prec):
     """Per-step velocities u+ and impulses h lambda at equal Newton/CR counts,
-    with the state re-synchronised from the oracle before every step."""
+    with the state re-synchronised from the oracle before every step (FP64
+    build; the FP32 path is judged per decision in test_gpu_fp32_decisions)."""
     s = SCENES[name]()
     p = STEP_PARAMS[name]
     o = orc.Oracle(s, **p)
     g = nsn.Solver(s, precision=prec, **p)
-    tol = TOL64 if prec == nsn.NSN_FP64 else TOL32_STEP[name]
+    tol = TOL64
     for step in range(3):
         eu, eb, el, so, sg = _resync_step(o, g, s, s["kind"])
         print(f"{name} prec {prec} step {step}: u {eu:.2e} body impulse {eb:.2e} row impulse {el:.2e} "
@@ -216,7 +230,7 @@ def test_cube_stack_60_steps_fp32(orc):
         eu, eb, el = step_errors(o, g, s["kind"], s)
         print(f"step {step}: u {eu:.2e} body impulse {eb:.2e} row impulse {el:.2e}")
         worst = max(worst, eu, eb)
-    assert worst < TOL32_STEP["cube_stack"], worst
+    assert worst < TOL32, worst
 
 
 def test_geometric_stiffness_parity(orc):

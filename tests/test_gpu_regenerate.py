@@ -1,0 +1,105 @@
+"""Contacts regenerated at every step (Sec. 10: collision detection once per
+time step, candidates from the unconstrained velocity, normals from the
+closest points at the start of the step), through nsn_collide_and_step.
+
+The GPU runs its collider on its own state, replaces its contacts and steps;
+the oracle runs its own collider (the FP32-decision version, which the GPU's
+reproduces bit for bit) and its own step on the same state.  The state is
+re-synchronised from the oracle before every step: a step of a nonsmooth
+iteration that has not converged moves by far more than its inputs' rounding,
+so only per-step comparisons are meaningful.  The previous step's multipliers
+carry over a regeneration by contact key (body pair and the vertex on a)."""
+import numpy as np
+import pytest
+
+from paper_1907_04587_gb300 import nsn, scenes
+
+pytestmark = pytest.mark.gpu
+
+H = 1.0 / 60.0
+GRAV = np.array([0.0, 0.0, -9.81])
+Z = ((0.0, 0.0, 1.0, 0.0),)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def cuda():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    yield
+
+
+def unconstrained_vel32(vel32):
+    """v + h g in FP32, as the context forms it before running its collider."""
+    return (vel32 + np.float32(H) * GRAV.astype(np.float32)).astype(np.float32)
+
+
+def test_previous_multipliers_follow_contacts_by_key():
+    """Replacing the contact set (reordered, one contact dropped, one new):
+    the previous step's multipliers read by the next warm start are the old
+    ones of the same (body pair, point) key, zero for the new contact; joint
+    rows keep theirs."""
+    s = scenes.batched_envs(seed=6, n_envs=3, links=(3, 4), boxes=(4, 8))
+    g = nsn.Solver(s, newton_iters=6, cr_iters=40, tol_rel=1e-6, island_stop=1, cone_project=1)
+    g.set_warm_start(nsn.NSN_WARM_PREV)
+    g.step()
+    lam = g.get_lambda()
+    nc, nj = len(s["c_body"]), len(s["j_body"])
+    rng = np.random.default_rng(1)
+    perm = rng.permutation(nc)[1:]                 # drop one contact, reorder the rest
+    new = dict(s)
+    for k in ("c_body", "c_pa", "c_pb", "c_n", "c_d", "c_mu"):
+        new[k] = np.concatenate([s[k][perm], s[k][perm[:1]]])
+    new["c_pa"] = new["c_pa"].copy()
+    new["c_pa"][-1] = new["c_pa"][-1] * np.float32(0.5)   # a contact at a new point: no match
+    g.set_contacts(new)
+    lp = g.get_prev_lambda()
+    for i, o in enumerate(perm):
+        np.testing.assert_array_equal(lp[3 * i:3 * i + 3], lam[3 * o:3 * o + 3])
+    np.testing.assert_array_equal(lp[3 * (nc - 1):3 * nc], 0.0)
+    np.testing.assert_array_equal(lp[3 * nc:3 * nc + 5 * nj], lam[3 * nc:3 * nc + 5 * nj])
+    g.step()   # the rebuilt context steps
+
+
+def test_collide_and_step_matches_the_oracle_pipeline(orc):
+    """64 batched environments over 10 steps, FP64 build, islands to 1e-6 with
+    the line search: at every step the GPU's regenerated contacts equal the
+    oracle's collider's, and the stepped states agree (islands that converged
+    on both sides within 1e-9, stop iterations equal on 95% of islands)."""
+    s = scenes.batched_envs(seed=3, n_envs=64)
+    prm = dict(newton_iters=12, cr_iters=80, tol_rel=1e-6, island_stop=1, cone_project=1, line_search=1)
+    n_envs = int(s["n_envs"])
+    col = nsn.Collider(s, mu_env=s["mu_env"])
+    g = nsn.Solver(s, precision=nsn.NSN_FP64, **prm)
+    st = {k: s[k].astype(np.float64) for k in ("pos", "quat", "vel", "omega")}
+    for step in range(10):
+        f32 = {k: v.astype(np.float32) for k, v in st.items()}
+        g.set_state(**f32)
+        g.collide_and_step(col, 1)
+        co = orc.collide(s["kind"], f32["pos"], f32["quat"], unconstrained_vel32(f32["vel"]), f32["omega"], s["half"],
+                         s["env"], Z, col.exclude, s["mu_env"], 0.01, H)
+        # the context holds the collider's contacts: same count of rows
+        assert g.R == 3 * len(co["c_body"]) + 5 * len(s["j_body"])
+        cg = col.run(f32["pos"], f32["quat"], unconstrained_vel32(f32["vel"]), f32["omega"])
+        np.testing.assert_array_equal(cg["c_body"], co["c_body"])
+        np.testing.assert_array_equal(cg["c_pa"], co["c_pa"].astype(np.float32))
+        o = orc.Oracle(scenes.finalize({**s, **co}), **prm)
+        o.set_state(**{k: v.astype(np.float64) for k, v in f32.items()})
+        o.step()
+        so, sg = o.get_state(), g.get_state_f64()
+        io, ig = o.island_stats(), g.island_stats()
+        _, bi, _ = o.islands()
+        stop_o, stop_g = io["stopped_at"], ig["stopped_at"]
+        same_stop = (stop_o == stop_g).mean()
+        both = (stop_o >= 0) & (stop_g >= 0)
+        sel = both[bi]
+        dv = np.abs(sg["vel"][sel] - so["vel"][sel]).max() if sel.any() else 0.0
+        dw = np.abs(sg["omega"][sel] - so["omega"][sel]).max() if sel.any() else 0.0
+        print(f"step {step}: {len(co['c_body'])} contacts, islands {len(stop_o)} (stop equal {same_stop:.3f}), "
+              f"converged on both {both.sum()}: max |dv| {dv:.2e} |dw| {dw:.2e}")
+        assert same_stop >= 0.95
+        assert dv < 1e-9 and dw < 1e-9
+        st = so                                   # re-synchronise from the oracle
+    assert n_envs == 64

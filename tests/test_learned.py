@@ -148,7 +148,8 @@ def test_precond_targets_equal_the_dense_inverse(torch_cuda):
 
 def test_precond_scale_one_is_the_jacobi_preconditioner(torch_cuda):
     """A network whose fourth output is zero scales every contact by exp(0) = 1:
-    the step is the one without the scale, bit for bit."""
+    the step is the one without the scale, to FP32 rounding of the CR
+    iterations (the two launch configurations sum in different orders)."""
     s = scenes.batched_envs(seed=8, n_envs=4)
     p = learn.init_params(3)
     p[-4 * 128 - 4 + 3 * 128:-4 * 128 - 4 + 4 * 128] = 0.0   # fourth row of the last layer
@@ -161,4 +162,4 @@ def test_precond_scale_one_is_the_jacobi_preconditioner(torch_cuda):
         g.step(); g.step()
         out.append(g.get_state())
     for k in ("pos", "vel", "omega"):
-        assert np.array_equal(out[0][k], out[1][k])
+        np.testing.assert_allclose(out[0][k], out[1][k], rtol=0, atol=1e-6 * max(1.0, np.abs(out[0][k]).max()))
