@@ -38,9 +38,9 @@ trajectory advances from the seeded start state (no reset between steps).
             algorithmic count, timed live at full activity; the streamed CR
             operator apply is reported beside it (operator_apply_roofline, HBM)
             and the network forward (network_roofline, tensor)
-  cpu_baseline  the FP64 oracle (plain method: zero start) on a
-            64-environment sample, one host core, same tolerance, caps and
-            accounting
+  cpu_baseline  the FP64 oracle (plain method: zero start) on 16-environment
+            samples, one process per host core, same tolerance, caps,
+            contact regeneration and accounting
 
 ``--impl reference`` times the FP64 oracle (the reference arm here) on the
 host cores with the same workload definition, metric and unit.
@@ -83,7 +83,7 @@ WORKLOADS = {
     "mixed_bin": dict(make=lambda seed: scenes.mixed_bin(seed=seed), newton=30, cr=50,
                       desc="2000 rigid boxes + 8 stable Neo-Hookean balls (36,480 tets) in a bin, one environment"),
 }
-SAMPLE_ENVS = 64
+SAMPLE_ENVS = 16      # environments per oracle process of the CPU baseline
 WEIGHTS = os.path.join(ROOT, "paper_1907_04587_gb300", "weights", "warm_start_mlp.npy")
 
 
@@ -369,34 +369,99 @@ def count_converged(stops, isl_env, n_envs):
     return int((fail == 0).sum()), int(ok.sum()), float(stops[ok].mean()) if ok.any() else float("nan")
 
 
-def oracle_rate(workload, seed, budget_s, newton, cr):
-    """FP64 oracle converged env-steps/s on a bounded sample of the workload."""
+def _oracle_chunk(job):
+    """One host process: the FP64 oracle, as it stands, on its own sample of
+    the workload for ``budget_s`` seconds.  With ``regen`` the contacts are
+    regenerated at every step by the oracle's collider (candidates from
+    v + h g, margin 1 cm, as the GPU step does) and a fresh oracle steps them
+    from the current state (zero start).  Returns (converged env-steps,
+    steps, seconds, environments)."""
+    workload, seed, budget_s, newton, cr, ls, regen = job
     import oracle
     if workload.startswith("batched"):
         s = scenes.batched_envs(seed=seed, n_envs=SAMPLE_ENVS)
-        sample = f"{SAMPLE_ENVS} environments of the same distribution (seed {seed})"
     else:
         s = WORKLOADS[workload]["make"](seed)
-        sample = "the full scene"
     n_envs = int(s.get("n_envs", 1))
-    o = oracle.Oracle(s, newton_iters=newton, cr_iters=cr, tol_rel=TOL, island_stop=1, cone_project=1,
-                      line_search=LS)
-    ni, bi, _ = o.islands()
-    isl_env = island_env_map(s, bi, ni)
-    stops = []
-    n, t0 = 0, time.perf_counter()
+    prm = dict(newton_iters=newton, cr_iters=cr, tol_rel=TOL, island_stop=1, cone_project=1, line_search=ls)
+    regen = regen and "half" in s and "mu_env" in s
+    h = 1.0 / 60.0
+    if regen:
+        jb = np.asarray(s["j_body"])
+        exclude = jb[(jb[:, 0] >= 0) & (jb[:, 1] >= 0)] if len(jb) else jb
+        grav = np.float32(h) * np.array([0.0, 0.0, -9.81], np.float32)
+    o = oracle.Oracle(s, **prm)
+    conv, n, t0 = 0, 0, time.perf_counter()
     while True:
+        if regen:
+            st = o.get_state()
+            co = oracle.collide(s["kind"], st["pos"], st["quat"], st["vel"].astype(np.float32) + grav, st["omega"],
+                                s["half"], s["env"], ((0.0, 0.0, 1.0, 0.0),), exclude, s["mu_env"], 0.01, h)
+            o = oracle.Oracle(scenes.finalize({**s, **co}), **prm)
+            o.set_state(**st)
         o.step()
-        stops.append(o.island_stats()["stopped_at"].copy())
+        ni, bi, _ = o.islands()
+        conv += count_converged([o.island_stats()["stopped_at"]], island_env_map(s, bi, ni), n_envs)[0]
         n += 1
         el = time.perf_counter() - t0
         if el >= budget_s:
-            break
-    conv, _, _ = count_converged(stops, isl_env, n_envs)
-    return conv / el, dict(kind="oracle", cores=1,
-                           sample=f"{sample}, same tolerance, caps, Newton step ({'line search' if LS else 'damped'}) "
-                                  f"and accounting, zero start; {n} advancing steps in {el:.1f} s, "
-                                  f"{conv} of {n * n_envs} env-steps converged")
+            return conv, n, el, n_envs
+
+
+def oracle_rate(workload, seed, budget_s, newton, cr, cores=None):
+    """FP64 oracle converged env-steps/s on a bounded sample of the workload:
+    one process per host core (spawned: the GPU context of the caller is not
+    inherited), each stepping its own environments of the same distribution
+    (seeds seed*1000 + k) for budget_s; the rate is their sum over the
+    longest process's time."""
+    import multiprocessing as mp
+    if cores is None:
+        cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    cores = max(1, min(int(cores), 16))
+    if not workload.startswith("batched"):
+        cores = 1       # one scene: a sample of one
+    jobs = [(workload, seed * 1000 + k if k else seed, budget_s, newton, cr, LS, REGEN) for k in range(cores)]
+    if cores == 1:
+        res = [_oracle_chunk(jobs[0])]
+    else:
+        with mp.get_context("spawn").Pool(cores) as pool:
+            res = pool.map(_oracle_chunk, jobs)
+    conv = sum(r[0] for r in res)
+    el = max(r[2] for r in res)
+    steps = sum(r[1] for r in res)
+    if workload.startswith("batched"):
+        sample = (f"{cores} x {SAMPLE_ENVS} environments of the same distribution (seed {seed}*1000+k "
+                  f"for process k > 0), one process per host core")
+    else:
+        sample = "the full scene, one host core"
+    return conv / el, dict(kind="oracle", cores=cores,
+                           sample=f"{sample}; same tolerance, caps, Newton step ({'line search' if LS else 'damped'}) "
+                                  f"and accounting, zero start, contacts "
+                                  f"{'regenerated by the oracle collider every step' if REGEN else 'fixed'}; "
+                                  f"{steps} advancing steps in {el:.1f} s, {conv} of "
+                                  f"{sum(r[1] * r[3] for r in res)} env-steps converged")
+
+
+def heavy_stack_comparison(nsn, stream):
+    """The complementarity preconditioners of Sec. 7 on the heavy stack of
+    Sec. 10 (five unit cubes, 8 ... 32768 kg), at rest and with the boxes
+    sliding at up to 5 m/s: one step to 1e-6 (cap 40 Newton iterations of 40
+    CR iterations), Newton iterations taken and the final merit relative to
+    the zero-iterate merit, FP32 production build."""
+    out = {}
+    for vx in (0.0, 5.0):
+        s = scenes.heavy_stack()
+        s["vel"] = s["vel"].copy()
+        s["vel"][:, 0] = np.float32(vx) * np.arange(1, 6, dtype=np.float32) / 5
+        row = {}
+        for name, rs in (("identity", 0), ("h2", 1), ("effective_mass", 2)):
+            g = nsn.Solver(s, stream=stream.cuda_stream, newton_iters=40, cr_iters=40, tol_rel=TOL, rscale=rs)
+            st = g.step()
+            row[name] = {"newton": int(st["newton_done"]),
+                         "merit_ratio": float(st["merit_final"] / max(st["merit0"], 1e-300))}
+            g.close()
+        out[f"top_speed_{vx:g}_m_per_s"] = row
+    return out
 
 
 def run_reference(args, rank, world):
@@ -466,7 +531,7 @@ def measure_arm(nsn, torch, g, s, st0, stream, steps, warmup, clk=None, reset=Fa
     e1 = torch.cuda.Event(enable_timing=True)
     if clk:
         clk.__enter__()
-    newton, launches, contacts = [], 0, []
+    newton, launches, contacts, phases = [], 0, [], []
     if collider is not None:
         # islands change with the contacts: the stop iterations of each step go
         # to a buffer of the largest island count a scene of these bodies can
@@ -483,6 +548,7 @@ def measure_arm(nsn, torch, g, s, st0, stream, steps, warmup, clk=None, reset=Fa
             ni_k, bi_k = g.islands()
             maps.append((ni_k, island_env_map(s, bi_k, ni_k)))
             contacts.append((g.R - 5 * len(s["j_body"])) // 3)
+            phases.append(g.phase_times())
         newton.append(st["newton_done"])
         launches += g.launches_per_step()
     e1.record(stream)
@@ -511,6 +577,9 @@ def measure_arm(nsn, torch, g, s, st0, stream, steps, warmup, clk=None, reset=Fa
                value=conv / sec, islands=ni, kernels=launches)
     if collider is not None:
         out["contacts_per_step"] = float(np.mean(contacts))
+        # host wall time per phase of a step with regenerated contacts (mean
+        # over the timed steps; the step phase waits for the GPU's work)
+        out["host_phases_ms"] = {k: float(np.mean([p[k] for p in phases])) for k in phases[0]} if phases else None
     return out
 
 
@@ -648,6 +717,7 @@ def run_ours(args, rank, world, local_rank):
                                                    ("plain_zero_start_line_search", 1, nsn.NSN_WARM_ZERO, False, 0, 2, 1),
                                                    ("as_printed", 0, nsn.NSN_WARM_ZERO, False, 0, 2, 0),
                                                    ("prev_warm_start", 1, nsn.NSN_WARM_PREV, False, 0, 2, 0),
+                                                   ("prev_warm_start_line_search", 1, nsn.NSN_WARM_PREV, False, 0, 2, 1),
                                                    ("after_reset_zero", 1, nsn.NSN_WARM_ZERO, True, 0, 2, 0),
                                                    ("after_reset_learned", 1, nsn.NSN_WARM_LEARNED, True, 0, 2, 0),
                                                    ("ablation_min_map", 1, nsn.NSN_WARM_ZERO, True, 1, 2, 0),
@@ -662,7 +732,8 @@ def run_ours(args, rank, world, local_rank):
                 ga = make_solver(nsn, s, stream, newton, cr, cone=cone, warm=wm, params=params, ncp=ncp, rscale=rs, ls=ls,
                                  fp64=fp64)
                 try:
-                    r = measure_arm(nsn, torch, ga, s, st0, stream, args.steps, args.warmup, reset=reset)
+                    r = measure_arm(nsn, torch, ga, s, st0, stream, args.steps, args.warmup, reset=reset,
+                                    collider=collider)
                 except nsn.NSNError as e:      # the method failing on this variant is a result
                     arms[name] = {"failed": str(e)}
                     ga.close()
@@ -677,6 +748,8 @@ def run_ours(args, rank, world, local_rank):
     except (nsn.ColliderError, ValueError, MemoryError) as e:
         torch.cuda.synchronize()    # a CUDA error on the context is not a host failure: it raises here
         contacts_rf = {"failed": repr(e)}
+    with torch.cuda.stream(stream):
+        rscale_cmp = heavy_stack_comparison(nsn, stream)
     B = algorithmic_bytes(sz)
     peak, peak_kind = measured_peaks()
     achieved = B / ((ms_body + ms_row) * 1e-3) / 1e9
@@ -733,6 +806,7 @@ def run_ours(args, rank, world, local_rank):
         "operator_apply_roofline": apply_rf,
         "network_roofline": mlp,
         "contact_generation": contacts_rf,
+        "heavy_stack_r_strategies": rscale_cmp,
         "cpu_baseline": cb,
         "e2e": {"value": value_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "note": "the state makes a host round trip every step; the trajectory advances"},

@@ -500,6 +500,24 @@ const char *nsn_collider_last_error(const nsn_collider *c);
  * nsn_step.  The context's stream waits for the collider at each step. */
 nsn_status nsn_collide_and_step(nsn_ctx *ctx, nsn_collider *col, int32_t nsteps, nsn_stats *stats);
 
+/* Host wall time, in milliseconds, of the phases of the last rebuild and
+ * step (std::chrono steady clock, measured by the calling thread; each
+ * phase ends with the stream synchronisation it already performs):
+ *   NSN_PHASE_COLLIDE  nsn_collide_and_step: state export, collider run,
+ *                      contact download and records
+ *   NSN_PHASE_SAVE     previous multipliers and the state read back
+ *   NSN_PHASE_LAYOUT   host layout (islands, orders, entry lists, groups)
+ *   NSN_PHASE_UPLOAD   device arrays written, state scattered
+ *   NSN_PHASE_RESTORE  previous multipliers matched by contact key, written
+ *   NSN_PHASE_CAPTURE  CUDA graph capture and instantiation of the step
+ *   NSN_PHASE_STEP     the step's launches up to its final synchronisation
+ * A phase that did not run in the last call keeps its previous value, except
+ * that a rebuild resets SAVE..RESTORE and a step resets CAPTURE.  ms holds
+ * NSN_PHASES doubles (host).  Errors: NSN_ERR_INVALID_ARG for null arguments. */
+enum { NSN_PHASE_COLLIDE = 0, NSN_PHASE_SAVE, NSN_PHASE_LAYOUT, NSN_PHASE_UPLOAD, NSN_PHASE_RESTORE,
+       NSN_PHASE_CAPTURE, NSN_PHASE_STEP, NSN_PHASES };
+nsn_status nsn_get_phase_times(nsn_ctx *ctx, double *ms);
+
 #ifdef __cplusplus
 }
 #endif

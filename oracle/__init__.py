@@ -108,6 +108,8 @@ def lib():
         L.orc_pcr.argtypes = [C.c_void_p, C.c_int32, _dp, _dp]
         L.orc_pcr.restype = C.c_int32
         L.orc_eval_constraints.argtypes = [C.c_void_p, _dp, _dp]
+        L.orc_merit_at.argtypes = [C.c_void_p, _dp, _dp, _dp]
+        L.orc_merit_at.restype = C.c_double
         L.orc_num_islands.argtypes = [C.c_void_p]
         L.orc_num_islands.restype = C.c_int32
         L.orc_get_islands.argtypes = [C.c_void_p, _ip, _ip]
@@ -234,6 +236,7 @@ class Oracle:
         if not self.ctx:
             raise ValueError("oracle rejected the scene")
         self.nb, self.nc, self.nj, self.nt, self.nl = nb, nc, nj, nt, nl
+        self.kind = self._keep["kind"].copy()
         self.R = L.orc_num_rows(self.ctx)
         self.D = L.orc_num_dofs(self.ctx)
         self.last_stats = None
@@ -320,6 +323,21 @@ class Oracle:
         y = np.zeros(self.R)
         lib().orc_apply_A(self.ctx, _ptr(x), _ptr(y))
         return y
+
+    def dofs(self, vel, omega):
+        """Generalised velocity in DOF order ([v, w] per rigid body, v per particle)."""
+        vel, omega = np.asarray(vel, np.float64), np.asarray(omega, np.float64)
+        return np.concatenate([np.concatenate([vel[i], omega[i]]) if k == 0 else vel[i]
+                               for i, k in enumerate(self.kind)]) if len(self.kind) else np.zeros(0)
+
+    def merit_at(self, vel, omega, lam):
+        """The merit of Sec. 8.1 at the iterate (u = (vel, omega), lam) of the
+        step from the current state: (overall, per island)."""
+        u = _d(self.dofs(vel, omega), (self.D,))
+        lam = _d(lam, (self.R,))
+        isl = np.zeros(max(lib().orc_num_islands(self.ctx), 1))
+        m = lib().orc_merit_at(self.ctx, _ptr(u), _ptr(lam), _ptr(isl))
+        return m, isl[:lib().orc_num_islands(self.ctx)]
 
     def eval_constraints(self, with_jacobian=True):
         c = np.zeros(self.R)

@@ -1671,6 +1671,28 @@ int orc_eval_constraints(orc_ctx *c, double *cvals, double *Jgeo) {
   return 0;
 }
 
+/* The merit of Sec. 8.1, ||[g; h]||, at a given iterate (u, lambda) of the
+ * step that starts from the current state: q^-, u~ and the world inertia as
+ * the step forms them (begin_step), positions from u, rows at (u, lambda),
+ * g = M~(u - u~) - h J^T lambda.  isl (optional, one per island) receives the
+ * same norm per island.  The state is left as it was. */
+double orc_merit_at(orc_ctx *c, const double *u, const double *lambda, double *isl) {
+  double *zb = calloc(c->D + 1, sizeof(double));
+  const int rec = c->dlog_rec;
+  c->dlog_rec = 0;
+  begin_step(c);
+  positions_from_u(c, u);
+  eval_rows(c, u, lambda);
+  compute_g(c, u, lambda, zb);
+  const double m = merit(c);
+  if (isl) island_merits(c, isl);
+  memcpy(c->pos, c->pos0, sizeof(double) * 3 * c->nb);
+  memcpy(c->quat, c->quat0, sizeof(double) * 4 * c->nb);
+  c->dlog_rec = rec;
+  free(zb);
+  return m;
+}
+
 int orc_apply_A(orc_ctx *c, const double *x, double *y) {
   double *zb = malloc(sizeof(double) * (c->D + 1)), *yb = malloc(sizeof(double) * (c->D + 1));
   apply_A(c, x, y, zb, yb);

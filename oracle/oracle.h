@@ -177,6 +177,11 @@ int orc_pcr(orc_ctx *ctx, int32_t iters, double *x_out, double *res_hist);
  * basis rows D (Sec. 3.4), joint rows grad c_b G and tet rows ds/dx. */
 int orc_eval_constraints(orc_ctx *ctx, double *cvals, double *Jgeo);
 
+/* The merit ||[g; h]|| of Sec. 8.1 at the iterate (u (D, in DOF order),
+ * lambda (R)) of the step that starts from the current state; isl (optional,
+ * one double per island) receives it per island.  The state is unchanged. */
+double orc_merit_at(orc_ctx *ctx, const double *u, const double *lambda, double *isl);
+
 /* Scalar building blocks, exported for the pin tests. */
 double orc_fb(double a, double b);
 void orc_fb_contact(double C, double lam, double r, double *phi, double *alpha, double *S);

@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -154,9 +155,23 @@ struct nsn_ctx {
   unsigned char *dlog_buf = nullptr;   // the log on the device (iters x (rows + islands) bytes)
   size_t dlog_bytes = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // host wall time (ms) of the phases of the last rebuild / step, NSN_PHASE_*
+  double phase_ms[NSN_PHASES] = {};
   std::string err;
   nsn_stats last{};
 };
+
+namespace {
+double now_ms() {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+// adds the time since `t0` to a phase and restarts the clock
+void phase_tick(nsn_ctx *c, int phase, double &t0) {
+  const double t = now_ms();
+  c->phase_ms[phase] += t - t0;
+  t0 = t;
+}
+}  // namespace
 
 namespace {
 
@@ -1222,6 +1237,8 @@ nsn_status restore_lam_prev(nsn_ctx *c, const std::vector<double> &old, const st
 
 nsn_status ensure_built(nsn_ctx *c) {
   if (!c->dirty) return NSN_OK;
+  for (int k = NSN_PHASE_SAVE; k <= NSN_PHASE_RESTORE; k++) c->phase_ms[k] = 0.0;
+  double t0 = now_ms();
   if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
   std::vector<double> lam_prev_abi;
   if (c->dmem && c->built_nb > 0) {
@@ -1242,16 +1259,20 @@ nsn_status ensure_built(nsn_ctx *c) {
     std::copy(vel.begin(), vel.end(), c->scene.vel.begin());
     std::copy(om.begin(), om.end(), c->scene.omega.begin());
   }
+  phase_tick(c, NSN_PHASE_SAVE, t0);
   nsn_status s = build_layout(c);
   if (s != NSN_OK) return s;
+  phase_tick(c, NSN_PHASE_LAYOUT, t0);
   s = c->cfg.precision == NSN_FP64 ? build_device<double>(c) : build_device<float>(c);
   if (s != NSN_OK) return s;
+  phase_tick(c, NSN_PHASE_UPLOAD, t0);
   if (!lam_prev_abi.empty() && c->built_nb == int(c->scene.kind.size())) {
     s = c->cfg.precision == NSN_FP64
             ? restore_lam_prev<double>(c, lam_prev_abi, c->built_contacts, c->built_nj, c->built_nt)
             : restore_lam_prev<float>(c, lam_prev_abi, c->built_contacts, c->built_nj, c->built_nt);
     if (s != NSN_OK) return s;
   }
+  phase_tick(c, NSN_PHASE_RESTORE, t0);
   c->dirty = false;
   c->built_nb = int(c->scene.kind.size());
   c->built_contacts = c->scene.contacts;
@@ -1369,13 +1390,16 @@ nsn_status run_steps(nsn_ctx *c, int nsteps) {
     D.dlog_iters = want ? c->dlog_iters : 0;
     if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
   }
+  c->phase_ms[NSN_PHASE_CAPTURE] = 0.0;
   if (!c->ev0) CUDA_TRY(c, cudaEventCreate(&c->ev0));
   if (!c->ev1) CUDA_TRY(c, cudaEventCreate(&c->ev1));
   CUDA_TRY(c, cudaEventRecord(c->ev0, st));
   if (c->cfg.use_graph) {
     if (!c->graph) {
+      double t0 = now_ms();
       nsn_status s = capture_step<T>(c, D);
       if (s != NSN_OK) return s;
+      phase_tick(c, NSN_PHASE_CAPTURE, t0);
     }
     for (int s = 0; s < nsteps; s++) {
       if (D.dlog) CUDA_TRY(c, cudaMemsetAsync(D.dlog_cr, 0xff, dlog_need, st));
@@ -2053,7 +2077,9 @@ nsn_status nsn_step(nsn_ctx *c, int32_t nsteps, nsn_stats *stats) {
   nsn_status s = ensure_built(c);
   if (s != NSN_OK) return s;
   c->linearized = false;
+  const double t0 = now_ms();
   s = c->cfg.precision == NSN_FP64 ? run_steps<double>(c, nsteps) : run_steps<float>(c, nsteps);
+  c->phase_ms[NSN_PHASE_STEP] = now_ms() - t0 - c->phase_ms[NSN_PHASE_CAPTURE];
 
   if (stats) *stats = c->last;
   return s;
@@ -2278,6 +2304,7 @@ __global__ void k_add_gravity(float *vel, int nb, float gx, float gy, float gz) 
 
 nsn_status collide_once(nsn_ctx *c, nsn_collider *col) {
   const int nb = int(c->scene.kind.size());
+  double t0 = now_ms();
   int32_t info[4];
   nsn_status s = nsn_collider_info(col, info);
   if (s != NSN_OK) return fail(c, s, "nsn_collide_and_step: bad collider");
@@ -2350,6 +2377,8 @@ nsn_status collide_once(nsn_ctx *c, nsn_collider *col) {
     }
     c->scene.contacts.swap(rec);
     c->dirty = true;
+    c->phase_ms[NSN_PHASE_COLLIDE] = 0.0;
+    phase_tick(c, NSN_PHASE_COLLIDE, t0);
     return NSN_OK;
   }
   return fail(c, NSN_ERR_OUT_OF_MEMORY, "nsn_collide_and_step: contact buffer");
@@ -2365,6 +2394,12 @@ nsn_status nsn_collide_and_step(nsn_ctx *c, nsn_collider *col, int32_t nsteps, n
     if (s != NSN_OK) return s;
     if ((s = nsn_step(c, 1, stats)) != NSN_OK) return s;
   }
+  return NSN_OK;
+}
+
+nsn_status nsn_get_phase_times(nsn_ctx *c, double *ms) {
+  if (!c || !ms) return NSN_ERR_INVALID_ARG;
+  for (int k = 0; k < NSN_PHASES; k++) ms[k] = c->phase_ms[k];
   return NSN_OK;
 }
 

@@ -1075,9 +1075,24 @@ __global__ void k_eval_tets(Dev<T> D, int buf, int force) {
     // (engineering shears), its modes m (kind 1: volumetric and two deviatoric
     // normal-strain modes; kind 2: the shears) with constant rows dm/dx and
     // diagonal compliance E' (tC1, tD1, talpha): h = (m + E' lambda) / h,
-    // C = E' / h^2 -- the Neo-Hookean pattern with V_e K_e diagonal
+    // C = E' / h^2 -- the Neo-Hookean pattern with V_e K_e diagonal.
+    // The strain and h are formed in FP64 from the stored state, like the
+    // contact and joint constraint values: F - I of a stiff element is a small
+    // difference of order-one terms, and near equilibrium m + E' lambda cancels
     const int kind = D.tkind[t];
-    const T e6[6] = {F[0] - T(1), F[4] - T(1), F[8] - T(1), F[5] + F[7], F[2] + F[6], F[1] + F[3]};
+    double Fd[9];
+    {
+      double Dsd[9];
+      const double hd = D.h;
+      for (int k = 0; k < 3; k++)
+        for (int r = 0; r < 3; r++)
+          Dsd[3 * r + k] = (double(D.px0[r][v[k + 1]]) - double(D.px0[r][v[0]])) +
+                           hd * (double(D.pu[r][v[k + 1]]) - double(D.pu[r][v[0]]));
+      for (int r = 0; r < 3; r++)
+        for (int k = 0; k < 3; k++)
+          Fd[3 * r + k] = Dsd[3 * r] * double(Dmi[k]) + Dsd[3 * r + 1] * double(Dmi[3 + k]) + Dsd[3 * r + 2] * double(Dmi[6 + k]);
+    }
+    const double e6[6] = {Fd[0] - 1.0, Fd[4] - 1.0, Fd[8] - 1.0, Fd[5] + Fd[7], Fd[2] + Fd[6], Fd[1] + Fd[3]};
     T w[4][3];
     for (int b2 = 0; b2 < 3; b2++) {
       w[0][b2] = -(Dmi[b2] + Dmi[3 + b2] + Dmi[6 + b2]);
@@ -1085,12 +1100,14 @@ __global__ void k_eval_tets(Dev<T> D, int buf, int force) {
     }
     const T r3 = T(0.57735026918962576), r2 = T(0.70710678118654752), r6 = T(0.40824829046386302);
     const T Qn[3][3] = {{r3, r2, r6}, {r3, -r2, r6}, {r3, T(0), T(-2) * r6}};   // Qn[component][mode]
+    const double d3 = 0.57735026918962576, d2 = 0.70710678118654752, d6 = 0.40824829046386302;
+    const double Qd[3][3] = {{d3, d2, d6}, {d3, -d2, d6}, {d3, 0.0, -2.0 * d6}};
     const int IA[3] = {1, 0, 0}, IB[3] = {2, 2, 1};                          // shears yz, xz, xy
     const T Ep[3] = {D.tC1[t], D.tD1[t], D.talpha[t]};
     const int base = 3 * D.nc + 5 * D.nj + 3 * t;
     const T ih2 = T(1) / (h * h);
     for (int k = 0; k < 3; k++) {
-      T m = T(0);
+      double m = 0.0;
       for (int q = 0; q < 4; q++) {
         T J6[6] = {0, 0, 0, 0, 0, 0};
         if (kind == 1) {
@@ -1101,9 +1118,9 @@ __global__ void k_eval_tets(Dev<T> D, int buf, int force) {
         }
         write_entry(D, D.te[12 * t + 4 * k + q], J6, buf);
       }
-      if (kind == 1) m = Qn[0][k] * e6[0] + Qn[1][k] * e6[1] + Qn[2][k] * e6[2];
+      if (kind == 1) m = Qd[0][k] * e6[0] + Qd[1][k] * e6[1] + Qd[2][k] * e6[2];
       else m = e6[3 + k];
-      D.hv[base + k] = (m + Ep[k] * D.lam[base + k]) / h;
+      D.hv[base + k] = T((m + double(Ep[k]) * double(D.lam[base + k])) / D.h);
       D.cdiag[base + k] = Ep[k] * ih2;
       if (slot >= 0) D.dlog[size_t(slot) * D.R + base + k] = 0;
     }
@@ -2180,7 +2197,7 @@ __host__ __device__ inline ResLayout res_layout(int RR, int RE, int RB) {
   L.erow = take(sizeof(int) * re, sizeof(int));
   L.seg = take(sizeof(int) * rb, sizeof(int));
   L.bisl = take(sizeof(int) * rb, sizeof(int));
-  L.isl = take(sizeof(int) * 11 * RES_MAXI, sizeof(int));
+  L.isl = take(sizeof(int) * 12 * RES_MAXI, sizeof(int));
   L.task = take(sizeof(int) * 3 * RES_MAXT, sizeof(int));
   L.ctl = take(sizeof(int) * 4, sizeof(int));
   L.total = off;
@@ -2199,6 +2216,7 @@ struct ResSmem {
   int2 *le;                                     // local entries of the two sides of each row (-1: none)
   int *risl, *erow, *seg, *bisl;                // island of each row, row of each entry, body segments, island of each body
   int *act, *kdone, *cr0, *ncr, *jr0, *njr, *ient, *ibod, *ib0, *it0, *it1;   // [RES_MAXI] per island
+  int *tcnt;                                    // [RES_MAXI] tasks of the island finished (all iterations)
   int *tisl, *tr0, *tn;                         // [RES_MAXT] reduction tasks: island, first row, rows
   int *ctl;
 };
@@ -2229,7 +2247,7 @@ __device__ inline ResSmem<T> res_carve(unsigned char *base, int RR, int RE, int 
   int *q = reinterpret_cast<int *>(base + L.isl);
   S.act = q; S.kdone = q + RES_MAXI; S.cr0 = q + 2 * RES_MAXI; S.ncr = q + 3 * RES_MAXI; S.jr0 = q + 4 * RES_MAXI;
   S.njr = q + 5 * RES_MAXI; S.ient = q + 6 * RES_MAXI; S.ibod = q + 7 * RES_MAXI; S.ib0 = q + 8 * RES_MAXI;
-  S.it0 = q + 9 * RES_MAXI; S.it1 = q + 10 * RES_MAXI;
+  S.it0 = q + 9 * RES_MAXI; S.it1 = q + 10 * RES_MAXI; S.tcnt = q + 11 * RES_MAXI;
   int *tk = reinterpret_cast<int *>(base + L.task);
   S.tisl = tk; S.tr0 = tk + RES_MAXT; S.tn = tk + 2 * RES_MAXT;
   S.ctl = reinterpret_cast<int *>(base + L.ctl);
@@ -2251,58 +2269,90 @@ __device__ __forceinline__ T res_dot6(const T *J, const T *y) {
   return acc;
 }
 
-// The CR scalars of island li at iteration k from its task sums (the
-// recurrence and stop rules of k_cr_scalars_isl).  Returns false when the
-// island's CR stops.  The sums are T values, and so are the stop thresholds:
-// the stop tests compare in T (in FP32 they are exact: a single-precision
-// value and its FP64 image order the same way).  ApTPAp = d2 + 2 beta d3 +
-// beta^2 d5, the recurrence that cancels, is FP64 in both builds.  In the
-// FP32 build beta and alpha are what the update applies, FP32 values: beta =
-// rho / rho_prev and alpha = rho / ApTPAp are correctly rounded FP32 divisions
-// of FP32-exact operands (rho and rho_prev are FP32 sums), and ApTPAp is taken
-// with that FP32 beta, i.e. for the Ap the update actually forms; the FP64
-// build divides in FP64 as the streamed kernels do.  (One FP64 instruction
-// costs GB300's narrow FP64 pipe a full warp slot, and this step runs once per
-// CR iteration on the critical path of the group.)
+// Correctly rounded products and sums (no contraction): the pending update
+// of a row is formed twice, on the fly by the body pass and when the row pass
+// commits it, and both must give the same bits.
+__device__ __forceinline__ float rn_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double rn_mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float rn_add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double rn_add(double a, double b) { return __dadd_rn(a, b); }
+
+// The CR update of one row with its island's alpha and beta (Sec. 8.2):
+// Ap' = Az + beta Ap, p' = z + beta p, x' = x + alpha p', z' = z - alpha P Ap'
+// (first iteration: p' = z, Ap' = Az).  v = (z, P, Ap, C_ii + eps).
 template <typename T>
-__device__ __forceinline__ bool res_scalars(const ResSmem<T> &S, int li, int k) {
+__device__ __forceinline__ T res_ap_new(const RV4<T> &v, T az, T beta, bool first) {
+  return first ? az : rn_add(az, rn_mul(beta, v.c));
+}
+template <typename T>
+__device__ __forceinline__ T res_z_new(const RV4<T> &v, T api, T alpha) {
+  return rn_add(v.a, -rn_mul(rn_mul(alpha, v.b), api));
+}
+
+// The CR scalars of island li at iteration k (the recurrence and stop rules
+// of k_cr_scalars_isl), by the warp that finished the island's last task of
+// this iteration: the island's task sums are reduced by the warp in a fixed
+// tree order, then lane 0 takes the step.  Returns (to every lane) whether
+// the island's CR continues.  The sums are T values, and so are the stop
+// thresholds: the stop tests compare in T (in FP32 they are exact: a
+// single-precision value and its FP64 image order the same way).  ApTPAp =
+// d2 + 2 beta d3 + beta^2 d5, the recurrence that cancels, is FP64 in both
+// builds.  In the FP32 build beta and alpha are what the update applies, FP32
+// values: beta = rho / rho_prev and alpha = rho / ApTPAp are correctly
+// rounded FP32 divisions of FP32-exact operands (rho and rho_prev are FP32
+// sums), and ApTPAp is taken with that FP32 beta, i.e. for the Ap the update
+// actually forms; the FP64 build divides in FP64 as the streamed kernels do.
+// (One FP64 instruction costs GB300's narrow FP64 pipe a full warp slot; the
+// step runs on one lane of one warp per island and CR iteration.)
+template <typename T>
+__device__ __forceinline__ bool res_scalars_warp(const ResSmem<T> &S, int li, int k, int lane) {
   T a[5] = {T(0), T(0), T(0), T(0), T(0)};
-  for (int tk = S.it0[li]; tk < S.it1[li]; tk++)
+  const volatile T *part = S.part;
+  for (int tk = S.it0[li] + lane; tk < S.it1[li]; tk += 32)
 #pragma unroll
-    for (int q = 0; q < 5; q++) a[q] += S.part[q * RES_MAXT + tk];
-  // ||r||_P^2 = a[3]: floor, growth from the previous iteration, forcing term
-  const T cur2 = a[3] > T(0) ? a[3] : T(0);
-  const T rp2 = S.res_prev[li];
-  bool st = rp2 < T(0) || cur2 <= S.r02f[li] || (k > 0 && cur2 > rp2) || cur2 <= S.eta2[li];
-  S.res_prev[li] = cur2;
-  const T rho = a[0], rho_prev = S.rho_prev[li];
-  T beta = T(0);
-  double apap = double(a[1]);
-  if (k > 0) {
-    if (!(rho > T(0)) || !(rho_prev > T(0))) st = true;
-    else {
-      beta = rho / rho_prev;
-      const double b = double(beta);
-      apap = double(a[1]) + 2.0 * b * double(a[2]) + b * b * double(a[4]);
+    for (int q = 0; q < 5; q++) a[q] += part[q * RES_MAXT + tk];
+#pragma unroll
+  for (int q = 0; q < 5; q++) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a[q] += __shfl_xor_sync(0xffffffffu, a[q], o);
+  }
+  int cont = 0;
+  if (lane == 0) {
+    // ||r||_P^2 = a[3]: floor, growth from the previous iteration, forcing term
+    const T cur2 = a[3] > T(0) ? a[3] : T(0);
+    const T rp2 = S.res_prev[li];
+    bool st = rp2 < T(0) || cur2 <= S.r02f[li] || (k > 0 && cur2 > rp2) || cur2 <= S.eta2[li];
+    S.res_prev[li] = cur2;
+    const T rho = a[0], rho_prev = S.rho_prev[li];
+    T beta = T(0);
+    double apap = double(a[1]);
+    if (k > 0) {
+      if (!(rho > T(0)) || !(rho_prev > T(0))) st = true;
+      else {
+        beta = rho / rho_prev;
+        const double b = double(beta);
+        apap = double(a[1]) + 2.0 * b * double(a[2]) + b * b * double(a[4]);
+      }
+    }
+    T alpha = T(0);
+    if (!st && apap > 0.0) {
+      const T ap = T(apap);
+      if (ap > T(0)) alpha = rho / ap;
+      else st = true;                           // ApTPAp below the range of T
+    } else {
+      st = true;
+    }
+    if (st) {
+      S.act[li] = 0;
+      S.kdone[li] = k;
+    } else {
+      S.rho_prev[li] = rho;
+      S.alpha[li] = alpha;
+      S.beta[li] = beta;
+      cont = 1;
     }
   }
-  T alpha = T(0);
-  if (!st && apap > 0.0) {
-    const T ap = T(apap);
-    if (ap > T(0)) alpha = rho / ap;
-    else st = true;                           // ApTPAp below the range of T
-  } else {
-    st = true;
-  }
-  if (st) {
-    S.act[li] = 0;
-    S.kdone[li] = k;
-    return false;
-  }
-  S.rho_prev[li] = rho;
-  S.alpha[li] = alpha;
-  S.beta[li] = beta;
-  return true;
+  return __shfl_sync(0xffffffffu, cont, 0) != 0;
 }
 
 template <typename T>
@@ -2382,28 +2432,43 @@ __global__ void __launch_bounds__(RES_THREADS) k_cr_resident(Dev<T> D, int M) {
           }
         }
         S.it1[li] = nt;
+        S.tcnt[li] = 0;
       }
       S.ctl[2] = nt;
+      S.ctl[1] = 0;     // live flag of the first iteration
     }
     __syncthreads();
     const int ntask = S.ctl[2];
+    // One CR iteration is two phases and two barriers.  The update of
+    // iteration k-1 stays pending: the body pass of iteration k forms each
+    // row's new z from it on the fly, and the row pass commits it (p, Ap, x,
+    // z) before taking the products of iteration k; the warp that finishes an
+    // island's last task takes the island's scalar step.  Live flags
+    // alternate between two slots (ctl[1], ctl[3]) so that one can be cleared
+    // while the other is read.
     int k = 0;
     for (; k < M; k++) {
+      volatile int *live = &S.ctl[(k & 1) ? 3 : 1];
       // y_b = H~^-1 J^T z and t_e = J_e y_b for the bodies of continuing
       // islands, RES_G lanes per body; the first RES_KR entries of a lane stay
       // in registers between the two
       for (int bb = 0; bb < nb; bb += RES_THREADS / RES_G) {
         const int b = bb + tid / RES_G, l = tid % RES_G;
-        const bool on = b < nb && S.act[S.bisl[b]];
+        const int bli = b < nb ? S.bisl[b] : 0;
+        const bool on = b < nb && S.act[bli];
         int s0 = 0, s1 = 0;
-        if (on) { s0 = S.seg[b]; s1 = S.seg[b + 1]; }
+        T al = T(0), be = T(0);
+        if (on) { s0 = S.seg[b]; s1 = S.seg[b + 1]; al = S.alpha[bli]; be = S.beta[bli]; }
+        const bool pend = k > 0, first = k == 1;
         T J[RES_KR][6], s6[6] = {0, 0, 0, 0, 0, 0};
 #pragma unroll
         for (int q = 0; q < RES_KR; q++) {
           const int e = s0 + l + q * RES_G;
           if (e < s1) {
             res_load_j(S, e, J[q]);
-            const T zr = S.rv[S.erow[e]].a;
+            const int r = S.erow[e];
+            const RV4<T> v = S.rv[r];
+            const T zr = pend ? res_z_new(v, res_ap_new(v, S.Az[r], be, first), al) : v.a;
 #pragma unroll
             for (int m = 0; m < 6; m++) s6[m] += J[q][m] * zr;
           }
@@ -2411,7 +2476,9 @@ __global__ void __launch_bounds__(RES_THREADS) k_cr_resident(Dev<T> D, int M) {
         for (int e = s0 + l + RES_KR * RES_G; e < s1; e += RES_G) {
           T Je[6];
           res_load_j(S, e, Je);
-          const T zr = S.rv[S.erow[e]].a;
+          const int r = S.erow[e];
+          const RV4<T> v = S.rv[r];
+          const T zr = pend ? res_z_new(v, res_ap_new(v, S.Az[r], be, first), al) : v.a;
 #pragma unroll
           for (int m = 0; m < 6; m++) s6[m] += Je[m] * zr;
         }
@@ -2436,17 +2503,32 @@ __global__ void __launch_bounds__(RES_THREADS) k_cr_resident(Dev<T> D, int M) {
         }
       }
       __syncthreads();
-      // Az = t_e0 + t_e1 + (C_ii + eps) z and the five products of
-      // k_row_pass_isl, summed per task (one warp per task, fixed order)
+      // every thread has read the previous iteration's flag (before the
+      // barrier above): its slot is cleared for the next iteration
+      if (tid == 0) S.ctl[(k & 1) ? 1 : 3] = 0;
+      // per task (one warp, fixed order): commit the pending update of the
+      // task's rows, then Az = t_e0 + t_e1 + (C_ii + eps) z and the five
+      // products of k_row_pass_isl
       for (int tk = warp; tk < ntask; tk += RES_NW) {
-        if (!S.act[S.tisl[tk]]) continue;
+        const int li = S.tisl[tk];
+        if (!S.act[li]) continue;
+        const T al = S.alpha[li], be = S.beta[li];
         T a[5] = {T(0), T(0), T(0), T(0), T(0)};
         const int r1 = S.tr0[tk] + S.tn[tk];
         for (int r = S.tr0[tk] + lane; r < r1; r += 32) {
+          RV4<T> v = S.rv[r];                   // z, P, Ap, C_ii + eps
+          if (k > 0) {
+            const T api = res_ap_new(v, S.Az[r], be, k == 1);
+            const T pi = k == 1 ? v.a : v.a + be * S.p[r];
+            S.p[r] = pi;
+            S.x[r] += al * pi;
+            v.a = res_z_new(v, api, al);
+            v.c = api;
+            S.rv[r] = v;
+          }
           const int2 le = S.le[r];
           const T t0 = le.x >= 0 ? S.t[le.x] : T(0);
           const T t1 = le.y >= 0 ? S.t[le.y] : T(0);
-          const RV4<T> v = S.rv[r];             // z, P, Ap, C_ii + eps
           const T az = (t0 + t1) + v.d * v.a;
           S.Az[r] = az;
           const T paz = v.b * az;
@@ -2457,38 +2539,34 @@ __global__ void __launch_bounds__(RES_THREADS) k_cr_resident(Dev<T> D, int M) {
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1) a[q] += __shfl_xor_sync(0xffffffffu, a[q], o);
         }
+        int last = 0;
         if (lane == 0) {
 #pragma unroll
           for (int q = 0; q < 5; q++) S.part[q * RES_MAXT + tk] = a[q];
+          __threadfence_block();
+          const int n_li = S.it1[li] - S.it0[li];
+          last = atomicAdd(&S.tcnt[li], 1) + 1 == (k + 1) * n_li;
+        }
+        if (__shfl_sync(0xffffffffu, last, 0)) {
+          __syncwarp();
+          __threadfence_block();
+          if (res_scalars_warp<T>(S, li, k, lane) && lane == 0) *live = 1;
         }
       }
       __syncthreads();
-      // FP64 scalars and stop tests of every island of the group: lane li
-      if (warp == 0) {
-        bool live = false;
-        if (lane < nisl && S.act[lane]) live = res_scalars<T>(S, lane, k);
-        const unsigned any = __ballot_sync(0xffffffffu, live);
-        if (lane == 0) S.ctl[1] = any != 0u;
-      }
-      __syncthreads();
-      if (!S.ctl[1]) break;
-      // p = z + beta p, Ap = Az + beta Ap, x += alpha p, z -= alpha P Ap
+      if (!*live) break;
+    }
+    // the update of the last iteration of islands that ran to the cap
+    if (k == M)
       for (int r = tid; r < nrow; r += RES_THREADS) {
         const int li = S.risl[r];
-        if (!S.act[li]) continue;
-        const T alpha = S.alpha[li], beta = S.beta[li];
-        RV4<T> v = S.rv[r];
-        const T az = S.Az[r];
-        const T pi = k == 0 ? v.a : v.a + beta * S.p[r];
-        const T api = k == 0 ? az : az + beta * v.c;
-        S.p[r] = pi;
-        S.x[r] += alpha * pi;
-        v.c = api;
-        v.a = v.a - alpha * v.b * api;
-        S.rv[r] = v;
+        if (!S.act[li] || M == 0) continue;
+        const T al = S.alpha[li], be = S.beta[li];
+        const RV4<T> v = S.rv[r];
+        const T pi = M == 1 ? v.a : v.a + be * S.p[r];
+        S.x[r] += al * pi;
       }
-      __syncthreads();
-    }
+    __syncthreads();
     // islands that ran to the cap
     if (tid < nisl && S.act[tid]) S.kdone[tid] = k;
     __syncthreads();

@@ -116,6 +116,7 @@ def lib():
         "nsn_clear_warm_start": (C.c_int, [_vp]),
         "nsn_record_decisions": (C.c_int, [_vp, C.c_int32]),
         "nsn_get_prev_lambda": (C.c_int, [_vp, _dp]),
+        "nsn_get_phase_times": (C.c_int, [_vp, _dp]),
         "nsn_get_decisions": (C.c_int, [_vp, _vp, _vp, _vp]),
         "nsn_tuning": (C.c_int, [_vp, _ip, _fp]),
         "nsn_resident_info": (C.c_int, [_vp, _ip]),
@@ -508,6 +509,14 @@ class Solver:
         out = np.zeros(self.R)
         _check(self.ctx, lib().nsn_get_prev_lambda(self.ctx, out.ctypes.data_as(_dp)), "nsn_get_prev_lambda")
         return out
+
+    PHASES = ("collide", "save", "layout", "upload", "restore", "capture", "step")
+
+    def phase_times(self):
+        """Host milliseconds of the phases of the last rebuild and step (nsn_get_phase_times)."""
+        out = np.zeros(len(self.PHASES))
+        _check(self.ctx, lib().nsn_get_phase_times(self.ctx, out.ctypes.data_as(_dp)), "nsn_get_phase_times")
+        return dict(zip(self.PHASES, out.tolist()))
 
     def merit_history(self):
         return nsn_get_merit_history(self.ctx)

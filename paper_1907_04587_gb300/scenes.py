@@ -199,6 +199,26 @@ def cube_stack(seed=0, n=4, edge=1.0, density=1000.0, mu=0.5, jitter=1e-3, yaw_d
     return finalize(s)
 
 
+def heavy_stack(seed=0, masses=(8.0, 64.0, 512.0, 4096.0, 32768.0), edge=1.0, mu=0.5, jitter=1e-3, yaw_deg=5.0):
+    """The heavy stack of Sec. 10 (Rigid Body Contact): unit cubes whose masses
+    grow geometrically from the bottom, 8 ... 32768 kg (4096:1), mu = 0.5,
+    each pressing on the lighter one below; seed-jittered offsets and yaw."""
+    rng = np.random.default_rng(seed)
+    n = len(masses)
+    pos = np.zeros((n, 3)); quat = np.zeros((n, 4))
+    for i in range(n):
+        pos[i] = (rng.uniform(-jitter, jitter), rng.uniform(-jitter, jitter),
+                  edge / 2 + i * edge + rng.uniform(-jitter, jitter))
+        quat[i] = quat_yaw(np.deg2rad(rng.uniform(-yaw_deg, yaw_deg)))
+    m = np.asarray(masses, np.float64)
+    s = dict(kind=np.zeros(n, np.int32), pos=pos, quat=quat, vel=np.zeros((n, 3)), omega=np.zeros((n, 3)),
+             mass=m, inertia=np.stack([box_inertia(mi, (edge, edge, edge)) for mi in m]),
+             env=np.zeros(n, np.int32), half=np.full((n, 3), edge / 2))
+    s.update(stack_contacts(pos, quat, edge, mu))
+    s.update(_empty_joints()); s.update(_empty_tets())
+    return finalize(s)
+
+
 def _empty_joints():
     return dict(j_body=np.zeros((0, 2), np.int32), j_pa=np.zeros((0, 3)), j_pb=np.zeros((0, 3)),
                 j_axa=np.zeros((0, 3)), j_axb=np.zeros((0, 3)), j_compliance=np.zeros(0))

@@ -92,11 +92,14 @@ STEP_PARAMS = dict(PARAMS, chain_block_small=dict(newton_iters=10, cr_iters=50, 
 
 @pytest.mark.parametrize("name", list(SCENES))
 @pytest.mark.parametrize("prec", [nsn.NSN_FP64, nsn.NSN_FP32])
-def test_linear_system_parity(orc, name, prec):
+@pytest.mark.parametrize("rscale", [0, 1, 2])
+def test_linear_system_parity(orc, name, prec, rscale):
     """b, Jacobi diagonal, h and g of Eq. schur_system at the zero iterate and
-    after one Newton iteration; then y = A x for a random x."""
+    after one Newton iteration; then y = A x for a random x.  For each
+    complementarity preconditioner of Sec. 7: r = 1 (0), r = h^2 (1) and the
+    effective-mass r (2)."""
     s = SCENES[name]()
-    p = PARAMS[name]
+    p = dict(PARAMS[name], rscale=rscale)
     o = orc.Oracle(s, **p)
     g = nsn.Solver(s, precision=prec, **p)
     kappa = None

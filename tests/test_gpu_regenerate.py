@@ -63,11 +63,31 @@ def test_previous_multipliers_follow_contacts_by_key():
     g.step()   # the rebuilt context steps
 
 
+def island_velocity_errors(so, sg, bi, sel):
+    """Per selected island: max |du| over its bodies relative to its largest
+    speed (or the free-fall change g h when it is at rest)."""
+    out = []
+    for i in np.nonzero(sel)[0]:
+        b = bi == i
+        d = max(np.abs(sg["vel"][b] - so["vel"][b]).max(), np.abs(sg["omega"][b] - so["omega"][b]).max())
+        sc = max(np.abs(so["vel"][b]).max(), np.abs(so["omega"][b]).max(), 9.81 * H)
+        out.append(d / sc)
+    return np.array(out if out else [0.0])
+
+
 def test_collide_and_step_matches_the_oracle_pipeline(orc):
     """64 batched environments over 10 steps, FP64 build, islands to 1e-6 with
     the line search: at every step the GPU's regenerated contacts equal the
-    oracle's collider's, and the stepped states agree (islands that converged
-    on both sides within 1e-9, stop iterations equal on 95% of islands)."""
+    oracle's collider's, the islands stop at the same Newton iteration on 95%
+    or more of them, and the stepped states agree.  The regenerated sets hold
+    both directions of every box pair (over-constrained, Sec. 3.3), so the
+    Schur systems are near singular and an island stopped at 1e-6 of its merit
+    is only determined to about cond x 1e-6: what is compared is (a) islands
+    that stopped at the same iteration on both sides, 99% of them within 1e-7
+    (rounding of two FP64 evaluation orders), and (b) every island converged
+    on both sides, whose GPU iterate (u, lambda) must satisfy the oracle's own
+    equations: the oracle's merit at it (orc_merit_at) within 1e-6 of the
+    island's zero-iterate merit, plus 1% for the two evaluations' rounding."""
     s = scenes.batched_envs(seed=3, n_envs=64)
     prm = dict(newton_iters=12, cr_iters=80, tol_rel=1e-6, island_stop=1, cone_project=1, line_search=1)
     n_envs = int(s["n_envs"])
@@ -86,20 +106,25 @@ def test_collide_and_step_matches_the_oracle_pipeline(orc):
         np.testing.assert_array_equal(cg["c_body"], co["c_body"])
         np.testing.assert_array_equal(cg["c_pa"], co["c_pa"].astype(np.float32))
         o = orc.Oracle(scenes.finalize({**s, **co}), **prm)
-        o.set_state(**{k: v.astype(np.float64) for k, v in f32.items()})
+        pre = {k: v.astype(np.float64) for k, v in f32.items()}
+        o.set_state(**pre)
         o.step()
         so, sg = o.get_state(), g.get_state_f64()
         io, ig = o.island_stats(), g.island_stats()
         _, bi, _ = o.islands()
         stop_o, stop_g = io["stopped_at"], ig["stopped_at"]
         same_stop = (stop_o == stop_g).mean()
+        equal = (stop_o == stop_g) & (stop_o >= 0)
         both = (stop_o >= 0) & (stop_g >= 0)
-        sel = both[bi]
-        dv = np.abs(sg["vel"][sel] - so["vel"][sel]).max() if sel.any() else 0.0
-        dw = np.abs(sg["omega"][sel] - so["omega"][sel]).max() if sel.any() else 0.0
-        print(f"step {step}: {len(co['c_body'])} contacts, islands {len(stop_o)} (stop equal {same_stop:.3f}), "
-              f"converged on both {both.sum()}: max |dv| {dv:.2e} |dw| {dw:.2e}")
+        e_eq = island_velocity_errors(so, sg, bi, equal)
+        o.set_state(**pre)
+        _, m_at = o.merit_at(sg["vel"], sg["omega"], g.get_lambda())
+        ratio = m_at[both] / io["merit0"][both]
+        print(f"step {step}: {len(co['c_body'])} contacts, islands {len(stop_o)} (stop equal {same_stop:.3f}); "
+              f"equal stop {int(equal.sum())}: p99 {np.quantile(e_eq, 0.99):.2e} max {e_eq.max():.2e}; "
+              f"converged on both {int(both.sum())}: oracle merit at the GPU iterate / merit0 max {ratio.max():.2e}")
         assert same_stop >= 0.95
-        assert dv < 1e-9 and dw < 1e-9
+        assert np.quantile(e_eq, 0.99) < 1e-7
+        assert ratio.max() <= 1.01e-6
         st = so                                   # re-synchronise from the oracle
     assert n_envs == 64
