@@ -383,7 +383,8 @@ def _oracle_chunk(job):
     else:
         s = WORKLOADS[workload]["make"](seed)
     n_envs = int(s.get("n_envs", 1))
-    prm = dict(newton_iters=newton, cr_iters=cr, tol_rel=TOL, island_stop=1, cone_project=1, line_search=ls)
+    prm = dict(newton_iters=newton, cr_iters=cr, tol_rel=TOL, island_stop=1, cone_project=1, line_search=ls,
+               best_iterate=1)
     regen = regen and "half" in s and "mu_env" in s
     h = 1.0 / 60.0
     if regen:
@@ -490,7 +491,7 @@ LS = 1          # --line-search 0: the headline arm takes the damped step of Sec
 def make_solver(nsn, s, stream, newton, cr, cone, warm=0, params=None, ncp=0, rscale=2, ls=0, fp64=False):
     g = nsn.Solver(s, stream=stream.cuda_stream, newton_iters=newton, cr_iters=cr, tol_rel=TOL, island_stop=1,
                    cone_project=cone, precision=nsn.NSN_FP64 if fp64 else nsn.NSN_FP32, use_graph=0 if EAGER else 1, ncp=ncp, rscale=rscale,
-                   cr_resident=RESIDENT, cr_tol_mode=CR_TOL, line_search=ls)
+                   cr_resident=RESIDENT, cr_tol_mode=CR_TOL, line_search=ls, best_iterate=1)
     if params is not None:
         nsn.nsn_mlp_set_params(g.ctx, params)
     g.set_warm_start(warm)
@@ -788,6 +789,7 @@ def run_ours(args, rank, world, local_rank):
                    "newton_step": ("back-tracking line search (t = 1 .. 1/16, else the damped 0.75), per island"
                                    if LS else "damped, t = 0.75"),
                    "tol_rel": TOL, "cone_projection": True, "warm_start": warm_note,
+                   "best_iterate": "an island that does not reach the tolerance returns its least-merit iterate",
                    "device_bytes": sz["device_bytes"], "launch": "kernel by kernel" if EAGER else
                    "one CUDA graph per step (Newton loop as a conditional WHILE node)",
                    "cr": ("island-resident CR (groups of small islands in shared memory, one thread block "

@@ -122,7 +122,11 @@ typedef struct {
                              below the current iterate's is taken, else the damped step t =
                              damping; per island in island mode.  0 (default, the paper's
                              results): the damped step */
-  int32_t reserved;       /* 0 */
+  int32_t best_iterate;   /* 1 (requires island_stop = 1): each island that has not stopped
+                             returns the iterate of least merit among those its Newton
+                             iterations evaluated (the start included) when the final
+                             iterate's merit is larger -- a safeguard against a diverging
+                             iteration, not in the paper.  0 (default): the last iterate */
 } nsn_config;
 
 /* Fills the paper's defaults: h = 1/60, g = (0, 0, -9.81), 4 x 20 iterations,
@@ -517,6 +521,11 @@ nsn_status nsn_collide_and_step(nsn_ctx *ctx, nsn_collider *col, int32_t nsteps,
 enum { NSN_PHASE_COLLIDE = 0, NSN_PHASE_SAVE, NSN_PHASE_LAYOUT, NSN_PHASE_UPLOAD, NSN_PHASE_RESTORE,
        NSN_PHASE_CAPTURE, NSN_PHASE_STEP, NSN_PHASES };
 nsn_status nsn_get_phase_times(nsn_ctx *ctx, double *ms);
+
+/* best_iterate: the number of islands of the last step that returned an
+ * earlier iterate than their last (0 when the option is off).  Errors:
+ * NSN_ERR_INVALID_ARG for null arguments. */
+nsn_status nsn_best_restored(nsn_ctx *ctx, int32_t *n_islands);
 
 #ifdef __cplusplus
 }

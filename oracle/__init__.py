@@ -59,7 +59,7 @@ class _Params(C.Structure):
         ("cr_iters", C.c_int32), ("damping", C.c_double), ("eps", C.c_double),
         ("tol_rel", C.c_double), ("cr_tol_mode", C.c_int32), ("ncp", C.c_int32),
         ("rscale", C.c_int32), ("geom_stiffness", C.c_int32), ("cone_project", C.c_int32),
-        ("island_stop", C.c_int32), ("line_search", C.c_int32),
+        ("island_stop", C.c_int32), ("line_search", C.c_int32), ("best_iterate", C.c_int32),
     ]
 
 
@@ -156,7 +156,7 @@ def _ptr(a):
 DEFAULT_PARAMS = dict(h=1.0 / 60.0, gravity=(0.0, 0.0, -9.81), newton_iters=4, cr_iters=20,
                       damping=0.75, eps=1e-6, tol_rel=0.0, cr_tol_mode=0, ncp=NCP_FB,
                       rscale=R_EFFMASS, geom_stiffness=GS_PARTICLES, cone_project=0, island_stop=0,
-                      line_search=0)
+                      line_search=0, best_iterate=0)
 
 
 class Oracle:
@@ -231,6 +231,7 @@ class Oracle:
         pr.cone_project = p["cone_project"]
         pr.island_stop = p["island_stop"]
         pr.line_search = p["line_search"]
+        pr.best_iterate = p["best_iterate"]
         self._s, self._p = s, pr
         self.ctx = L.orc_create(C.byref(s), C.byref(pr))
         if not self.ctx:

@@ -405,6 +405,7 @@ static void build_islands(orc_ctx *c) {
 orc_ctx *orc_create(const orc_scene *s, const orc_params *prm) {
   if (!s || !prm || s->n_bodies < 0 || s->n_contacts < 0 || s->n_joints < 0 || s->n_tets < 0) return NULL;
   if (!(prm->h > 0.0)) return NULL;
+  if (prm->best_iterate && !prm->island_stop) return NULL;
   int nb = s->n_bodies;
   for (int i = 0; i < nb; i++) {
     if (s->kind[i] != ORC_RIGID && s->kind[i] != ORC_PARTICLE) return NULL;
@@ -1452,6 +1453,17 @@ static int newton(orc_ctx *c, const double *lambda0, int stop_at, orc_stats *st,
   double mfirst = 0.0;
   const int isl = c->p.island_stop && c->p.tol_rel > 0.0;
   for (int i = 0; i < c->ni; i++) c->isl_stop[i] = -1;
+  /* least-merit iterate per island (best_iterate): merit, u and lambda */
+  const int best = c->p.best_iterate && c->p.island_stop;
+  double *mbest = NULL, *ubest = NULL, *lbest = NULL;
+  int *bflag = NULL;
+  if (best) {
+    mbest = malloc(sizeof(double) * (c->ni + 1));
+    bflag = calloc(c->ni + 1, sizeof(int));
+    ubest = calloc(c->D + 1, sizeof(double));
+    lbest = calloc(c->R + 1, sizeof(double));
+    for (int i = 0; i < c->ni; i++) mbest[i] = INFINITY;
+  }
   for (n = 0; n < c->p.newton_iters || n == stop_at; n++) {
     c->dlog_n = n;
     c->dlog_rec = 1;
@@ -1467,6 +1479,20 @@ static int newton(orc_ctx *c, const double *lambda0, int stop_at, orc_stats *st,
     if (n > 0 && c->p.geom_stiffness == ORC_GS_PARTICLES) geometric_stiffness(c, w->u, w->uprev, lam, w->zb, w->zb2);
     build_rhs(c, w->yb);
     if (n == stop_at) break;
+    if (best) {
+      /* the iterate of each island that is still iterating, kept when its
+       * merit is below every earlier one */
+      island_merits(c, c->isl_acc);
+      for (int i = 0; i < c->ni; i++) {
+        bflag[i] = c->isl_stop[i] < 0 && c->isl_acc[i] < mbest[i];
+        if (bflag[i]) mbest[i] = c->isl_acc[i];
+      }
+      for (int b = 0; b < c->nb; b++)
+        if (bflag[c->body_isl[b]])
+          for (int k = c->dof[b]; k < c->dof[b + 1]; k++) ubest[k] = w->u[k];
+      for (int r = 0; r < c->R; r++)
+        if (bflag[c->row_isl[r]]) lbest[r] = lam[r];
+    }
     if (isl) {
       /* per-island stop: an island that reached tol_rel keeps its iterate */
       island_merits(c, c->isl_acc);
@@ -1527,6 +1553,28 @@ static int newton(orc_ctx *c, const double *lambda0, int stop_at, orc_stats *st,
     compute_g(c, w->u, lam, w->zb);
     double mf = merit(c);
     island_merits(c, c->isl_mf);
+    if (best) {
+      /* islands still iterating whose final merit is above their least:
+       * that iterate is returned (positions from its u) */
+      int any = 0;
+      for (int i = 0; i < c->ni; i++) {
+        bflag[i] = !(c->isl_stop[i] >= 0 || !(mbest[i] < INFINITY) || c->isl_mf[i] <= mbest[i]);
+        if (!bflag[i]) continue;
+        any = 1;
+        c->isl_mf[i] = mbest[i];
+      }
+      for (int b = 0; b < c->nb; b++)
+        if (bflag[c->body_isl[b]])
+          for (int k = c->dof[b]; k < c->dof[b + 1]; k++) w->u[k] = ubest[k];
+      for (int r = 0; r < c->R; r++)
+        if (bflag[c->row_isl[r]]) lam[r] = lbest[r];
+      if (any) {
+        positions_from_u(c, w->u);
+        double s2 = 0.0;
+        for (int i = 0; i < c->ni; i++) s2 += c->isl_mf[i] * c->isl_mf[i];
+        mf = sqrt(s2);
+      }
+    }
     if (c->merit_n < 4096) c->merit_hist[c->merit_n++] = mf;
     if (st) { st->merit_final = mf; }
     /* commit: u^+ and q^+ */
@@ -1540,6 +1588,7 @@ static int newton(orc_ctx *c, const double *lambda0, int stop_at, orc_stats *st,
   if (st) { st->newton_done = n; st->cr_total = cr_total; st->merit0 = m0; st->merit_first = mfirst; }
   if (lam_out) memcpy(lam_out, lam, sizeof(double) * c->R);
   free(lam);
+  free(mbest); free(ubest); free(lbest); free(bflag);
   return 0;
 }
 

@@ -99,6 +99,11 @@ typedef struct {
                                merit of the current iterate (per island in island mode);
                                none: the damped step t = damping.  0 (the paper's results):
                                always the damped step */
+  int32_t best_iterate;     /* 1 (island mode only): each island that has not stopped returns
+                               the iterate of least merit among those its Newton iterations
+                               evaluated (the start included) when the final iterate's merit
+                               is larger (not in the paper: a safeguard against a diverging
+                               iteration); 0: the last iterate */
 } orc_params;
 
 typedef struct {

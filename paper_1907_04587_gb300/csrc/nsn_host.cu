@@ -127,6 +127,7 @@ struct nsn_ctx {
   int launches_per_step = 0;  // kernels executed in the last step
   struct Segments { int prefix = 0, head = 0, cr = 0, tail = 0, suffix = 0; } seg;  // kernels per graph segment
   int last_newton_n = 0;     // Newton loop bodies executed in the last step
+  int best_restored = 0;     // best_iterate: islands of the last step that returned an earlier iterate
   float tune_ms[3] = {0.f, 0.f, 0.f};  // body-pass times measured by the tuner for 4, 8, 16 lanes
   int forced_lanes = 0;      // nsn_set_body_lanes (0: tuned)
   int tuned_lanes = 0, tuned_nb = -1;   // the tuner's choice and the body count it was made for
@@ -496,6 +497,11 @@ void carve(Arena &A, Dev<T> &D, const Layout &L, int nb) {
   D.isl.mls = A.take<double>(ni);
   D.isl.rigid = A.take<unsigned char>(ni);
   D.isl.crk = A.take<int>(ni);
+  D.isl.mbest = A.take<double>(ni);
+  D.isl.bmark = A.take<int>(ni);
+  for (int k = 0; k < 6; k++) D.rub[k] = tk(L.nr);
+  for (int k = 0; k < 3; k++) D.pub[k] = tk(L.np);
+  D.lbest = tk(L.R);
   // line search: du, u and lambda at the head of the Newton iteration, dlambda
   for (int k = 0; k < 6; k++) { D.rdu[k] = tk(L.nr); D.ru0[k] = tk(L.nr); }
   for (int k = 0; k < 3; k++) { D.pdu[k] = tk(L.np); D.pu0[k] = tk(L.np); }
@@ -534,6 +540,7 @@ void fill_sizes(Dev<T> &D, const Layout &L, const nsn_config &cfg) {
   D.isl_on = cfg.island_stop ? 1 : 0;
   D.cone = cfg.cone_project ? 1 : 0;
   D.ls = cfg.line_search ? 1 : 0;
+  D.best = cfg.best_iterate && cfg.island_stop ? 1 : 0;
   D.crM = cfg.cr_iters;
   // grid-stride kernels get at most one wave: SMs x resident blocks per SM of
   // the kernel (so that no partial second wave trails the first)
@@ -874,6 +881,10 @@ struct Launcher {
     // plain start of Sec. 8.1: lambda^0 = 0 (u^0 = 0 is set by the begin kernels)
     if (D.R) cudaMemsetAsync(D.lam, 0, sizeof(T) * D.R, st);
     if (D.isl_on && D.ni) {
+      if (D.best) {   // least merits start above any finite merit (0x7f bytes: 1.4e306)
+        cudaMemsetAsync(D.isl.mbest, 0x7f, sizeof(double) * D.ni, st);
+        cudaMemsetAsync(D.isl.bmark, 0, sizeof(int) * D.ni, st);
+      }
       cudaMemsetAsync(D.isl.stop, 0xff, sizeof(int) * D.ni, st);
       cudaMemsetAsync(D.isl.acc, 0, sizeof(double) * ISL_ACC * D.ni, st);
       cudaMemsetAsync(D.isl.ls_pre, 0, sizeof(int) * D.ni, st);   // no line-search evaluation carries over
@@ -1011,6 +1022,12 @@ struct Launcher {
     rows(RM_RHS, 1);
     merit(IT_FINAL, 1);
     count++;
+    if (D.best && D.ni) {   // islands whose last iterate is not their least-merit one
+      const int n = D.nr + D.np + D.R;
+      k_best_restore<T><<<clampb(cdiv(std::max(n, 1), 256), D.max_blk), 256, 0, st>>>(D);
+      k_best_final<T><<<1, RED_THREADS, 0, st>>>(D);
+      count += 2;
+    }
     if (D.R) { k_copy<T><<<D.nblk_upd, BLOCK, 0, st>>>(D.lam_prev, D.lam, D.R); count++; }
   }
   void step() {  // eager launch of the whole step
@@ -1429,6 +1446,7 @@ nsn_status run_steps(nsn_ctx *c, int nsteps) {
   c->last.merit_final = sc.merit_final;
   c->last.ms = ms;
   c->last_newton_n = fl.newton_n;
+  c->best_restored = D.best ? fl.best_restored : 0;
   c->kept_buf = fl.newton_n & 1;   // entries of the final evaluation
   D.pscale_on = 0;                 // the linearize / solve / apply paths use the Jacobi preconditioner
   if (c->cfg.use_graph)
@@ -1444,7 +1462,8 @@ bool valid_cfg(const nsn_config *cfg) {
          (cfg->precision == NSN_FP32 || cfg->precision == NSN_FP64) && (cfg->ncp == 0 || cfg->ncp == 1) &&
          cfg->rscale >= 0 && cfg->rscale <= 2 && (cfg->cone_project == 0 || cfg->cone_project == 1) &&
          (cfg->island_stop == 0 || cfg->island_stop == 1) && (cfg->cr_resident == 0 || cfg->cr_resident == 1) &&
-         (cfg->line_search == 0 || cfg->line_search == 1);
+         (cfg->line_search == 0 || cfg->line_search == 1) && (cfg->best_iterate == 0 || cfg->best_iterate == 1) &&
+         (cfg->best_iterate == 0 || cfg->island_stop == 1);
 }
 
 template <typename T>
@@ -2394,6 +2413,12 @@ nsn_status nsn_collide_and_step(nsn_ctx *c, nsn_collider *col, int32_t nsteps, n
     if (s != NSN_OK) return s;
     if ((s = nsn_step(c, 1, stats)) != NSN_OK) return s;
   }
+  return NSN_OK;
+}
+
+nsn_status nsn_best_restored(nsn_ctx *c, int32_t *n) {
+  if (!c || !n) return NSN_ERR_INVALID_ARG;
+  *n = c->best_restored;
   return NSN_OK;
 }
 

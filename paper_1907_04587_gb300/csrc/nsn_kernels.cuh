@@ -62,6 +62,7 @@ struct Flags {
   // island still searches (kernels of a trial skip the islands that accepted,
   // and return at once when none searches); the OR of this trial's islands
   int ls_trial, ls_search, ls_next;
+  int best_restored;   // best_iterate: islands that returned an earlier iterate (k_best_final)
 };
 
 // iteration index / entry buffer taken from Flags::newton_n
@@ -99,6 +100,11 @@ struct IslState {
   double *mls;
   unsigned char *rigid;
   int *crk;                  // CR updates the island took in this Newton iteration
+  // best_iterate: least merit of the island's evaluated iterates, and 1 when
+  // the iterate at the head of this Newton iteration is that one (its u and
+  // lambda are copied before the iteration changes them)
+  double *mbest;
+  int *bmark;
 };
 
 // FP64 scalars kept on the device
@@ -182,6 +188,8 @@ struct Dev {
   int max_blk;       // resident 256-thread blocks of the device (SMs x threads per SM / 256):
                      // the grid cap and the capacity of part_body / part_row
   int res_work;      // 1: k_cr_resident counts its row-, entry- and body-iterations
+  int best;          // best_iterate (island mode)
+  T *rub[6], *pub[3], *lbest;   // best_iterate: u of rigid bodies and particles, lambda
                      // (only the timing entry point sets it)
   int G;             // lanes per body segment in the body pass (4, 8 or 16; tuned per scene)
   Scalars *sc;
@@ -1273,6 +1281,10 @@ __global__ void __launch_bounds__(BLOCK) k_body_pass(Dev<T> D, const T *__restri
         for (int k = 0; k < 6; k++) r6[k] = h * s[k] - D.rg[k][b];
         du[0] = r6[0] * im; du[1] = r6[1] * im; du[2] = r6[2] * im;
         sym3v(Si, r6 + 3, du + 3);
+        if (lane == 0 && D.best && D.isl.bmark[D.bisl_r[b]]) {
+#pragma unroll
+          for (int k = 0; k < 6; k++) D.rub[k][b] = D.ru[k][b];
+        }
         if (lane == 0 && D.ls) {   // line search: keep du and the iterate; k_ls_set commits
 #pragma unroll
           for (int k = 0; k < 6; k++) { D.rdu[k][b] = du[k]; D.ru0[k][b] = D.ru[k][b]; }
@@ -1419,10 +1431,12 @@ __global__ void __launch_bounds__(BLOCK) k_body_pass(Dev<T> D, const T *__restri
       if (MODE == BM_UPDATE) {
         if (lane == 0) {
           const T t = D.dampT;
+          const bool keep = D.best && D.isl.bmark[D.bisl_p[b]];
 #pragma unroll
           for (int k = 0; k < 3; k++) {
             const T du = (h * s[k] - D.pg[k][b]) * D.phinv[k][b];
             const T u = D.pu[k][b];
+            if (keep) D.pub[k][b] = u;
             D.puprev[k][b] = u;
             if (D.ls) {   // line search: keep du and the iterate; k_ls_set commits
               D.pdu[k][b] = du;
@@ -1763,10 +1777,16 @@ __device__ __forceinline__ bool isl_merit_one(const Dev<T> &D, int i, int n, int
   if (st >= 0) {                            // stopped: not evaluated, keeps its last merit
     m2 += D.isl.mf[i] * D.isl.mf[i];
     D.isl.crdone[i] = 1;
+    if (D.best) D.isl.bmark[i] = 0;
     return false;
   }
   m2 += an;
   D.isl.mf[i] = mn;
+  if (D.best) {                             // least merit so far: this iterate is kept
+    const bool better = mn < D.isl.mbest[i];
+    if (better) D.isl.mbest[i] = mn;
+    D.isl.bmark[i] = better ? 1 : 0;
+  }
   if (n == 0 && !D.warm) D.isl.m0[i] = mn;
   const double m0 = D.isl.m0[i];
   if (D.tol_rel > 0.0 && mn <= D.tol_rel * m0) { st = n; D.isl.stop[i] = n; }
@@ -2690,7 +2710,10 @@ template <typename T>
 __global__ void k_ls_begin(Dev<T> D) {
   if (D.fl->newton_stop) return;
   const int stride = gridDim.x * blockDim.x;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < D.R; i += stride) { D.lam0[i] = D.lam[i]; D.xs[i] = D.x[i]; }
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < D.R; i += stride) {
+    D.lam0[i] = D.lam[i]; D.xs[i] = D.x[i];
+    if (D.best && D.isl.bmark[D.risl[i]]) D.lbest[i] = D.lam[i];
+  }
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < D.ni; i += stride) D.isl.tacc[i] = -1.0;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     D.sc->ls_t = -1.0;
@@ -2807,6 +2830,7 @@ __global__ void k_lambda_update(Dev<T> D) {
     if (j < nc) {
       const int r = 3 * j;
       if (D.isl_on && D.isl.stop[D.risl[r]] >= 0) continue;
+      if (D.best && D.isl.bmark[D.risl[r]]) { D.lbest[r] = D.lam[r]; D.lbest[r + 1] = D.lam[r + 1]; D.lbest[r + 2] = D.lam[r + 2]; }
       T l0 = D.lam[r] + t * D.x[r], l1 = D.lam[r + 1] + t * D.x[r + 1], l2 = D.lam[r + 2] + t * D.x[r + 2];
       unsigned char bits = 0;
       if (D.cone) {
@@ -2819,8 +2843,86 @@ __global__ void k_lambda_update(Dev<T> D) {
     } else {
       const int r = 3 * nc + (j - nc);
       if (D.isl_on && D.isl.stop[D.risl[r]] >= 0) continue;
+      if (D.best && D.isl.bmark[D.risl[r]]) D.lbest[r] = D.lam[r];
       D.lam[r] += t * D.x[r];
     }
+  }
+}
+
+// best_iterate (island mode): an island that has not stopped and whose final
+// merit is above the least merit of its evaluated iterates returns that
+// iterate -- u, positions from u (as the update forms them) and lambda.
+template <typename T>
+__device__ __forceinline__ bool best_restore_island(const Dev<T> &D, int is) {
+  return D.isl.stop[is] < 0 && D.isl.mbest[is] < 1e300 && !(D.isl.mf[is] <= D.isl.mbest[is]);
+}
+
+template <typename T>
+__global__ void k_best_restore(Dev<T> D) {
+  const T h = D.hT;
+  const int n = D.nr + D.np + D.R;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    if (j < D.nr) {
+      const int b = j;
+      if (!best_restore_island(D, D.bisl_r[b])) continue;
+      T u[6], q0[4];
+#pragma unroll
+      for (int k = 0; k < 6; k++) { u[k] = D.rub[k][b]; D.ru[k][b] = u[k]; }
+#pragma unroll
+      for (int k = 0; k < 4; k++) q0[k] = D.rq0[k][b];
+#pragma unroll
+      for (int k = 0; k < 3; k++) D.rx[k][b] = D.rx0[k][b] + h * u[k];
+      const T *w = u + 3;
+      T qd[4];
+      qd[0] = T(0.5) * (-q0[1] * w[0] - q0[2] * w[1] - q0[3] * w[2]);
+      qd[1] = T(0.5) * (q0[0] * w[0] + q0[3] * w[1] - q0[2] * w[2]);
+      qd[2] = T(0.5) * (-q0[3] * w[0] + q0[0] * w[1] + q0[1] * w[2]);
+      qd[3] = T(0.5) * (q0[2] * w[0] - q0[1] * w[1] + q0[0] * w[2]);
+      T qn[4], nn = 0;
+#pragma unroll
+      for (int k = 0; k < 4; k++) { qn[k] = q0[k] + h * qd[k]; nn += qn[k] * qn[k]; }
+      nn = dsqrt(nn);
+#pragma unroll
+      for (int k = 0; k < 4; k++) D.rq[k][b] = qn[k] / nn;
+    } else if (j < D.nr + D.np) {
+      const int b = j - D.nr;
+      if (!best_restore_island(D, D.bisl_p[b])) continue;
+#pragma unroll
+      for (int k = 0; k < 3; k++) {
+        const T u = D.pub[k][b];
+        D.pu[k][b] = u;
+        D.px[k][b] = D.px0[k][b] + h * u;
+      }
+    } else {
+      const int r = j - D.nr - D.np;
+      if (best_restore_island(D, D.risl[r])) D.lam[r] = D.lbest[r];
+    }
+  }
+}
+
+// After k_best_restore (one block): the restored islands' final merits, and
+// the step's final merit from the islands' (a norm over disjoint parts), in
+// a fixed order; fl->best_restored counts the restored islands.
+template <typename T>
+__global__ void __launch_bounds__(RED_THREADS) k_best_final(Dev<T> D) {
+  __shared__ double sm[RED_THREADS];
+  __shared__ int cnt[RED_THREADS];
+  double s2 = 0.0;
+  int c = 0;
+  for (int i = threadIdx.x; i < D.ni; i += RED_THREADS) {
+    if (best_restore_island(D, i)) { D.isl.mf[i] = D.isl.mbest[i]; c++; }
+    s2 += D.isl.mf[i] * D.isl.mf[i];
+  }
+  sm[threadIdx.x] = s2;
+  cnt[threadIdx.x] = c;
+  __syncthreads();
+  for (int o = RED_THREADS / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) { sm[threadIdx.x] += sm[threadIdx.x + o]; cnt[threadIdx.x] += cnt[threadIdx.x + o]; }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    D.fl->best_restored = cnt[0];
+    if (cnt[0] > 0) D.sc->merit_final = sqrt(sm[0]);
   }
 }
 

@@ -43,7 +43,7 @@ class nsn_config(C.Structure):
                 ("rscale", C.c_int32), ("geom_stiffness", C.c_int32), ("precision", C.c_int32),
                 ("use_graph", C.c_int32), ("cone_project", C.c_int32), ("island_stop", C.c_int32),
                 ("cr_resident", C.c_int32), ("res_max_rows", C.c_int32), ("line_search", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("best_iterate", C.c_int32)]
 
 
 class nsn_stats(C.Structure):
@@ -117,6 +117,7 @@ def lib():
         "nsn_record_decisions": (C.c_int, [_vp, C.c_int32]),
         "nsn_get_prev_lambda": (C.c_int, [_vp, _dp]),
         "nsn_get_phase_times": (C.c_int, [_vp, _dp]),
+        "nsn_best_restored": (C.c_int, [_vp, C.POINTER(C.c_int32)]),
         "nsn_get_decisions": (C.c_int, [_vp, _vp, _vp, _vp]),
         "nsn_tuning": (C.c_int, [_vp, _ip, _fp]),
         "nsn_resident_info": (C.c_int, [_vp, _ip]),
@@ -414,7 +415,7 @@ def joint_runs(s):
 DEFAULTS = dict(h=1.0 / 60.0, gravity=(0.0, 0.0, -9.81), newton_iters=4, cr_iters=20, damping=0.75, eps=1e-6,
                 tol_rel=0.0, cr_tol_mode=0, ncp=0, rscale=2, geom_stiffness=1, precision=NSN_FP32, use_graph=1,
                 cone_project=0, island_stop=0, cr_resident=1, res_max_rows=384,
-                line_search=0)
+                line_search=0, best_iterate=0)
 
 
 def make_config(**params):
@@ -427,7 +428,7 @@ def make_config(**params):
     cfg.h = p["h"]
     cfg.gravity = (C.c_double * 3)(*p["gravity"])
     for k in ("newton_iters", "cr_iters", "cr_tol_mode", "ncp", "rscale", "geom_stiffness", "precision", "use_graph",
-              "cone_project", "island_stop", "cr_resident", "res_max_rows", "line_search"):
+              "cone_project", "island_stop", "cr_resident", "res_max_rows", "line_search", "best_iterate"):
         setattr(cfg, k, int(p[k]))
     for k in ("damping", "eps", "tol_rel"):
         setattr(cfg, k, float(p[k]))
@@ -511,6 +512,12 @@ class Solver:
         return out
 
     PHASES = ("collide", "save", "layout", "upload", "restore", "capture", "step")
+
+    def best_restored(self):
+        """Islands of the last step that returned an earlier, lower-merit iterate (best_iterate)."""
+        n = C.c_int32()
+        _check(self.ctx, lib().nsn_best_restored(self.ctx, C.byref(n)), "nsn_best_restored")
+        return int(n.value)
 
     def phase_times(self):
         """Host milliseconds of the phases of the last rebuild and step (nsn_get_phase_times)."""

@@ -39,6 +39,7 @@ def test_config_struct_and_defaults(libnsn):
     assert abs(cfg.h - 1.0 / 60.0) < 1e-15 and cfg.newton_iters == 4 and cfg.cr_iters == 20
     assert cfg.damping == 0.75 and cfg.eps == 1e-6 and cfg.precision == nsn.NSN_FP32
     assert cfg.cone_project == 0 and cfg.island_stop == 0    # the printed method, one system
+    assert cfg.line_search == 0 and cfg.best_iterate == 0
     # h, gravity[3], 2 ints, damping, eps, tol_rel, 8 ints
     assert ctypes.sizeof(nsn.nsn_config) == 8 * 4 + 4 * 2 + 8 * 3 + 4 * 12
 
@@ -48,6 +49,9 @@ def test_invalid_arguments_are_rejected_without_gpu(libnsn):
     assert libnsn.nsn_create(None, None, ctypes.byref(out)) == 1
     cfg = nsn.nsn_default_config()
     cfg.h = -1.0
+    assert libnsn.nsn_create(ctypes.byref(cfg), None, ctypes.byref(out)) == 1
+    cfg = nsn.nsn_default_config()
+    cfg.best_iterate = 1                   # island mode required
     assert libnsn.nsn_create(ctypes.byref(cfg), None, ctypes.byref(out)) == 1
     assert libnsn.nsn_destroy(None) == 1
 

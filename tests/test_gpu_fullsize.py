@@ -17,7 +17,7 @@ pytestmark = pytest.mark.gpu
 
 H = 1.0 / 60.0
 G = 9.81
-PRM = dict(newton_iters=30, cr_iters=400, tol_rel=1e-6, island_stop=1, cone_project=1, line_search=1)
+PRM = dict(newton_iters=30, cr_iters=400, tol_rel=1e-6, island_stop=1, cone_project=1, line_search=1, best_iterate=1)
 SAMPLE = tuple(int(e) for e in np.linspace(0, 4095, 64))   # 64 environments spread over the batch
 
 
