@@ -12,24 +12,26 @@ by side, each stops when its merit reaches 1e-6 of its own zero-iterate merit
 counts only if every island of the environment reached the tolerance.  The
 trajectory advances from the seeded start state (no reset between steps).
   value     converged env-steps/s, state resident in HBM (device-timed), of
-            the learned + batched form: per island the least-merit start among
-            the network's lambda^0, the previous step's multipliers (its
-            fallback) and zero; Newton steps with the back-tracking line search
-            of Sec. 8.1 (trials t = 1 .. 1/16, else the damped 0.75; --line-search
-            0: the damped step), projected onto the friction cone (option
-            cone_project); CR per island in shared memory where it fits
-  arms      the same measurement for: the headline with the network's
-            preconditioner scale on the contacts' Jacobi entries, the headline
-            in the FP64 build, the
-            headline with the damped step, the
-            plain batched method (zero start; damped and with the line
-            search), the printed update, the previous-step start alone, the
-            first step after an environment reset with the zero / learned
-            start, and the ablations of Sec. 7 (min-map NCP; r = h^2 and r = 1
-            instead of the effective-mass r), each on the first step after a
-            reset with the zero start (compare after_reset_zero): on the
-            advancing trajectory the min-map variant diverges, in the FP64
-            oracle as well
+            the batched form with the previous step's multipliers as the start
+            (per island, kept if not worse than zero), Newton steps with the
+            back-tracking line search of Sec. 8.1 (trials t = 1 .. 1/16, else
+            the damped 0.75; --line-search 0: the damped step), projected onto
+            the friction cone (option cone_project), the least-merit iterate
+            of an island that does not reach the tolerance (best_iterate);
+            CR per island in shared memory where it fits; contacts generated
+            on the GPU at the start of every step (--contacts fixed: the
+            scene's contacts throughout)
+  arms      the same measurement for: the learned start (per-contact BF16
+            network, previous-step start as fallback; with and without its
+            preconditioner scale), the headline in the FP64 build, the
+            headline with the damped step, the plain batched method (zero
+            start; damped and with the line search), the printed update, the
+            previous-step start with the damped step, the first step after an
+            environment reset with the zero / learned start, and the ablations
+            of Sec. 7 (min-map NCP; r = h^2 and r = 1 instead of the
+            effective-mass r), each on the first step after a reset with the
+            zero start (compare after_reset_zero): on the advancing trajectory
+            the min-map variant diverges, in the FP64 oracle as well
   e2e       converged env-steps/s through the C ABI with host buffers: host->
             device copy of the state, the step, device->host copy of the state
             (the state makes that round trip every step)
@@ -431,8 +433,8 @@ def oracle_rate(workload, seed, budget_s, newton, cr, cores=None):
     el = max(r[2] for r in res)
     steps = sum(r[1] for r in res)
     if workload.startswith("batched"):
-        sample = (f"{cores} x {SAMPLE_ENVS} environments of the same distribution (seed {seed}*1000+k "
-                  f"for process k > 0), one process per host core")
+        sample = (f"{cores} x {SAMPLE_ENVS} environments of the same distribution (process k: seed "
+                  f"{seed} for k = 0, else 1000 x {seed} + k), one process per host core")
     else:
         sample = "the full scene, one host core"
     return conv / el, dict(kind="oracle", cores=cores,
@@ -709,7 +711,8 @@ def run_ours(args, rank, world, local_rank):
         arms = {}
         if args.arms:
             # (name, cone projection, warm start, reset every step, NCP function, r strategy, line search)
-            for name, cone, wm, reset, ncp, rs, ls in (("learned_precond", 1, nsn.NSN_WARM_LEARNED | nsn.NSN_WARM_PRECOND,
+            for name, cone, wm, reset, ncp, rs, ls in (("learned_warm_start", 1, nsn.NSN_WARM_LEARNED, False, 0, 2, LS),
+                                                   ("learned_precond", 1, nsn.NSN_WARM_LEARNED | nsn.NSN_WARM_PRECOND,
                                                     False, 0, 2, LS),
                                                    ("fp64_bulk", 1, warm_names[warm], False, 0, 2, LS),
                                                    ("damped_update" if LS else "line_search", 1, warm_names[warm],
@@ -828,8 +831,9 @@ def main():
     ap.add_argument("--newton", type=int, default=0)
     ap.add_argument("--cr", type=int, default=0)
     ap.add_argument("--arms", type=int, default=1, help="also measure the plain, as-printed and reset arms")
-    ap.add_argument("--warm", default="learned", choices=["learned", "prev", "zero"],
-                    help="warm start of the headline arm (learned: network with previous-step fallback)")
+    ap.add_argument("--warm", default="prev", choices=["learned", "prev", "zero"],
+                    help="warm start of the headline arm (prev: the previous step's multipliers; learned: the "
+                         "network with the previous-step start as fallback)")
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--ref-budget", type=float, default=60.0, help="seconds of oracle work for --impl reference")
     ap.add_argument("--eager", type=int, default=0,

@@ -11,7 +11,6 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
-#include <functional>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -90,6 +89,21 @@ struct Layout {
   std::vector<int> gres, gisl, grp_of;
   std::vector<int> isl_order;       // island ids in the internal (rank) order
   int n_streamed = 0;               // islands with rows that the resident CR does not take
+  // scratch of the layout build (kept, like the arrays above, across rebuilds:
+  // contacts are regenerated every step and their allocations are reused)
+  std::vector<int> s_key, s_start, s_rank, s_size, s_cnt, s_fill, s_aux;
+  // a new build: every array emptied, its allocation kept
+  void reset() {
+    for (std::vector<int> *v : {&bmap, &rig_of, &par_of, &eslot, &rseg, &vseg, &re0, &re1, &te, &body_isl, &risl,
+                                &bisl_r, &bisl_p, &cperm, &jperm, &tperm, &row_abi, &tb_kind, &tb_abi, &ires, &gres,
+                                &gisl, &grp_of, &isl_order})
+      v->clear();
+    tb_rec.clear();
+    isres.clear();
+    isl_rigid.clear();
+    nr = np = nc = nj = nt = R = Rpair = ER = EV = ni = 0;
+    n_res = res_rows = res_ent = res_bod = n_streamed = 0;
+  }
 };
 
 struct MlpState {
@@ -108,6 +122,37 @@ struct MlpState {
 };
 
 }  // namespace
+
+// Pinned host staging for the arrays a (re)build writes to the device: chunks
+// of page-locked memory kept for the context's lifetime and reused by every
+// rebuild (contacts are regenerated every step), so that the host fills no
+// fresh pages and the copies run at pinned-memory speed.  A rebuild rewinds
+// it; its copies complete before the rebuild returns (stream synchronised).
+struct PinnedStage {
+  struct Chunk { unsigned char *p; size_t size; };
+  std::vector<Chunk> chunks;
+  size_t cur = 0, off = 0;
+  void rewind() { cur = 0; off = 0; }
+  template <typename X>
+  X *take(size_t n) {
+    const size_t bytes = ((n ? n : 1) * sizeof(X) + 255) & ~size_t(255);
+    while (cur < chunks.size() && off + bytes > chunks[cur].size) { cur++; off = 0; }
+    if (cur == chunks.size()) {
+      Chunk ch{nullptr, std::max<size_t>(bytes, size_t(64) << 20)};
+      if (cudaMallocHost(reinterpret_cast<void **>(&ch.p), ch.size) != cudaSuccess) return nullptr;
+      chunks.push_back(ch);
+      off = 0;
+    }
+    X *r = reinterpret_cast<X *>(chunks[cur].p + off);
+    off += bytes;
+    return r;
+  }
+  void release() {
+    for (Chunk &ch : chunks) cudaFreeHost(ch.p);
+    chunks.clear();
+    rewind();
+  }
+};
 
 struct nsn_ctx {
   nsn_config cfg;
@@ -156,6 +201,9 @@ struct nsn_ctx {
   unsigned char *dlog_buf = nullptr;   // the log on the device (iters x (rows + islands) bytes)
   size_t dlog_bytes = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  PinnedStage stage;         // pinned staging of the (re)build's uploads
+  std::vector<double> lam_abi, lam_abi2;   // previous multipliers in ABI order across a rebuild
+  std::vector<int> key_end, key_list;      // old contacts bucketed by body a (key matching)
   // host wall time (ms) of the phases of the last rebuild / step, NSN_PHASE_*
   double phase_ms[NSN_PHASES] = {};
   std::string err;
@@ -238,12 +286,14 @@ void find_islands(const HostScene &S, Layout &L, int nb) {
 
 // stable order of n items by an integer key in [0, K) (counting sort: the
 // layout is rebuilt whenever contacts are regenerated, so it stays linear)
-std::vector<int> order_by(int n, int K, const std::function<int(int)> &key) {
-  std::vector<int> k(n), start(size_t(K) + 1, 0), o(n);
+template <typename Key>
+void order_by(int n, int K, const Key &key, std::vector<int> &o, std::vector<int> &k, std::vector<int> &start) {
+  k.resize(n);
+  start.assign(size_t(K) + 1, 0);
+  o.resize(n);
   for (int i = 0; i < n; i++) { k[i] = key(i); start[size_t(k[i]) + 1]++; }
   for (int j = 0; j < K; j++) start[size_t(j) + 1] += start[j];
   for (int i = 0; i < n; i++) o[start[k[i]]++] = i;
-  return o;
 }
 
 // ------------------------------------------------------------------------------------
@@ -252,23 +302,25 @@ std::vector<int> order_by(int n, int K, const std::function<int(int)> &key) {
 nsn_status build_layout(nsn_ctx *c) {
   HostScene &S = c->scene;
   Layout &L = c->L;
-  L = Layout();
+  L.reset();
   const int nb = int(S.kind.size());
   find_islands(S, L, nb);
   // Internal island order: largest islands first (ties by id).  Islands that
   // keep iterating after most have stopped are the large ones (long chains),
   // so they cluster and blocks of finished islands are skipped as a whole.
-  std::vector<int> isl_size(L.ni, 0), rank(L.ni);
+  std::vector<int> &isl_size = L.s_size, &rank = L.s_rank;
+  isl_size.assign(L.ni, 0);
+  rank.resize(L.ni);
   for (int b = 0; b < nb; b++) isl_size[L.body_isl[b]]++;
   {
     const int maxsz = L.ni ? *std::max_element(isl_size.begin(), isl_size.end()) : 0;
-    std::vector<int> o = order_by(L.ni, maxsz + 1, [&](int i) { return maxsz - isl_size[i]; });
-    for (int k = 0; k < L.ni; k++) rank[o[k]] = k;
-    L.isl_order = o;
+    order_by(L.ni, maxsz + 1, [&](int i) { return maxsz - isl_size[i]; }, L.isl_order, L.s_key, L.s_start);
+    for (int k = 0; k < L.ni; k++) rank[L.isl_order[k]] = k;
   }
   // bodies in island order (rigid and particle numbered separately)
   L.bmap.resize(nb);
-  for (int i : order_by(nb, std::max(L.ni, 1), [&](int b) { return rank[L.body_isl[b]]; })) {
+  order_by(nb, std::max(L.ni, 1), [&](int b) { return rank[L.body_isl[b]]; }, L.s_aux, L.s_key, L.s_start);
+  for (int i : L.s_aux) {
     if (S.kind[i] == NSN_RIGID) { L.bmap[i] = L.nr++; L.rig_of.push_back(i); }
     else { L.bmap[i] = -2 - L.np++; L.par_of.push_back(i); }
   }
@@ -288,9 +340,11 @@ nsn_status build_layout(nsn_ctx *c) {
   // constraints in island order
   auto isl2 = [&](int a, int b) { return L.body_isl[a >= 0 ? a : b]; };
   const int K = std::max(L.ni, 1);
-  L.cperm = order_by(L.nc, K, [&](int i) { return rank[isl2(S.contacts[i].body_a, S.contacts[i].body_b)]; });
-  L.jperm = order_by(L.nj, K, [&](int i) { return rank[isl2(S.joints[i].body_a, S.joints[i].body_b)]; });
-  L.tperm = order_by(L.nt, K, [&](int i) { return rank[L.body_isl[L.tb_rec[i]->v[0]]]; });
+  order_by(L.nc, K, [&](int i) { return rank[isl2(S.contacts[i].body_a, S.contacts[i].body_b)]; }, L.cperm, L.s_key,
+           L.s_start);
+  order_by(L.nj, K, [&](int i) { return rank[isl2(S.joints[i].body_a, S.joints[i].body_b)]; }, L.jperm, L.s_key,
+           L.s_start);
+  order_by(L.nt, K, [&](int i) { return rank[L.body_isl[L.tb_rec[i]->v[0]]]; }, L.tperm, L.s_key, L.s_start);
   L.row_abi.resize(L.R);
   L.risl.resize(L.R);
   for (int ci = 0; ci < L.nc; ci++) {
@@ -313,58 +367,67 @@ nsn_status build_layout(nsn_ctx *c) {
   L.bisl_p.resize(L.np);
   for (int i = 0; i < L.nr; i++) L.bisl_r[i] = L.body_isl[L.rig_of[i]];
   for (int i = 0; i < L.np; i++) L.bisl_p[i] = L.body_isl[L.par_of[i]];
-  // (row, side, body) list
-  struct Side { int row, slot, enc; };
-  std::vector<Side> sides;
-  sides.reserve(size_t(L.R) * 2 + size_t(L.nt) * 6);
+  // entries: one per (row, side) with a body, sorted by body (rigid, then
+  // particle) and within a body by row -- a counting sort in two passes over
+  // the constraints in row order (count, then place)
+  std::vector<int> &rcnt = L.rseg, &pcnt = L.vseg;
+  rcnt.assign(size_t(L.nr) + 1, 0);
+  pcnt.assign(size_t(L.np) + 1, 0);
+  auto count = [&](int enc, int n) {
+    if (enc >= 0) rcnt[size_t(enc) + 1] += n;
+    else pcnt[size_t(-enc - 2) + 1] += n;
+  };
   for (int ci = 0; ci < L.nc; ci++) {
-    int a = S.contacts[L.cperm[ci]].body_a, b = S.contacts[L.cperm[ci]].body_b;
-    for (int k = 0; k < 3; k++) {
-      if (a >= 0) sides.push_back({3 * ci + k, 0, L.bmap[a]});
-      if (b >= 0) sides.push_back({3 * ci + k, 1, L.bmap[b]});
-    }
+    const nsn_contact &r = S.contacts[L.cperm[ci]];
+    if (r.body_a >= 0) count(L.bmap[r.body_a], 3);
+    if (r.body_b >= 0) count(L.bmap[r.body_b], 3);
   }
   for (int j = 0; j < L.nj; j++) {
-    int a = S.joints[L.jperm[j]].body_a, b = S.joints[L.jperm[j]].body_b;
-    for (int k = 0; k < 5; k++) {
-      int row = 3 * L.nc + 5 * j + k;
-      if (a >= 0) sides.push_back({row, 0, L.bmap[a]});
-      if (b >= 0) sides.push_back({row, 1, L.bmap[b]});
-    }
+    const nsn_revolute &r = S.joints[L.jperm[j]];
+    if (r.body_a >= 0) count(L.bmap[r.body_a], 5);
+    if (r.body_b >= 0) count(L.bmap[r.body_b], 5);
   }
   for (int t = 0; t < L.nt; t++)
-    for (int k = 0; k < 3; k++)
-      for (int q = 0; q < 4; q++) sides.push_back({L.Rpair + 3 * t + k, q, L.bmap[L.tb_rec[L.tperm[t]]->v[q]]});
-  // counting sort by body: rigid then particle
-  std::vector<int> rcnt(L.nr + 1, 0), pcnt(L.np + 1, 0);
-  for (auto &s : sides) {
-    if (s.enc >= 0) rcnt[s.enc + 1]++;
-    else pcnt[-s.enc - 2 + 1]++;
-  }
-  for (int i = 0; i < L.nr; i++) rcnt[i + 1] += rcnt[i];
-  for (int i = 0; i < L.np; i++) pcnt[i + 1] += pcnt[i];
-  L.rseg = rcnt;
-  L.vseg = pcnt;
+    for (int q = 0; q < 4; q++) count(L.bmap[L.tb_rec[L.tperm[t]]->v[q]], 3);
+  for (int i = 0; i < L.nr; i++) rcnt[size_t(i) + 1] += rcnt[i];
+  for (int i = 0; i < L.np; i++) pcnt[size_t(i) + 1] += pcnt[i];
   L.ER = rcnt[L.nr];
   L.EV = pcnt[L.np];
-  L.eslot.assign(size_t(L.ER) + L.EV, 0);
+  L.eslot.resize(size_t(L.ER) + L.EV);
   L.re0.assign(L.Rpair, -1);
   L.re1.assign(L.Rpair, -1);
   L.te.assign(size_t(12) * L.nt, -1);
-  std::vector<int> rfill(rcnt.begin(), rcnt.end() - 1), pfill(pcnt.begin(), pcnt.end() - 1);
-  // sides were appended in row order, so entries within a body stay row-ordered
-  for (auto &s : sides) {
-    int e;
-    if (s.enc >= 0) e = rfill[s.enc]++;
-    else e = L.ER + pfill[-s.enc - 2]++;
-    if (s.row < L.Rpair) {
-      (s.slot == 0 ? L.re0 : L.re1)[s.row] = e;
-      L.eslot[e] = 2 * s.row + s.slot;
-    } else {
-      int t = (s.row - L.Rpair) / 3, k = (s.row - L.Rpair) % 3;
-      L.te[12 * t + 4 * k + s.slot] = e;
-      L.eslot[e] = 2 * L.Rpair + 12 * t + 4 * k + s.slot;
+  std::vector<int> &fill = L.s_fill;
+  fill.resize(size_t(L.nr) + L.np);
+  for (int i = 0; i < L.nr; i++) fill[i] = rcnt[i];
+  for (int i = 0; i < L.np; i++) fill[size_t(L.nr) + i] = L.ER + pcnt[i];
+  auto place = [&](int enc) { return enc >= 0 ? fill[enc]++ : fill[size_t(L.nr) + (-enc - 2)]++; };
+  for (int ci = 0; ci < L.nc; ci++) {
+    const nsn_contact &r = S.contacts[L.cperm[ci]];
+    const int ea = r.body_a >= 0 ? L.bmap[r.body_a] : 0, eb = r.body_b >= 0 ? L.bmap[r.body_b] : 0;
+    for (int k = 0; k < 3; k++) {
+      const int row = 3 * ci + k;
+      if (r.body_a >= 0) { const int e = place(ea); L.re0[row] = e; L.eslot[e] = 2 * row; }
+      if (r.body_b >= 0) { const int e = place(eb); L.re1[row] = e; L.eslot[e] = 2 * row + 1; }
     }
+  }
+  for (int j = 0; j < L.nj; j++) {
+    const nsn_revolute &r = S.joints[L.jperm[j]];
+    const int ea = r.body_a >= 0 ? L.bmap[r.body_a] : 0, eb = r.body_b >= 0 ? L.bmap[r.body_b] : 0;
+    for (int k = 0; k < 5; k++) {
+      const int row = 3 * L.nc + 5 * j + k;
+      if (r.body_a >= 0) { const int e = place(ea); L.re0[row] = e; L.eslot[e] = 2 * row; }
+      if (r.body_b >= 0) { const int e = place(eb); L.re1[row] = e; L.eslot[e] = 2 * row + 1; }
+    }
+  }
+  for (int t = 0; t < L.nt; t++) {
+    const nsn_tet &r = *L.tb_rec[L.tperm[t]];
+    for (int k = 0; k < 3; k++)
+      for (int q = 0; q < 4; q++) {
+        const int e = place(L.bmap[r.v[q]]);
+        L.te[12 * t + 4 * k + q] = e;
+        L.eslot[e] = 2 * L.Rpair + 12 * t + 4 * k + q;
+      }
   }
   // per-island ranges (each island's bodies, contacts and joints are
   // contiguous in the internal order) and eligibility for the resident CR
@@ -577,6 +640,9 @@ void fill_sizes(Dev<T> &D, const Layout &L, const nsn_config &cfg) {
     const size_t smem = res_smem_bytes<T>(L.res_rows, L.res_ent, L.res_bod);
     int per_sm = 0;
     const void *kern = reinterpret_cast<const void *>(&k_cr_resident<T>);
+    // all of the SM's unified L1 / shared memory as shared memory: the
+    // resident groups are bound by it (the kernel reads no global data in its loop)
+    cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, int(cudaSharedmemCarveoutMaxShared));
     if (smem <= 200 * 1024 &&
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) == cudaSuccess &&
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, RES_THREADS, smem) == cudaSuccess && per_sm > 0) {
@@ -595,79 +661,97 @@ nsn_status upload(nsn_ctx *c, Dev<T> &D) {
   const Layout &L = c->L;
   const HostScene &S = c->scene;
   cudaStream_t st = c->stream;
-  std::vector<T> buf;
-  auto put = [&](T *dst, const std::vector<T> &src) -> cudaError_t {
-    if (src.empty()) return cudaSuccess;
-    return cudaMemcpyAsync(dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, st);
+  // per-field host arrays are written into the pinned stage and copied from there
+  PinnedStage &P = c->stage;
+  P.rewind();
+  bool oom = false;
+  auto stage = [&](size_t n) {
+    T *q = P.take<T>(n);
+    if (!q) oom = true;
+    return q;
   };
-  auto puti = [&](int *dst, const std::vector<int> &src) -> cudaError_t {
-    if (src.empty()) return cudaSuccess;
-    return cudaMemcpyAsync(dst, src.data(), src.size() * sizeof(int), cudaMemcpyHostToDevice, st);
+  auto stagei = [&](size_t n) {
+    int *q = P.take<int>(n);
+    if (!q) oom = true;
+    return q;
   };
+  auto put = [&](T *dst, const T *src, size_t n) -> cudaError_t {
+    if (!n) return cudaSuccess;
+    return cudaMemcpyAsync(dst, src, n * sizeof(T), cudaMemcpyHostToDevice, st);
+  };
+  auto puti = [&](int *dst, const int *src, size_t n) -> cudaError_t {
+    if (!n) return cudaSuccess;
+    return cudaMemcpyAsync(dst, src, n * sizeof(int), cudaMemcpyHostToDevice, st);
+  };
+  auto putv = [&](int *dst, const std::vector<int> &v) { return puti(dst, v.data(), v.size()); };
+  const size_t nr = L.nr, np = L.np, nc = L.nc, nj = L.nj, nt = L.nt;
   // rigid static data
   {
-    std::vector<T> m(L.nr), im(L.nr), I[3];
-    for (int k = 0; k < 3; k++) I[k].resize(L.nr);
-    for (int i = 0; i < L.nr; i++) {
-      int id = L.rig_of[i];
+    T *m = stage(nr), *im = stage(nr), *I0 = stage(nr), *I1 = stage(nr), *I2 = stage(nr), *pm = stage(np);
+    if (oom) return fail(c, NSN_ERR_OUT_OF_MEMORY, "pinned staging of the upload");
+    T *I[3] = {I0, I1, I2};
+    for (size_t i = 0; i < nr; i++) {
+      const int id = L.rig_of[i];
       m[i] = T(S.mass[id]);
       im[i] = T(1.0 / double(S.mass[id]));
-      for (int k = 0; k < 3; k++) I[k][i] = T(S.inertia[3 * id + k]);
+      for (int k = 0; k < 3; k++) I[k][i] = T(S.inertia[3 * size_t(id) + k]);
     }
-    CUDA_TRY(c, put(D.rm, m)); CUDA_TRY(c, put(D.rinvm, im));
-    for (int k = 0; k < 3; k++) CUDA_TRY(c, put(D.rIb[k], I[k]));
-    std::vector<T> pm(L.np);
-    for (int i = 0; i < L.np; i++) pm[i] = T(S.mass[L.par_of[i]]);
-    CUDA_TRY(c, put(D.pm, pm));
+    CUDA_TRY(c, put(D.rm, m, nr)); CUDA_TRY(c, put(D.rinvm, im, nr));
+    for (int k = 0; k < 3; k++) CUDA_TRY(c, put(D.rIb[k], I[k], nr));
+    for (size_t i = 0; i < np; i++) pm[i] = T(S.mass[L.par_of[i]]);
+    CUDA_TRY(c, put(D.pm, pm, np));
   }
-  CUDA_TRY(c, puti(D.eslot, L.eslot));
+  CUDA_TRY(c, putv(D.eslot, L.eslot));
   // slots of world sides are never written and must read as zero
   CUDA_TRY(c, cudaMemsetAsync(D.t, 0, sizeof(T) * std::max(2 * L.Rpair + 12 * L.nt, 1), st));
   CUDA_TRY(c, cudaMemsetAsync(D.t2, 0, sizeof(T) * std::max(2 * L.Rpair + 12 * L.nt, 1), st));
-  CUDA_TRY(c, puti(D.rseg, L.rseg));
-  CUDA_TRY(c, puti(D.vseg, L.vseg));
-  CUDA_TRY(c, puti(D.re0, L.re0));
-  CUDA_TRY(c, puti(D.re1, L.re1));
-  CUDA_TRY(c, puti(D.te, L.te));
+  CUDA_TRY(c, putv(D.rseg, L.rseg));
+  CUDA_TRY(c, putv(D.vseg, L.vseg));
+  CUDA_TRY(c, putv(D.re0, L.re0));
+  CUDA_TRY(c, putv(D.re1, L.re1));
+  CUDA_TRY(c, putv(D.te, L.te));
   // contacts
   {
-    std::vector<int> a(L.nc), b(L.nc);
-    std::vector<T> pa[3], pb[3], n[3], d(L.nc), mu(L.nc);
-    for (int k = 0; k < 3; k++) { pa[k].resize(L.nc); pb[k].resize(L.nc); n[k].resize(L.nc); }
-    for (int i = 0; i < L.nc; i++) {
+    int *a = stagei(nc), *b = stagei(nc);
+    T *f[11];
+    for (int k = 0; k < 11; k++) f[k] = stage(nc);
+    if (oom) return fail(c, NSN_ERR_OUT_OF_MEMORY, "pinned staging of the upload");
+    for (size_t i = 0; i < nc; i++) {
       const nsn_contact &r = S.contacts[L.cperm[i]];
       a[i] = r.body_a >= 0 ? L.bmap[r.body_a] : -1;
       b[i] = r.body_b >= 0 ? L.bmap[r.body_b] : -1;
-      double nn = std::sqrt(double(r.n[0]) * r.n[0] + double(r.n[1]) * r.n[1] + double(r.n[2]) * r.n[2]);
-      (void)nn;
-      for (int k = 0; k < 3; k++) { pa[k][i] = T(r.pa[k]); pb[k][i] = T(r.pb[k]); n[k][i] = T(r.n[k]); }
-      d[i] = T(r.d); mu[i] = T(r.mu);
+      for (int k = 0; k < 3; k++) { f[k][i] = T(r.pa[k]); f[3 + k][i] = T(r.pb[k]); f[6 + k][i] = T(r.n[k]); }
+      f[9][i] = T(r.d); f[10][i] = T(r.mu);
     }
-    CUDA_TRY(c, puti(D.cba, a)); CUDA_TRY(c, puti(D.cbb, b));
-    for (int k = 0; k < 3; k++) { CUDA_TRY(c, put(D.cpa[k], pa[k])); CUDA_TRY(c, put(D.cpb[k], pb[k])); CUDA_TRY(c, put(D.cn[k], n[k])); }
-    CUDA_TRY(c, put(D.cdd, d)); CUDA_TRY(c, put(D.cmu, mu));
+    CUDA_TRY(c, puti(D.cba, a, nc)); CUDA_TRY(c, puti(D.cbb, b, nc));
+    for (int k = 0; k < 3; k++) {
+      CUDA_TRY(c, put(D.cpa[k], f[k], nc)); CUDA_TRY(c, put(D.cpb[k], f[3 + k], nc)); CUDA_TRY(c, put(D.cn[k], f[6 + k], nc));
+    }
+    CUDA_TRY(c, put(D.cdd, f[9], nc)); CUDA_TRY(c, put(D.cmu, f[10], nc));
   }
   // joints
   {
-    std::vector<int> a(L.nj), b(L.nj);
-    std::vector<T> pa[3], pb[3], xa[3], xb[3], e(L.nj);
-    for (int k = 0; k < 3; k++) { pa[k].resize(L.nj); pb[k].resize(L.nj); xa[k].resize(L.nj); xb[k].resize(L.nj); }
-    for (int i = 0; i < L.nj; i++) {
+    int *a = stagei(nj), *b = stagei(nj), *jk = stagei(nj);
+    T *f[13];
+    for (int k = 0; k < 13; k++) f[k] = stage(nj);
+    if (oom) return fail(c, NSN_ERR_OUT_OF_MEMORY, "pinned staging of the upload");
+    for (size_t i = 0; i < nj; i++) {
       const nsn_revolute &r = S.joints[L.jperm[i]];
       a[i] = r.body_a >= 0 ? L.bmap[r.body_a] : -1;
       b[i] = r.body_b >= 0 ? L.bmap[r.body_b] : -1;
-      for (int k = 0; k < 3; k++) { pa[k][i] = T(r.pa[k]); pb[k][i] = T(r.pb[k]); xa[k][i] = T(r.axis_a[k]); xb[k][i] = T(r.axis_b[k]); }
-      e[i] = T(r.compliance);
+      for (int k = 0; k < 3; k++) {
+        f[k][i] = T(r.pa[k]); f[3 + k][i] = T(r.pb[k]); f[6 + k][i] = T(r.axis_a[k]); f[9 + k][i] = T(r.axis_b[k]);
+      }
+      f[12][i] = T(r.compliance);
+      jk[i] = S.jkind[L.jperm[i]];
     }
-    CUDA_TRY(c, puti(D.jba, a)); CUDA_TRY(c, puti(D.jbb, b));
+    CUDA_TRY(c, puti(D.jba, a, nj)); CUDA_TRY(c, puti(D.jbb, b, nj));
     for (int k = 0; k < 3; k++) {
-      CUDA_TRY(c, put(D.jpa[k], pa[k])); CUDA_TRY(c, put(D.jpb[k], pb[k]));
-      CUDA_TRY(c, put(D.jaxa[k], xa[k])); CUDA_TRY(c, put(D.jaxb[k], xb[k]));
+      CUDA_TRY(c, put(D.jpa[k], f[k], nj)); CUDA_TRY(c, put(D.jpb[k], f[3 + k], nj));
+      CUDA_TRY(c, put(D.jaxa[k], f[6 + k], nj)); CUDA_TRY(c, put(D.jaxb[k], f[9 + k], nj));
     }
-    CUDA_TRY(c, put(D.je, e));
-    std::vector<int> jk(L.nj);
-    for (int i = 0; i < L.nj; i++) jk[i] = L.jperm.empty() ? 0 : S.jkind[L.jperm[i]];
-    CUDA_TRY(c, puti(D.jkind, jk));
+    CUDA_TRY(c, put(D.je, f[12], nj));
+    CUDA_TRY(c, puti(D.jkind, jk, nj));
   }
   // tets: rest-shape inverse, volume and stable Neo-Hookean constants (App. B):
   // C1 = mu/2, D1 = lambda/2 (Lame), alpha = 1 + mu/lambda (rest state stress
@@ -677,9 +761,10 @@ nsn_status upload(nsn_ctx *c, Dev<T> &D) {
   // the volumetric mode, 2 mu on the two deviatoric normal modes and mu on the
   // three shears, so (V_e K_e)^-1 is diagonal in that basis.
   {
-    std::vector<int> v(4 * L.nt), kind(L.nt);
-    std::vector<T> Dmi(9 * L.nt), Ve(L.nt), C1(L.nt), D1(L.nt), al(L.nt);
-    for (int t = 0; t < L.nt; t++) {
+    int *v = stagei(4 * nt), *kind = stagei(nt);
+    T *Dmi = stage(9 * nt), *Ve = stage(nt), *C1 = stage(nt), *D1 = stage(nt), *al = stage(nt);
+    if (oom) return fail(c, NSN_ERR_OUT_OF_MEMORY, "pinned staging of the upload");
+    for (size_t t = 0; t < nt; t++) {
       const nsn_tet &r = *L.tb_rec[L.tperm[t]];
       kind[t] = L.tb_kind[L.tperm[t]];
       for (int q = 0; q < 4; q++) v[4 * t + q] = -L.bmap[r.v[q]] - 2;
@@ -706,31 +791,33 @@ nsn_status upload(nsn_ctx *c, Dev<T> &D) {
         C1[t] = T(1.0 / (V * mu)); D1[t] = C1[t]; al[t] = C1[t];
       }
     }
-    CUDA_TRY(c, puti(D.tv, v));
-    CUDA_TRY(c, puti(D.tkind, kind));
-    CUDA_TRY(c, put(D.tDmi, Dmi)); CUDA_TRY(c, put(D.tVe, Ve)); CUDA_TRY(c, put(D.tC1, C1));
-    CUDA_TRY(c, put(D.tD1, D1)); CUDA_TRY(c, put(D.talpha, al));
+    CUDA_TRY(c, puti(D.tv, v, 4 * nt));
+    CUDA_TRY(c, puti(D.tkind, kind, nt));
+    CUDA_TRY(c, put(D.tDmi, Dmi, 9 * nt)); CUDA_TRY(c, put(D.tVe, Ve, nt)); CUDA_TRY(c, put(D.tC1, C1, nt));
+    CUDA_TRY(c, put(D.tD1, D1, nt)); CUDA_TRY(c, put(D.talpha, al, nt));
   }
   {
-    std::vector<T> ones(std::max(L.nc, 1), T(1));
-    CUDA_TRY(c, put(D.pscale, ones));
+    T *ones = stage(std::max<size_t>(nc, 1));
+    if (oom) return fail(c, NSN_ERR_OUT_OF_MEMORY, "pinned staging of the upload");
+    for (size_t i = 0; i < std::max<size_t>(nc, 1); i++) ones[i] = T(1);
+    CUDA_TRY(c, put(D.pscale, ones, std::max<size_t>(nc, 1)));
   }
   CUDA_TRY(c, cudaMemsetAsync(D.lam, 0, sizeof(T) * std::max(L.R, 1), st));
   CUDA_TRY(c, cudaMemsetAsync(D.lam_prev, 0, sizeof(T) * std::max(L.R, 1), st));
   CUDA_TRY(c, cudaMemsetAsync(D.sc, 0, sizeof(Scalars), st));
   CUDA_TRY(c, cudaMemsetAsync(D.fl, 0, sizeof(Flags), st));
-  CUDA_TRY(c, puti(D.risl, L.risl));
-  CUDA_TRY(c, puti(D.cabi, L.cperm));
-  CUDA_TRY(c, puti(D.row_abi_dev, L.row_abi));
-  CUDA_TRY(c, puti(D.bisl_r, L.bisl_r));
-  CUDA_TRY(c, puti(D.bisl_p, L.bisl_p));
-  CUDA_TRY(c, puti(D.ires, L.ires));
+  CUDA_TRY(c, putv(D.risl, L.risl));
+  CUDA_TRY(c, putv(D.cabi, L.cperm));
+  CUDA_TRY(c, putv(D.row_abi_dev, L.row_abi));
+  CUDA_TRY(c, putv(D.bisl_r, L.bisl_r));
+  CUDA_TRY(c, putv(D.bisl_p, L.bisl_p));
+  CUDA_TRY(c, putv(D.ires, L.ires));
   CUDA_TRY(c, cudaMemcpyAsync(D.isres, L.isres.data(), L.isres.size(), cudaMemcpyHostToDevice, st));
   CUDA_TRY(c, cudaMemcpyAsync(D.isl.rigid, L.isl_rigid.data(), L.isl_rigid.size(), cudaMemcpyHostToDevice, st));
   CUDA_TRY(c, cudaMemsetAsync(D.isl.ls_pre, 0, sizeof(int) * size_t(std::max(L.ni, 1)), st));
-  CUDA_TRY(c, puti(D.gres, L.gres));
-  CUDA_TRY(c, puti(D.gisl, L.gisl));
-  CUDA_TRY(c, puti(D.grp_of, L.grp_of));
+  CUDA_TRY(c, putv(D.gres, L.gres));
+  CUDA_TRY(c, putv(D.gisl, L.gisl));
+  CUDA_TRY(c, putv(D.grp_of, L.grp_of));
   CUDA_TRY(c, cudaMemsetAsync(D.resact, 0, size_t(std::max(L.ni, 1)), st));
   CUDA_TRY(c, cudaMemsetAsync(D.gact, 0, std::max<size_t>(L.gres.size() / 10, 1), st));
   {
@@ -1200,10 +1287,12 @@ nsn_status save_lam_prev(nsn_ctx *c, std::vector<double> &out) {
   const Dev<T> &D = dev<T>(c);
   const Layout &L = c->L;
   if (!c->dmem || L.R == 0 || !D.lam_prev) return NSN_OK;
-  std::vector<T> v(L.R);
-  CUDA_TRY(c, cudaMemcpyAsync(v.data(), D.lam_prev, sizeof(T) * L.R, cudaMemcpyDeviceToHost, c->stream));
+  c->stage.rewind();
+  T *v = c->stage.take<T>(L.R);
+  if (!v) return fail(c, NSN_ERR_OUT_OF_MEMORY, "pinned staging of the previous multipliers");
+  CUDA_TRY(c, cudaMemcpyAsync(v, D.lam_prev, sizeof(T) * L.R, cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-  out.assign(L.R, 0.0);
+  out.resize(L.R);
   for (int i = 0; i < L.R; i++) out[L.row_abi[i]] = double(v[i]);
   return NSN_OK;
 }
@@ -1219,13 +1308,16 @@ nsn_status restore_lam_prev(nsn_ctx *c, const std::vector<double> &old, const st
   const Layout &L = c->L;
   const HostScene &S = c->scene;
   if (L.R == 0) return NSN_OK;
-  std::vector<double> abi(L.R, 0.0);
+  std::vector<double> &abi = c->lam_abi2;
+  abi.assign(L.R, 0.0);
   const int onc = int(old_contacts.size());
   // the old contacts bucketed by body a + 1 (a = -1: the world), scanned per
   // new contact: a vertex has few contacts, so this stays linear
   const int nb = int(S.kind.size());
   // slot s = body_a + 1; after the fill, slot s holds list[end(s - 1) .. end(s))
-  std::vector<int> end(size_t(nb) + 2, 0), list(onc);
+  std::vector<int> &end = c->key_end, &list = c->key_list;
+  end.assign(size_t(nb) + 2, 0);
+  list.resize(onc);
   for (int i = 0; i < onc; i++) end[size_t(old_contacts[i].body_a) + 2]++;
   for (int b = 0; b <= nb; b++) end[size_t(b) + 1] += end[b];
   for (int i = 0; i < onc; i++) list[end[size_t(old_contacts[i].body_a) + 1]++] = i;
@@ -1245,9 +1337,10 @@ nsn_status restore_lam_prev(nsn_ctx *c, const std::vector<double> &old, const st
     for (int r = 0; r < 5 * L.nj; r++) abi[3 * L.nc + r] = old[3 * size_t(onc) + r];
   if (old_nt == L.nt && old_nj == L.nj)
     for (int r = 0; r < 3 * L.nt; r++) abi[L.Rpair + r] = old[3 * size_t(onc) + 5 * size_t(old_nj) + r];
-  std::vector<T> v(L.R);
+  T *v = c->stage.take<T>(L.R);
+  if (!v) return fail(c, NSN_ERR_OUT_OF_MEMORY, "pinned staging of the previous multipliers");
   for (int i = 0; i < L.R; i++) v[i] = T(abi[L.row_abi[i]]);
-  CUDA_TRY(c, cudaMemcpyAsync(D.lam_prev, v.data(), sizeof(T) * L.R, cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(D.lam_prev, v, sizeof(T) * L.R, cudaMemcpyHostToDevice, c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   return NSN_OK;
 }
@@ -1257,7 +1350,8 @@ nsn_status ensure_built(nsn_ctx *c) {
   for (int k = NSN_PHASE_SAVE; k <= NSN_PHASE_RESTORE; k++) c->phase_ms[k] = 0.0;
   double t0 = now_ms();
   if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
-  std::vector<double> lam_prev_abi;
+  std::vector<double> &lam_prev_abi = c->lam_abi;
+  lam_prev_abi.clear();
   if (c->dmem && c->built_nb > 0) {
     nsn_status sl = c->cfg.precision == NSN_FP64 ? save_lam_prev<double>(c, lam_prev_abi)
                                                  : save_lam_prev<float>(c, lam_prev_abi);
@@ -1938,6 +2032,7 @@ nsn_status nsn_destroy(nsn_ctx *c) {
   if (c->col_body) cudaFree(c->col_body);
   if (c->col_f) cudaFree(c->col_f);
   if (c->col_found) cudaFree(c->col_found);
+  c->stage.release();
   if (c->col_found_h) cudaFreeHost(c->col_found_h);
   if (c->col_f_h) cudaFreeHost(c->col_f_h);
   if (c->col_body_h) cudaFreeHost(c->col_body_h);

@@ -26,6 +26,7 @@
 #include <stdint.h>
 
 #include <type_traits>
+#include "nsn_bits.h"
 
 namespace nsn {
 
@@ -253,6 +254,12 @@ struct Dev {
 // FP64 accumulator.  Keys < 0 contribute nothing.  Rows and bodies of one
 // island are mostly consecutive, so a warp issues few atomics; a key that
 // recurs in two runs adds twice, which is still the right sum.
+// FP32 -> FP64 for the FP64 accumulations: the exact re-encoding on the
+// integer pipe (nsn_bits.h) instead of the conversion instruction, which
+// occupies GB300's narrow FP64 pipe
+__device__ __forceinline__ double to_f64(float x) { return nsn_f32_to_f64_exact(x); }
+__device__ __forceinline__ double to_f64(double x) { return x; }
+
 template <typename V, int NV>
 __device__ __forceinline__ void warp_runs_add(int key, V (&v)[NV], double *acc, int stride) {
   const unsigned full = 0xffffffffu;
@@ -270,7 +277,7 @@ __device__ __forceinline__ void warp_runs_add(int key, V (&v)[NV], double *acc, 
   }
   if (key >= 0 && ((head >> lane) & 1u))
 #pragma unroll
-    for (int k = 0; k < NV; k++) atomicAdd(acc + size_t(k) * stride + key, double(v[k]));
+    for (int k = 0; k < NV; k++) atomicAdd(acc + size_t(k) * stride + key, to_f64(v[k]));
 }
 
 // ------------------------------------------------------------------------------------
@@ -1213,7 +1220,7 @@ __device__ __forceinline__ bool isl_skip(const Dev<T> &D, int is, int force) {
 }
 
 template <typename T, int G, int MODE>
-__global__ void __launch_bounds__(BLOCK) k_body_pass(Dev<T> D, const T *__restrict__ in, int buf, int newton_it, int force) {
+__global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 && MODE == BM_APPLY ? 5 : 1) k_body_pass(Dev<T> D, const T *__restrict__ in, int buf, int newton_it, int force) {
   if (ls_idle(D)) return;
   if (!force && D.fl->newton_stop) return;
   if (newton_it == IT_DEV) newton_it = D.fl->newton_n;
@@ -1234,15 +1241,23 @@ __global__ void __launch_bounds__(BLOCK) k_body_pass(Dev<T> D, const T *__restri
     for (int j = blockIdx.x; j < nch; j += D.nblk_body_r) {
       const int b0 = (blk_skip ? D.list_br[j] : j) * gpb;
       const int b = b0 + gid;
-      bool act = b < D.nr;
-      if (act && D.isl_on && isl_skip<MODE>(D, D.bisl_r[b], force)) act = false;
-      int s0 = 0, s1 = 0;
-      if (act) { s0 = D.rseg[b]; s1 = D.rseg[b + 1]; }
+      // the segment bounds, the island and then the island's flag and the
+      // first slots are loaded side by side (each level waits only for the
+      // one before); an inactive body then drops its slots
+      const bool inb = b < D.nr;
+      int s0 = 0, s1 = 0, bis = 0;
+      if (inb) { s0 = D.rseg[b]; s1 = D.rseg[b + 1]; if (D.isl_on) bis = D.bisl_r[b]; }
       int sl[KR];
 #pragma unroll
       for (int r = 0; r < KR; r++) {
         const int e = s0 + lane + r * G;
         sl[r] = e < s1 ? D.eslot[e] : -1;
+      }
+      const bool act = inb && !(D.isl_on && isl_skip<MODE>(D, bis, force));
+      if (!act) {
+        s1 = s0;
+#pragma unroll
+        for (int r = 0; r < KR; r++) sl[r] = -1;
       }
       T J[KR][6], xv[KR];
 #pragma unroll
@@ -1335,7 +1350,7 @@ __global__ void __launch_bounds__(BLOCK) k_body_pass(Dev<T> D, const T *__restri
             T gg = T(0);
 #pragma unroll
             for (int k = 0; k < 6; k++) gg += g[k] * g[k];
-            atomicAdd(D.isl.acc + D.bisl_r[b], double(gg));
+            atomicAdd(D.isl.acc + D.bisl_r[b], to_f64(gg));
           }
         }
       }
@@ -1377,15 +1392,20 @@ __global__ void __launch_bounds__(BLOCK) k_body_pass(Dev<T> D, const T *__restri
     for (int j = bid; j < nch; j += D.nblk_body_p) {
       const int b0 = (blk_skip ? D.list_bp[j] : j) * gpb;
       const int b = b0 + gid;
-      bool act = b < D.np;
-      if (act && D.isl_on && isl_skip<MODE>(D, D.bisl_p[b], force)) act = false;
-      int s0 = 0, s1 = 0;
-      if (act) { s0 = D.vseg[b]; s1 = D.vseg[b + 1]; }
+      const bool inb = b < D.np;
+      int s0 = 0, s1 = 0, bis = 0;
+      if (inb) { s0 = D.vseg[b]; s1 = D.vseg[b + 1]; if (D.isl_on) bis = D.bisl_p[b]; }
       int sl[KR];
 #pragma unroll
       for (int r = 0; r < KR; r++) {
         const int e = s0 + lane + r * G;
         sl[r] = e < s1 ? eslot[e] : -1;
+      }
+      const bool act = inb && !(D.isl_on && isl_skip<MODE>(D, bis, force));
+      if (!act) {
+        s1 = s0;
+#pragma unroll
+        for (int r = 0; r < KR; r++) sl[r] = -1;
       }
       T J[KR][3], xv[KR];
 #pragma unroll
@@ -1480,7 +1500,7 @@ __global__ void __launch_bounds__(BLOCK) k_body_pass(Dev<T> D, const T *__restri
             D.pg[k][b] = g[k]; D.pyg[k][b] = y[k]; D.phinv[k][b] = hi[k];
             acc_g2.add_prod(g[k], g[k]);
           }
-          if (D.isl_on) atomicAdd(D.isl.acc + D.bisl_p[b], double(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]));
+          if (D.isl_on) atomicAdd(D.isl.acc + D.bisl_p[b], to_f64(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]));
         }
       }
 #pragma unroll
@@ -2376,7 +2396,7 @@ __device__ __forceinline__ bool res_scalars_warp(const ResSmem<T> &S, int li, in
 }
 
 template <typename T>
-__global__ void __launch_bounds__(RES_THREADS) k_cr_resident(Dev<T> D, int M) {
+__global__ void __launch_bounds__(RES_THREADS, sizeof(T) == 4 ? 5 : 2) k_cr_resident(Dev<T> D, int M) {
   if (D.fl->newton_stop) return;
   extern __shared__ __align__(32) unsigned char res_raw[];
   const ResSmem<T> S = res_carve<T>(res_raw, D.res_rows, D.res_ent, D.res_bod);

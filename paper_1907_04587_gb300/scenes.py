@@ -338,7 +338,10 @@ def batched_envs(seed=0, n_envs=4096, links=(3, 20), boxes=(0, 64), box_edge=(0.
     ``boxes``, edge log-uniform in ``box_edge``) stacked in up to four layers,
     with per-environment friction uniform in ``mu``.  Links get random spin about
     z and boxes random horizontal velocities so contacts mix stick and slip.
-    Vertices of every body bottom face contact the ground or the box beneath.
+    Vertices of every body bottom face contact the ground or the box beneath:
+    a box above another is at most 0.7 of its edge, turned by at most 0.15 rad
+    and offset by at most 15% of its half edge from it, so its bottom face lies
+    on the lower box's top face.
     """
     rng = np.random.default_rng(seed)
     L = np.asarray(link_dims, np.float64)
@@ -382,13 +385,24 @@ def batched_envs(seed=0, n_envs=4096, links=(3, 20), boxes=(0, 64), box_edge=(0.
     # boxes of one env are consecutive and ordered by k, so the support of box k is box k-16
     has_below = layer > 0
     below[has_below] = np.nonzero(has_below)[0] - 16
+    # a box above another rests with its whole bottom face on the top face of
+    # the one below: edge at most 0.7 of the lower edge, yaw within 0.15 rad
+    # of it, centre within 15% of its half edge (0.7 (cos 0.15 + sin 0.15)
+    # + 0.15 < 1, so every bottom corner lies over the lower top face)
+    rel_yaw = rng.uniform(-0.15, 0.15, len(bi))
+    rel_off = rng.uniform(-0.15, 0.15, (len(bi), 2))
     for lay in range(int(layer.max()) + 1 if len(layer) else 0):
         sel = layer == lay
         if lay == 0:
             zc[sel] = edge[sel] / 2
         else:
             idx = np.nonzero(sel)[0]
-            zc[idx] = zc[below[idx]] + edge[below[idx]] / 2 + edge[idx] / 2
+            lo = below[idx]
+            edge[idx] = np.minimum(edge[idx], 0.7 * edge[lo])
+            yaw[idx] = yaw[lo] + rel_yaw[idx]
+            cx[idx] = cx[lo] + rel_off[idx, 0] * edge[lo] / 2
+            cy[idx] = cy[lo] + rel_off[idx, 1] * edge[lo] / 2
+            zc[idx] = zc[lo] + edge[lo] / 2 + edge[idx] / 2
     zc += rng.uniform(-5e-4, 5e-4, len(bi))
     pos[bi] = origin[be] + np.stack([cx, cy, zc], 1)
     quat[bi] = quat_yaw(yaw)

@@ -147,6 +147,10 @@ CASES = {
     "chain_block_small_gs": (lambda: scenes.chain_block(seed=1, hexes=4, links=7),
                              dict(newton_iters=10, cr_iters=50), 4),
     "batched_small": (lambda: scenes.batched_envs(seed=2, n_envs=12), dict(newton_iters=5, cr_iters=25), 6),
+    # the full-size FEM scenes: the chain on the 24^3-hex Neo-Hookean block
+    # (69,120 tets, 209,660 rows) and the bin (2000 boxes, 8 Neo-Hookean balls)
+    "chain_block_full": (lambda: scenes.chain_block(seed=0), dict(newton_iters=3, cr_iters=20, geom_stiffness=0), 2),
+    "mixed_bin_full": (lambda: scenes.mixed_bin(seed=0), dict(newton_iters=3, cr_iters=20), 2),
     "batched_small_islands_ls": (lambda: scenes.batched_envs(seed=2, n_envs=12),
                                  dict(newton_iters=8, cr_iters=60, tol_rel=1e-6, island_stop=1, cone_project=1,
                                       line_search=1), 6),
