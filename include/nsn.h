@@ -288,9 +288,10 @@ nsn_status nsn_operator_sizes(nsn_ctx *ctx, int64_t *sizes8);
  * previous step's multipliers; NSN_WARM_LEARNED sets the contact rows'
  * lambda^0 from a per-contact network (16 features -> 128 -> 128 -> 128 -> 4,
  * ReLU, BF16 tensor-core GEMMs with FP32 accumulation; contact rows only,
- * joint and tet rows start at zero): outputs are the
- * normal and two friction multipliers over the contact's gravity-scaled
- * effective mass |g| / (1/m_a + 1/m_b) and a log preconditioner scale.
+ * joint and tet rows start at zero): outputs are the change of the normal and
+ * two friction multipliers from their previous-step values (a contact new in
+ * this step has zero there), over the contact's gravity-scaled effective mass
+ * |g| / (1/m_a + 1/m_b), and a log preconditioner scale.
  * NSN_WARM_PREV keeps the previous step's multipliers only if the merit at
  * (u = 0, lambda^0) is not above the merit at the zero start.  NSN_WARM_LEARNED
  * falls back on the previous-step start: of the three candidates (network,

@@ -53,3 +53,57 @@ def loss_and_grad(p, X, T, w):
     da1 = dz2 @ P["W2"]; dz1 = da1 * (z1 > 0)
     g["W1"] = dz1.T @ a0; g["b1"] = dz1.sum(0)
     return loss, pack(g)
+
+
+# --------------------------------------------------------------------------
+# The same network with the rounding of the tensor-core kernels: BF16 inputs,
+# weights and hidden activations (round to nearest even of the FP32 value),
+# FP32 biases and outputs, exact products, sums in FP64 (the kernels sum in
+# FP32: their results differ from these by the FP32 accumulation error, and,
+# where that moves a value across a BF16 rounding boundary, by one BF16 unit
+# in that activation).  Backward as the training kernels round it: dY and
+# dz in BF16 for the GEMM operands, in FP32 for the bias sums; the ReLU mask
+# from the FP32 activation.
+
+def round_bf16(a):
+    """Round to the nearest BF16 value (ties to even), via the FP32 value."""
+    f = np.ascontiguousarray(np.asarray(a, np.float64).astype(np.float32))
+    u = f.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _f32(a):
+    return np.asarray(a, np.float64).astype(np.float32).astype(np.float64)
+
+
+def forward_bf16(p, X):
+    P = unpack(p)
+    W = {k: round_bf16(P[k]) for k in ("W1", "W2", "W3", "W4")}
+    b = {k: _f32(P[k]) for k in ("b1", "b2", "b3", "b4")}
+    a0 = round_bf16(X)
+    z1 = _f32(a0 @ W["W1"].T + b["b1"]); a1f = np.maximum(z1, 0); a1 = round_bf16(a1f)
+    z2 = _f32(a1 @ W["W2"].T + b["b2"]); a2f = np.maximum(z2, 0); a2 = round_bf16(a2f)
+    z3 = _f32(a2 @ W["W3"].T + b["b3"]); a3f = np.maximum(z3, 0); a3 = round_bf16(a3f)
+    y = _f32(a3 @ W["W4"].T + b["b4"])
+    return y, (a0, a1f, a1, a2f, a2, a3f, a3, W)
+
+
+def loss_and_grad_bf16(p, X, T, w):
+    y, (a0, a1f, a1, a2f, a2, a3f, a3, W) = forward_bf16(p, X)
+    n = len(X)
+    d = y - np.asarray(T, np.float64)
+    loss = 0.5 * float((w * d * d).sum()) / n
+    dyf = _f32(w * d / n)
+    dyb = round_bf16(dyf)
+    g = {"W4": dyb.T @ a3, "b4": dyf.sum(0)}
+    da = _f32(dyb @ W["W4"])
+    dzf = da * (a3f > 0); dzb = round_bf16(dzf)
+    g["W3"] = dzb.T @ a2; g["b3"] = dzf.sum(0)
+    da = _f32(dzb @ W["W3"])
+    dzf = da * (a2f > 0); dzb = round_bf16(dzf)
+    g["W2"] = dzb.T @ a1; g["b2"] = dzf.sum(0)
+    da = _f32(dzb @ W["W2"])
+    dzf = da * (a1f > 0); dzb = round_bf16(dzf)
+    g["W1"] = dzb.T @ a0; g["b1"] = dzf.sum(0)
+    return loss, pack(g)

@@ -3044,7 +3044,8 @@ __device__ __forceinline__ T contact_lscale(const Dev<T> &D, int c) {
 }
 
 // training targets: the current multipliers of each contact over lambda_s, and
-// a zero log preconditioner scale
+// a zero log preconditioner scale (the training data subtracts the features'
+// previous-step multipliers, the network's target being their change)
 template <typename T>
 __global__ void k_contact_targets(Dev<T> D, float *Y) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -3055,8 +3056,11 @@ __global__ void k_contact_targets(Dev<T> D, float *Y) {
   Y[o + 3] = 0.f;
 }
 
-// lambda^0 from the network outputs: lambda_n >= 0; friction rows start at
-// zero unless warm_friction (then |lambda_f| <= mu lambda_n)
+// lambda^0 from the network outputs, which are the change of each multiplier
+// from its previous-step value over lambda_s (the network corrects the
+// previous-step start; BF16 rounding then touches only the correction):
+// lambda_n >= 0; friction rows start at zero unless warm_friction (then
+// |lambda_f| <= mu lambda_n)
 template <typename T>
 __global__ void k_warm_from_pred(Dev<T> D, const float *Y, int warm_friction) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -3069,11 +3073,11 @@ __global__ void k_warm_from_pred(Dev<T> D, const float *Y, int warm_friction) {
     const float e = fminf(fmaxf(Y[o + 3], -1.3862944f), 1.3862944f);
     D.pscale[c] = T(expf(e));
   }
-  T ln = T(Y[o]) * ls;
+  T ln = D.lam_prev[3 * c] + T(Y[o]) * ls;
   if (!(ln > T(0))) ln = T(0);
   T f1 = T(0), f2 = T(0);
   if (warm_friction) {
-    f1 = T(Y[o + 1]) * ls; f2 = T(Y[o + 2]) * ls;
+    f1 = D.lam_prev[3 * c + 1] + T(Y[o + 1]) * ls; f2 = D.lam_prev[3 * c + 2] + T(Y[o + 2]) * ls;
     const T lim = D.cmu[c] * ln, fn = dnorm2(f1, f2);
     if (fn > lim) { const T s = fn > T(0) ? lim / fn : T(0); f1 *= s; f2 *= s; }
   }

@@ -100,7 +100,8 @@ def generate(seeds, n_envs=512, steps=3, solve=None, precond=True):
     For each seed, a batched scene is advanced `steps` steps by the island
     solver to a relative residual of 1e-6.  Before each step the contact
     features are taken at the committed state (the previous-step multipliers
-    among them); after it, the converged multipliers are the targets.  Only
+    among them); after it, the change from those to the converged multipliers
+    is the target (the difference taken on the device by torch).  Only
     contacts of islands that reached the tolerance are kept, so every target
     is a converged solution.  The fourth target is the logarithm of the
     contact's preconditioner scale (precond_targets) at the converged state."""
@@ -117,6 +118,9 @@ def generate(seeds, n_envs=512, steps=3, solve=None, precond=True):
             nsn.nsn_contact_features(g.ctx, X.data_ptr())
             g.step()
             nsn.nsn_contact_features(g.ctx, 0, T.data_ptr())
+            # the network predicts the change from the previous-step multipliers
+            # (features 9..11, over the same lambda_s)
+            T[:, :3] -= X[:, 9:12]
             if precond:
                 # log scale, clamped to the range the solver applies ([1, 4]:
                 # nearly singular blocks of redundant contacts give ratios of 1e7)

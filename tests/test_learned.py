@@ -54,6 +54,39 @@ def test_forward_and_gradients_match_fp64_reference(torch_cuda):
         assert rel(G[name], Gr[name]) < 5e-2, name
 
 
+def test_forward_and_gradients_match_bf16_rounding_reference(torch_cuda):
+    """Against the FP64 reference rounded to BF16 where the kernels round
+    (inputs, weights, hidden activations, dY and dz for the GEMM operands):
+    forward (the fused inference kernel) and every gradient within 1e-3."""
+    torch = torch_cuda
+    rng = np.random.default_rng(5)
+    p = learn.init_params(7)
+    n = 333                                       # ragged against the 16- and 64-row tiles
+    X = rng.normal(size=(n, 16)).astype(np.float32).astype(np.float64)
+    T = rng.normal(size=(n, 4)).astype(np.float32).astype(np.float64)
+    w = np.array([1.0, 1.0, 1.0, 0.1], np.float32)
+    tr = learn.Trainer(params=p.astype(np.float32))
+    Xd = torch.tensor(X, dtype=torch.float32, device="cuda")
+    Yd = torch.empty((n, 4), dtype=torch.float32, device="cuda")
+    nsn.nsn_mlp_forward(tr.host.ctx, Xd.data_ptr(), n, Yd.data_ptr())
+    torch.cuda.synchronize()
+    y_ref, _ = mlp_ref.forward_bf16(p, X)
+    e = rel(Yd.cpu().numpy(), y_ref)
+    print(f"forward {e:.2e}")
+    assert e < 1e-3
+    Td = torch.tensor(T, dtype=torch.float32, device="cuda")
+    wd = torch.tensor(w, device="cuda")
+    loss = nsn.nsn_mlp_train_step(tr.host.ctx, Xd.data_ptr(), Td.data_ptr(), wd.data_ptr(), n, 0.0)
+    l_ref, g_ref = mlp_ref.loss_and_grad_bf16(p, X, T, w.astype(np.float64))
+    assert abs(loss - l_ref) < 1e-3 * l_ref
+    _, g = nsn.nsn_mlp_get_params(tr.host.ctx)
+    G, Gr = mlp_ref.unpack(g), mlp_ref.unpack(g_ref)
+    for name in ("W1", "b1", "W2", "b2", "W3", "b3", "W4", "b4"):
+        e = rel(G[name], Gr[name])
+        print(f"{name} {e:.2e}")
+        assert e < 1e-3, name
+
+
 def test_training_reduces_loss(torch_cuda):
     torch = torch_cuda
     rng = np.random.default_rng(2)

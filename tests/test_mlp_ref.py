@@ -28,3 +28,39 @@ def test_reference_layout_is_the_abi_layout():
     P = mlp_ref.unpack(p)
     assert P["W1"][1, 0] == 16 and P["b1"][0] == 128 * 16
     np.testing.assert_array_equal(mlp_ref.pack(P), p)
+
+
+def test_bf16_rounding():
+    """round_bf16 against values whose BF16 rounding is known: exact BF16
+    values stay, a value just above a midpoint rounds up, a tie rounds to the
+    even mantissa, and the result always has 8 significant bits."""
+    one = 1.0
+    ulp = 2.0 ** -7                                  # BF16 spacing in [1, 2)
+    assert mlp_ref.round_bf16(np.array([one]))[0] == one
+    assert mlp_ref.round_bf16(np.array([one + ulp]))[0] == one + ulp
+    assert mlp_ref.round_bf16(np.array([one + 0.5 * ulp]))[0] == one          # tie: even (1.0)
+    assert mlp_ref.round_bf16(np.array([one + 1.5 * ulp]))[0] == one + 2 * ulp  # tie: even (1 + 2 ulp)
+    assert mlp_ref.round_bf16(np.array([one + 0.51 * ulp]))[0] == one + ulp
+    assert mlp_ref.round_bf16(np.array([-(one + 0.49 * ulp)]))[0] == -one
+    x = np.random.default_rng(0).normal(size=1000)
+    r = mlp_ref.round_bf16(x)
+    m, e = np.frexp(r)
+    assert np.all(m * 2 ** 8 == np.round(m * 2 ** 8))
+    assert np.all(np.abs(r - x) <= 2.0 ** -8 * np.abs(x) * 1.0001)
+
+
+def test_bf16_reference_stays_within_bf16_rounding_of_fp64():
+    """The BF16-rounded network differs from the FP64 one by the BF16 unit
+    (2^-8 relative per rounding, a few roundings deep), neither more nor
+    (as a check that the rounding is applied at all) much less."""
+    rng = np.random.default_rng(3)
+    p = np.concatenate([rng.normal(0, 0.3, s).ravel() for _, s in mlp_ref.SHAPES])
+    X = rng.normal(size=(40, mlp_ref.NIN)); T = rng.normal(size=(40, mlp_ref.NOUT)); w = np.array([1, 1, 1, 0.1])
+    y64, _ = mlp_ref.forward(p, X)
+    y16, _ = mlp_ref.forward_bf16(p, X)
+    e = np.linalg.norm(y16 - y64) / np.linalg.norm(y64)
+    assert 1e-4 < e < 3e-2
+    l64, g64 = mlp_ref.loss_and_grad(p, X, T, w)
+    l16, g16 = mlp_ref.loss_and_grad_bf16(p, X, T, w)
+    assert abs(l16 - l64) < 3e-2 * l64
+    assert np.linalg.norm(g16 - g64) < 5e-2 * np.linalg.norm(g64)
