@@ -1654,11 +1654,62 @@ __global__ void __launch_bounds__(BLOCK) k_row_pass_isl(Dev<T> D, int force) {
     // blocks of BLOCK rows: all of them, or (CR loop) the listed ones
     const bool listed = MODE == RM_APPLY && !force;
     const int nch = listed ? D.fl->n_list_row : (D.Rpair + BLOCK - 1) / BLOCK;
-    for (int j = blockIdx.x; j < nch; j += D.nblk_row_pair) {
+    if (MODE == RM_APPLY) {
+      // the operator apply: each warp takes two chunks of 32 rows per
+      // iteration and issues the loads of both (rows, then the islands'
+      // CR-done flags) before reducing either, so that twice as many
+      // independent loads are in flight
+      for (int j = blockIdx.x; j < nch; j += 2 * D.nblk_row_pair) {
+        int ii[2], key[2];
+        bool ok[2];
+        T ta[2], tb[2], zz[2], pp[2], cd[2], ap[2];
+#pragma unroll
+        for (int u = 0; u < 2; u++) {
+          const int jj = j + u * D.nblk_row_pair;
+          const int w0 = jj < nch ? (listed ? D.list_row[jj] : jj) * BLOCK + (threadIdx.x & ~31) : D.Rpair;
+          ok[u] = w0 < D.Rpair;                     // uniform per warp
+          ii[u] = w0 + lane;
+          ta[u] = tb[u] = zz[u] = pp[u] = cd[u] = ap[u] = T(0);
+          key[u] = -1;
+          if (ok[u] && ii[u] < D.Rpair) {
+            const int r = ii[u];
+            ta[u] = D.t[2 * r]; tb[u] = D.t[2 * r + 1]; zz[u] = D.z[r]; pp[u] = D.P[r]; cd[u] = D.cdiag[r];
+            ap[u] = D.Ap[r]; key[u] = D.risl[r];
+          }
+        }
+        int done[2];
+#pragma unroll
+        for (int u = 0; u < 2; u++) done[u] = key[u] >= 0 ? D.isl.crdone[key[u]] : 1;
+#pragma unroll
+        for (int u = 0; u < 2; u++) {
+          if (!ok[u]) continue;
+          const int k = done[u] ? -1 : key[u];
+          const bool v = k >= 0;
+          if (!__any_sync(0xffffffffu, v)) continue;   // the whole warp's islands are finished
+          T a[5] = {T(0), T(0), T(0), T(0), T(0)};
+          if (v) {
+            const T az = (ta[u] + tb[u]) + (cd[u] + eps) * zz[u];
+            D.Az[ii[u]] = az;
+            const T paz = pp[u] * az;
+            a[0] = zz[u] * az; a[1] = az * paz; a[2] = paz * ap[u]; a[3] = zz[u] * zz[u] / pp[u];
+            a[4] = ap[u] * pp[u] * ap[u];
+          }
+          warp_runs_add<T, 5>(k, a, D.isl.acc + 2 * size_t(ni), ni);
+        }
+      }
+    }
+    for (int j = blockIdx.x; MODE != RM_APPLY && j < nch; j += D.nblk_row_pair) {
       const int w0 = (listed ? D.list_row[j] : j) * BLOCK + (threadIdx.x & ~31);
       if (w0 >= D.Rpair) continue;                  // a listed block of tet rows (uniform per warp)
       const int i = w0 + lane;
-      int key = i < D.Rpair ? D.risl[i] : -1;
+      const bool in_rows = i < D.Rpair;
+      // the operator apply's row data is loaded alongside the island flags
+      // (the two dependent loads of risl and crdone), not after them
+      T ta = T(0), tb2 = T(0), zi0 = T(0), Pi0 = T(0), cd0 = T(0), ap0 = T(0);
+      if (MODE == RM_APPLY && in_rows) {
+        ta = D.t[2 * i]; tb2 = D.t[2 * i + 1]; zi0 = D.z[i]; Pi0 = D.P[i]; cd0 = D.cdiag[i]; ap0 = D.Ap[i];
+      }
+      int key = in_rows ? D.risl[i] : -1;
       if (key >= 0 && (MODE == RM_APPLY ? D.isl.crdone[key] != 0 : (!force && (D.isl.stop[key] >= 0 || ls_done(D, key))))) key = -1;
       const bool v = key >= 0;
       if (!__any_sync(0xffffffffu, v)) continue;   // the whole warp's islands are finished
@@ -1682,11 +1733,11 @@ __global__ void __launch_bounds__(BLOCK) k_row_pass_isl(Dev<T> D, int force) {
       } else {
         T a[5] = {T(0), T(0), T(0), T(0), T(0)};
         if (v) {
-          const T acc = D.t[2 * i] + D.t[2 * i + 1];
-          const T zi = D.z[i];
-          const T Pi = D.P[i];
-          const T az = acc + (D.cdiag[i] + eps) * zi;
-          const T api = D.Ap[i];
+          const T acc = ta + tb2;
+          const T zi = zi0;
+          const T Pi = Pi0;
+          const T az = acc + (cd0 + eps) * zi;
+          const T api = ap0;
           D.Az[i] = az;
           const T paz = Pi * az;
           a[0] = zi * az; a[1] = az * paz; a[2] = paz * api; a[3] = zi * zi / Pi; a[4] = api * Pi * api;
@@ -2493,6 +2544,9 @@ __global__ void __launch_bounds__(RES_THREADS, sizeof(T) == 4 ? 5 : 2) k_cr_resi
       // islands, RES_G lanes per body; the first RES_KR entries of a lane stay
       // in registers between the two
       for (int bb = 0; bb < nb; bb += RES_THREADS / RES_G) {
+        // a warp whose bodies all lie past the group's skips the pass (warp
+        // uniform: its 32 / RES_G bodies start at bb + warp * 32 / RES_G)
+        if (bb + warp * (32 / RES_G) >= nb) continue;
         const int b = bb + tid / RES_G, l = tid % RES_G;
         const int bli = b < nb ? S.bisl[b] : 0;
         const bool on = b < nb && S.act[bli];

