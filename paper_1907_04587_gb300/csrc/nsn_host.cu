@@ -154,6 +154,15 @@ struct PinnedStage {
   }
 };
 
+// a contact's identity across contact regenerations: body pair and the bit
+// pattern of its point on a (the collider emits corners at fixed body-frame
+// points), with the old contact's internal index
+struct ContactKeyRec {
+  int32_t a, b;
+  uint32_t p[3];
+  int idx;
+};
+
 struct nsn_ctx {
   nsn_config cfg;
   cudaStream_t stream = nullptr;
@@ -189,6 +198,18 @@ struct nsn_ctx {
   // joint and tet counts, so that the next build can match them by key
   std::vector<nsn_contact> built_contacts;
   int built_nj = 0, built_nt = 0;   // joints and tet blocks (3 rows each) of the built scene
+  // a rebuild keeps the device's state and previous multipliers on the
+  // device: the state in ABI order (13 floats per body, the staging layout)
+  // and lam_prev in the old internal row order, with the old internal index
+  // of every ABI contact, joint and tet block
+  float *keep_state = nullptr;
+  size_t keep_state_n = 0;
+  void *keep_lam = nullptr;
+  size_t keep_lam_bytes = 0;
+  bool keep_state_ready = false;
+  std::vector<int> old_cinv, old_jinv, old_tinv, lam_map;
+  int old_nc = 0, old_Rpair = 0, old_R = 0;
+  std::vector<ContactKeyRec> okeys;
   // nsn_collide_and_step: the state handed to the collider (13 floats per
   // body) and its contact buffers (device), with a pinned host copy
   float *col_state = nullptr;
@@ -202,7 +223,6 @@ struct nsn_ctx {
   size_t dlog_bytes = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   PinnedStage stage;         // pinned staging of the (re)build's uploads
-  std::vector<double> lam_abi, lam_abi2;   // previous multipliers in ABI order across a rebuild
   std::vector<int> key_end, key_list;      // old contacts bucketed by body a (key matching)
   // host wall time (ms) of the phases of the last rebuild / step, NSN_PHASE_*
   double phase_ms[NSN_PHASES] = {};
@@ -1246,7 +1266,12 @@ nsn_status build_device(nsn_ctx *c) {
   const HostScene &S = c->scene;
   float *st = c->d_stage;
   float *dpos = st, *dquat = st + 3 * nb, *dvel = st + 7 * nb, *dom = st + 10 * nb;
-  if (nb) {
+  if (nb && c->keep_state_ready && c->keep_state_n >= 13 * size_t(nb)) {
+    // a rebuild with the same bodies: the state kept on the device (same layout)
+    CUDA_TRY(c, cudaMemcpyAsync(st, c->keep_state, sizeof(float) * 13 * size_t(nb), cudaMemcpyDeviceToDevice, c->stream));
+    k_scatter_state<T><<<cdiv(nb, 128), 128, 0, c->stream>>>(D, c->d_bmap, nb, dpos, dquat, dvel, dom);
+    CUDA_TRY(c, cudaGetLastError());
+  } else if (nb) {
     CUDA_TRY(c, cudaMemcpyAsync(dpos, S.pos.data(), sizeof(float) * 3 * nb, cudaMemcpyHostToDevice, c->stream));
     CUDA_TRY(c, cudaMemcpyAsync(dquat, S.quat.data(), sizeof(float) * 4 * nb, cudaMemcpyHostToDevice, c->stream));
     CUDA_TRY(c, cudaMemcpyAsync(dvel, S.vel.data(), sizeof(float) * 3 * nb, cudaMemcpyHostToDevice, c->stream));
@@ -1266,19 +1291,6 @@ namespace {
 // Key of a contact for matching across regenerations: its two bodies and the
 // bit patterns of its body-local point on a (for a generated contact, the
 // vertex: a box corner, or the particle).
-struct ContactKey {
-  int32_t a, b;
-  uint32_t p[3];
-  bool operator==(const ContactKey &o) const {
-    return a == o.a && b == o.b && p[0] == o.p[0] && p[1] == o.p[1] && p[2] == o.p[2];
-  }
-};
-ContactKey contact_key(const nsn_contact &r) {
-  ContactKey k{r.body_a, r.body_b, {0, 0, 0}};
-  std::memcpy(k.p, r.pa, sizeof k.p);
-  return k;
-}
-
 // The previous step's multipliers of the built scene, in ABI row order
 // (empty if there is no built scene), to carry over a rebuild.
 template <typename T>
@@ -1297,50 +1309,125 @@ nsn_status save_lam_prev(nsn_ctx *c, std::vector<double> &out) {
   return NSN_OK;
 }
 
-// Restores them into the new build: contact rows by key, joint and tet rows
-// by position when their counts did not change.  Rows without a match start
-// from zero (a new contact has no previous-step multiplier).
 template <typename T>
-nsn_status restore_lam_prev(nsn_ctx *c, const std::vector<double> &old, const std::vector<nsn_contact> &old_contacts,
-                            int old_nj, int old_nt) {
-  if (old.empty()) return NSN_OK;
+__global__ void k_gather_lam(T *dst, const T *src, const int *map, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int o = map[i];
+    dst[i] = o >= 0 ? src[o] : T(0);
+  }
+}
+
+// Before a rebuild (contacts replaced, the layout built anew): the device's
+// state, in ABI order, and its previous-step multipliers, in the old internal
+// row order, are copied aside on the device, with the old internal index of
+// every ABI contact, joint and tet block (host), so that the new build takes
+// them over without a round trip through the host.
+template <typename T>
+nsn_status keep_for_rebuild(nsn_ctx *c) {
+  const Dev<T> &D = dev<T>(c);
+  const Layout &L = c->L;
+  const size_t nb = size_t(c->built_nb);
+  if (c->keep_state_n < 13 * nb) {
+    if (c->keep_state) cudaFree(c->keep_state);
+    c->keep_state = nullptr;
+    c->keep_state_n = 0;
+    CUDA_TRY(c, cudaMalloc(&c->keep_state, sizeof(float) * 13 * nb));
+    c->keep_state_n = 13 * nb;
+  }
+  float *p = c->keep_state;
+  c->dirty = false;
+  nsn_status s = state_io(c, false, true, nullptr, nullptr, nullptr, nullptr, p, p + 3 * nb, p + 7 * nb, p + 10 * nb);
+  c->dirty = true;
+  if (s != NSN_OK) return s;
+  const size_t bytes = sizeof(T) * std::max(L.R, 1);
+  if (c->keep_lam_bytes < bytes) {
+    if (c->keep_lam) cudaFree(c->keep_lam);
+    c->keep_lam = nullptr;
+    c->keep_lam_bytes = 0;
+    CUDA_TRY(c, cudaMalloc(&c->keep_lam, bytes));
+    c->keep_lam_bytes = bytes;
+  }
+  if (L.R) CUDA_TRY(c, cudaMemcpyAsync(c->keep_lam, D.lam_prev, sizeof(T) * L.R, cudaMemcpyDeviceToDevice, c->stream));
+  c->old_cinv.resize(L.nc);
+  for (int ci = 0; ci < L.nc; ci++) c->old_cinv[L.cperm[ci]] = ci;
+  c->old_jinv.resize(L.nj);
+  for (int j = 0; j < L.nj; j++) c->old_jinv[L.jperm[j]] = j;
+  c->old_tinv.resize(L.nt);
+  for (int tb = 0; tb < L.nt; tb++) c->old_tinv[L.tperm[tb]] = tb;
+  c->old_nc = L.nc;
+  c->old_Rpair = L.Rpair;
+  c->old_R = L.R;
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  c->keep_state_ready = true;
+  return NSN_OK;
+}
+
+// After the rebuild: lam_prev of the new build from the kept one -- contact
+// rows by key (body pair and point on a), joint and tet rows by position when
+// their counts did not change; rows without a match start from zero (a new
+// contact has no previous-step multiplier).  The host computes the map from
+// new to old internal rows; a kernel gathers.
+template <typename T>
+nsn_status restore_from_keep(nsn_ctx *c, const std::vector<nsn_contact> &old_contacts, int old_nj, int old_nt) {
   Dev<T> &D = dev<T>(c);
   const Layout &L = c->L;
   const HostScene &S = c->scene;
-  if (L.R == 0) return NSN_OK;
-  std::vector<double> &abi = c->lam_abi2;
-  abi.assign(L.R, 0.0);
+  if (L.R == 0 || !c->keep_lam) return NSN_OK;
+  int *map = c->stage.take<int>(L.R);
+  if (!map) return fail(c, NSN_ERR_OUT_OF_MEMORY, "pinned staging of the multiplier map");
+  std::fill(map, map + L.R, -1);
+  // the old contacts bucketed by body a + 1 (a = -1: the world), their keys
+  // stored in bucket order so that each lookup scans a short contiguous run
   const int onc = int(old_contacts.size());
-  // the old contacts bucketed by body a + 1 (a = -1: the world), scanned per
-  // new contact: a vertex has few contacts, so this stays linear
   const int nb = int(S.kind.size());
-  // slot s = body_a + 1; after the fill, slot s holds list[end(s - 1) .. end(s))
   std::vector<int> &end = c->key_end, &list = c->key_list;
   end.assign(size_t(nb) + 2, 0);
   list.resize(onc);
   for (int i = 0; i < onc; i++) end[size_t(old_contacts[i].body_a) + 2]++;
   for (int b = 0; b <= nb; b++) end[size_t(b) + 1] += end[b];
   for (int i = 0; i < onc; i++) list[end[size_t(old_contacts[i].body_a) + 1]++] = i;
-  for (int i = 0; i < L.nc; i++) {
-    const ContactKey k = contact_key(S.contacts[i]);
-    const int sl = k.a + 1;
+  std::vector<ContactKeyRec> &ok = c->okeys;
+  ok.resize(onc);
+  for (int jj = 0; jj < onc; jj++) {
+    const nsn_contact &r = old_contacts[list[jj]];
+    ContactKeyRec &k = ok[jj];
+    k.a = r.body_a; k.b = r.body_b;
+    std::memcpy(k.p, r.pa, sizeof k.p);
+    k.idx = list[jj] < int(c->old_cinv.size()) ? c->old_cinv[list[jj]] : -1;
+  }
+  for (int ci = 0; ci < L.nc; ci++) {
+    const nsn_contact &r = S.contacts[L.cperm[ci]];
+    const int sl = r.body_a + 1;
     if (sl < 0 || sl > nb) continue;
-    for (int j = sl == 0 ? 0 : end[sl - 1]; j < end[sl]; j++) {
-      const int o = list[j];
-      if (contact_key(old_contacts[o]) == k) {
-        for (int q = 0; q < 3; q++) abi[3 * i + q] = old[3 * size_t(o) + q];
+    uint32_t p[3];
+    std::memcpy(p, r.pa, sizeof p);
+    for (int jj = sl == 0 ? 0 : end[sl - 1]; jj < end[sl]; jj++) {
+      const ContactKeyRec &k = ok[jj];
+      if (k.b == r.body_b && k.p[0] == p[0] && k.p[1] == p[1] && k.p[2] == p[2] && k.a == r.body_a) {
+        if (k.idx >= 0)
+          for (int q = 0; q < 3; q++) map[3 * ci + q] = 3 * k.idx + q;
         break;
       }
     }
   }
-  if (old_nj == L.nj)
-    for (int r = 0; r < 5 * L.nj; r++) abi[3 * L.nc + r] = old[3 * size_t(onc) + r];
-  if (old_nt == L.nt && old_nj == L.nj)
-    for (int r = 0; r < 3 * L.nt; r++) abi[L.Rpair + r] = old[3 * size_t(onc) + 5 * size_t(old_nj) + r];
-  T *v = c->stage.take<T>(L.R);
-  if (!v) return fail(c, NSN_ERR_OUT_OF_MEMORY, "pinned staging of the previous multipliers");
-  for (int i = 0; i < L.R; i++) v[i] = T(abi[L.row_abi[i]]);
-  CUDA_TRY(c, cudaMemcpyAsync(D.lam_prev, v, sizeof(T) * L.R, cudaMemcpyHostToDevice, c->stream));
+  if (old_nj == L.nj && int(c->old_jinv.size()) == L.nj)
+    for (int j = 0; j < L.nj; j++) {
+      const int oj = c->old_jinv[L.jperm[j]];
+      for (int q = 0; q < 5; q++) map[3 * L.nc + 5 * j + q] = 3 * c->old_nc + 5 * oj + q;
+    }
+  if (old_nt == L.nt && old_nj == L.nj && int(c->old_tinv.size()) == L.nt)
+    for (int tb = 0; tb < L.nt; tb++) {
+      const int ot = c->old_tinv[L.tperm[tb]];
+      for (int q = 0; q < 3; q++) map[L.Rpair + 3 * tb + q] = c->old_Rpair + 3 * ot + q;
+    }
+  // the map goes to the device through the entry scratch t2 (rewritten by
+  // every evaluation before it is read)
+  int *dmap = reinterpret_cast<int *>(D.t2);
+  CUDA_TRY(c, cudaMemcpyAsync(dmap, map, sizeof(int) * L.R, cudaMemcpyHostToDevice, c->stream));
+  k_gather_lam<T><<<clampb(cdiv(L.R, 256), D.max_blk), 256, 0, c->stream>>>(D.lam_prev, static_cast<const T *>(c->keep_lam),
+                                                                         dmap, L.R);
+  CUDA_TRY(c, cudaGetLastError());
+  CUDA_TRY(c, cudaMemsetAsync(D.t2, 0, sizeof(T) * std::max(2 * L.Rpair + 12 * L.nt, 1), c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   return NSN_OK;
 }
@@ -1350,15 +1437,16 @@ nsn_status ensure_built(nsn_ctx *c) {
   for (int k = NSN_PHASE_SAVE; k <= NSN_PHASE_RESTORE; k++) c->phase_ms[k] = 0.0;
   double t0 = now_ms();
   if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
-  std::vector<double> &lam_prev_abi = c->lam_abi;
-  lam_prev_abi.clear();
-  if (c->dmem && c->built_nb > 0) {
-    nsn_status sl = c->cfg.precision == NSN_FP64 ? save_lam_prev<double>(c, lam_prev_abi)
-                                                 : save_lam_prev<float>(c, lam_prev_abi);
-    if (sl != NSN_OK) return sl;
-  }
-  // keep the current state of the bodies that already live on the device
-  if (c->dmem && c->built_nb > 0) {
+  const int nb = int(c->scene.kind.size());
+  // the bodies did not change: state and multipliers stay on the device
+  const bool keep = c->dmem && c->built_nb > 0 && c->built_nb == nb;
+  c->keep_state_ready = false;
+  if (keep) {
+    nsn_status sk = c->cfg.precision == NSN_FP64 ? keep_for_rebuild<double>(c) : keep_for_rebuild<float>(c);
+    if (sk != NSN_OK) return sk;
+  } else if (c->dmem && c->built_nb > 0) {
+    // bodies were added: the state of those already built comes back to the
+    // host scene (multipliers start from zero)
     const int nb0 = c->built_nb;
     std::vector<float> pos(3 * nb0), quat(4 * nb0), vel(3 * nb0), om(3 * nb0);
     c->dirty = false;
@@ -1377,15 +1465,14 @@ nsn_status ensure_built(nsn_ctx *c) {
   s = c->cfg.precision == NSN_FP64 ? build_device<double>(c) : build_device<float>(c);
   if (s != NSN_OK) return s;
   phase_tick(c, NSN_PHASE_UPLOAD, t0);
-  if (!lam_prev_abi.empty() && c->built_nb == int(c->scene.kind.size())) {
-    s = c->cfg.precision == NSN_FP64
-            ? restore_lam_prev<double>(c, lam_prev_abi, c->built_contacts, c->built_nj, c->built_nt)
-            : restore_lam_prev<float>(c, lam_prev_abi, c->built_contacts, c->built_nj, c->built_nt);
+  if (keep) {
+    s = c->cfg.precision == NSN_FP64 ? restore_from_keep<double>(c, c->built_contacts, c->built_nj, c->built_nt)
+                                     : restore_from_keep<float>(c, c->built_contacts, c->built_nj, c->built_nt);
     if (s != NSN_OK) return s;
   }
   phase_tick(c, NSN_PHASE_RESTORE, t0);
   c->dirty = false;
-  c->built_nb = int(c->scene.kind.size());
+  c->built_nb = nb;
   c->built_contacts = c->scene.contacts;
   c->built_nj = int(c->scene.joints.size());
   c->built_nt = c->L.nt;
@@ -2033,6 +2120,8 @@ nsn_status nsn_destroy(nsn_ctx *c) {
   if (c->col_f) cudaFree(c->col_f);
   if (c->col_found) cudaFree(c->col_found);
   c->stage.release();
+  if (c->keep_state) cudaFree(c->keep_state);
+  if (c->keep_lam) cudaFree(c->keep_lam);
   if (c->col_found_h) cudaFreeHost(c->col_found_h);
   if (c->col_f_h) cudaFreeHost(c->col_f_h);
   if (c->col_body_h) cudaFreeHost(c->col_body_h);

@@ -1654,51 +1654,7 @@ __global__ void __launch_bounds__(BLOCK) k_row_pass_isl(Dev<T> D, int force) {
     // blocks of BLOCK rows: all of them, or (CR loop) the listed ones
     const bool listed = MODE == RM_APPLY && !force;
     const int nch = listed ? D.fl->n_list_row : (D.Rpair + BLOCK - 1) / BLOCK;
-    if (MODE == RM_APPLY) {
-      // the operator apply: each warp takes two chunks of 32 rows per
-      // iteration and issues the loads of both (rows, then the islands'
-      // CR-done flags) before reducing either, so that twice as many
-      // independent loads are in flight
-      for (int j = blockIdx.x; j < nch; j += 2 * D.nblk_row_pair) {
-        int ii[2], key[2];
-        bool ok[2];
-        T ta[2], tb[2], zz[2], pp[2], cd[2], ap[2];
-#pragma unroll
-        for (int u = 0; u < 2; u++) {
-          const int jj = j + u * D.nblk_row_pair;
-          const int w0 = jj < nch ? (listed ? D.list_row[jj] : jj) * BLOCK + (threadIdx.x & ~31) : D.Rpair;
-          ok[u] = w0 < D.Rpair;                     // uniform per warp
-          ii[u] = w0 + lane;
-          ta[u] = tb[u] = zz[u] = pp[u] = cd[u] = ap[u] = T(0);
-          key[u] = -1;
-          if (ok[u] && ii[u] < D.Rpair) {
-            const int r = ii[u];
-            ta[u] = D.t[2 * r]; tb[u] = D.t[2 * r + 1]; zz[u] = D.z[r]; pp[u] = D.P[r]; cd[u] = D.cdiag[r];
-            ap[u] = D.Ap[r]; key[u] = D.risl[r];
-          }
-        }
-        int done[2];
-#pragma unroll
-        for (int u = 0; u < 2; u++) done[u] = key[u] >= 0 ? D.isl.crdone[key[u]] : 1;
-#pragma unroll
-        for (int u = 0; u < 2; u++) {
-          if (!ok[u]) continue;
-          const int k = done[u] ? -1 : key[u];
-          const bool v = k >= 0;
-          if (!__any_sync(0xffffffffu, v)) continue;   // the whole warp's islands are finished
-          T a[5] = {T(0), T(0), T(0), T(0), T(0)};
-          if (v) {
-            const T az = (ta[u] + tb[u]) + (cd[u] + eps) * zz[u];
-            D.Az[ii[u]] = az;
-            const T paz = pp[u] * az;
-            a[0] = zz[u] * az; a[1] = az * paz; a[2] = paz * ap[u]; a[3] = zz[u] * zz[u] / pp[u];
-            a[4] = ap[u] * pp[u] * ap[u];
-          }
-          warp_runs_add<T, 5>(k, a, D.isl.acc + 2 * size_t(ni), ni);
-        }
-      }
-    }
-    for (int j = blockIdx.x; MODE != RM_APPLY && j < nch; j += D.nblk_row_pair) {
+    for (int j = blockIdx.x; j < nch; j += D.nblk_row_pair) {
       const int w0 = (listed ? D.list_row[j] : j) * BLOCK + (threadIdx.x & ~31);
       if (w0 >= D.Rpair) continue;                  // a listed block of tet rows (uniform per warp)
       const int i = w0 + lane;
@@ -2241,7 +2197,7 @@ constexpr int RES_NW = RES_THREADS / 32;
 constexpr int RES_G = 8;      // lanes per body in the J^T z gather
 constexpr int RES_KR = 3;     // entries per lane kept in registers between the gather and t_e = J_e y_b
 constexpr int RES_MAXI = 32;  // islands per group (one lane each in the scalar warp)
-constexpr int RES_TASK = 64;  // rows per task (a piece of one island's contact or joint rows)
+constexpr int RES_TASK = 128; // rows per task (a piece of one island's contact or joint rows)
 constexpr int RES_MAXT = 2 * RES_MAXI + 32;   // tasks per group (groups of at most 2048 rows)
 
 __host__ __device__ inline int res_pad(int n) { return (n + 3) & ~3; }
@@ -2255,7 +2211,7 @@ struct alignas(2 * sizeof(T)) RV2 { T a, b; };
 // byte offsets of the arrays of the shared-memory image of one group: RR rows,
 // RE entries, RB bodies, RES_MAXI islands (the same on host and device)
 struct ResLayout {
-  size_t rv, jA, bm, bn, jB, p, x, Az, t, part, alpha, beta, isT, le, risl, erow, seg, bisl, isl, task,
+  size_t rv, jA, bm, bn, jB, p, x, Az, pd, t, part, alpha, beta, isT, le, risl, erow, seg, bisl, isl, task,
       ctl, total;
 };
 
@@ -2278,6 +2234,7 @@ __host__ __device__ inline ResLayout res_layout(int RR, int RE, int RB) {
   L.p = take(sizeof(T) * rr, sizeof(T));
   L.x = take(sizeof(T) * rr, sizeof(T));
   L.Az = take(sizeof(T) * rr, sizeof(T));
+  L.pd = take(sizeof(T) * rr, sizeof(T));
   L.t = take(sizeof(T) * re, sizeof(T));
   L.part = take(sizeof(T) * 5 * RES_MAXT, sizeof(T));
   L.alpha = take(sizeof(T) * RES_MAXI, sizeof(T));
@@ -2303,6 +2260,7 @@ struct ResSmem {
   RV4<T> *rv, *jA, *bm, *bn;
   RV2<T> *jB;
   T *p, *x, *Az, *t, *part, *alpha, *beta;   // part: [5][RES_MAXT] task sums
+  T *pd;                                        // 1 / P per row (the Jacobi diagonal), for ||r||_P^2 = z^2 / P
   T *r02f, *eta2, *res_prev, *rho_prev;        // [RES_MAXI] per island: stop thresholds, ||r||_P^2 and rho of the last iteration
   int2 *le;                                     // local entries of the two sides of each row (-1: none)
   int *risl, *erow, *seg, *bisl;                // island of each row, row of each entry, body segments, island of each body
@@ -2324,6 +2282,7 @@ __device__ inline ResSmem<T> res_carve(unsigned char *base, int RR, int RE, int 
   S.p = reinterpret_cast<T *>(base + L.p);
   S.x = reinterpret_cast<T *>(base + L.x);
   S.Az = reinterpret_cast<T *>(base + L.Az);
+  S.pd = reinterpret_cast<T *>(base + L.pd);
   S.t = reinterpret_cast<T *>(base + L.t);
   S.part = reinterpret_cast<T *>(base + L.part);
   S.alpha = reinterpret_cast<T *>(base + L.alpha);
@@ -2496,7 +2455,9 @@ __global__ void __launch_bounds__(RES_THREADS, sizeof(T) == 4 ? 5 : 2) k_cr_resi
     for (int r = tid; r < nrow; r += RES_THREADS) {
       const int gw = r < ncr_g ? 3 * c0 + r : gc + 5 * j0 + (r - ncr_g);
       const T zi = D.z[gw];                   // P b, from the rhs pass
-      S.rv[r] = RV4<T>{zi, D.P[gw], T(0), D.cdiag[gw] + eps};
+      const T Pr = D.P[gw];
+      S.rv[r] = RV4<T>{zi, Pr, T(0), D.cdiag[gw] + eps};
+      S.pd[r] = T(1) / Pr;
       S.p[r] = zi; S.x[r] = T(0);
       const int a0 = D.re0[gw], a1 = D.re1[gw];
       S.le[r] = make_int2(a0 >= 0 ? a0 - e0 : -1, a1 >= 0 ? a1 - e0 : -1);
@@ -2626,7 +2587,7 @@ __global__ void __launch_bounds__(RES_THREADS, sizeof(T) == 4 ? 5 : 2) k_cr_resi
           const T az = (t0 + t1) + v.d * v.a;
           S.Az[r] = az;
           const T paz = v.b * az;
-          a[0] += v.a * az; a[1] += az * paz; a[2] += paz * v.c; a[3] += v.a * v.a / v.b; a[4] += v.c * v.b * v.c;
+          a[0] += v.a * az; a[1] += az * paz; a[2] += paz * v.c; a[3] += v.a * v.a * S.pd[r]; a[4] += v.c * v.b * v.c;
         }
 #pragma unroll
         for (int q = 0; q < 5; q++) {
