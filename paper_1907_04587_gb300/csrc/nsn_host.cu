@@ -12,6 +12,7 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <thread>
 #include <string>
 #include <vector>
 
@@ -316,6 +317,24 @@ void order_by(int n, int K, const Key &key, std::vector<int> &o, std::vector<int
   for (int i = 0; i < n; i++) o[start[k[i]]++] = i;
 }
 
+// Runs fn(k) for k = 0 .. n-1 on n host threads (the calling thread takes k = 0).
+template <typename F>
+void parallel_for_threads(int n, const F &fn) {
+  if (n <= 1) { fn(0); return; }
+  std::vector<std::thread> th;
+  th.reserve(n - 1);
+  for (int k = 1; k < n; k++) th.emplace_back([&fn, k] { fn(k); });
+  fn(0);
+  for (std::thread &x : th) x.join();
+}
+
+// host threads for a layout pass over n items: one per ~64k items, at most
+// the hardware threads and 16
+int layout_threads(long long n) {
+  const int hw = std::max(1, int(std::thread::hardware_concurrency()));
+  return int(std::max(1LL, std::min<long long>({(n + 65535) / 65536, (long long)hw, 16LL})));
+}
+
 // ------------------------------------------------------------------------------------
 // layout: entries sorted by body (counting sort), rows -> entry ids
 
@@ -367,9 +386,16 @@ nsn_status build_layout(nsn_ctx *c) {
   order_by(L.nt, K, [&](int i) { return rank[L.body_isl[L.tb_rec[i]->v[0]]]; }, L.tperm, L.s_key, L.s_start);
   L.row_abi.resize(L.R);
   L.risl.resize(L.R);
-  for (int ci = 0; ci < L.nc; ci++) {
-    const auto &r = S.contacts[L.cperm[ci]];
-    for (int k = 0; k < 3; k++) { L.row_abi[3 * ci + k] = 3 * L.cperm[ci] + k; L.risl[3 * ci + k] = isl2(r.body_a, r.body_b); }
+  {
+    const int nth = layout_threads(L.nc);
+    parallel_for_threads(nth, [&](int k0) {
+      const int c0 = int((long long)L.nc * k0 / nth), c1 = int((long long)L.nc * (k0 + 1) / nth);
+      for (int ci = c0; ci < c1; ci++) {
+        const auto &r = S.contacts[L.cperm[ci]];
+        const int is = isl2(r.body_a, r.body_b);
+        for (int k = 0; k < 3; k++) { L.row_abi[3 * ci + k] = 3 * L.cperm[ci] + k; L.risl[3 * ci + k] = is; }
+      }
+    });
   }
   for (int j = 0; j < L.nj; j++) {
     const auto &r = S.joints[L.jperm[j]];
@@ -388,67 +414,88 @@ nsn_status build_layout(nsn_ctx *c) {
   for (int i = 0; i < L.nr; i++) L.bisl_r[i] = L.body_isl[L.rig_of[i]];
   for (int i = 0; i < L.np; i++) L.bisl_p[i] = L.body_isl[L.par_of[i]];
   // entries: one per (row, side) with a body, sorted by body (rigid, then
-  // particle) and within a body by row -- a counting sort in two passes over
-  // the constraints in row order (count, then place)
+  // particle) and within a body by row -- a counting sort over the
+  // constraints in row order: each host thread counts the entries of its
+  // range of constraints per body, every (body, thread) pair gets its offset
+  // (bodies in order, threads in order within a body), and each thread
+  // places its range; the result is that of one sequential pass
+  const int nbod = L.nr + L.np;
+  const long long nitems = (long long)L.nc + L.nj + L.nt;
+  const int nth = layout_threads(nitems);
+  auto bidx = [&](int enc) { return enc >= 0 ? enc : L.nr + (-enc - 2); };
+  // item u: contact u, joint u - nc, tet block u - nc - nj (internal order);
+  // fn(row, slot, enc) for each of its entries, rows ascending
+  auto visit = [&](long long u, auto &&fn) {
+    if (u < L.nc) {
+      const int ci = int(u);
+      const nsn_contact &r = S.contacts[L.cperm[ci]];
+      const int ea = r.body_a >= 0 ? L.bmap[r.body_a] : 0, eb = r.body_b >= 0 ? L.bmap[r.body_b] : 0;
+      for (int k = 0; k < 3; k++) {
+        if (r.body_a >= 0) fn(3 * ci + k, 0, ea);
+        if (r.body_b >= 0) fn(3 * ci + k, 1, eb);
+      }
+    } else if (u < (long long)L.nc + L.nj) {
+      const int j = int(u - L.nc);
+      const nsn_revolute &r = S.joints[L.jperm[j]];
+      const int ea = r.body_a >= 0 ? L.bmap[r.body_a] : 0, eb = r.body_b >= 0 ? L.bmap[r.body_b] : 0;
+      for (int k = 0; k < 5; k++) {
+        if (r.body_a >= 0) fn(3 * L.nc + 5 * j + k, 0, ea);
+        if (r.body_b >= 0) fn(3 * L.nc + 5 * j + k, 1, eb);
+      }
+    } else {
+      const int tb = int(u - L.nc - L.nj);
+      const nsn_tet &r = *L.tb_rec[L.tperm[tb]];
+      for (int k = 0; k < 3; k++)
+        for (int q = 0; q < 4; q++) fn(L.Rpair + 3 * tb + k, q, L.bmap[r.v[q]]);
+    }
+  };
+  std::vector<int> &cnt = L.s_cnt;            // [thread][body]: counts, then offsets
+  cnt.assign(size_t(nth) * nbod, 0);
+  parallel_for_threads(nth, [&](int k) {
+    int *ck = cnt.data() + size_t(k) * nbod;
+    const long long u0 = nitems * k / nth, u1 = nitems * (k + 1) / nth;
+    for (long long u = u0; u < u1; u++) visit(u, [&](int, int, int enc) { ck[bidx(enc)]++; });
+  });
   std::vector<int> &rcnt = L.rseg, &pcnt = L.vseg;
   rcnt.assign(size_t(L.nr) + 1, 0);
   pcnt.assign(size_t(L.np) + 1, 0);
-  auto count = [&](int enc, int n) {
-    if (enc >= 0) rcnt[size_t(enc) + 1] += n;
-    else pcnt[size_t(-enc - 2) + 1] += n;
-  };
-  for (int ci = 0; ci < L.nc; ci++) {
-    const nsn_contact &r = S.contacts[L.cperm[ci]];
-    if (r.body_a >= 0) count(L.bmap[r.body_a], 3);
-    if (r.body_b >= 0) count(L.bmap[r.body_b], 3);
+  {
+    int run = 0;
+    for (int b = 0; b < nbod; b++) {
+      if (b == L.nr) run = 0;                 // particle entries are numbered after the rigid ones
+      for (int k = 0; k < nth; k++) {
+        int &x = cnt[size_t(k) * nbod + b];
+        const int n = x;
+        x = run;
+        run += n;
+      }
+      if (b < L.nr) rcnt[size_t(b) + 1] = run;
+      else pcnt[size_t(b - L.nr) + 1] = run;
+    }
   }
-  for (int j = 0; j < L.nj; j++) {
-    const nsn_revolute &r = S.joints[L.jperm[j]];
-    if (r.body_a >= 0) count(L.bmap[r.body_a], 5);
-    if (r.body_b >= 0) count(L.bmap[r.body_b], 5);
-  }
-  for (int t = 0; t < L.nt; t++)
-    for (int q = 0; q < 4; q++) count(L.bmap[L.tb_rec[L.tperm[t]]->v[q]], 3);
-  for (int i = 0; i < L.nr; i++) rcnt[size_t(i) + 1] += rcnt[i];
-  for (int i = 0; i < L.np; i++) pcnt[size_t(i) + 1] += pcnt[i];
   L.ER = rcnt[L.nr];
   L.EV = pcnt[L.np];
   L.eslot.resize(size_t(L.ER) + L.EV);
   L.re0.assign(L.Rpair, -1);
   L.re1.assign(L.Rpair, -1);
   L.te.assign(size_t(12) * L.nt, -1);
-  std::vector<int> &fill = L.s_fill;
-  fill.resize(size_t(L.nr) + L.np);
-  for (int i = 0; i < L.nr; i++) fill[i] = rcnt[i];
-  for (int i = 0; i < L.np; i++) fill[size_t(L.nr) + i] = L.ER + pcnt[i];
-  auto place = [&](int enc) { return enc >= 0 ? fill[enc]++ : fill[size_t(L.nr) + (-enc - 2)]++; };
-  for (int ci = 0; ci < L.nc; ci++) {
-    const nsn_contact &r = S.contacts[L.cperm[ci]];
-    const int ea = r.body_a >= 0 ? L.bmap[r.body_a] : 0, eb = r.body_b >= 0 ? L.bmap[r.body_b] : 0;
-    for (int k = 0; k < 3; k++) {
-      const int row = 3 * ci + k;
-      if (r.body_a >= 0) { const int e = place(ea); L.re0[row] = e; L.eslot[e] = 2 * row; }
-      if (r.body_b >= 0) { const int e = place(eb); L.re1[row] = e; L.eslot[e] = 2 * row + 1; }
-    }
-  }
-  for (int j = 0; j < L.nj; j++) {
-    const nsn_revolute &r = S.joints[L.jperm[j]];
-    const int ea = r.body_a >= 0 ? L.bmap[r.body_a] : 0, eb = r.body_b >= 0 ? L.bmap[r.body_b] : 0;
-    for (int k = 0; k < 5; k++) {
-      const int row = 3 * L.nc + 5 * j + k;
-      if (r.body_a >= 0) { const int e = place(ea); L.re0[row] = e; L.eslot[e] = 2 * row; }
-      if (r.body_b >= 0) { const int e = place(eb); L.re1[row] = e; L.eslot[e] = 2 * row + 1; }
-    }
-  }
-  for (int t = 0; t < L.nt; t++) {
-    const nsn_tet &r = *L.tb_rec[L.tperm[t]];
-    for (int k = 0; k < 3; k++)
-      for (int q = 0; q < 4; q++) {
-        const int e = place(L.bmap[r.v[q]]);
-        L.te[12 * t + 4 * k + q] = e;
-        L.eslot[e] = 2 * L.Rpair + 12 * t + 4 * k + q;
-      }
-  }
+  parallel_for_threads(nth, [&](int k) {
+    int *ok = cnt.data() + size_t(k) * nbod;
+    const long long u0 = nitems * k / nth, u1 = nitems * (k + 1) / nth;
+    for (long long u = u0; u < u1; u++)
+      visit(u, [&](int row, int slot, int enc) {
+        const int b = bidx(enc);
+        const int e = (b >= L.nr ? L.ER : 0) + ok[b]++;
+        if (row < L.Rpair) {
+          (slot == 0 ? L.re0 : L.re1)[row] = e;
+          L.eslot[e] = 2 * row + slot;
+        } else {
+          const int tb = (row - L.Rpair) / 3, kk = (row - L.Rpair) % 3;
+          L.te[12 * tb + 4 * kk + slot] = e;
+          L.eslot[e] = 2 * L.Rpair + 12 * tb + 4 * kk + slot;
+        }
+      });
+  });
   // per-island ranges (each island's bodies, contacts and joints are
   // contiguous in the internal order) and eligibility for the resident CR
   L.ires.assign(size_t(8) * std::max(L.ni, 1), 0);
@@ -1309,10 +1356,12 @@ nsn_status save_lam_prev(nsn_ctx *c, std::vector<double> &out) {
   return NSN_OK;
 }
 
+// lam_prev of the new build: row i takes the kept multiplier of the old
+// internal row that the map assigns to its ABI row (-1: zero)
 template <typename T>
-__global__ void k_gather_lam(T *dst, const T *src, const int *map, int n) {
+__global__ void k_gather_lam(T *dst, const T *src, const int *map_abi, const int *row_abi, int n) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const int o = map[i];
+    const int o = map_abi[row_abi[i]];
     dst[i] = o >= 0 ? src[o] : T(0);
   }
 }
@@ -1373,6 +1422,8 @@ nsn_status restore_from_keep(nsn_ctx *c, const std::vector<nsn_contact> &old_con
   const Layout &L = c->L;
   const HostScene &S = c->scene;
   if (L.R == 0 || !c->keep_lam) return NSN_OK;
+  // map[ABI row] = old internal row (-1: none), built in ABI order (the
+  // collider emits contacts by body, so the lookups walk the buckets in order)
   int *map = c->stage.take<int>(L.R);
   if (!map) return fail(c, NSN_ERR_OUT_OF_MEMORY, "pinned staging of the multiplier map");
   std::fill(map, map + L.R, -1);
@@ -1395,8 +1446,8 @@ nsn_status restore_from_keep(nsn_ctx *c, const std::vector<nsn_contact> &old_con
     std::memcpy(k.p, r.pa, sizeof k.p);
     k.idx = list[jj] < int(c->old_cinv.size()) ? c->old_cinv[list[jj]] : -1;
   }
-  for (int ci = 0; ci < L.nc; ci++) {
-    const nsn_contact &r = S.contacts[L.cperm[ci]];
+  for (int cc = 0; cc < L.nc; cc++) {
+    const nsn_contact &r = S.contacts[cc];
     const int sl = r.body_a + 1;
     if (sl < 0 || sl > nb) continue;
     uint32_t p[3];
@@ -1405,27 +1456,23 @@ nsn_status restore_from_keep(nsn_ctx *c, const std::vector<nsn_contact> &old_con
       const ContactKeyRec &k = ok[jj];
       if (k.b == r.body_b && k.p[0] == p[0] && k.p[1] == p[1] && k.p[2] == p[2] && k.a == r.body_a) {
         if (k.idx >= 0)
-          for (int q = 0; q < 3; q++) map[3 * ci + q] = 3 * k.idx + q;
+          for (int q = 0; q < 3; q++) map[3 * cc + q] = 3 * k.idx + q;
         break;
       }
     }
   }
   if (old_nj == L.nj && int(c->old_jinv.size()) == L.nj)
-    for (int j = 0; j < L.nj; j++) {
-      const int oj = c->old_jinv[L.jperm[j]];
-      for (int q = 0; q < 5; q++) map[3 * L.nc + 5 * j + q] = 3 * c->old_nc + 5 * oj + q;
-    }
+    for (int a = 0; a < L.nj; a++)
+      for (int q = 0; q < 5; q++) map[3 * L.nc + 5 * a + q] = 3 * c->old_nc + 5 * c->old_jinv[a] + q;
   if (old_nt == L.nt && old_nj == L.nj && int(c->old_tinv.size()) == L.nt)
-    for (int tb = 0; tb < L.nt; tb++) {
-      const int ot = c->old_tinv[L.tperm[tb]];
-      for (int q = 0; q < 3; q++) map[L.Rpair + 3 * tb + q] = c->old_Rpair + 3 * ot + q;
-    }
+    for (int b = 0; b < L.nt; b++)
+      for (int q = 0; q < 3; q++) map[L.tb_abi[b] + q] = c->old_Rpair + 3 * c->old_tinv[b] + q;
   // the map goes to the device through the entry scratch t2 (rewritten by
   // every evaluation before it is read)
   int *dmap = reinterpret_cast<int *>(D.t2);
   CUDA_TRY(c, cudaMemcpyAsync(dmap, map, sizeof(int) * L.R, cudaMemcpyHostToDevice, c->stream));
   k_gather_lam<T><<<clampb(cdiv(L.R, 256), D.max_blk), 256, 0, c->stream>>>(D.lam_prev, static_cast<const T *>(c->keep_lam),
-                                                                         dmap, L.R);
+                                                                         dmap, D.row_abi_dev, L.R);
   CUDA_TRY(c, cudaGetLastError());
   CUDA_TRY(c, cudaMemsetAsync(D.t2, 0, sizeof(T) * std::max(2 * L.Rpair + 12 * L.nt, 1), c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));

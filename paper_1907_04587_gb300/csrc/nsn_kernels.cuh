@@ -2197,7 +2197,7 @@ constexpr int RES_NW = RES_THREADS / 32;
 constexpr int RES_G = 8;      // lanes per body in the J^T z gather
 constexpr int RES_KR = 3;     // entries per lane kept in registers between the gather and t_e = J_e y_b
 constexpr int RES_MAXI = 32;  // islands per group (one lane each in the scalar warp)
-constexpr int RES_TASK = 128; // rows per task (a piece of one island's contact or joint rows)
+constexpr int RES_TASK = 64;  // rows per task (a piece of one island's contact or joint rows)
 constexpr int RES_MAXT = 2 * RES_MAXI + 32;   // tasks per group (groups of at most 2048 rows)
 
 __host__ __device__ inline int res_pad(int n) { return (n + 3) & ~3; }
