@@ -581,7 +581,8 @@ void carve(Arena &A, Dev<T> &D, const Layout &L, int nb) {
   D.eslot = A.take<int>(size_t(L.ER) + L.EV);
   D.rseg = A.take<int>(L.nr + 1);
   D.vseg = A.take<int>(L.np + 1);
-  for (int k = 0; k < 6; k++) D.ej6[k] = tk(L.ER);
+  D.ejA = A.take<RV4<T>>(L.ER);
+  D.ejB = A.take<RV2<T>>(L.ER);
   for (int b = 0; b < 2; b++)
     for (int k = 0; k < 3; k++) D.ej3[b][k] = tk(L.EV);
   D.t = tk(2 * L.Rpair + 12 * L.nt);
@@ -1804,8 +1805,13 @@ nsn_status do_solve(nsn_ctx *c, int iters, double *dl, double *du) {
     std::vector<T> g6(size_t(6) * L.nr), g3(size_t(3) * L.np), Iwi(size_t(6) * L.nr), hinv(size_t(3) * L.np), im(L.nr);
     int bufJ = -1;
     (void)bufJ;
+    std::vector<RV4<T>> jA(L.ER);
+    std::vector<RV2<T>> jB(L.ER);
+    if (L.ER) {
+      CUDA_TRY(c, cudaMemcpyAsync(jA.data(), D.ejA, sizeof(RV4<T>) * L.ER, cudaMemcpyDeviceToHost, st));
+      CUDA_TRY(c, cudaMemcpyAsync(jB.data(), D.ejB, sizeof(RV2<T>) * L.ER, cudaMemcpyDeviceToHost, st));
+    }
     for (int k = 0; k < 6; k++) {
-      if (L.ER) CUDA_TRY(c, cudaMemcpyAsync(J6.data() + size_t(k) * L.ER, D.ej6[k], sizeof(T) * L.ER, cudaMemcpyDeviceToHost, st));
       if (L.nr) {
         CUDA_TRY(c, cudaMemcpyAsync(g6.data() + size_t(k) * L.nr, D.rg[k], sizeof(T) * L.nr, cudaMemcpyDeviceToHost, st));
         CUDA_TRY(c, cudaMemcpyAsync(Iwi.data() + size_t(k) * L.nr, D.rIwi[k], sizeof(T) * L.nr, cudaMemcpyDeviceToHost, st));
@@ -1821,6 +1827,10 @@ nsn_status do_solve(nsn_ctx *c, int iters, double *dl, double *du) {
       }
     }
     CUDA_TRY(c, cudaStreamSynchronize(st));
+    for (int q = 0; q < L.ER; q++) {
+      const T v[6] = {jA[q].a, jA[q].b, jA[q].c, jA[q].d, jB[q].a, jB[q].b};
+      for (int k = 0; k < 6; k++) J6[size_t(k) * L.ER + q] = v[k];
+    }
     const double h = c->cfg.h;
     int off = 0;
     for (int i = 0; i < nb; i++) {

@@ -7,7 +7,7 @@
 //   entries        one per (row, side): rigid entries [0, ER) sorted by body,
 //                  particle entries [ER, ER+EV) sorted by particle; eslot[e]
 //                  is the row-ordered slot of the entry's output (its row
-//                  follows from it), ej6[6][ER] / ej3[2][3][EV] the Jacobian values
+//                  follows from it), ejA/ejB[ER] (4 + 2 values) / ej3[2][3][EV] the Jacobian values
 //                  (particle values double-buffered by Newton iteration for
 //                  the geometric stiffness), rseg / vseg the segment offsets.
 //   rows           pair rows (contacts, joints) carry entry ids re0/re1
@@ -144,6 +144,13 @@ struct RedT { using type = DS; };
 template <>
 struct RedT<double> { using type = double; };
 
+// vectors loaded and stored whole (the rigid Jacobian entries in HBM, the
+// resident CR's shared-memory image)
+template <typename T>
+struct alignas(4 * sizeof(T)) RV4 { T a, b, c, d; };
+template <typename T>
+struct alignas(2 * sizeof(T)) RV2 { T a, b; };
+
 template <typename T>
 struct Dev {
   // sizes
@@ -162,7 +169,8 @@ struct Dev {
   // entries
   int *eslot;        // row-ordered output slot of each entry (see slot_row)
   int *rseg, *vseg;
-  T *ej6[6];
+  RV4<T> *ejA;         // rigid entries: J_0..J_3 (one vector load)
+  RV2<T> *ejB;         //                J_4, J_5
   T *ej3[2][3];
   T *t, *t2;
   // rows
@@ -737,7 +745,8 @@ template <typename T>
 __device__ __forceinline__ void write_entry(const Dev<T> &D, int e, const T *J6, int buf) {
   if (e < 0) return;
   if (e < D.ER) {
-    for (int k = 0; k < 6; k++) D.ej6[k][e] = J6[k];
+    D.ejA[e] = RV4<T>{J6[0], J6[1], J6[2], J6[3]};
+    D.ejB[e] = RV2<T>{J6[4], J6[5]};
   } else {
     const int v = e - D.ER;
     for (int k = 0; k < 3; k++) D.ej3[buf][k][v] = J6[k];
@@ -1264,8 +1273,9 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 && MODE == BM_APPLY ? 5 
       for (int r = 0; r < KR; r++) {
         const int e = s0 + lane + r * G;
         if (sl[r] >= 0) {
-#pragma unroll
-          for (int k = 0; k < 6; k++) J[r][k] = D.ej6[k][e];
+          const RV4<T> ja = D.ejA[e];
+          const RV2<T> jb = D.ejB[e];
+          J[r][0] = ja.a; J[r][1] = ja.b; J[r][2] = ja.c; J[r][3] = ja.d; J[r][4] = jb.a; J[r][5] = jb.b;
           xv[r] = in[slot_row(sl[r], Rp)];
         } else {
 #pragma unroll
@@ -1280,8 +1290,9 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 && MODE == BM_APPLY ? 5 
         for (int k = 0; k < 6; k++) s[k] += J[r][k] * xv[r];
       for (int e = s0 + lane + KR * G; e < s1; e += G) {
         const T x = in[slot_row(D.eslot[e], Rp)];
-#pragma unroll
-        for (int k = 0; k < 6; k++) s[k] += D.ej6[k][e] * x;
+        const RV4<T> ja = D.ejA[e];
+        const RV2<T> jb = D.ejB[e];
+        s[0] += ja.a * x; s[1] += ja.b * x; s[2] += ja.c * x; s[3] += ja.d * x; s[4] += jb.a * x; s[5] += jb.b * x;
       }
 #pragma unroll
       for (int k = 0; k < 6; k++) s[k] = group_sum<G>(s[k]);
@@ -1369,8 +1380,9 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 && MODE == BM_APPLY ? 5 
       }
       for (int e = s0 + lane + KR * G; e < s1; e += G) {
         T Je[6];
-#pragma unroll
-        for (int k = 0; k < 6; k++) Je[k] = D.ej6[k][e];
+        const RV4<T> ja = D.ejA[e];
+        const RV2<T> jb = D.ejB[e];
+        Je[0] = ja.a; Je[1] = ja.b; Je[2] = ja.c; Je[3] = ja.d; Je[4] = jb.a; Je[5] = jb.b;
         T acc = T(0);
 #pragma unroll
         for (int k = 0; k < 6; k++) acc += Je[k] * y[k];
@@ -2202,16 +2214,11 @@ constexpr int RES_MAXT = 2 * RES_MAXI + 32;   // tasks per group (groups of at m
 
 __host__ __device__ inline int res_pad(int n) { return (n + 3) & ~3; }
 
-// vectors of the shared-memory image, loaded and stored whole
-template <typename T>
-struct alignas(4 * sizeof(T)) RV4 { T a, b, c, d; };
-template <typename T>
-struct alignas(2 * sizeof(T)) RV2 { T a, b; };
 
 // byte offsets of the arrays of the shared-memory image of one group: RR rows,
 // RE entries, RB bodies, RES_MAXI islands (the same on host and device)
 struct ResLayout {
-  size_t rv, jA, bm, bn, jB, p, x, Az, pd, t, part, alpha, beta, isT, le, risl, erow, seg, bisl, isl, task,
+  size_t rv, jA, bm, bn, jB, p, x, Az, t, part, alpha, beta, isT, le, risl, erow, seg, bisl, isl, task,
       ctl, total;
 };
 
@@ -2234,7 +2241,6 @@ __host__ __device__ inline ResLayout res_layout(int RR, int RE, int RB) {
   L.p = take(sizeof(T) * rr, sizeof(T));
   L.x = take(sizeof(T) * rr, sizeof(T));
   L.Az = take(sizeof(T) * rr, sizeof(T));
-  L.pd = take(sizeof(T) * rr, sizeof(T));
   L.t = take(sizeof(T) * re, sizeof(T));
   L.part = take(sizeof(T) * 5 * RES_MAXT, sizeof(T));
   L.alpha = take(sizeof(T) * RES_MAXI, sizeof(T));
@@ -2260,7 +2266,6 @@ struct ResSmem {
   RV4<T> *rv, *jA, *bm, *bn;
   RV2<T> *jB;
   T *p, *x, *Az, *t, *part, *alpha, *beta;   // part: [5][RES_MAXT] task sums
-  T *pd;                                        // 1 / P per row (the Jacobi diagonal), for ||r||_P^2 = z^2 / P
   T *r02f, *eta2, *res_prev, *rho_prev;        // [RES_MAXI] per island: stop thresholds, ||r||_P^2 and rho of the last iteration
   int2 *le;                                     // local entries of the two sides of each row (-1: none)
   int *risl, *erow, *seg, *bisl;                // island of each row, row of each entry, body segments, island of each body
@@ -2282,7 +2287,6 @@ __device__ inline ResSmem<T> res_carve(unsigned char *base, int RR, int RE, int 
   S.p = reinterpret_cast<T *>(base + L.p);
   S.x = reinterpret_cast<T *>(base + L.x);
   S.Az = reinterpret_cast<T *>(base + L.Az);
-  S.pd = reinterpret_cast<T *>(base + L.pd);
   S.t = reinterpret_cast<T *>(base + L.t);
   S.part = reinterpret_cast<T *>(base + L.part);
   S.alpha = reinterpret_cast<T *>(base + L.alpha);
@@ -2447,17 +2451,15 @@ __global__ void __launch_bounds__(RES_THREADS, sizeof(T) == 4 ? 5 : 2) k_cr_resi
     if (tid == 0) S.seg[nb] = ne;
     for (int e = tid; e < ne; e += RES_THREADS) {
       const int ge = e0 + e;
-      S.jA[e] = RV4<T>{D.ej6[0][ge], D.ej6[1][ge], D.ej6[2][ge], D.ej6[3][ge]};
-      S.jB[e] = RV2<T>{D.ej6[4][ge], D.ej6[5][ge]};
+      S.jA[e] = D.ejA[ge];
+      S.jB[e] = D.ejB[ge];
       const int gw = slot_row(D.eslot[ge], D.Rpair);
       S.erow[e] = gw < gc ? gw - 3 * c0 : ncr_g + (gw - gc - 5 * j0);
     }
     for (int r = tid; r < nrow; r += RES_THREADS) {
       const int gw = r < ncr_g ? 3 * c0 + r : gc + 5 * j0 + (r - ncr_g);
       const T zi = D.z[gw];                   // P b, from the rhs pass
-      const T Pr = D.P[gw];
-      S.rv[r] = RV4<T>{zi, Pr, T(0), D.cdiag[gw] + eps};
-      S.pd[r] = T(1) / Pr;
+      S.rv[r] = RV4<T>{zi, D.P[gw], T(0), D.cdiag[gw] + eps};
       S.p[r] = zi; S.x[r] = T(0);
       const int a0 = D.re0[gw], a1 = D.re1[gw];
       S.le[r] = make_int2(a0 >= 0 ? a0 - e0 : -1, a1 >= 0 ? a1 - e0 : -1);
@@ -2587,7 +2589,7 @@ __global__ void __launch_bounds__(RES_THREADS, sizeof(T) == 4 ? 5 : 2) k_cr_resi
           const T az = (t0 + t1) + v.d * v.a;
           S.Az[r] = az;
           const T paz = v.b * az;
-          a[0] += v.a * az; a[1] += az * paz; a[2] += paz * v.c; a[3] += v.a * v.a * S.pd[r]; a[4] += v.c * v.b * v.c;
+          a[0] += v.a * az; a[1] += az * paz; a[2] += paz * v.c; a[3] += v.a * v.a / v.b; a[4] += v.c * v.b * v.c;
         }
 #pragma unroll
         for (int q = 0; q < 5; q++) {
