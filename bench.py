@@ -195,6 +195,9 @@ SMEM_BYTES_PER_SM_CLK = 128
 FP32_FLOP_PER_SM_CLK = 256
 
 
+RESIDENT_TRAFFIC_ROWS = 1259819   # rows of the batched2048 scene the resident traffic was captured on
+
+
 def resident_roofline(g, clk):
     """k_cr_resident timed live at full activity (the first Newton iteration
     of a zero start: every resident island iterates), with its algorithmic
@@ -213,7 +216,9 @@ def resident_roofline(g, clk):
     smem_peak = nsm * SMEM_BYTES_PER_SM_CLK * mhz * 1e6 / 1e9
     fp32_peak = nsm * FP32_FLOP_PER_SM_CLK * mhz * 1e6 / 1e12
     ach = smem / (ms * 1e-3) / 1e9
-    traffic = operator_traffic(kernel_source_hash(), "resident_cr_batched4096.json", "dram_bytes_per_launch")
+    traffic = operator_traffic(kernel_source_hash(), "resident_cr_batched2048.json", "dram_bytes_per_launch")
+    if traffic is not None:      # captured at 2048 environments: scaled to this scene by its rows
+        traffic *= g.sizes()["rows"] / RESIDENT_TRAFFIC_ROWS
     return {"bound": "smem", "achieved": ach, "peak": smem_peak, "unit": "GB/s", "frac": ach / smem_peak,
             "traffic": traffic,
             "kernel": "k_cr_resident (one thread block per group of islands, all CR iterations of a Newton iteration from shared memory)",
@@ -345,9 +350,10 @@ def oracle_collide_rate(s, planes, exclude, margin=0.01, h=1.0 / 60.0, n_envs_sa
 
 
 def kernel_source_hash():
+    """sha256 of the kernels' source file: an ncu traffic figure counts only
+    if it was taken on these kernels."""
     h = hashlib.sha256()
-    for f in ("nsn_kernels.cuh", "nsn_host.cu"):
-        h.update(open(os.path.join(ROOT, "paper_1907_04587_gb300", "csrc", f), "rb").read())
+    h.update(open(os.path.join(ROOT, "paper_1907_04587_gb300", "csrc", "nsn_kernels.cuh"), "rb").read())
     return h.hexdigest()
 
 
@@ -752,7 +758,8 @@ def run_ours(args, rank, world, local_rank):
                 ga = make_solver(nsn, s, stream, newton, cr, cone=cone, warm=wm, params=params, ncp=ncp, rscale=rs, ls=ls,
                                  fp64=fp64)
                 try:
-                    r = measure_arm(nsn, torch, ga, s, st0, stream, args.steps, args.warmup, reset=reset,
+                    r = measure_arm(nsn, torch, ga, s, st0, stream, min(args.steps, args.arm_steps),
+                                    min(args.warmup, 3), reset=reset,
                                     collider=collider)
                 except nsn.NSNError as e:      # the method failing on this variant is a result
                     arms[name] = {"failed": str(e)}
@@ -840,8 +847,10 @@ def run_ours(args, rank, world, local_rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--arm-steps", type=int, default=20,
+                    help="timed steps of each comparison arm (after min(warmup, 3) warm-up steps)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="batched4096", choices=list(WORKLOADS))
     ap.add_argument("--newton", type=int, default=0)

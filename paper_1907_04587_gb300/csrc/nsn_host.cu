@@ -784,13 +784,17 @@ nsn_status upload(nsn_ctx *c, Dev<T> &D) {
     T *f[11];
     for (int k = 0; k < 11; k++) f[k] = stage(nc);
     if (oom) return fail(c, NSN_ERR_OUT_OF_MEMORY, "pinned staging of the upload");
-    for (size_t i = 0; i < nc; i++) {
-      const nsn_contact &r = S.contacts[L.cperm[i]];
-      a[i] = r.body_a >= 0 ? L.bmap[r.body_a] : -1;
-      b[i] = r.body_b >= 0 ? L.bmap[r.body_b] : -1;
-      for (int k = 0; k < 3; k++) { f[k][i] = T(r.pa[k]); f[3 + k][i] = T(r.pb[k]); f[6 + k][i] = T(r.n[k]); }
-      f[9][i] = T(r.d); f[10][i] = T(r.mu);
-    }
+    const int nth = layout_threads((long long)nc);
+    parallel_for_threads(nth, [&](int k0) {
+      const size_t i0 = nc * size_t(k0) / nth, i1 = nc * size_t(k0 + 1) / nth;
+      for (size_t i = i0; i < i1; i++) {
+        const nsn_contact &r = S.contacts[L.cperm[i]];
+        a[i] = r.body_a >= 0 ? L.bmap[r.body_a] : -1;
+        b[i] = r.body_b >= 0 ? L.bmap[r.body_b] : -1;
+        for (int k = 0; k < 3; k++) { f[k][i] = T(r.pa[k]); f[3 + k][i] = T(r.pb[k]); f[6 + k][i] = T(r.n[k]); }
+        f[9][i] = T(r.d); f[10][i] = T(r.mu);
+      }
+    });
     CUDA_TRY(c, puti(D.cba, a, nc)); CUDA_TRY(c, puti(D.cbb, b, nc));
     for (int k = 0; k < 3; k++) {
       CUDA_TRY(c, put(D.cpa[k], f[k], nc)); CUDA_TRY(c, put(D.cpb[k], f[3 + k], nc)); CUDA_TRY(c, put(D.cn[k], f[6 + k], nc));
@@ -1447,21 +1451,25 @@ nsn_status restore_from_keep(nsn_ctx *c, const std::vector<nsn_contact> &old_con
     std::memcpy(k.p, r.pa, sizeof k.p);
     k.idx = list[jj] < int(c->old_cinv.size()) ? c->old_cinv[list[jj]] : -1;
   }
-  for (int cc = 0; cc < L.nc; cc++) {
-    const nsn_contact &r = S.contacts[cc];
-    const int sl = r.body_a + 1;
-    if (sl < 0 || sl > nb) continue;
-    uint32_t p[3];
-    std::memcpy(p, r.pa, sizeof p);
-    for (int jj = sl == 0 ? 0 : end[sl - 1]; jj < end[sl]; jj++) {
-      const ContactKeyRec &k = ok[jj];
-      if (k.b == r.body_b && k.p[0] == p[0] && k.p[1] == p[1] && k.p[2] == p[2] && k.a == r.body_a) {
-        if (k.idx >= 0)
-          for (int q = 0; q < 3; q++) map[3 * cc + q] = 3 * k.idx + q;
-        break;
+  const int nthm = layout_threads(L.nc);
+  parallel_for_threads(nthm, [&](int k0) {
+    const int c0 = int((long long)L.nc * k0 / nthm), c1 = int((long long)L.nc * (k0 + 1) / nthm);
+    for (int cc = c0; cc < c1; cc++) {
+      const nsn_contact &r = S.contacts[cc];
+      const int sl = r.body_a + 1;
+      if (sl < 0 || sl > nb) continue;
+      uint32_t p[3];
+      std::memcpy(p, r.pa, sizeof p);
+      for (int jj = sl == 0 ? 0 : end[sl - 1]; jj < end[sl]; jj++) {
+        const ContactKeyRec &k = ok[jj];
+        if (k.b == r.body_b && k.p[0] == p[0] && k.p[1] == p[1] && k.p[2] == p[2] && k.a == r.body_a) {
+          if (k.idx >= 0)
+            for (int q = 0; q < 3; q++) map[3 * cc + q] = 3 * k.idx + q;
+          break;
+        }
       }
     }
-  }
+  });
   if (old_nj == L.nj && int(c->old_jinv.size()) == L.nj)
     for (int a = 0; a < L.nj; a++)
       for (int q = 0; q < 5; q++) map[3 * L.nc + 5 * a + q] = 3 * c->old_nc + 5 * c->old_jinv[a] + q;
