@@ -750,8 +750,8 @@ def run_ours(args, rank, world, local_rank):
                                                    ("ablation_r_h2", 1, nsn.NSN_WARM_ZERO, True, 0, 1, 0),
                                                    ("ablation_r_identity", 1, nsn.NSN_WARM_ZERO, True, 0, 0, 0)):
                 fp64 = name == "fp64_bulk"
-                if wm == warm_names[warm] and not reset and cone == 1 and ncp == 0 and rs == 2 and ls == LS and not fp64:
-                    continue
+                # the headline's own configuration runs as an arm too: the arms time
+                # fewer steps than the headline, and compare with it at equal length
                 if (wm & 0xff) == nsn.NSN_WARM_LEARNED and params is None:
                     arms[name] = {"unavailable": "no trained weights (paper_1907_04587_gb300/weights)"}
                     continue

@@ -307,12 +307,23 @@ void find_islands(const HostScene &S, Layout &L, int nb) {
 
 // stable order of n items by an integer key in [0, K) (counting sort: the
 // layout is rebuilt whenever contacts are regenerated, so it stays linear)
+template <typename F>
+void parallel_for_threads(int n, const F &fn);
+int layout_threads(long long n);
+
 template <typename Key>
 void order_by(int n, int K, const Key &key, std::vector<int> &o, std::vector<int> &k, std::vector<int> &start) {
   k.resize(n);
   start.assign(size_t(K) + 1, 0);
   o.resize(n);
-  for (int i = 0; i < n; i++) { k[i] = key(i); start[size_t(k[i]) + 1]++; }
+  // the keys (random reads of the constraint records and island tables) on
+  // host threads; the histogram and the stable scatter in one pass each
+  const int nth = layout_threads(n);
+  parallel_for_threads(nth, [&](int t) {
+    const int i0 = int((long long)n * t / nth), i1 = int((long long)n * (t + 1) / nth);
+    for (int i = i0; i < i1; i++) k[i] = key(i);
+  });
+  for (int i = 0; i < n; i++) start[size_t(k[i]) + 1]++;
   for (int j = 0; j < K; j++) start[size_t(j) + 1] += start[j];
   for (int i = 0; i < n; i++) o[start[k[i]]++] = i;
 }
@@ -449,12 +460,12 @@ nsn_status build_layout(nsn_ctx *c) {
         for (int q = 0; q < 4; q++) fn(L.Rpair + 3 * tb + k, q, L.bmap[r.v[q]]);
     }
   };
-  std::vector<int> &cnt = L.s_cnt;            // [thread][body]: counts, then offsets
+  std::vector<int> &cnt = L.s_cnt;            // [body][thread]: counts, then offsets
   cnt.assign(size_t(nth) * nbod, 0);
   parallel_for_threads(nth, [&](int k) {
-    int *ck = cnt.data() + size_t(k) * nbod;
+    int *ck = cnt.data() + k;
     const long long u0 = nitems * k / nth, u1 = nitems * (k + 1) / nth;
-    for (long long u = u0; u < u1; u++) visit(u, [&](int, int, int enc) { ck[bidx(enc)]++; });
+    for (long long u = u0; u < u1; u++) visit(u, [&](int, int, int enc) { ck[size_t(bidx(enc)) * nth]++; });
   });
   std::vector<int> &rcnt = L.rseg, &pcnt = L.vseg;
   rcnt.assign(size_t(L.nr) + 1, 0);
@@ -464,7 +475,7 @@ nsn_status build_layout(nsn_ctx *c) {
     for (int b = 0; b < nbod; b++) {
       if (b == L.nr) run = 0;                 // particle entries are numbered after the rigid ones
       for (int k = 0; k < nth; k++) {
-        int &x = cnt[size_t(k) * nbod + b];
+        int &x = cnt[size_t(b) * nth + k];
         const int n = x;
         x = run;
         run += n;
@@ -480,12 +491,12 @@ nsn_status build_layout(nsn_ctx *c) {
   L.re1.assign(L.Rpair, -1);
   L.te.assign(size_t(12) * L.nt, -1);
   parallel_for_threads(nth, [&](int k) {
-    int *ok = cnt.data() + size_t(k) * nbod;
+    int *ok = cnt.data() + k;
     const long long u0 = nitems * k / nth, u1 = nitems * (k + 1) / nth;
     for (long long u = u0; u < u1; u++)
       visit(u, [&](int row, int slot, int enc) {
         const int b = bidx(enc);
-        const int e = (b >= L.nr ? L.ER : 0) + ok[b]++;
+        const int e = (b >= L.nr ? L.ER : 0) + ok[size_t(b) * nth]++;
         if (row < L.Rpair) {
           (slot == 0 ? L.re0 : L.re1)[row] = e;
           L.eslot[e] = 2 * row + slot;
