@@ -372,8 +372,16 @@ nsn_status nsn_get_warm_stats(nsn_ctx *ctx, double *merit_zero, double *merit_wa
  * them resets the Adam state.  get_params also returns the last gradients. */
 nsn_status nsn_mlp_set_params(nsn_ctx *ctx, const float *params, int32_t n);
 nsn_status nsn_mlp_get_params(nsn_ctx *ctx, float *params, float *grads, int32_t n);
-/* Y[n][4] = network(X[n][16]); device pointers, context stream. */
+/* Y[n][4] = network(X[n][16]); device pointers, context stream; returns after
+ * the call has finished.  Inference runs on the tensor cores (tcgen05, FP32
+ * accumulators in tensor memory) with BF16 inputs, weights and activations;
+ * X may have any 4-byte alignment.  A completion wait of the tensor cores
+ * that exceeds its bound: NSN_ERR_TIMEOUT (the outputs are then incomplete).
+ * nsn_mlp_time_forward: the same call repeated reps >= 1 times on the
+ * context's stream between two CUDA events, *ms (host) = mean device time
+ * of one call. */
 nsn_status nsn_mlp_forward(nsn_ctx *ctx, const float *X, int32_t n, float *Y);
+nsn_status nsn_mlp_time_forward(nsn_ctx *ctx, const float *X, int32_t n, float *Y, int32_t reps, float *ms);
 /* One training step on a batch (device X[n][16], targets T[n][4], output
  * weights w[4]): loss 1/(2n) sum w_k (y_k - t_k)^2, backward on the tensor
  * cores, Adam (lr; lr = 0 only computes the gradients); *loss (host) gets the

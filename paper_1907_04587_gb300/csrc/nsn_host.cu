@@ -19,6 +19,7 @@
 #include "../../include/nsn.h"
 #include "nsn_kernels.cuh"
 #include "nsn_mlp.cuh"
+#include "nsn_mlp_tc.cuh"
 #include "nsn_internal.h"
 
 using namespace nsn;
@@ -120,6 +121,7 @@ struct MlpState {
   // per-contact features and predictions for the learned warm start
   int ncap = 0;
   float *X = nullptr, *Y = nullptr;
+  int *err = nullptr;   // set by the inference kernel when a tensor-core wait timed out
 };
 
 }  // namespace
@@ -161,6 +163,7 @@ struct PinnedStage {
 struct ContactKeyRec {
   int32_t a, b;
   uint32_t p[3];
+  uint32_t n[3];   // compared for contacts with the world only: the plane's normal
   int idx;
 };
 
@@ -994,6 +997,7 @@ __global__ void k_backup_state(Dev<T> D, T *buf, int restore) {
 // step orchestration
 
 nsn_status mlp_infer(nsn_ctx *c, const float *X, int n, float *Y, cudaStream_t st);
+nsn_status mlp_check(nsn_ctx *c, cudaStream_t st);
 
 template <typename T>
 struct Launcher {
@@ -1428,7 +1432,9 @@ nsn_status keep_for_rebuild(nsn_ctx *c) {
 }
 
 // After the rebuild: lam_prev of the new build from the kept one -- contact
-// rows by key (body pair and point on a), joint and tet rows by position when
+// rows by key (body pair and point on a; against the world also the normal,
+// which is the plane's, so that a vertex touching two planes keeps one
+// multiplier per plane), joint and tet rows by position when
 // their counts did not change; rows without a match start from zero (a new
 // contact has no previous-step multiplier).  The host computes the map from
 // new to old internal rows; a kernel gathers.
@@ -1460,6 +1466,7 @@ nsn_status restore_from_keep(nsn_ctx *c, const std::vector<nsn_contact> &old_con
     ContactKeyRec &k = ok[jj];
     k.a = r.body_a; k.b = r.body_b;
     std::memcpy(k.p, r.pa, sizeof k.p);
+    std::memcpy(k.n, r.n, sizeof k.n);
     k.idx = list[jj] < int(c->old_cinv.size()) ? c->old_cinv[list[jj]] : -1;
   }
   const int nthm = layout_threads(L.nc);
@@ -1469,11 +1476,13 @@ nsn_status restore_from_keep(nsn_ctx *c, const std::vector<nsn_contact> &old_con
       const nsn_contact &r = S.contacts[cc];
       const int sl = r.body_a + 1;
       if (sl < 0 || sl > nb) continue;
-      uint32_t p[3];
+      uint32_t p[3], n[3];
       std::memcpy(p, r.pa, sizeof p);
+      std::memcpy(n, r.n, sizeof n);
       for (int jj = sl == 0 ? 0 : end[sl - 1]; jj < end[sl]; jj++) {
         const ContactKeyRec &k = ok[jj];
-        if (k.b == r.body_b && k.p[0] == p[0] && k.p[1] == p[1] && k.p[2] == p[2] && k.a == r.body_a) {
+        if (k.b == r.body_b && k.p[0] == p[0] && k.p[1] == p[1] && k.p[2] == p[2] && k.a == r.body_a &&
+            (k.b >= 0 || (k.n[0] == n[0] && k.n[1] == n[1] && k.n[2] == n[2]))) {
           if (k.idx >= 0)
             for (int q = 0; q < 3; q++) map[3 * cc + q] = 3 * k.idx + q;
           break;
@@ -1701,6 +1710,7 @@ nsn_status run_steps(nsn_ctx *c, int nsteps) {
     c->launches_per_step = c->seg.prefix + fl.newton_n * (c->seg.head + c->seg.tail) + fl.cr_exec * c->seg.cr +
                            c->seg.suffix;
   if (!std::isfinite(c->last.merit_final)) return fail(c, NSN_ERR_NONFINITE, "merit is not finite");
+  if (c->warm_mode == NSN_WARM_LEARNED) return mlp_check(c, st);
   return NSN_OK;
 }
 
@@ -2009,7 +2019,7 @@ nsn_status dalloc(nsn_ctx *c, X **p, size_t n) {
 
 void mlp_free(MlpState &m) {
   void *ptrs[] = {m.pf, m.gr, m.m, m.v, m.pb, m.xb, m.a1b, m.a2b, m.a3b, m.dyb, m.dzb, m.a1f, m.a2f, m.a3f,
-                  m.y, m.dyf, m.da, m.dzf, m.lpart, m.X, m.Y};
+                  m.y, m.dyf, m.da, m.dzf, m.lpart, m.X, m.Y, m.err};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   m = MlpState();
@@ -2063,22 +2073,36 @@ nsn_status mlp_ensure(nsn_ctx *c, int rows_needed) {
   return NSN_OK;
 }
 
-// inference: one fused kernel (weights resident in shared memory), one CTA per SM
+// inference: one tcgen05 kernel (weights resident in shared memory, the
+// accumulator in TMEM), persistent over tiles of 128 rows, two CTAs per SM
 nsn_status mlp_infer(nsn_ctx *c, const float *X, int n, float *Y, cudaStream_t st) {
   MlpState &m = c->mlp;
   if (n <= 0) return NSN_OK;
-  const size_t smem = sizeof(mlp::FusedSmem);
+  const size_t smem = sizeof(mlp::TcSmem);
   static bool attr_set = false;
   if (!attr_set) {
-    CUDA_TRY(c, cudaFuncSetAttribute(mlp::k_forward_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+    CUDA_TRY(c, cudaFuncSetAttribute(mlp::k_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
     attr_set = true;
   }
   int dev = 0, nsm = 152;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  const int tiles = cdiv(n, mlp::FW * 16);
-  mlp::k_forward_fused<<<std::min(tiles, nsm), mlp::FW * 32, smem, st>>>(X, n, m.pb, m.pf, Y);
+  const int tiles = cdiv(n, mlp::TC_M);
+  const int xvec = (reinterpret_cast<uintptr_t>(X) & 15) == 0;
+  mlp::k_forward_tc<<<std::min(tiles, 2 * nsm), mlp::TC_THREADS, smem, st>>>(X, n, xvec, m.pb, m.pf, Y, m.err);
   return NSN_OK;
+}
+
+// the inference kernel's time-out flag (read and cleared; synchronises st)
+nsn_status mlp_check(nsn_ctx *c, cudaStream_t st) {
+  MlpState &m = c->mlp;
+  if (!m.err) return NSN_OK;
+  int e = 0;
+  CUDA_TRY(c, cudaMemcpyAsync(&e, m.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(c, cudaStreamSynchronize(st));
+  if (!e) return NSN_OK;
+  CUDA_TRY(c, cudaMemsetAsync(m.err, 0, sizeof(int), st));
+  return fail(c, NSN_ERR_TIMEOUT, "network inference: a tensor-core completion wait timed out");
 }
 
 nsn_status mlp_train(nsn_ctx *c, const float *X, const float *Tg, const float *w, int n, float lr, float *loss) {
@@ -2762,8 +2786,9 @@ nsn_status nsn_mlp_set_params(nsn_ctx *c, const float *params, int32_t n) {
   nsn_status s;
   if (!m.pf) {
     if ((s = dalloc(c, &m.pf, mlp::NPARAM)) || (s = dalloc(c, &m.gr, mlp::NPARAM)) || (s = dalloc(c, &m.m, mlp::NPARAM)) ||
-        (s = dalloc(c, &m.v, mlp::NPARAM)) || (s = dalloc(c, &m.pb, mlp::NPARAM)))
+        (s = dalloc(c, &m.v, mlp::NPARAM)) || (s = dalloc(c, &m.pb, mlp::NPARAM)) || (s = dalloc(c, &m.err, 1)))
       return s;
+    CUDA_TRY(c, cudaMemsetAsync(m.err, 0, sizeof(int), c->stream));
   }
   CUDA_TRY(c, cudaMemcpyAsync(m.pf, params, sizeof(float) * n, cudaMemcpyHostToDevice, c->stream));
   CUDA_TRY(c, cudaMemsetAsync(m.m, 0, sizeof(float) * n, c->stream));
@@ -2791,7 +2816,24 @@ nsn_status nsn_mlp_forward(nsn_ctx *c, const float *X, int32_t n, float *Y) {
   if (s != NSN_OK) return s;
   mlp_infer(c, X, n, Y, c->stream);
   CUDA_TRY(c, cudaGetLastError());
-  return NSN_OK;
+  return mlp_check(c, c->stream);
+}
+
+nsn_status nsn_mlp_time_forward(nsn_ctx *c, const float *X, int32_t n, float *Y, int32_t reps, float *ms) {
+  if (!c || !X || !Y || !ms || n < 0 || reps < 1 || !c->mlp.ready) return NSN_ERR_INVALID_ARG;
+  nsn_status s = mlp_workspace(c, kMlpChunk);
+  if (s != NSN_OK) return s;
+  if (!c->ev0) CUDA_TRY(c, cudaEventCreate(&c->ev0));
+  if (!c->ev1) CUDA_TRY(c, cudaEventCreate(&c->ev1));
+  CUDA_TRY(c, cudaEventRecord(c->ev0, c->stream));
+  for (int k = 0; k < reps; k++) mlp_infer(c, X, n, Y, c->stream);
+  CUDA_TRY(c, cudaGetLastError());
+  CUDA_TRY(c, cudaEventRecord(c->ev1, c->stream));
+  CUDA_TRY(c, cudaEventSynchronize(c->ev1));
+  float t = 0.f;
+  CUDA_TRY(c, cudaEventElapsedTime(&t, c->ev0, c->ev1));
+  *ms = t / float(reps);
+  return mlp_check(c, c->stream);
 }
 
 nsn_status nsn_mlp_train_step(nsn_ctx *c, const float *X, const float *T, const float *w, int32_t n, float lr, float *loss) {

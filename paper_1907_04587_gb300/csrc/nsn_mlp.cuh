@@ -3,9 +3,11 @@
 // The network maps 16 dimensionless contact features to 4 outputs (normal and
 // two friction multipliers in units of the contact's gravity-scaled effective
 // mass, and a log preconditioner scale): 16 -> 128 -> 128 -> 128 -> 4, ReLU.
-// Inference and training use one tiled GEMM kernel on mma.sync m16n8k16
-// (BF16 operands, FP32 accumulation) plus elementwise kernels; FP32 master
-// weights are updated with Adam and rounded to BF16 for the GEMMs.
+// Training uses one tiled GEMM kernel on mma.sync m16n8k16 (BF16 operands,
+// FP32 accumulation; its GEMMs have K = the batch, transposed operands and
+// narrow N) plus elementwise kernels; FP32 master weights are updated with
+// Adam and rounded to BF16 for the GEMMs.  Inference, the part that runs in
+// the time step, is one tcgen05 kernel (nsn_mlp_tc.cuh).
 #pragma once
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -110,140 +112,6 @@ __global__ void __launch_bounds__(128) k_gemm(const __nv_bfloat16 *__restrict__ 
         if (Cf) Cf[size_t(m) * ldc + n] = v;
         if (Cb) Cb[size_t(m) * ldc + n] = __float2bfloat16(v);
       }
-}
-
-// ------------------------------------------------------------------------------------
-// Fused inference: the whole network per row tile in one kernel.  The BF16
-// weights (70 KB) stay in shared memory for the CTA's lifetime; each warp
-// takes 16 rows, runs the four layers with mma.sync m16n8k16 (BF16 operands,
-// FP32 accumulation) and keeps its activations in one shared-memory tile
-// (BF16, as the layered path stores them), overwritten layer by layer once
-// the layer's fragments are in registers; only Y is written.  X is read once.
-// Fragments are loaded with ldmatrix (one instruction for the A fragment of a
-// k-step, one for the B fragments of two n8 tiles).  Shared rows are padded by
-// 8 BF16 (16 bytes), so that the eight 16-byte rows of each 8x8 matrix fall in
-// distinct bank groups.
-constexpr int FW = 16;           // warps per CTA, 16 rows each
-constexpr int FP1 = NIN + 8;     // padded row lengths (BF16)
-constexpr int FPH = NH + 8;
-constexpr int N4P = 8;           // layer 4 padded to one n8 tile
-struct FusedSmem {
-  __nv_bfloat16 W1[NH][FP1], W2[NH][FPH], W3[NH][FPH], W4[N4P][FPH];
-  float b1[NH], b2[NH], b3[NH], b4[N4P];
-  __nv_bfloat16 x[FW][16][FP1];
-  __nv_bfloat16 act[FW][16][FPH];
-};
-
-// four 8x8 BF16 matrices from shared memory (lane l gives the address of row
-// l % 8 of matrix l / 8); register i holds matrix i in the mma fragment layout
-__device__ __forceinline__ void ldsm_x4(const __nv_bfloat16 *p, uint32_t &r0, uint32_t &r1, uint32_t &r2,
-                                        uint32_t &r3) {
-  const unsigned a = static_cast<unsigned>(__cvta_generic_to_shared(p));
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];\n"
-               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-               : "r"(a));
-}
-
-// one dense layer for a warp's 16 rows: out = ReLU(A W^T + b) as BF16 (NT n8 tiles,
-// K = 16 * KS), A and W row-major in shared memory with padded row lengths; out
-// may be A (the stores follow the last fragment load of the warp)
-template <int KS, int NT, int LDA, int LDW>
-__device__ __forceinline__ void fused_layer(const __nv_bfloat16 *A, const __nv_bfloat16 *W, const float *b,
-                                            __nv_bfloat16 *out, int lane) {
-  const int g = lane >> 2, tq = lane & 3, m = lane >> 3, r8 = lane & 7;
-  float acc[NT][4];
-#pragma unroll
-  for (int j = 0; j < NT; j++)
-#pragma unroll
-    for (int r = 0; r < 4; r++) acc[j][r] = 0.f;
-#pragma unroll
-  for (int ks = 0; ks < KS; ks++) {
-    const int k0 = 16 * ks;
-    uint32_t a[4];
-    // A: matrices (rows 0-7, k0), (rows 8-15, k0), (rows 0-7, k0+8), (rows 8-15, k0+8)
-    ldsm_x4(A + (r8 + 8 * (m & 1)) * LDA + k0 + 8 * (m >> 1), a[0], a[1], a[2], a[3]);
-#pragma unroll
-    for (int j = 0; j < NT; j += 2) {
-      // B of tiles j, j+1: matrices (tile j, k0), (tile j, k0+8), (tile j+1, k0), (tile j+1, k0+8)
-      uint32_t bq[4];
-      ldsm_x4(W + (8 * (j + (m >> 1)) + r8) * LDW + k0 + 8 * (m & 1), bq[0], bq[1], bq[2], bq[3]);
-      uint32_t b0[2] = {bq[0], bq[1]}, b1[2] = {bq[2], bq[3]};
-      mma_bf16_16816(acc[j], a, b0);
-      mma_bf16_16816(acc[j + 1], a, b1);
-    }
-  }
-  __syncwarp();
-#pragma unroll
-  for (int j = 0; j < NT; j++) {
-    const int c = 8 * j + 2 * tq;
-    const float v0 = fmaxf(acc[j][0] + b[c], 0.f), v1 = fmaxf(acc[j][1] + b[c + 1], 0.f);
-    const float v2 = fmaxf(acc[j][2] + b[c], 0.f), v3 = fmaxf(acc[j][3] + b[c + 1], 0.f);
-    *reinterpret_cast<uint32_t *>(out + g * FPH + c) = pack_bf16(__float2bfloat16(v0), __float2bfloat16(v1));
-    *reinterpret_cast<uint32_t *>(out + (g + 8) * FPH + c) = pack_bf16(__float2bfloat16(v2), __float2bfloat16(v3));
-  }
-}
-
-// Y[n][NOUT] = network(X[n][NIN]); Wb: BF16 parameter block, pf: FP32 master
-// (biases).  Persistent: each CTA loads the weights once and loops over tiles
-// of FW * 16 rows.
-__global__ void __launch_bounds__(FW * 32) k_forward_fused(const float *__restrict__ X, int n,
-                                                           const __nv_bfloat16 *__restrict__ Wb,
-                                                           const float *__restrict__ pf, float *__restrict__ Y) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  FusedSmem &S = *reinterpret_cast<FusedSmem *>(smem_raw);
-  const __nv_bfloat16 zero = __float2bfloat16(0.f);
-  for (int i = threadIdx.x; i < NH * NIN; i += blockDim.x) S.W1[i / NIN][i % NIN] = Wb[OFF_W1 + i];
-  for (int i = threadIdx.x; i < NH * NH; i += blockDim.x) {
-    S.W2[i / NH][i % NH] = Wb[OFF_W2 + i];
-    S.W3[i / NH][i % NH] = Wb[OFF_W3 + i];
-  }
-  for (int i = threadIdx.x; i < N4P * NH; i += blockDim.x) S.W4[i / NH][i % NH] = i < NOUT * NH ? Wb[OFF_W4 + i] : zero;
-  for (int i = threadIdx.x; i < NH; i += blockDim.x) {
-    S.b1[i] = pf[OFF_B1 + i]; S.b2[i] = pf[OFF_B2 + i]; S.b3[i] = pf[OFF_B3 + i];
-  }
-  if (threadIdx.x < N4P) S.b4[threadIdx.x] = threadIdx.x < NOUT ? pf[OFF_B4 + threadIdx.x] : 0.f;
-  __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, tq = lane & 3;
-  __nv_bfloat16 *act = &S.act[warp][0][0];
-  for (int r0 = (blockIdx.x * FW + warp) * 16; r0 < n; r0 += gridDim.x * FW * 16) {
-    // 16 rows x 16 features: 8 per lane, coalesced
-#pragma unroll
-    for (int q = 0; q < 8; q++) {
-      const int e = q * 32 + lane, r = e / NIN, k = e % NIN;
-      const float v = r0 + r < n ? X[size_t(r0 + r) * NIN + k] : 0.f;
-      S.x[warp][r][k] = __float2bfloat16(v);
-    }
-    __syncwarp();
-    fused_layer<1, NH / 8, FP1, FP1>(&S.x[warp][0][0], &S.W1[0][0], S.b1, act, lane);
-    __syncwarp();
-    fused_layer<NH / 16, NH / 8, FPH, FPH>(act, &S.W2[0][0], S.b2, act, lane);
-    __syncwarp();
-    fused_layer<NH / 16, NH / 8, FPH, FPH>(act, &S.W3[0][0], S.b3, act, lane);
-    __syncwarp();
-    // layer 4 (no ReLU): one n8 tile, columns 0..NOUT-1 kept
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-    for (int ks = 0; ks < NH / 16; ks++) {
-      const int k0 = 16 * ks;
-      uint32_t a[4];
-      ldsm_x4(act + ((lane & 7) + 8 * ((lane >> 3) & 1)) * FPH + k0 + 8 * (lane >> 4), a[0], a[1], a[2], a[3]);
-      uint32_t bb[2] = {pack_bf16(S.W4[g][k0 + 2 * tq], S.W4[g][k0 + 2 * tq + 1]),
-                        pack_bf16(S.W4[g][k0 + 2 * tq + 8], S.W4[g][k0 + 2 * tq + 9])};
-      mma_bf16_16816(acc, a, bb);
-    }
-    const int c = 2 * tq;
-    if (c < NOUT) {
-      if (r0 + g < n) {
-        Y[size_t(r0 + g) * NOUT + c] = acc[0] + S.b4[c];
-        Y[size_t(r0 + g) * NOUT + c + 1] = acc[1] + S.b4[c + 1];
-      }
-      if (r0 + g + 8 < n) {
-        Y[size_t(r0 + g + 8) * NOUT + c] = acc[2] + S.b4[c];
-        Y[size_t(r0 + g + 8) * NOUT + c + 1] = acc[3] + S.b4[c + 1];
-      }
-    }
-    __syncwarp();
-  }
 }
 
 // FP32 -> BF16 copy

@@ -107,6 +107,7 @@ def lib():
         "nsn_mlp_set_params": (C.c_int, [_vp, _fp, C.c_int32]),
         "nsn_mlp_get_params": (C.c_int, [_vp, _fp, _fp, C.c_int32]),
         "nsn_mlp_forward": (C.c_int, [_vp, _vp, C.c_int32, _vp]),
+        "nsn_mlp_time_forward": (C.c_int, [_vp, _vp, C.c_int32, _vp, C.c_int32, C.POINTER(C.c_float)]),
         "nsn_mlp_train_step": (C.c_int, [_vp, _vp, _vp, _vp, C.c_int32, C.c_float, C.POINTER(C.c_float)]),
         "nsn_contact_features": (C.c_int, [_vp, _vp, _vp]),
         "nsn_islands": (C.c_int, [_vp, _ip, _ip]),
@@ -345,6 +346,13 @@ def nsn_mlp_get_params(ctx):
 
 def nsn_mlp_forward(ctx, X_dev, n, Y_dev):
     _check(ctx, lib().nsn_mlp_forward(ctx, _vp(X_dev), n, _vp(Y_dev)), "nsn_mlp_forward")
+
+
+def nsn_mlp_time_forward(ctx, X_dev, n, Y_dev, reps):
+    ms = C.c_float()
+    _check(ctx, lib().nsn_mlp_time_forward(ctx, _vp(X_dev), n, _vp(Y_dev), int(reps), C.byref(ms)),
+           "nsn_mlp_time_forward")
+    return ms.value
 
 
 def nsn_mlp_train_step(ctx, X_dev, T_dev, w_dev, n, lr):

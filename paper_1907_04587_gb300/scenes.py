@@ -264,6 +264,8 @@ def chain_block(seed=0, hexes=24, edge=0.5, E=1e5, nu=0.45, density=1000.0, link
     initial state is mildly pre-strained and singular values are distinct.
     Chain: ``links`` boxes along +x, pinned to a world anchor, lying on the top
     face; contacts: bottom block vertices vs ground, top vertices under a link.
+    ``planes`` (the ground) and ``mu_env`` let a collider regenerate the same
+    kinds of contact (block vertices against the ground and the links).
     """
     rng = np.random.default_rng(seed)
     n = hexes
@@ -323,7 +325,8 @@ def chain_block(seed=0, hexes=24, edge=0.5, E=1e5, nu=0.45, density=1000.0, link
     s = dict(kind=kind, pos=pos, quat=quat, vel=np.zeros((len(kind), 3)), omega=np.zeros((len(kind), 3)),
              mass=mass, inertia=inertia, env=np.zeros(len(kind), np.int32),
              half=np.concatenate([np.tile(L / 2, (links, 1)), np.zeros((nv, 3))]), t_v=(tets + links).astype(np.int32),
-             t_rest=t_rest, t_E=np.full(len(tets), E), t_nu=np.full(len(tets), nu))
+             t_rest=t_rest, t_E=np.full(len(tets), E), t_nu=np.full(len(tets), nu),
+             planes=np.array([[0.0, 0.0, 1.0, 0.0]]), mu_env=np.array([mu]))
     s.update(joints); s.update(contacts)
     return finalize(s)
 
@@ -489,29 +492,39 @@ def sphere_mesh(radius, res, rng, rest_jitter=0.01):
 
 
 def mixed_bin(seed=0, n_boxes=2000, n_spheres=8, sphere_radius=0.3, sphere_res=12, box_edge=(0.05, 0.3),
-              E=5e4, nu=0.4, density=1000.0, mu=0.5, margin=0.01, cell=0.35):
+              E=5e4, nu=0.4, density=1000.0, mu=0.5, margin=0.01, cell=0.42):
     """Config: one environment, a bin (floor z = 0, walls x = 0 and y = 0 used)
     holding ``n_boxes`` rigid boxes (edge uniform in ``box_edge``) stacked in
-    columns of up to four on a grid of ``cell`` m cells, random yaw, and
-    ``n_spheres`` stable Neo-Hookean balls (``sphere_res``^3-hex voxel meshes,
-    ~4,500 tets each at res 12) resting on the floor against the x = 0 wall.
-    Contacts: 4 bottom corners per box vs the floor or the box below; ball
-    vertices within ``margin`` of the floor or the wall vs that plane."""
+    columns of up to four on a grid of ``cell`` m cells, and ``n_spheres``
+    stable Neo-Hookean balls (``sphere_res``^3-hex voxel meshes, ~4,500 tets
+    each at res 12) resting on the floor against the x = 0 wall.  A column has
+    one random yaw (within +-0.3 rad) and centre (within +-0.01 m of its cell's
+    centre), and its edges decrease upwards, so each box rests wholly on the
+    one beneath; the cell (0.42 m) exceeds the widest yawed box plus the
+    jitter and the margin, so neighbouring columns do not touch.  Contacts: 4
+    bottom corners per box vs the floor or the box below; ball vertices within
+    ``margin`` of the floor or the wall vs that plane.  ``planes`` (floor and
+    the two walls) and ``mu_env`` let a collider regenerate the contacts."""
     rng = np.random.default_rng(seed)
     n_cols = int(np.ceil(n_boxes / 4))
     side = int(np.ceil(np.sqrt(n_cols)))
     x_off = 2 * sphere_radius + 0.1                   # the balls' strip along the x = 0 wall
     B = SceneBuilder()
     edges = rng.uniform(box_edge[0], box_edge[1], n_boxes)
+    for col in range(n_cols):                          # box k sits in column k % n_cols, level k // n_cols
+        members = np.arange(col, n_boxes, n_cols)
+        edges[members] = np.sort(edges[members])[::-1]
+    col_xy = rng.uniform(-0.01, 0.01, (n_cols, 2))
+    col_yaw = rng.uniform(-0.3, 0.3, n_cols)
     col_top = {}
     for k in range(n_boxes):
         col = k % n_cols
-        cx = x_off + (col % side + 0.5) * cell + rng.uniform(-0.01, 0.01)
-        cy = (col // side + 0.5) * cell + rng.uniform(-0.01, 0.01)
+        cx = x_off + (col % side + 0.5) * cell + col_xy[col, 0]
+        cy = (col // side + 0.5) * cell + col_xy[col, 1]
         e = edges[k]
         below = col_top.get(col)
         z0 = 0.0 if below is None else below[1]
-        yaw = rng.uniform(-0.3, 0.3)
+        yaw = col_yaw[col]
         m = density * e ** 3
         q = quat_yaw(yaw)
         bid = B.add_rigid((cx, cy, z0 + e / 2), tuple(q), mass=m, inertia=(m * e * e / 6,) * 3)
@@ -549,6 +562,8 @@ def mixed_bin(seed=0, n_boxes=2000, n_spheres=8, sphere_radius=0.3, sphere_res=1
     half = np.zeros((len(s["mass"]), 3), F32)        # the boxes are bodies 0 .. n_boxes-1
     half[:n_boxes] = (edges[:, None] / 2).astype(F32)
     s["half"] = half
+    s["planes"] = np.array([[0, 0, 1, 0], [1, 0, 0, 0], [0, 1, 0, 0]], F32)
+    s["mu_env"] = np.array([mu], F32)
     return s
 
 

@@ -57,7 +57,7 @@ def test_forward_and_gradients_match_fp64_reference(torch_cuda):
 def test_forward_and_gradients_match_bf16_rounding_reference(torch_cuda):
     """Against the FP64 reference rounded to BF16 where the kernels round
     (inputs, weights, hidden activations, dY and dz for the GEMM operands):
-    forward (the fused inference kernel) and every gradient within 1e-3."""
+    forward (the tensor-core inference kernel) and every gradient within 1e-3."""
     torch = torch_cuda
     rng = np.random.default_rng(5)
     p = learn.init_params(7)
@@ -85,6 +85,49 @@ def test_forward_and_gradients_match_bf16_rounding_reference(torch_cuda):
         e = rel(G[name], Gr[name])
         print(f"{name} {e:.2e}")
         assert e < 1e-3, name
+
+
+@pytest.mark.parametrize("n", [1, 127, 128, 129, 50000])
+@pytest.mark.parametrize("offset", [0, 1])
+def test_tensor_core_inference_against_bf16_reference(torch_cuda, n, offset):
+    """The inference kernel (tcgen05 MMAs, FP32 accumulators in tensor memory,
+    128 rows per tile, persistent over tiles: 50,000 rows are 391 tiles on at
+    most two CTAs per SM) against the FP64 network rounded to BF16 where the
+    kernel rounds: one row, a tile less one, one tile, one more, many tiles;
+    X at a 16-byte boundary and one float past it (scalar loads).  Norm-wise
+    within 1e-3.  Element-wise, against each output's RMS: all but four rows'
+    outputs and 0.1% of the rest within 2e-3, and all within 5e-2 -- an FP32
+    sum order that differs from the reference's moves an activation that lies
+    near a BF16 rounding boundary to the neighbouring BF16 value (2^-8 of it),
+    and a few such flips in one row move that row's outputs by up to about 1%
+    of the RMS."""
+    torch = torch_cuda
+    rng = np.random.default_rng(11 + n)
+    p = learn.init_params(5)
+    X = rng.normal(size=(n, 16)).astype(np.float32)
+    tr = learn.Trainer(params=p.astype(np.float32))
+    buf = torch.zeros(n * 16 + 4, dtype=torch.float32, device="cuda")
+    buf[offset:offset + n * 16] = torch.from_numpy(X.ravel()).cuda()
+    Xd = buf[offset:offset + n * 16]
+    Yd = torch.full((n, 4), float("nan"), dtype=torch.float32, device="cuda")
+    nsn.nsn_mlp_forward(tr.host.ctx, Xd.data_ptr(), n, Yd.data_ptr())
+    torch.cuda.synchronize()
+    y = Yd.cpu().numpy().astype(np.float64)
+    y_ref, _ = mlp_ref.forward_bf16(p, X.astype(np.float64))
+    assert np.isfinite(y).all()
+    e = rel(y, y_ref) if n > 1 else np.abs(y - y_ref).max() / max(np.abs(y_ref).max(), 1e-30)
+    scale = np.sqrt(np.mean(y_ref ** 2, axis=0)) + 1e-30
+    d = np.abs(y - y_ref) / scale
+    rows_off = int((d.max(axis=1) > 2e-3).sum())
+    print(f"n {n} offset {offset}: norm-wise {e:.2e}, rows beyond 2e-3 of the RMS {rows_off}, "
+          f"max {d.max():.2e}")
+    assert e < 1e-3
+    assert rows_off <= 4 + 0.001 * n
+    assert d.max() < 5e-2
+    # the timed entry point repeats the same call: bit-identical outputs
+    ms = nsn.nsn_mlp_time_forward(tr.host.ctx, Xd.data_ptr(), n, Yd.data_ptr(), 3)
+    assert ms > 0.0
+    np.testing.assert_array_equal(Yd.cpu().numpy(), y.astype(np.float32))
 
 
 def test_training_reduces_loss(torch_cuda):
