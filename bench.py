@@ -435,6 +435,8 @@ def oracle_rate(workload, seed, budget_s, newton, cr, cores=None):
     if not workload.startswith("batched"):
         cores = 1       # one scene: a sample of one
     jobs = [(workload, seed * 1000 + k if k else seed, budget_s, newton, cr, LS, REGEN) for k in range(cores)]
+    probe = WORKLOADS[workload]["make"](seed) if not workload.startswith("batched") else None
+    regen_used = bool(REGEN) and (probe is None or ("half" in probe and "mu_env" in probe))
     if cores == 1:
         res = [_oracle_chunk(jobs[0])]
     else:
@@ -451,7 +453,7 @@ def oracle_rate(workload, seed, budget_s, newton, cr, cores=None):
     return conv / el, dict(kind="oracle", cores=cores,
                            sample=f"{sample}; same tolerance, caps, Newton step ({'line search' if LS else 'damped'}) "
                                   f"and accounting, zero start, contacts "
-                                  f"{'regenerated by the oracle collider every step' if REGEN else 'fixed'}; "
+                                  f"{'regenerated by the oracle collider every step' if regen_used else 'fixed'}; "
                                   f"{steps} advancing steps in {el:.1f} s, {conv} of "
                                   f"{sum(r[1] * r[3] for r in res)} env-steps converged")
 
@@ -577,7 +579,7 @@ def measure_arm(nsn, torch, g, s, st0, stream, steps, warmup, clk=None, reset=Fa
         if collider is not None:
             ni_k, bi_k = g.islands()
             maps.append((ni_k, island_env_map(s, bi_k, ni_k)))
-            contacts.append((g.R - 5 * len(s["j_body"])) // 3)
+            contacts.append((g.R - 5 * len(s["j_body"]) - 3 * len(s["t_v"]) - 3 * len(s.get("l_v", ()))) // 3)
             phases.append(g.phase_times())
         newton.append(st["newton_done"])
         launches += g.launches_per_step()
