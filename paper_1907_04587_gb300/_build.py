@@ -9,7 +9,7 @@ CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libnsn.so")
 SOURCES = [os.path.join(CSRC, "nsn_host.cu"), os.path.join(CSRC, "nsn_collide.cu")]
 DEPS = SOURCES + [os.path.join(CSRC, "nsn_kernels.cuh"), os.path.join(CSRC, "nsn_mlp.cuh"), os.path.join(CSRC, "nsn_mlp_tc.cuh"),
-                  os.path.join(CSRC, "nsn_internal.h"), os.path.join(CSRC, "nsn_bits.h"),
+                  os.path.join(CSRC, "nsn_internal.h"), os.path.join(CSRC, "nsn_bits.h"), os.path.join(CSRC, "nsn_hostpar.h"),
                   os.path.join(os.path.dirname(HERE), "include", "nsn.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -7,6 +7,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <condition_variable>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -21,6 +22,7 @@
 #include "nsn_mlp.cuh"
 #include "nsn_mlp_tc.cuh"
 #include "nsn_internal.h"
+#include "nsn_hostpar.h"
 
 using namespace nsn;
 
@@ -228,6 +230,7 @@ struct nsn_ctx {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   PinnedStage stage;         // pinned staging of the (re)build's uploads
   std::vector<int> key_end, key_list;      // old contacts bucketed by body a (key matching)
+  std::vector<int> key_k, key_cnt;         // scratch of that bucketing
   // host wall time (ms) of the phases of the last rebuild / step, NSN_PHASE_*
   double phase_ms[NSN_PHASES] = {};
   std::string err;
@@ -308,46 +311,11 @@ void find_islands(const HostScene &S, Layout &L, int nb) {
   }
 }
 
-// stable order of n items by an integer key in [0, K) (counting sort: the
-// layout is rebuilt whenever contacts are regenerated, so it stays linear)
-template <typename F>
-void parallel_for_threads(int n, const F &fn);
-int layout_threads(long long n);
 
-template <typename Key>
-void order_by(int n, int K, const Key &key, std::vector<int> &o, std::vector<int> &k, std::vector<int> &start) {
-  k.resize(n);
-  start.assign(size_t(K) + 1, 0);
-  o.resize(n);
-  // the keys (random reads of the constraint records and island tables) on
-  // host threads; the histogram and the stable scatter in one pass each
-  const int nth = layout_threads(n);
-  parallel_for_threads(nth, [&](int t) {
-    const int i0 = int((long long)n * t / nth), i1 = int((long long)n * (t + 1) / nth);
-    for (int i = i0; i < i1; i++) k[i] = key(i);
-  });
-  for (int i = 0; i < n; i++) start[size_t(k[i]) + 1]++;
-  for (int j = 0; j < K; j++) start[size_t(j) + 1] += start[j];
-  for (int i = 0; i < n; i++) o[start[k[i]]++] = i;
-}
 
-// Runs fn(k) for k = 0 .. n-1 on n host threads (the calling thread takes k = 0).
-template <typename F>
-void parallel_for_threads(int n, const F &fn) {
-  if (n <= 1) { fn(0); return; }
-  std::vector<std::thread> th;
-  th.reserve(n - 1);
-  for (int k = 1; k < n; k++) th.emplace_back([&fn, k] { fn(k); });
-  fn(0);
-  for (std::thread &x : th) x.join();
-}
 
-// host threads for a layout pass over n items: one per ~64k items, at most
-// the hardware threads and 16
-int layout_threads(long long n) {
-  const int hw = std::max(1, int(std::thread::hardware_concurrency()));
-  return int(std::max(1LL, std::min<long long>({(n + 65535) / 65536, (long long)hw, 16LL})));
-}
+
+
 
 // ------------------------------------------------------------------------------------
 // layout: entries sorted by body (counting sort), rows -> entry ids
@@ -474,18 +442,36 @@ nsn_status build_layout(nsn_ctx *c) {
   rcnt.assign(size_t(L.nr) + 1, 0);
   pcnt.assign(size_t(L.np) + 1, 0);
   {
-    int run = 0;
-    for (int b = 0; b < nbod; b++) {
-      if (b == L.nr) run = 0;                 // particle entries are numbered after the rigid ones
-      for (int k = 0; k < nth; k++) {
-        int &x = cnt[size_t(b) * nth + k];
-        const int n = x;
-        x = run;
-        run += n;
-      }
-      if (b < L.nr) rcnt[size_t(b) + 1] = run;
-      else pcnt[size_t(b - L.nr) + 1] = run;
-    }
+    // exclusive prefix sums of the counts in (body, thread) order, rigid
+    // bodies and particles each from zero (particle entries are numbered
+    // after the rigid ones): per chunk of bodies a sum, the chunk starts in
+    // order, then each chunk's offsets -- the result of one sequential pass
+    auto scan = [&](int b0, int b1, int *seg) {
+      const int nb = b1 - b0, nch = layout_threads((long long)nb * nth);
+      std::vector<int> part(size_t(nch) + 1, 0);
+      parallel_for_threads(nch, [&](int h) {
+        const int c0 = b0 + int((long long)nb * h / nch), c1 = b0 + int((long long)nb * (h + 1) / nch);
+        int s = 0;
+        for (size_t i = size_t(c0) * nth; i < size_t(c1) * nth; i++) s += cnt[i];
+        part[size_t(h) + 1] = s;
+      });
+      for (int h = 0; h < nch; h++) part[size_t(h) + 1] += part[h];
+      parallel_for_threads(nch, [&](int h) {
+        const int c0 = b0 + int((long long)nb * h / nch), c1 = b0 + int((long long)nb * (h + 1) / nch);
+        int run = part[h];
+        for (int b = c0; b < c1; b++) {
+          for (int k = 0; k < nth; k++) {
+            int &x = cnt[size_t(b) * nth + k];
+            const int n = x;
+            x = run;
+            run += n;
+          }
+          seg[b - b0 + 1] = run;
+        }
+      });
+    };
+    scan(0, L.nr, rcnt.data());
+    scan(L.nr, nbod, pcnt.data());
   }
   L.ER = rcnt[L.nr];
   L.EV = pcnt[L.np];
@@ -517,12 +503,29 @@ nsn_status build_layout(nsn_ctx *c) {
   L.isl_rigid.assign(std::max(L.ni, 1), 0);
   {
     std::vector<int> npar(L.ni, 0), ntet(L.ni, 0);
-    auto first = [&](int i, int slot, int v) { if (L.ires[8 * i + slot + 1] == 0) L.ires[8 * i + slot] = v; L.ires[8 * i + slot + 1]++; };
-    for (int ci = 0; ci < L.nc; ci++) first(L.risl[3 * ci], 0, ci);
-    for (int j = 0; j < L.nj; j++) first(L.risl[3 * L.nc + 5 * j], 2, j);
-    for (int b = 0; b < L.nr; b++) first(L.bisl_r[b], 4, b);
-    for (int b = 0; b < L.np; b++) npar[L.bisl_p[b]]++;
-    for (int t = 0; t < L.nt; t++) ntet[L.risl[L.Rpair + 3 * t]]++;
+    // an island's items are one run of equal island ids in each list: the
+    // thread whose range holds the run's first item records it
+    auto runs = [&](int n, auto &&isl_of, auto &&put) {
+      const int nth_r = layout_threads(n);
+      parallel_for_threads(nth_r, [&](int h) {
+        const int i0 = int((long long)n * h / nth_r), i1 = int((long long)n * (h + 1) / nth_r);
+        for (int i = i0; i < i1; i++) {
+          const int is = isl_of(i);
+          if (i > 0 && isl_of(i - 1) == is) continue;
+          int j = i + 1;
+          while (j < n && isl_of(j) == is) j++;
+          put(is, i, j - i);
+        }
+      });
+    };
+    auto first = [&](int slot) {
+      return [&L, slot](int is, int f, int cnt_) { L.ires[8 * size_t(is) + slot] = f; L.ires[8 * size_t(is) + slot + 1] = cnt_; };
+    };
+    runs(L.nc, [&](int ci) { return L.risl[3 * size_t(ci)]; }, first(0));
+    runs(L.nj, [&](int j) { return L.risl[3 * size_t(L.nc) + 5 * size_t(j)]; }, first(2));
+    runs(L.nr, [&](int b) { return L.bisl_r[b]; }, first(4));
+    runs(L.np, [&](int b) { return L.bisl_p[b]; }, [&](int is, int, int cnt_) { npar[is] = cnt_; });
+    runs(L.nt, [&](int tt) { return L.risl[size_t(L.Rpair) + 3 * size_t(tt)]; }, [&](int is, int, int cnt_) { ntet[is] = cnt_; });
     // (at most 2048 rows: the reduction task table of a group holds 2 per island + rows / 128)
     const int cap = std::min(c->cfg.res_max_rows > 0 ? c->cfg.res_max_rows : 384, 2048);
     for (int i = 0; i < L.ni; i++) L.isl_rigid[i] = npar[i] == 0 && ntet[i] == 0;
@@ -1453,21 +1456,38 @@ nsn_status restore_from_keep(nsn_ctx *c, const std::vector<nsn_contact> &old_con
   // stored in bucket order so that each lookup scans a short contiguous run
   const int onc = int(old_contacts.size());
   const int nb = int(S.kind.size());
-  std::vector<int> &end = c->key_end, &list = c->key_list;
+  // (a stable counting sort on host threads; end[s] = the old contacts with
+  // key <= s: bucket s is list[end[s - 1] .. end[s]))
+  std::vector<int> &end = c->key_end, &list = c->key_list, &bkey = c->key_k;
+  order_by(onc, nb + 1, [&](int i) { return old_contacts[i].body_a + 1; }, list, bkey, c->key_cnt);
   end.assign(size_t(nb) + 2, 0);
-  list.resize(onc);
-  for (int i = 0; i < onc; i++) end[size_t(old_contacts[i].body_a) + 2]++;
-  for (int b = 0; b <= nb; b++) end[size_t(b) + 1] += end[b];
-  for (int i = 0; i < onc; i++) list[end[size_t(old_contacts[i].body_a) + 1]++] = i;
+  {
+    const int nth = layout_threads(onc);
+    parallel_for_threads(nth, [&](int h) {
+      const int i0 = int((long long)onc * h / nth), i1 = int((long long)onc * (h + 1) / nth);
+      for (int i = i0; i < i1; i++) {
+        const int kk = bkey[list[i]];
+        if (i == onc - 1 || bkey[list[i + 1]] != kk) end[kk] = i + 1;
+      }
+    });
+  }
+  for (int s = 1; s <= nb + 1; s++) end[s] = std::max(end[s], end[size_t(s) - 1]);
   std::vector<ContactKeyRec> &ok = c->okeys;
   ok.resize(onc);
-  for (int jj = 0; jj < onc; jj++) {
-    const nsn_contact &r = old_contacts[list[jj]];
-    ContactKeyRec &k = ok[jj];
-    k.a = r.body_a; k.b = r.body_b;
-    std::memcpy(k.p, r.pa, sizeof k.p);
-    std::memcpy(k.n, r.n, sizeof k.n);
-    k.idx = list[jj] < int(c->old_cinv.size()) ? c->old_cinv[list[jj]] : -1;
+  {
+    const int nth = layout_threads(onc);
+    const int ncinv = int(c->old_cinv.size());
+    parallel_for_threads(nth, [&](int h) {
+      const int j0 = int((long long)onc * h / nth), j1 = int((long long)onc * (h + 1) / nth);
+      for (int jj = j0; jj < j1; jj++) {
+        const nsn_contact &r = old_contacts[list[jj]];
+        ContactKeyRec &k = ok[jj];
+        k.a = r.body_a; k.b = r.body_b;
+        std::memcpy(k.p, r.pa, sizeof k.p);
+        std::memcpy(k.n, r.n, sizeof k.n);
+        k.idx = list[jj] < ncinv ? c->old_cinv[list[jj]] : -1;
+      }
+    });
   }
   const int nthm = layout_threads(L.nc);
   parallel_for_threads(nthm, [&](int k0) {
