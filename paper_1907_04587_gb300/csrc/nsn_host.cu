@@ -614,9 +614,11 @@ void carve(Arena &A, Dev<T> &D, const Layout &L, int nb) {
   D.cba = A.take<int>(L.nc); D.cbb = A.take<int>(L.nc);
   for (int k = 0; k < 3; k++) { D.cpa[k] = tk(L.nc); D.cpb[k] = tk(L.nc); D.cn[k] = tk(L.nc); }
   D.cdd = tk(L.nc); D.cmu = tk(L.nc);
+  D.cr0 = A.take<double>(sizeof(T) == 4 ? 6 * size_t(L.nc) : 1);
   D.jba = A.take<int>(L.nj); D.jbb = A.take<int>(L.nj);
   for (int k = 0; k < 3; k++) { D.jpa[k] = tk(L.nj); D.jpb[k] = tk(L.nj); D.jaxa[k] = tk(L.nj); D.jaxb[k] = tk(L.nj); }
   D.je = tk(L.nj);
+  D.jr0 = A.take<double>(sizeof(T) == 4 ? 15 * size_t(L.nj) : 1);
   D.tv = A.take<int>(4 * L.nt);
   D.tkind = A.take<int>(L.nt);
   D.jkind = A.take<int>(L.nj);
@@ -1069,6 +1071,8 @@ struct Launcher {
     k_begin_rigid<T><<<cdiv(std::max(D.nr, 1), 128), 128, 0, st>>>(D);
     count++;
     if (D.np) { k_begin_particle<T><<<cdiv(D.np, 128), 128, 0, st>>>(D); count++; }
+    if (sizeof(T) == 4 && D.nc) { k_contact_r0<T><<<cdiv(D.nc, 256), 256, 0, st>>>(D); count++; }
+    if (sizeof(T) == 4 && D.nj) { k_joint_r0<T><<<cdiv(D.nj, 128), 128, 0, st>>>(D); count++; }
   }
   void linearize_at(int n) {  // rows, g, H~, b, diag at Newton iteration n (or IT_DEV)
     const int buf = n == IT_DEV ? IT_DEV : (n & 1);

@@ -181,9 +181,12 @@ struct Dev {
   // contacts
   int *cba, *cbb;
   T *cpa[3], *cpb[3], *cn[3], *cdd, *cmu;
+  double *cr0;   // FP32 build: per contact, R(q0 / |q0|) p of its rigid sides (FP64, [6][nc]), set per step
   // joints
   int *jba, *jbb;
   T *jpa[3], *jpb[3], *jaxa[3], *jaxb[3], *je;
+  double *jr0;   // FP32 build: per revolute joint, R(q0 / |q0|) of its anchors, a's axis and b's two
+                 // normals (FP64, [15][nj]), set per step
   // tets: blocks of three rows (kind 0 stable Neo-Hookean; a linear tet is two
   // blocks, kind 1 its normal-strain modes, kind 2 its shears, with the three
   // mode compliances in place of C1, D1, alpha)
@@ -650,15 +653,12 @@ __device__ __forceinline__ void side_diff(const Side<T> &A, const Side<T> &B, T 
 // stored in FP32 (rq) would carry its rounding -- different at every
 // iterate -- into every constraint value.  The FP64 build stores rq in FP64
 // and rotates with it directly, in the oracle's order of operations.
+// rot_start_f64: r0 = R(q0 / |q0|) v, the part fixed for the whole step
+// (FP32 build); rot_iter_from: R(q(u)) v from it.  Contacts keep r0 per side
+// (Dev::cr0, k_contact_r0 at the step's start): the FP64 quaternion
+// arithmetic then runs once per step instead of once per evaluation.
 template <typename T>
-__device__ __forceinline__ void rot_iter_f64(const Dev<T> &D, int b, const double *v, double *out) {
-  if (sizeof(T) == sizeof(double)) {
-    double q[4], R[9];
-    for (int k = 0; k < 4; k++) q[k] = double(D.rq[k][b]);
-    quat_R(q, R);
-    mat3v(R, v, out);
-    return;
-  }
+__device__ __forceinline__ void rot_start_f64(const Dev<T> &D, int b, const double *v, double *r0out) {
   const double w = D.rq0[0][b], x = D.rq0[1][b], y = D.rq0[2][b], z = D.rq0[3][b];
   const double ww = w * w, xx = x * x, yy = y * y, zz = z * z;
   const double n2 = (ww + xx) + (yy + zz);
@@ -670,23 +670,43 @@ __device__ __forceinline__ void rot_iter_f64(const Dev<T> &D, int b, const doubl
                        2 * (x * z - w * y), 2 * (y * z + w * x), (ww - xx) - (yy - zz)};
   double r0[3];
   mat3v(R, v, r0);
+  for (int k = 0; k < 3; k++) r0out[k] = r0[k] * inv;
+}
+
+template <typename T>
+__device__ __forceinline__ void rot_iter_from(const Dev<T> &D, int b, const double *r0, double *out) {
   const T hh = T(0.5) * D.hT;
   const T s[3] = {hh * D.ru[3][b], hh * D.ru[4][b], hh * D.ru[5][b]};
-  const T r0t[3] = {T(r0[0] * inv), T(r0[1] * inv), T(r0[2] * inv)};
+  const T r0t[3] = {T(r0[0]), T(r0[1]), T(r0[2])};
   T c1[3], c2[3];
   cross3(s, r0t, c1);
   cross3(s, c1, c2);
   const T f = T(2) / (T(1) + dot3(s, s));
-  for (int k = 0; k < 3; k++) out[k] = r0[k] * inv + double(f * (c1[k] + c2[k]));
+  for (int k = 0; k < 3; k++) out[k] = __dadd_rn(r0[k], double(f * (c1[k] + c2[k])));
+}
+
+template <typename T>
+__device__ __forceinline__ void rot_iter_f64(const Dev<T> &D, int b, const double *v, double *out) {
+  if (sizeof(T) == sizeof(double)) {
+    double q[4], R[9];
+    for (int k = 0; k < 4; k++) q[k] = double(D.rq[k][b]);
+    quat_R(q, R);
+    mat3v(R, v, out);
+    return;
+  }
+  double r0[3];
+  rot_start_f64(D, b, v, r0);
+  rot_iter_from(D, b, r0, out);
 }
 
 template <typename T>
 __device__ __forceinline__ void point_parts_f64(const Dev<T> &D, int enc, const T *p, double *x0, double *hu,
-                                                double *r) {
+                                                double *r, const double *r0 = nullptr) {
   const double h = D.h;
   if (enc >= 0) {
     const double pd[3] = {double(p[0]), double(p[1]), double(p[2])};
-    rot_iter_f64(D, enc, pd, r);
+    if (r0) rot_iter_from(D, enc, r0, r);
+    else rot_iter_f64(D, enc, pd, r);
     for (int k = 0; k < 3; k++) { x0[k] = double(D.rx0[k][enc]); hu[k] = h * double(D.ru[k][enc]); }
   } else if (enc == -1) {
     for (int k = 0; k < 3; k++) { x0[k] = double(p[k]); hu[k] = 0.0; r[k] = 0.0; }
@@ -697,10 +717,11 @@ __device__ __forceinline__ void point_parts_f64(const Dev<T> &D, int enc, const 
 }
 
 template <typename T>
-__device__ __forceinline__ void gap_f64(const Dev<T> &D, int ea, const T *pa, int eb, const T *pb, double *dd) {
+__device__ __forceinline__ void gap_f64(const Dev<T> &D, int ea, const T *pa, int eb, const T *pb, double *dd,
+                                       const double *r0a = nullptr, const double *r0b = nullptr) {
   double xa[3], ha[3], ra[3], xb[3], hb[3], rb[3];
-  point_parts_f64(D, ea, pa, xa, ha, ra);
-  point_parts_f64(D, eb, pb, xb, hb, rb);
+  point_parts_f64(D, ea, pa, xa, ha, ra, r0a);
+  point_parts_f64(D, eb, pb, xb, hb, rb, r0b);
   for (int k = 0; k < 3; k++) dd[k] = ((xa[k] - xb[k]) + (ha[k] - hb[k])) + (ra[k] - rb[k]);
 }
 
@@ -803,6 +824,25 @@ __device__ __forceinline__ int dlog_slot(const Dev<T> &D, int buf, int force) {
   return n < D.dlog_iters ? n : -1;
 }
 
+// FP32 build, once per step after k_begin_rigid: r0 = R(q0 / |q0|) p of each
+// contact's rigid sides (zero for particle and world sides), [6][nc].
+template <typename T>
+__global__ void k_contact_r0(Dev<T> D) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= D.nc) return;
+  const size_t nc = size_t(D.nc);
+  for (int s = 0; s < 2; s++) {
+    const int enc = s ? D.cbb[c] : D.cba[c];
+    double r0[3] = {0.0, 0.0, 0.0};
+    if (enc >= 0) {
+      const double pd[3] = {double(s ? D.cpb[0][c] : D.cpa[0][c]), double(s ? D.cpb[1][c] : D.cpa[1][c]),
+                            double(s ? D.cpb[2][c] : D.cpa[2][c])};
+      rot_start_f64(D, enc, pd, r0);
+    }
+    for (int k = 0; k < 3; k++) D.cr0[(3 * s + k) * nc + c] = r0[k];
+  }
+}
+
 template <typename T>
 __global__ void k_eval_contacts(Dev<T> D, int buf, int force) {
   if (ls_idle(D)) return;
@@ -821,7 +861,14 @@ __global__ void k_eval_contacts(Dev<T> D, int buf, int force) {
   load_side(D, D.cba[c], pa, A);
   load_side(D, D.cbb[c], pb, B);
   double dd[3];
-  gap_f64(D, D.cba[c], pa, D.cbb[c], pb, dd);
+  if (sizeof(T) == 4) {   // the sides' start-of-step rotations, kept by k_contact_r0
+    const size_t nc = size_t(D.nc);
+    const double r0a[3] = {D.cr0[c], D.cr0[nc + c], D.cr0[2 * nc + c]};
+    const double r0b[3] = {D.cr0[3 * nc + c], D.cr0[4 * nc + c], D.cr0[5 * nc + c]};
+    gap_f64(D, D.cba[c], pa, D.cbb[c], pb, dd, r0a, r0b);
+  } else {
+    gap_f64(D, D.cba[c], pa, D.cbb[c], pb, dd);
+  }
   const T Cn = T((double(n[0]) * dd[0] + double(n[1]) * dd[1] + double(n[2]) * dd[2]) - double(D.cdd[c]));
   // geometric normal row and effective-mass r (Eq. rscaling)
   T Ja[6], Jb[6];
@@ -988,6 +1035,31 @@ __device__ void eval_prismatic(const Dev<T> &D, int ea, int eb, const T *pa, con
   }
 }
 
+// FP32 build, once per step after k_begin_rigid: for each revolute joint,
+// r0 = R(q0 / |q0|) v of a's anchor, b's anchor, a's axis and the two
+// normals of b's axis (zero on a static side), [15][nj].
+template <typename T>
+__global__ void k_joint_r0(Dev<T> D) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= D.nj || D.jkind[j] == 1) return;
+  const size_t nj = size_t(D.nj);
+  const int ea = D.jba[j], eb = D.jbb[j];
+  T axb[3], bl[2][3];
+  for (int k = 0; k < 3; k++) axb[k] = D.jaxb[k][j];
+  basis(axb, bl[0], bl[1]);
+  for (int v = 0; v < 5; v++) {
+    const int enc = (v == 1 || v >= 3) ? eb : ea;
+    double r0[3] = {0.0, 0.0, 0.0};
+    if (enc >= 0) {
+      double vd[3];
+      for (int k = 0; k < 3; k++)
+        vd[k] = double(v == 0 ? D.jpa[k][j] : v == 1 ? D.jpb[k][j] : v == 2 ? D.jaxa[k][j] : bl[v - 3][k]);
+      rot_start_f64(D, enc, vd, r0);
+    }
+    for (int k = 0; k < 3; k++) D.jr0[(3 * v + k) * nj + j] = r0[k];
+  }
+}
+
 template <typename T>
 __global__ void k_eval_joints(Dev<T> D, int buf, int force) {
   if (ls_idle(D)) return;
@@ -1015,8 +1087,18 @@ __global__ void k_eval_joints(Dev<T> D, int buf, int force) {
     eval_prismatic(D, ea, eb, pa, pb, axa, axb, A, B, e, base, buf);
     return;
   }
+  const bool cached = sizeof(T) == 4;   // start-of-step rotations kept by k_joint_r0
+  const size_t nj = size_t(D.nj);
+  auto jr0 = [&](int v, double *r) { for (int k = 0; k < 3; k++) r[k] = D.jr0[(3 * v + k) * nj + j]; };
   double dd[3];
-  gap_f64(D, ea, pa, eb, pb, dd);
+  if (cached) {
+    double r0a[3], r0b[3];
+    jr0(0, r0a);
+    jr0(1, r0b);
+    gap_f64(D, ea, pa, eb, pb, dd, r0a, r0b);
+  } else {
+    gap_f64(D, ea, pa, eb, pb, dd);
+  }
   for (int k = 0; k < 3; k++) {
     T ek[3] = {T(0), T(0), T(0)};
     ek[k] = T(1);
@@ -1038,7 +1120,8 @@ __global__ void k_eval_joints(Dev<T> D, int buf, int force) {
     quat_R(q, R);
     mat3v(R, axa, aw);
     const double ad[3] = {double(axa[0]), double(axa[1]), double(axa[2])};
-    rot_iter_f64(D, ea, ad, awd);
+    if (cached) { double r0[3]; jr0(2, r0); rot_iter_from(D, ea, r0, awd); }
+    else rot_iter_f64(D, ea, ad, awd);
   } else {
     for (int k = 0; k < 3; k++) { aw[k] = axa[k]; awd[k] = double(axa[k]); }
   }
@@ -1051,7 +1134,11 @@ __global__ void k_eval_joints(Dev<T> D, int buf, int force) {
   }
   for (int k = 0; k < 2; k++) {
     double bwd[3], bld[3] = {double(bl[k][0]), double(bl[k][1]), double(bl[k][2])};
-    if (eb >= 0) { mat3v(Rb, bl[k], bw[k]); rot_iter_f64(D, eb, bld, bwd); }
+    if (eb >= 0) {
+      mat3v(Rb, bl[k], bw[k]);
+      if (cached) { double r0[3]; jr0(3 + k, r0); rot_iter_from(D, eb, r0, bwd); }
+      else rot_iter_f64(D, eb, bld, bwd);
+    }
     else for (int m = 0; m < 3; m++) { bw[k][m] = bl[k][m]; bwd[m] = bld[m]; }
     T axb2[3];
     cross3(aw, bw[k], axb2);
