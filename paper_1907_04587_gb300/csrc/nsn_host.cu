@@ -203,6 +203,7 @@ struct nsn_ctx {
   // regenerated every step, Sec. 10): the contacts of the built scene, and its
   // joint and tet counts, so that the next build can match them by key
   std::vector<nsn_contact> built_contacts;
+  std::vector<nsn_contact> col_rec;   // nsn_collide_and_step: the collider's contacts (reused buffer)
   int built_nj = 0, built_nt = 0;   // joints and tet blocks (3 rows each) of the built scene
   // a rebuild keeps the device's state and previous multipliers on the
   // device: the state in ABI order (13 floats per body, the staging layout)
@@ -1573,7 +1574,17 @@ nsn_status ensure_built(nsn_ctx *c) {
   phase_tick(c, NSN_PHASE_RESTORE, t0);
   c->dirty = false;
   c->built_nb = nb;
-  c->built_contacts = c->scene.contacts;
+  {   // the contacts the device holds, for the next rebuild's key matching (copied on host threads)
+    const std::vector<nsn_contact> &src = c->scene.contacts;
+    std::vector<nsn_contact> &dst = c->built_contacts;
+    const size_t n = src.size();
+    dst.resize(n);
+    const int nth = layout_threads((long long)n);
+    parallel_for_threads(nth, [&](int h) {
+      const size_t i0 = n * size_t(h) / size_t(nth), i1 = n * size_t(h + 1) / size_t(nth);
+      if (i1 > i0) std::memcpy(dst.data() + i0, src.data() + i0, sizeof(nsn_contact) * (i1 - i0));
+    });
+  }
   c->built_nj = int(c->scene.joints.size());
   c->built_nt = c->L.nt;
   return NSN_OK;
@@ -2692,16 +2703,21 @@ nsn_status collide_once(nsn_ctx *c, nsn_collider *col) {
     for (int k = 0; k < 5; k++)
       CUDA_TRY(c, cudaMemcpyAsync(c->col_f_h + o[k], src[k], sizeof(float) * w[k] * size_t(found), cudaMemcpyDeviceToHost, cs));
     CUDA_TRY(c, cudaStreamSynchronize(cs));
-    std::vector<nsn_contact> rec(found);
+    std::vector<nsn_contact> &rec = c->col_rec;
+    rec.resize(size_t(found));
     const float *hf = c->col_f_h;
-    for (int i = 0; i < found; i++) {
-      nsn_contact &r = rec[i];
-      r.body_a = c->col_body_h[2 * i];
-      r.body_b = c->col_body_h[2 * i + 1];
-      for (int k = 0; k < 3; k++) { r.pa[k] = hf[3 * i + k]; r.pb[k] = hf[3 * cap + 3 * i + k]; r.n[k] = hf[6 * cap + 3 * i + k]; }
-      r.d = hf[9 * cap + i];
-      r.mu = hf[10 * cap + i];
-    }
+    const int nth = layout_threads(found);
+    parallel_for_threads(nth, [&](int h) {
+      const int i0 = int((long long)found * h / nth), i1 = int((long long)found * (h + 1) / nth);
+      for (int i = i0; i < i1; i++) {
+        nsn_contact &r = rec[i];
+        r.body_a = c->col_body_h[2 * i];
+        r.body_b = c->col_body_h[2 * i + 1];
+        for (int k = 0; k < 3; k++) { r.pa[k] = hf[3 * i + k]; r.pb[k] = hf[3 * cap + 3 * i + k]; r.n[k] = hf[6 * cap + 3 * i + k]; }
+        r.d = hf[9 * cap + i];
+        r.mu = hf[10 * cap + i];
+      }
+    });
     c->scene.contacts.swap(rec);
     c->dirty = true;
     c->phase_ms[NSN_PHASE_COLLIDE] = 0.0;
