@@ -282,31 +282,27 @@ bool finite_all(const float *p, size_t n) {
 // not a node); ids follow the order of each island's lowest body, and a row
 // belongs to the island of its constraint's bodies
 
-int uf_find(std::vector<int> &par, int x) {
-  while (par[x] != x) { par[x] = par[par[x]]; x = par[x]; }
-  return x;
-}
-void uf_union(std::vector<int> &par, int a, int b) {
-  if (a < 0 || b < 0) return;
-  a = uf_find(par, a); b = uf_find(par, b);
-  if (a == b) return;
-  if (a < b) par[b] = a; else par[a] = b;
-}
-
 void find_islands(const HostScene &S, Layout &L, int nb) {
-  std::vector<int> par(nb);
-  for (int i = 0; i < nb; i++) par[i] = i;
-  for (const auto &r : S.contacts) uf_union(par, r.body_a, r.body_b);
-  for (const auto &r : S.joints) uf_union(par, r.body_a, r.body_b);
-  for (const auto &r : S.tets)
-    for (int q = 1; q < 4; q++) uf_union(par, r.v[0], r.v[q]);
-  for (const auto &r : S.ltets)
-    for (int q = 1; q < 4; q++) uf_union(par, r.v[0], r.v[q]);
+  // components on host threads, each rooted at its smallest body
+  const long long nc = (long long)S.contacts.size(), nj = (long long)S.joints.size(),
+                  nt = (long long)S.tets.size(), nl = (long long)S.ltets.size(), ne = nc + nj + nt + nl;
+  std::vector<int> &root = L.s_aux;
+  components_min_root(nb, layout_threads(ne), [&](int t, int nth, auto &&unite) {
+    const long long e0 = ne * t / nth, e1 = ne * (t + 1) / nth;
+    for (long long e = e0; e < e1; e++) {
+      if (e < nc) { const auto &r = S.contacts[size_t(e)]; unite(r.body_a, r.body_b); }
+      else if (e < nc + nj) { const auto &r = S.joints[size_t(e - nc)]; unite(r.body_a, r.body_b); }
+      else {
+        const nsn_tet &r = e < nc + nj + nt ? S.tets[size_t(e - nc - nj)] : S.ltets[size_t(e - nc - nj - nt)];
+        for (int q = 1; q < 4; q++) unite(r.v[0], r.v[q]);
+      }
+    }
+  }, root);
   std::vector<int> id(nb, -1);
   L.body_isl.assign(nb, 0);
   L.ni = 0;
   for (int i = 0; i < nb; i++) {
-    const int r = uf_find(par, i);
+    const int r = root[size_t(i)];
     if (id[r] < 0) id[r] = L.ni++;
     L.body_isl[i] = id[r];
   }

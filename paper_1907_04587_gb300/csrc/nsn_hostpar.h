@@ -4,6 +4,7 @@
 // C++17 (no CUDA), so that the CPU tests compile it on its own.
 #pragma once
 #include <algorithm>
+#include <atomic>
 #include <condition_variable>
 #include <mutex>
 #include <thread>
@@ -157,6 +158,46 @@ void order_by(int n, int K, const Key &key, std::vector<int> &o, std::vector<int
     const int i0 = int((long long)n * t / nth), i1 = int((long long)n * (t + 1) / nth);
     int *ct = start.data() + t;
     for (int i = i0; i < i1; i++) o[ct[size_t(k[i]) * nth]++] = i;
+  });
+}
+
+// Connected components of nodes 0 .. n-1 under the unions that edges(fn)
+// reports (fn(a, b) for every edge; negative ends are ignored), on host
+// threads: lock-free union-find whose root is always the smallest node of
+// its component (a root is hooked only under a smaller root, with a
+// compare-and-swap; finds halve their paths), so the result does not depend
+// on the order of the unions.  root[i] = the smallest node of i's component.
+// each_edge(t, nth, fn) calls fn for thread t's share of the edges.
+template <typename EachEdge>
+void components_min_root(int n, int nth, const EachEdge &each_edge, std::vector<int> &root) {
+  std::vector<std::atomic<int>> par(static_cast<size_t>(std::max(n, 1)));
+  for (int i = 0; i < n; i++) par[size_t(i)].store(i, std::memory_order_relaxed);
+  auto find = [&](int x) {
+    for (;;) {
+      int p = par[size_t(x)].load(std::memory_order_acquire);
+      if (p == x) return x;
+      const int g = par[size_t(p)].load(std::memory_order_acquire);
+      if (g != p) par[size_t(x)].compare_exchange_weak(p, g, std::memory_order_acq_rel);
+      x = g;
+    }
+  };
+  auto unite = [&](int a, int b) {
+    if (a < 0 || b < 0) return;
+    for (;;) {
+      a = find(a);
+      b = find(b);
+      if (a == b) return;
+      if (a > b) std::swap(a, b);   // hook the larger root b under the smaller a
+      int expect = b;
+      if (par[size_t(b)].compare_exchange_strong(expect, a, std::memory_order_acq_rel)) return;
+    }
+  };
+  parallel_for_threads(nth, [&](int t) { each_edge(t, nth, unite); });
+  root.resize(size_t(n));
+  const int nr = layout_threads(n);
+  parallel_for_threads(nr, [&](int t) {
+    const int i0 = int((long long)n * t / nr), i1 = int((long long)n * (t + 1) / nr);
+    for (int i = i0; i < i1; i++) root[size_t(i)] = find(i);
   });
 }
 

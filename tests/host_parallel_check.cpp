@@ -1,8 +1,8 @@
 // Checks the host-side parallel passes of the layout build (nsn_hostpar.h)
 // against their sequential definitions: the stable counting sort against
-// std::stable_sort, the exclusive scan against a running sum, every item of
-// a pass run exactly once, from two calling threads at once and from inside
-// a pass.  Prints "ok" and exits 0, else names the first failure.
+// std::stable_sort, the exclusive scan against a running sum, the parallel
+// union-find against a sequential one, every item of a pass run exactly
+// once, from two calling threads at once and from inside a pass.  Prints "ok" and exits 0, else names the first failure.
 #include <algorithm>
 #include <atomic>
 #include <cstdio>
@@ -39,6 +39,31 @@ int main() {
     parallel_for_threads(n, [&](int q) { hit[size_t(q)]++; });
     for (int q = 0; q < n; q++)
       if (hit[size_t(q)] != 1) { std::printf("item %d of %d ran %d times\n", q, n, hit[size_t(q)]); return 1; }
+  }
+  // components: against a sequential union-find (root = smallest node)
+  for (int trial = 0; trial < 12; trial++) {
+    const int n = 1000 + int(rng() % 200000), m = int(rng() % (2 * n));
+    std::vector<std::pair<int, int>> edges(static_cast<size_t>(m));
+    for (auto &e : edges) {
+      e.first = int(rng() % n) - (rng() % 50 == 0 ? n : 0);   // some ends negative (ignored)
+      e.second = trial % 2 ? int(rng() % n) : std::min(n - 1, std::max(0, e.first + int(rng() % 9) - 4));
+    }
+    std::vector<int> ref(static_cast<size_t>(n));
+    for (int i = 0; i < n; i++) ref[size_t(i)] = i;
+    auto f = [&](int x) { while (ref[size_t(x)] != x) x = ref[size_t(x)] = ref[size_t(ref[size_t(x)])]; return x; };
+    for (auto &e : edges) {
+      if (e.first < 0 || e.second < 0) continue;
+      int a = f(e.first), b = f(e.second);
+      if (a == b) continue;
+      if (a < b) ref[size_t(b)] = a; else ref[size_t(a)] = b;
+    }
+    for (int i = 0; i < n; i++) ref[size_t(i)] = f(i);
+    std::vector<int> root;
+    components_min_root(n, layout_threads(m), [&](int t, int nth, auto &&unite) {
+      const long long e0 = (long long)m * t / nth, e1 = (long long)m * (t + 1) / nth;
+      for (long long e = e0; e < e1; e++) unite(edges[size_t(e)].first, edges[size_t(e)].second);
+    }, root);
+    if (root != ref) { std::printf("components differ: n %d m %d\n", n, m); return 1; }
   }
   std::atomic<int> bad{0};
   auto user = [&] {

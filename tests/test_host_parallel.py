@@ -1,9 +1,10 @@
 """The layout build's host-side parallel passes (csrc/nsn_hostpar.h: the
-worker pool, the exclusive scan and the stable counting sort that order
-islands, bodies and constraints) equal their sequential definitions: a C++
-driver compiled with the host compiler checks them against std::stable_sort
-and a running sum, with the pool called from two threads at once and from
-inside a pass."""
+worker pool, the exclusive scan, the stable counting sort that orders
+islands, bodies and constraints, and the union-find that finds the islands)
+equal their sequential definitions: a C++ driver compiled with the host
+compiler checks them against std::stable_sort, a running sum and a
+sequential union-find, with the pool called from two threads at once and
+from inside a pass."""
 import os
 import shutil
 import subprocess
