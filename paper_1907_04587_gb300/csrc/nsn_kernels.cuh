@@ -2430,41 +2430,6 @@ __device__ __forceinline__ T res_z_new(const RV4<T> &v, T api, T alpha) {
   return rn_add(v.a, -rn_mul(rn_mul(alpha, v.b), api));
 }
 
-// Error-free transformations in FP32: a + b = s + e exactly (Knuth's
-// TwoSum), a b = p + e exactly (the FMA form of TwoProduct, Ogita, Rump and
-// Oishi, "Accurate sum and dot product", 2005).
-__device__ __forceinline__ void ef_two_sum(float a, float b, float &s, float &e) {
-  s = __fadd_rn(a, b);
-  const float bb = __fsub_rn(s, a);
-  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-}
-__device__ __forceinline__ void ef_two_prod(float a, float b, float &p, float &e) {
-  p = __fmul_rn(a, b);
-  e = __fmaf_rn(a, b, -p);
-}
-
-// ApTPAp = d2 + 2 beta d3 + beta^2 d5 of FP32 terms, for the FP32 build: the
-// products are split exactly (2 beta d3 = ph + pl; beta^2 = bh + bl, then
-// bh d5 exactly and bl d5 rounded: a relative error of 2^-48 of that term)
-// and the sum is carried in two FP32 words, so the cancellation of the
-// recurrence costs no more than in FP64 (a 48-bit significand against 53)
-// while the arithmetic stays on the FP32 pipes: on GB300 each FP64
-// instruction of a warp occupies the narrow FP64 pipe for many cycles, on
-// the path between the resident CR's two barriers.  Returns the sum rounded
-// to FP32.
-__device__ __forceinline__ float res_apap_f32(float d2, float d3, float d5, float beta) {
-  float ph, pl, bh, bl, qh, ql, s, e, s2, e2;
-  ef_two_prod(beta, d3, ph, pl);
-  ph = 2.0f * ph; pl = 2.0f * pl;                  // exact
-  ef_two_prod(beta, beta, bh, bl);
-  ef_two_prod(bh, d5, qh, ql);
-  ql = __fmaf_rn(bl, d5, ql);
-  ef_two_sum(d2, ph, s, e);
-  ef_two_sum(s, qh, s2, e2);
-  const float lo = __fadd_rn(__fadd_rn(e, pl), __fadd_rn(e2, ql));
-  return __fadd_rn(s2, lo);
-}
-
 // The CR scalars of island li at iteration k (the recurrence and stop rules
 // of k_cr_scalars_isl), by the warp that finished the island's last task of
 // this iteration: the island's task sums are reduced by the warp in a fixed
@@ -2474,7 +2439,9 @@ __device__ __forceinline__ float res_apap_f32(float d2, float d3, float d5, floa
 // single-precision value and its FP64 image order the same way).  ApTPAp =
 // d2 + 2 beta d3 + beta^2 d5, the recurrence that cancels, is FP64 in the
 // FP64 build and carried in two FP32 words in the FP32 build
-// (res_apap_f32).  In the FP32 build beta and alpha are what the update
+// (nsn_apap_f32, nsn_bits.h: error-free products and sums, rounded once; the
+// FP64 pipe of GB300 is narrow, and this step lies on the path between the
+// resident CR's two barriers).  In the FP32 build beta and alpha are what the update
 // applies, FP32 values: beta = rho / rho_prev and alpha = rho / ApTPAp are
 // correctly rounded FP32 divisions of FP32-exact operands (rho and rho_prev
 // are FP32 sums), and ApTPAp is taken with that FP32 beta, i.e. for the Ap
@@ -2508,7 +2475,7 @@ __device__ __forceinline__ bool res_scalars_warp(const ResSmem<T> &S, int li, in
         if (!(rho > T(0)) || !(rho_prev > T(0))) st = true;
         else {
           beta = rho / rho_prev;
-          ap = res_apap_f32(float(a[1]), float(a[2]), float(a[4]), float(beta));
+          ap = nsn_apap_f32(float(a[1]), float(a[2]), float(a[4]), float(beta));
         }
       }
       if (!st && ap > 0.0f) alpha = T(float(rho) / ap);
