@@ -10,6 +10,9 @@
 #include <thread>
 #include <vector>
 
+#include <sys/types.h>
+#include <unistd.h>
+
 namespace nsn {
 
 // Host worker threads kept for the life of the process: a layout pass hands
@@ -24,7 +27,9 @@ class HostPool {
     static HostPool pool;
     return pool;
   }
-  int workers() const { return int(th_.size()); }
+  // workers of this process (0 in a child forked after they started: they do
+  // not exist there, and its passes run on the calling thread)
+  int workers() const { return pid_ == getpid() ? int(th_.size()) : 0; }
   // false: the pool is busy, the caller runs the items itself
   bool run(int n, void (*call)(const void *, int), const void *obj) {
     std::unique_lock<std::mutex> busy(pass_, std::try_to_lock);
@@ -40,6 +45,10 @@ class HostPool {
     return true;
   }
   ~HostPool() {
+    if (pid_ != getpid()) {   // a forked child: the threads are not this process's
+      for (std::thread &x : th_) x.detach();
+      return;
+    }
     {
       std::lock_guard<std::mutex> g(m_);
       stop_ = true;
@@ -49,7 +58,7 @@ class HostPool {
   }
 
  private:
-  HostPool() {
+  HostPool() : pid_(getpid()) {
     const int hw = std::max(1, int(std::thread::hardware_concurrency()));
     const int nw = std::min(hw, 16) - 1;
     for (int w = 1; w <= nw; w++) th_.emplace_back([this, w] { loop(w); });
@@ -72,6 +81,7 @@ class HostPool {
       if (--left_ == 0) done_.notify_one();
     }
   }
+  pid_t pid_;
   std::vector<std::thread> th_;
   std::mutex pass_, m_;
   std::condition_variable cv_, done_;

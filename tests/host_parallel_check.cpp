@@ -2,12 +2,16 @@
 // against their sequential definitions: the stable counting sort against
 // std::stable_sort, the exclusive scan against a running sum, the parallel
 // union-find against a sequential one, every item of a pass run exactly
-// once, from two calling threads at once and from inside a pass.  Prints "ok" and exits 0, else names the first failure.
+// once, from two calling threads at once, from inside a pass and in a child
+// forked after the workers started.  Prints "ok" and exits 0, else names the first failure.
 #include <algorithm>
 #include <atomic>
 #include <cstdio>
 #include <random>
 #include <vector>
+
+#include <sys/wait.h>
+#include <unistd.h>
 
 #include "nsn_hostpar.h"
 
@@ -83,6 +87,20 @@ int main() {
     outer[size_t(q)] = in[0] + in[1] + in[2] + in[3];
   });
   for (int x : outer) bad += x != 4;
+  // a child forked after the workers started runs its passes on its own thread
+  {
+    const pid_t child = fork();
+    if (child == 0) {
+      std::vector<int> hit(12, 0);
+      parallel_for_threads(12, [&](int q) { hit[size_t(q)]++; });
+      int ok = 1;
+      for (int x : hit) ok &= x == 1;
+      _exit(ok ? 0 : 1);
+    }
+    int status = 0;
+    waitpid(child, &status, 0);
+    if (!WIFEXITED(status) || WEXITSTATUS(status) != 0) { std::printf("forked child failed\n"); return 1; }
+  }
   if (bad) { std::printf("%d items ran other than once\n", bad.load()); return 1; }
   std::printf("ok\n");
   return 0;
